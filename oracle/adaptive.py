@@ -33,6 +33,7 @@ from .bddc import CoarseDof
 from .levels import Level
 
 NULL_TOL = 1e-10
+NULL_RANK_TOL = 1e-6
 DROP_TOL = 1e-12
 
 
@@ -102,12 +103,15 @@ class PairProblem:
         Z[:ns_, :Zs.shape[1]] = Zs
         Z[ns_:, Zs.shape[1]:] = Zt
         if Z.shape[1]:
+            # Z has orthonormal columns, so a combination that leaves range Pi
+            # has (I - Pi) Z c of order one; the computed null vectors are only
+            # accurate to eps ||S|| / gap (about 1e-9 at a coefficient contrast
+            # of 1e6), hence the loose rank cut.
             M = (np.eye(n) - Pi) @ Z
             _, sv, Vt = np.linalg.svd(M)
-            smax = max(np.abs(Z).max(), 1.0)
-            rank = int(np.sum(sv > 1e-10 * smax))
+            rank = int(np.sum(sv > NULL_RANK_TOL))
             cnull = Vt[rank:].T
-            N = _orth_rows((Z @ cnull).T) if cnull.shape[1] else np.zeros((n, 0))
+            N = _orth_rows((Pi @ Z @ cnull).T) if cnull.shape[1] else np.zeros((n, 0))
         else:
             N = np.zeros((n, 0))
         Pib = np.eye(n) - N @ N.T
