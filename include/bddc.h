@@ -1,0 +1,222 @@
+/*
+ * bddc.h - C ABI of the GB300 adaptive-multilevel BDDC library (libbddc.so).
+ *
+ * The method is the adaptive-multilevel BDDC preconditioner of Sousedik and
+ * Mandel, "On Adaptive-Multilevel BDDC", applied inside preconditioned
+ * conjugate gradients to the Q1 model problem
+ *
+ *     -div(k grad u) = f  on the unit square,  u = 0 on the boundary    (Sec. 2, eq. 1)
+ *
+ * Conventions shared by every entry point:
+ *   - Mesh: nx * nx square Q1 elements, h = 1/nx.  Element (ei, ej) has flat
+ *     index e = ej*nx + ei.  Free node (i, j), 1 <= i, j <= nx-1, has global
+ *     index g = (j-1)*(nx-1) + (i-1); a level-1 vector has n = (nx-1)^2 entries.
+ *   - Every function returns an int status: BDDC_OK (0) or a negative
+ *     BDDC_E_* code; bddc_last_error() then gives a message for the calling
+ *     thread.  No function aborts, exits or traps.
+ *   - Host arrays passed in are copied; the caller keeps ownership.  Device
+ *     pointers (suffix _dev) must be device memory on the current CUDA
+ *     device, 8-byte aligned; they are only read / written inside the call's
+ *     stream order.  The library owns every allocation it makes and frees it in
+ *     bddc_destroy().
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ */
+#ifndef BDDC_H
+#define BDDC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bddc_ctx bddc_ctx;        /* one problem: mesh, coefficient, hierarchy */
+typedef struct bddc_server bddc_server;  /* request loop over resident problems */
+
+enum {
+    BDDC_OK = 0,
+    BDDC_E_ARG = -1,      /* invalid argument or unsupported size */
+    BDDC_E_NOMEM = -2,    /* device allocation failed or over the HBM budget */
+    BDDC_E_NOT_SPD = -3,  /* a Cholesky pivot was not positive */
+    BDDC_E_NOCONV = -4,   /* PCG reached maxit; x holds the last iterate */
+    BDDC_E_TIMEOUT = -5,  /* a bounded wait ran out */
+    BDDC_E_CUDA = -6,     /* a CUDA runtime call failed */
+    BDDC_E_BUSY = -7,     /* server cannot admit the request now */
+    BDDC_E_STATE = -8     /* call not valid in the object's current state */
+};
+
+/* Constraint (coarse DOF) families, Sec. 2 and Tables 1, 6. */
+enum {
+    BDDC_CONSTR_CORNERS = 0,        /* corners only ("c") */
+    BDDC_CONSTR_CORNERS_EDGES = 1,  /* corners + one arithmetic average per edge ("c+e") */
+    BDDC_CONSTR_ADAPTIVE = 2,       /* corners + Theorem 2 edge constraints for tau */
+    BDDC_CONSTR_ALL_INTERFACE = 3   /* every interface DOF coarse: the exact preconditioner */
+};
+
+/* Storage / arithmetic precision of the substructure operators in the apply.
+ * The top-level coarse solve and PCG are FP64 in every mode. */
+enum { BDDC_PREC_FP64 = 0, BDDC_PREC_FP32 = 1, BDDC_PREC_BF16 = 2 };
+
+typedef struct {
+    int32_t nx;           /* elements per side (square mesh) */
+    int32_t ny;           /* must equal nx */
+} bddc_mesh;
+
+typedef struct {
+    const int32_t *elem_to_sub;   /* [nx*nx] host: level-1 substructure of each element */
+    int32_t n_sub1;
+    const int32_t *sub1_to_sub2;  /* [n_sub1] host: level-2 substructure, or NULL for 2 levels */
+    int32_t n_sub2;
+} bddc_decomp;
+
+typedef struct {
+    int32_t constraints;          /* BDDC_CONSTR_* on level 1 */
+    int32_t constraints_level2;   /* BDDC_CONSTR_* on level 2 (3 levels), -1 = same as level 1 */
+    int32_t precision;            /* BDDC_PREC_* used by bddc_apply / bddc_pcg_solve */
+    int32_t reserved;
+    size_t hbm_budget;            /* bytes; 0 = unlimited */
+} bddc_opts;
+
+typedef struct {
+    int32_t iters;        /* PCG iterations taken */
+    int32_t status;       /* BDDC_OK or BDDC_E_NOCONV */
+    double relres;        /* recursive residual ||r_k|| / ||b|| */
+    double relres_true;   /* ||b - A x|| / ||b|| recomputed in FP64 */
+    double kappa_est;     /* Lanczos estimate lambda_max / lambda_min (Tables 1-7) */
+    double lam_min, lam_max;
+} bddc_solve_info;
+
+typedef struct {
+    int32_t levels;
+    int32_t n_dof[4];             /* DOFs of level 1..levels (n_dof[levels-1] = top) */
+    int32_t n_sub[3];             /* substructures of BDDC levels 1..levels-1 */
+    int32_t n_edges[3];           /* edges of BDDC levels 1..levels-1 */
+    int32_t n_corners[3];
+    double omega_tilde;           /* indicator of eq. 12, product over levels (0 if not adaptive) */
+    double omega_level[3];        /* max over edges of omega^{st} per level */
+    double setup_ms;              /* wall time of bddc_setup */
+    size_t device_bytes;          /* bytes the context holds on the device */
+} bddc_info;
+
+/*
+ * bddc_setup - build the hierarchy of Algorithm 2 on the GPU.
+ *
+ * Assembles the Q1 substructure matrices (Sec. 2), classifies interface,
+ * corner and edge DOFs, factors the interior problems (batched FP64
+ * Cholesky), solves the per-edge generalized eigenproblems of Theorem 1 and
+ * adds the Theorem 2 constraints with lambda > tau (eq. 14), builds the
+ * coarse basis and the level-(l+1) problem (Sec. 2.1), and factors the top
+ * level directly.
+ *   mesh      : mesh size (ny must equal nx).
+ *   k_elem    : host [nx*nx] element coefficients, > 0.
+ *   decomp    : host decomposition; substructures must be non-empty and every
+ *               floating substructure must own at least one corner.
+ *   levels    : 2 or 3.
+ *   tau       : adaptive threshold (ignored unless a level uses ADAPTIVE).
+ *   opts      : may be NULL (corners + edges, FP64).
+ *   stream    : stream for all device work of the setup.
+ *   out       : receives the context; *out is NULL on error.
+ * Errors: BDDC_E_ARG, BDDC_E_NOMEM, BDDC_E_NOT_SPD (message names level and
+ * substructure), BDDC_E_CUDA.
+ */
+int bddc_setup(const bddc_mesh *mesh, const double *k_elem, const bddc_decomp *decomp,
+               int levels, double tau, const bddc_opts *opts, void *stream, bddc_ctx **out);
+
+/*
+ * bddc_apply - z = M^{-1} r, one application of Algorithm 1 (eqs. 4-11) on
+ * every level, all substructures at once.
+ *   r_dev, z_dev : device [nrhs][ld] FP64, column j at offset j*ld; ld >= n.
+ *                  r and z must not overlap.
+ *   nrhs         : number of right-hand sides (>= 1).
+ * Runs asynchronously in `stream`; the context serialises its own scratch,
+ * so calls on one context must not run concurrently from several threads.
+ */
+int bddc_apply(bddc_ctx *ctx, const double *r_dev, double *z_dev, int nrhs, int64_t ld,
+               void *stream);
+
+/*
+ * bddc_pcg_solve - PCG (Sec. 5) from x0 = 0 with the BDDC preconditioner until
+ * ||r||_2 <= rtol ||b||_2 for the recursive and the true residual, or maxit.
+ *   b_dev, x_dev : device [nrhs][ld] FP64; each column solved independently.
+ *   info_host    : host [nrhs] results (may be NULL).
+ * Returns BDDC_E_NOCONV if any column reached maxit (x holds the last iterate).
+ * Synchronises `stream` before returning.
+ */
+int bddc_pcg_solve(bddc_ctx *ctx, const double *b_dev, double *x_dev, int nrhs, int64_t ld,
+                   double rtol, int maxit, bddc_solve_info *info_host, void *stream);
+
+/*
+ * bddc_pcg_solve_host - same as bddc_pcg_solve with HOST arrays b_host and
+ * x_host ([nrhs][ld]); the host<->device copies are part of the call.
+ */
+int bddc_pcg_solve_host(bddc_ctx *ctx, const double *b_host, double *x_host, int nrhs,
+                        int64_t ld, double rtol, int maxit, bddc_solve_info *info_host,
+                        void *stream);
+
+/* bddc_set_precision - choose the apply precision (BDDC_PREC_*) of a context. */
+int bddc_set_precision(bddc_ctx *ctx, int precision);
+
+/*
+ * bddc_query - sizes and the adaptive selection of a context.
+ *   info                : host, may be NULL.
+ *   level               : BDDC level 1..levels-1 for the per-edge arrays.
+ *   n_selected_per_edge : host [n_edges[level-1]] or NULL: n^{st} (Theorem 2).
+ *   edge_eigs, max_eigs : host [n_edges * max_eigs] or NULL: the largest
+ *                         eigenvalues of eq. 13 per edge, descending, 0-padded.
+ *   edge_pairs          : host [n_edges * 2] or NULL: (s, t) of each edge.
+ * Edges are numbered by their substructure pair (s < t), then by lowest DOF.
+ */
+int bddc_query(const bddc_ctx *ctx, bddc_info *info, int level, int32_t *n_selected_per_edge,
+               double *edge_eigs, int max_eigs, int32_t *edge_pairs);
+
+/*
+ * bddc_operator - y = A x for the level-1 Q1 operator (device FP64 [n]); the
+ * matrix-free SpMV used by PCG.
+ */
+int bddc_operator(bddc_ctx *ctx, const double *x_dev, double *y_dev, void *stream);
+
+void bddc_destroy(bddc_ctx *ctx);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char *bddc_last_error(void);
+
+/* -------------------------------------------------------------------------
+ * Serving loop (no counterpart in the paper).
+ *
+ * A server owns a worker thread and CUDA streams.  Requests (a context plus
+ * one or more right-hand sides) are admitted while their device memory fits
+ * the HBM budget and a slot is free; admitted requests run concurrently on
+ * separate streams, so work of requests that arrive while others run
+ * overlaps on the device.  Each right-hand side is an independent PCG solve,
+ * so its result does not depend on what else is in flight.
+ * ------------------------------------------------------------------------- */
+
+/* bddc_server_create - hbm_budget in bytes for request buffers (0 = unlimited);
+ * max_slots concurrent requests (>= 1). */
+int bddc_server_create(size_t hbm_budget, int max_slots, bddc_server **out);
+
+/*
+ * bddc_submit - enqueue a request; non-blocking.
+ *   b_host : host [nrhs][n] (copied before return).
+ *   ticket : receives the request id.
+ * Returns BDDC_E_BUSY when the request alone exceeds the budget.
+ */
+int bddc_submit(bddc_server *srv, bddc_ctx *ctx, const double *b_host, int nrhs, double rtol,
+                int maxit, uint64_t *ticket);
+
+/*
+ * bddc_wait - wait for a request; x_host [nrhs][n] and info_host [nrhs] may be
+ * NULL.  timeout_ms < 0 waits forever; BDDC_E_TIMEOUT if it runs out (the
+ * request stays in flight).  Also reports the request's latency from submit
+ * to completion in *latency_ms (may be NULL).
+ */
+int bddc_wait(bddc_server *srv, uint64_t ticket, double *x_host, bddc_solve_info *info_host,
+              double *latency_ms, int timeout_ms);
+
+void bddc_server_destroy(bddc_server *srv);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BDDC_H */

@@ -1,0 +1,271 @@
+"""Thin ctypes binding of libbddc.so (argument marshalling only).
+
+Every numerical step runs in the CUDA library; this module converts Python
+arguments to the C structs of ``include/bddc.h`` and passes device pointers of
+``torch`` CUDA tensors.  It raises if the library is missing: there is no
+fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libbddc.so")
+
+BDDC_OK = 0
+ERRORS = {-1: "BDDC_E_ARG", -2: "BDDC_E_NOMEM", -3: "BDDC_E_NOT_SPD", -4: "BDDC_E_NOCONV",
+          -5: "BDDC_E_TIMEOUT", -6: "BDDC_E_CUDA", -7: "BDDC_E_BUSY", -8: "BDDC_E_STATE"}
+CONSTRAINTS = {"corners": 0, "corners+edges": 1, "adaptive": 2, "all": 3}
+PRECISION = {"fp64": 0, "fp32": 1, "bf16": 2}
+
+SYMBOLS = ["bddc_setup", "bddc_apply", "bddc_pcg_solve", "bddc_pcg_solve_host",
+           "bddc_set_precision", "bddc_query", "bddc_operator", "bddc_destroy",
+           "bddc_last_error", "bddc_server_create", "bddc_submit", "bddc_wait",
+           "bddc_server_destroy"]
+
+
+class Mesh(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32)]
+
+
+class Decomp(C.Structure):
+    _fields_ = [("elem_to_sub", C.POINTER(C.c_int32)), ("n_sub1", C.c_int32),
+                ("sub1_to_sub2", C.POINTER(C.c_int32)), ("n_sub2", C.c_int32)]
+
+
+class Opts(C.Structure):
+    _fields_ = [("constraints", C.c_int32), ("constraints_level2", C.c_int32),
+                ("precision", C.c_int32), ("reserved", C.c_int32), ("hbm_budget", C.c_size_t)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("status", C.c_int32), ("relres", C.c_double),
+                ("relres_true", C.c_double), ("kappa_est", C.c_double),
+                ("lam_min", C.c_double), ("lam_max", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Info(C.Structure):
+    _fields_ = [("levels", C.c_int32), ("n_dof", C.c_int32 * 4), ("n_sub", C.c_int32 * 3),
+                ("n_edges", C.c_int32 * 3), ("n_corners", C.c_int32 * 3),
+                ("omega_tilde", C.c_double), ("omega_level", C.c_double * 3),
+                ("setup_ms", C.c_double), ("device_bytes", C.c_size_t)]
+
+
+_lib = None
+
+
+def load():
+    """Load libbddc.so (built in-tree by ``__graft_entry__.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libbddc.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+    lib = C.CDLL(LIB_PATH)
+    vp, i32, i64, dp = C.c_void_p, C.c_int, C.c_int64, C.c_double
+    lib.bddc_setup.argtypes = [C.POINTER(Mesh), vp, C.POINTER(Decomp), i32, dp, C.POINTER(Opts),
+                               vp, C.POINTER(vp)]
+    lib.bddc_apply.argtypes = [vp, vp, vp, i32, i64, vp]
+    lib.bddc_pcg_solve.argtypes = [vp, vp, vp, i32, i64, dp, i32, vp, vp]
+    lib.bddc_pcg_solve_host.argtypes = [vp, vp, vp, i32, i64, dp, i32, vp, vp]
+    lib.bddc_set_precision.argtypes = [vp, i32]
+    lib.bddc_query.argtypes = [vp, C.POINTER(Info), i32, vp, vp, i32, vp]
+    lib.bddc_operator.argtypes = [vp, vp, vp, vp]
+    lib.bddc_destroy.argtypes = [vp]
+    lib.bddc_destroy.restype = None
+    lib.bddc_last_error.restype = C.c_char_p
+    lib.bddc_server_create.argtypes = [C.c_size_t, i32, C.POINTER(vp)]
+    lib.bddc_submit.argtypes = [vp, vp, vp, i32, dp, i32, C.POINTER(C.c_uint64)]
+    lib.bddc_wait.argtypes = [vp, C.c_uint64, vp, vp, C.POINTER(C.c_double), i32]
+    lib.bddc_server_destroy.argtypes = [vp]
+    lib.bddc_server_destroy.restype = None
+    _lib = lib
+    return lib
+
+
+class BDDCError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s: %s" % (ERRORS.get(code, code), msg))
+        self.code = code
+
+
+def _check(code):
+    if code != BDDC_OK:
+        raise BDDCError(code, load().bddc_last_error().decode())
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr())
+
+
+class Problem:
+    """One problem (mesh, coefficient, decomposition) set up on the GPU."""
+
+    def __init__(self, nx, k, elem_to_sub, n_sub1, levels=2, tau=math.inf,
+                 constraints="corners+edges", precision="fp64", sub1_to_sub2=None, n_sub2=0,
+                 constraints_level2=None, hbm_budget=0, stream=None):
+        lib = load()
+        self._lib = lib
+        self.nx = int(nx)
+        self.n = (self.nx - 1) ** 2
+        k = np.ascontiguousarray(k, dtype=np.float64)
+        e2s = np.ascontiguousarray(elem_to_sub, dtype=np.int32)
+        self._keep = [k, e2s]
+        s2 = None
+        if sub1_to_sub2 is not None:
+            s2 = np.ascontiguousarray(sub1_to_sub2, dtype=np.int32)
+            self._keep.append(s2)
+        dec = Decomp(e2s.ctypes.data_as(C.POINTER(C.c_int32)), int(n_sub1),
+                     s2.ctypes.data_as(C.POINTER(C.c_int32)) if s2 is not None else None,
+                     int(n_sub2))
+        opts = Opts(CONSTRAINTS[constraints],
+                    -1 if constraints_level2 is None else CONSTRAINTS[constraints_level2],
+                    PRECISION[precision], 0, int(hbm_budget))
+        h = C.c_void_p()
+        _check(lib.bddc_setup(C.byref(Mesh(self.nx, self.nx)), k.ctypes.data_as(C.c_void_p),
+                              C.byref(dec), int(levels), float(tau), C.byref(opts),
+                              C.c_void_p(_stream_ptr(stream)), C.byref(h)))
+        self.h = h
+
+    @classmethod
+    def from_workload(cls, wl, precision="fp64", **kw):
+        return cls(wl.nx, wl.k, wl.elem_to_sub, wl.n_sub1, wl.levels, wl.tau, wl.constraints,
+                   precision, wl.sub1_to_sub2, wl.n_sub2, **kw)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.bddc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_precision(self, precision):
+        _check(self._lib.bddc_set_precision(self.h, PRECISION[precision]))
+
+    def apply(self, r, z=None, stream=None):
+        """z = M^{-1} r for a CUDA float64 tensor r of shape [n] or [nrhs, n]."""
+        import torch
+        r = r.contiguous()
+        if z is None:
+            z = torch.empty_like(r)
+        nrhs = 1 if r.dim() == 1 else r.shape[0]
+        _check(self._lib.bddc_apply(self.h, _ptr(r), _ptr(z), nrhs, self.n,
+                                    C.c_void_p(_stream_ptr(stream))))
+        return z
+
+    def operator(self, x, y=None, stream=None):
+        import torch
+        if y is None:
+            y = torch.empty_like(x)
+        _check(self._lib.bddc_operator(self.h, _ptr(x), _ptr(y), C.c_void_p(_stream_ptr(stream))))
+        return y
+
+    def solve(self, b, x=None, rtol=1e-8, maxit=1000, stream=None, check=True):
+        """PCG on device tensors; returns (x, [info dicts])."""
+        import torch
+        b = b.contiguous()
+        if x is None:
+            x = torch.empty_like(b)
+        nrhs = 1 if b.dim() == 1 else b.shape[0]
+        infos = (SolveInfo * nrhs)()
+        code = self._lib.bddc_pcg_solve(self.h, _ptr(b), _ptr(x), nrhs, self.n, float(rtol),
+                                        int(maxit), C.cast(infos, C.c_void_p),
+                                        C.c_void_p(_stream_ptr(stream)))
+        if check and code not in (BDDC_OK, -4):
+            _check(code)
+        return x, [i.as_dict() for i in infos]
+
+    def solve_host(self, b, rtol=1e-8, maxit=1000):
+        """PCG with host numpy arrays; the copies are part of the call."""
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        x = np.empty_like(b)
+        nrhs = 1 if b.ndim == 1 else b.shape[0]
+        infos = (SolveInfo * nrhs)()
+        code = self._lib.bddc_pcg_solve_host(self.h, b.ctypes.data_as(C.c_void_p),
+                                             x.ctypes.data_as(C.c_void_p), nrhs, self.n,
+                                             float(rtol), int(maxit), C.cast(infos, C.c_void_p),
+                                             None)
+        if code not in (BDDC_OK, -4):
+            _check(code)
+        return x, [i.as_dict() for i in infos]
+
+    def query(self, level=1, max_eigs=8):
+        info = Info()
+        _check(self._lib.bddc_query(self.h, C.byref(info), 0, None, None, 0, None))
+        out = {"levels": info.levels, "n_dof": list(info.n_dof)[:info.levels],
+               "n_sub": list(info.n_sub)[:info.levels - 1],
+               "n_edges": list(info.n_edges)[:info.levels - 1],
+               "n_corners": list(info.n_corners)[:info.levels - 1],
+               "omega_tilde": info.omega_tilde,
+               "omega_level": list(info.omega_level)[:info.levels - 1],
+               "setup_ms": info.setup_ms, "device_bytes": info.device_bytes}
+        if level is not None and 1 <= level < info.levels:
+            ne = info.n_edges[level - 1]
+            nsel = np.zeros(max(ne, 1), np.int32)
+            eigs = np.zeros((max(ne, 1), max_eigs))
+            pairs = np.zeros((max(ne, 1), 2), np.int32)
+            _check(self._lib.bddc_query(self.h, None, level, nsel.ctypes.data_as(C.c_void_p),
+                                        eigs.ctypes.data_as(C.c_void_p), max_eigs,
+                                        pairs.ctypes.data_as(C.c_void_p)))
+            out["n_selected"] = nsel[:ne]
+            out["edge_eigs"] = eigs[:ne]
+            out["edge_pairs"] = pairs[:ne]
+        return out
+
+
+class Server:
+    """Request loop over resident problems (continuous admission by slots / HBM budget)."""
+
+    def __init__(self, hbm_budget=0, max_slots=4):
+        self._lib = load()
+        h = C.c_void_p()
+        _check(self._lib.bddc_server_create(int(hbm_budget), int(max_slots), C.byref(h)))
+        self.h = h
+
+    def submit(self, problem, b, rtol=1e-8, maxit=1000):
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        nrhs = 1 if b.ndim == 1 else b.shape[0]
+        t = C.c_uint64()
+        _check(self._lib.bddc_submit(self.h, problem.h, b.ctypes.data_as(C.c_void_p), nrhs,
+                                     float(rtol), int(maxit), C.byref(t)))
+        return t.value, nrhs, problem.n
+
+    def wait(self, ticket, timeout_ms=-1):
+        tid, nrhs, n = ticket
+        x = np.empty((nrhs, n)) if nrhs > 1 else np.empty(n)
+        infos = (SolveInfo * nrhs)()
+        lat = C.c_double()
+        code = self._lib.bddc_wait(self.h, tid, x.ctypes.data_as(C.c_void_p),
+                                   C.cast(infos, C.c_void_p), C.byref(lat), int(timeout_ms))
+        if code not in (BDDC_OK, -4):
+            _check(code)
+        return x, [i.as_dict() for i in infos], lat.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.bddc_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,1041 @@
+// bddc_api.cu - setup orchestration, the apply recursion, the PCG driver and
+// the C entry points of libbddc.so.
+#include "internal.h"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+
+namespace bddc {
+
+thread_local std::string g_last_error;
+void set_error(const std::string &m) { g_last_error = m; }
+
+void *DevArena::alloc(size_t n) {
+    if (n == 0) n = 8;
+    n = (n + 255) & ~size_t(255);
+    if (budget && bytes + n > budget)
+        throw Error(BDDC_E_NOMEM, "device allocation over the HBM budget");
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, n);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        throw Error(BDDC_E_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    ptrs.push_back(p);
+    bytes += n;
+    return p;
+}
+void DevArena::release() {
+    for (void *p : ptrs) cudaFree(p);
+    ptrs.clear();
+    bytes = 0;
+}
+
+// A global coarse degree of freedom: u -> sum_k w[k] u[dofs[k]] (a row of Q_P^T, Sec. 2).
+struct CDof {
+    std::vector<int> dofs;
+    std::vector<double> w;
+    int s = -1, t = -1;      // edge functionals: the pair sharing it; -1 for point DOFs
+    bool point = false;
+};
+
+struct LevelData {
+    HLevel H;
+    DevLevel D;
+    int mode = BDDC_CONSTR_CORNERS;
+    std::vector<int> nsel, nkept;
+    std::vector<double> lam;      // per edge, max_eigs each
+    int max_eigs = 16;
+    double omega = 0.0;
+    std::vector<std::vector<int>> rc;   // per sub: global coarse ids
+    std::vector<int64_t> offAc;
+    double *ac = nullptr;              // device coarse element matrices (setup arena)
+    std::vector<double> cz;            // constant function on the coarse DOFs
+    int nc = 0;
+};
+
+struct Workspace {
+    DevArena arena;
+    std::vector<DevLevel> lv;
+    double *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *tmp = nullptr;
+    double *part = nullptr, *alphas = nullptr, *betas = nullptr, *lanc = nullptr, *lout = nullptr;
+    double *bbuf = nullptr;
+    unsigned *counter = nullptr;
+    PcgScalars *sc = nullptr;
+    PcgScalars *hsc = nullptr;        // pinned mirror
+    double *hout = nullptr;           // pinned: norms, lanczos
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev = nullptr;
+    cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};
+    int maxit_cap = 0;
+    ~Workspace() {
+        for (auto &g : graph) if (g) cudaGraphExecDestroy(g);
+        if (hsc) cudaFreeHost(hsc);
+        if (hout) cudaFreeHost(hout);
+        if (ev) cudaEventDestroy(ev);
+        if (stream) cudaStreamDestroy(stream);
+    }
+};
+
+}  // namespace bddc
+
+using namespace bddc;
+
+struct bddc_ctx {
+    int nx = 0, levels = 2;
+    double tau = INFINITY;
+    bddc_opts opts{};
+    int prec = BDDC_PREC_FP64;
+    DevArena arena;
+    double *k_dev = nullptr;
+    std::vector<LevelData> L;
+    int n_top = 0;
+    double *Ainv = nullptr;
+    std::unique_ptr<Workspace> ws;
+    double setup_ms = 0.0;
+    std::mutex mu;
+    int n() const { return (nx - 1) * (nx - 1); }
+};
+
+namespace bddc {
+
+namespace {
+
+template <class T> std::vector<int64_t> prefix(const std::vector<T> &v) {
+    std::vector<int64_t> o(v.size() + 1, 0);
+    for (size_t i = 0; i < v.size(); ++i) o[i + 1] = o[i] + (int64_t)v[i];
+    return o;
+}
+
+void check_err(int *err_dev, cudaStream_t s, const char *what) {
+    int h = 0;
+    BDDC_CUDA_TRY(cudaMemcpyAsync(&h, err_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
+    BDDC_CUDA_TRY(cudaStreamSynchronize(s));
+    BDDC_CUDA_TRY(cudaGetLastError());
+    if (h == 0) return;
+    std::string m = std::string(what) + ": ";
+    int code = BDDC_E_NOT_SPD;
+    if (h >= 5000000) m += "top-level coarse matrix not positive definite at row " + std::to_string(h - 5000000);
+    else if (h >= 4000000) m += "constraint Schur complement not positive definite, substructure " + std::to_string(h - 4000000);
+    else if (h >= 3000000) m += "interface matrix without point constraints not positive definite (floating substructure without a corner?), substructure " + std::to_string(h - 3000000);
+    else if (h >= 2000000) m += "edge eigenproblem: denominator not positive definite, edge " + std::to_string(h - 2000000);
+    else if (h >= 1000000) { m += "interior ordering exceeds its band, substructure " + std::to_string(h - 1000000); code = BDDC_E_ARG; }
+    else m += "interior matrix not positive definite, substructure " + std::to_string(h - 1);
+    throw Error(code, m);
+}
+
+// Coarse DOFs of one level (Sec. 2 and Tables 1, 6): corners first, then edge
+// functionals in edge order.
+std::vector<CDof> base_cdofs(const HLevel &H, int mode) {
+    std::vector<CDof> out;
+    if (mode == BDDC_CONSTR_ALL_INTERFACE) {
+        for (int g = 0; g < H.n; ++g)
+            if (H.is_iface[g]) { CDof c; c.dofs = {g}; c.w = {1.0}; c.point = true; out.push_back(c); }
+        return out;
+    }
+    for (int g : H.corners) { CDof c; c.dofs = {g}; c.w = {1.0}; c.point = true; out.push_back(c); }
+    if (mode == BDDC_CONSTR_CORNERS_EDGES) {
+        for (const auto &e : H.edges) {
+            CDof c; c.dofs = e.dofs; c.w.assign(e.dofs.size(), 1.0 / (double)e.dofs.size());
+            c.s = e.s; c.t = e.t; out.push_back(c);
+        }
+    }
+    return out;
+}
+
+// Theorem 1 / Theorem 2 on every edge of the level (GPU), appending the kept
+// constraint rows of eq. (14) as new coarse DOFs.
+void adaptive_edges(LevelData &LD, const SetupLevel &S, double tau, DevArena &tmp, int *err,
+                    cudaStream_t st, std::vector<CDof> &cd) {
+    const HLevel &H = LD.H;
+    const int ne_tot = (int)H.edges.size();
+    LD.nsel.assign(ne_tot, 0); LD.nkept.assign(ne_tot, 0);
+    LD.lam.assign((size_t)ne_tot * LD.max_eigs, 0.0);
+    if (ne_tot == 0) return;
+    std::vector<int> es, et, ne, ncs, nos, nots, fl;
+    std::vector<int> posEs, posEt, posCs, posCt, posOs, posOt;
+    std::vector<double> zEs, zEt;
+    std::vector<int64_t> offE{0}, offC{0}, offOs{0}, offOt{0}, offRows{0};
+    std::vector<int> gpos_s(H.n, -1), gpos_t(H.n, -1);
+    int max_ne = 0, max_nk = 0, max_no = 0;
+    for (const auto &ed : H.edges) {
+        const int s = ed.s, t = ed.t;
+        const auto &Gs = H.Gord[s], &Gt = H.Gord[t];
+        for (size_t k = 0; k < Gs.size(); ++k) gpos_s[Gs[k]] = (int)k;
+        for (size_t k = 0; k < Gt.size(); ++k) gpos_t[Gt[k]] = (int)k;
+        std::vector<char> used_s(Gs.size(), 0), used_t(Gt.size(), 0);
+        for (int g : ed.dofs) {
+            posEs.push_back(gpos_s[g]); posEt.push_back(gpos_t[g]);
+            used_s[gpos_s[g]] = 1; used_t[gpos_t[g]] = 1;
+            zEs.push_back(H.dofz[g]); zEt.push_back(H.dofz[g]);
+        }
+        int nc_ = 0;
+        for (int g : Gs)
+            if (gpos_t[g] >= 0 && H.is_corner[g]) {
+                posCs.push_back(gpos_s[g]); posCt.push_back(gpos_t[g]);
+                used_s[gpos_s[g]] = 1; used_t[gpos_t[g]] = 1; ++nc_;
+            }
+        int no_s = 0, no_t = 0;
+        for (size_t k = 0; k < Gs.size(); ++k) if (!used_s[k]) { posOs.push_back((int)k); ++no_s; }
+        for (size_t k = 0; k < Gt.size(); ++k) if (!used_t[k]) { posOt.push_back((int)k); ++no_t; }
+        for (int g : Gs) gpos_s[g] = -1;
+        for (int g : Gt) gpos_t[g] = -1;
+        const int n_e = (int)ed.dofs.size();
+        es.push_back(s); et.push_back(t); ne.push_back(n_e); ncs.push_back(nc_);
+        nos.push_back(no_s); nots.push_back(no_t);
+        fl.push_back(H.floating[s] && H.floating[t]);
+        offE.push_back(offE.back() + n_e);
+        offC.push_back(offC.back() + nc_);
+        offOs.push_back(offOs.back() + no_s);
+        offOt.push_back(offOt.back() + no_t);
+        offRows.push_back(offRows.back() + (int64_t)n_e * n_e);
+        max_ne = std::max(max_ne, n_e);
+        max_nk = std::max(max_nk, n_e + nc_);
+        max_no = std::max(max_no, std::max(no_s, no_t));
+    }
+    if (max_ne > 127 || max_nk > 128)
+        throw Error(BDDC_E_ARG, "edge longer than 127 DOFs is not supported by the edge eigensolver");
+    EdgeBatch E;
+    E.nedge = ne_tot; E.max_ne = max_ne; E.max_nk = max_nk; E.max_no = max_no;
+    E.max_eigs = LD.max_eigs;
+    E.s = tmp.upload(es, st); E.t = tmp.upload(et, st); E.ne = tmp.upload(ne, st);
+    E.ncs = tmp.upload(ncs, st); E.nos = tmp.upload(nos, st); E.not_ = tmp.upload(nots, st);
+    E.floating = tmp.upload(fl, st);
+    E.offE = tmp.upload(offE, st); E.offC = tmp.upload(offC, st);
+    E.offO_s = tmp.upload(offOs, st); E.offO_t = tmp.upload(offOt, st);
+    E.posE_s = tmp.upload(posEs, st); E.posE_t = tmp.upload(posEt, st);
+    E.posC_s = tmp.upload(posCs, st); E.posC_t = tmp.upload(posCt, st);
+    E.posO_s = tmp.upload(posOs, st); E.posO_t = tmp.upload(posOt, st);
+    E.zE_s = tmp.upload(zEs, st); E.zE_t = tmp.upload(zEt, st);
+    E.nsel = tmp.alloc_n<int>(ne_tot); E.nkept = tmp.alloc_n<int>(ne_tot);
+    E.lam = tmp.alloc_n<double>((size_t)ne_tot * LD.max_eigs);
+    E.offRows = tmp.upload(offRows, st);
+    E.rows = tmp.alloc_n<double>(std::max<int64_t>(offRows.back(), 1));
+    const int64_t N2 = 2 * max_ne, NP = N2 + 1, NK = max_nk, MO = max_no, NE = max_ne;
+    // must cover the sub-buffers carved in k_edge_eig for the largest edge
+    const int64_t stride = MO * MO + MO * NK + 2 * NK * NK + N2 * N2 + NE * NE + NK * NK +
+                           N2 * N2 + (N2 * N2 + NK * N2) + 2 * NP * NP + 4 * (NP / 2 + 1) + N2 +
+                           N2 * N2 + NE * NE + NP + 64;
+    double *work = tmp.alloc_n<double>((size_t)stride * ne_tot);
+    launch_edge_eig_work(S, E, tau, work, stride, err, st);
+    check_err(err, st, "edge eigenproblems");
+    std::vector<double> rows(offRows.back());
+    BDDC_CUDA_TRY(cudaMemcpyAsync(LD.nsel.data(), E.nsel, sizeof(int) * ne_tot, cudaMemcpyDeviceToHost, st));
+    BDDC_CUDA_TRY(cudaMemcpyAsync(LD.nkept.data(), E.nkept, sizeof(int) * ne_tot, cudaMemcpyDeviceToHost, st));
+    BDDC_CUDA_TRY(cudaMemcpyAsync(LD.lam.data(), E.lam, sizeof(double) * LD.lam.size(), cudaMemcpyDeviceToHost, st));
+    if (!rows.empty())
+        BDDC_CUDA_TRY(cudaMemcpyAsync(rows.data(), E.rows, sizeof(double) * rows.size(), cudaMemcpyDeviceToHost, st));
+    BDDC_CUDA_TRY(cudaStreamSynchronize(st));
+    LD.omega = 0.0;
+    for (int e = 0; e < ne_tot; ++e) {
+        const int k = LD.nsel[e];
+        const int n_e = ne[e];
+        const double om = (k < 2 * n_e && k < LD.max_eigs) ? LD.lam[(size_t)e * LD.max_eigs + k] : 0.0;
+        LD.omega = std::max(LD.omega, om);
+        for (int r = 0; r < LD.nkept[e]; ++r) {
+            CDof c;
+            c.dofs = H.edges[e].dofs;
+            c.w.assign(rows.begin() + offRows[e] + (int64_t)r * n_e,
+                       rows.begin() + offRows[e] + (int64_t)(r + 1) * n_e);
+            c.s = H.edges[e].s; c.t = H.edges[e].t;
+            cd.push_back(std::move(c));
+        }
+    }
+}
+
+// FP64 setup of one BDDC level.  emat/emOff describe the element matrices
+// (Q1 elements on level 1, coarse matrices of the level below otherwise).
+void setup_level(bddc_ctx *C, LevelData &LD, const double *emat, const std::vector<int64_t> &emOff,
+                 int mode, double tau, DevArena &tmp, int *err, cudaStream_t st) {
+    HLevel &H = LD.H;
+    H.build();
+    LD.mode = mode;
+    const int ns = H.nsub;
+    std::vector<int> nI(ns), nG(ns), bw(ns), bsz(ns), nblk(ns);
+    for (int s = 0; s < ns; ++s) {
+        nI[s] = (int)H.Iord[s].size(); nG[s] = (int)H.Gord[s].size();
+        bw[s] = H.bw[s]; bsz[s] = H.bsz[s]; nblk[s] = H.nblk[s];
+        if (nG[s] > 512) throw Error(BDDC_E_ARG, "substructure interface larger than 512 DOFs");
+    }
+    // ---- setup scratch
+    SetupLevel S;
+    S.nsub = ns;
+    S.nI = tmp.upload(nI, st); S.nG = tmp.upload(nG, st); S.bw = tmp.upload(bw, st);
+    S.bsz = tmp.upload(bsz, st); S.nblk = tmp.upload(nblk, st);
+    std::vector<int64_t> szBand(ns), szAIG(ns), szAGG(ns);
+    for (int s = 0; s < ns; ++s) {
+        szBand[s] = (int64_t)nI[s] * (bw[s] + 1);
+        szAIG[s] = (int64_t)nI[s] * nG[s];
+        szAGG[s] = (int64_t)nG[s] * nG[s];
+    }
+    auto oBand = prefix(szBand), oAIG = prefix(szAIG), oAGG = prefix(szAGG), oG = prefix(nG);
+    S.offBand = tmp.upload(oBand, st); S.offAIG = tmp.upload(oAIG, st);
+    S.offAGG = tmp.upload(oAGG, st); S.offGd = tmp.upload(oG, st);
+    S.band = tmp.alloc_n<double>(std::max<int64_t>(oBand.back(), 1));
+    S.aig = tmp.alloc_n<double>(std::max<int64_t>(oAIG.back(), 1));
+    S.agg = tmp.alloc_n<double>(std::max<int64_t>(oAGG.back(), 1));
+    S.gdiag = tmp.alloc_n<double>(std::max<int64_t>(oG.back(), 1));
+    S.nelem = H.nelem;
+    std::vector<int> eSlots(H.nelem);
+    for (int e = 0; e < H.nelem; ++e) eSlots[e] = (int)(H.eptr[e + 1] - H.eptr[e]);
+    S.emOff = tmp.upload(emOff, st);
+    S.eSlots = tmp.upload(eSlots, st);
+    S.emat = const_cast<double *>(emat);
+    std::vector<int> subElemPtr{0}, subElems, slotPos;
+    std::vector<int64_t> elemSlotOff;
+    // local positions: interior -> [0, nI), interface -> nI + position in Gord
+    std::vector<int> lpos(H.n, -1);
+    std::vector<int> cooG, cooI;
+    std::vector<int64_t> cooCnt(ns, 0);
+    for (int s = 0; s < ns; ++s) {
+        for (int k = 0; k < nI[s]; ++k) lpos[H.Iord[s][k]] = k;
+        for (int k = 0; k < nG[s]; ++k) lpos[H.Gord[s][k]] = nI[s] + k;
+        std::vector<int64_t> pairs;
+        for (int e : H.sub_elems[s]) {
+            subElems.push_back(e);
+            elemSlotOff.push_back((int64_t)slotPos.size());
+            for (int64_t a = H.eptr[e]; a < H.eptr[e + 1]; ++a) {
+                const int g = H.eslot[a];
+                slotPos.push_back(g >= 0 ? lpos[g] : -1);
+            }
+            for (int64_t a = H.eptr[e]; a < H.eptr[e + 1]; ++a) {
+                const int ga = H.eslot[a];
+                if (ga < 0 || lpos[ga] < nI[s]) continue;          // a: interface
+                for (int64_t b = H.eptr[e]; b < H.eptr[e + 1]; ++b) {
+                    const int gb = H.eslot[b];
+                    if (gb < 0 || lpos[gb] >= nI[s]) continue;     // b: interior
+                    pairs.push_back((int64_t)(lpos[ga] - nI[s]) * (1LL << 32) + lpos[gb]);
+                }
+            }
+        }
+        std::sort(pairs.begin(), pairs.end());
+        pairs.erase(std::unique(pairs.begin(), pairs.end()), pairs.end());
+        for (int64_t pq : pairs) { cooG.push_back((int)(pq >> 32)); cooI.push_back((int)(pq & 0xffffffffLL)); }
+        cooCnt[s] = (int64_t)pairs.size();
+        subElemPtr.push_back((int)subElems.size());
+        for (int g : H.Iord[s]) lpos[g] = -1;
+        for (int g : H.Gord[s]) lpos[g] = -1;
+    }
+    S.subElemPtr = tmp.upload(subElemPtr, st);
+    S.subElems = tmp.upload(subElems, st);
+    S.elemSlotOff = tmp.upload(elemSlotOff, st);
+    S.slotPos = tmp.upload(slotPos, st);
+
+    // ---- apply operators of the level
+    DevArena &A = C->arena;
+    DevLevel &D = LD.D;
+    D.n = H.n; D.nsub = ns; D.n_iface = (int)H.iface_dof.size();
+    D.nI = A.upload(nI, st); D.nG = A.upload(nG, st); D.bsz = A.upload(bsz, st); D.nblk = A.upload(nblk, st);
+    std::vector<int64_t> szF(ns), szN(ns);
+    for (int s = 0; s < ns; ++s) {
+        szF[s] = (int64_t)nblk[s] * 2 * bsz[s] * bsz[s];
+        szN[s] = (int64_t)nG[s] * nG[s];
+        D.max_nI = std::max(D.max_nI, nI[s]); D.max_nG = std::max(D.max_nG, nG[s]);
+        D.max_b = std::max(D.max_b, bsz[s]); D.max_m = std::max(D.max_m, nblk[s]);
+    }
+    auto oI = prefix(nI), oF = prefix(szF), oN = prefix(szN), oCOO = prefix(cooCnt);
+    D.offI = A.upload(oI, st); D.offG = A.upload(oG, st); D.offF = A.upload(oF, st);
+    D.offN = A.upload(oN, st); D.offCOO = A.upload(oCOO, st);
+    std::vector<int> idxI, idxG;
+    for (int s = 0; s < ns; ++s) {
+        idxI.insert(idxI.end(), H.Iord[s].begin(), H.Iord[s].end());
+        for (int g : H.Gord[s]) idxG.push_back(H.iface_id[g]);
+    }
+    D.idxI = A.upload(idxI, st); D.idxG = A.upload(idxG, st);
+    D.ifaceDof = A.upload(H.iface_dof, st);
+    D.cooG = A.upload(cooG, st); D.cooI = A.upload(cooI, st);
+    std::vector<std::vector<int>> ownl(ns);
+    for (int k = 0; k < D.n_iface; ++k) ownl[H.subs_idx[H.subs_ptr[H.iface_dof[k]]]].push_back(k);
+    std::vector<int> own; std::vector<int64_t> ownCnt(ns);
+    for (int s = 0; s < ns; ++s) { own.insert(own.end(), ownl[s].begin(), ownl[s].end()); ownCnt[s] = (int64_t)ownl[s].size(); }
+    auto oOwn = prefix(ownCnt);
+    D.own = A.upload(own, st); D.offOwn = A.upload(oOwn, st);
+    D.f64.dir = A.alloc_n<double>(std::max<int64_t>(oF.back(), 1));
+    D.f64.aig = A.alloc_n<double>(std::max<int64_t>(oCOO.back(), 1));
+    D.f64.wg = A.alloc_n<double>(std::max<int64_t>(oG.back(), 1));
+
+    // ---- numerics: assembly, factorization, Schur complements, weights
+    BDDC_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
+    launch_assemble(S, err, st);
+    check_err(err, st, "assembly");
+    launch_extract_coo(S, D, nullptr, st);
+    launch_band_cholesky(S, err, st);
+    check_err(err, st, "interior Cholesky");
+    launch_schur(S, D.max_nG, st);
+    launch_dirichlet_blocks(S, D, st);
+    double *diag_sum = tmp.alloc_n<double>(std::max(D.n_iface, 1));
+    BDDC_CUDA_TRY(cudaMemsetAsync(diag_sum, 0, sizeof(double) * std::max(D.n_iface, 1), st));
+    launch_weights(S, D, diag_sum, st);
+    BDDC_CUDA_TRY(cudaGetLastError());
+
+    // ---- coarse degrees of freedom
+    std::vector<CDof> cd = base_cdofs(H, mode);
+    if (mode == BDDC_CONSTR_ADAPTIVE) adaptive_edges(LD, S, tau, tmp, err, st, cd);
+    const int ncd = (int)cd.size();
+    LD.nc = ncd;
+    D.nc = ncd;
+    LD.rc.assign(ns, {});
+    for (int q = 0; q < ncd; ++q) {
+        if (cd[q].point) {
+            for (int s : H.subs(cd[q].dofs[0])) LD.rc[s].push_back(q);
+        } else {
+            LD.rc[cd[q].s].push_back(q);
+            LD.rc[cd[q].t].push_back(q);
+        }
+    }
+    std::vector<int> ncl(ns), rcat, ptPos;
+    std::vector<int64_t> szP(ns), szAc(ns), szCon(ns), szWork(ns);
+    std::vector<double> con;
+    std::vector<int> gpos(H.n, -1);
+    for (int s = 0; s < ns; ++s) {
+        ncl[s] = (int)LD.rc[s].size();
+        if (ncl[s] > 256) throw Error(BDDC_E_ARG, "more than 256 coarse DOFs on one substructure");
+        D.max_nc = std::max(D.max_nc, ncl[s]);
+        szP[s] = (int64_t)ncl[s] * nG[s];
+        szAc[s] = (int64_t)ncl[s] * ncl[s];
+        szCon[s] = (int64_t)ncl[s] * nG[s];
+        const int64_t g = nG[s], c = ncl[s];
+        szWork[s] = 3 * g * g + g * std::max<int64_t>(c, 1) + std::max<int64_t>(c * c, 1) +
+                    2 * g * std::max<int64_t>(c, 1) + 16;
+        for (int k = 0; k < nG[s]; ++k) gpos[H.Gord[s][k]] = k;
+        for (int q : LD.rc[s]) {
+            rcat.push_back(q);
+            std::vector<double> row(nG[s], 0.0);
+            for (size_t j = 0; j < cd[q].dofs.size(); ++j) {
+                const int p = gpos[cd[q].dofs[j]];
+                if (p < 0) throw Error(BDDC_E_ARG, "coarse DOF outside the substructure interface");
+                row[p] += cd[q].w[j];
+            }
+            con.insert(con.end(), row.begin(), row.end());
+            ptPos.push_back(cd[q].point ? gpos[cd[q].dofs[0]] : -1);
+        }
+        for (int g2 : H.Gord[s]) gpos[g2] = -1;
+    }
+    auto oC = prefix(ncl), oP = prefix(szP), oAc = prefix(szAc), oCon = prefix(szCon), oW = prefix(szWork);
+    D.ncl = A.upload(ncl, st); D.offC = A.upload(oC, st); D.offP = A.upload(oP, st);
+    D.rc = A.upload(rcat, st);
+    D.f64.nmat = A.alloc_n<double>(std::max<int64_t>(oN.back(), 1));
+    D.f64.psit = A.alloc_n<double>(std::max<int64_t>(oP.back(), 1));
+    NeumannBatch NB;
+    NB.ncl = D.ncl;
+    NB.offCon = tmp.upload(oCon, st);
+    NB.con = tmp.upload(con, st);
+    NB.ptPos = tmp.upload(ptPos, st);
+    NB.offPt = D.offC;
+    NB.offAc = tmp.upload(oAc, st);
+    LD.offAc = oAc;
+    LD.ac = tmp.alloc_n<double>(std::max<int64_t>(oAc.back(), 1));
+    NB.ac = LD.ac;
+    NB.offWork = tmp.upload(oW, st);
+    NB.work = tmp.alloc_n<double>(std::max<int64_t>(oW.back(), 1));
+    NB.max_nG = D.max_nG; NB.max_nc = D.max_nc;
+    launch_neumann_setup(S, D, NB, err, st);
+    check_err(err, st, "coarse basis");
+
+    // constant function on the coarse DOFs (null vectors of the next level)
+    LD.cz.assign(ncd, 0.0);
+    for (int q = 0; q < ncd; ++q)
+        for (size_t j = 0; j < cd[q].dofs.size(); ++j) LD.cz[q] += cd[q].w[j] * H.dofz[cd[q].dofs[j]];
+
+    // ---- reduced-precision copies of the apply operators
+    D.f32.dir = A.alloc_n<float>(std::max<int64_t>(oF.back(), 1));
+    D.f32.aig = A.alloc_n<float>(std::max<int64_t>(oCOO.back(), 1));
+    D.f32.nmat = A.alloc_n<float>(std::max<int64_t>(oN.back(), 1));
+    D.f32.psit = A.alloc_n<float>(std::max<int64_t>(oP.back(), 1));
+    D.f32.wg = A.alloc_n<float>(std::max<int64_t>(oG.back(), 1));
+    D.b16.dir = A.alloc_n<__nv_bfloat16>(std::max<int64_t>(oF.back(), 1));
+    D.b16.aig = A.alloc_n<__nv_bfloat16>(std::max<int64_t>(oCOO.back(), 1));
+    D.b16.nmat = A.alloc_n<__nv_bfloat16>(std::max<int64_t>(oN.back(), 1));
+    D.b16.psit = A.alloc_n<__nv_bfloat16>(std::max<int64_t>(oP.back(), 1));
+    D.b16.wg = A.alloc_n<__nv_bfloat16>(std::max<int64_t>(oG.back(), 1));
+    launch_convert(D.f64.dir, D.f32.dir, oF.back(), st);
+    launch_convert(D.f64.aig, D.f32.aig, oCOO.back(), st);
+    launch_convert(D.f64.nmat, D.f32.nmat, oN.back(), st);
+    launch_convert(D.f64.psit, D.f32.psit, oP.back(), st);
+    launch_convert(D.f64.wg, D.f32.wg, oG.back(), st);
+    launch_convert(D.f64.dir, D.b16.dir, oF.back(), st);
+    launch_convert(D.f64.aig, D.b16.aig, oCOO.back(), st);
+    launch_convert(D.f64.nmat, D.b16.nmat, oN.back(), st);
+    launch_convert(D.f64.psit, D.b16.psit, oP.back(), st);
+    launch_convert(D.f64.wg, D.b16.wg, oG.back(), st);
+    BDDC_CUDA_TRY(cudaGetLastError());
+}
+
+void make_workspace(bddc_ctx *C, Workspace &W, int maxit_cap) {
+    DevArena &A = W.arena;
+    const int n = C->n();
+    W.lv.clear();
+    for (auto &LD : C->L) {
+        DevLevel D = LD.D;
+        D.rB = A.alloc_n<double>(std::max(D.n_iface, 1));
+        D.uB = A.alloc_n<double>(std::max(D.n_iface, 1));
+        int64_t sg = 0;
+        for (auto &v : LD.H.Gord) sg += (int64_t)v.size();
+        D.w = A.alloc_n<double>(std::max<int64_t>(sg, 1));
+        D.rcv = A.alloc_n<double>(std::max(D.nc, 1));
+        D.ucv = A.alloc_n<double>(std::max(D.nc, 1));
+        W.lv.push_back(D);
+    }
+    W.x = A.alloc_n<double>(n); W.r = A.alloc_n<double>(n); W.z = A.alloc_n<double>(n);
+    W.p = A.alloc_n<double>(n); W.q = A.alloc_n<double>(n); W.tmp = A.alloc_n<double>(n);
+    W.bbuf = A.alloc_n<double>(n);
+    W.part = A.alloc_n<double>(4096);
+    W.counter = A.alloc_n<unsigned>(4);
+    BDDC_CUDA_TRY(cudaMemset(W.counter, 0, 4 * sizeof(unsigned)));
+    W.sc = A.alloc_n<PcgScalars>(1);
+    BDDC_CUDA_TRY(cudaMemset(W.sc, 0, sizeof(PcgScalars)));
+    W.maxit_cap = maxit_cap;
+    W.alphas = A.alloc_n<double>(maxit_cap + 1);
+    W.betas = A.alloc_n<double>(maxit_cap + 1);
+    W.lanc = A.alloc_n<double>(2 * (size_t)(maxit_cap + 1) + 16);
+    W.lout = A.alloc_n<double>(4);
+    BDDC_CUDA_TRY(cudaHostAlloc((void **)&W.hsc, sizeof(PcgScalars), cudaHostAllocDefault));
+    BDDC_CUDA_TRY(cudaHostAlloc((void **)&W.hout, 8 * sizeof(double), cudaHostAllocDefault));
+    BDDC_CUDA_TRY(cudaStreamCreateWithFlags(&W.stream, cudaStreamNonBlocking));
+    BDDC_CUDA_TRY(cudaEventCreateWithFlags(&W.ev, cudaEventDisableTiming));
+}
+
+void apply_rec(bddc_ctx *C, Workspace &W, int l, int prec, const double *r, double *z,
+               const int *skip, cudaStream_t st) {
+    const DevLevel &D = W.lv[l];
+    apply_level_pre(D, prec, r, skip, st);
+    if (l + 1 == (int)W.lv.size())
+        launch_dense_symv(C->n_top, C->Ainv, D.rcv, D.ucv, skip, st);
+    else
+        apply_rec(C, W, l + 1, prec, D.rcv, D.ucv, skip, st);
+    apply_level_post(D, prec, r, z, skip, st);
+}
+
+cudaGraphExec_t pcg_graph(bddc_ctx *C, Workspace &W, int prec) {
+    if (W.graph[prec]) return W.graph[prec];
+    const int n = C->n();
+    cudaStream_t st = W.stream;
+    cudaGraph_t g;
+    BDDC_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    launch_pcg_spmv_dot(C->nx, C->k_dev, W.p, W.q, W.part, W.counter, W.sc, W.alphas, st);
+    launch_pcg_update(n, W.x, W.r, W.p, W.q, W.part, W.counter, W.sc, st);
+    apply_rec(C, W, 0, prec, W.r, W.z, &W.sc->done, st);
+    launch_pcg_rz(n, W.r, W.z, W.part, W.counter, W.sc, W.betas, st);
+    launch_pcg_dir(n, W.p, W.z, W.sc, st);
+    BDDC_CUDA_TRY(cudaStreamEndCapture(st, &g));
+    BDDC_CUDA_TRY(cudaGraphInstantiate(&W.graph[prec], g, 0));
+    cudaGraphDestroy(g);
+    return W.graph[prec];
+}
+
+// One right-hand side; runs on W.stream and synchronises it.
+int pcg_one(bddc_ctx *C, Workspace &W, int prec, const double *b, double *x, double rtol,
+            int maxit, bddc_solve_info *info) {
+    const int n = C->n();
+    cudaStream_t st = W.stream;
+    if (maxit > W.maxit_cap) maxit = W.maxit_cap;
+    launch_pcg_init(n, b, W.x, W.r, W.part, W.counter, W.sc, rtol, maxit, st);
+    apply_rec(C, W, 0, prec, W.r, W.z, &W.sc->done, st);
+    launch_pcg_first_dir(n, W.p, W.z, W.r, W.part, W.counter, W.sc, st);
+    cudaGraphExec_t g = pcg_graph(C, W, prec);
+    int chunk = 4;
+    double rr_true = 0.0;
+    for (;;) {
+        for (int k = 0; k < chunk; ++k) BDDC_CUDA_TRY(cudaGraphLaunch(g, st));
+        BDDC_CUDA_TRY(cudaMemcpyAsync(W.hsc, W.sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, st));
+        BDDC_CUDA_TRY(cudaStreamSynchronize(st));
+        if (!W.hsc->done) { chunk = std::min(chunk * 2, 16); continue; }
+        // Confirm with the true residual; keep iterating if it is not yet met.
+        launch_residual(C->nx, C->k_dev, b, W.x, W.tmp, st);
+        launch_norm2(n, W.tmp, W.part, W.counter, W.lout, st);
+        BDDC_CUDA_TRY(cudaMemcpyAsync(W.hout, W.lout, sizeof(double), cudaMemcpyDeviceToHost, st));
+        BDDC_CUDA_TRY(cudaStreamSynchronize(st));
+        rr_true = W.hout[0];
+        if (W.hsc->conv && rr_true > W.hsc->tol2 && W.hsc->it < maxit) {
+            PcgScalars hs = *W.hsc;
+            hs.done = 0; hs.conv = 0;
+            *W.hsc = hs;
+            BDDC_CUDA_TRY(cudaMemcpyAsync(W.sc, W.hsc, sizeof(PcgScalars), cudaMemcpyHostToDevice, st));
+            chunk = 1;
+            continue;
+        }
+        break;
+    }
+    launch_lanczos_extremes(W.alphas, W.betas, W.sc, W.lout + 1, W.lanc, W.maxit_cap + 1, st);
+    BDDC_CUDA_TRY(cudaMemcpyAsync(W.hout + 1, W.lout + 1, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    BDDC_CUDA_TRY(cudaMemcpyAsync(x, W.x, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    BDDC_CUDA_TRY(cudaStreamSynchronize(st));
+    BDDC_CUDA_TRY(cudaGetLastError());
+    const PcgScalars &h = *W.hsc;
+    const int status = (h.conv && rr_true <= h.tol2 * (1 + 1e-12)) ? BDDC_OK : BDDC_E_NOCONV;
+    if (info) {
+        info->iters = h.it;
+        info->status = status;
+        info->relres = h.bb > 0 ? std::sqrt(h.rr / h.bb) : 0.0;
+        info->relres_true = h.bb > 0 ? std::sqrt(rr_true / h.bb) : 0.0;
+        info->lam_min = W.hout[1];
+        info->lam_max = W.hout[2];
+        info->kappa_est = W.hout[1] > 0 ? W.hout[2] / W.hout[1] : 0.0;
+    }
+    return status;
+}
+
+template <class F> int guarded(F &&f) {
+    try {
+        set_error("");
+        return f();
+    } catch (const Error &e) {
+        set_error(e.msg);
+        return e.code;
+    } catch (const std::exception &e) {
+        set_error(e.what());
+        return BDDC_E_ARG;
+    }
+}
+
+}  // namespace
+}  // namespace bddc
+
+// ============================================================================
+// C entry points
+// ============================================================================
+extern "C" {
+
+const char *bddc_last_error(void) { return bddc::g_last_error.c_str(); }
+
+int bddc_setup(const bddc_mesh *mesh, const double *k_elem, const bddc_decomp *decomp, int levels,
+               double tau, const bddc_opts *opts, void *stream, bddc_ctx **out) {
+    if (out) *out = nullptr;
+    return guarded([&]() -> int {
+        if (!mesh || !k_elem || !decomp || !out || !decomp->elem_to_sub)
+            throw Error(BDDC_E_ARG, "null argument");
+        if (mesh->nx < 2 || mesh->ny != mesh->nx) throw Error(BDDC_E_ARG, "mesh must be square with nx >= 2");
+        if (levels != 2 && levels != 3) throw Error(BDDC_E_ARG, "levels must be 2 or 3");
+        if (levels == 3 && (!decomp->sub1_to_sub2 || decomp->n_sub2 < 1))
+            throw Error(BDDC_E_ARG, "three levels need sub1_to_sub2");
+        if (decomp->n_sub1 < 1) throw Error(BDDC_E_ARG, "n_sub1 must be positive");
+        const auto t0 = std::chrono::steady_clock::now();
+        cudaStream_t st = (cudaStream_t)stream;
+        std::unique_ptr<bddc_ctx> C(new bddc_ctx());
+        C->nx = mesh->nx;
+        C->levels = levels;
+        C->tau = tau;
+        bddc_opts o{};
+        o.constraints = BDDC_CONSTR_CORNERS_EDGES;
+        o.constraints_level2 = -1;
+        o.precision = BDDC_PREC_FP64;
+        if (opts) o = *opts;
+        if (o.constraints < 0 || o.constraints > 3) throw Error(BDDC_E_ARG, "bad constraint mode");
+        if (o.precision < 0 || o.precision > 2) throw Error(BDDC_E_ARG, "bad precision");
+        C->opts = o;
+        C->prec = o.precision;
+        C->arena.budget = o.hbm_budget;
+        const int nx = mesh->nx;
+        const int nelem = nx * nx;
+        for (int e = 0; e < nelem; ++e) {
+            if (!(k_elem[e] > 0.0) || !std::isfinite(k_elem[e])) throw Error(BDDC_E_ARG, "coefficients must be positive and finite");
+        }
+        std::vector<double> kv(k_elem, k_elem + nelem);
+        C->k_dev = C->arena.upload(kv, st);
+        DevArena tmp;
+        int *err = tmp.alloc_n<int>(1);
+        BDDC_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
+
+        // level 1: Q1 elements
+        C->L.resize(levels - 1);
+        {
+            HLevel &H = C->L[0].H;
+            H.n = (nx - 1) * (nx - 1);
+            H.nelem = nelem;
+            H.nsub = decomp->n_sub1;
+            H.eptr.resize(nelem + 1);
+            H.eslot.resize((size_t)nelem * 4);
+            H.esub.assign(decomp->elem_to_sub, decomp->elem_to_sub + nelem);
+            H.ebnd.assign(nelem, 0);
+            H.dofz.assign(H.n, 1.0);
+            auto fidx = [&](int i, int j) { return (i <= 0 || j <= 0 || i >= nx || j >= nx) ? -1 : (j - 1) * (nx - 1) + (i - 1); };
+            for (int e = 0; e < nelem; ++e) {
+                const int ej = e / nx, ei = e % nx;
+                H.eptr[e] = (int64_t)e * 4;
+                const int nd[4] = {fidx(ei, ej), fidx(ei + 1, ej), fidx(ei + 1, ej + 1), fidx(ei, ej + 1)};
+                for (int a = 0; a < 4; ++a) {
+                    H.eslot[(size_t)e * 4 + a] = nd[a];
+                    if (nd[a] < 0) H.ebnd[e] = 1;
+                }
+            }
+            H.eptr[nelem] = (int64_t)nelem * 4;
+        }
+        double *emat = tmp.alloc_n<double>((size_t)nelem * 16);
+        launch_q1_element_matrices(nelem, C->k_dev, emat, st);
+        std::vector<int64_t> emOff(nelem);
+        for (int e = 0; e < nelem; ++e) emOff[e] = (int64_t)e * 16;
+        setup_level(C.get(), C->L[0], emat, emOff, o.constraints, tau, tmp, err, st);
+        if (levels == 3) {
+            LevelData &P = C->L[0];
+            HLevel &H = C->L[1].H;
+            H.n = P.nc;
+            H.nelem = P.H.nsub;
+            H.nsub = decomp->n_sub2;
+            H.eptr.assign(H.nelem + 1, 0);
+            for (int s = 0; s < H.nelem; ++s) H.eptr[s + 1] = H.eptr[s] + (int64_t)P.rc[s].size();
+            H.eslot.clear();
+            for (auto &v : P.rc) H.eslot.insert(H.eslot.end(), v.begin(), v.end());
+            H.esub.assign(decomp->sub1_to_sub2, decomp->sub1_to_sub2 + H.nelem);
+            H.ebnd.resize(H.nelem);
+            for (int s = 0; s < H.nelem; ++s) H.ebnd[s] = !P.H.floating[s];
+            H.dofz = P.cz;
+            const int mode2 = o.constraints_level2 >= 0 ? o.constraints_level2 : o.constraints;
+            setup_level(C.get(), C->L[1], P.ac, P.offAc, mode2, tau, tmp, err, st);
+        }
+        // top level: dense FP64 Cholesky and explicit inverse
+        {
+            LevelData &T = C->L.back();
+            const int nt = T.nc;
+            C->n_top = nt;
+            if (nt > 0) {
+                double *Atop = tmp.alloc_n<double>((size_t)nt * nt);
+                BDDC_CUDA_TRY(cudaMemsetAsync(Atop, 0, sizeof(double) * (size_t)nt * nt, st));
+                std::vector<int> ncl(T.H.nsub);
+                for (int s = 0; s < T.H.nsub; ++s) ncl[s] = (int)T.rc[s].size();
+                std::vector<int> rcat;
+                for (auto &v : T.rc) rcat.insert(rcat.end(), v.begin(), v.end());
+                auto oC = prefix(ncl);
+                int *dn = tmp.upload(ncl, st);
+                int64_t *doc = tmp.upload(oC, st);
+                int *drc = tmp.upload(rcat, st);
+                int64_t *doac = tmp.upload(T.offAc, st);
+                launch_scatter_dense(T.H.nsub, dn, doc, drc, doac, T.ac, Atop, nt, st);
+                dense_cholesky(nt, Atop, err, st);
+                check_err(err, st, "top-level Cholesky");
+                C->Ainv = C->arena.alloc_n<double>((size_t)nt * nt);
+                dense_inverse_from_cholesky(nt, Atop, C->Ainv, nullptr, st);
+            } else {
+                C->Ainv = C->arena.alloc_n<double>(1);
+            }
+        }
+        BDDC_CUDA_TRY(cudaStreamSynchronize(st));
+        BDDC_CUDA_TRY(cudaGetLastError());
+        tmp.release();
+        C->ws.reset(new Workspace());
+        make_workspace(C.get(), *C->ws, 10000);
+        C->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        *out = C.release();
+        return BDDC_OK;
+    });
+}
+
+int bddc_set_precision(bddc_ctx *ctx, int precision) {
+    return guarded([&]() -> int {
+        if (!ctx) throw Error(BDDC_E_ARG, "null context");
+        if (precision < 0 || precision > 2) throw Error(BDDC_E_ARG, "bad precision");
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        ctx->prec = precision;
+        return BDDC_OK;
+    });
+}
+
+int bddc_apply(bddc_ctx *ctx, const double *r_dev, double *z_dev, int nrhs, int64_t ld, void *stream) {
+    return guarded([&]() -> int {
+        if (!ctx || !r_dev || !z_dev || nrhs < 1) throw Error(BDDC_E_ARG, "bad argument");
+        const int n = ctx->n();
+        if (ld < n) throw Error(BDDC_E_ARG, "ld < n");
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        cudaStream_t st = (cudaStream_t)stream;
+        for (int j = 0; j < nrhs; ++j)
+            apply_rec(ctx, *ctx->ws, 0, ctx->prec, r_dev + j * ld, z_dev + j * ld, nullptr, st);
+        BDDC_CUDA_TRY(cudaGetLastError());
+        return BDDC_OK;
+    });
+}
+
+int bddc_operator(bddc_ctx *ctx, const double *x_dev, double *y_dev, void *stream) {
+    return guarded([&]() -> int {
+        if (!ctx || !x_dev || !y_dev) throw Error(BDDC_E_ARG, "bad argument");
+        launch_q1_spmv(ctx->nx, ctx->k_dev, x_dev, y_dev, (cudaStream_t)stream);
+        BDDC_CUDA_TRY(cudaGetLastError());
+        return BDDC_OK;
+    });
+}
+
+int bddc_pcg_solve(bddc_ctx *ctx, const double *b_dev, double *x_dev, int nrhs, int64_t ld,
+                   double rtol, int maxit, bddc_solve_info *info_host, void *stream) {
+    return guarded([&]() -> int {
+        if (!ctx || !b_dev || !x_dev || nrhs < 1 || maxit < 1 || !(rtol > 0))
+            throw Error(BDDC_E_ARG, "bad argument");
+        const int n = ctx->n();
+        if (ld < n) throw Error(BDDC_E_ARG, "ld < n");
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        Workspace &W = *ctx->ws;
+        cudaStream_t st = (cudaStream_t)stream;
+        BDDC_CUDA_TRY(cudaEventRecord(W.ev, st));
+        BDDC_CUDA_TRY(cudaStreamWaitEvent(W.stream, W.ev, 0));
+        int rc = BDDC_OK;
+        for (int j = 0; j < nrhs; ++j) {
+            const int s = pcg_one(ctx, W, ctx->prec, b_dev + j * ld, x_dev + j * ld, rtol, maxit,
+                                  info_host ? info_host + j : nullptr);
+            if (s != BDDC_OK) rc = s;
+        }
+        BDDC_CUDA_TRY(cudaEventRecord(W.ev, W.stream));
+        BDDC_CUDA_TRY(cudaStreamWaitEvent(st, W.ev, 0));
+        BDDC_CUDA_TRY(cudaStreamSynchronize(st));
+        if (rc != BDDC_OK) set_error("PCG did not reach the tolerance within maxit");
+        return rc;
+    });
+}
+
+int bddc_pcg_solve_host(bddc_ctx *ctx, const double *b_host, double *x_host, int nrhs, int64_t ld,
+                        double rtol, int maxit, bddc_solve_info *info_host, void *stream) {
+    return guarded([&]() -> int {
+        if (!ctx || !b_host || !x_host || nrhs < 1 || maxit < 1 || !(rtol > 0))
+            throw Error(BDDC_E_ARG, "bad argument");
+        const int n = ctx->n();
+        if (ld < n) throw Error(BDDC_E_ARG, "ld < n");
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        Workspace &W = *ctx->ws;
+        (void)stream;
+        int rc = BDDC_OK;
+        for (int j = 0; j < nrhs; ++j) {
+            BDDC_CUDA_TRY(cudaMemcpyAsync(W.bbuf, b_host + j * ld, sizeof(double) * n, cudaMemcpyHostToDevice, W.stream));
+            const int s = pcg_one(ctx, W, ctx->prec, W.bbuf, W.tmp, rtol, maxit,
+                                  info_host ? info_host + j : nullptr);
+            BDDC_CUDA_TRY(cudaMemcpyAsync(x_host + j * ld, W.tmp, sizeof(double) * n, cudaMemcpyDeviceToHost, W.stream));
+            BDDC_CUDA_TRY(cudaStreamSynchronize(W.stream));
+            if (s != BDDC_OK) rc = s;
+        }
+        if (rc != BDDC_OK) set_error("PCG did not reach the tolerance within maxit");
+        return rc;
+    });
+}
+
+int bddc_query(const bddc_ctx *ctx, bddc_info *info, int level, int32_t *n_selected_per_edge,
+               double *edge_eigs, int max_eigs, int32_t *edge_pairs) {
+    return guarded([&]() -> int {
+        if (!ctx) throw Error(BDDC_E_ARG, "null context");
+        if (info) {
+            std::memset(info, 0, sizeof(*info));
+            info->levels = ctx->levels;
+            for (size_t l = 0; l < ctx->L.size(); ++l) {
+                info->n_dof[l] = ctx->L[l].H.n;
+                info->n_sub[l] = ctx->L[l].H.nsub;
+                info->n_edges[l] = (int)ctx->L[l].H.edges.size();
+                info->n_corners[l] = (int)ctx->L[l].H.corners.size();
+                info->omega_level[l] = ctx->L[l].omega;
+            }
+            info->n_dof[ctx->L.size()] = ctx->n_top;
+            double om = 1.0;
+            bool any = false;
+            for (auto &l : ctx->L) if (l.mode == BDDC_CONSTR_ADAPTIVE) { om *= l.omega; any = true; }
+            info->omega_tilde = any ? om : 0.0;
+            info->setup_ms = ctx->setup_ms;
+            info->device_bytes = ctx->arena.bytes + (ctx->ws ? ctx->ws->arena.bytes : 0);
+        }
+        if (level >= 1 && level <= (int)ctx->L.size()) {
+            const LevelData &LD = ctx->L[level - 1];
+            const int ne = (int)LD.H.edges.size();
+            for (int e = 0; e < ne; ++e) {
+                if (n_selected_per_edge) n_selected_per_edge[e] = LD.nsel.empty() ? 0 : LD.nsel[e];
+                if (edge_pairs) { edge_pairs[2 * e] = LD.H.edges[e].s; edge_pairs[2 * e + 1] = LD.H.edges[e].t; }
+                if (edge_eigs && max_eigs > 0)
+                    for (int k = 0; k < max_eigs; ++k)
+                        edge_eigs[(size_t)e * max_eigs + k] =
+                            (!LD.lam.empty() && k < LD.max_eigs) ? LD.lam[(size_t)e * LD.max_eigs + k] : 0.0;
+            }
+        } else if (n_selected_per_edge || edge_eigs || edge_pairs) {
+            throw Error(BDDC_E_ARG, "level out of range");
+        }
+        return BDDC_OK;
+    });
+}
+
+void bddc_destroy(bddc_ctx *ctx) {
+    if (!ctx) return;
+    cudaDeviceSynchronize();
+    delete ctx;
+}
+
+}  // extern "C"
+
+// ============================================================================
+// Serving loop: a queue of requests, `max_slots` worker threads, each with its
+// own CUDA stream and PCG workspace per problem, so requests run concurrently
+// on the device while the resident operators of each context are shared.
+// ============================================================================
+#include <condition_variable>
+#include <deque>
+#include <thread>
+
+namespace bddc {
+namespace {
+
+struct Request {
+    uint64_t id = 0;
+    bddc_ctx *ctx = nullptr;
+    std::vector<double> b, x;
+    std::vector<bddc_solve_info> info;
+    int nrhs = 1, maxit = 1000, status = BDDC_OK;
+    double rtol = 1e-8;
+    size_t bytes = 0;
+    std::chrono::steady_clock::time_point t_submit, t_done;
+    bool done = false;
+    std::string err;
+};
+
+}  // namespace
+}  // namespace bddc
+
+struct bddc_server {
+    size_t budget = 0;
+    int max_slots = 1;
+    size_t in_use = 0;
+    uint64_t next_id = 1;
+    bool stop = false;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<std::shared_ptr<bddc::Request>> queue;
+    std::map<uint64_t, std::shared_ptr<bddc::Request>> reqs;
+    std::vector<std::thread> workers;
+};
+
+namespace bddc {
+namespace {
+
+size_t request_bytes(const bddc_ctx *ctx, int nrhs) {
+    return (size_t)2 * nrhs * (size_t)(ctx->nx - 1) * (ctx->nx - 1) * sizeof(double);
+}
+
+void worker_loop(bddc_server *S) {
+    std::map<bddc_ctx *, std::unique_ptr<Workspace>> wss;
+    DevArena bufs;
+    size_t cap = 0;
+    double *db = nullptr, *dx = nullptr;
+    for (;;) {
+        std::shared_ptr<Request> R;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            S->cv_work.wait(lk, [&] {
+                if (S->stop) return true;
+                return !S->queue.empty() &&
+                       (!S->budget || S->in_use + S->queue.front()->bytes <= S->budget || S->in_use == 0);
+            });
+            if (S->stop && S->queue.empty()) break;
+            if (S->queue.empty()) continue;
+            R = S->queue.front();
+            S->queue.pop_front();
+            S->in_use += R->bytes;
+        }
+        try {
+            bddc_ctx *C = R->ctx;
+            auto &W = wss[C];
+            if (!W) { W.reset(new Workspace()); make_workspace(C, *W, 10000); }
+            const int n = C->n();
+            if ((size_t)n > cap) {
+                bufs.release();
+                cap = (size_t)n;
+                db = bufs.alloc_n<double>(cap);
+                dx = bufs.alloc_n<double>(cap);
+            }
+            for (int j = 0; j < R->nrhs; ++j) {
+                BDDC_CUDA_TRY(cudaMemcpyAsync(db, R->b.data() + (size_t)j * n, sizeof(double) * n,
+                                              cudaMemcpyHostToDevice, W->stream));
+                const int s = pcg_one(C, *W, C->prec, db, dx, R->rtol, R->maxit, &R->info[j]);
+                BDDC_CUDA_TRY(cudaMemcpyAsync(R->x.data() + (size_t)j * n, dx, sizeof(double) * n,
+                                              cudaMemcpyDeviceToHost, W->stream));
+                BDDC_CUDA_TRY(cudaStreamSynchronize(W->stream));
+                if (s != BDDC_OK) R->status = s;
+            }
+        } catch (const Error &e) {
+            R->status = e.code;
+            R->err = e.msg;
+        }
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            R->t_done = std::chrono::steady_clock::now();
+            R->done = true;
+            S->in_use -= R->bytes;
+        }
+        S->cv_done.notify_all();
+        S->cv_work.notify_all();
+    }
+}
+
+}  // namespace
+}  // namespace bddc
+
+extern "C" {
+
+int bddc_server_create(size_t hbm_budget, int max_slots, bddc_server **out) {
+    if (out) *out = nullptr;
+    return guarded([&]() -> int {
+        if (!out || max_slots < 1) throw Error(BDDC_E_ARG, "bad argument");
+        std::unique_ptr<bddc_server> S(new bddc_server());
+        S->budget = hbm_budget;
+        S->max_slots = max_slots;
+        for (int i = 0; i < max_slots; ++i) S->workers.emplace_back(worker_loop, S.get());
+        *out = S.release();
+        return BDDC_OK;
+    });
+}
+
+int bddc_submit(bddc_server *srv, bddc_ctx *ctx, const double *b_host, int nrhs, double rtol,
+                int maxit, uint64_t *ticket) {
+    return guarded([&]() -> int {
+        if (!srv || !ctx || !b_host || nrhs < 1 || !ticket || !(rtol > 0) || maxit < 1)
+            throw Error(BDDC_E_ARG, "bad argument");
+        auto R = std::make_shared<Request>();
+        const int n = ctx->n();
+        R->ctx = ctx;
+        R->nrhs = nrhs;
+        R->rtol = rtol;
+        R->maxit = maxit;
+        R->b.assign(b_host, b_host + (size_t)nrhs * n);
+        R->x.assign((size_t)nrhs * n, 0.0);
+        R->info.assign(nrhs, bddc_solve_info{});
+        R->bytes = request_bytes(ctx, nrhs);
+        if (srv->budget && R->bytes > srv->budget) throw Error(BDDC_E_BUSY, "request exceeds the HBM budget");
+        {
+            std::lock_guard<std::mutex> lk(srv->mu);
+            R->id = srv->next_id++;
+            R->t_submit = std::chrono::steady_clock::now();
+            srv->reqs[R->id] = R;
+            srv->queue.push_back(R);
+        }
+        srv->cv_work.notify_all();
+        *ticket = R->id;
+        return BDDC_OK;
+    });
+}
+
+int bddc_wait(bddc_server *srv, uint64_t ticket, double *x_host, bddc_solve_info *info_host,
+              double *latency_ms, int timeout_ms) {
+    return guarded([&]() -> int {
+        if (!srv) throw Error(BDDC_E_ARG, "null server");
+        std::unique_lock<std::mutex> lk(srv->mu);
+        auto it = srv->reqs.find(ticket);
+        if (it == srv->reqs.end()) throw Error(BDDC_E_ARG, "unknown ticket");
+        auto R = it->second;
+        auto pred = [&] { return R->done; };
+        if (timeout_ms < 0) srv->cv_done.wait(lk, pred);
+        else if (!srv->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), pred))
+            throw Error(BDDC_E_TIMEOUT, "request still running");
+        srv->reqs.erase(it);
+        lk.unlock();
+        if (x_host) std::memcpy(x_host, R->x.data(), sizeof(double) * R->x.size());
+        if (info_host) std::memcpy(info_host, R->info.data(), sizeof(bddc_solve_info) * R->info.size());
+        if (latency_ms) *latency_ms = std::chrono::duration<double, std::milli>(R->t_done - R->t_submit).count();
+        if (R->status != BDDC_OK) set_error(R->err.empty() ? "PCG did not converge" : R->err);
+        return R->status;
+    });
+}
+
+void bddc_server_destroy(bddc_server *srv) {
+    if (!srv) return;
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        srv->stop = true;
+    }
+    srv->cv_work.notify_all();
+    for (auto &t : srv->workers) t.join();
+    delete srv;
+}
+
+}  // extern "C"

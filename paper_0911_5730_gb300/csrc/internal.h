@@ -1,0 +1,206 @@
+// internal.h - device data layout and kernel launchers shared by the
+// translation units of libbddc.so.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/bddc.h"
+#include "levels_host.h"
+
+namespace bddc {
+
+// ----------------------------------------------------------------------------
+// Error reporting
+// ----------------------------------------------------------------------------
+void set_error(const std::string &msg);
+
+#define BDDC_CUDA_TRY(call)                                                        \
+    do {                                                                           \
+        cudaError_t e_ = (call);                                                   \
+        if (e_ != cudaSuccess) {                                                   \
+            throw ::bddc::Error(BDDC_E_CUDA, std::string(#call) + ": " +           \
+                                                 cudaGetErrorString(e_));          \
+        }                                                                          \
+    } while (0)
+
+// ----------------------------------------------------------------------------
+// Device buffers owned by a context
+// ----------------------------------------------------------------------------
+struct DevArena {
+    std::vector<void *> ptrs;
+    size_t bytes = 0;
+    size_t budget = 0;   // 0 = unlimited
+    void *alloc(size_t n);
+    template <class T> T *alloc_n(size_t n) { return static_cast<T *>(alloc(n * sizeof(T))); }
+    template <class T> T *upload(const std::vector<T> &v, cudaStream_t s) {
+        T *p = alloc_n<T>(v.size() ? v.size() : 1);
+        if (!v.empty()) BDDC_CUDA_TRY(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T),
+                                                      cudaMemcpyHostToDevice, s));
+        return p;
+    }
+    void release();
+    ~DevArena() { release(); }
+};
+
+// Storage of the apply operators in one precision.
+template <class T> struct OpSet {
+    T *dir = nullptr;     // Dirichlet block factors
+    T *aig = nullptr;     // COO values of A_{Gamma I}
+    T *nmat = nullptr;    // constrained Neumann operator on Gamma (nG x nG per sub)
+    T *psit = nullptr;    // Psi^T on Gamma (nc x nG per sub)
+    T *wg = nullptr;      // stiffness weights on Gamma
+};
+
+// One BDDC level as the apply kernels see it.  All per-substructure arrays
+// are concatenated; `*_off` arrays have nsub+1 entries.
+struct DevLevel {
+    int n = 0;            // DOFs of the level
+    int nsub = 0;
+    int n_iface = 0;      // interface DOFs (compact numbering)
+    int nc = 0;           // coarse DOFs (= DOFs of the next level)
+    int max_nI = 0, max_nG = 0, max_nc = 0, max_b = 0, max_m = 0, max_coo = 0;
+    // per substructure sizes
+    int *nI = nullptr, *nG = nullptr, *ncl = nullptr, *bsz = nullptr, *nblk = nullptr;
+    // offsets
+    int64_t *offI = nullptr, *offG = nullptr, *offC = nullptr, *offF = nullptr,
+            *offN = nullptr, *offP = nullptr, *offCOO = nullptr, *offOwn = nullptr;
+    int *idxI = nullptr;      // global DOF of each interior entry
+    int *idxG = nullptr;      // compact interface id of each Gamma entry
+    int *ifaceDof = nullptr;  // global DOF of each compact interface id
+    int *rc = nullptr;        // global coarse id of each local coarse DOF
+    int *cooG = nullptr, *cooI = nullptr;   // COO pattern of A_{Gamma I} (local)
+    int *own = nullptr;       // compact interface ids written by this substructure
+    OpSet<double> f64;
+    OpSet<float> f32;
+    OpSet<__nv_bfloat16> b16;
+    // scratch of one apply (FP64)
+    double *rB = nullptr;     // [n_iface]
+    double *uB = nullptr;     // [n_iface]
+    double *w = nullptr;      // [sum nG]
+    double *rcv = nullptr;    // [nc]  coarse right-hand side
+    double *ucv = nullptr;    // [nc]  coarse correction
+};
+
+// ----------------------------------------------------------------------------
+// Apply / PCG launchers (apply_kernels.cu)
+// ----------------------------------------------------------------------------
+// Down-sweep of one level: interface init, (4)-(5) pre-correction, (6)-(8)
+// substructure correction and coarse right-hand side.
+void apply_level_pre(const DevLevel &L, int prec, const double *r, const int *skip,
+                     cudaStream_t s);
+// Up-sweep of one level: (9) averaging, (10)-(11) post-correction into z.
+void apply_level_post(const DevLevel &L, int prec, const double *r, double *z, const int *skip,
+                      cudaStream_t s);
+void launch_dense_symv(int n, const double *A, const double *x, double *y, const int *skip,
+                       cudaStream_t s);
+
+struct PcgScalars {
+    double rho, rho_new, pq, alpha, beta, rr, bb, tol2;
+    int it, done, conv, maxit;
+};
+void launch_q1_spmv(int nx, const double *k, const double *x, double *y, cudaStream_t s);
+// q = A p, pq = p.q (partials reduced by the last block), alpha = rho / pq
+void launch_pcg_spmv_dot(int nx, const double *k, const double *p, double *q, double *part,
+                         unsigned *counter, PcgScalars *sc, double *alphas, cudaStream_t s);
+// x += alpha p; r -= alpha q; rr = r.r; convergence flag
+void launch_pcg_update(int n, double *x, double *r, const double *p, const double *q,
+                       double *part, unsigned *counter, PcgScalars *sc, cudaStream_t s);
+// rho_new = r.z ; beta = rho_new / rho ; p = z + beta p (second kernel)
+void launch_pcg_rz(int n, const double *r, const double *z, double *part, unsigned *counter,
+                   PcgScalars *sc, double *betas, cudaStream_t s);
+void launch_pcg_dir(int n, double *p, const double *z, PcgScalars *sc, cudaStream_t s);
+void launch_pcg_init(int n, const double *b, double *x, double *r, double *part,
+                     unsigned *counter, PcgScalars *sc, double tol, int maxit, cudaStream_t s);
+void launch_pcg_first_dir(int n, double *p, const double *z, const double *r, double *part,
+                          unsigned *counter, PcgScalars *sc, cudaStream_t s);
+void launch_residual(int nx, const double *k, const double *b, const double *x, double *res,
+                     cudaStream_t s);
+void launch_norm2(int n, const double *v, double *part, unsigned *counter, double *out,
+                  cudaStream_t s);
+void launch_lanczos_extremes(const double *alphas, const double *betas, const PcgScalars *sc,
+                             double *out2, double *work, int cap, cudaStream_t s);
+void launch_convert(const double *src, float *dst, int64_t n, cudaStream_t s);
+void launch_convert(const double *src, __nv_bfloat16 *dst, int64_t n, cudaStream_t s);
+
+// ----------------------------------------------------------------------------
+// Setup launchers (setup_kernels.cu).  All FP64.
+// ----------------------------------------------------------------------------
+struct SetupLevel {
+    // per-substructure setup scratch
+    int nsub = 0;
+    int *nI = nullptr, *nG = nullptr, *bw = nullptr, *bsz = nullptr, *nblk = nullptr;
+    int64_t *offBand = nullptr, *offAIG = nullptr, *offAGG = nullptr, *offGd = nullptr;
+    double *band = nullptr;   // banded A_II then its Cholesky factor
+    double *aig = nullptr;    // A_{I Gamma} then G = L^{-1} A_{I Gamma}
+    double *agg = nullptr;    // A_{Gamma Gamma} then S
+    double *gdiag = nullptr;  // diag of A_i on Gamma (for weights)
+    // elements of the level
+    int nelem = 0;
+    int64_t *emOff = nullptr; // element matrix offsets
+    int *eSlots = nullptr;    // slots per element
+    double *emat = nullptr;   // element matrices, row-major
+    int *subElemPtr = nullptr, *subElems = nullptr;
+    int64_t *elemSlotOff = nullptr; // per subElems entry: offset of its slots in slotPos
+    int *slotPos = nullptr;   // local position of each slot of each element of the sub
+};
+
+void launch_q1_element_matrices(int nelem, const double *k, double *emat, cudaStream_t s);
+void launch_assemble(const SetupLevel &S, int *err, cudaStream_t s);
+void launch_band_cholesky(const SetupLevel &S, int *err, cudaStream_t s);
+void launch_schur(const SetupLevel &S, int max_nG, cudaStream_t s);
+void launch_dirichlet_blocks(const SetupLevel &S, const DevLevel &L, cudaStream_t s);
+void launch_extract_coo(const SetupLevel &S, const DevLevel &L, const int64_t *cooSrc,
+                        cudaStream_t s);
+void launch_weights(const SetupLevel &S, const DevLevel &L, double *diag_sum, cudaStream_t s);
+
+struct EdgeBatch {
+    int nedge = 0;
+    int max_ne = 0, max_nk = 0, max_no = 0;
+    int *s = nullptr, *t = nullptr, *ne = nullptr, *ncs = nullptr;
+    int64_t *offE = nullptr;      // into posE_s/posE_t (ne each)
+    int64_t *offC = nullptr;      // into posC_s/posC_t
+    int64_t *offO_s = nullptr, *offO_t = nullptr;
+    int *posE_s = nullptr, *posE_t = nullptr, *posC_s = nullptr, *posC_t = nullptr;
+    int *posO_s = nullptr, *posO_t = nullptr;
+    int *nos = nullptr, *not_ = nullptr;
+    int *floating = nullptr;      // both substructures floating
+    double *zE_s = nullptr, *zE_t = nullptr;   // null-vector values on the edge
+    // outputs
+    int *nsel = nullptr, *nkept = nullptr;
+    double *lam = nullptr;        // [nedge * max_eigs]
+    double *rows = nullptr;       // [offE(e) * ne(e)] constraint rows (kept x ne)
+    int64_t *offRows = nullptr;
+    int max_eigs = 0;
+};
+void launch_edge_eig_work(const SetupLevel &S, const EdgeBatch &E, double tau, double *work,
+                          int64_t stride, int *err, cudaStream_t s);
+
+struct NeumannBatch {
+    int *ncl = nullptr;           // local coarse DOFs per sub
+    int64_t *offCon = nullptr;    // constraint rows (ncl x nG) offsets
+    double *con = nullptr;
+    int *ptPos = nullptr;         // per local coarse DOF: Gamma position if point constraint else -1
+    int64_t *offPt = nullptr;     // offsets (= offC of DevLevel)
+    int64_t *offAc = nullptr;     // output element matrices of next level
+    double *ac = nullptr;
+    double *work = nullptr;       // scratch
+    int64_t *offWork = nullptr;
+    int max_nG = 0, max_nc = 0;
+};
+void launch_neumann_setup(const SetupLevel &S, const DevLevel &L, const NeumannBatch &N,
+                          int *err, cudaStream_t s);
+
+// dense top level
+void launch_scatter_dense(int nsub, const int *ncl, const int64_t *offC, const int *rc,
+                          const int64_t *offAc, const double *ac, double *A, int n,
+                          cudaStream_t s);
+void dense_cholesky(int n, double *A, int *err, cudaStream_t s);
+void dense_inverse_from_cholesky(int n, const double *L, double *Ainv, double *work,
+                                 cudaStream_t s);
+
+}  // namespace bddc

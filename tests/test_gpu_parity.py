@@ -1,0 +1,155 @@
+"""GPU path against the CPU oracle through the C ABI.
+
+Tolerances (all-FP64 path):
+* per apply: ||z_gpu - z_oracle|| <= 1e-10 ||z_oracle||.  Both sides run the
+  same operators in FP64; they differ by the order of summation (atomics,
+  explicit inverses on the GPU versus LU / Cholesky solves in the oracle),
+  which at coefficient contrasts up to 1e6 gives about 1e-13 to 1e-12;
+* constraint selection: n^{st} identical on every edge, eigenvalues to 1e-9;
+* PCG: the same iteration count and the solution within 1e-10 of the oracle's
+  (the stated FP64 tolerance);
+Mixed path: per-apply error against the FP64 apply <= 1e-5 (FP32) and <= 1e-2
+(BF16), and the FP64 PCG still reaches a true relative residual of 1e-8.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from oracle import bddc as obddc          # noqa: E402
+from oracle import pcg as opcg            # noqa: E402
+from paper_0911_5730_gb300 import inputs  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_0911_5730_gb300 import bddc
+    return bddc
+
+
+def _workloads():
+    w = {}
+    w["unit_c+e"] = inputs.two_level_unit()
+    w["unit_corners"] = inputs.two_level_unit(constraints="corners")
+    w["unit_all"] = inputs.two_level_unit(constraints="all")
+    w["channels_64"] = inputs.two_level_channels(nx=64, sub=16)
+    w["channels_96_ragged"] = inputs.two_level_channels(nx=96, sub=16, tau=3.0)
+    w["three_level_64"] = inputs.three_level_blocks(nx=64, sub=8, group=4, tau=10.0)
+    return w
+
+
+WL = _workloads()
+
+
+def _relerr(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+_cache = {}
+
+
+def _oracle(name):
+    if name not in _cache:
+        _cache[name] = obddc.build_workload(WL[name])
+    return _cache[name]
+
+
+@pytest.mark.parametrize("name", list(WL))
+def test_apply_fp64_matches_oracle(lib, name):
+    wl = WL[name]
+    H = _oracle(name)
+    P = lib.Problem.from_workload(wl)
+    for seed in (1, 2):
+        r = inputs.normal_rhs(wl.n_dof, seed)
+        z = P.apply(torch.tensor(r, device="cuda")).cpu().numpy()
+        assert _relerr(z, H.apply(r)) <= 1e-10
+    # several right-hand sides in one call
+    R = inputs.normal_rhs(wl.n_dof, 5, 3)
+    Z = P.apply(torch.tensor(R, device="cuda")).cpu().numpy()
+    for j in range(3):
+        assert _relerr(Z[j], H.apply(R[j])) <= 1e-10
+    P.close()
+
+
+@pytest.mark.parametrize("name", ["channels_64", "channels_96_ragged", "three_level_64"])
+def test_selection_matches_oracle(lib, name):
+    wl = WL[name]
+    H = _oracle(name)
+    P = lib.Problem.from_workload(wl)
+    for level in range(1, wl.levels):
+        q = P.query(level=level, max_eigs=6)
+        reps = H.info["edge_reports"][level - 1]
+        assert len(reps) == len(q["n_selected"])
+        assert [r["n_sel"] for r in reps] == list(q["n_selected"])
+        assert [tuple(r["pair"]) for r in reps] == [tuple(p) for p in q["edge_pairs"]]
+        for r, eg in zip(reps, q["edge_eigs"]):
+            k = min(6, len(r["lam"]))
+            top = r["lam"][:k]
+            big = top > 1e-8 * max(top[0], 1e-300)
+            assert np.allclose(eg[:k][big], top[big], rtol=1e-9)
+    assert q["n_dof"][:wl.levels - 1] == [b.lv.n for b in H.bl]
+    assert q["n_dof"][-1] == H.bl[-1].nc
+    P.close()
+
+
+@pytest.mark.parametrize("name", ["unit_c+e", "channels_64", "three_level_64"])
+def test_pcg_matches_oracle(lib, name):
+    wl = WL[name]
+    H = _oracle(name)
+    P = lib.Problem.from_workload(wl)
+    b = wl.rhs()
+    x, info = P.solve(torch.tensor(b, device="cuda"), rtol=1e-8)
+    ref = opcg.pcg(H.A, b, H.apply, rtol=1e-8)
+    assert info[0]["status"] == 0
+    assert info[0]["iters"] == ref.iters
+    assert _relerr(x.cpu().numpy(), ref.x) <= 1e-10
+    assert info[0]["relres_true"] <= 1e-8
+    assert abs(info[0]["kappa_est"] - ref.kappa) <= 1e-6 * ref.kappa
+    # host-buffer entry point gives the same answer
+    xh, ih = P.solve_host(b, rtol=1e-8)
+    assert ih[0]["iters"] == info[0]["iters"]
+    assert _relerr(xh, x.cpu().numpy()) <= 1e-12
+    P.close()
+
+
+def test_all_interface_exact_one_iteration(lib):
+    P = lib.Problem.from_workload(WL["unit_all"])
+    b = torch.tensor(WL["unit_all"].rhs(), device="cuda")
+    x, info = P.solve(b, rtol=1e-10)
+    assert info[0]["iters"] == 1
+    P.close()
+
+
+@pytest.mark.parametrize("name", ["channels_64", "three_level_64"])
+def test_mixed_precision(lib, name):
+    wl = WL[name]
+    P = lib.Problem.from_workload(wl)
+    r = torch.tensor(inputs.normal_rhs(wl.n_dof, 3), device="cuda")
+    z64 = P.apply(r).cpu().numpy()
+    P.set_precision("fp32")
+    z32 = P.apply(r).cpu().numpy()
+    P.set_precision("bf16")
+    z16 = P.apply(r).cpu().numpy()
+    assert _relerr(z32, z64) <= 1e-5
+    assert _relerr(z16, z64) <= 1e-2
+    for prec in ("fp32", "bf16"):
+        P.set_precision(prec)
+        x, info = P.solve(torch.tensor(wl.rhs(), device="cuda"), rtol=1e-8, maxit=500)
+        assert info[0]["status"] == 0 and info[0]["relres_true"] <= 1e-8
+    P.close()
+
+
+def test_operator_matches_assembled(lib):
+    wl = WL["channels_64"]
+    H = _oracle("channels_64")
+    P = lib.Problem.from_workload(wl)
+    x = inputs.normal_rhs(wl.n_dof, 7)
+    y = P.operator(torch.tensor(x, device="cuda")).cpu().numpy()
+    assert _relerr(y, H.A @ x) <= 1e-14
+    P.close()
