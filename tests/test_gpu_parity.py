@@ -5,7 +5,9 @@ Tolerances (all-FP64 path):
   same operators in FP64; they differ by the order of summation (atomics,
   explicit inverses on the GPU versus LU / Cholesky solves in the oracle),
   which at coefficient contrasts up to 1e6 gives about 1e-13 to 1e-12;
-* constraint selection: n^{st} identical on every edge, eigenvalues to 1e-9;
+* constraint selection: n^{st} identical on every edge; eigenvalues to 1e-7
+  relative (the Theorem 1 denominators reach a condition number of about 1e7
+  at coefficient contrast 1e6, so either route carries eps * kappa ~ 1e-8);
 * PCG: the same iteration count and the solution within 1e-10 of the oracle's
   (the stated FP64 tolerance);
 Mixed path: per-apply error against the FP64 apply <= 1e-5 (FP32) and <= 1e-2
@@ -92,7 +94,7 @@ def test_selection_matches_oracle(lib, name):
             k = min(6, len(r["lam"]))
             top = r["lam"][:k]
             big = top > 1e-8 * max(top[0], 1e-300)
-            assert np.allclose(eg[:k][big], top[big], rtol=1e-9)
+            assert np.allclose(eg[:k][big], top[big], rtol=1e-7)
     assert q["n_dof"][:wl.levels - 1] == [b.lv.n for b in H.bl]
     assert q["n_dof"][-1] == H.bl[-1].nc
     P.close()
