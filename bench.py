@@ -1,0 +1,388 @@
+#!/usr/bin/env python
+"""Benchmark: BDDC PCG solves/s at relative residual 1e-8, mixed vs FP64.
+
+Workload (the two-level adaptive configuration): 512x512 Q1 mesh of the unit
+square, 32x32 substructures of 16x16 elements (H/h = 16), coefficient
+k = 1e6 on seeded random one-element-wide horizontal/vertical channels
+(about 10% of the elements) and 1 elsewhere, adaptive edge constraints with
+tau = 10, seeded N(0,1) load vector.  One step = one PCG solve of one
+right-hand side from x0 = 0 to ||r|| <= 1e-8 ||b|| (recursive and true
+residual) with the BDDC preconditioner applied in the chosen precision.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+The GPU arm prints one JSON line (rank 0).  `--impl reference` times the CPU
+FP64 oracle on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "two_level_channels_512"
+METRIC = "BDDC PCG solves/s at rel-res 1e-8 (mixed vs FP64); p50/p99 latency"
+UNIT = "solves/s"
+RTOL = 1e-8
+SAMPLE_NX = 128          # CPU sample: the 128x128 corner of the 512x512 field (64 substructures)
+FULL_SUBS = 1024
+
+# DRAM traffic of the dominant kernel from the ncu capture summarised in
+# profiles/, keyed by kernel, valid only while the kernel source is unchanged.
+NCU_TRAFFIC = {}
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+FP64_PEAK_GFLOPS = 1250.0   # nominal GB300 FP64 rate (no measured FP64 peak available)
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), "--query-gpu=" + self.QUERY,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = [l.split(",") for l in open(self.f.name).read().strip().splitlines() if l.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1])); mx = max(mx, float(r[2]))
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip() == "Active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _cpu_sample_workload():
+    from paper_0911_5730_gb300 import inputs
+    wl = inputs.two_level_channels()
+    k = wl.k.reshape(wl.nx, wl.nx)[:SAMPLE_NX, :SAMPLE_NX].ravel().copy()
+    e2s, ns = inputs.grid_decomposition(SAMPLE_NX, 16)
+    b = inputs.normal_rhs((SAMPLE_NX - 1) ** 2, 2002)
+    return k, e2s, ns, b
+
+
+def _golden_iters():
+    p = os.path.join(ROOT, "tests", "golden", WORKLOAD + ".json")
+    if os.path.exists(p):
+        return json.load(open(p))["pcg"]["iters"], "oracle on the full workload (tests/golden)"
+    return None, None
+
+
+def cpu_sample_run(iters=250):
+    """Oracle PCG iterations on the sample; returns seconds per iteration."""
+    from oracle import bddc as obddc
+    from oracle import pcg as opcg
+    k, e2s, ns, b = _cpu_sample_workload()
+    H = obddc.build(SAMPLE_NX, k, e2s, ns, 2, "adaptive", 10.0)
+    opcg.pcg(H.A, b, H.apply, fixed_iters=2)
+    t0 = time.perf_counter()
+    opcg.pcg(H.A, b, H.apply, fixed_iters=iters)
+    return (time.perf_counter() - t0) / iters, ns
+
+
+def cpu_baseline(gpu_iters):
+    """Run the oracle sample in a single-threaded subprocess (spawned, BLAS at 1 thread)."""
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    code = ("import sys, json; sys.path.insert(0, %r); import bench; "
+            "t, ns = bench.cpu_sample_run(); print(json.dumps({'t_iter': t, 'ns': ns}))" % ROOT)
+    p = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                       timeout=900)
+    d = json.loads(p.stdout.strip().splitlines()[-1])
+    iters, src = _golden_iters()
+    if iters is None:
+        iters, src = gpu_iters, "GPU iteration count"
+    t_solve = d["t_iter"] * FULL_SUBS / d["ns"] * iters
+    return {"value": 1.0 / t_solve, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": ("oracle PCG (FP64, CPU, 1 thread) on the %dx%d corner of the same coefficient "
+                       "field with %d substructures of 16x16 elements, 250 iterations timed; seconds "
+                       "per iteration scaled by %d/%d substructures and %d iterations per solve (%s)"
+                       % (SAMPLE_NX, SAMPLE_NX, d["ns"], FULL_SUBS, d["ns"], iters, src))}
+
+
+def _kernel_bytes(q, n_top, prec_bytes):
+    """Algorithmic bytes (and flops) of each apply kernel on level 1.
+
+    Dirichlet solves: the banded Cholesky factor read for the forward and the
+    backward sweep (2 nnz(L) elements), the interior vector in and out and the
+    coupling A_{Gamma I}; Neumann / Psi products: the dense operators once plus
+    the interface vectors; top level: the dense FP64 inverse.
+    """
+    e = prec_bytes
+    sI, sG, sC = q["sum_interior"][0], q["sum_interface"][0], q["sum_coarse_local"][0]
+    band, coo = q["band_nnz"][0], q["coupling_nnz"][0]
+    nent, pent = q["neumann_entries"][0], q["psi_entries"][0]
+    niface = q["n_interface"][0]
+    b = {
+        "iface_init": 8 * (3 * niface + n_top),
+        "pre": 2 * band * e + 8 * sI + coo * (e + 8) + 16 * sG,
+        "neumann": nent * e + pent * e + 8 * sG * 2 + e * sG + 16 * sC,
+        "top_solve": 8 * n_top * n_top + 16 * n_top,
+        "average": pent * e + 8 * sG * 3 + e * sG + 8 * sC,
+        "post": 2 * band * e + 16 * sI + coo * (e + 8) + 8 * sG,
+    }
+    flops = {"top_solve": 2.0 * n_top * n_top}
+    return b, flops
+
+
+def gpu_arm(a):
+    import torch
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_0911_5730_gb300 import bddc, inputs
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def max_over_ranks(v):
+        if world == 1:
+            return v
+        t = torch.tensor([v], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    wl = inputs.two_level_channels()
+    t0 = time.perf_counter()
+    P = bddc.Problem.from_workload(wl, precision="fp32")
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    q = P.query(level=1)
+    b = torch.tensor(wl.rhs(), device="cuda")
+    x = torch.empty_like(b)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+
+    def solves(prec, K, W, clocks=False):
+        P.set_precision(prec)
+        for _ in range(W):
+            P.solve(b, x, rtol=RTOL)
+        st = torch.cuda.current_stream()
+        ms, infos = [], []
+        barrier()
+        torch.cuda.synchronize()
+        clk = Clocks(local) if clocks else None
+        wall0 = time.perf_counter()
+        for _ in range(K):
+            flush.zero_()                     # write > L2 between timed solves (not timed)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            _, info = P.solve(b, x, rtol=RTOL, stream=st)
+            e1.record(st)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            infos.append(info[0])
+        torch.cuda.synchronize()
+        barrier()
+        wall = time.perf_counter() - wall0
+        c = clk.stop() if clk else None
+        for i in infos:
+            assert i["status"] == 0 and i["relres_true"] <= RTOL, i
+        return ms, infos, wall, c
+
+    ms32, inf32, wall32, clocks = solves("fp32", a.steps, a.warmup, clocks=True)
+    ms64, inf64, _, _ = solves("fp64", a.steps, a.warmup)
+    msbf, infbf, _, _ = solves("bf16", max(3, a.steps // 2), 1)
+    t32 = max_over_ranks(sum(ms32) / 1e3)
+    t64 = max_over_ranks(sum(ms64) / 1e3)
+    tbf = max_over_ranks(sum(msbf) / 1e3)
+    value = world * a.steps / t32
+
+    # end to end: host buffers (pinned), copies inside the timed call
+    P.set_precision("fp32")
+    bh = torch.from_numpy(wl.rhs()).pin_memory()
+    xh = torch.empty_like(bh).pin_memory()
+    P.solve_host(bh, xh, rtol=RTOL)
+    e2e_t = []
+    for _ in range(a.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, ih = P.solve_host(bh, xh, rtol=RTOL)
+        e2e_t.append(time.perf_counter() - t0)
+        assert ih[0]["status"] == 0
+    e2e = world * a.steps / max_over_ranks(sum(e2e_t))
+
+    # roofline: per-kernel device times of the FP32 apply, measured with events
+    names = ["iface_init", "pre", "neumann", "top_solve", "average", "post"]
+    prof = P.profile_apply(b, reps=50)
+    n_top = q["n_dof"][-1]
+    kb, kf = _kernel_bytes(q, n_top, 4)
+    kern = {nm: {"ms": float(t), "bytes": kb[nm]} for nm, t in zip(names, prof)}
+    iters = inf32[0]["iters"]
+    dom = max(kern, key=lambda k: kern[k]["ms"])
+    hbm, peak_kind = _peaks()
+    ms_dom = kern[dom]["ms"]
+    src_hash = hashlib.sha1(open(os.path.join(ROOT, "paper_0911_5730_gb300", "csrc",
+                                              "apply_kernels.cu"), "rb").read()).hexdigest()[:12]
+    tr = NCU_TRAFFIC.get(dom)
+    traffic = tr["bytes"] if tr and tr.get("src") == src_hash else None
+    if dom == "top_solve":
+        ach = kf[dom] / (ms_dom * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s",
+                "frac": ach / (FP64_PEAK_GFLOPS / 1e3), "traffic": traffic, "kernel": dom,
+                "peak_kind": "nominal FP64"}
+    else:
+        ach = kern[dom]["bytes"] / (ms_dom * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "traffic": traffic, "kernel": dom, "peak_kind": peak_kind}
+    for nm in kern:
+        kern[nm]["GBps"] = kern[nm]["bytes"] / (kern[nm]["ms"] * 1e-3) / 1e9
+    launches = sum(i["kernel_launches"] for i in inf32)
+
+    cpu = None
+    if rank == 0 and not a.no_cpu_baseline:
+        try:
+            cpu = cpu_baseline(iters)
+        except Exception as ex:       # reported, never silently replaced
+            cpu = {"error": str(ex)[:200]}
+    lat = sorted(ms32)
+
+    def pct(v, p):
+        return v[min(len(v) - 1, int(math.ceil(p / 100.0 * len(v))) - 1)]
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": t32 * 1e3 / a.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "fp32 apply, fp64 PCG",
+        "data": "synthetic (seeded inputs, paper's model problem)",
+        "config": {"workload": WORKLOAD, "mesh": "512x512 Q1", "substructures": "32x32 (H/h=16)",
+                   "levels": 2, "tau": 10.0, "constraints": "adaptive",
+                   "coefficient": "k=1e6 on random one-element channels (~10%), else 1",
+                   "rhs": "N(0,1)", "rtol": RTOL, "apply_precision": "fp32",
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": "512 MiB buffer written between timed solves (untimed)"},
+        "latency_ms": {"p50": pct(lat, 50), "p99": pct(lat, 99)},
+        "iterations": iters,
+        "compare": {"fp64_solves_per_s": world * a.steps / t64,
+                    "fp64_ms_per_solve": t64 * 1e3 / a.steps, "fp64_iterations": inf64[0]["iters"],
+                    "bf16_solves_per_s": world * len(msbf) / tbf,
+                    "bf16_iterations": infbf[0]["iters"],
+                    "mixed_over_fp64": t64 / t32},
+        "setup_ms": setup_s * 1e3,
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 8 * wl.n_dof,
+                "d2h_bytes_per_step": 8 * wl.n_dof},
+        "roofline": roof,
+        "kernels_fp32_apply": kern,
+        "gpu_launches": launches,
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+        "wall_s_mixed": wall32,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def reference_arm(a):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return
+    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+    from oracle import bddc as obddc
+    from oracle import pcg as opcg
+    k, e2s, ns, b = _cpu_sample_workload()
+    H = obddc.build(SAMPLE_NX, k, e2s, ns, 2, "adaptive", 10.0)
+    iters, src = _golden_iters()
+    if iters is None:
+        iters, src = 27, "assumed"
+    per_step_iters = 10
+
+    def step():
+        t0 = time.perf_counter()
+        opcg.pcg(H.A, b, H.apply, fixed_iters=per_step_iters)
+        return (time.perf_counter() - t0) / per_step_iters * FULL_SUBS / ns * iters
+
+    for _ in range(a.warmup):
+        step()
+    t = [step() for _ in range(a.steps)]
+    value = a.steps / sum(t)
+    cores = 1 if os.environ.get("OPENBLAS_NUM_THREADS") == "1" else (os.cpu_count() or 1)
+    sample = ("oracle PCG (FP64, CPU) on the %dx%d corner of the same coefficient field, %d "
+              "substructures, %d iterations per step; scaled by %d/%d substructures and %d "
+              "iterations per solve (%s)" % (SAMPLE_NX, SAMPLE_NX, ns, per_step_iters, FULL_SUBS,
+                                             ns, iters, src))
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * sum(t) / a.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded inputs, paper's model problem)",
+        "config": {"workload": WORKLOAD},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+if __name__ == "__main__":
+    args = _args()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)

@@ -81,6 +81,8 @@ typedef struct {
 typedef struct {
     int32_t iters;        /* PCG iterations taken */
     int32_t status;       /* BDDC_OK or BDDC_E_NOCONV */
+    int32_t kernel_launches;  /* device kernels this solve launched */
+    int32_t reserved;
     double relres;        /* recursive residual ||r_k|| / ||b|| */
     double relres_true;   /* ||b - A x|| / ||b|| recomputed in FP64 */
     double kappa_est;     /* Lanczos estimate lambda_max / lambda_min (Tables 1-7) */
@@ -97,6 +99,17 @@ typedef struct {
     double omega_level[3];        /* max over edges of omega^{st} per level */
     double setup_ms;              /* wall time of bddc_setup */
     size_t device_bytes;          /* bytes the context holds on the device */
+    /* per BDDC level, for byte / flop accounting of the apply kernels */
+    int64_t sum_interior[3];      /* sum over substructures of interior DOFs */
+    int64_t sum_interface[3];     /* sum over substructures of interface DOFs */
+    int64_t sum_coarse_local[3];  /* sum over substructures of local coarse DOFs */
+    int64_t band_nnz[3];          /* entries of the banded interior Cholesky factors */
+    int64_t block_entries[3];     /* entries stored by the block interior factors */
+    int64_t coupling_nnz[3];      /* entries of A_{Gamma I} */
+    int64_t neumann_entries[3];   /* sum over substructures of nG^2 */
+    int64_t psi_entries[3];       /* sum over substructures of nc * nG */
+    int32_t n_interface[3];       /* interface DOFs of the level (each counted once) */
+    int32_t reserved2;
 } bddc_info;
 
 /*
@@ -175,6 +188,19 @@ int bddc_query(const bddc_ctx *ctx, bddc_info *info, int level, int32_t *n_selec
  * matrix-free SpMV used by PCG.
  */
 int bddc_operator(bddc_ctx *ctx, const double *x_dev, double *y_dev, void *stream);
+
+/*
+ * bddc_profile_apply - device time of every kernel of one apply, for roofline
+ * reporting.  Runs `reps` applies of r_dev (device FP64 [n]) on the
+ * context's stream with CUDA events between consecutive kernels and writes
+ * the mean milliseconds of each kernel to ms_out[0..k) (k <= max_out is
+ * returned in *n_out).  Order: for each BDDC level from 1 down: interface
+ * init, pre-correction (4)-(5), substructure correction (6)-(8); then the
+ * top-level solve; then for each level from the deepest up: averaging (9),
+ * post-correction (10)-(11).
+ */
+int bddc_profile_apply(bddc_ctx *ctx, const double *r_dev, int reps, double *ms_out, int max_out,
+                       int32_t *n_out);
 
 void bddc_destroy(bddc_ctx *ctx);
 

@@ -25,7 +25,7 @@ PRECISION = {"fp64": 0, "fp32": 1, "bf16": 2}
 SYMBOLS = ["bddc_setup", "bddc_apply", "bddc_pcg_solve", "bddc_pcg_solve_host",
            "bddc_set_precision", "bddc_query", "bddc_operator", "bddc_destroy",
            "bddc_last_error", "bddc_server_create", "bddc_submit", "bddc_wait",
-           "bddc_server_destroy"]
+           "bddc_server_destroy", "bddc_profile_apply"]
 
 
 class Mesh(C.Structure):
@@ -43,7 +43,8 @@ class Opts(C.Structure):
 
 
 class SolveInfo(C.Structure):
-    _fields_ = [("iters", C.c_int32), ("status", C.c_int32), ("relres", C.c_double),
+    _fields_ = [("iters", C.c_int32), ("status", C.c_int32), ("kernel_launches", C.c_int32),
+                ("reserved", C.c_int32), ("relres", C.c_double),
                 ("relres_true", C.c_double), ("kappa_est", C.c_double),
                 ("lam_min", C.c_double), ("lam_max", C.c_double)]
 
@@ -55,7 +56,12 @@ class Info(C.Structure):
     _fields_ = [("levels", C.c_int32), ("n_dof", C.c_int32 * 4), ("n_sub", C.c_int32 * 3),
                 ("n_edges", C.c_int32 * 3), ("n_corners", C.c_int32 * 3),
                 ("omega_tilde", C.c_double), ("omega_level", C.c_double * 3),
-                ("setup_ms", C.c_double), ("device_bytes", C.c_size_t)]
+                ("setup_ms", C.c_double), ("device_bytes", C.c_size_t),
+                ("sum_interior", C.c_int64 * 3), ("sum_interface", C.c_int64 * 3),
+                ("sum_coarse_local", C.c_int64 * 3), ("band_nnz", C.c_int64 * 3),
+                ("block_entries", C.c_int64 * 3), ("coupling_nnz", C.c_int64 * 3),
+                ("neumann_entries", C.c_int64 * 3), ("psi_entries", C.c_int64 * 3),
+                ("n_interface", C.c_int32 * 3), ("reserved2", C.c_int32)]
 
 
 _lib = None
@@ -84,6 +90,7 @@ def load():
     lib.bddc_server_create.argtypes = [C.c_size_t, i32, C.POINTER(vp)]
     lib.bddc_submit.argtypes = [vp, vp, vp, i32, dp, i32, C.POINTER(C.c_uint64)]
     lib.bddc_wait.argtypes = [vp, C.c_uint64, vp, vp, C.POINTER(C.c_double), i32]
+    lib.bddc_profile_apply.argtypes = [vp, vp, i32, vp, i32, C.POINTER(C.c_int32)]
     lib.bddc_server_destroy.argtypes = [vp]
     lib.bddc_server_destroy.restype = None
     _lib = lib
@@ -193,19 +200,35 @@ class Problem:
             _check(code)
         return x, [i.as_dict() for i in infos]
 
-    def solve_host(self, b, rtol=1e-8, maxit=1000):
-        """PCG with host numpy arrays; the copies are part of the call."""
-        b = np.ascontiguousarray(b, dtype=np.float64)
-        x = np.empty_like(b)
-        nrhs = 1 if b.ndim == 1 else b.shape[0]
+    def solve_host(self, b, x=None, rtol=1e-8, maxit=1000):
+        """PCG with host arrays (numpy, or torch CPU tensors such as pinned
+        buffers); the host<->device copies are part of the call."""
+        if hasattr(b, "data_ptr"):
+            if x is None:
+                x = b.new_empty(b.shape)
+            nrhs = 1 if b.dim() == 1 else b.shape[0]
+            pb, px = C.c_void_p(b.data_ptr()), C.c_void_p(x.data_ptr())
+        else:
+            b = np.ascontiguousarray(b, dtype=np.float64)
+            if x is None:
+                x = np.empty_like(b)
+            nrhs = 1 if b.ndim == 1 else b.shape[0]
+            pb, px = b.ctypes.data_as(C.c_void_p), x.ctypes.data_as(C.c_void_p)
         infos = (SolveInfo * nrhs)()
-        code = self._lib.bddc_pcg_solve_host(self.h, b.ctypes.data_as(C.c_void_p),
-                                             x.ctypes.data_as(C.c_void_p), nrhs, self.n,
+        code = self._lib.bddc_pcg_solve_host(self.h, pb, px, nrhs, self.n,
                                              float(rtol), int(maxit), C.cast(infos, C.c_void_p),
                                              None)
         if code not in (BDDC_OK, -4):
             _check(code)
         return x, [i.as_dict() for i in infos]
+
+    def profile_apply(self, r, reps=20):
+        """Mean device milliseconds of each apply kernel (see bddc_profile_apply)."""
+        out = np.zeros(64)
+        n = C.c_int32()
+        _check(self._lib.bddc_profile_apply(self.h, _ptr(r), int(reps),
+                                            out.ctypes.data_as(C.c_void_p), 64, C.byref(n)))
+        return out[:n.value]
 
     def query(self, level=1, max_eigs=8):
         info = Info()
@@ -217,6 +240,11 @@ class Problem:
                "omega_tilde": info.omega_tilde,
                "omega_level": list(info.omega_level)[:info.levels - 1],
                "setup_ms": info.setup_ms, "device_bytes": info.device_bytes}
+        nl = info.levels - 1
+        for key in ("sum_interior", "sum_interface", "sum_coarse_local", "band_nnz",
+                    "block_entries", "coupling_nnz", "neumann_entries", "psi_entries",
+                    "n_interface"):
+            out[key] = list(getattr(info, key))[:nl]
         if level is not None and 1 <= level < info.levels:
             ne = info.n_edges[level - 1]
             nsel = np.zeros(max(ne, 1), np.int32)

@@ -475,27 +475,35 @@ template <class T, class ACC> void post_t(const DevLevel &L, const double *r, do
 // ----------------------------------------------------------------------------
 // launchers
 // ----------------------------------------------------------------------------
-void apply_level_pre(const DevLevel &L, int prec, const double *r, const int *skip, cudaStream_t s) {
+void apply_level_pre(const DevLevel &L, int prec, const double *r, const int *skip, cudaStream_t s,
+                     cudaEvent_t *ev) {
     const int n = L.n_iface > L.nc ? L.n_iface : L.nc;
+    if (ev) cudaEventRecord(ev[0], s);
     k_iface_init<<<(n + 255) / 256, 256, 0, s>>>(L, r, skip);
+    if (ev) cudaEventRecord(ev[1], s);
     if (prec == BDDC_PREC_FP64) pre_t<double, double>(L, r, skip, s);
     else if (prec == BDDC_PREC_FP32) pre_t<float, float>(L, r, skip, s);
     else pre_t<__nv_bfloat16, float>(L, r, skip, s);
+    if (ev) cudaEventRecord(ev[2], s);
     const size_t smn = sizeof(double) * (size_t)(L.max_nG > L.max_nc ? L.max_nG : L.max_nc);
     if (prec == BDDC_PREC_FP64) k_neumann<double, double><<<L.nsub, 128, smn, s>>>(L, skip);
     else if (prec == BDDC_PREC_FP32) k_neumann<float, float><<<L.nsub, 128, smn, s>>>(L, skip);
     else k_neumann<__nv_bfloat16, float><<<L.nsub, 128, smn, s>>>(L, skip);
+    if (ev) cudaEventRecord(ev[3], s);
 }
 
 void apply_level_post(const DevLevel &L, int prec, const double *r, double *z, const int *skip,
-                      cudaStream_t s) {
+                      cudaStream_t s, cudaEvent_t *ev) {
     const size_t smn = sizeof(double) * (size_t)(L.max_nc > 0 ? L.max_nc : 1);
+    if (ev) cudaEventRecord(ev[0], s);
     if (prec == BDDC_PREC_FP64) k_average<double, double><<<L.nsub, 128, smn, s>>>(L, skip);
     else if (prec == BDDC_PREC_FP32) k_average<float, float><<<L.nsub, 128, smn, s>>>(L, skip);
     else k_average<__nv_bfloat16, float><<<L.nsub, 128, smn, s>>>(L, skip);
+    if (ev) cudaEventRecord(ev[1], s);
     if (prec == BDDC_PREC_FP64) post_t<double, double>(L, r, z, skip, s);
     else if (prec == BDDC_PREC_FP32) post_t<float, float>(L, r, z, skip, s);
     else post_t<__nv_bfloat16, float>(L, r, z, skip, s);
+    if (ev) cudaEventRecord(ev[2], s);
 }
 
 void launch_dense_symv(int n, const double *A, const double *x, double *y, const int *skip,

@@ -57,6 +57,7 @@ struct LevelData {
     double *ac = nullptr;              // device coarse element matrices (setup arena)
     std::vector<double> cz;            // constant function on the coarse DOFs
     int nc = 0;
+    int64_t sumI = 0, sumG = 0, sumC = 0, bandnnz = 0, blockent = 0, coonnz = 0, nent = 0, pent = 0;
 };
 
 struct Workspace {
@@ -339,6 +340,11 @@ void setup_level(bddc_ctx *C, LevelData &LD, const double *emat, const std::vect
         D.max_b = std::max(D.max_b, bsz[s]); D.max_m = std::max(D.max_m, nblk[s]);
     }
     auto oI = prefix(nI), oF = prefix(szF), oN = prefix(szN), oCOO = prefix(cooCnt);
+    LD.sumI = oI.back(); LD.sumG = oG.back(); LD.blockent = oF.back(); LD.coonnz = oCOO.back();
+    LD.nent = oN.back();
+    LD.bandnnz = 0;
+    for (int s = 0; s < ns; ++s)
+        for (int j = 0; j < nI[s]; ++j) LD.bandnnz += std::min(bw[s], nI[s] - 1 - j) + 1;
     D.offI = A.upload(oI, st); D.offG = A.upload(oG, st); D.offF = A.upload(oF, st);
     D.offN = A.upload(oN, st); D.offCOO = A.upload(oCOO, st);
     std::vector<int> idxI, idxG;
@@ -417,6 +423,8 @@ void setup_level(bddc_ctx *C, LevelData &LD, const double *emat, const std::vect
         for (int g2 : H.Gord[s]) gpos[g2] = -1;
     }
     auto oC = prefix(ncl), oP = prefix(szP), oAc = prefix(szAc), oCon = prefix(szCon), oW = prefix(szWork);
+    LD.sumC = oC.back();
+    LD.pent = oP.back();
     D.ncl = A.upload(ncl, st); D.offC = A.upload(oC, st); D.offP = A.upload(oP, st);
     D.rc = A.upload(rcat, st);
     D.f64.nmat = A.alloc_n<double>(std::max<int64_t>(oN.back(), 1));
@@ -538,16 +546,20 @@ int pcg_one(bddc_ctx *C, Workspace &W, int prec, const double *b, double *x, dou
     apply_rec(C, W, 0, prec, W.r, W.z, &W.sc->done, st);
     launch_pcg_first_dir(n, W.p, W.z, W.r, W.part, W.counter, W.sc, st);
     cudaGraphExec_t g = pcg_graph(C, W, prec);
+    const int per_apply = 5 * (int)W.lv.size() + 1;
+    int launches = 2 + per_apply;
     int chunk = 4;
     double rr_true = 0.0;
     for (;;) {
         for (int k = 0; k < chunk; ++k) BDDC_CUDA_TRY(cudaGraphLaunch(g, st));
+        launches += chunk * (4 + per_apply);
         BDDC_CUDA_TRY(cudaMemcpyAsync(W.hsc, W.sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, st));
         BDDC_CUDA_TRY(cudaStreamSynchronize(st));
         if (!W.hsc->done) { chunk = std::min(chunk * 2, 16); continue; }
         // Confirm with the true residual; keep iterating if it is not yet met.
         launch_residual(C->nx, C->k_dev, b, W.x, W.tmp, st);
         launch_norm2(n, W.tmp, W.part, W.counter, W.lout, st);
+        launches += 2;
         BDDC_CUDA_TRY(cudaMemcpyAsync(W.hout, W.lout, sizeof(double), cudaMemcpyDeviceToHost, st));
         BDDC_CUDA_TRY(cudaStreamSynchronize(st));
         rr_true = W.hout[0];
@@ -562,6 +574,7 @@ int pcg_one(bddc_ctx *C, Workspace &W, int prec, const double *b, double *x, dou
         break;
     }
     launch_lanczos_extremes(W.alphas, W.betas, W.sc, W.lout + 1, W.lanc, W.maxit_cap + 1, st);
+    launches += 1;
     BDDC_CUDA_TRY(cudaMemcpyAsync(W.hout + 1, W.lout + 1, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
     BDDC_CUDA_TRY(cudaMemcpyAsync(x, W.x, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
     BDDC_CUDA_TRY(cudaStreamSynchronize(st));
@@ -571,6 +584,7 @@ int pcg_one(bddc_ctx *C, Workspace &W, int prec, const double *b, double *x, dou
     if (info) {
         info->iters = h.it;
         info->status = status;
+        info->kernel_launches = launches;
         info->relres = h.bb > 0 ? std::sqrt(h.rr / h.bb) : 0.0;
         info->relres_true = h.bb > 0 ? std::sqrt(rr_true / h.bb) : 0.0;
         info->lam_min = W.hout[1];
@@ -820,6 +834,15 @@ int bddc_query(const bddc_ctx *ctx, bddc_info *info, int level, int32_t *n_selec
                 info->n_edges[l] = (int)ctx->L[l].H.edges.size();
                 info->n_corners[l] = (int)ctx->L[l].H.corners.size();
                 info->omega_level[l] = ctx->L[l].omega;
+                info->sum_interior[l] = ctx->L[l].sumI;
+                info->sum_interface[l] = ctx->L[l].sumG;
+                info->sum_coarse_local[l] = ctx->L[l].sumC;
+                info->band_nnz[l] = ctx->L[l].bandnnz;
+                info->block_entries[l] = ctx->L[l].blockent;
+                info->coupling_nnz[l] = ctx->L[l].coonnz;
+                info->neumann_entries[l] = ctx->L[l].nent;
+                info->psi_entries[l] = ctx->L[l].pent;
+                info->n_interface[l] = ctx->L[l].D.n_iface;
             }
             info->n_dof[ctx->L.size()] = ctx->n_top;
             double om = 1.0;
@@ -843,6 +866,55 @@ int bddc_query(const bddc_ctx *ctx, bddc_info *info, int level, int32_t *n_selec
         } else if (n_selected_per_edge || edge_eigs || edge_pairs) {
             throw Error(BDDC_E_ARG, "level out of range");
         }
+        return BDDC_OK;
+    });
+}
+
+int bddc_profile_apply(bddc_ctx *ctx, const double *r_dev, int reps, double *ms_out, int max_out,
+                       int32_t *n_out) {
+    return guarded([&]() -> int {
+        if (!ctx || !r_dev || reps < 1 || !ms_out) throw Error(BDDC_E_ARG, "bad argument");
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        Workspace &W = *ctx->ws;
+        const int nl = (int)W.lv.size();
+        const int nseg = 3 * nl + 1 + 2 * nl;
+        if (max_out < nseg) throw Error(BDDC_E_ARG, "max_out too small");
+        std::vector<cudaEvent_t> ev(5 * nl + 2 + 4 * nl);
+        for (auto &e : ev) BDDC_CUDA_TRY(cudaEventCreate(&e));
+        std::vector<double> acc(nseg, 0.0);
+        cudaStream_t st = W.stream;
+        double *z = W.tmp;
+        for (int rep = 0; rep < reps; ++rep) {
+            // down-sweep with 4 events per level, top with 2, up-sweep with 3 per level
+            std::vector<cudaEvent_t *> down(nl), up(nl);
+            int k = 0;
+            for (int l = 0; l < nl; ++l) { down[l] = &ev[k]; k += 4; }
+            cudaEvent_t *top = &ev[k]; k += 2;
+            for (int l = 0; l < nl; ++l) { up[l] = &ev[k]; k += 3; }
+            std::vector<const double *> rin(nl);
+            rin[0] = r_dev;
+            for (int l = 0; l < nl; ++l) {
+                apply_level_pre(W.lv[l], ctx->prec, rin[l], nullptr, st, down[l]);
+                if (l + 1 < nl) rin[l + 1] = W.lv[l].rcv;
+            }
+            BDDC_CUDA_TRY(cudaEventRecord(top[0], st));
+            launch_dense_symv(ctx->n_top, ctx->Ainv, W.lv[nl - 1].rcv, W.lv[nl - 1].ucv, nullptr, st);
+            BDDC_CUDA_TRY(cudaEventRecord(top[1], st));
+            for (int l = nl - 1; l >= 0; --l)
+                apply_level_post(W.lv[l], ctx->prec, rin[l], l == 0 ? z : W.lv[l - 1].ucv, nullptr, st, up[l]);
+            BDDC_CUDA_TRY(cudaStreamSynchronize(st));
+            int seg = 0;
+            float ms;
+            for (int l = 0; l < nl; ++l)
+                for (int j = 0; j < 3; ++j) { cudaEventElapsedTime(&ms, down[l][j], down[l][j + 1]); acc[seg++] += ms; }
+            cudaEventElapsedTime(&ms, top[0], top[1]); acc[seg++] += ms;
+            for (int l = nl - 1; l >= 0; --l)
+                for (int j = 0; j < 2; ++j) { cudaEventElapsedTime(&ms, up[l][j], up[l][j + 1]); acc[seg++] += ms; }
+        }
+        for (auto &e : ev) cudaEventDestroy(e);
+        for (int i = 0; i < nseg; ++i) ms_out[i] = acc[i] / reps;
+        if (n_out) *n_out = nseg;
+        BDDC_CUDA_TRY(cudaGetLastError());
         return BDDC_OK;
     });
 }

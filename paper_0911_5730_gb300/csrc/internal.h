@@ -91,11 +91,13 @@ struct DevLevel {
 // ----------------------------------------------------------------------------
 // Down-sweep of one level: interface init, (4)-(5) pre-correction, (6)-(8)
 // substructure correction and coarse right-hand side.
+// ev (optional, 4 events) are recorded before each kernel and after the last.
 void apply_level_pre(const DevLevel &L, int prec, const double *r, const int *skip,
-                     cudaStream_t s);
+                     cudaStream_t s, cudaEvent_t *ev = nullptr);
 // Up-sweep of one level: (9) averaging, (10)-(11) post-correction into z.
+// ev (optional, 3 events) are recorded before each kernel and after the last.
 void apply_level_post(const DevLevel &L, int prec, const double *r, double *z, const int *skip,
-                      cudaStream_t s);
+                      cudaStream_t s, cudaEvent_t *ev = nullptr);
 void launch_dense_symv(int n, const double *A, const double *x, double *y, const int *skip,
                        cudaStream_t s);
 

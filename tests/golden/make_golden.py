@@ -1,0 +1,61 @@
+"""Write the oracle's results for the full-size workloads to tests/golden/.
+
+Calls only the CPU oracle (oracle/) on the seeded inputs of
+paper_0911_5730_gb300.inputs; nothing here touches the CUDA path.
+
+    python tests/golden/make_golden.py two_level_channels_512
+"""
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+sys.path.insert(0, ROOT)
+
+from oracle import bddc, pcg                      # noqa: E402
+from paper_0911_5730_gb300 import inputs          # noqa: E402
+
+WORKLOADS = {
+    "two_level_channels_512": lambda: inputs.two_level_channels(nx=512, sub=16, tau=10.0),
+    "two_level_unit_32": lambda: inputs.two_level_unit(),
+}
+SAMPLE_STRIDE = 997
+
+
+def make(name):
+    wl = WORKLOADS[name]()
+    t0 = time.time()
+    H = bddc.build_workload(wl)
+    t_setup = time.time() - t0
+    b = wl.rhs()
+    t0 = time.time()
+    res = pcg.pcg(H.A, b, H.apply, rtol=1e-8)
+    t_solve = time.time() - t0
+    idx = np.arange(0, wl.n_dof, SAMPLE_STRIDE)
+    out = {
+        "workload": name,
+        "source": "oracle/ (CPU FP64), seeded inputs of paper_0911_5730_gb300.inputs",
+        "n_dof": [b_.lv.n for b_ in H.bl] + [H.bl[-1].nc],
+        "n_coarse": H.info["n_coarse"],
+        "omega_tilde": H.info["omega_tilde"],
+        "n_sel": [[int(r["n_sel"]) for r in reps] for reps in H.info["edge_reports"]],
+        "edge_pairs": [[list(map(int, r["pair"])) for r in reps] for reps in H.info["edge_reports"]],
+        "lam_top": [[[float(v) for v in r["lam"][:4]] for r in reps] for reps in H.info["edge_reports"]],
+        "pcg": {"rtol": 1e-8, "iters": res.iters, "kappa": res.kappa, "relres_true": res.relres_true},
+        "x_sample_stride": SAMPLE_STRIDE,
+        "x_sample": [float(v) for v in res.x[idx]],
+        "x_norm": float(np.linalg.norm(res.x)),
+        "oracle_seconds": {"setup": t_setup, "solve": t_solve},
+    }
+    with open(os.path.join(HERE, name + ".json"), "w") as f:
+        json.dump(out, f)
+    print(name, "iters", res.iters, "nc", H.info["n_coarse"], "setup %.1fs solve %.1fs" % (t_setup, t_solve))
+
+
+if __name__ == "__main__":
+    for name in sys.argv[1:] or list(WORKLOADS):
+        make(name)
