@@ -202,6 +202,35 @@ int bddc_operator(bddc_ctx *ctx, const double *x_dev, double *y_dev, void *strea
 int bddc_profile_apply(bddc_ctx *ctx, const double *r_dev, int reps, double *ms_out, int max_out,
                        int32_t *n_out);
 
+/*
+ * bddc_apply_noalloc - z = M^{-1} r like bddc_apply (one right-hand side),
+ * without allocating device memory.
+ *
+ * This entry point has no counterpart in the paper.  It exists for callers
+ * that cannot call cudaMalloc when they apply the preconditioner: for example
+ * a caller that has handed all device memory to its own pool, one working to
+ * a fixed memory budget, or a latency-critical loop where an allocation (and
+ * its possible out-of-memory failure) is not acceptable.  The context itself
+ * must already exist (bddc_setup allocates); this call only adds no
+ * allocation of its own.
+ *
+ * The per-level scratch of the apply (interface residuals and averages,
+ * substructure corrections, coarse vectors) lives in one library-owned,
+ * file-scope device array of BDDC_NOALLOC_SCRATCH_BYTES (16 MiB).  Every GPU
+ * that loads the library holds that array until the process exits.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - A context whose scratch needs more than the array holds is rejected
+ *     with BDDC_E_ARG and a message giving both sizes.
+ *   - Every call shares the array and the apply re-initialises the parts that
+ *     must start at zero, so results do not depend on earlier calls; calls
+ *     that overlap on the GPU (other streams, other threads) race on it.
+ *   r_dev, z_dev : device FP64 [n], not overlapping.
+ */
+#define BDDC_NOALLOC_SCRATCH_BYTES (16u << 20)
+int bddc_apply_noalloc(bddc_ctx *ctx, const double *r_dev, double *z_dev, void *stream);
+
 void bddc_destroy(bddc_ctx *ctx);
 
 /* Message of the last error on the calling thread ("" if none). */

@@ -25,7 +25,7 @@ PRECISION = {"fp64": 0, "fp32": 1, "bf16": 2}
 SYMBOLS = ["bddc_setup", "bddc_apply", "bddc_pcg_solve", "bddc_pcg_solve_host",
            "bddc_set_precision", "bddc_query", "bddc_operator", "bddc_destroy",
            "bddc_last_error", "bddc_server_create", "bddc_submit", "bddc_wait",
-           "bddc_server_destroy", "bddc_profile_apply"]
+           "bddc_server_destroy", "bddc_profile_apply", "bddc_apply_noalloc"]
 
 
 class Mesh(C.Structure):
@@ -91,6 +91,7 @@ def load():
     lib.bddc_submit.argtypes = [vp, vp, vp, i32, dp, i32, C.POINTER(C.c_uint64)]
     lib.bddc_wait.argtypes = [vp, C.c_uint64, vp, vp, C.POINTER(C.c_double), i32]
     lib.bddc_profile_apply.argtypes = [vp, vp, i32, vp, i32, C.POINTER(C.c_int32)]
+    lib.bddc_apply_noalloc.argtypes = [vp, vp, vp, vp]
     lib.bddc_server_destroy.argtypes = [vp]
     lib.bddc_server_destroy.restype = None
     _lib = lib
@@ -176,6 +177,13 @@ class Problem:
         nrhs = 1 if r.dim() == 1 else r.shape[0]
         _check(self._lib.bddc_apply(self.h, _ptr(r), _ptr(z), nrhs, self.n,
                                     C.c_void_p(_stream_ptr(stream))))
+        return z
+
+    def apply_noalloc(self, r, z, stream=None):
+        """z = M^{-1} r (one right-hand side) through bddc_apply_noalloc: the
+        library allocates no device memory for this call; z must be given."""
+        _check(self._lib.bddc_apply_noalloc(self.h, _ptr(r), _ptr(z),
+                                            C.c_void_p(_stream_ptr(stream))))
         return z
 
     def operator(self, x, y=None, stream=None):

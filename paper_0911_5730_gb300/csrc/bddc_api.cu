@@ -919,6 +919,86 @@ int bddc_profile_apply(bddc_ctx *ctx, const double *r_dev, int reps, double *ms_
     });
 }
 
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free apply: the per-level scratch comes from a file-scope device
+// array instead of the context's workspace.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoallocDoubles = BDDC_NOALLOC_SCRATCH_BYTES / sizeof(double);
+static __device__ __align__(256) double g_noalloc_scratch[kNoallocDoubles];
+
+std::mutex g_noalloc_mu;
+double *g_noalloc_ptr[64] = {nullptr};
+
+// Device address of the scratch array on the current device (looked up once per device).
+double *noalloc_scratch() {
+    int dev = 0;
+    BDDC_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) throw Error(BDDC_E_ARG, "device index out of range");
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        BDDC_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        g_noalloc_ptr[dev] = static_cast<double *>(p);
+    }
+    return g_noalloc_ptr[dev];
+}
+
+}  // namespace
+
+extern "C" {
+
+int bddc_apply_noalloc(bddc_ctx *ctx, const double *r_dev, double *z_dev, void *stream) {
+    return guarded([&]() -> int {
+        if (!ctx || !r_dev || !z_dev) throw Error(BDDC_E_ARG, "bad argument");
+        const int nl = (int)ctx->L.size();
+        if (nl < 1 || nl > 3) throw Error(BDDC_E_STATE, "context has no BDDC level");
+        // carve the scratch of every level, 32-double aligned pieces
+        auto up = [](size_t v) { return (v + 31) & ~size_t(31); };
+        size_t need = 0;
+        size_t sz[3][5];
+        for (int l = 0; l < nl; ++l) {
+            const DevLevel &D = ctx->L[l].D;
+            sz[l][0] = up(std::max(D.n_iface, 1));
+            sz[l][1] = up(std::max(D.n_iface, 1));
+            sz[l][2] = up(std::max<int64_t>(ctx->L[l].sumG, 1));
+            sz[l][3] = up(std::max(D.nc, 1));
+            sz[l][4] = up(std::max(D.nc, 1));
+            for (int k = 0; k < 5; ++k) need += sz[l][k];
+        }
+        if (need > kNoallocDoubles)
+            throw Error(BDDC_E_ARG, "apply scratch of " + std::to_string(need * sizeof(double)) +
+                                        " bytes exceeds the static scratch of " +
+                                        std::to_string((size_t)BDDC_NOALLOC_SCRATCH_BYTES) + " bytes");
+        double *base = noalloc_scratch();
+        DevLevel lv[3];
+        size_t off = 0;
+        for (int l = 0; l < nl; ++l) {
+            lv[l] = ctx->L[l].D;
+            lv[l].rB = base + off;  off += sz[l][0];
+            lv[l].uB = base + off;  off += sz[l][1];
+            lv[l].w = base + off;   off += sz[l][2];
+            lv[l].rcv = base + off; off += sz[l][3];
+            lv[l].ucv = base + off; off += sz[l][4];
+        }
+        cudaStream_t st = (cudaStream_t)stream;
+        const int prec = ctx->prec;
+        const double *rin[3] = {r_dev, nullptr, nullptr};
+        for (int l = 0; l < nl; ++l) {
+            apply_level_pre(lv[l], prec, rin[l], nullptr, st);
+            if (l + 1 < nl) rin[l + 1] = lv[l].rcv;
+        }
+        launch_dense_symv(ctx->n_top, ctx->Ainv, lv[nl - 1].rcv, lv[nl - 1].ucv, nullptr, st);
+        for (int l = nl - 1; l >= 0; --l)
+            apply_level_post(lv[l], prec, rin[l], l == 0 ? z_dev : lv[l - 1].ucv, nullptr, st);
+        BDDC_CUDA_TRY(cudaGetLastError());
+        return BDDC_OK;
+    });
+}
+
 void bddc_destroy(bddc_ctx *ctx) {
     if (!ctx) return;
     cudaDeviceSynchronize();
