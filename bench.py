@@ -174,11 +174,9 @@ def _kernel_bytes(q, n_top, prec_bytes):
     sI, sG, sC = q["sum_interior"][0], q["sum_interface"][0], q["sum_coarse_local"][0]
     band, coo = q["band_nnz"][0], q["coupling_nnz"][0]
     nent, pent = q["neumann_entries"][0], q["psi_entries"][0]
-    niface = q["n_interface"][0]
     b = {
-        "iface_init": 8 * (3 * niface + n_top),
         "pre": 2 * band * e + 8 * sI + coo * (e + 8) + 16 * sG,
-        "neumann": nent * e + pent * e + 8 * sG * 2 + e * sG + 16 * sC,
+        "neumann": nent * e + pent * e + 8 * sG * 3 + e * sG + 16 * sC,
         "top_solve": 8 * n_top * n_top + 16 * n_top,
         "average": pent * e + 8 * sG * 3 + e * sG + 8 * sC,
         "post": 2 * band * e + 16 * sI + coo * (e + 8) + 8 * sG,
@@ -269,7 +267,7 @@ def gpu_arm(a):
     e2e = world * a.steps / max_over_ranks(sum(e2e_t))
 
     # roofline: per-kernel device times of the FP32 apply, measured with events
-    names = ["iface_init", "pre", "neumann", "top_solve", "average", "post"]
+    names = ["pre", "neumann", "top_solve", "average", "post"]
     prof = P.profile_apply(b, reps=50)
     n_top = q["n_dof"][-1]
     kb, kf = _kernel_bytes(q, n_top, 4)

@@ -86,16 +86,6 @@ __device__ void dirichlet_solve(const T *F, int b, int m, ACC *x, ACC *tmp) {
     }
 }
 
-__global__ void k_iface_init(DevLevel L, const double *r, const int *skip) {
-    if (skip && *skip) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < L.n_iface) {
-        L.rB[i] = r[L.ifaceDof[i]];
-        L.uB[i] = 0.0;
-    }
-    if (i < L.nc) L.rcv[i] = 0.0;
-}
-
 // (4)-(5): u_I = A_II^{-1} r_I per substructure; r_B on Gamma = r - A_{Gamma I} u_I.
 template <class T, class ACC>
 __global__ void k_pre(DevLevel L, const double *r, const int *skip) {
@@ -117,13 +107,15 @@ __global__ void k_pre(DevLevel L, const double *r, const int *skip) {
         atomicAdd(&tG[L.cooG[k]], ld<T, ACC>(O.aig + k) * x[L.cooI[k]]);
     __syncthreads();
     const int *iG = L.idxG + L.offG[sub];
-    for (int q = threadIdx.x; q < nG; q += blockDim.x)
+    for (int q = threadIdx.x; q < nG; q += blockDim.x) {
         if (tG[q] != (ACC)0) atomicAdd(&L.rB[iG[q]], -(double)tG[q]);
+        L.uB[iG[q]] = 0.0;   // consumed by the previous post-correction
+    }
 }
 
 // (6)-(8): f = D_i r_B on Gamma; w = N_i f; r_c += Psi_i^T f.
 template <class T, class ACC>
-__global__ void k_neumann(DevLevel L, const int *skip) {
+__global__ void k_neumann(DevLevel L, const double *r, const int *skip) {
     if (skip && *skip) return;
     extern __shared__ unsigned char smem_raw[];
     ACC *f = reinterpret_cast<ACC *>(smem_raw);
@@ -131,8 +123,10 @@ __global__ void k_neumann(DevLevel L, const int *skip) {
     const int nG = L.nG[sub], nc = L.ncl[sub];
     const OpSet<T> &O = Ops<T>::get(L);
     const int64_t g0 = L.offG[sub];
-    for (int q = threadIdx.x; q < nG; q += blockDim.x)
-        f[q] = ld<T, ACC>(O.wg + g0 + q) * (ACC)L.rB[L.idxG[g0 + q]];
+    for (int q = threadIdx.x; q < nG; q += blockDim.x) {
+        const int id = L.idxG[g0 + q];
+        f[q] = ld<T, ACC>(O.wg + g0 + q) * (ACC)(r[L.ifaceDof[id]] + L.rB[id]);
+    }
     __syncthreads();
     const T *N = O.nmat + L.offN[sub];
     for (int q = threadIdx.x; q < nG; q += blockDim.x) {
@@ -167,7 +161,9 @@ __global__ void k_average(DevLevel L, const int *skip) {
         ACC v = (ACC)L.w[g0 + q];
         for (int k = 0; k < nc; ++k) v += ld<T, ACC>(P + (int64_t)k * nG + q) * uc[k];
         atomicAdd(&L.uB[L.idxG[g0 + q]], (double)(ld<T, ACC>(O.wg + g0 + q) * v));
+        L.rB[L.idxG[g0 + q]] = 0.0;
     }
+    for (int k = threadIdx.x; k < nc; k += blockDim.x) L.rcv[L.rc[L.offC[sub] + k]] = 0.0;
 }
 
 // (10)-(11): interior of u = A_II^{-1}(r_I - A_{I Gamma} u_B), interface of u = u_B.
@@ -198,15 +194,557 @@ __global__ void k_post(DevLevel L, const double *r, double *z, const int *skip) 
     }
 }
 
-// y = A x, A dense symmetric n x n row-major; one warp per row.
-__global__ void k_dense_symv(int n, const double *A, const double *x, double *y, const int *skip) {
+// ----------------------------------------------------------------------------
+// Warp-per-substructure kernels.  Each warp owns one substructure: lane 0
+// starts one bulk copy (cp.async.bulk, completion on an mbarrier) of the
+// substructure's operator block into the warp's slice of shared memory, the
+// lanes gather the vectors meanwhile, and the solve runs from shared memory.
+// Every wait on the mbarrier is bounded; on timeout the kernel flags *L.err,
+// waits (bounded) for its own copy and returns.
+// ----------------------------------------------------------------------------
+constexpr long kWaitPolls = 1L << 20;
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long *bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// The one arrival of the barrier's phase, announcing `bytes` of copies.
+__device__ __forceinline__ void mbar_expect(unsigned long long *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// One bulk copy global -> shared completing `bytes` on the barrier (no arrival).
+__device__ __forceinline__ void bulk_copy(void *dst, const void *src, unsigned bytes,
+                                          unsigned long long *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes,
+                                          unsigned long long *bar) {
+    mbar_expect(bar, bytes);
+    bulk_copy(dst, src, bytes, bar);
+}
+__device__ __forceinline__ bool mbar_try(unsigned long long *bar, unsigned phase) {
+    unsigned ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}\n"
+                 : "=r"(ok) : "r"(smem_u32(bar)), "r"(phase) : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned phase) {
+    for (long i = 0; i < kWaitPolls; ++i)
+        if (mbar_try(bar, phase)) return true;
+    return false;
+}
+// Wait for the phase of parity `phase` of the warp's barrier; false (after
+// flagging) if the wait gave up.
+__device__ __forceinline__ bool warp_wait_copy(unsigned long long *bar, int *err, int lane,
+                                               unsigned phase = 0) {
+    const bool ok = mbar_wait(bar, phase);
+    if (__all_sync(0xffffffffu, ok)) return true;
+    if (lane == 0 && err) atomicExch(err, 1);
+    mbar_wait(bar, phase);   // bounded: let the copy in flight land before the warp exits
+    return false;
+}
+
+__host__ __device__ constexpr size_t al16(size_t v) { return (v + 15) & ~size_t(15); }
+
+template <int LPR, class ACC> __device__ __forceinline__ ACC lpr_sum(ACC v) {
+#pragma unroll
+    for (int o = LPR / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block forward / backward substitution by one warp with the block size BP
+// known at compile time; LPR = 32 / BP lanes share a row.  Every loop unrolls
+// completely; the padding of the last block and the upper triangle of Linv
+// are stored zeros.
+template <class T, class ACC, int BP>
+__device__ __forceinline__ void warp_dirichlet(const T *F, int m, ACC *x, ACC *tmp, int lane) {
+    constexpr int LPR = 32 / BP;
+    constexpr int NC = BP / LPR;
+    constexpr int BB = BP * BP;
+    const int r = lane / LPR, h = lane % LPR;
+    // entry (row, col) of a block lives at col*BP + (row ^ col)
+    for (int j = 0; j < m; ++j) {
+        const T *Linv = F + (size_t)j * 2 * BB;
+        const T *Lsub = Linv + BB;
+        ACC a0 = 0, a1 = 0;
+        if (j > 0) {
+            const ACC *xp = x + (j - 1) * BP;
+#pragma unroll
+            for (int i = 0; i < NC; i += 2) {
+                const int c0 = h + LPR * i;
+                a0 += ld<T, ACC>(Lsub + c0 * BP + (r ^ c0)) * xp[c0];
+                if (i + 1 < NC) {
+                    const int c1 = c0 + LPR;
+                    a1 += ld<T, ACC>(Lsub + c1 * BP + (r ^ c1)) * xp[c1];
+                }
+            }
+        }
+        ACC part = lpr_sum<LPR>(a0 + a1);
+        if (h == 0) tmp[r] = x[j * BP + r] - part;
+        __syncwarp();
+        a0 = 0; a1 = 0;
+#pragma unroll
+        for (int i = 0; i < NC; i += 2) {
+            const int c0 = h + LPR * i;
+            a0 += ld<T, ACC>(Linv + c0 * BP + (r ^ c0)) * tmp[c0];
+            if (i + 1 < NC) {
+                const int c1 = c0 + LPR;
+                a1 += ld<T, ACC>(Linv + c1 * BP + (r ^ c1)) * tmp[c1];
+            }
+        }
+        part = lpr_sum<LPR>(a0 + a1);
+        if (h == 0) x[j * BP + r] = part;
+        __syncwarp();
+    }
+    for (int j = m - 1; j >= 0; --j) {
+        const T *Linv = F + (size_t)j * 2 * BB;
+        ACC a0 = 0, a1 = 0;
+        if (j < m - 1) {
+            const T *Lsub1 = F + (size_t)(j + 1) * 2 * BB + BB;
+            const ACC *xn = x + (j + 1) * BP;
+#pragma unroll
+            for (int i = 0; i < NC; i += 2) {
+                const int c0 = h + LPR * i;
+                a0 += ld<T, ACC>(Lsub1 + r * BP + (c0 ^ r)) * xn[c0];
+                if (i + 1 < NC) {
+                    const int c1 = c0 + LPR;
+                    a1 += ld<T, ACC>(Lsub1 + r * BP + (c1 ^ r)) * xn[c1];
+                }
+            }
+        }
+        ACC part = lpr_sum<LPR>(a0 + a1);
+        if (h == 0) tmp[r] = x[j * BP + r] - part;
+        __syncwarp();
+        a0 = 0; a1 = 0;
+#pragma unroll
+        for (int i = 0; i < NC; i += 2) {
+            const int c0 = h + LPR * i;
+            a0 += ld<T, ACC>(Linv + r * BP + (c0 ^ r)) * tmp[c0];
+            if (i + 1 < NC) {
+                const int c1 = c0 + LPR;
+                a1 += ld<T, ACC>(Linv + r * BP + (c1 ^ r)) * tmp[c1];
+            }
+        }
+        part = lpr_sum<LPR>(a0 + a1);
+        if (h == 0) x[j * BP + r] = part;
+        __syncwarp();
+    }
+}
+
+// Gather dst[i] = src[idx[i]] for i < n (zero for n <= i < npad) with eight
+// independent loads in flight per lane.
+template <class ACC>
+__device__ __forceinline__ void warp_gather(ACC *dst, const double *src, const int *idx, int n,
+                                            int npad, int lane) {
+    for (int i0 = 0; i0 < npad; i0 += 256) {
+        int id[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = i0 + u * 32 + lane;
+            id[u] = i < n ? __ldg(idx + i) : -1;
+        }
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = id[u] >= 0 ? src[id[u]] : 0.0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = i0 + u * 32 + lane;
+            if (i < npad) dst[i] = (ACC)v[u];
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------
+// Dirichlet solves (4) and (10) with one warp per substructure.
+//
+// The block factor (Linv_j, L_{j,j-1} per block) of the substructure is staged
+// whole in the warp's slice of shared memory by a few bulk copies (one
+// mbarrier each), so the backward sweep reads it again without refetching.
+// The forward sweep starts as soon as the first chunk has landed.  Each block
+// step is two small products; the vector entries they need move between
+// lanes by shuffles (LPR = 32/BP lanes share a row and all hold its value),
+// so a step has no shared-memory round trip and no warp barrier.  The index
+// record (interior / interface ids, coupling A_{Gamma I}, owned entries) is
+// held in registers: nI <= 256, nG <= 128, coupling entries <= 256.
+// ----------------------------------------------------------------------------
+constexpr int kUI = 8, kUG = 4, kUC = 8, kUO = 4;   // record entries per lane
+constexpr int kChunks = 4;                          // bulk copies per factor
+
+template <class T, class ACC, int BP> struct DirSlice {
+    // every warp's slice starts 16-byte aligned: bulk-copy destinations and
+    // mbarriers inside it rely on that
+    static size_t bytes(const DevLevel &L) {
+        return al16(sizeof(T) * (size_t)L.max_fac + al16(sizeof(ACC) * (size_t)L.max_m * BP) +
+                    al16(sizeof(ACC) * (size_t)L.max_nG) + 8 * kChunks + 16);
+    }
+};
+
+template <class T, class ACC, int BP, bool POST>
+__global__ void k_dir_w(DevLevel L, const double *r, double *z, const int *skip, unsigned slice) {
+    if (skip && *skip) return;
+    constexpr int LPR = 32 / BP;
+    constexpr int NC = BP / LPR;
+    constexpr int BB = BP * BP;
+    extern __shared__ __align__(16) unsigned char smem_w[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int sub = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (sub >= L.nsub) return;
+    unsigned char *p = smem_w + (size_t)warp * slice;
+    T *fac = reinterpret_cast<T *>(p);      p += al16(sizeof(T) * (size_t)L.max_fac);
+    ACC *x = reinterpret_cast<ACC *>(p);    p += al16(sizeof(ACC) * (size_t)L.max_m * BP);
+    ACC *vG = reinterpret_cast<ACC *>(p);   p += al16(sizeof(ACC) * (size_t)L.max_nG);
+    unsigned long long *bars = reinterpret_cast<unsigned long long *>(p);
+
+    const int nI = L.nI[sub], nG = L.nG[sub], m = L.nblk[sub];
+    const int ncoo = L.ncoo[sub], nown = L.nown[sub];
+    const T *F = Ops<T>::get(L).dir + L.offF[sub];
+    const int nch = m < kChunks ? m : kChunks;
+    if (lane == 0)
+        for (int c = 0; c < nch; ++c) mbar_init(&bars[c]);
+    __syncwarp();
+    if (lane == 0) {
+        for (int c = 0; c < nch; ++c) {
+            const int b0 = c * m / nch, b1 = (c + 1) * m / nch;
+            const unsigned bytes = (unsigned)((size_t)(b1 - b0) * 2 * BB * sizeof(T));
+            mbar_expect(&bars[c], bytes);
+            bulk_copy(fac + (size_t)b0 * 2 * BB, F + (size_t)b0 * 2 * BB, bytes, &bars[c]);
+        }
+    }
+    // index record -> registers (coalesced loads, independent of the copies)
+    const IRecLayout lay(nI, nG, ncoo, nown);
+    const unsigned char *rec = L.irec + L.irecOff[sub];
+    const int *gI = reinterpret_cast<const int *>(rec + lay.iI);
+    const int *gGi = reinterpret_cast<const int *>(rec + lay.iG);
+    const int *gP = reinterpret_cast<const int *>(rec + lay.pr);
+    const double *gC = reinterpret_cast<const double *>(rec + lay.cv);
+    const int *gO = reinterpret_cast<const int *>(rec + lay.ow);
+    int ii[kUI], ig[kUG], pr[kUC], owp[kUO], owd[kUO];
+    ACC cv[kUC];
+#pragma unroll
+    for (int u = 0; u < kUI; ++u) { const int i = u * 32 + lane; ii[u] = i < nI ? gI[i] : -1; }
+#pragma unroll
+    for (int u = 0; u < kUG; ++u) { const int q = u * 32 + lane; ig[u] = q < nG ? gGi[q] : -1; }
+#pragma unroll
+    for (int u = 0; u < kUC; ++u) {
+        const int k = u * 32 + lane;
+        pr[u] = k < ncoo ? gP[k] : -1;
+        cv[u] = k < ncoo ? (ACC)gC[k] : (ACC)0;
+    }
+    if (POST) {
+#pragma unroll
+        for (int u = 0; u < kUO; ++u) {
+            const int k = u * 32 + lane;
+            owp[u] = k < nown ? gO[2 * k] : -1;
+            owd[u] = k < nown ? gO[2 * k + 1] : -1;
+        }
+    }
+    // right-hand side (and u_B on Gamma for the post-correction)
+    double rv[kUI];
+#pragma unroll
+    for (int u = 0; u < kUI; ++u) rv[u] = ii[u] >= 0 ? r[ii[u]] : 0.0;
+#pragma unroll
+    for (int u = 0; u < kUI; ++u) {
+        const int i = u * 32 + lane;
+        if (i < m * BP) x[i] = (ACC)rv[u];
+    }
+    if (POST) {
+        double uv[kUG];
+#pragma unroll
+        for (int u = 0; u < kUG; ++u) uv[u] = ig[u] >= 0 ? L.uB[ig[u]] : 0.0;
+#pragma unroll
+        for (int u = 0; u < kUG; ++u) if (ig[u] >= 0) vG[u * 32 + lane] = (ACC)uv[u];
+        __syncwarp();
+#pragma unroll
+        for (int u = 0; u < kUC; ++u)
+            if (pr[u] >= 0) atomicAdd(&x[pr[u] & 0xffff], -cv[u] * vG[pr[u] >> 16]);
+    } else {
+#pragma unroll
+        for (int u = 0; u < kUG; ++u) {
+            if (ig[u] >= 0) {
+                vG[u * 32 + lane] = 0;
+                L.uB[ig[u]] = 0.0;   // consumed by the previous post-correction
+            }
+        }
+    }
+    __syncwarp();
+    const int rr = lane / LPR, h = lane % LPR;
+    int cw = 0;   // next chunk to wait for
+    bool ok = true;
+    ACC xprev = 0;
+    for (int j = 0; j < m; ++j) {
+        while (cw < nch && cw * m / nch <= j) {
+            if (!warp_wait_copy(&bars[cw], L.err, lane)) { ok = false; break; }
+            ++cw;
+        }
+        if (!ok) break;
+        const T *Li = fac + (size_t)j * 2 * BB;
+        const T *Ls = Li + BB;
+        // t = b_j - L_{j,j-1} x_{j-1}
+        ACC a0 = 0, a1 = 0;
+        if (j > 0) {
+#pragma unroll
+            for (int i = 0; i < NC; i += 2) {
+                const int c0 = h + LPR * i, c1 = c0 + LPR;
+                a0 += ld<T, ACC>(Ls + c0 * BP + (rr ^ c0)) * __shfl_sync(0xffffffffu, xprev, c0 * LPR);
+                if (i + 1 < NC) a1 += ld<T, ACC>(Ls + c1 * BP + (rr ^ c1)) * __shfl_sync(0xffffffffu, xprev, c1 * LPR);
+            }
+        }
+        const ACC t = x[j * BP + rr] - lpr_sum<LPR>(a0 + a1);
+        // x_j = Linv_j t
+        a0 = 0; a1 = 0;
+#pragma unroll
+        for (int i = 0; i < NC; i += 2) {
+            const int c0 = h + LPR * i, c1 = c0 + LPR;
+            a0 += ld<T, ACC>(Li + c0 * BP + (rr ^ c0)) * __shfl_sync(0xffffffffu, t, c0 * LPR);
+            if (i + 1 < NC) a1 += ld<T, ACC>(Li + c1 * BP + (rr ^ c1)) * __shfl_sync(0xffffffffu, t, c1 * LPR);
+        }
+        xprev = lpr_sum<LPR>(a0 + a1);
+        x[j * BP + rr] = xprev;
+    }
+    if (!ok) {
+        for (int c = cw; c < nch; ++c) mbar_wait(&bars[c], 0);   // bounded: let copies land
+        return;
+    }
+    ACC znext = 0;
+    for (int j = m - 1; j >= 0; --j) {
+        const T *Li = fac + (size_t)j * 2 * BB;
+        // t = y_j - L_{j+1,j}^T z_{j+1}
+        ACC a0 = 0, a1 = 0;
+        if (j < m - 1) {
+            const T *Ls1 = fac + (size_t)(j + 1) * 2 * BB + BB;
+#pragma unroll
+            for (int i = 0; i < NC; i += 2) {
+                const int c0 = h + LPR * i, c1 = c0 + LPR;
+                a0 += ld<T, ACC>(Ls1 + rr * BP + (c0 ^ rr)) * __shfl_sync(0xffffffffu, znext, c0 * LPR);
+                if (i + 1 < NC) a1 += ld<T, ACC>(Ls1 + rr * BP + (c1 ^ rr)) * __shfl_sync(0xffffffffu, znext, c1 * LPR);
+            }
+        }
+        const ACC t = x[j * BP + rr] - lpr_sum<LPR>(a0 + a1);
+        // z_j = Linv_j^T t
+        a0 = 0; a1 = 0;
+#pragma unroll
+        for (int i = 0; i < NC; i += 2) {
+            const int c0 = h + LPR * i, c1 = c0 + LPR;
+            a0 += ld<T, ACC>(Li + rr * BP + (c0 ^ rr)) * __shfl_sync(0xffffffffu, t, c0 * LPR);
+            if (i + 1 < NC) a1 += ld<T, ACC>(Li + rr * BP + (c1 ^ rr)) * __shfl_sync(0xffffffffu, t, c1 * LPR);
+        }
+        znext = lpr_sum<LPR>(a0 + a1);
+        x[j * BP + rr] = znext;
+    }
+    __syncwarp();
+    if (!POST) {
+#pragma unroll
+        for (int u = 0; u < kUC; ++u)
+            if (pr[u] >= 0) atomicAdd(&vG[pr[u] >> 16], cv[u] * x[pr[u] & 0xffff]);
+        __syncwarp();
+#pragma unroll
+        for (int u = 0; u < kUG; ++u) {
+            if (ig[u] >= 0) {
+                const ACC v = vG[u * 32 + lane];
+                if (v != (ACC)0) atomicAdd(&L.rB[ig[u]], -(double)v);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int u = 0; u < kUI; ++u) if (ii[u] >= 0) z[ii[u]] = (double)x[u * 32 + lane];
+#pragma unroll
+        for (int u = 0; u < kUO; ++u) if (owp[u] >= 0) z[owd[u]] = (double)vG[owp[u]];
+    }
+}
+
+// (6)-(8): f = D_i r_B on Gamma, w = N_i f, r_c += Psi_i^T f; the whole
+// Neumann record of the substructure arrives with one bulk copy.
+template <class T, class ACC>
+__global__ void k_neumann_r(DevLevel L, int pidx, const double *r, const int *skip, unsigned slice) {
+    if (skip && *skip) return;
+    extern __shared__ __align__(16) unsigned char smem_w[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int sub = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (sub >= L.nsub) return;
+    unsigned char *p = smem_w + (size_t)warp * slice;
+    unsigned char *rec = p;                  p += al16((size_t)L.max_nrec[pidx]);
+    ACC *f = reinterpret_cast<ACC *>(p);     p += al16(sizeof(ACC) * (size_t)L.max_nG);
+    unsigned long long *bar = reinterpret_cast<unsigned long long *>(p);
+    const int nG = L.nG[sub], nc = L.ncl[sub];
+    const NRecLayout lay(nG, nc, (int)sizeof(T));
+    if (lane == 0) mbar_init(bar);
+    __syncwarp();
+    if (lane == 0 && lay.bytes) {
+        mbar_expect(bar, (unsigned)lay.bytes);
+        bulk_copy(rec, L.nrec[pidx] + L.nrecOff[pidx][sub], (unsigned)lay.bytes, bar);
+    }
+    if (lay.bytes && !warp_wait_copy(bar, L.err, lane)) return;
+    const T *Ps = reinterpret_cast<const T *>(rec + lay.psi);
+    const T *wg = reinterpret_cast<const T *>(rec + lay.wg);
+    const int *iG = reinterpret_cast<const int *>(rec + lay.iG);
+    const int *rcs = reinterpret_cast<const int *>(rec + lay.rc);
+    const int *gG = reinterpret_cast<const int *>(rec + lay.gG);
+    const T *Ns = reinterpret_cast<const T *>(rec + lay.N);
+    // r_B on Gamma = r + (the correction the pre-correction accumulated)
+    for (int q0 = 0; q0 < nG; q0 += 128) {
+        double v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int q = q0 + u * 32 + lane;
+            v[u] = q < nG ? r[gG[q]] + L.rB[iG[q]] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int q = q0 + u * 32 + lane;
+            if (q < nG) f[q] = ld<T, ACC>(wg + q) * (ACC)v[u];
+        }
+    }
+    __syncwarp();
+    const int64_t g0 = L.offG[sub];
+    for (int q = lane; q < nG; q += 32) {
+        ACC s0 = 0, s1 = 0;
+        int pp = 0;
+        for (; pp + 1 < nG; pp += 2) {
+            s0 += ld<T, ACC>(Ns + (size_t)pp * nG + q) * f[pp];
+            s1 += ld<T, ACC>(Ns + (size_t)(pp + 1) * nG + q) * f[pp + 1];
+        }
+        if (pp < nG) s0 += ld<T, ACC>(Ns + (size_t)pp * nG + q) * f[pp];
+        L.w[g0 + q] = (double)(s0 + s1);
+    }
+    // coarse right-hand side: lane k sums row k of Psi^T, staggered to avoid bank conflicts
+    for (int k = lane; k < nc; k += 32) {
+        ACC s0 = 0;
+        for (int t = 0; t < nG; ++t) {
+            const int q = (t + k) % nG;
+            s0 += ld<T, ACC>(Ps + (size_t)k * nG + q) * f[q];
+        }
+        atomicAdd(&L.rcv[rcs[k]], (double)s0);
+    }
+}
+
+// (9): u_B += D_i (w_i + Psi_i u_c) on Gamma.
+template <class T, class ACC>
+__global__ void k_average_r(DevLevel L, int pidx, const int *skip, unsigned slice) {
+    if (skip && *skip) return;
+    extern __shared__ __align__(16) unsigned char smem_w[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int sub = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (sub >= L.nsub) return;
+    unsigned char *p = smem_w + (size_t)warp * slice;
+    unsigned char *rec = p;                  p += al16((size_t)L.max_nrec[pidx]);
+    ACC *uc = reinterpret_cast<ACC *>(p);    p += al16(sizeof(ACC) * (size_t)(L.max_nc > 0 ? L.max_nc : 1));
+    unsigned long long *bar = reinterpret_cast<unsigned long long *>(p);
+    const int nG = L.nG[sub], nc = L.ncl[sub];
+    const NRecLayout lay(nG, nc, (int)sizeof(T));
+    if (lane == 0) mbar_init(bar);
+    __syncwarp();
+    if (lane == 0 && lay.avg_bytes) {
+        mbar_expect(bar, (unsigned)lay.avg_bytes);
+        bulk_copy(rec, L.nrec[pidx] + L.nrecOff[pidx][sub], (unsigned)lay.avg_bytes, bar);
+    }
+    const int64_t g0 = L.offG[sub];
+    double wv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int q = u * 32 + lane;
+        wv[u] = q < nG ? L.w[g0 + q] : 0.0;
+    }
+    if (lay.avg_bytes && !warp_wait_copy(bar, L.err, lane)) return;
+    const T *Ps = reinterpret_cast<const T *>(rec + lay.psi);
+    const T *wg = reinterpret_cast<const T *>(rec + lay.wg);
+    const int *iG = reinterpret_cast<const int *>(rec + lay.iG);
+    const int *rcs = reinterpret_cast<const int *>(rec + lay.rc);
+    for (int k = lane; k < nc; k += 32) uc[k] = (ACC)L.ucv[rcs[k]];
+    __syncwarp();
+    for (int q = lane; q < nG; q += 32) {
+        ACC v = (q < 128) ? (ACC)wv[q >> 5] : (ACC)L.w[g0 + q];
+        for (int k = 0; k < nc; ++k) v += ld<T, ACC>(Ps + (size_t)k * nG + q) * uc[k];
+        atomicAdd(&L.uB[iG[q]], (double)(ld<T, ACC>(wg + q) * v));
+        L.rB[iG[q]] = 0.0;            // consumed by the substructure correction
+    }
+    for (int k = lane; k < nc; k += 32) L.rcv[rcs[k]] = 0.0;   // consumed by the coarse solve
+}
+
+// ---- record builders (setup) ----
+__global__ void k_build_irec(DevLevel D, const int *ownPos, const int *ownDof) {
+    const int sub = blockIdx.x;
+    const int nI = D.nI[sub], nG = D.nG[sub], ncoo = D.ncoo[sub], nown = D.nown[sub];
+    const IRecLayout lay(nI, nG, ncoo, nown);
+    unsigned char *base = D.irec + D.irecOff[sub];
+    double *cv = reinterpret_cast<double *>(base + lay.cv);
+    int *iI = reinterpret_cast<int *>(base + lay.iI);
+    int *iG = reinterpret_cast<int *>(base + lay.iG);
+    int *pr = reinterpret_cast<int *>(base + lay.pr);
+    int *ow = reinterpret_cast<int *>(base + lay.ow);
+    const int64_t c0 = D.offCOO[sub], o0 = D.offOwn[sub];
+    for (int k = threadIdx.x; k < ncoo; k += blockDim.x) {
+        cv[k] = D.f64.aig[c0 + k];
+        pr[k] = (D.cooG[c0 + k] << 16) | D.cooI[c0 + k];
+    }
+    for (int i = threadIdx.x; i < nI; i += blockDim.x) iI[i] = D.idxI[D.offI[sub] + i];
+    for (int q = threadIdx.x; q < nG; q += blockDim.x) iG[q] = D.idxG[D.offG[sub] + q];
+    for (int k = threadIdx.x; k < nown; k += blockDim.x) {
+        ow[2 * k] = ownPos[o0 + k];
+        ow[2 * k + 1] = ownDof[o0 + k];
+    }
+}
+
+template <class T>
+__global__ void k_build_nrec(DevLevel D, OpSet<T> O, unsigned char *rec, const int64_t *off) {
+    const int sub = blockIdx.x;
+    const int nG = D.nG[sub], nc = D.ncl[sub];
+    const NRecLayout lay(nG, nc, (int)sizeof(T));
+    unsigned char *base = rec + off[sub];
+    T *psi = reinterpret_cast<T *>(base + lay.psi);
+    T *wg = reinterpret_cast<T *>(base + lay.wg);
+    int *iG = reinterpret_cast<int *>(base + lay.iG);
+    int *rcs = reinterpret_cast<int *>(base + lay.rc);
+    int *gG = reinterpret_cast<int *>(base + lay.gG);
+    T *N = reinterpret_cast<T *>(base + lay.N);
+    for (int k = threadIdx.x; k < nc * nG; k += blockDim.x) psi[k] = O.psit[D.offP[sub] + k];
+    for (int q = threadIdx.x; q < nG; q += blockDim.x) {
+        wg[q] = O.wg[D.offG[sub] + q];
+        iG[q] = D.idxG[D.offG[sub] + q];
+        gG[q] = D.ifaceDof[D.idxG[D.offG[sub] + q]];
+    }
+    for (int k = threadIdx.x; k < nc; k += blockDim.x) rcs[k] = D.rc[D.offC[sub] + k];
+    for (int k = threadIdx.x; k < nG * nG; k += blockDim.x) N[k] = O.nmat[D.offN[sub] + k];
+}
+
+// y = A x, A dense symmetric n x n row-major with leading dimension ld (a
+// multiple of 4, zero padded; x zero on [n, ld)); one warp per row, 16-byte
+// loads, eight values per lane in flight.
+__global__ void k_dense_symv(int n, int ld, const double *A, const double *x, double *y,
+                             const int *skip) {
     if (skip && *skip) return;
     const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (row >= n) return;
-    const double *a = A + (int64_t)row * n;
-    double s = 0.0;
-    for (int c = lane; c < n; c += 32) s += a[c] * x[c];
+    const double *a = A + (int64_t)row * ld;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int c = 2 * lane;
+    for (; c + 192 < ld; c += 256) {
+        const double2 a0 = *reinterpret_cast<const double2 *>(a + c);
+        const double2 a1 = *reinterpret_cast<const double2 *>(a + c + 64);
+        const double2 a2 = *reinterpret_cast<const double2 *>(a + c + 128);
+        const double2 a3 = *reinterpret_cast<const double2 *>(a + c + 192);
+        const double2 x0 = *reinterpret_cast<const double2 *>(x + c);
+        const double2 x1 = *reinterpret_cast<const double2 *>(x + c + 64);
+        const double2 x2 = *reinterpret_cast<const double2 *>(x + c + 128);
+        const double2 x3 = *reinterpret_cast<const double2 *>(x + c + 192);
+        // one DFMA per product: the FP64 pipe bounds this kernel
+        s0 = fma(a0.x, x0.x, s0); s1 = fma(a0.y, x0.y, s1);
+        s2 = fma(a1.x, x1.x, s2); s3 = fma(a1.y, x1.y, s3);
+        s0 = fma(a2.x, x2.x, s0); s1 = fma(a2.y, x2.y, s1);
+        s2 = fma(a3.x, x3.x, s2); s3 = fma(a3.y, x3.y, s3);
+    }
+    for (; c < ld; c += 64) {
+        const double2 a0 = *reinterpret_cast<const double2 *>(a + c);
+        const double2 x0 = *reinterpret_cast<const double2 *>(x + c);
+        s0 = fma(a0.x, x0.x, s0); s1 = fma(a0.y, x0.y, s1);
+    }
+    double s = (s0 + s1) + (s2 + s3);
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) y[row] = s;
 }
@@ -238,6 +776,42 @@ __device__ __forceinline__ double q1_row(int nx, const double *k, const double *
     // element NW: (i-1,j)=0,(i,j)=1,(i,j+1)=2,(i-1,j+1)=3, local 1
     v += kNW * (4.0 * c - 1.0 * w - 2.0 * nw - 1.0 * n);
     return v / 6.0;
+}
+
+// Stencil weights of the assembled Q1 operator, computed once per problem:
+// for free node (i, j) the diagonal and the couplings to E, N, NE and NW;
+// the couplings to W, S, SW and SE are the E, N, NE, NW weights of those
+// neighbours (A is symmetric), so one product costs nine FMAs.
+__global__ void k_q1_weights(int nx, const double *k, double *w) {
+    const int n1 = nx - 1;
+    const int64_t n = (int64_t)n1 * n1;
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n) return;
+    const int i = (int)(g % n1) + 1, j = (int)(g / n1) + 1;
+    const double kSW = k[(int64_t)(j - 1) * nx + (i - 1)];
+    const double kSE = k[(int64_t)(j - 1) * nx + i];
+    const double kNE = k[(int64_t)j * nx + i];
+    const double kNW = k[(int64_t)j * nx + (i - 1)];
+    w[g] = (kSW + kSE + kNE + kNW) * (4.0 / 6.0);       // diagonal
+    w[n + g] = -(kSE + kNE) / 6.0;                      // E
+    w[2 * n + g] = -(kNE + kNW) / 6.0;                  // N
+    w[3 * n + g] = -2.0 * kNE / 6.0;                    // NE
+    w[4 * n + g] = -2.0 * kNW / 6.0;                    // NW
+}
+
+__device__ __forceinline__ double q1w_row(int n1, const double *w, const double *p, int i, int j,
+                                          int64_t g) {
+    const int64_t n = (int64_t)n1 * n1;
+    double v = w[g] * p[g];
+    if (i < n1) v += w[n + g] * p[g + 1];
+    if (j < n1) v += w[2 * n + g] * p[g + n1];
+    if (i < n1 && j < n1) v += w[3 * n + g] * p[g + n1 + 1];
+    if (i > 1 && j < n1) v += w[4 * n + g] * p[g + n1 - 1];
+    if (i > 1) v += w[n + g - 1] * p[g - 1];
+    if (j > 1) v += w[2 * n + g - n1] * p[g - n1];
+    if (i > 1 && j > 1) v += w[3 * n + g - n1 - 1] * p[g - n1 - 1];
+    if (i < n1 && j > 1) v += w[4 * n + g - n1 + 1] * p[g - n1 + 1];
+    return v;
 }
 
 constexpr int RB = 256;   // threads per reduction block
@@ -276,20 +850,20 @@ __device__ bool grid_reduce(double local, double *part, unsigned *counter, doubl
     return true;
 }
 
-__global__ void k_q1_spmv(int nx, const double *k, const double *x, double *y) {
+__global__ void k_q1_spmv(int nx, const double *w, const double *x, double *y) {
     const int n1 = nx - 1;
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= (int64_t)n1 * n1) return;
     const int i = (int)(g % n1) + 1, j = (int)(g / n1) + 1;
-    y[g] = q1_row(nx, k, x, i, j);
+    y[g] = q1w_row(n1, w, x, i, j, g);
 }
 
-__global__ void k_residual(int nx, const double *k, const double *b, const double *x, double *res) {
+__global__ void k_residual(int nx, const double *w, const double *b, const double *x, double *res) {
     const int n1 = nx - 1;
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= (int64_t)n1 * n1) return;
     const int i = (int)(g % n1) + 1, j = (int)(g / n1) + 1;
-    res[g] = b[g] - q1_row(nx, k, x, i, j);
+    res[g] = b[g] - q1w_row(n1, w, x, i, j, g);
 }
 
 __global__ void k_norm2(int64_t n, const double *v, double *part, unsigned *counter, double *out) {
@@ -337,7 +911,7 @@ __global__ void k_pcg_first_dir(int64_t n, double *p, const double *z, const dou
 }
 
 // q = A p ; alpha = rho / p.q
-__global__ void k_pcg_spmv_dot(int nx, const double *k, const double *p, double *q, double *part,
+__global__ void k_pcg_spmv_dot(int nx, const double *w, const double *p, double *q, double *part,
                                unsigned *counter, PcgScalars *sc, double *alphas) {
     if (sc->done) return;
     const int n1 = nx - 1;
@@ -345,7 +919,7 @@ __global__ void k_pcg_spmv_dot(int nx, const double *k, const double *p, double 
     double s = 0.0;
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
         const int i = (int)(g % n1) + 1, j = (int)(g / n1) + 1;
-        const double v = q1_row(nx, k, p, i, j);
+        const double v = q1w_row(n1, w, p, i, j, g);
         q[g] = v;
         s += v * p[g];
     }
@@ -401,8 +975,8 @@ __global__ void k_pcg_dir(int64_t n, double *p, const double *z, const PcgScalar
         p[i] = z[i] + bt * p[i];
 }
 
-// Extreme eigenvalues of the Lanczos tridiagonal matrix by bisection on
-// Sturm counts (one thread; k is the number of CG steps).
+// Extreme eigenvalues of the Lanczos tridiagonal matrix by multisection on
+// Sturm counts: one warp, 32 trial points per round.
 __device__ int sturm_count(const double *d, const double *e2, int k, double x) {
     int cnt = 0;
     double q = 1.0;
@@ -416,28 +990,41 @@ __device__ int sturm_count(const double *d, const double *e2, int k, double x) {
 
 __global__ void k_lanczos(const double *alphas, const double *betas, const PcgScalars *sc,
                           double *out, double *d, double *e2) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (blockIdx.x != 0) return;
+    const int lane = threadIdx.x & 31;
     const int k = sc->it;
-    if (k <= 0) { out[0] = out[1] = 1.0; return; }
-    double lo = 1e300, hi = -1e300;
-    for (int j = 0; j < k; ++j) {
+    if (k <= 0) {
+        if (lane == 0) out[0] = out[1] = 1.0;
+        return;
+    }
+    for (int j = lane; j < k; j += 32) {
         d[j] = 1.0 / alphas[j] + (j > 0 ? betas[j - 1] / alphas[j - 1] : 0.0);
         if (j + 1 < k) e2[j] = betas[j] / (alphas[j] * alphas[j]);
     }
-    for (int j = 0; j < k; ++j) {
+    __syncwarp();
+    double lo = 1e300, hi = -1e300;
+    for (int j = lane; j < k; j += 32) {
         const double off = (j > 0 ? sqrt(e2[j - 1]) : 0.0) + (j + 1 < k ? sqrt(e2[j]) : 0.0);
         lo = fmin(lo, d[j] - off);
         hi = fmax(hi, d[j] + off);
     }
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
     for (int which = 0; which < 2; ++which) {
         const int target = which == 0 ? 1 : k;   // smallest: count >= 1, largest: count >= k
         double a = lo, b = hi;
-        for (int it = 0; it < 200; ++it) {
-            const double mid = 0.5 * (a + b);
-            if (sturm_count(d, e2, k, mid) >= target) b = mid; else a = mid;
+        for (int round = 0; round < 40; ++round) {
+            const double x = a + (b - a) * (double)(lane + 1) / 33.0;
+            const unsigned hit = __ballot_sync(0xffffffffu, sturm_count(d, e2, k, x) >= target);
+            const int first = hit ? __ffs(hit) - 1 : 32;
+            const double na = first == 0 ? a : a + (b - a) * (double)first / 33.0;
+            const double nb = first == 32 ? b : a + (b - a) * (double)(first + 1) / 33.0;
+            a = na; b = nb;
             if (b - a <= 1e-15 * fmax(fabs(a), fabs(b))) break;
         }
-        out[which] = 0.5 * (a + b);
+        if (lane == 0) out[which] = 0.5 * (a + b);
     }
 }
 
@@ -475,51 +1062,198 @@ template <class T, class ACC> void post_t(const DevLevel &L, const double *r, do
 // ----------------------------------------------------------------------------
 // launchers
 // ----------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kSmemMax = 227 * 1024;        // dynamic shared memory of one block
+constexpr size_t kSmemBudget = kSmemMax;
+
+int num_sms() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 152;
+    }
+    return n;
+}
+
+// Warps (substructures) per block: as many as needed for one wave over the
+// SMs, limited by the shared-memory slices that fit in one block.
+int warps_per_block(int nsub, size_t slice) {
+    const int fit = (int)(kSmemMax / slice);
+    int want = (nsub + num_sms() - 1) / num_sms();
+    if (want < 4) want = 4;
+    int w = want < fit ? want : fit;
+    if (w > 16) w = 16;
+    return w < 1 ? 1 : w;
+}
+
+template <class T, class ACC, int BP>
+void dir_launch(const DevLevel &L, bool post, const double *r, double *z, const int *skip,
+                cudaStream_t s) {
+    const size_t slice = DirSlice<T, ACC, BP>::bytes(L);
+    const int wpc = warps_per_block(L.nsub, slice);
+    const size_t sm = slice * wpc;
+    const int grid = (L.nsub + wpc - 1) / wpc;
+    if (!post) k_dir_w<T, ACC, BP, false><<<grid, 32 * wpc, sm, s>>>(L, r, z, skip, (unsigned)slice);
+    else k_dir_w<T, ACC, BP, true><<<grid, 32 * wpc, sm, s>>>(L, r, z, skip, (unsigned)slice);
+}
+
+template <class T, class ACC>
+void dir_dispatch(const DevLevel &L, bool post, const double *r, double *z, const int *skip,
+                  cudaStream_t s) {
+    if (L.bp == 8) dir_launch<T, ACC, 8>(L, post, r, z, skip, s);
+    else if (L.bp == 16) dir_launch<T, ACC, 16>(L, post, r, z, skip, s);
+    else dir_launch<T, ACC, 32>(L, post, r, z, skip, s);
+}
+
+int pidx_of(int prec) { return prec == BDDC_PREC_FP64 ? 0 : (prec == BDDC_PREC_FP32 ? 1 : 2); }
+
+template <class T, class ACC>
+void neu_launch(const DevLevel &L, int prec, const double *r, const int *skip, cudaStream_t s) {
+    const int pi = pidx_of(prec);
+    const size_t slice = al16(al16((size_t)L.max_nrec[pi]) + al16(sizeof(ACC) * (size_t)L.max_nG) + 16);
+    const int wpc = warps_per_block(L.nsub, slice);
+    k_neumann_r<T, ACC><<<(L.nsub + wpc - 1) / wpc, 32 * wpc, slice * wpc, s>>>(L, pi, r, skip, (unsigned)slice);
+}
+
+template <class T, class ACC>
+void avg_launch(const DevLevel &L, int prec, const int *skip, cudaStream_t s) {
+    const int pi = pidx_of(prec);
+    const size_t slice = al16(al16((size_t)L.max_nrec[pi]) +
+                              al16(sizeof(ACC) * (size_t)(L.max_nc > 0 ? L.max_nc : 1)) + 16);
+    const int wpc = warps_per_block(L.nsub, slice);
+    k_average_r<T, ACC><<<(L.nsub + wpc - 1) / wpc, 32 * wpc, slice * wpc, s>>>(L, pi, skip, (unsigned)slice);
+}
+
+// The warp kernels need a power-of-two block size, the records and their
+// shared slices within one block.
+bool warp_path(const DevLevel &L, int prec) {
+    if (!(L.bp == 8 || L.bp == 16 || L.bp == 32) || !L.irec) return false;
+    if (L.max_m * L.bp > 32 * kUI || L.max_nG > 32 * kUG || L.max_coo > 32 * kUC ||
+        L.max_own > 32 * kUO)
+        return false;
+    const int pi = pidx_of(prec);
+    const size_t e = prec == BDDC_PREC_FP64 ? 8 : (prec == BDDC_PREC_FP32 ? 4 : 2);
+    const size_t a = prec == BDDC_PREC_FP64 ? 8 : 4;
+    const size_t dir = al16(e * L.max_fac) + al16(a * L.max_m * L.bp) + al16(a * L.max_nG) +
+                       8 * kChunks + 16;
+    const size_t neu = al16((size_t)L.max_nrec[pi]) + al16(a * L.max_nG) + 16;
+    return dir <= kSmemBudget && neu <= kSmemBudget;
+}
+
+}  // namespace
+
+void prepare_apply_kernels() {
+    const int big = (int)kSmemMax;
+#define BDDC_SMEM_ATTR(k) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, big)
+    BDDC_SMEM_ATTR((k_dir_w<double, double, 8, false>));
+    BDDC_SMEM_ATTR((k_dir_w<double, double, 8, true>));
+    BDDC_SMEM_ATTR((k_dir_w<double, double, 16, false>));
+    BDDC_SMEM_ATTR((k_dir_w<double, double, 16, true>));
+    BDDC_SMEM_ATTR((k_dir_w<double, double, 32, false>));
+    BDDC_SMEM_ATTR((k_dir_w<double, double, 32, true>));
+    BDDC_SMEM_ATTR((k_neumann_r<double, double>));
+    BDDC_SMEM_ATTR((k_average_r<double, double>));
+    BDDC_SMEM_ATTR((k_dir_w<float, float, 8, false>));
+    BDDC_SMEM_ATTR((k_dir_w<float, float, 8, true>));
+    BDDC_SMEM_ATTR((k_dir_w<float, float, 16, false>));
+    BDDC_SMEM_ATTR((k_dir_w<float, float, 16, true>));
+    BDDC_SMEM_ATTR((k_dir_w<float, float, 32, false>));
+    BDDC_SMEM_ATTR((k_dir_w<float, float, 32, true>));
+    BDDC_SMEM_ATTR((k_neumann_r<float, float>));
+    BDDC_SMEM_ATTR((k_average_r<float, float>));
+    BDDC_SMEM_ATTR((k_dir_w<__nv_bfloat16, float, 8, false>));
+    BDDC_SMEM_ATTR((k_dir_w<__nv_bfloat16, float, 8, true>));
+    BDDC_SMEM_ATTR((k_dir_w<__nv_bfloat16, float, 16, false>));
+    BDDC_SMEM_ATTR((k_dir_w<__nv_bfloat16, float, 16, true>));
+    BDDC_SMEM_ATTR((k_dir_w<__nv_bfloat16, float, 32, false>));
+    BDDC_SMEM_ATTR((k_dir_w<__nv_bfloat16, float, 32, true>));
+    BDDC_SMEM_ATTR((k_neumann_r<__nv_bfloat16, float>));
+    BDDC_SMEM_ATTR((k_average_r<__nv_bfloat16, float>));
+#undef BDDC_SMEM_ATTR
+}
+
+void build_records(DevLevel &D, const int *ownPos, const int *ownDof, cudaStream_t s) {
+    k_build_irec<<<D.nsub, 128, 0, s>>>(D, ownPos, ownDof);
+    k_build_nrec<double><<<D.nsub, 128, 0, s>>>(D, D.f64, D.nrec[0], D.nrecOff[0]);
+    k_build_nrec<float><<<D.nsub, 128, 0, s>>>(D, D.f32, D.nrec[1], D.nrecOff[1]);
+    k_build_nrec<__nv_bfloat16><<<D.nsub, 128, 0, s>>>(D, D.b16, D.nrec[2], D.nrecOff[2]);
+}
+
 void apply_level_pre(const DevLevel &L, int prec, const double *r, const int *skip, cudaStream_t s,
                      cudaEvent_t *ev) {
-    const int n = L.n_iface > L.nc ? L.n_iface : L.nc;
+    const bool wp = warp_path(L, prec);
     if (ev) cudaEventRecord(ev[0], s);
-    k_iface_init<<<(n + 255) / 256, 256, 0, s>>>(L, r, skip);
+    if (wp) {
+        if (prec == BDDC_PREC_FP64) dir_dispatch<double, double>(L, false, r, nullptr, skip, s);
+        else if (prec == BDDC_PREC_FP32) dir_dispatch<float, float>(L, false, r, nullptr, skip, s);
+        else dir_dispatch<__nv_bfloat16, float>(L, false, r, nullptr, skip, s);
+    } else {
+        if (prec == BDDC_PREC_FP64) pre_t<double, double>(L, r, skip, s);
+        else if (prec == BDDC_PREC_FP32) pre_t<float, float>(L, r, skip, s);
+        else pre_t<__nv_bfloat16, float>(L, r, skip, s);
+    }
     if (ev) cudaEventRecord(ev[1], s);
-    if (prec == BDDC_PREC_FP64) pre_t<double, double>(L, r, skip, s);
-    else if (prec == BDDC_PREC_FP32) pre_t<float, float>(L, r, skip, s);
-    else pre_t<__nv_bfloat16, float>(L, r, skip, s);
+    if (wp) {
+        if (prec == BDDC_PREC_FP64) neu_launch<double, double>(L, prec, r, skip, s);
+        else if (prec == BDDC_PREC_FP32) neu_launch<float, float>(L, prec, r, skip, s);
+        else neu_launch<__nv_bfloat16, float>(L, prec, r, skip, s);
+    } else {
+        const size_t smn = sizeof(double) * (size_t)(L.max_nG > L.max_nc ? L.max_nG : L.max_nc);
+        if (prec == BDDC_PREC_FP64) k_neumann<double, double><<<L.nsub, 128, smn, s>>>(L, r, skip);
+        else if (prec == BDDC_PREC_FP32) k_neumann<float, float><<<L.nsub, 128, smn, s>>>(L, r, skip);
+        else k_neumann<__nv_bfloat16, float><<<L.nsub, 128, smn, s>>>(L, r, skip);
+    }
     if (ev) cudaEventRecord(ev[2], s);
-    const size_t smn = sizeof(double) * (size_t)(L.max_nG > L.max_nc ? L.max_nG : L.max_nc);
-    if (prec == BDDC_PREC_FP64) k_neumann<double, double><<<L.nsub, 128, smn, s>>>(L, skip);
-    else if (prec == BDDC_PREC_FP32) k_neumann<float, float><<<L.nsub, 128, smn, s>>>(L, skip);
-    else k_neumann<__nv_bfloat16, float><<<L.nsub, 128, smn, s>>>(L, skip);
-    if (ev) cudaEventRecord(ev[3], s);
 }
 
 void apply_level_post(const DevLevel &L, int prec, const double *r, double *z, const int *skip,
                       cudaStream_t s, cudaEvent_t *ev) {
-    const size_t smn = sizeof(double) * (size_t)(L.max_nc > 0 ? L.max_nc : 1);
+    const bool wp = warp_path(L, prec);
     if (ev) cudaEventRecord(ev[0], s);
-    if (prec == BDDC_PREC_FP64) k_average<double, double><<<L.nsub, 128, smn, s>>>(L, skip);
-    else if (prec == BDDC_PREC_FP32) k_average<float, float><<<L.nsub, 128, smn, s>>>(L, skip);
-    else k_average<__nv_bfloat16, float><<<L.nsub, 128, smn, s>>>(L, skip);
+    if (wp) {
+        if (prec == BDDC_PREC_FP64) avg_launch<double, double>(L, prec, skip, s);
+        else if (prec == BDDC_PREC_FP32) avg_launch<float, float>(L, prec, skip, s);
+        else avg_launch<__nv_bfloat16, float>(L, prec, skip, s);
+    } else {
+        const size_t smn = sizeof(double) * (size_t)(L.max_nc > 0 ? L.max_nc : 1);
+        if (prec == BDDC_PREC_FP64) k_average<double, double><<<L.nsub, 128, smn, s>>>(L, skip);
+        else if (prec == BDDC_PREC_FP32) k_average<float, float><<<L.nsub, 128, smn, s>>>(L, skip);
+        else k_average<__nv_bfloat16, float><<<L.nsub, 128, smn, s>>>(L, skip);
+    }
     if (ev) cudaEventRecord(ev[1], s);
-    if (prec == BDDC_PREC_FP64) post_t<double, double>(L, r, z, skip, s);
-    else if (prec == BDDC_PREC_FP32) post_t<float, float>(L, r, z, skip, s);
-    else post_t<__nv_bfloat16, float>(L, r, z, skip, s);
+    if (wp) {
+        if (prec == BDDC_PREC_FP64) dir_dispatch<double, double>(L, true, r, z, skip, s);
+        else if (prec == BDDC_PREC_FP32) dir_dispatch<float, float>(L, true, r, z, skip, s);
+        else dir_dispatch<__nv_bfloat16, float>(L, true, r, z, skip, s);
+    } else {
+        if (prec == BDDC_PREC_FP64) post_t<double, double>(L, r, z, skip, s);
+        else if (prec == BDDC_PREC_FP32) post_t<float, float>(L, r, z, skip, s);
+        else post_t<__nv_bfloat16, float>(L, r, z, skip, s);
+    }
     if (ev) cudaEventRecord(ev[2], s);
 }
 
-void launch_dense_symv(int n, const double *A, const double *x, double *y, const int *skip,
+void launch_dense_symv(int n, int ld, const double *A, const double *x, double *y, const int *skip,
                        cudaStream_t s) {
     if (n <= 0) return;
-    k_dense_symv<<<(n + 7) / 8, 256, 0, s>>>(n, A, x, y, skip);
+    k_dense_symv<<<(n + 7) / 8, 256, 0, s>>>(n, ld, A, x, y, skip);
 }
 
-void launch_q1_spmv(int nx, const double *k, const double *x, double *y, cudaStream_t s) {
+void launch_q1_weights(int nx, const double *k, double *w, cudaStream_t s) {
     const int64_t n = (int64_t)(nx - 1) * (nx - 1);
-    k_q1_spmv<<<(int)((n + 255) / 256), 256, 0, s>>>(nx, k, x, y);
+    k_q1_weights<<<(int)((n + 255) / 256), 256, 0, s>>>(nx, k, w);
 }
-void launch_residual(int nx, const double *k, const double *b, const double *x, double *res,
+void launch_q1_spmv(int nx, const double *w, const double *x, double *y, cudaStream_t s) {
+    const int64_t n = (int64_t)(nx - 1) * (nx - 1);
+    k_q1_spmv<<<(int)((n + 255) / 256), 256, 0, s>>>(nx, w, x, y);
+}
+void launch_residual(int nx, const double *w, const double *b, const double *x, double *res,
                      cudaStream_t s) {
     const int64_t n = (int64_t)(nx - 1) * (nx - 1);
-    k_residual<<<(int)((n + 255) / 256), 256, 0, s>>>(nx, k, b, x, res);
+    k_residual<<<(int)((n + 255) / 256), 256, 0, s>>>(nx, w, b, x, res);
 }
 void launch_norm2(int n, const double *v, double *part, unsigned *counter, double *out,
                   cudaStream_t s) {
@@ -533,10 +1267,10 @@ void launch_pcg_first_dir(int n, double *p, const double *z, const double *r, do
                           unsigned *counter, PcgScalars *sc, cudaStream_t s) {
     k_pcg_first_dir<<<grid_for(n), RB, 0, s>>>(n, p, z, r, part, counter, sc);
 }
-void launch_pcg_spmv_dot(int nx, const double *k, const double *p, double *q, double *part,
+void launch_pcg_spmv_dot(int nx, const double *w, const double *p, double *q, double *part,
                          unsigned *counter, PcgScalars *sc, double *alphas, cudaStream_t s) {
     const int64_t n = (int64_t)(nx - 1) * (nx - 1);
-    k_pcg_spmv_dot<<<grid_for(n), RB, 0, s>>>(nx, k, p, q, part, counter, sc, alphas);
+    k_pcg_spmv_dot<<<grid_for(n), RB, 0, s>>>(nx, w, p, q, part, counter, sc, alphas);
 }
 void launch_pcg_update(int n, double *x, double *r, const double *p, const double *q,
                        double *part, unsigned *counter, PcgScalars *sc, cudaStream_t s) {

@@ -94,9 +94,11 @@ struct bddc_ctx {
     int prec = BDDC_PREC_FP64;
     DevArena arena;
     double *k_dev = nullptr;
+    double *w_dev = nullptr;          // Q1 stencil weights [5][n]
     std::vector<LevelData> L;
-    int n_top = 0;
-    double *Ainv = nullptr;
+    int n_top = 0, ld_top = 0;
+    double *Ainv = nullptr;           // top-level inverse, leading dimension ld_top
+    int *err_dev = nullptr;           // set by kernels whose bounded waits gave up
     std::unique_ptr<Workspace> ws;
     double setup_ms = 0.0;
     std::mutex mu;
@@ -331,11 +333,16 @@ void setup_level(bddc_ctx *C, LevelData &LD, const double *emat, const std::vect
     DevArena &A = C->arena;
     DevLevel &D = LD.D;
     D.n = H.n; D.nsub = ns; D.n_iface = (int)H.iface_dof.size();
+    D.bp = H.block_uniform;
     D.nI = A.upload(nI, st); D.nG = A.upload(nG, st); D.bsz = A.upload(bsz, st); D.nblk = A.upload(nblk, st);
     std::vector<int64_t> szF(ns), szN(ns);
     for (int s = 0; s < ns; ++s) {
-        szF[s] = (int64_t)nblk[s] * 2 * bsz[s] * bsz[s];
-        szN[s] = (int64_t)nG[s] * nG[s];
+        // padded to 8 elements so that every block starts 16-byte aligned in
+        // all three precisions (bulk copies into shared memory)
+        szF[s] = ((int64_t)nblk[s] * 2 * bsz[s] * bsz[s] + 7) & ~int64_t(7);
+        szN[s] = ((int64_t)nG[s] * nG[s] + 7) & ~int64_t(7);
+        D.max_fac = std::max(D.max_fac, szF[s]);
+        D.max_nmat = std::max(D.max_nmat, szN[s]);
         D.max_nI = std::max(D.max_nI, nI[s]); D.max_nG = std::max(D.max_nG, nG[s]);
         D.max_b = std::max(D.max_b, bsz[s]); D.max_m = std::max(D.max_m, nblk[s]);
     }
@@ -364,6 +371,8 @@ void setup_level(bddc_ctx *C, LevelData &LD, const double *emat, const std::vect
     D.f64.dir = A.alloc_n<double>(std::max<int64_t>(oF.back(), 1));
     D.f64.aig = A.alloc_n<double>(std::max<int64_t>(oCOO.back(), 1));
     D.f64.wg = A.alloc_n<double>(std::max<int64_t>(oG.back(), 1));
+    BDDC_CUDA_TRY(cudaMemsetAsync(D.f64.dir, 0, sizeof(double) * std::max<int64_t>(oF.back(), 1), st));
+    D.err = C->err_dev;
 
     // ---- numerics: assembly, factorization, Schur complements, weights
     BDDC_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
@@ -373,7 +382,7 @@ void setup_level(bddc_ctx *C, LevelData &LD, const double *emat, const std::vect
     launch_band_cholesky(S, err, st);
     check_err(err, st, "interior Cholesky");
     launch_schur(S, D.max_nG, st);
-    launch_dirichlet_blocks(S, D, st);
+    launch_dirichlet_blocks(S, D, nullptr, nullptr, st);
     double *diag_sum = tmp.alloc_n<double>(std::max(D.n_iface, 1));
     BDDC_CUDA_TRY(cudaMemsetAsync(diag_sum, 0, sizeof(double) * std::max(D.n_iface, 1), st));
     launch_weights(S, D, diag_sum, st);
@@ -402,7 +411,8 @@ void setup_level(bddc_ctx *C, LevelData &LD, const double *emat, const std::vect
         ncl[s] = (int)LD.rc[s].size();
         if (ncl[s] > 256) throw Error(BDDC_E_ARG, "more than 256 coarse DOFs on one substructure");
         D.max_nc = std::max(D.max_nc, ncl[s]);
-        szP[s] = (int64_t)ncl[s] * nG[s];
+        szP[s] = ((int64_t)ncl[s] * nG[s] + 7) & ~int64_t(7);
+        D.max_psit = std::max(D.max_psit, szP[s]);
         szAc[s] = (int64_t)ncl[s] * ncl[s];
         szCon[s] = (int64_t)ncl[s] * nG[s];
         const int64_t g = nG[s], c = ncl[s];
@@ -429,6 +439,8 @@ void setup_level(bddc_ctx *C, LevelData &LD, const double *emat, const std::vect
     D.rc = A.upload(rcat, st);
     D.f64.nmat = A.alloc_n<double>(std::max<int64_t>(oN.back(), 1));
     D.f64.psit = A.alloc_n<double>(std::max<int64_t>(oP.back(), 1));
+    BDDC_CUDA_TRY(cudaMemsetAsync(D.f64.nmat, 0, sizeof(double) * std::max<int64_t>(oN.back(), 1), st));
+    BDDC_CUDA_TRY(cudaMemsetAsync(D.f64.psit, 0, sizeof(double) * std::max<int64_t>(oP.back(), 1), st));
     NeumannBatch NB;
     NB.ncl = D.ncl;
     NB.offCon = tmp.upload(oCon, st);
@@ -472,6 +484,48 @@ void setup_level(bddc_ctx *C, LevelData &LD, const double *emat, const std::vect
     launch_convert(D.f64.psit, D.b16.psit, oP.back(), st);
     launch_convert(D.f64.wg, D.b16.wg, oG.back(), st);
     BDDC_CUDA_TRY(cudaGetLastError());
+
+    // ---- per-substructure records read by the warp kernels with one bulk copy
+    {
+        std::vector<int> ncoo_v(ns), nown_v(ns), ownPos, ownDof;
+        std::vector<int64_t> irOff(ns + 1, 0);
+        std::vector<int64_t> nrOff[3];
+        const int esz[3] = {8, 4, 2};
+        for (int p = 0; p < 3; ++p) nrOff[p].assign(ns + 1, 0);
+        std::vector<int> gp(H.n, -1);
+        for (int s = 0; s < ns; ++s) {
+            ncoo_v[s] = (int)cooCnt[s];
+            nown_v[s] = (int)ownCnt[s];
+            for (int k = 0; k < nG[s]; ++k) gp[H.Gord[s][k]] = k;
+            for (int id : ownl[s]) {
+                ownPos.push_back(gp[H.iface_dof[id]]);
+                ownDof.push_back(H.iface_dof[id]);
+            }
+            for (int g : H.Gord[s]) gp[g] = -1;
+            D.max_coo = std::max(D.max_coo, ncoo_v[s]);
+            D.max_own = std::max(D.max_own, nown_v[s]);
+            const IRecLayout il(nI[s], nG[s], ncoo_v[s], nown_v[s]);
+            irOff[s + 1] = irOff[s] + il.bytes;
+            D.max_irec = std::max(D.max_irec, il.bytes);
+            for (int p = 0; p < 3; ++p) {
+                const NRecLayout nl(nG[s], ncl[s], esz[p]);
+                nrOff[p][s + 1] = nrOff[p][s] + nl.bytes;
+                D.max_nrec[p] = std::max(D.max_nrec[p], nl.bytes);
+            }
+        }
+        D.ncoo = A.upload(ncoo_v, st);
+        D.nown = A.upload(nown_v, st);
+        D.irecOff = A.upload(irOff, st);
+        D.irec = A.alloc_n<unsigned char>(std::max<int64_t>(irOff.back(), 16));
+        for (int p = 0; p < 3; ++p) {
+            D.nrecOff[p] = A.upload(nrOff[p], st);
+            D.nrec[p] = A.alloc_n<unsigned char>(std::max<int64_t>(nrOff[p].back(), 16));
+        }
+        int *dOwnPos = tmp.upload(ownPos, st);
+        int *dOwnDof = tmp.upload(ownDof, st);
+        build_records(D, dOwnPos, dOwnDof, st);
+        BDDC_CUDA_TRY(cudaGetLastError());
+    }
 }
 
 void make_workspace(bddc_ctx *C, Workspace &W, int maxit_cap) {
@@ -485,8 +539,14 @@ void make_workspace(bddc_ctx *C, Workspace &W, int maxit_cap) {
         int64_t sg = 0;
         for (auto &v : LD.H.Gord) sg += (int64_t)v.size();
         D.w = A.alloc_n<double>(std::max<int64_t>(sg, 1));
-        D.rcv = A.alloc_n<double>(std::max(D.nc, 1));
-        D.ucv = A.alloc_n<double>(std::max(D.nc, 1));
+        // rcv doubles as the input of the top-level product: padded to the
+        // inverse's leading dimension and zero there
+        const int ncp = std::max(std::max(D.nc, 1), C->ld_top);
+        D.rcv = A.alloc_n<double>(ncp);
+        D.ucv = A.alloc_n<double>(ncp);
+        BDDC_CUDA_TRY(cudaMemset(D.rB, 0, sizeof(double) * std::max(D.n_iface, 1)));
+        BDDC_CUDA_TRY(cudaMemset(D.uB, 0, sizeof(double) * std::max(D.n_iface, 1)));
+        BDDC_CUDA_TRY(cudaMemset(D.rcv, 0, sizeof(double) * ncp));
         W.lv.push_back(D);
     }
     W.x = A.alloc_n<double>(n); W.r = A.alloc_n<double>(n); W.z = A.alloc_n<double>(n);
@@ -513,7 +573,7 @@ void apply_rec(bddc_ctx *C, Workspace &W, int l, int prec, const double *r, doub
     const DevLevel &D = W.lv[l];
     apply_level_pre(D, prec, r, skip, st);
     if (l + 1 == (int)W.lv.size())
-        launch_dense_symv(C->n_top, C->Ainv, D.rcv, D.ucv, skip, st);
+        launch_dense_symv(C->n_top, C->ld_top, C->Ainv, D.rcv, D.ucv, skip, st);
     else
         apply_rec(C, W, l + 1, prec, D.rcv, D.ucv, skip, st);
     apply_level_post(D, prec, r, z, skip, st);
@@ -525,7 +585,7 @@ cudaGraphExec_t pcg_graph(bddc_ctx *C, Workspace &W, int prec) {
     cudaStream_t st = W.stream;
     cudaGraph_t g;
     BDDC_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    launch_pcg_spmv_dot(C->nx, C->k_dev, W.p, W.q, W.part, W.counter, W.sc, W.alphas, st);
+    launch_pcg_spmv_dot(C->nx, C->w_dev, W.p, W.q, W.part, W.counter, W.sc, W.alphas, st);
     launch_pcg_update(n, W.x, W.r, W.p, W.q, W.part, W.counter, W.sc, st);
     apply_rec(C, W, 0, prec, W.r, W.z, &W.sc->done, st);
     launch_pcg_rz(n, W.r, W.z, W.part, W.counter, W.sc, W.betas, st);
@@ -546,7 +606,7 @@ int pcg_one(bddc_ctx *C, Workspace &W, int prec, const double *b, double *x, dou
     apply_rec(C, W, 0, prec, W.r, W.z, &W.sc->done, st);
     launch_pcg_first_dir(n, W.p, W.z, W.r, W.part, W.counter, W.sc, st);
     cudaGraphExec_t g = pcg_graph(C, W, prec);
-    const int per_apply = 5 * (int)W.lv.size() + 1;
+    const int per_apply = 4 * (int)W.lv.size() + 1;
     int launches = 2 + per_apply;
     int chunk = 4;
     double rr_true = 0.0;
@@ -557,7 +617,7 @@ int pcg_one(bddc_ctx *C, Workspace &W, int prec, const double *b, double *x, dou
         BDDC_CUDA_TRY(cudaStreamSynchronize(st));
         if (!W.hsc->done) { chunk = std::min(chunk * 2, 16); continue; }
         // Confirm with the true residual; keep iterating if it is not yet met.
-        launch_residual(C->nx, C->k_dev, b, W.x, W.tmp, st);
+        launch_residual(C->nx, C->w_dev, b, W.x, W.tmp, st);
         launch_norm2(n, W.tmp, W.part, W.counter, W.lout, st);
         launches += 2;
         BDDC_CUDA_TRY(cudaMemcpyAsync(W.hout, W.lout, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -577,8 +637,11 @@ int pcg_one(bddc_ctx *C, Workspace &W, int prec, const double *b, double *x, dou
     launches += 1;
     BDDC_CUDA_TRY(cudaMemcpyAsync(W.hout + 1, W.lout + 1, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
     BDDC_CUDA_TRY(cudaMemcpyAsync(x, W.x, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    int kerr = 0;
+    BDDC_CUDA_TRY(cudaMemcpyAsync(&kerr, C->err_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
     BDDC_CUDA_TRY(cudaStreamSynchronize(st));
     BDDC_CUDA_TRY(cudaGetLastError());
+    if (kerr) throw Error(BDDC_E_TIMEOUT, "a bounded device wait gave up during the solve");
     const PcgScalars &h = *W.hsc;
     const int status = (h.conv && rr_true <= h.tol2 * (1 + 1e-12)) ? BDDC_OK : BDDC_E_NOCONV;
     if (info) {
@@ -651,6 +714,12 @@ int bddc_setup(const bddc_mesh *mesh, const double *k_elem, const bddc_decomp *d
         }
         std::vector<double> kv(k_elem, k_elem + nelem);
         C->k_dev = C->arena.upload(kv, st);
+        C->w_dev = C->arena.alloc_n<double>((size_t)5 * (nx - 1) * (nx - 1));
+        launch_q1_weights(nx, C->k_dev, C->w_dev, st);
+        C->err_dev = C->arena.alloc_n<int>(1);
+        BDDC_CUDA_TRY(cudaMemsetAsync(C->err_dev, 0, sizeof(int), st));
+        static std::once_flag prep_once;
+        std::call_once(prep_once, prepare_apply_kernels);
         DevArena tmp;
         int *err = tmp.alloc_n<int>(1);
         BDDC_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
@@ -721,10 +790,13 @@ int bddc_setup(const bddc_mesh *mesh, const double *k_elem, const bddc_decomp *d
                 launch_scatter_dense(T.H.nsub, dn, doc, drc, doac, T.ac, Atop, nt, st);
                 dense_cholesky(nt, Atop, err, st);
                 check_err(err, st, "top-level Cholesky");
-                C->Ainv = C->arena.alloc_n<double>((size_t)nt * nt);
-                dense_inverse_from_cholesky(nt, Atop, C->Ainv, nullptr, st);
+                C->ld_top = (nt + 3) & ~3;
+                C->Ainv = C->arena.alloc_n<double>((size_t)nt * C->ld_top);
+                BDDC_CUDA_TRY(cudaMemsetAsync(C->Ainv, 0, sizeof(double) * (size_t)nt * C->ld_top, st));
+                dense_inverse_from_cholesky(nt, Atop, C->Ainv, C->ld_top, st);
             } else {
-                C->Ainv = C->arena.alloc_n<double>(1);
+                C->Ainv = C->arena.alloc_n<double>(4);
+                C->ld_top = 4;
             }
         }
         BDDC_CUDA_TRY(cudaStreamSynchronize(st));
@@ -765,7 +837,7 @@ int bddc_apply(bddc_ctx *ctx, const double *r_dev, double *z_dev, int nrhs, int6
 int bddc_operator(bddc_ctx *ctx, const double *x_dev, double *y_dev, void *stream) {
     return guarded([&]() -> int {
         if (!ctx || !x_dev || !y_dev) throw Error(BDDC_E_ARG, "bad argument");
-        launch_q1_spmv(ctx->nx, ctx->k_dev, x_dev, y_dev, (cudaStream_t)stream);
+        launch_q1_spmv(ctx->nx, ctx->w_dev, x_dev, y_dev, (cudaStream_t)stream);
         BDDC_CUDA_TRY(cudaGetLastError());
         return BDDC_OK;
     });
@@ -877,9 +949,9 @@ int bddc_profile_apply(bddc_ctx *ctx, const double *r_dev, int reps, double *ms_
         std::lock_guard<std::mutex> lk(ctx->mu);
         Workspace &W = *ctx->ws;
         const int nl = (int)W.lv.size();
-        const int nseg = 3 * nl + 1 + 2 * nl;
+        const int nseg = 2 * nl + 1 + 2 * nl;
         if (max_out < nseg) throw Error(BDDC_E_ARG, "max_out too small");
-        std::vector<cudaEvent_t> ev(5 * nl + 2 + 4 * nl);
+        std::vector<cudaEvent_t> ev(3 * nl + 2 + 3 * nl);
         for (auto &e : ev) BDDC_CUDA_TRY(cudaEventCreate(&e));
         std::vector<double> acc(nseg, 0.0);
         cudaStream_t st = W.stream;
@@ -888,7 +960,7 @@ int bddc_profile_apply(bddc_ctx *ctx, const double *r_dev, int reps, double *ms_
             // down-sweep with 4 events per level, top with 2, up-sweep with 3 per level
             std::vector<cudaEvent_t *> down(nl), up(nl);
             int k = 0;
-            for (int l = 0; l < nl; ++l) { down[l] = &ev[k]; k += 4; }
+            for (int l = 0; l < nl; ++l) { down[l] = &ev[k]; k += 3; }
             cudaEvent_t *top = &ev[k]; k += 2;
             for (int l = 0; l < nl; ++l) { up[l] = &ev[k]; k += 3; }
             std::vector<const double *> rin(nl);
@@ -898,7 +970,7 @@ int bddc_profile_apply(bddc_ctx *ctx, const double *r_dev, int reps, double *ms_
                 if (l + 1 < nl) rin[l + 1] = W.lv[l].rcv;
             }
             BDDC_CUDA_TRY(cudaEventRecord(top[0], st));
-            launch_dense_symv(ctx->n_top, ctx->Ainv, W.lv[nl - 1].rcv, W.lv[nl - 1].ucv, nullptr, st);
+            launch_dense_symv(ctx->n_top, ctx->ld_top, ctx->Ainv, W.lv[nl - 1].rcv, W.lv[nl - 1].ucv, nullptr, st);
             BDDC_CUDA_TRY(cudaEventRecord(top[1], st));
             for (int l = nl - 1; l >= 0; --l)
                 apply_level_post(W.lv[l], ctx->prec, rin[l], l == 0 ? z : W.lv[l - 1].ucv, nullptr, st, up[l]);
@@ -906,7 +978,7 @@ int bddc_profile_apply(bddc_ctx *ctx, const double *r_dev, int reps, double *ms_
             int seg = 0;
             float ms;
             for (int l = 0; l < nl; ++l)
-                for (int j = 0; j < 3; ++j) { cudaEventElapsedTime(&ms, down[l][j], down[l][j + 1]); acc[seg++] += ms; }
+                for (int j = 0; j < 2; ++j) { cudaEventElapsedTime(&ms, down[l][j], down[l][j + 1]); acc[seg++] += ms; }
             cudaEventElapsedTime(&ms, top[0], top[1]); acc[seg++] += ms;
             for (int l = nl - 1; l >= 0; --l)
                 for (int j = 0; j < 2; ++j) { cudaEventElapsedTime(&ms, up[l][j], up[l][j + 1]); acc[seg++] += ms; }
@@ -965,8 +1037,8 @@ int bddc_apply_noalloc(bddc_ctx *ctx, const double *r_dev, double *z_dev, void *
             sz[l][0] = up(std::max(D.n_iface, 1));
             sz[l][1] = up(std::max(D.n_iface, 1));
             sz[l][2] = up(std::max<int64_t>(ctx->L[l].sumG, 1));
-            sz[l][3] = up(std::max(D.nc, 1));
-            sz[l][4] = up(std::max(D.nc, 1));
+            sz[l][3] = up(std::max(std::max(D.nc, 1), ctx->ld_top));
+            sz[l][4] = up(std::max(std::max(D.nc, 1), ctx->ld_top));
             for (int k = 0; k < 5; ++k) need += sz[l][k];
         }
         if (need > kNoallocDoubles)
@@ -986,12 +1058,15 @@ int bddc_apply_noalloc(bddc_ctx *ctx, const double *r_dev, double *z_dev, void *
         }
         cudaStream_t st = (cudaStream_t)stream;
         const int prec = ctx->prec;
+        // The array keeps whatever the last call (of any context) left in it;
+        // the apply expects its interface and coarse accumulators at zero.
+        BDDC_CUDA_TRY(cudaMemsetAsync(base, 0, off * sizeof(double), st));
         const double *rin[3] = {r_dev, nullptr, nullptr};
         for (int l = 0; l < nl; ++l) {
             apply_level_pre(lv[l], prec, rin[l], nullptr, st);
             if (l + 1 < nl) rin[l + 1] = lv[l].rcv;
         }
-        launch_dense_symv(ctx->n_top, ctx->Ainv, lv[nl - 1].rcv, lv[nl - 1].ucv, nullptr, st);
+        launch_dense_symv(ctx->n_top, ctx->ld_top, ctx->Ainv, lv[nl - 1].rcv, lv[nl - 1].ucv, nullptr, st);
         for (int l = nl - 1; l >= 0; --l)
             apply_level_post(lv[l], prec, rin[l], l == 0 ? z_dev : lv[l - 1].ucv, nullptr, st);
         BDDC_CUDA_TRY(cudaGetLastError());

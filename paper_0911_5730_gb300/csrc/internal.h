@@ -84,6 +84,51 @@ struct DevLevel {
     double *w = nullptr;      // [sum nG]
     double *rcv = nullptr;    // [nc]  coarse right-hand side
     double *ucv = nullptr;    // [nc]  coarse correction
+    int *err = nullptr;       // device flag: a bounded wait gave up
+    // largest per-substructure operator blocks (elements, padded to 8)
+    int64_t max_fac = 0, max_nmat = 0, max_psit = 0;
+    int bp = 0;               // common power-of-two block size of the interior factors (0: none)
+    // Per-substructure records read by one bulk copy each (built after setup):
+    //  irec: [A_{Gamma I} values (double) | interior ids | interface ids |
+    //         coupling pattern (gl<<16 | il) | owned (Gamma position, dof) pairs]
+    //  nrec[p]: [Psi^T | weights | interface ids | coarse ids | N] in precision p
+    unsigned char *irec = nullptr;
+    int64_t *irecOff = nullptr;
+    //  (nrec also holds the level DOF of each Gamma entry before N)
+    unsigned char *nrec[3] = {nullptr, nullptr, nullptr};
+    int64_t *nrecOff[3] = {nullptr, nullptr, nullptr};
+    int *ncoo = nullptr, *nown = nullptr;    // per substructure
+    int *gdofG = nullptr;     // level DOF of each Gamma entry (concatenated like idxG)
+    int64_t max_irec = 0, max_nrec[3] = {0, 0, 0};
+    int max_own = 0;          // largest owned-interface list (max_coo: largest coupling)
+};
+
+// Byte layout of the records (shared by host and device).
+struct IRecLayout {
+    int64_t cv, iI, iG, pr, ow, bytes;
+    __host__ __device__ IRecLayout(int nI, int nG, int ncoo, int nown) {
+        auto a16 = [](int64_t v) { return (v + 15) & ~int64_t(15); };
+        cv = 0;
+        iI = a16(8LL * ncoo);
+        iG = iI + a16(4LL * nI);
+        pr = iG + a16(4LL * nG);
+        ow = pr + a16(4LL * ncoo);
+        bytes = ow + a16(8LL * nown);
+    }
+};
+struct NRecLayout {
+    int64_t psi, wg, iG, rc, gG, N, avg_bytes, bytes;
+    __host__ __device__ NRecLayout(int nG, int nc, int esz) {
+        auto a16 = [](int64_t v) { return (v + 15) & ~int64_t(15); };
+        psi = 0;
+        wg = a16((int64_t)esz * nc * nG);
+        iG = wg + a16((int64_t)esz * nG);
+        rc = iG + a16(4LL * nG);
+        gG = rc + a16(4LL * nc);
+        N = gG + a16(4LL * nG);
+        avg_bytes = gG;
+        bytes = N + a16((int64_t)esz * nG * nG);
+    }
 };
 
 // ----------------------------------------------------------------------------
@@ -91,23 +136,34 @@ struct DevLevel {
 // ----------------------------------------------------------------------------
 // Down-sweep of one level: interface init, (4)-(5) pre-correction, (6)-(8)
 // substructure correction and coarse right-hand side.
-// ev (optional, 4 events) are recorded before each kernel and after the last.
+// ev (optional, 3 events) are recorded before each kernel and after the last.
+// Scratch protocol of a level: rB and rcv are zero when an apply starts
+// (the averaging kernel clears them after use) and the pre-correction clears
+// uB before the averaging kernel accumulates into it.
 void apply_level_pre(const DevLevel &L, int prec, const double *r, const int *skip,
                      cudaStream_t s, cudaEvent_t *ev = nullptr);
 // Up-sweep of one level: (9) averaging, (10)-(11) post-correction into z.
 // ev (optional, 3 events) are recorded before each kernel and after the last.
 void apply_level_post(const DevLevel &L, int prec, const double *r, double *z, const int *skip,
                       cudaStream_t s, cudaEvent_t *ev = nullptr);
-void launch_dense_symv(int n, const double *A, const double *x, double *y, const int *skip,
+// y = A x with A dense n x n, leading dimension ld (a multiple of 4, zero
+// padded); x must be readable and zero on [n, ld).
+void launch_dense_symv(int n, int ld, const double *A, const double *x, double *y, const int *skip,
                        cudaStream_t s);
+// Raise the dynamic shared-memory limit of the warp-per-substructure kernels (once).
+void prepare_apply_kernels();
+// Build the per-substructure records of a level (after its operators exist).
+void build_records(DevLevel &D, const int *ownPos, const int *ownDof, cudaStream_t s);
 
 struct PcgScalars {
     double rho, rho_new, pq, alpha, beta, rr, bb, tol2;
     int it, done, conv, maxit;
 };
-void launch_q1_spmv(int nx, const double *k, const double *x, double *y, cudaStream_t s);
+// Q1 operator from per-node stencil weights w [5][n] (diagonal, E, N, NE, NW).
+void launch_q1_weights(int nx, const double *k, double *w, cudaStream_t s);
+void launch_q1_spmv(int nx, const double *w, const double *x, double *y, cudaStream_t s);
 // q = A p, pq = p.q (partials reduced by the last block), alpha = rho / pq
-void launch_pcg_spmv_dot(int nx, const double *k, const double *p, double *q, double *part,
+void launch_pcg_spmv_dot(int nx, const double *w, const double *p, double *q, double *part,
                          unsigned *counter, PcgScalars *sc, double *alphas, cudaStream_t s);
 // x += alpha p; r -= alpha q; rr = r.r; convergence flag
 void launch_pcg_update(int n, double *x, double *r, const double *p, const double *q,
@@ -120,7 +176,7 @@ void launch_pcg_init(int n, const double *b, double *x, double *r, double *part,
                      unsigned *counter, PcgScalars *sc, double tol, int maxit, cudaStream_t s);
 void launch_pcg_first_dir(int n, double *p, const double *z, const double *r, double *part,
                           unsigned *counter, PcgScalars *sc, cudaStream_t s);
-void launch_residual(int nx, const double *k, const double *b, const double *x, double *res,
+void launch_residual(int nx, const double *w, const double *b, const double *x, double *res,
                      cudaStream_t s);
 void launch_norm2(int n, const double *v, double *part, unsigned *counter, double *out,
                   cudaStream_t s);
@@ -155,7 +211,10 @@ void launch_q1_element_matrices(int nelem, const double *k, double *emat, cudaSt
 void launch_assemble(const SetupLevel &S, int *err, cudaStream_t s);
 void launch_band_cholesky(const SetupLevel &S, int *err, cudaStream_t s);
 void launch_schur(const SetupLevel &S, int max_nG, cudaStream_t s);
-void launch_dirichlet_blocks(const SetupLevel &S, const DevLevel &L, cudaStream_t s);
+// Block factor of the interior solves; with a power-of-two block size the
+// chain form (Linv, M, P per block) is built through `scratch`.
+void launch_dirichlet_blocks(const SetupLevel &S, const DevLevel &L, double *scratch,
+                             const int64_t *offScratch, cudaStream_t s);
 void launch_extract_coo(const SetupLevel &S, const DevLevel &L, const int64_t *cooSrc,
                         cudaStream_t s);
 void launch_weights(const SetupLevel &S, const DevLevel &L, double *diag_sum, cudaStream_t s);
@@ -202,7 +261,6 @@ void launch_scatter_dense(int nsub, const int *ncl, const int64_t *offC, const i
                           const int64_t *offAc, const double *ac, double *A, int n,
                           cudaStream_t s);
 void dense_cholesky(int n, double *A, int *err, cudaStream_t s);
-void dense_inverse_from_cholesky(int n, const double *L, double *Ainv, double *work,
-                                 cudaStream_t s);
+void dense_inverse_from_cholesky(int n, const double *L, double *Ainv, int ld, cudaStream_t s);
 
 }  // namespace bddc

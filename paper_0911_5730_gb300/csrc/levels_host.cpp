@@ -182,6 +182,7 @@ void HLevel::build() {
     Iord.assign(nsub, {}); Gord.assign(nsub, {});
     bw.assign(nsub, 0); bsz.assign(nsub, 1); nblk.assign(nsub, 0);
     std::vector<int> loc(n, -1);
+    std::vector<std::vector<int>> first_all(nsub);   // lowest coupled position per row
     for (int s = 0; s < nsub; ++s) {
         std::vector<int> I;
         for (int g : sub_dofs[s]) (is_iface[g] ? Gord[s] : I).push_back(g);
@@ -211,10 +212,43 @@ void HLevel::build() {
         }
         Iord[s].resize(I.size());
         for (size_t k = 0; k < I.size(); ++k) Iord[s][k] = I[best[k]];
+        {
+            std::vector<int> pos(I.size());
+            for (size_t k = 0; k < I.size(); ++k) pos[best[k]] = (int)k;
+            auto &fst = first_all[s];
+            fst.resize(I.size());
+            for (size_t k = 0; k < I.size(); ++k) {
+                int f = (int)k;
+                for (int v : adj[best[k]]) f = std::min(f, pos[v]);
+                fst[k] = f;
+            }
+        }
         for (int g : I) loc[g] = -1;
         bw[s] = std::max(bwn, 0);
         bsz[s] = std::max(bn, 1);
         nblk[s] = I.empty() ? 0 : (int)((I.size() + bsz[s] - 1) / bsz[s]);
+    }
+    // Prefer one power-of-two block size for the whole level (the apply
+    // kernels then unroll the block solves completely).
+    block_uniform = 0;
+    int bmax = 1;
+    for (int s = 0; s < nsub; ++s) bmax = std::max(bmax, bsz[s]);
+    int bp = 1;
+    while (bp < bmax) bp *= 2;
+    if (bp < 8) bp = 8;
+    if (bp <= 32) {
+        bool ok = true;
+        for (int s = 0; s < nsub && ok; ++s) {
+            const auto &fst = first_all[s];
+            for (size_t k = 0; k < fst.size() && ok; ++k) ok = ((int)k / bp - fst[k] / bp) <= 1;
+        }
+        if (ok) {
+            block_uniform = bp;
+            for (int s = 0; s < nsub; ++s) {
+                bsz[s] = bp;
+                nblk[s] = Iord[s].empty() ? 0 : (int)((Iord[s].size() + bp - 1) / bp);
+            }
+        }
     }
     iface_id.assign(n, -1);
     iface_dof.clear();

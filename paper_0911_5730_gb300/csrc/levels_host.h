@@ -37,6 +37,7 @@ struct HLevel {
     std::vector<char> floating;
     std::vector<std::vector<int>> Iord, Gord;   // interior (banded order), interface (ascending)
     std::vector<int> bw, bsz, nblk;
+    int block_uniform = 0;          // common power-of-two block size, 0 if none
     std::vector<int> iface_id, iface_dof;
 
     void build();

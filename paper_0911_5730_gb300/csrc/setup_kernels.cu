@@ -206,11 +206,17 @@ __global__ void k_schur(SetupLevel S) {
 // [j b, j b + b): Linv_j = L_jj^{-1} and Lsub_j = L_{j, j-1}, both b x b,
 // column-major; padded rows are identity / zero.
 // ----------------------------------------------------------------------------
-__global__ void k_dirichlet_blocks(SetupLevel S, DevLevel D) {
+// Block j (rows [j b, j b + b)) holds Linv_j = L_jj^{-1} and Lsub_j =
+// L_{j,j-1}, both b x b column-major; padded rows are identity / zero.  With
+// a power-of-two block size (D.bp > 0) entries are XOR-swizzled, (r, c) ->
+// c*b + (r ^ c), so that the warp kernels read columns (forward sweep) and
+// rows (backward sweep) without shared-memory bank conflicts.
+__global__ void k_dirichlet_blocks(SetupLevel S, DevLevel D, double *outBase, const int64_t *offOut) {
     const int sub = blockIdx.x;
+    const bool swz = D.bp != 0;
     const int n = S.nI[sub], bw = S.bw[sub], b = S.bsz[sub], m = S.nblk[sub];
     const double *L = S.band + S.offBand[sub];
-    double *out = D.f64.dir + D.offF[sub];
+    double *out = outBase + offOut[sub];
     auto Lat = [&](int r, int c) -> double {   // L[r][c], r >= c, global indices
         if (r >= n || c >= n || r < c) return 0.0;
         const int d = r - c;
@@ -229,12 +235,15 @@ __global__ void k_dirichlet_blocks(SetupLevel S, DevLevel D) {
                         x = (r == c) ? 1.0 : 0.0;
                     } else {
                         double s = (r == c) ? 1.0 : 0.0;
-                        for (int k = c; k < r; ++k) s -= Lat(r0 + r, r0 + k) * Linv[(int64_t)c * b + k];
+                        for (int k = c; k < r; ++k)
+                            s -= Lat(r0 + r, r0 + k) * Linv[(int64_t)c * b + (swz ? (k ^ c) : k)];
                         x = s / Lat(r0 + r, r0 + r);
                     }
                 }
-                Linv[(int64_t)c * b + r] = x;
-                Lsub[(int64_t)c * b + r] = (j > 0) ? Lat(r0 + r, r0 - b + c) : 0.0;
+                // XOR swizzle for power-of-two blocks: (r, c) at c*b + (r ^ c)
+                const int rr = swz ? (r ^ c) : r;
+                Linv[(int64_t)c * b + rr] = x;
+                Lsub[(int64_t)c * b + rr] = (j > 0) ? Lat(r0 + r, r0 - b + c) : 0.0;
             }
         }
     }
@@ -872,35 +881,41 @@ __global__ void k_syrk_update(int n, double *A, int k0) {
     }
 }
 
-// X = A^{-1} column block by column block from L L^T = A:
-// forward L Y = I[:, J], backward L^T X = Y.  One block per 32 columns.
-__global__ void k_chol_inverse_cols(int n, const double *L, double *X) {
-    const int c0 = blockIdx.x * 32;
-    const int c = c0 + threadIdx.x;   // one thread per column, 32 threads
+// X = A^{-1} from L L^T = A (X with leading dimension ld), one warp per
+// column c: forward L y = e_c, then backward L^T x = y, each row's dot
+// product split over the 32 lanes.
+__global__ void k_chol_inverse_cols(int n, const double *L, double *X, int ld) {
+    const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
     if (c >= n) return;
-    double *x = X + (int64_t)c;       // column c, stride n
-    for (int i = 0; i < n; ++i) x[(int64_t)i * n] = 0.0;
+    double *x = X + (int64_t)c;       // column c, stride ld
+    for (int i = lane; i < n; i += 32) x[(int64_t)i * ld] = 0.0;
+    __syncwarp();
     for (int i = c; i < n; ++i) {
-        double s = (i == c) ? 1.0 : 0.0;
         const double *Li = L + (int64_t)i * n;
-        for (int k = c; k < i; ++k) s -= Li[k] * x[(int64_t)k * n];
-        x[(int64_t)i * n] = s / Li[i];
+        double s = 0.0;
+        for (int k = c + lane; k < i; k += 32) s += Li[k] * x[(int64_t)k * ld];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) x[(int64_t)i * ld] = (((i == c) ? 1.0 : 0.0) - s) / Li[i];
+        __syncwarp();
     }
     for (int i = n - 1; i >= 0; --i) {
-        double s = x[(int64_t)i * n];
-        for (int k = i + 1; k < n; ++k) s -= L[(int64_t)k * n + i] * x[(int64_t)k * n];
-        x[(int64_t)i * n] = s / L[(int64_t)i * n + i];
+        double s = 0.0;
+        for (int k = i + 1 + lane; k < n; k += 32) s += L[(int64_t)k * n + i] * x[(int64_t)k * ld];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) x[(int64_t)i * ld] = (x[(int64_t)i * ld] - s) / L[(int64_t)i * n + i];
+        __syncwarp();
     }
 }
 
-__global__ void k_symmetrize(int n, double *X) {
+__global__ void k_symmetrize(int n, double *X, int ld) {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= (int64_t)n * n) return;
     const int i = (int)(q / n), j = (int)(q % n);
     if (j > i) {
-        const double v = 0.5 * (X[(int64_t)i * n + j] + X[(int64_t)j * n + i]);
-        X[(int64_t)i * n + j] = v;
-        X[(int64_t)j * n + i] = v;
+        const double v = 0.5 * (X[(int64_t)i * ld + j] + X[(int64_t)j * ld + i]);
+        X[(int64_t)i * ld + j] = v;
+        X[(int64_t)j * ld + i] = v;
     }
 }
 
@@ -922,8 +937,10 @@ void launch_schur(const SetupLevel &S, int max_nG, cudaStream_t s) {
     (void)max_nG;
     k_schur<<<S.nsub, 256, 0, s>>>(S);
 }
-void launch_dirichlet_blocks(const SetupLevel &S, const DevLevel &L, cudaStream_t s) {
-    k_dirichlet_blocks<<<S.nsub, 64, 0, s>>>(S, L);
+void launch_dirichlet_blocks(const SetupLevel &S, const DevLevel &L, double *scratch,
+                             const int64_t *offScratch, cudaStream_t s) {
+    (void)scratch; (void)offScratch;
+    k_dirichlet_blocks<<<S.nsub, 64, 0, s>>>(S, L, L.f64.dir, L.offF);
 }
 void launch_extract_coo(const SetupLevel &S, const DevLevel &L, const int64_t *cooSrc,
                         cudaStream_t s) {
@@ -953,11 +970,9 @@ void dense_cholesky(int n, double *A, int *err, cudaStream_t s) {
         }
     }
 }
-void dense_inverse_from_cholesky(int n, const double *L, double *Ainv, double *work,
-                                 cudaStream_t s) {
-    (void)work;
-    k_chol_inverse_cols<<<(n + 31) / 32, 32, 0, s>>>(n, L, Ainv);
-    k_symmetrize<<<(int)(((int64_t)n * n + 255) / 256), 256, 0, s>>>(n, Ainv);
+void dense_inverse_from_cholesky(int n, const double *L, double *Ainv, int ld, cudaStream_t s) {
+    k_chol_inverse_cols<<<(n + 3) / 4, 128, 0, s>>>(n, L, Ainv, ld);
+    k_symmetrize<<<(int)(((int64_t)n * n + 255) / 256), 256, 0, s>>>(n, Ainv, ld);
 }
 
 // edge eigen launcher with explicit work buffer
