@@ -185,6 +185,24 @@ def _kernel_bytes(q, n_top, prec_bytes):
     return b, flops
 
 
+def replica_barrier(world):
+    """Barrier across the replicas (no-op for one process)."""
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def replica_max(v, world, device):
+    """Max of a per-rank scalar over the replicas (the timing rule of the bench)."""
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def gpu_arm(a):
     import torch
     rank, world, local = _dist()
@@ -195,15 +213,10 @@ def gpu_arm(a):
     from paper_0911_5730_gb300 import bddc, inputs
 
     def barrier():
-        if world > 1:
-            torch.distributed.barrier()
+        replica_barrier(world)
 
     def max_over_ranks(v):
-        if world == 1:
-            return v
-        t = torch.tensor([v], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
+        return replica_max(v, world, "cuda")
 
     wl = inputs.two_level_channels()
     t0 = time.perf_counter()

@@ -184,6 +184,25 @@ int bddc_query(const bddc_ctx *ctx, bddc_info *info, int level, int32_t *n_selec
                double *edge_eigs, int max_eigs, int32_t *edge_pairs);
 
 /*
+ * bddc_inspect - host-only classification of a level-1 decomposition (no
+ * device work): interface, corners and edges as in Sec. 2 and Sec. 3
+ * (corners = DOFs in >= 3 substructures, edges = connected chains of the
+ * other interface DOFs shared by one pair), and the interior block size the
+ * setup would use.
+ *   n_corners, n_edges : outputs (may be NULL).
+ *   edge_pairs         : host [max_edges * 2] or NULL: (s, t) per edge, in
+ *                        the numbering of bddc_query.
+ *   edge_len           : host [max_edges] or NULL: DOFs per edge.
+ *   block_size         : output (may be NULL): the common interior block size,
+ *                        0 if the substructures use different sizes.
+ * Returns BDDC_E_ARG if max_edges is smaller than the number of edges and an
+ * array was given.
+ */
+int bddc_inspect(const bddc_mesh *mesh, const bddc_decomp *decomp, int32_t *n_corners,
+                 int32_t *n_edges, int32_t *edge_pairs, int32_t *edge_len, int max_edges,
+                 int32_t *block_size);
+
+/*
  * bddc_operator - y = A x for the level-1 Q1 operator (device FP64 [n]); the
  * matrix-free SpMV used by PCG.
  */
@@ -230,6 +249,16 @@ int bddc_profile_apply(bddc_ctx *ctx, const double *r_dev, int reps, double *ms_
  */
 #define BDDC_NOALLOC_SCRATCH_BYTES (16u << 20)
 int bddc_apply_noalloc(bddc_ctx *ctx, const double *r_dev, double *z_dev, void *stream);
+
+/*
+ * bddc_selftest_wait_timeout - exercise the bounded device wait used by the
+ * apply kernels: one kernel waits on an mbarrier whose bytes never arrive,
+ * gives up after its poll limit and flags an error word that the host reads.
+ * Returns BDDC_E_TIMEOUT when the wait gave up as designed (the context
+ * stays usable), BDDC_OK if it unexpectedly completed.  No counterpart in
+ * the paper.
+ */
+int bddc_selftest_wait_timeout(void *stream);
 
 void bddc_destroy(bddc_ctx *ctx);
 

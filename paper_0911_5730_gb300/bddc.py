@@ -25,7 +25,8 @@ PRECISION = {"fp64": 0, "fp32": 1, "bf16": 2}
 SYMBOLS = ["bddc_setup", "bddc_apply", "bddc_pcg_solve", "bddc_pcg_solve_host",
            "bddc_set_precision", "bddc_query", "bddc_operator", "bddc_destroy",
            "bddc_last_error", "bddc_server_create", "bddc_submit", "bddc_wait",
-           "bddc_server_destroy", "bddc_profile_apply", "bddc_apply_noalloc"]
+           "bddc_server_destroy", "bddc_profile_apply", "bddc_apply_noalloc", "bddc_inspect",
+           "bddc_selftest_wait_timeout"]
 
 
 class Mesh(C.Structure):
@@ -92,6 +93,8 @@ def load():
     lib.bddc_wait.argtypes = [vp, C.c_uint64, vp, vp, C.POINTER(C.c_double), i32]
     lib.bddc_profile_apply.argtypes = [vp, vp, i32, vp, i32, C.POINTER(C.c_int32)]
     lib.bddc_apply_noalloc.argtypes = [vp, vp, vp, vp]
+    lib.bddc_selftest_wait_timeout.argtypes = [vp]
+    lib.bddc_inspect.argtypes = [C.POINTER(Mesh), C.POINTER(Decomp), vp, vp, vp, vp, i32, vp]
     lib.bddc_server_destroy.argtypes = [vp]
     lib.bddc_server_destroy.restype = None
     _lib = lib
@@ -118,6 +121,23 @@ def _stream_ptr(stream):
 
 def _ptr(t):
     return C.c_void_p(t.data_ptr())
+
+
+def inspect(nx, elem_to_sub, n_sub1):
+    """Host-only classification of a level-1 decomposition (no GPU needed)."""
+    lib = load()
+    e2s = np.ascontiguousarray(elem_to_sub, dtype=np.int32)
+    dec = Decomp(e2s.ctypes.data_as(C.POINTER(C.c_int32)), int(n_sub1), None, 0)
+    nc, ne, bs = C.c_int32(), C.c_int32(), C.c_int32()
+    _check(lib.bddc_inspect(C.byref(Mesh(nx, nx)), C.byref(dec), C.byref(nc), C.byref(ne),
+                            None, None, 0, C.byref(bs)))
+    pairs = np.zeros((max(ne.value, 1), 2), np.int32)
+    lens = np.zeros(max(ne.value, 1), np.int32)
+    _check(lib.bddc_inspect(C.byref(Mesh(nx, nx)), C.byref(dec), None, None,
+                            pairs.ctypes.data_as(C.c_void_p), lens.ctypes.data_as(C.c_void_p),
+                            ne.value, None))
+    return {"n_corners": nc.value, "n_edges": ne.value, "edge_pairs": pairs[:ne.value],
+            "edge_len": lens[:ne.value], "block_size": bs.value}
 
 
 class Problem:

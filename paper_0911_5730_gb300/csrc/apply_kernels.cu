@@ -1039,6 +1039,19 @@ template <> __global__ void k_convert<__nv_bfloat16>(const double *src, __nv_bfl
     if (i < n) dst[i] = __float2bfloat16((float)src[i]);
 }
 
+// Self-test of the bounded wait: a barrier expects bytes that no copy will
+// ever deliver; the wait must give up after `polls` polls and flag *err.
+__global__ void k_selftest_wait(int *err, long polls) {
+    __shared__ __align__(8) unsigned long long bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar);
+        mbar_expect(&bar, 16);           // nothing will complete these 16 bytes
+        bool ok = false;
+        for (long i = 0; i < polls && !ok; ++i) ok = mbar_try(&bar, 0);
+        if (!ok) atomicExch(err, 1);
+    }
+}
+
 int grid_for(int64_t n) {
     int64_t g = (n + RB - 1) / RB;
     if (g > 152 * 8) g = 152 * 8;
@@ -1286,6 +1299,9 @@ void launch_pcg_dir(int n, double *p, const double *z, PcgScalars *sc, cudaStrea
 void launch_lanczos_extremes(const double *alphas, const double *betas, const PcgScalars *sc,
                              double *out2, double *work, int cap, cudaStream_t s) {
     k_lanczos<<<1, 32, 0, s>>>(alphas, betas, sc, out2, work, work + cap);
+}
+void launch_selftest_wait(int *err, long polls, cudaStream_t s) {
+    k_selftest_wait<<<1, 32, 0, s>>>(err, polls);
 }
 void launch_convert(const double *src, float *dst, int64_t n, cudaStream_t s) {
     if (n > 0) k_convert<float><<<(int)((n + 255) / 256), 256, 0, s>>>(src, dst, n);

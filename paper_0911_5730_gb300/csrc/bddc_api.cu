@@ -657,6 +657,33 @@ int pcg_one(bddc_ctx *C, Workspace &W, int prec, const double *b, double *x, dou
     return status;
 }
 
+// Level 1 of Sec. 2: the Q1 elements of the mesh with their free nodes
+// (Dirichlet nodes are dropped slots).
+void level_one(HLevel &H, int nx, const bddc_decomp *decomp) {
+    const int nelem = nx * nx;
+    H.n = (nx - 1) * (nx - 1);
+    H.nelem = nelem;
+    H.nsub = decomp->n_sub1;
+    H.eptr.resize(nelem + 1);
+    H.eslot.resize((size_t)nelem * 4);
+    H.esub.assign(decomp->elem_to_sub, decomp->elem_to_sub + nelem);
+    H.ebnd.assign(nelem, 0);
+    H.dofz.assign(H.n, 1.0);
+    auto fidx = [&](int i, int j) {
+        return (i <= 0 || j <= 0 || i >= nx || j >= nx) ? -1 : (j - 1) * (nx - 1) + (i - 1);
+    };
+    for (int e = 0; e < nelem; ++e) {
+        const int ej = e / nx, ei = e % nx;
+        H.eptr[e] = (int64_t)e * 4;
+        const int nd[4] = {fidx(ei, ej), fidx(ei + 1, ej), fidx(ei + 1, ej + 1), fidx(ei, ej + 1)};
+        for (int a = 0; a < 4; ++a) {
+            H.eslot[(size_t)e * 4 + a] = nd[a];
+            if (nd[a] < 0) H.ebnd[e] = 1;
+        }
+    }
+    H.eptr[nelem] = (int64_t)nelem * 4;
+}
+
 template <class F> int guarded(F &&f) {
     try {
         set_error("");
@@ -726,28 +753,7 @@ int bddc_setup(const bddc_mesh *mesh, const double *k_elem, const bddc_decomp *d
 
         // level 1: Q1 elements
         C->L.resize(levels - 1);
-        {
-            HLevel &H = C->L[0].H;
-            H.n = (nx - 1) * (nx - 1);
-            H.nelem = nelem;
-            H.nsub = decomp->n_sub1;
-            H.eptr.resize(nelem + 1);
-            H.eslot.resize((size_t)nelem * 4);
-            H.esub.assign(decomp->elem_to_sub, decomp->elem_to_sub + nelem);
-            H.ebnd.assign(nelem, 0);
-            H.dofz.assign(H.n, 1.0);
-            auto fidx = [&](int i, int j) { return (i <= 0 || j <= 0 || i >= nx || j >= nx) ? -1 : (j - 1) * (nx - 1) + (i - 1); };
-            for (int e = 0; e < nelem; ++e) {
-                const int ej = e / nx, ei = e % nx;
-                H.eptr[e] = (int64_t)e * 4;
-                const int nd[4] = {fidx(ei, ej), fidx(ei + 1, ej), fidx(ei + 1, ej + 1), fidx(ei, ej + 1)};
-                for (int a = 0; a < 4; ++a) {
-                    H.eslot[(size_t)e * 4 + a] = nd[a];
-                    if (nd[a] < 0) H.ebnd[e] = 1;
-                }
-            }
-            H.eptr[nelem] = (int64_t)nelem * 4;
-        }
+        level_one(C->L[0].H, nx, decomp);
         double *emat = tmp.alloc_n<double>((size_t)nelem * 16);
         launch_q1_element_matrices(nelem, C->k_dev, emat, st);
         std::vector<int64_t> emOff(nelem);
@@ -830,6 +836,28 @@ int bddc_apply(bddc_ctx *ctx, const double *r_dev, double *z_dev, int nrhs, int6
         for (int j = 0; j < nrhs; ++j)
             apply_rec(ctx, *ctx->ws, 0, ctx->prec, r_dev + j * ld, z_dev + j * ld, nullptr, st);
         BDDC_CUDA_TRY(cudaGetLastError());
+        return BDDC_OK;
+    });
+}
+
+int bddc_inspect(const bddc_mesh *mesh, const bddc_decomp *decomp, int32_t *n_corners,
+                 int32_t *n_edges, int32_t *edge_pairs, int32_t *edge_len, int max_edges,
+                 int32_t *block_size) {
+    return guarded([&]() -> int {
+        if (!mesh || !decomp || !decomp->elem_to_sub) throw Error(BDDC_E_ARG, "null argument");
+        if (mesh->nx < 2 || mesh->ny != mesh->nx) throw Error(BDDC_E_ARG, "mesh must be square with nx >= 2");
+        HLevel H;
+        level_one(H, mesh->nx, decomp);
+        H.build();
+        const int ne = (int)H.edges.size();
+        if (n_corners) *n_corners = (int32_t)H.corners.size();
+        if (n_edges) *n_edges = ne;
+        if ((edge_pairs || edge_len) && max_edges < ne) throw Error(BDDC_E_ARG, "max_edges too small");
+        for (int e = 0; e < ne; ++e) {
+            if (edge_pairs) { edge_pairs[2 * e] = H.edges[e].s; edge_pairs[2 * e + 1] = H.edges[e].t; }
+            if (edge_len) edge_len[e] = (int32_t)H.edges[e].dofs.size();
+        }
+        if (block_size) *block_size = H.block_uniform;
         return BDDC_OK;
     });
 }
@@ -1070,6 +1098,22 @@ int bddc_apply_noalloc(bddc_ctx *ctx, const double *r_dev, double *z_dev, void *
         for (int l = nl - 1; l >= 0; --l)
             apply_level_post(lv[l], prec, rin[l], l == 0 ? z_dev : lv[l - 1].ucv, nullptr, st);
         BDDC_CUDA_TRY(cudaGetLastError());
+        return BDDC_OK;
+    });
+}
+
+int bddc_selftest_wait_timeout(void *stream) {
+    return guarded([&]() -> int {
+        cudaStream_t st = (cudaStream_t)stream;
+        DevArena a;
+        int *err = a.alloc_n<int>(1);
+        BDDC_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
+        launch_selftest_wait(err, 2000, st);
+        int h = 0;
+        BDDC_CUDA_TRY(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        BDDC_CUDA_TRY(cudaStreamSynchronize(st));
+        BDDC_CUDA_TRY(cudaGetLastError());
+        if (h) throw Error(BDDC_E_TIMEOUT, "device wait gave up after its poll limit (expected)");
         return BDDC_OK;
     });
 }

@@ -183,6 +183,7 @@ void launch_norm2(int n, const double *v, double *part, unsigned *counter, doubl
 void launch_lanczos_extremes(const double *alphas, const double *betas, const PcgScalars *sc,
                              double *out2, double *work, int cap, cudaStream_t s);
 void launch_convert(const double *src, float *dst, int64_t n, cudaStream_t s);
+void launch_selftest_wait(int *err, long polls, cudaStream_t s);
 void launch_convert(const double *src, __nv_bfloat16 *dst, int64_t n, cudaStream_t s);
 
 // ----------------------------------------------------------------------------

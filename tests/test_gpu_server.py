@@ -1,0 +1,69 @@
+"""The serving loop: requests for several resident problems, each with 1-4
+right-hand sides, submitted while others run.  Every result must equal the
+problem's solo solve within the FP64 tolerance (1e-10 relative: each RHS is
+an independent PCG with the same operators), latencies are reported, a
+request larger than the HBM budget is refused with BDDC_E_BUSY, and a
+bounded wait returns BDDC_E_TIMEOUT for a request that cannot finish yet."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+from paper_0911_5730_gb300 import inputs  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_0911_5730_gb300 import bddc
+    return bddc
+
+
+def test_results_same_alone_and_in_the_mix(lib):
+    wls = [inputs.two_level_channels(nx=64, sub=16), inputs.two_level_unit(),
+           inputs.three_level_blocks(nx=64, sub=8, group=4, tau=10.0)]
+    probs = [lib.Problem.from_workload(w) for w in wls]
+    rng = np.random.default_rng(5)
+    reqs = []
+    for k in range(9):
+        j = k % 3
+        nrhs = 1 + (k % 4)
+        b = rng.standard_normal((nrhs, wls[j].n_dof)) if nrhs > 1 else rng.standard_normal(wls[j].n_dof)
+        reqs.append((j, b))
+    srv = lib.Server(hbm_budget=0, max_slots=3)
+    tickets = [srv.submit(probs[j], b, rtol=1e-8) for j, b in reqs]
+    outs = [srv.wait(t) for t in tickets]
+    for (j, b), (x, infos, lat) in zip(reqs, outs):
+        assert lat > 0
+        bb = np.atleast_2d(b)
+        xx = np.atleast_2d(x)
+        for r in range(bb.shape[0]):
+            xs, info = probs[j].solve(torch.tensor(bb[r], device="cuda"), rtol=1e-8)
+            assert infos[r]["status"] == 0 and infos[r]["iters"] == info[0]["iters"]
+            xs = xs.cpu().numpy()
+            assert np.linalg.norm(xx[r] - xs) <= 1e-10 * np.linalg.norm(xs)
+    srv.close()
+    for p in probs:
+        p.close()
+
+
+def test_budget_and_timeout(lib):
+    wl = inputs.two_level_channels(nx=64, sub=16)
+    P = lib.Problem.from_workload(wl)
+    srv = lib.Server(hbm_budget=4096, max_slots=1)
+    with pytest.raises(lib.BDDCError) as e:
+        srv.submit(P, np.ones(wl.n_dof))
+    assert e.value.code == -7
+    srv.close()
+    srv = lib.Server(hbm_budget=0, max_slots=1)
+    big = inputs.normal_rhs(wl.n_dof, 3, 16)
+    t = srv.submit(P, big, rtol=1e-12, maxit=500)
+    with pytest.raises(lib.BDDCError) as e:
+        srv.wait(t, timeout_ms=0)
+    assert e.value.code == -5
+    srv.close()
+    P.close()

@@ -1,0 +1,59 @@
+"""Host-side logic of the C++ library against the oracle (no GPU needed).
+
+bddc_inspect runs only the level-1 bookkeeping of bddc_setup: interface,
+corners (DOFs in >= 3 substructures), edges (connected chains of the other
+interface DOFs shared by one pair, numbered by pair then lowest DOF) and the
+interior block size.  The oracle classifies the same decompositions in
+Python; both must agree exactly, including on irregular partitions with
+several chains between one pair.
+"""
+import numpy as np
+import pytest
+
+from oracle import levels
+from paper_0911_5730_gb300 import inputs
+
+
+@pytest.fixture(scope="module")
+def bddc():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_0911_5730_gb300 import bddc as b
+    return b
+
+
+def _nearest_seed_partition(nx, nseeds, seed):
+    rng = np.random.default_rng(seed)
+    seeds = rng.uniform(0, nx, size=(nseeds, 2))
+    ej, ei = np.divmod(np.arange(nx * nx), nx)
+    c = np.stack([ei + 0.5, ej + 0.5], axis=1)
+    d = ((c[:, None, :] - seeds[None, :, :]) ** 2).sum(-1)
+    lab = d.argmin(1)
+    used = np.unique(lab)
+    remap = -np.ones(nseeds, int)
+    remap[used] = np.arange(len(used))
+    return remap[lab].astype(np.int32), len(used)
+
+
+CASES = [("grid32_8",) + inputs.grid_decomposition(32, 8) + (32,),
+         ("grid48_16",) + inputs.grid_decomposition(48, 16) + (48,),
+         ("grid24_4",) + inputs.grid_decomposition(24, 4) + (24,)]
+for sd in (1, 2, 3):
+    e2s, ns = _nearest_seed_partition(24, 7, sd)
+    CASES.append(("seeds24_%d" % sd, e2s, ns, 24))
+
+
+@pytest.mark.parametrize("name,e2s,ns,nx", CASES, ids=[c[0] for c in CASES])
+def test_classification_matches_oracle(bddc, name, e2s, ns, nx):
+    lv = levels.level_one(nx, np.ones(nx * nx), e2s, ns)
+    got = bddc.inspect(nx, e2s, ns)
+    assert got["n_corners"] == len(lv.corners)
+    assert got["n_edges"] == len(lv.edges)
+    assert [tuple(p) for p in got["edge_pairs"]] == [tuple(p) for p, _ in lv.edges]
+    assert list(got["edge_len"]) == [len(d) for _, d in lv.edges]
+
+
+def test_block_size_power_of_two_for_grids(bddc):
+    for nx, sub, bp in [(512, 16, 16), (64, 8, 8), (32, 8, 8)]:
+        e2s, ns = inputs.grid_decomposition(nx, sub)
+        assert bddc.inspect(nx, e2s, ns)["block_size"] == bp
