@@ -14,6 +14,8 @@
 //    A_II^{-1} (r_I - A_{I Gamma} u_B,Gamma) and its interface is u_B.
 #include "internal.h"
 
+#include <cstdlib>
+
 namespace bddc {
 
 namespace {
@@ -252,6 +254,48 @@ __device__ __forceinline__ bool warp_wait_copy(unsigned long long *bar, int *err
 
 __host__ __device__ constexpr size_t al16(size_t v) { return (v + 15) & ~size_t(15); }
 
+// Programmatic dependent launch.  The kernels of the apply and of the PCG
+// iteration are launched so that each may start while its predecessor in the
+// stream drains.  pdl_wait() returns once the predecessor grid has completed
+// and its writes are visible (at once for an ordinary launch), so a kernel
+// reads nothing another kernel of the iteration writes before it, and every
+// thread calls it before it exits; only setup-time data (factors, records) is
+// read earlier.  pdl_trigger() lets the successor be scheduled.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Warp sum of r.z partials of the level-1 post-correction; the last warp of
+// the launch to finish adds the per-substructure partials in a fixed order.
+__device__ __forceinline__ void finish_rz(double tot, PcgScalars *sc, double *betas) {
+    const double beta = sc->fresh ? 0.0 : tot / sc->rho;
+    sc->fresh = 0;
+    sc->rho_new = tot;
+    sc->beta = beta;
+    if (sc->it > 0) betas[sc->it - 1] = beta;
+    sc->rho = tot;
+}
+__device__ __forceinline__ void warp_rz(double acc, int sub, int nsub, const RzArgs &rz, int lane) {
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    unsigned last = 0;
+    if (lane == 0) {
+        rz.part[sub] = acc;
+        __threadfence();
+        last = atomicAdd(rz.counter, 1u) == (unsigned)nsub - 1u;
+    }
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (!last) return;
+    __threadfence();
+    double t = 0.0;
+    for (int k = lane; k < nsub; k += 32) t += __ldcg(&rz.part[k]);
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) {
+        finish_rz(t, rz.sc, rz.betas);
+        *rz.counter = 0u;
+    }
+}
+
 template <int LPR, class ACC> __device__ __forceinline__ ACC lpr_sum(ACC v) {
 #pragma unroll
     for (int o = LPR / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -386,15 +430,15 @@ template <class T, class ACC, int BP> struct DirSlice {
 };
 
 template <class T, class ACC, int BP, bool POST>
-__global__ void k_dir_w(DevLevel L, const double *r, double *z, const int *skip, unsigned slice) {
-    if (skip && *skip) return;
+__global__ void k_dir_w(DevLevel L, const double *r, double *z, const int *skip, unsigned slice,
+                        RzArgs rz) {
     constexpr int LPR = 32 / BP;
     constexpr int NC = BP / LPR;
     constexpr int BB = BP * BP;
     extern __shared__ __align__(16) unsigned char smem_w[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int sub = blockIdx.x * (blockDim.x >> 5) + warp;
-    if (sub >= L.nsub) return;
+    if (sub >= L.nsub) { pdl_wait(); return; }
     unsigned char *p = smem_w + (size_t)warp * slice;
     T *fac = reinterpret_cast<T *>(p);      p += al16(sizeof(T) * (size_t)L.max_fac);
     ACC *x = reinterpret_cast<ACC *>(p);    p += al16(sizeof(ACC) * (size_t)L.max_m * BP);
@@ -443,6 +487,14 @@ __global__ void k_dir_w(DevLevel L, const double *r, double *z, const int *skip,
             owp[u] = k < nown ? gO[2 * k] : -1;
             owd[u] = k < nown ? gO[2 * k + 1] : -1;
         }
+    }
+    // everything above reads setup data only; r, u_B and the scratch below
+    // are written by the preceding kernels
+    pdl_wait();
+    pdl_trigger();
+    if (skip && *skip) {
+        for (int c = 0; c < nch; ++c) mbar_wait(&bars[c], 0);   // bounded: copies land first
+        return;
     }
     // right-hand side (and u_B on Gamma for the post-correction)
     double rv[kUI];
@@ -551,10 +603,25 @@ __global__ void k_dir_w(DevLevel L, const double *r, double *z, const int *skip,
             }
         }
     } else {
+        double acc = 0.0;
 #pragma unroll
-        for (int u = 0; u < kUI; ++u) if (ii[u] >= 0) z[ii[u]] = (double)x[u * 32 + lane];
+        for (int u = 0; u < kUI; ++u) {
+            if (ii[u] >= 0) {
+                const double zv = (double)x[u * 32 + lane];
+                z[ii[u]] = zv;
+                acc = fma(rv[u], zv, acc);
+            }
+        }
 #pragma unroll
-        for (int u = 0; u < kUO; ++u) if (owp[u] >= 0) z[owd[u]] = (double)vG[owp[u]];
+        for (int u = 0; u < kUO; ++u) {
+            if (owp[u] >= 0) {
+                const double zv = (double)vG[owp[u]];
+                z[owd[u]] = zv;
+                if (rz.sc) acc = fma(r[owd[u]], zv, acc);
+            }
+        }
+        // every entry of z is written once, by the substructure that owns it
+        if (rz.sc) warp_rz(acc, sub, L.nsub, rz, lane);
     }
 }
 
@@ -562,11 +629,10 @@ __global__ void k_dir_w(DevLevel L, const double *r, double *z, const int *skip,
 // Neumann record of the substructure arrives with one bulk copy.
 template <class T, class ACC>
 __global__ void k_neumann_r(DevLevel L, int pidx, const double *r, const int *skip, unsigned slice) {
-    if (skip && *skip) return;
     extern __shared__ __align__(16) unsigned char smem_w[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int sub = blockIdx.x * (blockDim.x >> 5) + warp;
-    if (sub >= L.nsub) return;
+    if (sub >= L.nsub) { pdl_wait(); return; }
     unsigned char *p = smem_w + (size_t)warp * slice;
     unsigned char *rec = p;                  p += al16((size_t)L.max_nrec[pidx]);
     ACC *f = reinterpret_cast<ACC *>(p);     p += al16(sizeof(ACC) * (size_t)L.max_nG);
@@ -578,6 +644,12 @@ __global__ void k_neumann_r(DevLevel L, int pidx, const double *r, const int *sk
     if (lane == 0 && lay.bytes) {
         mbar_expect(bar, (unsigned)lay.bytes);
         bulk_copy(rec, L.nrec[pidx] + L.nrecOff[pidx][sub], (unsigned)lay.bytes, bar);
+    }
+    pdl_wait();
+    pdl_trigger();
+    if (skip && *skip) {
+        if (lay.bytes) mbar_wait(bar, 0);   // bounded: the copy lands first
+        return;
     }
     if (lay.bytes && !warp_wait_copy(bar, L.err, lane)) return;
     const T *Ps = reinterpret_cast<const T *>(rec + lay.psi);
@@ -626,11 +698,10 @@ __global__ void k_neumann_r(DevLevel L, int pidx, const double *r, const int *sk
 // (9): u_B += D_i (w_i + Psi_i u_c) on Gamma.
 template <class T, class ACC>
 __global__ void k_average_r(DevLevel L, int pidx, const int *skip, unsigned slice) {
-    if (skip && *skip) return;
     extern __shared__ __align__(16) unsigned char smem_w[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int sub = blockIdx.x * (blockDim.x >> 5) + warp;
-    if (sub >= L.nsub) return;
+    if (sub >= L.nsub) { pdl_wait(); return; }
     unsigned char *p = smem_w + (size_t)warp * slice;
     unsigned char *rec = p;                  p += al16((size_t)L.max_nrec[pidx]);
     ACC *uc = reinterpret_cast<ACC *>(p);    p += al16(sizeof(ACC) * (size_t)(L.max_nc > 0 ? L.max_nc : 1));
@@ -642,6 +713,12 @@ __global__ void k_average_r(DevLevel L, int pidx, const int *skip, unsigned slic
     if (lane == 0 && lay.avg_bytes) {
         mbar_expect(bar, (unsigned)lay.avg_bytes);
         bulk_copy(rec, L.nrec[pidx] + L.nrecOff[pidx][sub], (unsigned)lay.avg_bytes, bar);
+    }
+    pdl_wait();
+    pdl_trigger();
+    if (skip && *skip) {
+        if (lay.avg_bytes) mbar_wait(bar, 0);   // bounded: the copy lands first
+        return;
     }
     const int64_t g0 = L.offG[sub];
     double wv[4];
@@ -713,40 +790,55 @@ __global__ void k_build_nrec(DevLevel D, OpSet<T> O, unsigned char *rec, const i
 }
 
 // y = A x, A dense symmetric n x n row-major with leading dimension ld (a
-// multiple of 4, zero padded; x zero on [n, ld)); one warp per row, 16-byte
-// loads, eight values per lane in flight.
-__global__ void k_dense_symv(int n, int ld, const double *A, const double *x, double *y,
-                             const int *skip) {
+// multiple of 4, zero padded; x zero on [n, ld)).  The FP64 pipe bounds it:
+// SV_WR warps share a row (interleaved 64-column strips, 16-byte loads) so
+// that enough warps are resident to keep that pipe busy; the strip sums are
+// added in a fixed order.
+constexpr int SV_WR = 4, SV_ROWS = 2;
+__global__ void __launch_bounds__(32 * SV_WR * SV_ROWS)
+k_dense_symv(int n, int ld, const double *A, const double *x, double *y, const int *skip) {
+    __shared__ double part[SV_ROWS][SV_WR];
+    pdl_wait();
+    pdl_trigger();
     if (skip && *skip) return;
-    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (row >= n) return;
-    const double *a = A + (int64_t)row * ld;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int lr = warp / SV_WR, ws = warp % SV_WR;
+    const int row = blockIdx.x * SV_ROWS + lr;
     double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-    int c = 2 * lane;
-    for (; c + 192 < ld; c += 256) {
-        const double2 a0 = *reinterpret_cast<const double2 *>(a + c);
-        const double2 a1 = *reinterpret_cast<const double2 *>(a + c + 64);
-        const double2 a2 = *reinterpret_cast<const double2 *>(a + c + 128);
-        const double2 a3 = *reinterpret_cast<const double2 *>(a + c + 192);
-        const double2 x0 = *reinterpret_cast<const double2 *>(x + c);
-        const double2 x1 = *reinterpret_cast<const double2 *>(x + c + 64);
-        const double2 x2 = *reinterpret_cast<const double2 *>(x + c + 128);
-        const double2 x3 = *reinterpret_cast<const double2 *>(x + c + 192);
-        // one DFMA per product: the FP64 pipe bounds this kernel
-        s0 = fma(a0.x, x0.x, s0); s1 = fma(a0.y, x0.y, s1);
-        s2 = fma(a1.x, x1.x, s2); s3 = fma(a1.y, x1.y, s3);
-        s0 = fma(a2.x, x2.x, s0); s1 = fma(a2.y, x2.y, s1);
-        s2 = fma(a3.x, x3.x, s2); s3 = fma(a3.y, x3.y, s3);
+    if (row < n) {
+        const double *a = A + (int64_t)row * ld;
+        int c = 64 * ws + 2 * lane;
+        constexpr int step = 64 * SV_WR;
+        for (; c + 3 * step < ld; c += 4 * step) {
+            double2 av[4], xv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) av[u] = *reinterpret_cast<const double2 *>(a + c + u * step);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) xv[u] = *reinterpret_cast<const double2 *>(x + c + u * step);
+            s0 = fma(av[0].x, xv[0].x, s0); s1 = fma(av[0].y, xv[0].y, s1);
+            s2 = fma(av[1].x, xv[1].x, s2); s3 = fma(av[1].y, xv[1].y, s3);
+            s0 = fma(av[2].x, xv[2].x, s0); s1 = fma(av[2].y, xv[2].y, s1);
+            s2 = fma(av[3].x, xv[3].x, s2); s3 = fma(av[3].y, xv[3].y, s3);
+        }
+        for (; c < ld; c += step) {
+            const double2 a0 = *reinterpret_cast<const double2 *>(a + c);
+            const double2 x0 = *reinterpret_cast<const double2 *>(x + c);
+            s0 = fma(a0.x, x0.x, s0); s1 = fma(a0.y, x0.y, s1);
+        }
     }
-    for (; c < ld; c += 64) {
-        const double2 a0 = *reinterpret_cast<const double2 *>(a + c);
-        const double2 x0 = *reinterpret_cast<const double2 *>(x + c);
-        s0 = fma(a0.x, x0.x, s0); s1 = fma(a0.y, x0.y, s1);
+    double sum = (s0 + s1) + (s2 + s3);
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0) part[lr][ws] = sum;
+    __syncthreads();
+    if (threadIdx.x < SV_ROWS) {
+        const int rr = blockIdx.x * SV_ROWS + threadIdx.x;
+        if (rr < n) {
+            double t = 0.0;
+#pragma unroll
+            for (int k = 0; k < SV_WR; ++k) t += part[threadIdx.x][k];
+            y[rr] = t;
+        }
     }
-    double s = (s0 + s1) + (s2 + s3);
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) y[row] = s;
 }
 
 // ----------------------------------------------------------------------------
@@ -834,16 +926,17 @@ __device__ __forceinline__ double block_sum(double v) {
 __device__ bool grid_reduce(double local, double *part, unsigned *counter, double *out) {
     const double bs = block_sum(local);
     __shared__ bool last;
+    const unsigned nb = gridDim.x * gridDim.y;             // 1D or 2D grids
     if (threadIdx.x == 0) {
-        part[blockIdx.x] = bs;
+        part[blockIdx.y * gridDim.x + blockIdx.x] = bs;
         __threadfence();
         const unsigned t = atomicAdd(counter, 1u);
-        last = (t == gridDim.x - 1);
+        last = (t == nb - 1);
     }
     __syncthreads();
     if (!last) return false;
     double s = 0.0;
-    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) s += __ldcg(&part[i]);
+    for (int i = threadIdx.x; i < (int)nb; i += blockDim.x) s += __ldcg(&part[i]);
     // in-order across threads is not needed for determinism: fixed partition
     const double tot = block_sum(s);
     if (threadIdx.x == 0) { *out = tot; *counter = 0u; }
@@ -876,13 +969,18 @@ __global__ void k_norm2(int64_t n, const double *v, double *part, unsigned *coun
     }
 }
 
-__global__ void k_pcg_init(int64_t n, const double *b, double *x, double *r, double *part,
-                           unsigned *counter, PcgScalars *sc, double tol, int maxit) {
+__global__ void k_pcg_init(int n, const double *b, double *x, double *r, double *p0, double *part,
+                           unsigned *counter, unsigned *rzcounter, PcgScalars *sc, double tol,
+                           int maxit) {
+    pdl_wait();
+    pdl_trigger();
     double s = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double bi = b[i];
         x[i] = 0.0;
-        r[i] = b[i];
-        s += b[i] * b[i];
+        r[i] = bi;
+        p0[i] = 0.0;
+        s = fma(bi, bi, s);
     }
     __shared__ double tot;
     if (grid_reduce(s, part, counter, &tot) && threadIdx.x == 0) {
@@ -892,36 +990,91 @@ __global__ void k_pcg_init(int64_t n, const double *b, double *x, double *r, dou
         sc->it = 0;
         sc->maxit = maxit;
         sc->conv = 0;
+        sc->fresh = 1;
+        sc->beta = 0.0;
         sc->done = (tot == 0.0) ? 1 : 0;
         if (tot == 0.0) sc->conv = 1;
+        *rzcounter = 0u;
     }
 }
 
-// p = z, rho = r.z
-__global__ void k_pcg_first_dir(int64_t n, double *p, const double *z, const double *r,
-                                double *part, unsigned *counter, PcgScalars *sc) {
-    if (sc->done) return;
-    double s = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        p[i] = z[i];
-        s += r[i] * z[i];
-    }
-    __shared__ double tot;
-    if (grid_reduce(s, part, counter, &tot) && threadIdx.x == 0) sc->rho = tot;
-}
-
-// q = A p ; alpha = rho / p.q
-__global__ void k_pcg_spmv_dot(int nx, const double *w, const double *p, double *q, double *part,
-                               unsigned *counter, PcgScalars *sc, double *alphas) {
+// Iteration `it` of PCG, first half: the new direction p_new = z + beta p_old
+// (into the other buffer, so that p_old stays intact for the halo of other
+// tiles), q = A p_new and alpha = rho / (p_new . q).  The FP64 pipe is the
+// limit here, so p_new is formed once per point of a PT_X x PT_Y tile plus its
+// halo in shared memory, and every thread handles PT_Y / 4 nodes of a column.
+constexpr int PT_X = 64, PT_Y = 16, PT_T = 256;
+__global__ void __launch_bounds__(PT_T)
+k_pcg_dir_spmv(int nx, const double *__restrict__ w, const double *__restrict__ z, double *p0,
+               double *p1, double *__restrict__ q, double *part, unsigned *counter, PcgScalars *sc,
+               double *alphas) {
+    __shared__ double ps[PT_Y + 2][PT_X + 2];
+    pdl_wait();
+    pdl_trigger();
     if (sc->done) return;
     const int n1 = nx - 1;
-    const int64_t n = (int64_t)n1 * n1;
+    const int n = n1 * n1;
+    const double bt = sc->beta;
+    const bool odd = sc->it & 1;
+    const double *po = odd ? p1 : p0;
+    double *pn = odd ? p0 : p1;
+    const int i0 = blockIdx.x * PT_X, j0 = blockIdx.y * PT_Y;   // 0-based node column / row
+    for (int t = threadIdx.x; t < (PT_Y + 2) * (PT_X + 2); t += PT_T) {
+        const int hy = t / (PT_X + 2), hx = t - hy * (PT_X + 2);
+        const int i = i0 + hx - 1, j = j0 + hy - 1;
+        double v = 0.0;
+        if (i >= 0 && i < n1 && j >= 0 && j < n1) {
+            const int g = j * n1 + i;
+            v = fma(bt, po[g], z[g]);
+        }
+        ps[hy][hx] = v;
+    }
+    __syncthreads();
+    constexpr int NY = PT_Y / (PT_T / PT_X);   // nodes per thread
+    const int tx = threadIdx.x % PT_X, ty = threadIdx.x / PT_X;
+    const int i = i0 + tx;
+    const bool W = i > 0, E = i < n1 - 1;
+    // all weights of the thread's nodes first (independent loads in flight),
+    // then the products from shared memory
+    double wv[NY][9];
+#pragma unroll
+    for (int k = 0; k < NY; ++k) {
+        const int j = j0 + ty + k * (PT_T / PT_X);
+        const bool in = i < n1 && j < n1;
+        const bool S = j > 0, N = j < n1 - 1;
+        const int g = j * n1 + i;
+        wv[k][0] = in ? __ldg(w + g) : 0.0;
+        wv[k][1] = in && E ? __ldg(w + n + g) : 0.0;
+        wv[k][2] = in && N ? __ldg(w + 2 * n + g) : 0.0;
+        wv[k][3] = in && N && E ? __ldg(w + 3 * n + g) : 0.0;
+        wv[k][4] = in && N && W ? __ldg(w + 4 * n + g) : 0.0;
+        wv[k][5] = in && W ? __ldg(w + n + g - 1) : 0.0;
+        wv[k][6] = in && S ? __ldg(w + 2 * n + g - n1) : 0.0;
+        wv[k][7] = in && S && W ? __ldg(w + 3 * n + g - n1 - 1) : 0.0;
+        wv[k][8] = in && S && E ? __ldg(w + 4 * n + g - n1 + 1) : 0.0;
+    }
     double s = 0.0;
-    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)(g % n1) + 1, j = (int)(g / n1) + 1;
-        const double v = q1w_row(n1, w, p, i, j, g);
+#pragma unroll
+    for (int k = 0; k < NY; ++k) {
+        const int ly = ty + k * (PT_T / PT_X);
+        const int j = j0 + ly;
+        if (i >= n1 || j >= n1) continue;
+        const int g = j * n1 + i;
+        const int hy = ly + 1, hx = tx + 1;
+        // neighbours outside the domain hold zero in ps and carry zero weight
+        const double pc = ps[hy][hx];
+        double v = wv[k][0] * pc;
+        v = fma(wv[k][1], ps[hy][hx + 1], v);
+        v = fma(wv[k][2], ps[hy + 1][hx], v);
+        v = fma(wv[k][3], ps[hy + 1][hx + 1], v);
+        v = fma(wv[k][4], ps[hy + 1][hx - 1], v);
+        v = fma(wv[k][5], ps[hy][hx - 1], v);
+        v = fma(wv[k][6], ps[hy - 1][hx], v);
+        v = fma(wv[k][7], ps[hy - 1][hx - 1], v);
+        v = fma(wv[k][8], ps[hy - 1][hx + 1], v);
+        pn[g] = pc;
         q[g] = v;
-        s += v * p[g];
+        s = fma(v, pc, s);
     }
     __shared__ double tot;
     if (grid_reduce(s, part, counter, &tot) && threadIdx.x == 0) {
@@ -931,17 +1084,40 @@ __global__ void k_pcg_spmv_dot(int nx, const double *w, const double *p, double 
     }
 }
 
-// x += alpha p ; r -= alpha q ; rr = r.r ; convergence / iteration count
-__global__ void k_pcg_update(int64_t n, double *x, double *r, const double *p, const double *q,
-                             double *part, unsigned *counter, PcgScalars *sc) {
+// Second half: x += alpha p_new; r -= alpha q; rr = r.r; convergence test;
+// it += 1 (by the last block, after every block has read it).  Several
+// entries per thread keep the FP64 block-reduction work per entry small.
+__global__ void k_pcg_update(int n, double *__restrict__ x, double *__restrict__ r, const double *p0,
+                             const double *p1, const double *__restrict__ q, double *part,
+                             unsigned *counter, PcgScalars *sc) {
+    pdl_wait();
+    pdl_trigger();
     if (sc->done) return;
     const double a = sc->alpha;
+    const double *__restrict__ p = (sc->it & 1) ? p0 : p1;
+    const int stride = gridDim.x * blockDim.x;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
     double s = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        x[i] += a * p[i];
-        const double ri = r[i] - a * q[i];
+    for (; i + 3 * stride < n; i += 4 * stride) {
+        double pv[4], qv[4], xv[4], rv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            pv[u] = p[i + u * stride]; qv[u] = q[i + u * stride];
+            xv[u] = x[i + u * stride]; rv[u] = r[i + u * stride];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            x[i + u * stride] = fma(a, pv[u], xv[u]);
+            const double ri = fma(-a, qv[u], rv[u]);
+            r[i + u * stride] = ri;
+            s = fma(ri, ri, s);
+        }
+    }
+    for (; i < n; i += stride) {
+        x[i] = fma(a, p[i], x[i]);
+        const double ri = fma(-a, q[i], r[i]);
         r[i] = ri;
-        s += ri * ri;
+        s = fma(ri, ri, s);
     }
     __shared__ double tot;
     if (grid_reduce(s, part, counter, &tot) && threadIdx.x == 0) {
@@ -952,80 +1128,24 @@ __global__ void k_pcg_update(int64_t n, double *x, double *r, const double *p, c
     }
 }
 
-// rho_new = r.z ; beta = rho_new / rho
-__global__ void k_pcg_rz(int64_t n, const double *r, const double *z, double *part,
-                         unsigned *counter, PcgScalars *sc, double *betas) {
-    if (sc->done) return;
+// rho = r.z and beta, when the post-correction could not fuse it.
+__global__ void k_pcg_rz(int n, const double *__restrict__ r, const double *__restrict__ z, RzArgs rz) {
+    pdl_wait();
+    pdl_trigger();
+    if (rz.sc->done) return;
     double s = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        s += r[i] * z[i];
+    const int stride = gridDim.x * blockDim.x;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i + 3 * stride < n; i += 4 * stride) {
+        double rv[4], zv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) { rv[u] = r[i + u * stride]; zv[u] = z[i + u * stride]; }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) s = fma(rv[u], zv[u], s);
+    }
+    for (; i < n; i += stride) s = fma(r[i], z[i], s);
     __shared__ double tot;
-    if (grid_reduce(s, part, counter, &tot) && threadIdx.x == 0) {
-        sc->rho_new = tot;
-        sc->beta = tot / sc->rho;
-        betas[sc->it - 1] = sc->beta;
-        sc->rho = tot;
-    }
-}
-
-__global__ void k_pcg_dir(int64_t n, double *p, const double *z, const PcgScalars *sc) {
-    if (sc->done) return;
-    const double bt = sc->beta;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        p[i] = z[i] + bt * p[i];
-}
-
-// Extreme eigenvalues of the Lanczos tridiagonal matrix by multisection on
-// Sturm counts: one warp, 32 trial points per round.
-__device__ int sturm_count(const double *d, const double *e2, int k, double x) {
-    int cnt = 0;
-    double q = 1.0;
-    for (int i = 0; i < k; ++i) {
-        q = d[i] - x - (i > 0 ? e2[i - 1] / q : 0.0);
-        if (q == 0.0) q = -1e-300;
-        if (q < 0.0) ++cnt;
-    }
-    return cnt;
-}
-
-__global__ void k_lanczos(const double *alphas, const double *betas, const PcgScalars *sc,
-                          double *out, double *d, double *e2) {
-    if (blockIdx.x != 0) return;
-    const int lane = threadIdx.x & 31;
-    const int k = sc->it;
-    if (k <= 0) {
-        if (lane == 0) out[0] = out[1] = 1.0;
-        return;
-    }
-    for (int j = lane; j < k; j += 32) {
-        d[j] = 1.0 / alphas[j] + (j > 0 ? betas[j - 1] / alphas[j - 1] : 0.0);
-        if (j + 1 < k) e2[j] = betas[j] / (alphas[j] * alphas[j]);
-    }
-    __syncwarp();
-    double lo = 1e300, hi = -1e300;
-    for (int j = lane; j < k; j += 32) {
-        const double off = (j > 0 ? sqrt(e2[j - 1]) : 0.0) + (j + 1 < k ? sqrt(e2[j]) : 0.0);
-        lo = fmin(lo, d[j] - off);
-        hi = fmax(hi, d[j] + off);
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-        hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
-    }
-    for (int which = 0; which < 2; ++which) {
-        const int target = which == 0 ? 1 : k;   // smallest: count >= 1, largest: count >= k
-        double a = lo, b = hi;
-        for (int round = 0; round < 40; ++round) {
-            const double x = a + (b - a) * (double)(lane + 1) / 33.0;
-            const unsigned hit = __ballot_sync(0xffffffffu, sturm_count(d, e2, k, x) >= target);
-            const int first = hit ? __ffs(hit) - 1 : 32;
-            const double na = first == 0 ? a : a + (b - a) * (double)first / 33.0;
-            const double nb = first == 32 ? b : a + (b - a) * (double)(first + 1) / 33.0;
-            a = na; b = nb;
-            if (b - a <= 1e-15 * fmax(fabs(a), fabs(b))) break;
-        }
-        if (lane == 0) out[which] = 0.5 * (a + b);
-    }
+    if (grid_reduce(s, rz.part, rz.counter, &tot) && threadIdx.x == 0) finish_rz(tot, rz.sc, rz.betas);
 }
 
 template <class D>
@@ -1054,6 +1174,13 @@ __global__ void k_selftest_wait(int *err, long polls) {
 
 int grid_for(int64_t n) {
     int64_t g = (n + RB - 1) / RB;
+    if (g > 152 * 8) g = 152 * 8;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+// Grid of the FP64 vector kernels of the PCG iteration: about four entries per thread.
+int vec_grid(int64_t n) {
+    int64_t g = (n + 4 * RB - 1) / (4 * RB);
     if (g > 152 * 8) g = 152 * 8;
     if (g < 1) g = 1;
     return (int)g;
@@ -1091,6 +1218,32 @@ int num_sms() {
     return n;
 }
 
+// Launch with programmatic stream serialisation (see pdl_wait); setting the
+// environment variable BDDC_PDL=0 launches in plain stream order instead.
+bool pdl_enabled() {
+    static const bool on = [] {
+        const char *e = std::getenv("BDDC_PDL");
+        return !(e && e[0] == '0');
+    }();
+    return on;
+}
+
+template <class... KArgs, class... Args>
+void launch_pdl(void (*k)(KArgs...), int grid, int block, size_t smem, cudaStream_t s,
+                Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 // Warps (substructures) per block: as many as needed for one wave over the
 // SMs, limited by the shared-memory slices that fit in one block.
 int warps_per_block(int nsub, size_t slice) {
@@ -1104,21 +1257,23 @@ int warps_per_block(int nsub, size_t slice) {
 
 template <class T, class ACC, int BP>
 void dir_launch(const DevLevel &L, bool post, const double *r, double *z, const int *skip,
-                cudaStream_t s) {
+                cudaStream_t s, const RzArgs *rz) {
     const size_t slice = DirSlice<T, ACC, BP>::bytes(L);
     const int wpc = warps_per_block(L.nsub, slice);
     const size_t sm = slice * wpc;
     const int grid = (L.nsub + wpc - 1) / wpc;
-    if (!post) k_dir_w<T, ACC, BP, false><<<grid, 32 * wpc, sm, s>>>(L, r, z, skip, (unsigned)slice);
-    else k_dir_w<T, ACC, BP, true><<<grid, 32 * wpc, sm, s>>>(L, r, z, skip, (unsigned)slice);
+    const RzArgs none{nullptr, nullptr, nullptr, nullptr};
+    if (!post) launch_pdl(k_dir_w<T, ACC, BP, false>, grid, 32 * wpc, sm, s, L, r, z, skip, (unsigned)slice, none);
+    else launch_pdl(k_dir_w<T, ACC, BP, true>, grid, 32 * wpc, sm, s, L, r, z, skip, (unsigned)slice,
+                    rz ? *rz : none);
 }
 
 template <class T, class ACC>
 void dir_dispatch(const DevLevel &L, bool post, const double *r, double *z, const int *skip,
-                  cudaStream_t s) {
-    if (L.bp == 8) dir_launch<T, ACC, 8>(L, post, r, z, skip, s);
-    else if (L.bp == 16) dir_launch<T, ACC, 16>(L, post, r, z, skip, s);
-    else dir_launch<T, ACC, 32>(L, post, r, z, skip, s);
+                  cudaStream_t s, const RzArgs *rz = nullptr) {
+    if (L.bp == 8) dir_launch<T, ACC, 8>(L, post, r, z, skip, s, rz);
+    else if (L.bp == 16) dir_launch<T, ACC, 16>(L, post, r, z, skip, s, rz);
+    else dir_launch<T, ACC, 32>(L, post, r, z, skip, s, rz);
 }
 
 int pidx_of(int prec) { return prec == BDDC_PREC_FP64 ? 0 : (prec == BDDC_PREC_FP32 ? 1 : 2); }
@@ -1128,7 +1283,8 @@ void neu_launch(const DevLevel &L, int prec, const double *r, const int *skip, c
     const int pi = pidx_of(prec);
     const size_t slice = al16(al16((size_t)L.max_nrec[pi]) + al16(sizeof(ACC) * (size_t)L.max_nG) + 16);
     const int wpc = warps_per_block(L.nsub, slice);
-    k_neumann_r<T, ACC><<<(L.nsub + wpc - 1) / wpc, 32 * wpc, slice * wpc, s>>>(L, pi, r, skip, (unsigned)slice);
+    launch_pdl(k_neumann_r<T, ACC>, (L.nsub + wpc - 1) / wpc, 32 * wpc, slice * wpc, s, L, pi, r, skip,
+               (unsigned)slice);
 }
 
 template <class T, class ACC>
@@ -1137,7 +1293,8 @@ void avg_launch(const DevLevel &L, int prec, const int *skip, cudaStream_t s) {
     const size_t slice = al16(al16((size_t)L.max_nrec[pi]) +
                               al16(sizeof(ACC) * (size_t)(L.max_nc > 0 ? L.max_nc : 1)) + 16);
     const int wpc = warps_per_block(L.nsub, slice);
-    k_average_r<T, ACC><<<(L.nsub + wpc - 1) / wpc, 32 * wpc, slice * wpc, s>>>(L, pi, skip, (unsigned)slice);
+    launch_pdl(k_average_r<T, ACC>, (L.nsub + wpc - 1) / wpc, 32 * wpc, slice * wpc, s, L, pi, skip,
+               (unsigned)slice);
 }
 
 // The warp kernels need a power-of-two block size, the records and their
@@ -1195,6 +1352,8 @@ void build_records(DevLevel &D, const int *ownPos, const int *ownDof, cudaStream
     k_build_nrec<__nv_bfloat16><<<D.nsub, 128, 0, s>>>(D, D.b16, D.nrec[2], D.nrecOff[2]);
 }
 
+bool apply_fuses_rz(const DevLevel &L, int prec) { return warp_path(L, prec); }
+
 void apply_level_pre(const DevLevel &L, int prec, const double *r, const int *skip, cudaStream_t s,
                      cudaEvent_t *ev) {
     const bool wp = warp_path(L, prec);
@@ -1223,7 +1382,7 @@ void apply_level_pre(const DevLevel &L, int prec, const double *r, const int *sk
 }
 
 void apply_level_post(const DevLevel &L, int prec, const double *r, double *z, const int *skip,
-                      cudaStream_t s, cudaEvent_t *ev) {
+                      cudaStream_t s, cudaEvent_t *ev, const RzArgs *rz) {
     const bool wp = warp_path(L, prec);
     if (ev) cudaEventRecord(ev[0], s);
     if (wp) {
@@ -1238,13 +1397,14 @@ void apply_level_post(const DevLevel &L, int prec, const double *r, double *z, c
     }
     if (ev) cudaEventRecord(ev[1], s);
     if (wp) {
-        if (prec == BDDC_PREC_FP64) dir_dispatch<double, double>(L, true, r, z, skip, s);
-        else if (prec == BDDC_PREC_FP32) dir_dispatch<float, float>(L, true, r, z, skip, s);
-        else dir_dispatch<__nv_bfloat16, float>(L, true, r, z, skip, s);
+        if (prec == BDDC_PREC_FP64) dir_dispatch<double, double>(L, true, r, z, skip, s, rz);
+        else if (prec == BDDC_PREC_FP32) dir_dispatch<float, float>(L, true, r, z, skip, s, rz);
+        else dir_dispatch<__nv_bfloat16, float>(L, true, r, z, skip, s, rz);
     } else {
         if (prec == BDDC_PREC_FP64) post_t<double, double>(L, r, z, skip, s);
         else if (prec == BDDC_PREC_FP32) post_t<float, float>(L, r, z, skip, s);
         else post_t<__nv_bfloat16, float>(L, r, z, skip, s);
+        if (rz) launch_pcg_rz((int)L.n, r, z, *rz, s);
     }
     if (ev) cudaEventRecord(ev[2], s);
 }
@@ -1252,7 +1412,7 @@ void apply_level_post(const DevLevel &L, int prec, const double *r, double *z, c
 void launch_dense_symv(int n, int ld, const double *A, const double *x, double *y, const int *skip,
                        cudaStream_t s) {
     if (n <= 0) return;
-    k_dense_symv<<<(n + 7) / 8, 256, 0, s>>>(n, ld, A, x, y, skip);
+    launch_pdl(k_dense_symv, (n + SV_ROWS - 1) / SV_ROWS, 32 * SV_WR * SV_ROWS, 0, s, n, ld, A, x, y, skip);
 }
 
 void launch_q1_weights(int nx, const double *k, double *w, cudaStream_t s) {
@@ -1272,33 +1432,33 @@ void launch_norm2(int n, const double *v, double *part, unsigned *counter, doubl
                   cudaStream_t s) {
     k_norm2<<<grid_for(n), RB, 0, s>>>(n, v, part, counter, out);
 }
-void launch_pcg_init(int n, const double *b, double *x, double *r, double *part,
-                     unsigned *counter, PcgScalars *sc, double tol, int maxit, cudaStream_t s) {
-    k_pcg_init<<<grid_for(n), RB, 0, s>>>(n, b, x, r, part, counter, sc, tol, maxit);
+void launch_pcg_init(int n, const double *b, double *x, double *r, double *p0, double *part,
+                     unsigned *counter, unsigned *rzcounter, PcgScalars *sc, double tol, int maxit,
+                     cudaStream_t s) {
+    k_pcg_init<<<grid_for(n), RB, 0, s>>>(n, b, x, r, p0, part, counter, rzcounter, sc, tol, maxit);
 }
-void launch_pcg_first_dir(int n, double *p, const double *z, const double *r, double *part,
-                          unsigned *counter, PcgScalars *sc, cudaStream_t s) {
-    k_pcg_first_dir<<<grid_for(n), RB, 0, s>>>(n, p, z, r, part, counter, sc);
+void launch_pcg_dir_spmv(int nx, const double *w, const double *z, double *p0, double *p1,
+                         double *q, double *part, unsigned *counter, PcgScalars *sc,
+                         double *alphas, cudaStream_t s) {
+    const int n1 = nx - 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)((n1 + PT_X - 1) / PT_X), (unsigned)((n1 + PT_Y - 1) / PT_Y));
+    cfg.blockDim = dim3(PT_T);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, k_pcg_dir_spmv, nx, w, z, p0, p1, q, part, counter, sc, alphas);
 }
-void launch_pcg_spmv_dot(int nx, const double *w, const double *p, double *q, double *part,
-                         unsigned *counter, PcgScalars *sc, double *alphas, cudaStream_t s) {
-    const int64_t n = (int64_t)(nx - 1) * (nx - 1);
-    k_pcg_spmv_dot<<<grid_for(n), RB, 0, s>>>(nx, w, p, q, part, counter, sc, alphas);
+void launch_pcg_update(int n, double *x, double *r, const double *p0, const double *p1,
+                       const double *q, double *part, unsigned *counter, PcgScalars *sc,
+                       cudaStream_t s) {
+    launch_pdl(k_pcg_update, vec_grid(n), RB, 0, s, n, x, r, p0, p1, q, part, counter, sc);
 }
-void launch_pcg_update(int n, double *x, double *r, const double *p, const double *q,
-                       double *part, unsigned *counter, PcgScalars *sc, cudaStream_t s) {
-    k_pcg_update<<<grid_for(n), RB, 0, s>>>(n, x, r, p, q, part, counter, sc);
-}
-void launch_pcg_rz(int n, const double *r, const double *z, double *part, unsigned *counter,
-                   PcgScalars *sc, double *betas, cudaStream_t s) {
-    k_pcg_rz<<<grid_for(n), RB, 0, s>>>(n, r, z, part, counter, sc, betas);
-}
-void launch_pcg_dir(int n, double *p, const double *z, PcgScalars *sc, cudaStream_t s) {
-    k_pcg_dir<<<grid_for(n), RB, 0, s>>>(n, p, z, sc);
-}
-void launch_lanczos_extremes(const double *alphas, const double *betas, const PcgScalars *sc,
-                             double *out2, double *work, int cap, cudaStream_t s) {
-    k_lanczos<<<1, 32, 0, s>>>(alphas, betas, sc, out2, work, work + cap);
+void launch_pcg_rz(int n, const double *r, const double *z, const RzArgs &rz, cudaStream_t s) {
+    launch_pdl(k_pcg_rz, vec_grid(n), RB, 0, s, n, r, z, rz);
 }
 void launch_selftest_wait(int *err, long polls, cudaStream_t s) {
     k_selftest_wait<<<1, 32, 0, s>>>(err, polls);

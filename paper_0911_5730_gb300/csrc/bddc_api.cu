@@ -63,8 +63,11 @@ struct LevelData {
 struct Workspace {
     DevArena arena;
     std::vector<DevLevel> lv;
-    double *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *tmp = nullptr;
-    double *part = nullptr, *alphas = nullptr, *betas = nullptr, *lanc = nullptr, *lout = nullptr;
+    double *x = nullptr, *r = nullptr, *z = nullptr, *q = nullptr, *tmp = nullptr;
+    double *p0 = nullptr, *p1 = nullptr;   // search direction, alternating by iteration
+    double *rzpart = nullptr;              // r.z partials, one per level-1 substructure
+    unsigned *rzcounter = nullptr;
+    double *part = nullptr, *alphas = nullptr, *betas = nullptr, *lout = nullptr;
     double *bbuf = nullptr;
     unsigned *counter = nullptr;
     PcgScalars *sc = nullptr;
@@ -74,6 +77,8 @@ struct Workspace {
     cudaEvent_t ev = nullptr;
     cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};
     int maxit_cap = 0;
+    int last_iters = 0;                 // iterations of the previous solve (chunking hint)
+    std::vector<double> hal, hbe;       // host copies of the CG coefficients
     ~Workspace() {
         for (auto &g : graph) if (g) cudaGraphExecDestroy(g);
         if (hsc) cudaFreeHost(hsc);
@@ -550,17 +555,22 @@ void make_workspace(bddc_ctx *C, Workspace &W, int maxit_cap) {
         W.lv.push_back(D);
     }
     W.x = A.alloc_n<double>(n); W.r = A.alloc_n<double>(n); W.z = A.alloc_n<double>(n);
-    W.p = A.alloc_n<double>(n); W.q = A.alloc_n<double>(n); W.tmp = A.alloc_n<double>(n);
+    W.p0 = A.alloc_n<double>(n); W.p1 = A.alloc_n<double>(n);
+    W.q = A.alloc_n<double>(n); W.tmp = A.alloc_n<double>(n);
+    BDDC_CUDA_TRY(cudaMemset(W.p0, 0, sizeof(double) * n));
+    BDDC_CUDA_TRY(cudaMemset(W.p1, 0, sizeof(double) * n));
     W.bbuf = A.alloc_n<double>(n);
-    W.part = A.alloc_n<double>(4096);
+    W.part = A.alloc_n<double>(std::max<int64_t>(4096, (int64_t)n / 1024 + 1024));   // block partials
+    W.rzpart = A.alloc_n<double>(std::max(4096, W.lv.empty() ? 1 : W.lv[0].nsub));
     W.counter = A.alloc_n<unsigned>(4);
+    W.rzcounter = A.alloc_n<unsigned>(4);
     BDDC_CUDA_TRY(cudaMemset(W.counter, 0, 4 * sizeof(unsigned)));
+    BDDC_CUDA_TRY(cudaMemset(W.rzcounter, 0, 4 * sizeof(unsigned)));
     W.sc = A.alloc_n<PcgScalars>(1);
     BDDC_CUDA_TRY(cudaMemset(W.sc, 0, sizeof(PcgScalars)));
     W.maxit_cap = maxit_cap;
     W.alphas = A.alloc_n<double>(maxit_cap + 1);
     W.betas = A.alloc_n<double>(maxit_cap + 1);
-    W.lanc = A.alloc_n<double>(2 * (size_t)(maxit_cap + 1) + 16);
     W.lout = A.alloc_n<double>(4);
     BDDC_CUDA_TRY(cudaHostAlloc((void **)&W.hsc, sizeof(PcgScalars), cudaHostAllocDefault));
     BDDC_CUDA_TRY(cudaHostAlloc((void **)&W.hout, 8 * sizeof(double), cudaHostAllocDefault));
@@ -569,14 +579,14 @@ void make_workspace(bddc_ctx *C, Workspace &W, int maxit_cap) {
 }
 
 void apply_rec(bddc_ctx *C, Workspace &W, int l, int prec, const double *r, double *z,
-               const int *skip, cudaStream_t st) {
+               const int *skip, cudaStream_t st, const RzArgs *rz = nullptr) {
     const DevLevel &D = W.lv[l];
     apply_level_pre(D, prec, r, skip, st);
     if (l + 1 == (int)W.lv.size())
         launch_dense_symv(C->n_top, C->ld_top, C->Ainv, D.rcv, D.ucv, skip, st);
     else
         apply_rec(C, W, l + 1, prec, D.rcv, D.ucv, skip, st);
-    apply_level_post(D, prec, r, z, skip, st);
+    apply_level_post(D, prec, r, z, skip, st, nullptr, rz);
 }
 
 cudaGraphExec_t pcg_graph(bddc_ctx *C, Workspace &W, int prec) {
@@ -585,11 +595,10 @@ cudaGraphExec_t pcg_graph(bddc_ctx *C, Workspace &W, int prec) {
     cudaStream_t st = W.stream;
     cudaGraph_t g;
     BDDC_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    launch_pcg_spmv_dot(C->nx, C->w_dev, W.p, W.q, W.part, W.counter, W.sc, W.alphas, st);
-    launch_pcg_update(n, W.x, W.r, W.p, W.q, W.part, W.counter, W.sc, st);
-    apply_rec(C, W, 0, prec, W.r, W.z, &W.sc->done, st);
-    launch_pcg_rz(n, W.r, W.z, W.part, W.counter, W.sc, W.betas, st);
-    launch_pcg_dir(n, W.p, W.z, W.sc, st);
+    const RzArgs rz{W.rzpart, W.rzcounter, W.sc, W.betas};
+    launch_pcg_dir_spmv(C->nx, C->w_dev, W.z, W.p0, W.p1, W.q, W.part, W.counter, W.sc, W.alphas, st);
+    launch_pcg_update(n, W.x, W.r, W.p0, W.p1, W.q, W.part, W.counter, W.sc, st);
+    apply_rec(C, W, 0, prec, W.r, W.z, &W.sc->done, st, &rz);
     BDDC_CUDA_TRY(cudaStreamEndCapture(st, &g));
     BDDC_CUDA_TRY(cudaGraphInstantiate(&W.graph[prec], g, 0));
     cudaGraphDestroy(g);
@@ -597,25 +606,67 @@ cudaGraphExec_t pcg_graph(bddc_ctx *C, Workspace &W, int prec) {
 }
 
 // One right-hand side; runs on W.stream and synchronises it.
+// Extreme eigenvalues of the Lanczos matrix of k CG steps (diagonal
+// 1/alpha_j + beta_{j-1}/alpha_{j-1}, off-diagonal sqrt(beta_j)/alpha_j) by
+// bisection on Sturm counts.  A k x k tridiagonal: host arithmetic on the
+// coefficients the device recorded.
+void lanczos_extremes(const std::vector<double> &al, const std::vector<double> &be, int k,
+                      double *lo_out, double *hi_out) {
+    if (k <= 0) { *lo_out = *hi_out = 1.0; return; }
+    std::vector<double> d(k), e2(k > 1 ? k - 1 : 1);
+    for (int j = 0; j < k; ++j) {
+        d[j] = 1.0 / al[j] + (j > 0 ? be[j - 1] / al[j - 1] : 0.0);
+        if (j + 1 < k) e2[j] = be[j] / (al[j] * al[j]);
+    }
+    double lo = 1e300, hi = -1e300;
+    for (int j = 0; j < k; ++j) {
+        const double off = (j > 0 ? std::sqrt(e2[j - 1]) : 0.0) + (j + 1 < k ? std::sqrt(e2[j]) : 0.0);
+        lo = std::min(lo, d[j] - off);
+        hi = std::max(hi, d[j] + off);
+    }
+    auto count = [&](double x) {
+        int c = 0;
+        double q = 1.0;
+        for (int i = 0; i < k; ++i) {
+            q = d[i] - x - (i > 0 ? e2[i - 1] / q : 0.0);
+            if (q == 0.0) q = -1e-300;
+            if (q < 0.0) ++c;
+        }
+        return c;
+    };
+    for (int which = 0; which < 2; ++which) {
+        const int target = which == 0 ? 1 : k;
+        double a = lo, b = hi;
+        for (int it = 0; it < 200 && b - a > 1e-15 * std::max(std::fabs(a), std::fabs(b)); ++it) {
+            const double mid = 0.5 * (a + b);
+            if (count(mid) >= target) b = mid; else a = mid;
+        }
+        (which == 0 ? *lo_out : *hi_out) = 0.5 * (a + b);
+    }
+}
+
 int pcg_one(bddc_ctx *C, Workspace &W, int prec, const double *b, double *x, double rtol,
             int maxit, bddc_solve_info *info) {
     const int n = C->n();
     cudaStream_t st = W.stream;
     if (maxit > W.maxit_cap) maxit = W.maxit_cap;
-    launch_pcg_init(n, b, W.x, W.r, W.part, W.counter, W.sc, rtol, maxit, st);
-    apply_rec(C, W, 0, prec, W.r, W.z, &W.sc->done, st);
-    launch_pcg_first_dir(n, W.p, W.z, W.r, W.part, W.counter, W.sc, st);
+    const RzArgs rz{W.rzpart, W.rzcounter, W.sc, W.betas};
+    launch_pcg_init(n, b, W.x, W.r, W.p0, W.part, W.counter, W.rzcounter, W.sc, rtol, maxit, st);
+    apply_rec(C, W, 0, prec, W.r, W.z, &W.sc->done, st, &rz);
     cudaGraphExec_t g = pcg_graph(C, W, prec);
-    const int per_apply = 4 * (int)W.lv.size() + 1;
-    int launches = 2 + per_apply;
-    int chunk = 4;
+    int per_apply = 4 * (int)W.lv.size() + 1;
+    if (!apply_fuses_rz(W.lv[0], prec)) per_apply += 1;
+    int launches = 1 + per_apply;
+    // launch the previous solve's iteration count before the first check
+    // (iterations past convergence only skip their kernels)
+    int chunk = W.last_iters > 1 ? std::min(W.last_iters, 256) : 4;
     double rr_true = 0.0;
     for (;;) {
         for (int k = 0; k < chunk; ++k) BDDC_CUDA_TRY(cudaGraphLaunch(g, st));
-        launches += chunk * (4 + per_apply);
+        launches += chunk * (2 + per_apply);
         BDDC_CUDA_TRY(cudaMemcpyAsync(W.hsc, W.sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, st));
         BDDC_CUDA_TRY(cudaStreamSynchronize(st));
-        if (!W.hsc->done) { chunk = std::min(chunk * 2, 16); continue; }
+        if (!W.hsc->done) { chunk = std::max(1, std::min(chunk / 2, 16)); continue; }
         // Confirm with the true residual; keep iterating if it is not yet met.
         launch_residual(C->nx, C->w_dev, b, W.x, W.tmp, st);
         launch_norm2(n, W.tmp, W.part, W.counter, W.lout, st);
@@ -624,18 +675,26 @@ int pcg_one(bddc_ctx *C, Workspace &W, int prec, const double *b, double *x, dou
         BDDC_CUDA_TRY(cudaStreamSynchronize(st));
         rr_true = W.hout[0];
         if (W.hsc->conv && rr_true > W.hsc->tol2 && W.hsc->it < maxit) {
+            // the recursive residual drifted: restart from the true residual
+            // with a fresh direction (beta = 0)
             PcgScalars hs = *W.hsc;
-            hs.done = 0; hs.conv = 0;
+            hs.done = 0; hs.conv = 0; hs.fresh = 1; hs.rr = rr_true;
             *W.hsc = hs;
             BDDC_CUDA_TRY(cudaMemcpyAsync(W.sc, W.hsc, sizeof(PcgScalars), cudaMemcpyHostToDevice, st));
+            BDDC_CUDA_TRY(cudaMemcpyAsync(W.r, W.tmp, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+            apply_rec(C, W, 0, prec, W.r, W.z, &W.sc->done, st, &rz);
+            launches += per_apply;
             chunk = 1;
             continue;
         }
         break;
     }
-    launch_lanczos_extremes(W.alphas, W.betas, W.sc, W.lout + 1, W.lanc, W.maxit_cap + 1, st);
-    launches += 1;
-    BDDC_CUDA_TRY(cudaMemcpyAsync(W.hout + 1, W.lout + 1, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    const int kit = std::min(W.hsc->it, W.maxit_cap);
+    if (W.hal.size() < (size_t)kit + 1) { W.hal.resize(kit + 1); W.hbe.resize(kit + 1); }
+    if (kit > 0) {
+        BDDC_CUDA_TRY(cudaMemcpyAsync(W.hal.data(), W.alphas, sizeof(double) * kit, cudaMemcpyDeviceToHost, st));
+        BDDC_CUDA_TRY(cudaMemcpyAsync(W.hbe.data(), W.betas, sizeof(double) * kit, cudaMemcpyDeviceToHost, st));
+    }
     BDDC_CUDA_TRY(cudaMemcpyAsync(x, W.x, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
     int kerr = 0;
     BDDC_CUDA_TRY(cudaMemcpyAsync(&kerr, C->err_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -644,15 +703,18 @@ int pcg_one(bddc_ctx *C, Workspace &W, int prec, const double *b, double *x, dou
     if (kerr) throw Error(BDDC_E_TIMEOUT, "a bounded device wait gave up during the solve");
     const PcgScalars &h = *W.hsc;
     const int status = (h.conv && rr_true <= h.tol2 * (1 + 1e-12)) ? BDDC_OK : BDDC_E_NOCONV;
+    W.last_iters = h.it;
     if (info) {
+        double lmin = 1.0, lmax = 1.0;
+        lanczos_extremes(W.hal, W.hbe, kit, &lmin, &lmax);
         info->iters = h.it;
         info->status = status;
         info->kernel_launches = launches;
         info->relres = h.bb > 0 ? std::sqrt(h.rr / h.bb) : 0.0;
         info->relres_true = h.bb > 0 ? std::sqrt(rr_true / h.bb) : 0.0;
-        info->lam_min = W.hout[1];
-        info->lam_max = W.hout[2];
-        info->kappa_est = W.hout[1] > 0 ? W.hout[2] / W.hout[1] : 0.0;
+        info->lam_min = lmin;
+        info->lam_max = lmax;
+        info->kappa_est = lmin > 0 ? lmax / lmin : 0.0;
     }
     return status;
 }

@@ -131,6 +131,22 @@ struct NRecLayout {
     }
 };
 
+struct PcgScalars {
+    double rho, rho_new, pq, alpha, beta, rr, bb, tol2;
+    int it, done, conv, maxit;
+    int fresh;        // next r.z starts a new direction sequence (beta = 0)
+    int pad_;
+};
+// r.z of the PCG iteration, reduced by the level-1 post-correction kernel
+// when it writes z (part holds one partial per substructure, counter is zero
+// between launches) or by a separate kernel otherwise.
+struct RzArgs {
+    double *part;
+    unsigned *counter;
+    PcgScalars *sc;
+    double *betas;
+};
+
 // ----------------------------------------------------------------------------
 // Apply / PCG launchers (apply_kernels.cu)
 // ----------------------------------------------------------------------------
@@ -144,8 +160,13 @@ void apply_level_pre(const DevLevel &L, int prec, const double *r, const int *sk
                      cudaStream_t s, cudaEvent_t *ev = nullptr);
 // Up-sweep of one level: (9) averaging, (10)-(11) post-correction into z.
 // ev (optional, 3 events) are recorded before each kernel and after the last.
+// With rz, also rho = r.z and beta = rho / rho_old (0 on a fresh start) for
+// the PCG recurrence, fused into the post-correction where it can be.
 void apply_level_post(const DevLevel &L, int prec, const double *r, double *z, const int *skip,
-                      cudaStream_t s, cudaEvent_t *ev = nullptr);
+                      cudaStream_t s, cudaEvent_t *ev = nullptr, const RzArgs *rz = nullptr);
+// Whether apply_level_post fuses the r.z reduction into its last kernel (one
+// kernel fewer per PCG iteration).
+bool apply_fuses_rz(const DevLevel &L, int prec);
 // y = A x with A dense n x n, leading dimension ld (a multiple of 4, zero
 // padded); x must be readable and zero on [n, ld).
 void launch_dense_symv(int n, int ld, const double *A, const double *x, double *y, const int *skip,
@@ -155,33 +176,29 @@ void prepare_apply_kernels();
 // Build the per-substructure records of a level (after its operators exist).
 void build_records(DevLevel &D, const int *ownPos, const int *ownDof, cudaStream_t s);
 
-struct PcgScalars {
-    double rho, rho_new, pq, alpha, beta, rr, bb, tol2;
-    int it, done, conv, maxit;
-};
 // Q1 operator from per-node stencil weights w [5][n] (diagonal, E, N, NE, NW).
 void launch_q1_weights(int nx, const double *k, double *w, cudaStream_t s);
 void launch_q1_spmv(int nx, const double *w, const double *x, double *y, cudaStream_t s);
-// q = A p, pq = p.q (partials reduced by the last block), alpha = rho / pq
-void launch_pcg_spmv_dot(int nx, const double *w, const double *p, double *q, double *part,
-                         unsigned *counter, PcgScalars *sc, double *alphas, cudaStream_t s);
-// x += alpha p; r -= alpha q; rr = r.r; convergence flag
-void launch_pcg_update(int n, double *x, double *r, const double *p, const double *q,
-                       double *part, unsigned *counter, PcgScalars *sc, cudaStream_t s);
-// rho_new = r.z ; beta = rho_new / rho ; p = z + beta p (second kernel)
-void launch_pcg_rz(int n, const double *r, const double *z, double *part, unsigned *counter,
-                   PcgScalars *sc, double *betas, cudaStream_t s);
-void launch_pcg_dir(int n, double *p, const double *z, PcgScalars *sc, cudaStream_t s);
-void launch_pcg_init(int n, const double *b, double *x, double *r, double *part,
-                     unsigned *counter, PcgScalars *sc, double tol, int maxit, cudaStream_t s);
-void launch_pcg_first_dir(int n, double *p, const double *z, const double *r, double *part,
-                          unsigned *counter, PcgScalars *sc, cudaStream_t s);
+// PCG iteration (all FP64).  The search direction lives in two buffers p0, p1:
+// iteration `it` reads p_old = p[it & 1] and writes p_new = p[(it + 1) & 1].
+// p_new = z + beta p_old; q = A p_new; alpha = rho / (p_new . q)
+void launch_pcg_dir_spmv(int nx, const double *w, const double *z, double *p0, double *p1,
+                         double *q, double *part, unsigned *counter, PcgScalars *sc,
+                         double *alphas, cudaStream_t s);
+// x += alpha p_new; r -= alpha q; rr = r.r; convergence flag; it += 1
+void launch_pcg_update(int n, double *x, double *r, const double *p0, const double *p1,
+                       const double *q, double *part, unsigned *counter, PcgScalars *sc,
+                       cudaStream_t s);
+// rho = r.z, beta (the unfused form of RzArgs)
+void launch_pcg_rz(int n, const double *r, const double *z, const RzArgs &rz, cudaStream_t s);
+// x = 0, r = b, p0 = 0, bb = b.b, a fresh start
+void launch_pcg_init(int n, const double *b, double *x, double *r, double *p0, double *part,
+                     unsigned *counter, unsigned *rzcounter, PcgScalars *sc, double tol, int maxit,
+                     cudaStream_t s);
 void launch_residual(int nx, const double *w, const double *b, const double *x, double *res,
                      cudaStream_t s);
 void launch_norm2(int n, const double *v, double *part, unsigned *counter, double *out,
                   cudaStream_t s);
-void launch_lanczos_extremes(const double *alphas, const double *betas, const PcgScalars *sc,
-                             double *out2, double *work, int cap, cudaStream_t s);
 void launch_convert(const double *src, float *dst, int64_t n, cudaStream_t s);
 void launch_selftest_wait(int *err, long polls, cudaStream_t s);
 void launch_convert(const double *src, __nv_bfloat16 *dst, int64_t n, cudaStream_t s);
