@@ -39,7 +39,12 @@ FULL_SUBS = 1024
 
 # DRAM traffic of the dominant kernel from the ncu capture summarised in
 # profiles/, keyed by kernel, valid only while the kernel source is unchanged.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # ncu --set full, FP32 solve of two_level_channels_512 (one launch each)
+    "pre": {"bytes": 37124352 + 10752, "src": "9dc0a638d7bc"},
+    "post": {"bytes": 37405184 + 9472, "src": "9dc0a638d7bc"},
+    "top_solve": {"bytes": 40696064, "src": "9dc0a638d7bc"},
+}
 
 
 def _args():
