@@ -81,8 +81,10 @@ typedef struct {
 typedef struct {
     int32_t iters;        /* PCG iterations taken */
     int32_t status;       /* BDDC_OK or BDDC_E_NOCONV */
-    int32_t kernel_launches;  /* device kernels this solve launched */
-    int32_t reserved;
+    int32_t kernel_launches;  /* device kernels this solve launched (for a batch: all of
+                                 them, reported on its first right-hand side, 0 on the rest) */
+    int32_t batch_width;  /* right-hand sides solved together with this one: K of the
+                             lockstep batch (bddc_pcg_solve with nrhs > 1), 1 otherwise */
     double relres;        /* recursive residual ||r_k|| / ||b|| */
     double relres_true;   /* ||b - A x|| / ||b|| recomputed in FP64 */
     double kappa_est;     /* Lanczos estimate lambda_max / lambda_min (Tables 1-7) */
@@ -259,6 +261,18 @@ int bddc_apply_noalloc(bddc_ctx *ctx, const double *r_dev, double *z_dev, void *
  * the paper.
  */
 int bddc_selftest_wait_timeout(void *stream);
+
+/*
+ * bddc_selftest_convert - check the integer-operation conversions the batch
+ * kernels use between binary64 and binary32 (IEEE 754-2008, Sec. 5.4.2:
+ * narrowing rounds to nearest, ties to even) against the hardware
+ * conversions, bit for bit.  For each of the n values d_dev[i] (device FP64)
+ * it narrows d_dev[i] and widens the binary32 whose bits are the low word of
+ * d_dev[i]; *mismatches (host) receives the number of differing results
+ * (NaN results compare equal).  Allocates 8 bytes of device memory and
+ * synchronises the stream.  No counterpart in the paper.
+ */
+int bddc_selftest_convert(const double *d_dev, int64_t n, int64_t *mismatches, void *stream);
 
 void bddc_destroy(bddc_ctx *ctx);
 

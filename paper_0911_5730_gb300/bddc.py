@@ -26,7 +26,7 @@ SYMBOLS = ["bddc_setup", "bddc_apply", "bddc_pcg_solve", "bddc_pcg_solve_host",
            "bddc_set_precision", "bddc_query", "bddc_operator", "bddc_destroy",
            "bddc_last_error", "bddc_server_create", "bddc_submit", "bddc_wait",
            "bddc_server_destroy", "bddc_profile_apply", "bddc_apply_noalloc", "bddc_inspect",
-           "bddc_selftest_wait_timeout"]
+           "bddc_selftest_wait_timeout", "bddc_selftest_convert"]
 
 
 class Mesh(C.Structure):
@@ -45,7 +45,7 @@ class Opts(C.Structure):
 
 class SolveInfo(C.Structure):
     _fields_ = [("iters", C.c_int32), ("status", C.c_int32), ("kernel_launches", C.c_int32),
-                ("reserved", C.c_int32), ("relres", C.c_double),
+                ("batch_width", C.c_int32), ("relres", C.c_double),
                 ("relres_true", C.c_double), ("kappa_est", C.c_double),
                 ("lam_min", C.c_double), ("lam_max", C.c_double)]
 
@@ -94,6 +94,7 @@ def load():
     lib.bddc_profile_apply.argtypes = [vp, vp, i32, vp, i32, C.POINTER(C.c_int32)]
     lib.bddc_apply_noalloc.argtypes = [vp, vp, vp, vp]
     lib.bddc_selftest_wait_timeout.argtypes = [vp]
+    lib.bddc_selftest_convert.argtypes = [vp, C.c_int64, C.POINTER(C.c_int64), vp]
     lib.bddc_inspect.argtypes = [C.POINTER(Mesh), C.POINTER(Decomp), vp, vp, vp, vp, i32, vp]
     lib.bddc_server_destroy.argtypes = [vp]
     lib.bddc_server_destroy.restype = None
@@ -138,6 +139,15 @@ def inspect(nx, elem_to_sub, n_sub1):
                             ne.value, None))
     return {"n_corners": nc.value, "n_edges": ne.value, "edge_pairs": pairs[:ne.value],
             "edge_len": lens[:ne.value], "block_size": bs.value}
+
+
+def selftest_convert(values):
+    """Mismatches of the library's integer-operation binary64 <-> binary32
+    conversions against the hardware ones on a CUDA float64 tensor."""
+    out = C.c_int64()
+    _check(load().bddc_selftest_convert(_ptr(values.contiguous()), int(values.numel()),
+                                        C.byref(out), None))
+    return out.value
 
 
 class Problem:

@@ -13,34 +13,11 @@
 //  * in (10)-(11) the interior values of u_B cancel, so the interior of u is
 //    A_II^{-1} (r_I - A_{I Gamma} u_B,Gamma) and its interface is u_B.
 #include "internal.h"
-
-#include <cstdlib>
+#include "device_util.cuh"
 
 namespace bddc {
 
 namespace {
-
-template <class T> __device__ __forceinline__ float to_f(T v);
-template <> __device__ __forceinline__ float to_f<float>(float v) { return v; }
-template <> __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v) {
-    return __bfloat162float(v);
-}
-
-template <class T, class ACC> __device__ __forceinline__ ACC ld(const T *p) {
-    return static_cast<ACC>(to_f<T>(*p));
-}
-template <> __device__ __forceinline__ double ld<double, double>(const double *p) { return *p; }
-
-template <class T> struct Ops;
-template <> struct Ops<double> {
-    __host__ __device__ static const OpSet<double> &get(const DevLevel &L) { return L.f64; }
-};
-template <> struct Ops<float> {
-    __host__ __device__ static const OpSet<float> &get(const DevLevel &L) { return L.f32; }
-};
-template <> struct Ops<__nv_bfloat16> {
-    __host__ __device__ static const OpSet<__nv_bfloat16> &get(const DevLevel &L) { return L.b16; }
-};
 
 // Interior solve with the block factor of one substructure; x holds the
 // right-hand side on entry (m*b entries, padding zero) and the solution on
@@ -204,68 +181,6 @@ __global__ void k_post(DevLevel L, const double *r, double *z, const int *skip) 
 // Every wait on the mbarrier is bounded; on timeout the kernel flags *L.err,
 // waits (bounded) for its own copy and returns.
 // ----------------------------------------------------------------------------
-constexpr long kWaitPolls = 1L << 20;
-
-__device__ __forceinline__ unsigned smem_u32(const void *p) {
-    return (unsigned)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(unsigned long long *bar) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-// The one arrival of the barrier's phase, announcing `bytes` of copies.
-__device__ __forceinline__ void mbar_expect(unsigned long long *bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-                 ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-// One bulk copy global -> shared completing `bytes` on the barrier (no arrival).
-__device__ __forceinline__ void bulk_copy(void *dst, const void *src, unsigned bytes,
-                                          unsigned long long *bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes,
-                                          unsigned long long *bar) {
-    mbar_expect(bar, bytes);
-    bulk_copy(dst, src, bytes, bar);
-}
-__device__ __forceinline__ bool mbar_try(unsigned long long *bar, unsigned phase) {
-    unsigned ok;
-    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                 "selp.u32 %0, 1, 0, p;\n\t}\n"
-                 : "=r"(ok) : "r"(smem_u32(bar)), "r"(phase) : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned phase) {
-    for (long i = 0; i < kWaitPolls; ++i)
-        if (mbar_try(bar, phase)) return true;
-    return false;
-}
-// Wait for the phase of parity `phase` of the warp's barrier; false (after
-// flagging) if the wait gave up.
-__device__ __forceinline__ bool warp_wait_copy(unsigned long long *bar, int *err, int lane,
-                                               unsigned phase = 0) {
-    const bool ok = mbar_wait(bar, phase);
-    if (__all_sync(0xffffffffu, ok)) return true;
-    if (lane == 0 && err) atomicExch(err, 1);
-    mbar_wait(bar, phase);   // bounded: let the copy in flight land before the warp exits
-    return false;
-}
-
-__host__ __device__ constexpr size_t al16(size_t v) { return (v + 15) & ~size_t(15); }
-
-// Programmatic dependent launch.  The kernels of the apply and of the PCG
-// iteration are launched so that each may start while its predecessor in the
-// stream drains.  pdl_wait() returns once the predecessor grid has completed
-// and its writes are visible (at once for an ordinary launch), so a kernel
-// reads nothing another kernel of the iteration writes before it, and every
-// thread calls it before it exits; only setup-time data (factors, records) is
-// read earlier.  pdl_trigger() lets the successor be scheduled.
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_trigger() {
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
-
 // Warp sum of r.z partials of the level-1 post-correction; the last warp of
 // the launch to finish adds the per-substructure partials in a fixed order.
 __device__ __forceinline__ void finish_rz(double tot, PcgScalars *sc, double *betas) {
@@ -1216,32 +1131,6 @@ int num_sms() {
         if (n <= 0) n = 152;
     }
     return n;
-}
-
-// Launch with programmatic stream serialisation (see pdl_wait); setting the
-// environment variable BDDC_PDL=0 launches in plain stream order instead.
-bool pdl_enabled() {
-    static const bool on = [] {
-        const char *e = std::getenv("BDDC_PDL");
-        return !(e && e[0] == '0');
-    }();
-    return on;
-}
-
-template <class... KArgs, class... Args>
-void launch_pdl(void (*k)(KArgs...), int grid, int block, size_t smem, cudaStream_t s,
-                Args... args) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)grid);
-    cfg.blockDim = dim3((unsigned)block);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = pdl_enabled() ? 1 : 0;
-    cudaLaunchKernelEx(&cfg, k, args...);
 }
 
 // Warps (substructures) per block: as many as needed for one wave over the

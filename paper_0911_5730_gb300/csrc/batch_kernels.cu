@@ -1,0 +1,997 @@
+// batch_kernels.cu - Algorithm 1 (eqs. 4-11) and the PCG recurrences for a
+// batch of K <= 32 right-hand sides solved in lockstep.
+//
+// Every global vector of the batch is stored interleaved, entry (g, k) at
+// g * K + k, so that the K values of one DOF are contiguous.  The operator
+// blocks of a substructure are staged once in shared memory and used for all
+// K right-hand sides, so operator bytes are read once per batch instead of
+// once per right-hand side.  The Dirichlet kernel gives a block of four warps
+// to one substructure (eight right-hand sides per warp, four lanes per
+// right-hand side); the substructure-correction and averaging kernels give a
+// warp to a substructure and a lane to a right-hand side.
+//
+// The PCG scalars are per right-hand side; a right-hand side that has
+// converged keeps its state while the others iterate.
+#include "internal.h"
+#include "device_util.cuh"
+
+#include <type_traits>
+
+namespace bddc {
+
+namespace {
+
+constexpr int kChunksB = 4;   // bulk copies per factor
+
+// N consecutive storage elements (N * sizeof(T) bytes aligned) into accumulators.
+template <class T, class ACC, int N>
+__device__ __forceinline__ void load_vec(const T *src, ACC (&v)[N]) {
+    if constexpr (std::is_same<T, double>::value) {
+#pragma unroll
+        for (int i = 0; i < N / 2; ++i) {
+            const double2 q = reinterpret_cast<const double2 *>(src)[i];
+            v[2 * i] = q.x; v[2 * i + 1] = q.y;
+        }
+    } else if constexpr (std::is_same<T, float>::value) {
+        if constexpr (N == 2) {
+            const float2 q = *reinterpret_cast<const float2 *>(src);
+            v[0] = q.x; v[1] = q.y;
+        } else {
+#pragma unroll
+            for (int i = 0; i < N / 4; ++i) {
+                const float4 q = reinterpret_cast<const float4 *>(src)[i];
+                v[4 * i] = q.x; v[4 * i + 1] = q.y; v[4 * i + 2] = q.z; v[4 * i + 3] = q.w;
+            }
+        }
+    } else {
+        unsigned u[N / 2];
+        if constexpr (N == 2) {
+            u[0] = *reinterpret_cast<const unsigned *>(src);
+        } else if constexpr (N == 4) {
+            const uint2 q = *reinterpret_cast<const uint2 *>(src);
+            u[0] = q.x; u[1] = q.y;
+        } else {
+#pragma unroll
+            for (int i = 0; i < N / 8; ++i) {
+                const uint4 q = reinterpret_cast<const uint4 *>(src)[i];
+                u[4 * i] = q.x; u[4 * i + 1] = q.y; u[4 * i + 2] = q.z; u[4 * i + 3] = q.w;
+            }
+        }
+#pragma unroll
+        for (int h = 0; h < N / 2; ++h) {
+            v[2 * h] = __uint_as_float(u[h] << 16);
+            v[2 * h + 1] = __uint_as_float(u[h] & 0xffff0000u);
+        }
+    }
+}
+
+// The batched Dirichlet kernel gives one block of kDW warps to one
+// substructure.  Warp w takes right-hand sides 8w .. 8w+7; lane 4g + h holds
+// rows h*RPL .. h*RPL + RPL - 1 (RPL = BP / 4) of every block of right-hand
+// side 8w + g.  The blocks' warps only meet at the gathers and the coupling
+// terms; the sweeps run without block barriers.
+constexpr int kDW = 4;
+
+template <class T, class ACC, int BP> struct DirSmemB {
+    static size_t bytes(const DevLevel &L) {
+        return al16(sizeof(T) * (size_t)L.max_fac) + al16(sizeof(ACC) * (size_t)L.max_m * BP * 32) +
+               al16(sizeof(ACC) * (size_t)(L.max_nG > 0 ? L.max_nG : 1) * 32) + al16((size_t)L.max_irec) +
+               al16(sizeof(ACC) * (size_t)(L.max_coo > 0 ? L.max_coo : 1)) + 8 * (kChunksB + 1) + 16;
+    }
+};
+
+// (4)-(5) [pre] or (10)-(11) [post] for K right-hand sides.  Block factor
+// storage as in the single right-hand-side kernel: per block j, [Linv_j |
+// L_{j,j-1}] of BP x BP each, element (r, c) at c * BP + (r ^ c), Linv_j lower
+// triangular (zeros stored above the diagonal).
+template <class T, class ACC, int BP, bool POST>
+__global__ void __launch_bounds__(32 * kDW) k_dir_b(DevLevel L, BatchLevel B, const double *r, double *z,
+                                                    const int *skip) {
+    constexpr int BB = BP * BP, RPL = BP / 4;
+    extern __shared__ __align__(16) unsigned char smem_b[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int sub = blockIdx.x;
+    const int K = B.K;
+    const bool act = lane < K;
+    unsigned char *p = smem_b;
+    T *fac = reinterpret_cast<T *>(p);      p += al16(sizeof(T) * (size_t)L.max_fac);
+    ACC *xs = reinterpret_cast<ACC *>(p);   p += al16(sizeof(ACC) * (size_t)L.max_m * BP * 32);
+    ACC *vG = reinterpret_cast<ACC *>(p);   p += al16(sizeof(ACC) * (size_t)(L.max_nG > 0 ? L.max_nG : 1) * 32);
+    unsigned char *rec = p;                 p += al16((size_t)L.max_irec);
+    ACC *cvs = reinterpret_cast<ACC *>(p);  p += al16(sizeof(ACC) * (size_t)(L.max_coo > 0 ? L.max_coo : 1));
+    unsigned long long *bars = reinterpret_cast<unsigned long long *>(p);   // kChunksB factor + 1 record
+
+    const int nI = L.nI[sub], nG = L.nG[sub], m = L.nblk[sub];
+    const int ncoo = L.ncoo[sub], nown = L.nown[sub];
+    const T *F = Ops<T>::get(L).dir + L.offF[sub];
+    const int nch = m < kChunksB ? m : kChunksB;
+    const IRecLayout lay(nI, nG, ncoo, nown);
+    if (tid == 0) {
+        for (int c = 0; c < nch; ++c) mbar_init(&bars[c]);
+        mbar_init(&bars[kChunksB]);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        // the index record first: the gathers wait for it, the sweeps for the factor
+        mbar_expect(&bars[kChunksB], (unsigned)lay.bytes);
+        bulk_copy(rec, L.irec + L.irecOff[sub], (unsigned)lay.bytes, &bars[kChunksB]);
+        for (int c = 0; c < nch; ++c) {
+            const int b0 = c * m / nch, b1 = (c + 1) * m / nch;
+            const unsigned bytes = (unsigned)((size_t)(b1 - b0) * 2 * BB * sizeof(T));
+            mbar_expect(&bars[c], bytes);
+            bulk_copy(fac + (size_t)b0 * 2 * BB, F + (size_t)b0 * 2 * BB, bytes, &bars[c]);
+        }
+    }
+    const int *gI = reinterpret_cast<const int *>(rec + lay.iI);
+    const int *gGi = reinterpret_cast<const int *>(rec + lay.iG);
+    const int *gP = reinterpret_cast<const int *>(rec + lay.pr);
+    const double *gC = reinterpret_cast<const double *>(rec + lay.cv);
+    const int *gO = reinterpret_cast<const int *>(rec + lay.ow);
+    pdl_wait();
+    pdl_trigger();
+    auto drain = [&](int from) {   // bounded: copies in flight land before the block exits
+        if (tid == 0) {
+            for (int c = from; c < nch; ++c) mbar_wait(&bars[c], 0);
+            mbar_wait(&bars[kChunksB], 0);
+        }
+    };
+    if (skip && *skip) { drain(0); return; }
+    const bool rec_ok = mbar_wait(&bars[kChunksB], 0);
+    if (!__syncthreads_and(rec_ok)) {
+        if (tid == 0) atomicExch(L.err, 1);
+        drain(0);
+        return;
+    }
+    // right-hand sides (lane = right-hand side), sixteen row loads in flight per warp
+    constexpr int kG = 16;
+    for (int i0 = warp * kG; i0 < m * BP; i0 += kDW * kG) {
+        double v[kG];
+#pragma unroll
+        for (int u = 0; u < kG; ++u) {
+            const int i = i0 + u;
+            v[u] = (i < nI && act) ? r[(int64_t)gI[i] * K + lane] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kG; ++u)
+            if (i0 + u < m * BP) xs[(i0 + u) * 32 + lane] = from_f64<ACC>(v[u]);
+    }
+    for (int e = tid; e < ncoo; e += 32 * kDW) cvs[e] = from_f64<ACC>(gC[e]);
+    if (POST) {
+        for (int q0 = warp * kG; q0 < nG; q0 += kDW * kG) {
+            double v[kG];
+#pragma unroll
+            for (int u = 0; u < kG; ++u)
+                v[u] = (q0 + u < nG && act) ? B.uB[(int64_t)gGi[q0 + u] * K + lane] : 0.0;
+#pragma unroll
+            for (int u = 0; u < kG; ++u)
+                if (q0 + u < nG) vG[(q0 + u) * 32 + lane] = from_f64<ACC>(v[u]);
+        }
+        __syncthreads();
+        // interior right-hand side r_I - A_{I Gamma} u_B; warp w applies, in
+        // entry order, the entries of the interior rows il = w (mod kDW), so
+        // the sums do not depend on scheduling
+        for (int e = 0; e < ncoo; ++e) {
+            const int pr = gP[e];
+            if (((pr & 0xffff) & (kDW - 1)) != warp) continue;
+            xs[(pr & 0xffff) * 32 + lane] -= cvs[e] * vG[(pr >> 16) * 32 + lane];
+        }
+    } else {
+        for (int q = warp; q < nG; q += kDW) {
+            vG[q * 32 + lane] = 0;
+            if (act) B.uB[(int64_t)gGi[q] * K + lane] = 0.0;   // consumed by the previous post-correction
+        }
+    }
+    __syncthreads();
+
+    const int g = lane >> 2, h = lane & 3;
+    const int kc = warp * 8 + g;           // column of xs: the right-hand side of this lane
+    const int rb = h * RPL;                // first row of this lane within a block
+    const int src0 = lane & ~3;            // lane holding rows 0 .. RPL-1 of the same right-hand side
+    int cw = 0;
+    bool ok = true;
+    ACC xp[RPL];
+#pragma unroll
+    for (int q = 0; q < RPL; ++q) xp[q] = 0;
+    for (int j = 0; j < m; ++j) {
+        while (cw < nch && cw * m / nch <= j) {
+            if (!mbar_wait(&bars[cw], 0)) { ok = false; break; }
+            ++cw;
+        }
+        if (!ok) break;
+        const T *Li = fac + (size_t)j * 2 * BB;
+        const T *Ls = Li + BB;
+        ACC t[RPL];
+#pragma unroll
+        for (int q = 0; q < RPL; ++q) t[q] = xs[(j * BP + rb + q) * 32 + kc];
+        if (j > 0) {
+            // t -= L_{j,j-1} x_{j-1}: the whole x_{j-1} of this right-hand side by shuffles
+            ACC xf[BP];
+#pragma unroll
+            for (int c = 0; c < BP; ++c) xf[c] = __shfl_sync(0xffffffffu, xp[c % RPL], src0 | (c / RPL));
+#pragma unroll
+            for (int c = 0; c < BP; ++c) {
+                ACC cv[RPL];
+                load_vec<T, ACC, RPL>(Ls + c * BP + (rb ^ (c & ~(RPL - 1))), cv);
+#pragma unroll
+                for (int q = 0; q < RPL; ++q) t[q ^ (c & (RPL - 1))] -= cv[q] * xf[c];
+            }
+        }
+        ACC tf[BP];
+#pragma unroll
+        for (int c = 0; c < BP; ++c) tf[c] = __shfl_sync(0xffffffffu, t[c % RPL], src0 | (c / RPL));
+#pragma unroll
+        for (int q = 0; q < RPL; ++q) xp[q] = 0;
+#pragma unroll
+        for (int c = 0; c < BP; ++c) {
+            ACC cv[RPL];
+            load_vec<T, ACC, RPL>(Li + c * BP + (rb ^ (c & ~(RPL - 1))), cv);
+#pragma unroll
+            for (int q = 0; q < RPL; ++q) xp[q ^ (c & (RPL - 1))] += cv[q] * tf[c];
+        }
+#pragma unroll
+        for (int q = 0; q < RPL; ++q) xs[(j * BP + rb + q) * 32 + kc] = xp[q];
+    }
+    if (ok) {
+        // backward sweep: z_j = Linv_j^T (y_j - L_{j+1,j}^T z_{j+1}).  Each lane
+        // forms the column partials of its own rows for all BP output rows and
+        // the four lanes of a right-hand side reduce-scatter them.
+        const bool hiA = (h & 2) != 0, hiB = (h & 1) != 0;
+        auto reduce_scatter = [&](ACC (&part)[BP], ACC (&out)[RPL]) {
+            ACC half[BP / 2];
+#pragma unroll
+            for (int i = 0; i < BP / 2; ++i) {
+                const ACC send = hiA ? part[i] : part[BP / 2 + i];
+                const ACC keep = hiA ? part[BP / 2 + i] : part[i];
+                half[i] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+            }
+#pragma unroll
+            for (int i = 0; i < RPL; ++i) {
+                const ACC send = hiB ? half[i] : half[RPL + i];
+                const ACC keep = hiB ? half[RPL + i] : half[i];
+                out[i] = keep + __shfl_xor_sync(0xffffffffu, send, 1);
+            }
+        };
+        ACC zn[RPL];
+#pragma unroll
+        for (int q = 0; q < RPL; ++q) zn[q] = 0;
+        for (int j = m - 1; j >= 0; --j) {
+            const T *Li = fac + (size_t)j * 2 * BB;
+            ACC t[RPL];
+#pragma unroll
+            for (int q = 0; q < RPL; ++q) t[q] = xs[(j * BP + rb + q) * 32 + kc];
+            if (j < m - 1) {
+                const T *Ls1 = fac + (size_t)(j + 1) * 2 * BB + BB;
+                ACC part[BP];
+#pragma unroll
+                for (int rr = 0; rr < BP; ++rr) {
+                    // L_{j+1,j}(c, rr) for this lane's c = rb + q' at rr * BP + (c ^ rr)
+                    ACC v[RPL];
+                    load_vec<T, ACC, RPL>(Ls1 + rr * BP + (rb ^ (rr & ~(RPL - 1))), v);
+                    ACC a = 0;
+#pragma unroll
+                    for (int q = 0; q < RPL; ++q) a += v[q] * zn[q ^ (rr & (RPL - 1))];
+                    part[rr] = a;
+                }
+                ACC red[RPL];
+                reduce_scatter(part, red);
+#pragma unroll
+                for (int q = 0; q < RPL; ++q) t[q] -= red[q];
+            }
+            ACC part[BP];
+#pragma unroll
+            for (int rr = 0; rr < BP; ++rr) {
+                ACC v[RPL];
+                load_vec<T, ACC, RPL>(Li + rr * BP + (rb ^ (rr & ~(RPL - 1))), v);
+                ACC a = 0;
+#pragma unroll
+                for (int q = 0; q < RPL; ++q) a += v[q] * t[q ^ (rr & (RPL - 1))];
+                part[rr] = a;
+            }
+            reduce_scatter(part, zn);
+#pragma unroll
+            for (int q = 0; q < RPL; ++q) xs[(j * BP + rb + q) * 32 + kc] = zn[q];
+        }
+    }
+    if (!__syncthreads_and(ok)) {
+        if (tid == 0) atomicExch(L.err, 1);
+        drain(0);
+        return;
+    }
+    if (!POST) {
+        // A_{Gamma I} u_I into vG (warp w: the rows gl = w (mod kDW), entry
+        // order), then r_B -= it on Gamma
+        for (int e = 0; e < ncoo; ++e) {
+            const int pr = gP[e];
+            if (((pr >> 16) & (kDW - 1)) != warp) continue;
+            vG[(pr >> 16) * 32 + lane] += cvs[e] * xs[(pr & 0xffff) * 32 + lane];
+        }
+        __syncthreads();
+        if (act) {
+            for (int q = warp; q < nG; q += kDW) {
+                const ACC v = vG[q * 32 + lane];
+                if (v != (ACC)0) atomicAdd(&B.rB[(int64_t)gGi[q] * K + lane], -to_f64(v));
+            }
+        }
+    } else if (act) {
+        for (int i = warp; i < nI; i += kDW) z[(int64_t)gI[i] * K + lane] = to_f64(xs[i * 32 + lane]);
+        for (int e = warp; e < nown; e += kDW) {
+            const int owp = gO[2 * e], owd = gO[2 * e + 1];
+            z[(int64_t)owd * K + lane] = to_f64(vG[owp * 32 + lane]);
+        }
+    }
+}
+
+// (6)-(8) for K right-hand sides: f = D_i r_B on Gamma, w = N_i f,
+// r_c += Psi_i^T f.
+template <class T, class ACC>
+__global__ void k_neu_b(DevLevel L, BatchLevel B, int pidx, const double *r, const int *skip,
+                        unsigned slice) {
+    extern __shared__ __align__(16) unsigned char smem_b[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int sub = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (sub >= L.nsub) { pdl_wait(); return; }
+    const int K = B.K;
+    const bool act = lane < K;
+    unsigned char *p = smem_b + (size_t)warp * slice;
+    unsigned char *rec = p;                  p += al16((size_t)L.max_nrec[pidx]);
+    ACC *f = reinterpret_cast<ACC *>(p);     p += al16(sizeof(ACC) * (size_t)(L.max_nG > 0 ? L.max_nG : 1) * 32);
+    unsigned long long *bar = reinterpret_cast<unsigned long long *>(p);
+    const int nG = L.nG[sub], nc = L.ncl[sub];
+    const NRecLayout lay(nG, nc, (int)sizeof(T));
+    if (lane == 0) mbar_init(bar);
+    __syncwarp();
+    if (lane == 0 && lay.bytes) {
+        mbar_expect(bar, (unsigned)lay.bytes);
+        bulk_copy(rec, L.nrec[pidx] + L.nrecOff[pidx][sub], (unsigned)lay.bytes, bar);
+    }
+    pdl_wait();
+    pdl_trigger();
+    if (skip && *skip) {
+        if (lay.bytes) mbar_wait(bar, 0);   // bounded: the copy lands first
+        return;
+    }
+    if (lay.bytes && !warp_wait_copy(bar, L.err, lane)) return;
+    const T *Ps = reinterpret_cast<const T *>(rec + lay.psi);
+    const T *wg = reinterpret_cast<const T *>(rec + lay.wg);
+    const int *iG = reinterpret_cast<const int *>(rec + lay.iG);
+    const int *rcs = reinterpret_cast<const int *>(rec + lay.rc);
+    const int *gG = reinterpret_cast<const int *>(rec + lay.gG);
+    const T *Ns = reinterpret_cast<const T *>(rec + lay.N);
+    for (int q0 = 0; q0 < nG; q0 += 16) {
+        double v[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int q = q0 + u;
+            v[u] = (q < nG && act) ? r[(int64_t)gG[q] * K + lane] + B.rB[(int64_t)iG[q] * K + lane] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 16; ++u)
+            if (q0 + u < nG) f[(q0 + u) * 32 + lane] = ld<T, ACC>(wg + q0 + u) * from_f64<ACC>(v[u]);
+    }
+    const int64_t g0 = L.offG[sub];
+    // w = N f, four output rows at a time (each f entry read once per four rows)
+    for (int q0 = 0; q0 < nG; q0 += 4) {
+        ACC s[4] = {0, 0, 0, 0};
+        const int nq = nG - q0 < 4 ? nG - q0 : 4;
+        for (int pp = 0; pp < nG; ++pp) {
+            const ACC fv = f[pp * 32 + lane];
+            const T *Nr = Ns + (size_t)pp * nG + q0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (u < nq) s[u] += ld<T, ACC>(Nr + u) * fv;
+        }
+        if (act)
+            for (int u = 0; u < nq; ++u) B.w[(g0 + q0 + u) * K + lane] = to_f64(s[u]);
+    }
+    for (int k0 = 0; k0 < nc; k0 += 4) {
+        ACC s[4] = {0, 0, 0, 0};
+        const int nk = nc - k0 < 4 ? nc - k0 : 4;
+        for (int q = 0; q < nG; ++q) {
+            const ACC fv = f[q * 32 + lane];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (u < nk) s[u] += ld<T, ACC>(Ps + (size_t)(k0 + u) * nG + q) * fv;
+        }
+        if (act)
+            for (int u = 0; u < nk; ++u) atomicAdd(&B.rcv[(int64_t)rcs[k0 + u] * K + lane], to_f64(s[u]));
+    }
+}
+
+// (9) for K right-hand sides: u_B += D_i (w_i + Psi_i u_c) on Gamma; clears
+// the r_B and r_c entries it consumed.
+template <class T, class ACC>
+__global__ void k_avg_b(DevLevel L, BatchLevel B, int pidx, const int *skip, unsigned slice) {
+    extern __shared__ __align__(16) unsigned char smem_b[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int sub = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (sub >= L.nsub) { pdl_wait(); return; }
+    const int K = B.K;
+    const bool act = lane < K;
+    unsigned char *p = smem_b + (size_t)warp * slice;
+    unsigned char *rec = p;                  p += al16((size_t)L.max_nrec[pidx]);
+    ACC *uc = reinterpret_cast<ACC *>(p);    p += al16(sizeof(ACC) * (size_t)(L.max_nc > 0 ? L.max_nc : 1) * 32);
+    unsigned long long *bar = reinterpret_cast<unsigned long long *>(p);
+    const int nG = L.nG[sub], nc = L.ncl[sub];
+    const NRecLayout lay(nG, nc, (int)sizeof(T));
+    if (lane == 0) mbar_init(bar);
+    __syncwarp();
+    if (lane == 0 && lay.avg_bytes) {
+        mbar_expect(bar, (unsigned)lay.avg_bytes);
+        bulk_copy(rec, L.nrec[pidx] + L.nrecOff[pidx][sub], (unsigned)lay.avg_bytes, bar);
+    }
+    pdl_wait();
+    pdl_trigger();
+    if (skip && *skip) {
+        if (lay.avg_bytes) mbar_wait(bar, 0);   // bounded: the copy lands first
+        return;
+    }
+    if (lay.avg_bytes && !warp_wait_copy(bar, L.err, lane)) return;
+    const T *Ps = reinterpret_cast<const T *>(rec + lay.psi);
+    const T *wg = reinterpret_cast<const T *>(rec + lay.wg);
+    const int *iG = reinterpret_cast<const int *>(rec + lay.iG);
+    const int *rcs = reinterpret_cast<const int *>(rec + lay.rc);
+    for (int k = 0; k < nc; ++k) uc[k * 32 + lane] = act ? from_f64<ACC>(B.ucv[(int64_t)rcs[k] * K + lane]) : (ACC)0;
+    const int64_t g0 = L.offG[sub];
+    for (int q0 = 0; q0 < nG; q0 += 4) {
+        const int nq = nG - q0 < 4 ? nG - q0 : 4;
+        ACC v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = (act && u < nq) ? from_f64<ACC>(B.w[(g0 + q0 + u) * K + lane]) : (ACC)0;
+        for (int k = 0; k < nc; ++k) {
+            const ACC ucv = uc[k * 32 + lane];
+            const T *Pr = Ps + (size_t)k * nG + q0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (u < nq) v[u] += ld<T, ACC>(Pr + u) * ucv;
+        }
+        if (act) {
+            for (int u = 0; u < nq; ++u) {
+                const int64_t e = (int64_t)iG[q0 + u] * K + lane;
+                atomicAdd(&B.uB[e], to_f64(ld<T, ACC>(wg + q0 + u) * v[u]));
+                B.rB[e] = 0.0;            // consumed by the substructure correction
+            }
+        }
+    }
+    if (act)
+        for (int k = 0; k < nc; ++k) B.rcv[(int64_t)rcs[k] * K + lane] = 0.0;   // consumed by the coarse solve
+}
+
+// Y = A X, A dense n x n row-major (leading dimension ld, a multiple of 4,
+// zero padded), X and Y interleaved [ld][K] (X zero on rows [n, ld)).  FP64;
+// the FP64 pipe bounds it.  A block owns GM_R rows; the columns stream in
+// chunks of GM_C through a GM_S-stage ring of bulk copies (the GM_R row
+// segments of A and the GM_C x K block of X, contiguous in the interleaved
+// layout), thread 0 refilling a stage once all warps have used it.  Warp w
+// computes rows 2w, 2w + 1 for all K columns (lane k: column k), reading the
+// A entries by broadcast.
+constexpr int GM_R = 16, GM_C = 64, GM_S = 3;
+constexpr size_t GM_STAGE = (size_t)GM_R * GM_C * 8 + (size_t)GM_C * 32 * 8;
+
+__global__ void __launch_bounds__(256) k_gemm_b(int n, int ld, const double *A, const double *X,
+                                                double *Y, int K, const int *skip, int *err) {
+    extern __shared__ __align__(16) unsigned char smem_g[];
+    __shared__ __align__(8) unsigned long long full[GM_S];
+    __shared__ int ok_all;
+    pdl_wait();
+    pdl_trigger();
+    if (skip && *skip) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int row0 = blockIdx.x * GM_R;
+    const int nrow = n - row0 < GM_R ? n - row0 : GM_R;
+    const int nchunk = (ld + GM_C - 1) / GM_C;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < GM_S; ++s) mbar_init(&full[s]);
+        ok_all = 1;
+    }
+    __syncthreads();
+    auto issue = [&](int c) {   // thread 0: chunk c into stage c % GM_S
+        unsigned char *st = smem_g + (size_t)(c % GM_S) * GM_STAGE;
+        const int c0 = c * GM_C;
+        const int w = ld - c0 < GM_C ? ld - c0 : GM_C;
+        const unsigned abytes = (unsigned)(w * 8), xbytes = (unsigned)((size_t)w * K * 8);
+        mbar_expect(&full[c % GM_S], abytes * nrow + xbytes);
+        for (int r = 0; r < nrow; ++r)
+            bulk_copy(st + (size_t)r * GM_C * 8, A + (int64_t)(row0 + r) * ld + c0, abytes, &full[c % GM_S]);
+        bulk_copy(st + (size_t)GM_R * GM_C * 8, X + (int64_t)c0 * K, xbytes, &full[c % GM_S]);
+    };
+    if (threadIdx.x == 0)
+        for (int c = 0; c < GM_S && c < nchunk; ++c) issue(c);
+    const int r0 = 2 * warp, r1 = r0 + 1;
+    double s0 = 0.0, s1 = 0.0, t0 = 0.0, t1 = 0.0;
+    for (int c = 0; c < nchunk; ++c) {
+        const unsigned phase = (unsigned)((c / GM_S) & 1);
+        if (!mbar_wait(&full[c % GM_S], phase)) {
+            if (lane == 0) { atomicExch(err, 1); ok_all = 0; }
+        }
+        __syncthreads();
+        if (!ok_all) break;
+        const unsigned char *st = smem_g + (size_t)(c % GM_S) * GM_STAGE;
+        const double *As = reinterpret_cast<const double *>(st);
+        const double *Xs = reinterpret_cast<const double *>(st + (size_t)GM_R * GM_C * 8);
+        const int w = ld - c * GM_C < GM_C ? ld - c * GM_C : GM_C;
+        if (r0 < nrow) {
+            const double *a0 = As + r0 * GM_C, *a1 = As + r1 * GM_C;
+            int i = 0;
+            for (; i + 1 < w; i += 2) {
+                const double x0 = lane < K ? Xs[i * K + lane] : 0.0;
+                const double x1 = lane < K ? Xs[(i + 1) * K + lane] : 0.0;
+                s0 = fma(a0[i], x0, s0); s1 = fma(a1[i], x0, s1);
+                t0 = fma(a0[i + 1], x1, t0); t1 = fma(a1[i + 1], x1, t1);
+            }
+            for (; i < w; ++i) {
+                const double x0 = lane < K ? Xs[i * K + lane] : 0.0;
+                s0 = fma(a0[i], x0, s0); s1 = fma(a1[i], x0, s1);
+            }
+        }
+        __syncthreads();                                   // every warp is done with the stage
+        if (threadIdx.x == 0 && c + GM_S < nchunk) issue(c + GM_S);
+    }
+    if (!ok_all) {
+        // bounded: let the copies still in flight land before the block exits
+        if (threadIdx.x == 0)
+            for (int s = 0; s < GM_S; ++s) mbar_wait(&full[s], 0), mbar_wait(&full[s], 1);
+        return;
+    }
+    if (lane < K) {
+        if (r0 < nrow) Y[(int64_t)(row0 + r0) * K + lane] = s0 + t0;
+        if (r1 < nrow) Y[(int64_t)(row0 + r1) * K + lane] = s1 + t1;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// PCG for K right-hand sides (FP64).  Blocks have K * floor(256 / K) threads
+// and the grid stride is a multiple of K, so a thread always serves the same
+// right-hand side k = threadIdx.x % K.
+// ---------------------------------------------------------------------------
+constexpr int kRB = 256;
+
+__host__ __device__ inline int bblock(int K) { return K * (kRB / K); }
+
+// Sum of v over the threads of each right-hand side and over the grid; the
+// last block to finish calls fin(k, total) for every k < K (deterministic:
+// fixed partition and order), then post() once.
+template <class Fin, class Post>
+__device__ void grid_reduce_k(double v, int K, double *part, unsigned *counter, Fin fin, Post post) {
+    __shared__ double red[kRB];
+    __shared__ bool last;
+    const int per = blockDim.x / K;     // threads per right-hand side in a block
+    red[threadIdx.x] = v;
+    __syncthreads();
+    if (threadIdx.x < K) {
+        double s = 0.0;
+        for (int t = 0; t < per; ++t) s += red[t * K + threadIdx.x];
+        part[(int64_t)blockIdx.x * K + threadIdx.x] = s;
+        __threadfence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    // thread t sums blocks b = t / K, t / K + per, ... of right-hand side t % K
+    double s = 0.0;
+    if ((int)threadIdx.x < per * K)
+        for (unsigned b = threadIdx.x / K; b < gridDim.x; b += per)
+            s += __ldcg(&part[(int64_t)b * K + threadIdx.x % K]);
+    red[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x < K) {
+        double tot = 0.0;
+        for (int t = 0; t < per; ++t) tot += red[t * K + threadIdx.x];
+        fin(threadIdx.x, tot);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        post();
+        *counter = 0u;
+    }
+}
+
+struct NoPost { __device__ void operator()() const {} };
+
+__global__ void k_b_init(int n, int K, const double *b, int64_t ldb, double *x, double *r, double *p,
+                         double *part, unsigned *counter, BatchScalars *sc, double tol, int maxit) {
+    pdl_wait();
+    pdl_trigger();
+    const int k = threadIdx.x % K;
+    const int64_t nK = (int64_t)n * K;
+    double s = 0.0;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nK; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t g = e / K;
+        const double bv = b[(int64_t)k * ldb + g];
+        x[e] = 0.0;
+        r[e] = bv;
+        p[e] = 0.0;
+        s = fma(bv, bv, s);
+    }
+    grid_reduce_k(s, K, part, counter,
+        [&](int kk, double tot) {
+            sc->bb[kk] = tot; sc->rr[kk] = tot; sc->tol2[kk] = tol * tol * tot;
+            sc->it[kk] = 0; sc->fresh[kk] = 1; sc->beta[kk] = 0.0;
+            sc->conv[kk] = tot == 0.0 ? 1 : 0;
+            sc->done[kk] = tot == 0.0 ? 1 : 0;
+        },
+        [&]() {
+            sc->K = K; sc->maxit = maxit;
+            int all = 1;
+            for (int kk = 0; kk < K; ++kk) all &= sc->done[kk];
+            sc->all_done = all;
+        });
+}
+
+// p = z + beta p for the right-hand sides still iterating
+__global__ void k_b_dir(int64_t nK, int K, const double *__restrict__ z, double *__restrict__ p,
+                        const BatchScalars *sc) {
+    pdl_wait();
+    pdl_trigger();
+    if (sc->all_done) return;
+    const int k = threadIdx.x % K;
+    if (sc->done[k]) return;
+    const double bt = sc->beta[k];
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nK; e += (int64_t)gridDim.x * blockDim.x)
+        p[e] = fma(bt, p[e], z[e]);
+}
+
+// q = A p (matrix-free Q1 stencil), pq_k, alpha_k = rho_k / pq_k
+__global__ void k_b_spmv_dot(int nx, int K, const double *__restrict__ w, const double *__restrict__ p,
+                             double *__restrict__ q, double *part, unsigned *counter, BatchScalars *sc,
+                             double *alphas) {
+    pdl_wait();
+    pdl_trigger();
+    if (sc->all_done) return;
+    const int k = threadIdx.x % K;
+    const int n1 = nx - 1;
+    const int n = n1 * n1;
+    const int64_t nK = (int64_t)n * K;
+    double s = 0.0;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nK; e += (int64_t)gridDim.x * blockDim.x) {
+        const int g = (int)(e / K);
+        const int jj = g / n1, ii = g - jj * n1;
+        const bool W = ii > 0, E = ii < n1 - 1, S = jj > 0, N = jj < n1 - 1;
+        auto P = [&](int gg) { return p[(int64_t)gg * K + k]; };
+        const double pc = P(g);
+        double v = w[g] * pc;
+        if (E) v = fma(w[n + g], P(g + 1), v);
+        if (N) v = fma(w[2 * n + g], P(g + n1), v);
+        if (N && E) v = fma(w[3 * n + g], P(g + n1 + 1), v);
+        if (N && W) v = fma(w[4 * n + g], P(g + n1 - 1), v);
+        if (W) v = fma(w[n + g - 1], P(g - 1), v);
+        if (S) v = fma(w[2 * n + g - n1], P(g - n1), v);
+        if (S && W) v = fma(w[3 * n + g - n1 - 1], P(g - n1 - 1), v);
+        if (S && E) v = fma(w[4 * n + g - n1 + 1], P(g - n1 + 1), v);
+        q[e] = v;
+        s = fma(v, pc, s);
+    }
+    grid_reduce_k(s, K, part, counter,
+        [&](int kk, double tot) {
+            if (sc->done[kk]) return;
+            sc->pq[kk] = tot;
+            sc->alpha[kk] = sc->rho[kk] / tot;
+            alphas[(int64_t)sc->it[kk] * K + kk] = sc->alpha[kk];
+        }, NoPost{});
+}
+
+// x += alpha p; r -= alpha q; rr_k; convergence; it_k += 1
+__global__ void k_b_update(int64_t nK, int K, double *__restrict__ x, double *__restrict__ r,
+                           const double *__restrict__ p, const double *__restrict__ q, double *part,
+                           unsigned *counter, BatchScalars *sc) {
+    pdl_wait();
+    pdl_trigger();
+    if (sc->all_done) return;
+    const int k = threadIdx.x % K;
+    const bool live = !sc->done[k];
+    const double a = sc->alpha[k];
+    double s = 0.0;
+    if (live) {
+        for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nK; e += (int64_t)gridDim.x * blockDim.x) {
+            x[e] = fma(a, p[e], x[e]);
+            const double ri = fma(-a, q[e], r[e]);
+            r[e] = ri;
+            s = fma(ri, ri, s);
+        }
+    }
+    grid_reduce_k(s, K, part, counter,
+        [&](int kk, double tot) {
+            if (sc->done[kk]) return;
+            sc->rr[kk] = tot;
+            sc->it[kk] += 1;
+            if (tot <= sc->tol2[kk]) { sc->conv[kk] = 1; sc->done[kk] = 1; }
+            if (sc->it[kk] >= sc->maxit) sc->done[kk] = 1;
+        },
+        [&]() {
+            int all = 1;
+            for (int kk = 0; kk < K; ++kk) all &= sc->done[kk];
+            sc->all_done = all;
+        });
+}
+
+// rho_k = r.z, beta_k (0 on a fresh start)
+__global__ void k_b_rz(int64_t nK, int K, const double *__restrict__ r, const double *__restrict__ z,
+                       double *part, unsigned *counter, BatchScalars *sc, double *betas) {
+    pdl_wait();
+    pdl_trigger();
+    if (sc->all_done) return;
+    const int k = threadIdx.x % K;
+    double s = 0.0;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nK; e += (int64_t)gridDim.x * blockDim.x)
+        s = fma(r[e], z[e], s);
+    grid_reduce_k(s, K, part, counter,
+        [&](int kk, double tot) {
+            if (sc->done[kk]) return;
+            const double beta = sc->fresh[kk] ? 0.0 : tot / sc->rho[kk];
+            sc->fresh[kk] = 0;
+            sc->beta[kk] = beta;
+            if (sc->it[kk] > 0) betas[(int64_t)(sc->it[kk] - 1) * K + kk] = beta;
+            sc->rho[kk] = tot;
+        }, NoPost{});
+}
+
+// res = b - A x (b in the caller's layout, column k at b + k * ldb)
+__global__ void k_b_residual(int nx, int K, const double *w, const double *b, int64_t ldb,
+                             const double *x, double *res) {
+    const int n1 = nx - 1;
+    const int n = n1 * n1;
+    const int64_t nK = (int64_t)n * K;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nK) return;
+    const int k = (int)(e % K);
+    const int g = (int)(e / K);
+    const int jj = g / n1, ii = g - jj * n1;
+    const bool W = ii > 0, E = ii < n1 - 1, S = jj > 0, N = jj < n1 - 1;
+    auto X = [&](int gg) { return x[(int64_t)gg * K + k]; };
+    double v = w[g] * X(g);
+    if (E) v = fma(w[n + g], X(g + 1), v);
+    if (N) v = fma(w[2 * n + g], X(g + n1), v);
+    if (N && E) v = fma(w[3 * n + g], X(g + n1 + 1), v);
+    if (N && W) v = fma(w[4 * n + g], X(g + n1 - 1), v);
+    if (W) v = fma(w[n + g - 1], X(g - 1), v);
+    if (S) v = fma(w[2 * n + g - n1], X(g - n1), v);
+    if (S && W) v = fma(w[3 * n + g - n1 - 1], X(g - n1 - 1), v);
+    if (S && E) v = fma(w[4 * n + g - n1 + 1], X(g - n1 + 1), v);
+    res[e] = b[(int64_t)k * ldb + g] - v;
+}
+
+__global__ void k_b_norm2(int64_t nK, int K, const double *v, double *part, unsigned *counter,
+                          double *out) {
+    const int k = threadIdx.x % K;
+    (void)k;
+    double s = 0.0;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nK; e += (int64_t)gridDim.x * blockDim.x)
+        s = fma(v[e], v[e], s);
+    grid_reduce_k(s, K, part, counter, [&](int kk, double tot) { out[kk] = tot; }, NoPost{});
+}
+
+// r(:, k) = res(:, k) for the right-hand sides that restart
+__global__ void k_b_restart(int64_t nK, int K, const double *res, double *r, const BatchScalars *sc) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nK) return;
+    const int k = (int)(e % K);
+    if (sc->fresh[k] && !sc->done[k]) r[e] = res[e];
+}
+
+// dst[g * K + k] = src[k * ld + g] and back
+__global__ void k_b_gather(int n, int K, const double *src, int64_t ld, double *dst) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)n * K) return;
+    const int k = (int)(e % K);
+    dst[e] = src[(int64_t)k * ld + e / K];
+}
+__global__ void k_b_scatter(int n, int K, const double *src, double *dst, int64_t ld) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)n * K) return;
+    const int k = (int)(e % K);
+    dst[(int64_t)k * ld + e / K] = src[e];
+}
+
+// Both integer-operation conversions against the hardware ones, bit for bit
+// (NaN results compared as NaN).
+__global__ void k_selftest_convert(const double *d, int64_t n, unsigned long long *bad) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double v = d[i];
+    const float a = f64_to_f32(v), b = __double2float_rn(v);
+    const bool nan1 = a != a && b != b;
+    if (!nan1 && __float_as_uint(a) != __float_as_uint(b)) atomicAdd(bad, 1ull);
+    // every low word, read as a binary32, widened
+    const float f = __uint_as_float((unsigned)__double2loint(v));
+    const double x = f32_to_f64(f), y = (double)f;
+    const bool nan2 = x != x && y != y;
+    if (!nan2 && __double_as_longlong(x) != __double_as_longlong(y)) atomicAdd(bad, 1ull);
+}
+
+constexpr size_t kSmemMaxB = 227 * 1024;
+
+int num_sms_b() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 152;
+    }
+    return n;
+}
+
+int warps_b(int nsub, size_t slice) {
+    const int fit = (int)(kSmemMaxB / slice);
+    int want = (nsub + num_sms_b() - 1) / num_sms_b();
+    if (want < 1) want = 1;
+    int w = want < fit ? want : fit;
+    if (w > 8) w = 8;
+    return w < 1 ? 1 : w;
+}
+
+int pidx_b(int prec) { return prec == BDDC_PREC_FP64 ? 0 : (prec == BDDC_PREC_FP32 ? 1 : 2); }
+
+template <class T, class ACC, int BP>
+void dir_b_launch(const DevLevel &L, const BatchLevel &B, bool post, const double *r, double *z,
+                  const int *skip, cudaStream_t s) {
+    const size_t sm = DirSmemB<T, ACC, BP>::bytes(L);
+    if (!post) launch_pdl(k_dir_b<T, ACC, BP, false>, L.nsub, 32 * kDW, sm, s, L, B, r, z, skip);
+    else launch_pdl(k_dir_b<T, ACC, BP, true>, L.nsub, 32 * kDW, sm, s, L, B, r, z, skip);
+}
+
+template <class T, class ACC>
+void dir_b(const DevLevel &L, const BatchLevel &B, bool post, const double *r, double *z,
+           const int *skip, cudaStream_t s) {
+    if (L.bp == 8) dir_b_launch<T, ACC, 8>(L, B, post, r, z, skip, s);
+    else if (L.bp == 16) dir_b_launch<T, ACC, 16>(L, B, post, r, z, skip, s);
+    else dir_b_launch<T, ACC, 32>(L, B, post, r, z, skip, s);
+}
+
+template <class T, class ACC>
+void neu_b(const DevLevel &L, const BatchLevel &B, int prec, const double *r, const int *skip,
+           cudaStream_t s) {
+    const int pi = pidx_b(prec);
+    const size_t slice = al16(al16((size_t)L.max_nrec[pi]) +
+                              al16(sizeof(ACC) * (size_t)(L.max_nG > 0 ? L.max_nG : 1) * 32) + 16);
+    const int wpc = warps_b(L.nsub, slice);
+    launch_pdl(k_neu_b<T, ACC>, (L.nsub + wpc - 1) / wpc, 32 * wpc, slice * wpc, s, L, B, pi, r, skip,
+               (unsigned)slice);
+}
+
+template <class T, class ACC>
+void avg_b(const DevLevel &L, const BatchLevel &B, int prec, const int *skip, cudaStream_t s) {
+    const int pi = pidx_b(prec);
+    const size_t slice = al16(al16((size_t)L.max_nrec[pi]) +
+                              al16(sizeof(ACC) * (size_t)(L.max_nc > 0 ? L.max_nc : 1) * 32) + 16);
+    const int wpc = warps_b(L.nsub, slice);
+    launch_pdl(k_avg_b<T, ACC>, (L.nsub + wpc - 1) / wpc, 32 * wpc, slice * wpc, s, L, B, pi, skip,
+               (unsigned)slice);
+}
+
+template <class T, class ACC> size_t dir_slice_b(const DevLevel &L) {
+    if (L.bp == 8) return DirSmemB<T, ACC, 8>::bytes(L);
+    if (L.bp == 16) return DirSmemB<T, ACC, 16>::bytes(L);
+    return DirSmemB<T, ACC, 32>::bytes(L);
+}
+
+int vgrid_b(int64_t nK, int K) {
+    const int bd = bblock(K);
+    int64_t g = (nK + 4 * (int64_t)bd - 1) / (4 * (int64_t)bd);
+    if (g > 152 * 8) g = 152 * 8;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+}  // namespace
+
+bool batch_path(const DevLevel &L, int prec) {
+    if (!(L.bp == 8 || L.bp == 16 || L.bp == 32) || !L.irec) return false;
+    const int pi = pidx_b(prec);
+    const size_t a = prec == BDDC_PREC_FP64 ? 8 : 4;
+    size_t dir;
+    if (prec == BDDC_PREC_FP64) dir = dir_slice_b<double, double>(L);
+    else if (prec == BDDC_PREC_FP32) dir = dir_slice_b<float, float>(L);
+    else dir = dir_slice_b<__nv_bfloat16, float>(L);
+    const size_t neu = al16((size_t)L.max_nrec[pi]) + al16(a * (size_t)(L.max_nG > 0 ? L.max_nG : 1) * 32) + 16;
+    const size_t avg = al16((size_t)L.max_nrec[pi]) + al16(a * (size_t)(L.max_nc > 0 ? L.max_nc : 1) * 32) + 16;
+    return dir <= kSmemMaxB && neu <= kSmemMaxB && avg <= kSmemMaxB;
+}
+
+void prepare_batch_kernels() {
+    const int big = (int)kSmemMaxB;
+#define BDDC_SMEM_ATTR_B(k) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, big)
+#define BDDC_DIR_B(T, A, BPV)                                   \
+    BDDC_SMEM_ATTR_B((k_dir_b<T, A, BPV, false>));              \
+    BDDC_SMEM_ATTR_B((k_dir_b<T, A, BPV, true>));
+    BDDC_DIR_B(double, double, 8) BDDC_DIR_B(double, double, 16) BDDC_DIR_B(double, double, 32)
+    BDDC_DIR_B(float, float, 8) BDDC_DIR_B(float, float, 16) BDDC_DIR_B(float, float, 32)
+    BDDC_DIR_B(__nv_bfloat16, float, 8) BDDC_DIR_B(__nv_bfloat16, float, 16) BDDC_DIR_B(__nv_bfloat16, float, 32)
+    BDDC_SMEM_ATTR_B((k_neu_b<double, double>)); BDDC_SMEM_ATTR_B((k_neu_b<float, float>));
+    BDDC_SMEM_ATTR_B((k_neu_b<__nv_bfloat16, float>));
+    // (k_gemm_b also has static shared memory: its dynamic limit is its own size)
+    cudaFuncSetAttribute(k_gemm_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(GM_S * GM_STAGE));
+    BDDC_SMEM_ATTR_B((k_avg_b<double, double>)); BDDC_SMEM_ATTR_B((k_avg_b<float, float>));
+    BDDC_SMEM_ATTR_B((k_avg_b<__nv_bfloat16, float>));
+#undef BDDC_DIR_B
+#undef BDDC_SMEM_ATTR_B
+}
+
+void apply_level_pre_b(const DevLevel &L, const BatchLevel &B, int prec, const double *r,
+                       const int *skip, cudaStream_t s) {
+    if (prec == BDDC_PREC_FP64) {
+        dir_b<double, double>(L, B, false, r, nullptr, skip, s);
+        neu_b<double, double>(L, B, prec, r, skip, s);
+    } else if (prec == BDDC_PREC_FP32) {
+        dir_b<float, float>(L, B, false, r, nullptr, skip, s);
+        neu_b<float, float>(L, B, prec, r, skip, s);
+    } else {
+        dir_b<__nv_bfloat16, float>(L, B, false, r, nullptr, skip, s);
+        neu_b<__nv_bfloat16, float>(L, B, prec, r, skip, s);
+    }
+}
+
+void apply_level_post_b(const DevLevel &L, const BatchLevel &B, int prec, const double *r, double *z,
+                        const int *skip, cudaStream_t s) {
+    if (prec == BDDC_PREC_FP64) {
+        avg_b<double, double>(L, B, prec, skip, s);
+        dir_b<double, double>(L, B, true, r, z, skip, s);
+    } else if (prec == BDDC_PREC_FP32) {
+        avg_b<float, float>(L, B, prec, skip, s);
+        dir_b<float, float>(L, B, true, r, z, skip, s);
+    } else {
+        avg_b<__nv_bfloat16, float>(L, B, prec, skip, s);
+        dir_b<__nv_bfloat16, float>(L, B, true, r, z, skip, s);
+    }
+}
+
+void launch_gemm_b(int n, int ld, const double *A, const double *X, double *Y, int K, const int *skip,
+                   int *err, cudaStream_t s) {
+    if (n <= 0) return;
+    launch_pdl(k_gemm_b, (n + GM_R - 1) / GM_R, 256, GM_S * GM_STAGE, s, n, ld, A, X, Y, K, skip, err);
+}
+
+void launch_b_init(int n, int K, const double *b, int64_t ldb, double *x, double *r, double *p,
+                   double *part, unsigned *counter, BatchScalars *sc, double tol, int maxit,
+                   cudaStream_t s) {
+    const int64_t nK = (int64_t)n * K;
+    k_b_init<<<vgrid_b(nK, K), bblock(K), 0, s>>>(n, K, b, ldb, x, r, p, part, counter, sc, tol, maxit);
+}
+void launch_b_dir(int n, int K, const double *z, double *p, const BatchScalars *sc, cudaStream_t s) {
+    const int64_t nK = (int64_t)n * K;
+    launch_pdl(k_b_dir, vgrid_b(nK, K), bblock(K), 0, s, nK, K, z, p, sc);
+}
+void launch_b_spmv_dot(int nx, int K, const double *w, const double *p, double *q, double *part,
+                       unsigned *counter, BatchScalars *sc, double *alphas, cudaStream_t s) {
+    const int64_t nK = (int64_t)(nx - 1) * (nx - 1) * K;
+    launch_pdl(k_b_spmv_dot, vgrid_b(nK, K), bblock(K), 0, s, nx, K, w, p, q, part, counter, sc, alphas);
+}
+void launch_b_update(int n, int K, double *x, double *r, const double *p, const double *q,
+                     double *part, unsigned *counter, BatchScalars *sc, cudaStream_t s) {
+    const int64_t nK = (int64_t)n * K;
+    launch_pdl(k_b_update, vgrid_b(nK, K), bblock(K), 0, s, nK, K, x, r, p, q, part, counter, sc);
+}
+void launch_b_rz(int n, int K, const double *r, const double *z, double *part, unsigned *counter,
+                 BatchScalars *sc, double *betas, cudaStream_t s) {
+    const int64_t nK = (int64_t)n * K;
+    launch_pdl(k_b_rz, vgrid_b(nK, K), bblock(K), 0, s, nK, K, r, z, part, counter, sc, betas);
+}
+void launch_b_residual(int nx, int K, const double *w, const double *b, int64_t ldb, const double *x,
+                       double *res, cudaStream_t s) {
+    const int64_t nK = (int64_t)(nx - 1) * (nx - 1) * K;
+    k_b_residual<<<(int)((nK + 255) / 256), 256, 0, s>>>(nx, K, w, b, ldb, x, res);
+}
+void launch_b_norm2(int n, int K, const double *v, double *part, unsigned *counter, double *out,
+                    cudaStream_t s) {
+    const int64_t nK = (int64_t)n * K;
+    k_b_norm2<<<vgrid_b(nK, K), bblock(K), 0, s>>>(nK, K, v, part, counter, out);
+}
+void launch_b_restart(int n, int K, const double *res, double *r, const BatchScalars *sc,
+                      cudaStream_t s) {
+    const int64_t nK = (int64_t)n * K;
+    k_b_restart<<<(int)((nK + 255) / 256), 256, 0, s>>>(nK, K, res, r, sc);
+}
+void launch_selftest_convert(const double *d, int64_t n, unsigned long long *bad, cudaStream_t s) {
+    if (n > 0) k_selftest_convert<<<(int)((n + 255) / 256), 256, 0, s>>>(d, n, bad);
+}
+void launch_b_gather(int n, int K, const double *src, int64_t ld, double *dst, cudaStream_t s) {
+    const int64_t nK = (int64_t)n * K;
+    if (nK > 0) k_b_gather<<<(int)((nK + 255) / 256), 256, 0, s>>>(n, K, src, ld, dst);
+}
+void launch_b_scatter(int n, int K, const double *src, double *dst, int64_t ld, cudaStream_t s) {
+    const int64_t nK = (int64_t)n * K;
+    if (nK > 0) k_b_scatter<<<(int)((nK + 255) / 256), 256, 0, s>>>(n, K, src, dst, ld);
+}
+
+}  // namespace bddc

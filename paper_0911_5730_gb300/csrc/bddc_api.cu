@@ -60,8 +60,29 @@ struct LevelData {
     int64_t sumI = 0, sumG = 0, sumC = 0, bandnnz = 0, blockent = 0, coonnz = 0, nent = 0, pent = 0;
 };
 
+// Buffers of the batched solve (allocated on first use, sized for kMaxBatch).
+struct BatchWs {
+    std::vector<BatchLevel> lv;
+    double *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *tmp = nullptr;
+    double *bcol = nullptr, *xcol = nullptr;   // caller-layout staging for host buffers
+    double *part = nullptr, *alphas = nullptr, *betas = nullptr, *nrm = nullptr;
+    unsigned *counter = nullptr;
+    BatchScalars *sc = nullptr;
+    BatchScalars *hsc = nullptr;         // pinned mirror
+    double *hnrm = nullptr;              // pinned
+    std::map<int, cudaGraphExec_t> graphs;   // key: prec * 64 + K
+    int last_iters = 0;
+    std::vector<double> hal, hbe;
+    ~BatchWs() {
+        for (auto &g : graphs) cudaGraphExecDestroy(g.second);
+        if (hsc) cudaFreeHost(hsc);
+        if (hnrm) cudaFreeHost(hnrm);
+    }
+};
+
 struct Workspace {
     DevArena arena;
+    std::unique_ptr<BatchWs> bw;
     std::vector<DevLevel> lv;
     double *x = nullptr, *r = nullptr, *z = nullptr, *q = nullptr, *tmp = nullptr;
     double *p0 = nullptr, *p1 = nullptr;   // search direction, alternating by iteration
@@ -80,6 +101,7 @@ struct Workspace {
     int last_iters = 0;                 // iterations of the previous solve (chunking hint)
     std::vector<double> hal, hbe;       // host copies of the CG coefficients
     ~Workspace() {
+        bw.reset();
         for (auto &g : graph) if (g) cudaGraphExecDestroy(g);
         if (hsc) cudaFreeHost(hsc);
         if (hout) cudaFreeHost(hout);
@@ -710,6 +732,7 @@ int pcg_one(bddc_ctx *C, Workspace &W, int prec, const double *b, double *x, dou
         info->iters = h.it;
         info->status = status;
         info->kernel_launches = launches;
+        info->batch_width = 1;
         info->relres = h.bb > 0 ? std::sqrt(h.rr / h.bb) : 0.0;
         info->relres_true = h.bb > 0 ? std::sqrt(rr_true / h.bb) : 0.0;
         info->lam_min = lmin;
@@ -721,6 +744,184 @@ int pcg_one(bddc_ctx *C, Workspace &W, int prec, const double *b, double *x, dou
 
 // Level 1 of Sec. 2: the Q1 elements of the mesh with their free nodes
 // (Dirichlet nodes are dropped slots).
+// ---------------------------------------------------------------------------
+// Batches of right-hand sides
+// ---------------------------------------------------------------------------
+bool batch_ok(bddc_ctx *C, Workspace &W, int prec) {
+    (void)C;
+    for (auto &D : W.lv)
+        if (!batch_path(D, prec)) return false;
+    return true;
+}
+
+BatchWs &batch_ws(bddc_ctx *C, Workspace &W) {
+    if (W.bw) return *W.bw;
+    auto bw = std::make_unique<BatchWs>();
+    DevArena &A = W.arena;
+    const int64_t n = C->n();
+    const int KB = kMaxBatch;
+    for (size_t l = 0; l < W.lv.size(); ++l) {
+        const DevLevel &D = W.lv[l];
+        BatchLevel B;
+        const int64_t ni = std::max(D.n_iface, 1);
+        int64_t sg = 0;
+        for (auto &v : C->L[l].H.Gord) sg += (int64_t)v.size();
+        const int64_t ncp = std::max<int64_t>(std::max(D.nc, 1), C->ld_top);
+        B.rB = A.alloc_n<double>(ni * KB);
+        B.uB = A.alloc_n<double>(ni * KB);
+        B.w = A.alloc_n<double>(std::max<int64_t>(sg, 1) * KB);
+        B.rcv = A.alloc_n<double>(ncp * KB);
+        B.ucv = A.alloc_n<double>(ncp * KB);
+        BDDC_CUDA_TRY(cudaMemset(B.rB, 0, sizeof(double) * ni * KB));
+        BDDC_CUDA_TRY(cudaMemset(B.uB, 0, sizeof(double) * ni * KB));
+        BDDC_CUDA_TRY(cudaMemset(B.rcv, 0, sizeof(double) * ncp * KB));
+        bw->lv.push_back(B);
+    }
+    bw->x = A.alloc_n<double>(n * KB); bw->r = A.alloc_n<double>(n * KB);
+    bw->z = A.alloc_n<double>(n * KB); bw->p = A.alloc_n<double>(n * KB);
+    bw->q = A.alloc_n<double>(n * KB); bw->tmp = A.alloc_n<double>(n * KB);
+    bw->bcol = A.alloc_n<double>(n * KB); bw->xcol = A.alloc_n<double>(n * KB);
+    bw->part = A.alloc_n<double>(1216 * KB + 64);
+    bw->counter = A.alloc_n<unsigned>(4);
+    BDDC_CUDA_TRY(cudaMemset(bw->counter, 0, 4 * sizeof(unsigned)));
+    bw->sc = A.alloc_n<BatchScalars>(1);
+    BDDC_CUDA_TRY(cudaMemset(bw->sc, 0, sizeof(BatchScalars)));
+    bw->alphas = A.alloc_n<double>((int64_t)(W.maxit_cap + 1) * KB);
+    bw->betas = A.alloc_n<double>((int64_t)(W.maxit_cap + 1) * KB);
+    bw->nrm = A.alloc_n<double>(KB);
+    BDDC_CUDA_TRY(cudaHostAlloc((void **)&bw->hsc, sizeof(BatchScalars), cudaHostAllocDefault));
+    BDDC_CUDA_TRY(cudaHostAlloc((void **)&bw->hnrm, sizeof(double) * KB, cudaHostAllocDefault));
+    W.bw = std::move(bw);
+    return *W.bw;
+}
+
+void apply_b_rec(bddc_ctx *C, Workspace &W, BatchWs &BW, int l, int prec, const double *r, double *z,
+                 const int *skip, cudaStream_t st) {
+    const DevLevel &D = W.lv[l];
+    const BatchLevel &B = BW.lv[l];
+    apply_level_pre_b(D, B, prec, r, skip, st);
+    if (l + 1 == (int)W.lv.size())
+        launch_gemm_b(C->n_top, C->ld_top, C->Ainv, B.rcv, B.ucv, B.K, skip, C->err_dev, st);
+    else
+        apply_b_rec(C, W, BW, l + 1, prec, B.rcv, B.ucv, skip, st);
+    apply_level_post_b(D, B, prec, r, z, skip, st);
+}
+
+void set_batch_width(BatchWs &BW, int K) {
+    for (auto &B : BW.lv) B.K = K;
+}
+
+cudaGraphExec_t batch_graph(bddc_ctx *C, Workspace &W, BatchWs &BW, int prec, int K) {
+    const int key = prec * 64 + K;
+    auto it = BW.graphs.find(key);
+    if (it != BW.graphs.end()) return it->second;
+    const int n = C->n();
+    cudaStream_t st = W.stream;
+    cudaGraph_t g;
+    BDDC_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    launch_b_dir(n, K, BW.z, BW.p, BW.sc, st);
+    launch_b_spmv_dot(C->nx, K, C->w_dev, BW.p, BW.q, BW.part, BW.counter, BW.sc, BW.alphas, st);
+    launch_b_update(n, K, BW.x, BW.r, BW.p, BW.q, BW.part, BW.counter, BW.sc, st);
+    apply_b_rec(C, W, BW, 0, prec, BW.r, BW.z, &BW.sc->all_done, st);
+    launch_b_rz(n, K, BW.r, BW.z, BW.part, BW.counter, BW.sc, BW.betas, st);
+    BDDC_CUDA_TRY(cudaStreamEndCapture(st, &g));
+    cudaGraphExec_t ge;
+    BDDC_CUDA_TRY(cudaGraphInstantiate(&ge, g, 0));
+    cudaGraphDestroy(g);
+    BW.graphs[key] = ge;
+    return ge;
+}
+
+// PCG (Sec. 5) for K right-hand sides in lockstep; each keeps its own
+// scalars, iteration count and stopping test (recursive residual, then the
+// true residual as in the single right-hand-side solve).  b and x in the
+// caller's layout (column k at b + k * ldb, x + k * ldx).  Runs on W.stream.
+int pcg_batch(bddc_ctx *C, Workspace &W, int prec, const double *b, int64_t ldb, double *x,
+              int64_t ldx, int K, double rtol, int maxit, bddc_solve_info *info) {
+    BatchWs &BW = batch_ws(C, W);
+    const int n = C->n();
+    cudaStream_t st = W.stream;
+    if (maxit > W.maxit_cap) maxit = W.maxit_cap;
+    set_batch_width(BW, K);
+    launch_b_init(n, K, b, ldb, BW.x, BW.r, BW.p, BW.part, BW.counter, BW.sc, rtol, maxit, st);
+    apply_b_rec(C, W, BW, 0, prec, BW.r, BW.z, &BW.sc->all_done, st);
+    launch_b_rz(n, K, BW.r, BW.z, BW.part, BW.counter, BW.sc, BW.betas, st);
+    cudaGraphExec_t g = batch_graph(C, W, BW, prec, K);
+    const int per_apply = 4 * (int)W.lv.size() + 1;
+    int launches = 2 + per_apply;
+    int chunk = BW.last_iters > 1 ? std::min(BW.last_iters, 256) : 4;
+    BatchScalars &h = *BW.hsc;
+    for (;;) {
+        for (int k = 0; k < chunk; ++k) BDDC_CUDA_TRY(cudaGraphLaunch(g, st));
+        launches += chunk * (4 + per_apply);
+        BDDC_CUDA_TRY(cudaMemcpyAsync(BW.hsc, BW.sc, sizeof(BatchScalars), cudaMemcpyDeviceToHost, st));
+        BDDC_CUDA_TRY(cudaStreamSynchronize(st));
+        if (!h.all_done) { chunk = std::max(1, std::min(chunk / 2, 16)); continue; }
+        // true residuals of every right-hand side
+        launch_b_residual(C->nx, K, C->w_dev, b, ldb, BW.x, BW.tmp, st);
+        launch_b_norm2(n, K, BW.tmp, BW.part, BW.counter, BW.nrm, st);
+        launches += 2;
+        BDDC_CUDA_TRY(cudaMemcpyAsync(BW.hnrm, BW.nrm, sizeof(double) * K, cudaMemcpyDeviceToHost, st));
+        BDDC_CUDA_TRY(cudaStreamSynchronize(st));
+        bool again = false;
+        for (int k = 0; k < K; ++k) {
+            if (h.conv[k] && BW.hnrm[k] > h.tol2[k] && h.it[k] < maxit) {
+                // the recursive residual drifted: restart this one from the
+                // true residual with a fresh direction
+                h.done[k] = 0; h.conv[k] = 0; h.fresh[k] = 1; h.rr[k] = BW.hnrm[k];
+                again = true;
+            }
+        }
+        if (!again) break;
+        h.all_done = 0;
+        BDDC_CUDA_TRY(cudaMemcpyAsync(BW.sc, BW.hsc, sizeof(BatchScalars), cudaMemcpyHostToDevice, st));
+        launch_b_restart(n, K, BW.tmp, BW.r, BW.sc, st);
+        apply_b_rec(C, W, BW, 0, prec, BW.r, BW.z, &BW.sc->all_done, st);
+        launch_b_rz(n, K, BW.r, BW.z, BW.part, BW.counter, BW.sc, BW.betas, st);
+        launches += 2 + per_apply;
+        chunk = 1;
+    }
+    int kmax = 0;
+    for (int k = 0; k < K; ++k) kmax = std::max(kmax, std::min(h.it[k], W.maxit_cap));
+    const size_t nab = (size_t)(kmax + 1) * K;
+    if (BW.hal.size() < nab) { BW.hal.resize(nab); BW.hbe.resize(nab); }
+    if (kmax > 0) {
+        BDDC_CUDA_TRY(cudaMemcpyAsync(BW.hal.data(), BW.alphas, sizeof(double) * kmax * K, cudaMemcpyDeviceToHost, st));
+        BDDC_CUDA_TRY(cudaMemcpyAsync(BW.hbe.data(), BW.betas, sizeof(double) * kmax * K, cudaMemcpyDeviceToHost, st));
+    }
+    launch_b_scatter(n, K, BW.x, x, ldx, st);
+    int kerr = 0;
+    BDDC_CUDA_TRY(cudaMemcpyAsync(&kerr, C->err_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
+    BDDC_CUDA_TRY(cudaStreamSynchronize(st));
+    BDDC_CUDA_TRY(cudaGetLastError());
+    if (kerr) throw Error(BDDC_E_TIMEOUT, "a bounded device wait gave up during the solve");
+    int rc = BDDC_OK;
+    int itmax = 0;
+    for (int k = 0; k < K; ++k) {
+        const int status = (h.conv[k] && BW.hnrm[k] <= h.tol2[k] * (1 + 1e-12)) ? BDDC_OK : BDDC_E_NOCONV;
+        if (status != BDDC_OK) rc = status;
+        itmax = std::max(itmax, h.it[k]);
+        if (!info) continue;
+        const int kit = std::min(h.it[k], W.maxit_cap);
+        std::vector<double> al(kit + 1), be(kit + 1);
+        for (int j = 0; j < kit; ++j) { al[j] = BW.hal[(size_t)j * K + k]; be[j] = BW.hbe[(size_t)j * K + k]; }
+        double lmin = 1.0, lmax = 1.0;
+        lanczos_extremes(al, be, kit, &lmin, &lmax);
+        bddc_solve_info &I = info[k];
+        I.iters = h.it[k];
+        I.status = status;
+        I.kernel_launches = k == 0 ? launches : 0;
+        I.batch_width = K;
+        I.relres = h.bb[k] > 0 ? std::sqrt(h.rr[k] / h.bb[k]) : 0.0;
+        I.relres_true = h.bb[k] > 0 ? std::sqrt(BW.hnrm[k] / h.bb[k]) : 0.0;
+        I.lam_min = lmin;
+        I.lam_max = lmax;
+        I.kappa_est = lmin > 0 ? lmax / lmin : 0.0;
+    }
+    BW.last_iters = itmax;
+    return rc;
+}
+
 void level_one(HLevel &H, int nx, const bddc_decomp *decomp) {
     const int nelem = nx * nx;
     H.n = (nx - 1) * (nx - 1);
@@ -808,7 +1009,7 @@ int bddc_setup(const bddc_mesh *mesh, const double *k_elem, const bddc_decomp *d
         C->err_dev = C->arena.alloc_n<int>(1);
         BDDC_CUDA_TRY(cudaMemsetAsync(C->err_dev, 0, sizeof(int), st));
         static std::once_flag prep_once;
-        std::call_once(prep_once, prepare_apply_kernels);
+        std::call_once(prep_once, [] { prepare_apply_kernels(); prepare_batch_kernels(); });
         DevArena tmp;
         int *err = tmp.alloc_n<int>(1);
         BDDC_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
@@ -895,8 +1096,20 @@ int bddc_apply(bddc_ctx *ctx, const double *r_dev, double *z_dev, int nrhs, int6
         if (ld < n) throw Error(BDDC_E_ARG, "ld < n");
         std::lock_guard<std::mutex> lk(ctx->mu);
         cudaStream_t st = (cudaStream_t)stream;
-        for (int j = 0; j < nrhs; ++j)
-            apply_rec(ctx, *ctx->ws, 0, ctx->prec, r_dev + j * ld, z_dev + j * ld, nullptr, st);
+        Workspace &W = *ctx->ws;
+        if (nrhs > 1 && batch_ok(ctx, W, ctx->prec)) {
+            BatchWs &BW = batch_ws(ctx, W);
+            for (int j0 = 0; j0 < nrhs; j0 += kMaxBatch) {
+                const int K = std::min(kMaxBatch, nrhs - j0);
+                set_batch_width(BW, K);
+                launch_b_gather(n, K, r_dev + j0 * ld, ld, BW.r, st);
+                apply_b_rec(ctx, W, BW, 0, ctx->prec, BW.r, BW.z, nullptr, st);
+                launch_b_scatter(n, K, BW.z, z_dev + j0 * ld, ld, st);
+            }
+        } else {
+            for (int j = 0; j < nrhs; ++j)
+                apply_rec(ctx, W, 0, ctx->prec, r_dev + j * ld, z_dev + j * ld, nullptr, st);
+        }
         BDDC_CUDA_TRY(cudaGetLastError());
         return BDDC_OK;
     });
@@ -946,10 +1159,19 @@ int bddc_pcg_solve(bddc_ctx *ctx, const double *b_dev, double *x_dev, int nrhs, 
         BDDC_CUDA_TRY(cudaEventRecord(W.ev, st));
         BDDC_CUDA_TRY(cudaStreamWaitEvent(W.stream, W.ev, 0));
         int rc = BDDC_OK;
-        for (int j = 0; j < nrhs; ++j) {
-            const int s = pcg_one(ctx, W, ctx->prec, b_dev + j * ld, x_dev + j * ld, rtol, maxit,
-                                  info_host ? info_host + j : nullptr);
-            if (s != BDDC_OK) rc = s;
+        if (nrhs > 1 && batch_ok(ctx, W, ctx->prec)) {
+            for (int j0 = 0; j0 < nrhs; j0 += kMaxBatch) {
+                const int K = std::min(kMaxBatch, nrhs - j0);
+                const int s = pcg_batch(ctx, W, ctx->prec, b_dev + j0 * ld, ld, x_dev + j0 * ld, ld, K,
+                                        rtol, maxit, info_host ? info_host + j0 : nullptr);
+                if (s != BDDC_OK) rc = s;
+            }
+        } else {
+            for (int j = 0; j < nrhs; ++j) {
+                const int s = pcg_one(ctx, W, ctx->prec, b_dev + j * ld, x_dev + j * ld, rtol, maxit,
+                                      info_host ? info_host + j : nullptr);
+                if (s != BDDC_OK) rc = s;
+            }
         }
         BDDC_CUDA_TRY(cudaEventRecord(W.ev, W.stream));
         BDDC_CUDA_TRY(cudaStreamWaitEvent(st, W.ev, 0));
@@ -970,6 +1192,24 @@ int bddc_pcg_solve_host(bddc_ctx *ctx, const double *b_host, double *x_host, int
         Workspace &W = *ctx->ws;
         (void)stream;
         int rc = BDDC_OK;
+        if (nrhs > 1 && batch_ok(ctx, W, ctx->prec)) {
+            BatchWs &BW = batch_ws(ctx, W);
+            for (int j0 = 0; j0 < nrhs; j0 += kMaxBatch) {
+                const int K = std::min(kMaxBatch, nrhs - j0);
+                for (int k = 0; k < K; ++k)
+                    BDDC_CUDA_TRY(cudaMemcpyAsync(BW.bcol + (int64_t)k * n, b_host + (j0 + k) * ld,
+                                                  sizeof(double) * n, cudaMemcpyHostToDevice, W.stream));
+                const int s = pcg_batch(ctx, W, ctx->prec, BW.bcol, n, BW.xcol, n, K, rtol, maxit,
+                                        info_host ? info_host + j0 : nullptr);
+                for (int k = 0; k < K; ++k)
+                    BDDC_CUDA_TRY(cudaMemcpyAsync(x_host + (j0 + k) * ld, BW.xcol + (int64_t)k * n,
+                                                  sizeof(double) * n, cudaMemcpyDeviceToHost, W.stream));
+                BDDC_CUDA_TRY(cudaStreamSynchronize(W.stream));
+                if (s != BDDC_OK) rc = s;
+            }
+            if (rc != BDDC_OK) set_error("PCG did not reach the tolerance within maxit");
+            return rc;
+        }
         for (int j = 0; j < nrhs; ++j) {
             BDDC_CUDA_TRY(cudaMemcpyAsync(W.bbuf, b_host + j * ld, sizeof(double) * n, cudaMemcpyHostToDevice, W.stream));
             const int s = pcg_one(ctx, W, ctx->prec, W.bbuf, W.tmp, rtol, maxit,
@@ -1160,6 +1400,27 @@ int bddc_apply_noalloc(bddc_ctx *ctx, const double *r_dev, double *z_dev, void *
         for (int l = nl - 1; l >= 0; --l)
             apply_level_post(lv[l], prec, rin[l], l == 0 ? z_dev : lv[l - 1].ucv, nullptr, st);
         BDDC_CUDA_TRY(cudaGetLastError());
+        return BDDC_OK;
+    });
+}
+
+int bddc_selftest_convert(const double *d_dev, int64_t n, int64_t *mismatches, void *stream) {
+    return guarded([&]() -> int {
+        if (!d_dev || n < 0 || !mismatches) throw Error(BDDC_E_ARG, "bad argument");
+        cudaStream_t st = (cudaStream_t)stream;
+        unsigned long long *bad = nullptr;
+        BDDC_CUDA_TRY(cudaMalloc(&bad, sizeof(unsigned long long)));
+        unsigned long long h = 0;
+        cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(h), st);
+        if (e == cudaSuccess) {
+            launch_selftest_convert(d_dev, n, bad, st);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&h, bad, sizeof(h), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        cudaFree(bad);
+        if (e != cudaSuccess) throw Error(BDDC_E_CUDA, cudaGetErrorString(e));
+        *mismatches = (int64_t)h;
         return BDDC_OK;
     });
 }

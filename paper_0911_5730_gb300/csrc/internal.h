@@ -164,6 +164,62 @@ void apply_level_pre(const DevLevel &L, int prec, const double *r, const int *sk
 // the PCG recurrence, fused into the post-correction where it can be.
 void apply_level_post(const DevLevel &L, int prec, const double *r, double *z, const int *skip,
                       cudaStream_t s, cudaEvent_t *ev = nullptr, const RzArgs *rz = nullptr);
+// ----------------------------------------------------------------------------
+// Batches of K <= kMaxBatch right-hand sides (batch_kernels.cu).  Every batch
+// vector is interleaved: entry (g, k) at g * K + k.
+// ----------------------------------------------------------------------------
+constexpr int kMaxBatch = 32;
+struct BatchLevel {
+    int K = 0;                 // right-hand sides in the batch
+    double *rB = nullptr;      // [n_iface][K]
+    double *uB = nullptr;      // [n_iface][K]
+    double *w = nullptr;       // [sum nG][K]
+    double *rcv = nullptr;     // [max(nc, ld_top)][K], zero beyond nc
+    double *ucv = nullptr;     // [max(nc, ld_top)][K]
+};
+struct BatchScalars {
+    double rho[kMaxBatch], pq[kMaxBatch], alpha[kMaxBatch], beta[kMaxBatch], rr[kMaxBatch],
+        bb[kMaxBatch], tol2[kMaxBatch];
+    int it[kMaxBatch], done[kMaxBatch], conv[kMaxBatch], fresh[kMaxBatch];
+    int K, maxit, all_done, pad_;
+};
+// Whether a level's operators fit the batched kernels' shared-memory slices.
+bool batch_path(const DevLevel &L, int prec);
+void prepare_batch_kernels();
+// Algorithm 1 on one level for a batch (same scratch protocol as the single
+// right-hand-side launchers, on the BatchLevel buffers).
+void apply_level_pre_b(const DevLevel &L, const BatchLevel &B, int prec, const double *r,
+                       const int *skip, cudaStream_t s);
+void apply_level_post_b(const DevLevel &L, const BatchLevel &B, int prec, const double *r, double *z,
+                        const int *skip, cudaStream_t s);
+// Y = A X for the top level (A as in launch_dense_symv; X, Y interleaved [ld][K])
+void launch_gemm_b(int n, int ld, const double *A, const double *X, double *Y, int K, const int *skip,
+                   int *err, cudaStream_t s);
+// PCG for a batch; b in the caller's layout (column k at b + k * ldb)
+void launch_b_init(int n, int K, const double *b, int64_t ldb, double *x, double *r, double *p,
+                   double *part, unsigned *counter, BatchScalars *sc, double tol, int maxit,
+                   cudaStream_t s);
+void launch_b_dir(int n, int K, const double *z, double *p, const BatchScalars *sc, cudaStream_t s);
+void launch_b_spmv_dot(int nx, int K, const double *w, const double *p, double *q, double *part,
+                       unsigned *counter, BatchScalars *sc, double *alphas, cudaStream_t s);
+void launch_b_update(int n, int K, double *x, double *r, const double *p, const double *q,
+                     double *part, unsigned *counter, BatchScalars *sc, cudaStream_t s);
+void launch_b_rz(int n, int K, const double *r, const double *z, double *part, unsigned *counter,
+                 BatchScalars *sc, double *betas, cudaStream_t s);
+void launch_b_residual(int nx, int K, const double *w, const double *b, int64_t ldb, const double *x,
+                       double *res, cudaStream_t s);
+void launch_b_norm2(int n, int K, const double *v, double *part, unsigned *counter, double *out,
+                    cudaStream_t s);
+// r(:, k) = res(:, k) for every k with fresh && !done
+void launch_b_restart(int n, int K, const double *res, double *r, const BatchScalars *sc,
+                      cudaStream_t s);
+// mismatches of the integer-operation binary32/binary64 conversions against
+// the hardware conversions on n values (added to *bad)
+void launch_selftest_convert(const double *d, int64_t n, unsigned long long *bad, cudaStream_t s);
+// caller layout (column k at src + k * ld) <-> interleaved
+void launch_b_gather(int n, int K, const double *src, int64_t ld, double *dst, cudaStream_t s);
+void launch_b_scatter(int n, int K, const double *src, double *dst, int64_t ld, cudaStream_t s);
+
 // Whether apply_level_post fuses the r.z reduction into its last kernel (one
 // kernel fewer per PCG iteration).
 bool apply_fuses_rz(const DevLevel &L, int prec);
