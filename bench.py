@@ -31,20 +31,18 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "two_level_channels_512"
+BATCH = 32               # right-hand sides per step, solved together
+RHS_SEED = 2002
 METRIC = "BDDC PCG solves/s at rel-res 1e-8 (mixed vs FP64); p50/p99 latency"
 UNIT = "solves/s"
 RTOL = 1e-8
 SAMPLE_NX = 128          # CPU sample: the 128x128 corner of the 512x512 field (64 substructures)
 FULL_SUBS = 1024
 
-# DRAM traffic of the dominant kernel from the ncu capture summarised in
-# profiles/, keyed by kernel, valid only while the kernel source is unchanged.
-NCU_TRAFFIC = {
-    # ncu --set full, FP32 solve of two_level_channels_512 (one launch each)
-    "pre": {"bytes": 37124352 + 10752, "src": "9dc0a638d7bc"},
-    "post": {"bytes": 37405184 + 9472, "src": "9dc0a638d7bc"},
-    "top_solve": {"bytes": 40696064, "src": "9dc0a638d7bc"},
-}
+# DRAM traffic per launch of the dominant kernel from the ncu capture
+# summarised in profiles/: {kernel: {"bytes", "file", "src"}}, valid only while
+# the sha1 prefix of csrc/<file> equals "src".
+NCU_TRAFFIC = {}
 
 
 def _args():
@@ -167,26 +165,29 @@ def cpu_baseline(gpu_iters):
                        % (SAMPLE_NX, SAMPLE_NX, d["ns"], FULL_SUBS, d["ns"], iters, src))}
 
 
-def _kernel_bytes(q, n_top, prec_bytes):
-    """Algorithmic bytes (and flops) of each apply kernel on level 1.
+def _kernel_bytes(q, n_top, prec_bytes, K=1):
+    """Algorithmic bytes (and flops) of each apply kernel on level 1 for K
+    right-hand sides applied together.
 
     Dirichlet solves: the banded Cholesky factor read for the forward and the
-    backward sweep (2 nnz(L) elements), the interior vector in and out and the
-    coupling A_{Gamma I}; Neumann / Psi products: the dense operators once plus
-    the interface vectors; top level: the dense FP64 inverse.
+    backward sweep (2 nnz(L) elements) once per batch, the interior vectors and
+    the coupling A_{Gamma I} per right-hand side; Neumann / Psi products: the
+    dense operators once per batch plus the interface vectors per right-hand
+    side; top level: the dense FP64 inverse once, the coarse vectors per
+    right-hand side (2 n_top^2 K flops).
     """
     e = prec_bytes
     sI, sG, sC = q["sum_interior"][0], q["sum_interface"][0], q["sum_coarse_local"][0]
     band, coo = q["band_nnz"][0], q["coupling_nnz"][0]
     nent, pent = q["neumann_entries"][0], q["psi_entries"][0]
     b = {
-        "pre": 2 * band * e + 8 * sI + coo * (e + 8) + 16 * sG,
-        "neumann": nent * e + pent * e + 8 * sG * 3 + e * sG + 16 * sC,
-        "top_solve": 8 * n_top * n_top + 16 * n_top,
-        "average": pent * e + 8 * sG * 3 + e * sG + 8 * sC,
-        "post": 2 * band * e + 16 * sI + coo * (e + 8) + 8 * sG,
+        "pre": 2 * band * e + coo * (e + 8) + K * (8 * sI + 16 * sG),
+        "neumann": nent * e + pent * e + e * sG + K * (8 * sG * 3 + 16 * sC),
+        "top_solve": 8 * n_top * n_top + K * 16 * n_top,
+        "average": pent * e + e * sG + K * (8 * sG * 3 + 8 * sC),
+        "post": 2 * band * e + coo * (e + 8) + K * (16 * sI + 8 * sG),
     }
-    flops = {"top_solve": 2.0 * n_top * n_top}
+    flops = {"top_solve": 2.0 * n_top * n_top * K}
     return b, flops
 
 
@@ -229,14 +230,18 @@ def gpu_arm(a):
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
     q = P.query(level=1)
-    b = torch.tensor(wl.rhs(), device="cuda")
-    x = torch.empty_like(b)
+    # one step: BATCH seeded N(0,1) right-hand sides solved together
+    Bh = inputs.normal_rhs(wl.n_dof, RHS_SEED, BATCH)
+    B = torch.tensor(Bh, device="cuda")
+    X = torch.empty_like(B)
+    b1 = B[0].contiguous()
+    x1 = torch.empty_like(b1)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
 
-    def solves(prec, K, W, clocks=False):
+    def timed(prec, K, W, rhs, out, clocks=False):
         P.set_precision(prec)
         for _ in range(W):
-            P.solve(b, x, rtol=RTOL)
+            P.solve(rhs, out, rtol=RTOL)
         st = torch.cuda.current_stream()
         ms, infos = [], []
         barrier()
@@ -244,34 +249,40 @@ def gpu_arm(a):
         clk = Clocks(local) if clocks else None
         wall0 = time.perf_counter()
         for _ in range(K):
-            flush.zero_()                     # write > L2 between timed solves (not timed)
+            flush.zero_()                     # write > L2 between timed steps (not timed)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(st)
-            _, info = P.solve(b, x, rtol=RTOL, stream=st)
+            _, info = P.solve(rhs, out, rtol=RTOL, stream=st)
             e1.record(st)
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
-            infos.append(info[0])
+            infos.append(info)
         torch.cuda.synchronize()
         barrier()
         wall = time.perf_counter() - wall0
         c = clk.stop() if clk else None
-        for i in infos:
-            assert i["status"] == 0 and i["relres_true"] <= RTOL, i
+        for inf in infos:
+            for i in inf:
+                assert i["status"] == 0 and i["relres_true"] <= RTOL, i
         return ms, infos, wall, c
 
-    ms32, inf32, wall32, clocks = solves("fp32", a.steps, a.warmup, clocks=True)
-    ms64, inf64, _, _ = solves("fp64", a.steps, a.warmup)
-    msbf, infbf, _, _ = solves("bf16", max(3, a.steps // 2), 1)
+    ms32, inf32, wall32, clocks = timed("fp32", a.steps, a.warmup, B, X, clocks=True)
+    ms64, inf64, _, _ = timed("fp64", max(3, a.steps // 2), 1, B, X)
+    msbf, infbf, _, _ = timed("bf16", max(3, a.steps // 2), 1, B, X)
     t32 = max_over_ranks(sum(ms32) / 1e3)
     t64 = max_over_ranks(sum(ms64) / 1e3)
     tbf = max_over_ranks(sum(msbf) / 1e3)
-    value = world * a.steps / t32
+    value = world * BATCH * a.steps / t32
+    # one right-hand side at a time: latency
+    ms1, inf1, _, _ = timed("fp32", a.steps, a.warmup, b1, x1)
+    ms1_64, _, _, _ = timed("fp64", max(3, a.steps // 2), 1, b1, x1)
+    t1 = max_over_ranks(sum(ms1) / 1e3)
+    t1_64 = max_over_ranks(sum(ms1_64) / 1e3)
 
     # end to end: host buffers (pinned), copies inside the timed call
     P.set_precision("fp32")
-    bh = torch.from_numpy(wl.rhs()).pin_memory()
+    bh = torch.from_numpy(Bh).pin_memory()
     xh = torch.empty_like(bh).pin_memory()
     P.solve_host(bh, xh, rtol=RTOL)
     e2e_t = []
@@ -281,35 +292,38 @@ def gpu_arm(a):
         t0 = time.perf_counter()
         _, ih = P.solve_host(bh, xh, rtol=RTOL)
         e2e_t.append(time.perf_counter() - t0)
-        assert ih[0]["status"] == 0
-    e2e = world * a.steps / max_over_ranks(sum(e2e_t))
+        assert all(i["status"] == 0 for i in ih)
+    e2e = world * BATCH * a.steps / max_over_ranks(sum(e2e_t))
 
-    # roofline: per-kernel device times of the FP32 apply, measured with events
+    # roofline: per-kernel device times of the batched FP32 apply, CUDA events
+    # on the library's stream around each kernel
     names = ["pre", "neumann", "top_solve", "average", "post"]
-    prof = P.profile_apply(b, reps=50)
+    prof = P.profile_apply_batch(B, reps=20)
     n_top = q["n_dof"][-1]
-    kb, kf = _kernel_bytes(q, n_top, 4)
+    kb, kf = _kernel_bytes(q, n_top, 4, BATCH)
     kern = {nm: {"ms": float(t), "bytes": kb[nm]} for nm, t in zip(names, prof)}
-    iters = inf32[0]["iters"]
+    iters = inf32[0][0]["iters"]
     dom = max(kern, key=lambda k: kern[k]["ms"])
     hbm, peak_kind = _peaks()
     ms_dom = kern[dom]["ms"]
-    src_hash = hashlib.sha1(open(os.path.join(ROOT, "paper_0911_5730_gb300", "csrc",
-                                              "apply_kernels.cu"), "rb").read()).hexdigest()[:12]
     tr = NCU_TRAFFIC.get(dom)
-    traffic = tr["bytes"] if tr and tr.get("src") == src_hash else None
+    traffic = None
+    if tr:
+        src = hashlib.sha1(open(os.path.join(ROOT, "paper_0911_5730_gb300", "csrc", tr["file"]),
+                                "rb").read()).hexdigest()[:12]
+        traffic = tr["bytes"] if src == tr["src"] else None
     if dom == "top_solve":
         ach = kf[dom] / (ms_dom * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s",
                 "frac": ach / (FP64_PEAK_GFLOPS / 1e3), "traffic": traffic, "kernel": dom,
-                "peak_kind": "nominal FP64"}
+                "peak_kind": "FP64 pipe: 2 FMA/clk/SM x 152 SMs x 2.07 GHz (nominal 1.25 TFLOP/s)"}
     else:
         ach = kern[dom]["bytes"] / (ms_dom * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                 "traffic": traffic, "kernel": dom, "peak_kind": peak_kind}
     for nm in kern:
         kern[nm]["GBps"] = kern[nm]["bytes"] / (kern[nm]["ms"] * 1e-3) / 1e9
-    launches = sum(i["kernel_launches"] for i in inf32)
+    launches = sum(i["kernel_launches"] for inf in inf32 for i in inf)
 
     cpu = None
     if rank == 0 and not a.no_cpu_baseline:
@@ -317,7 +331,7 @@ def gpu_arm(a):
             cpu = cpu_baseline(iters)
         except Exception as ex:       # reported, never silently replaced
             cpu = {"error": str(ex)[:200]}
-    lat = sorted(ms32)
+    lat = sorted(ms1)
 
     def pct(v, p):
         return v[min(len(v) - 1, int(math.ceil(p / 100.0 * len(v))) - 1)]
@@ -330,21 +344,25 @@ def gpu_arm(a):
         "config": {"workload": WORKLOAD, "mesh": "512x512 Q1", "substructures": "32x32 (H/h=16)",
                    "levels": 2, "tau": 10.0, "constraints": "adaptive",
                    "coefficient": "k=1e6 on random one-element channels (~10%), else 1",
-                   "rhs": "N(0,1)", "rtol": RTOL, "apply_precision": "fp32",
+                   "rhs": "N(0,1), %d per step (seed %d), solved together" % (BATCH, RHS_SEED),
+                   "batch": BATCH, "rtol": RTOL, "apply_precision": "fp32",
                    "parallelism": "replicas" if world > 1 else "single GPU",
-                   "l2": "512 MiB buffer written between timed solves (untimed)"},
-        "latency_ms": {"p50": pct(lat, 50), "p99": pct(lat, 99)},
+                   "l2": "512 MiB buffer written between timed steps (untimed)"},
+        "latency_ms": {"p50": pct(lat, 50), "p99": pct(lat, 99),
+                       "what": "one right-hand side per solve, FP32 apply"},
         "iterations": iters,
-        "compare": {"fp64_solves_per_s": world * a.steps / t64,
-                    "fp64_ms_per_solve": t64 * 1e3 / a.steps, "fp64_iterations": inf64[0]["iters"],
-                    "bf16_solves_per_s": world * len(msbf) / tbf,
-                    "bf16_iterations": infbf[0]["iters"],
-                    "mixed_over_fp64": t64 / t32},
+        "compare": {"fp64_solves_per_s": world * BATCH * len(ms64) / t64,
+                    "fp64_iterations": inf64[0][0]["iters"],
+                    "bf16_solves_per_s": world * BATCH * len(msbf) / tbf,
+                    "bf16_iterations": infbf[0][0]["iters"],
+                    "mixed_over_fp64": value / (world * BATCH * len(ms64) / t64),
+                    "single_rhs_fp32_solves_per_s": world * len(ms1) / t1,
+                    "single_rhs_fp64_solves_per_s": world * len(ms1_64) / t1_64},
         "setup_ms": setup_s * 1e3,
-        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 8 * wl.n_dof,
-                "d2h_bytes_per_step": 8 * wl.n_dof},
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 8 * wl.n_dof * BATCH,
+                "d2h_bytes_per_step": 8 * wl.n_dof * BATCH},
         "roofline": roof,
-        "kernels_fp32_apply": kern,
+        "kernels_fp32_apply_batch": kern,
         "gpu_launches": launches,
         "cpu_baseline": cpu,
         "clocks": clocks,

@@ -215,13 +215,23 @@ int bddc_operator(bddc_ctx *ctx, const double *x_dev, double *y_dev, void *strea
  * reporting.  Runs `reps` applies of r_dev (device FP64 [n]) on the
  * context's stream with CUDA events between consecutive kernels and writes
  * the mean milliseconds of each kernel to ms_out[0..k) (k <= max_out is
- * returned in *n_out).  Order: for each BDDC level from 1 down: interface
- * init, pre-correction (4)-(5), substructure correction (6)-(8); then the
+ * returned in *n_out).  Order: for each BDDC level from 1 down:
+ * pre-correction (4)-(5), substructure correction (6)-(8); then the
  * top-level solve; then for each level from the deepest up: averaging (9),
  * post-correction (10)-(11).
  */
 int bddc_profile_apply(bddc_ctx *ctx, const double *r_dev, int reps, double *ms_out, int max_out,
                        int32_t *n_out);
+
+/*
+ * bddc_profile_apply_batch - as bddc_profile_apply for the batch kernels: one
+ * apply of the nrhs <= 32 right-hand sides r_dev + k * ld (device FP64,
+ * k < nrhs) together, `reps` times; same kernel order, the top-level solve
+ * being the FP64 product with nrhs columns.  BDDC_E_STATE if the operators
+ * do not fit the batch kernels.
+ */
+int bddc_profile_apply_batch(bddc_ctx *ctx, const double *r_dev, int nrhs, int64_t ld, int reps,
+                             double *ms_out, int max_out, int32_t *n_out);
 
 /*
  * bddc_apply_noalloc - z = M^{-1} r like bddc_apply (one right-hand side),

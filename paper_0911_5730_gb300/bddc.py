@@ -26,7 +26,7 @@ SYMBOLS = ["bddc_setup", "bddc_apply", "bddc_pcg_solve", "bddc_pcg_solve_host",
            "bddc_set_precision", "bddc_query", "bddc_operator", "bddc_destroy",
            "bddc_last_error", "bddc_server_create", "bddc_submit", "bddc_wait",
            "bddc_server_destroy", "bddc_profile_apply", "bddc_apply_noalloc", "bddc_inspect",
-           "bddc_selftest_wait_timeout", "bddc_selftest_convert"]
+           "bddc_selftest_wait_timeout", "bddc_selftest_convert", "bddc_profile_apply_batch"]
 
 
 class Mesh(C.Structure):
@@ -92,6 +92,7 @@ def load():
     lib.bddc_submit.argtypes = [vp, vp, vp, i32, dp, i32, C.POINTER(C.c_uint64)]
     lib.bddc_wait.argtypes = [vp, C.c_uint64, vp, vp, C.POINTER(C.c_double), i32]
     lib.bddc_profile_apply.argtypes = [vp, vp, i32, vp, i32, C.POINTER(C.c_int32)]
+    lib.bddc_profile_apply_batch.argtypes = [vp, vp, i32, C.c_int64, i32, vp, i32, C.POINTER(C.c_int32)]
     lib.bddc_apply_noalloc.argtypes = [vp, vp, vp, vp]
     lib.bddc_selftest_wait_timeout.argtypes = [vp]
     lib.bddc_selftest_convert.argtypes = [vp, C.c_int64, C.POINTER(C.c_int64), vp]
@@ -259,6 +260,16 @@ class Problem:
         if code not in (BDDC_OK, -4):
             _check(code)
         return x, [i.as_dict() for i in infos]
+
+    def profile_apply_batch(self, R, reps=20):
+        """Mean device milliseconds of each batch-kernel of one apply of the
+        rows of R (CUDA float64 [nrhs, n], nrhs <= 32) together."""
+        R = R.contiguous()
+        out = np.zeros(64)
+        n = C.c_int32()
+        _check(self._lib.bddc_profile_apply_batch(self.h, _ptr(R), int(R.shape[0]), self.n, int(reps),
+                                                  out.ctypes.data_as(C.c_void_p), 64, C.byref(n)))
+        return out[:n.value]
 
     def profile_apply(self, r, reps=20):
         """Mean device milliseconds of each apply kernel (see bddc_profile_apply)."""

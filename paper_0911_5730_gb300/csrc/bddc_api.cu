@@ -1321,6 +1321,63 @@ int bddc_profile_apply(bddc_ctx *ctx, const double *r_dev, int reps, double *ms_
     });
 }
 
+int bddc_profile_apply_batch(bddc_ctx *ctx, const double *r_dev, int nrhs, int64_t ld, int reps,
+                             double *ms_out, int max_out, int32_t *n_out) {
+    return guarded([&]() -> int {
+        if (!ctx || !r_dev || reps < 1 || !ms_out || nrhs < 1 || nrhs > kMaxBatch)
+            throw Error(BDDC_E_ARG, "bad argument");
+        const int n = ctx->n();
+        if (ld < n) throw Error(BDDC_E_ARG, "ld < n");
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        Workspace &W = *ctx->ws;
+        if (!batch_ok(ctx, W, ctx->prec)) throw Error(BDDC_E_STATE, "operators do not fit the batch kernels");
+        BatchWs &BW = batch_ws(ctx, W);
+        const int K = nrhs;
+        set_batch_width(BW, K);
+        const int nl = (int)W.lv.size();
+        const int nseg = 2 * nl + 1 + 2 * nl;
+        if (max_out < nseg) throw Error(BDDC_E_ARG, "max_out too small");
+        cudaStream_t st = W.stream;
+        launch_b_gather(n, K, r_dev, ld, BW.r, st);
+        std::vector<cudaEvent_t> ev(3 * nl + 2 + 3 * nl);
+        for (auto &e : ev) BDDC_CUDA_TRY(cudaEventCreate(&e));
+        std::vector<double> acc(nseg, 0.0);
+        for (int rep = 0; rep < reps; ++rep) {
+            std::vector<cudaEvent_t *> down(nl), up(nl);
+            int k = 0;
+            for (int l = 0; l < nl; ++l) { down[l] = &ev[k]; k += 3; }
+            cudaEvent_t *top = &ev[k]; k += 2;
+            for (int l = 0; l < nl; ++l) { up[l] = &ev[k]; k += 3; }
+            std::vector<const double *> rin(nl);
+            rin[0] = BW.r;
+            for (int l = 0; l < nl; ++l) {
+                apply_level_pre_b(W.lv[l], BW.lv[l], ctx->prec, rin[l], nullptr, st, down[l]);
+                if (l + 1 < nl) rin[l + 1] = BW.lv[l].rcv;
+            }
+            BDDC_CUDA_TRY(cudaEventRecord(top[0], st));
+            launch_gemm_b(ctx->n_top, ctx->ld_top, ctx->Ainv, BW.lv[nl - 1].rcv, BW.lv[nl - 1].ucv, K, nullptr,
+                          ctx->err_dev, st);
+            BDDC_CUDA_TRY(cudaEventRecord(top[1], st));
+            for (int l = nl - 1; l >= 0; --l)
+                apply_level_post_b(W.lv[l], BW.lv[l], ctx->prec, rin[l], l == 0 ? BW.z : BW.lv[l - 1].ucv,
+                                   nullptr, st, up[l]);
+            BDDC_CUDA_TRY(cudaStreamSynchronize(st));
+            int seg = 0;
+            float ms;
+            for (int l = 0; l < nl; ++l)
+                for (int j = 0; j < 2; ++j) { cudaEventElapsedTime(&ms, down[l][j], down[l][j + 1]); acc[seg++] += ms; }
+            cudaEventElapsedTime(&ms, top[0], top[1]); acc[seg++] += ms;
+            for (int l = nl - 1; l >= 0; --l)
+                for (int j = 0; j < 2; ++j) { cudaEventElapsedTime(&ms, up[l][j], up[l][j + 1]); acc[seg++] += ms; }
+        }
+        for (auto &e : ev) cudaEventDestroy(e);
+        for (int i = 0; i < nseg; ++i) ms_out[i] = acc[i] / reps;
+        if (n_out) *n_out = nseg;
+        BDDC_CUDA_TRY(cudaGetLastError());
+        return BDDC_OK;
+    });
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------------------

@@ -134,9 +134,10 @@ inline bool pdl_enabled() {
     return on;
 }
 
+// Launch with (pdl) or without programmatic stream serialisation.
 template <class... KArgs, class... Args>
-inline void launch_pdl(void (*k)(KArgs...), int grid, int block, size_t smem, cudaStream_t s,
-                Args... args) {
+inline void launch_k(bool pdl, void (*k)(KArgs...), int grid, int block, size_t smem, cudaStream_t s,
+                     Args... args) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3((unsigned)block);
@@ -146,8 +147,14 @@ inline void launch_pdl(void (*k)(KArgs...), int grid, int block, size_t smem, cu
     at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
-    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    cfg.numAttrs = (pdl && pdl_enabled()) ? 1 : 0;
     cudaLaunchKernelEx(&cfg, k, args...);
+}
+
+template <class... KArgs, class... Args>
+inline void launch_pdl(void (*k)(KArgs...), int grid, int block, size_t smem, cudaStream_t s,
+                       Args... args) {
+    launch_k(true, k, grid, block, smem, s, args...);
 }
 
 

@@ -188,10 +188,11 @@ bool batch_path(const DevLevel &L, int prec);
 void prepare_batch_kernels();
 // Algorithm 1 on one level for a batch (same scratch protocol as the single
 // right-hand-side launchers, on the BatchLevel buffers).
+// ev (optional, 3 events) as for the single right-hand-side launchers.
 void apply_level_pre_b(const DevLevel &L, const BatchLevel &B, int prec, const double *r,
-                       const int *skip, cudaStream_t s);
+                       const int *skip, cudaStream_t s, cudaEvent_t *ev = nullptr);
 void apply_level_post_b(const DevLevel &L, const BatchLevel &B, int prec, const double *r, double *z,
-                        const int *skip, cudaStream_t s);
+                        const int *skip, cudaStream_t s, cudaEvent_t *ev = nullptr);
 // Y = A X for the top level (A as in launch_dense_symv; X, Y interleaved [ld][K])
 void launch_gemm_b(int n, int ld, const double *A, const double *X, double *Y, int K, const int *skip,
                    int *err, cudaStream_t s);

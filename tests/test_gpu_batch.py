@@ -157,3 +157,12 @@ def _conversion_cases():
 def test_integer_conversions_match_hardware(lib):
     vals = torch.tensor(_conversion_cases(), device="cuda")
     assert lib.selftest_convert(vals) == 0
+
+
+def test_profile_apply_batch(lib):
+    wl = WL["channels_64"]
+    P = lib.Problem.from_workload(wl)
+    R = torch.tensor(inputs.normal_rhs(wl.n_dof, 61, 8), device="cuda")
+    ms = P.profile_apply_batch(R, reps=3)
+    assert len(ms) == 5 and all(t > 0 for t in ms)       # pre, neumann, top, average, post
+    P.close()
