@@ -86,7 +86,8 @@ template <class T, class ACC, int BP> struct DirSmemB {
     static size_t bytes(const DevLevel &L) {
         return al16(sizeof(T) * (size_t)L.max_fac) + al16(sizeof(ACC) * (size_t)L.max_m * BP * 32) +
                al16(sizeof(ACC) * (size_t)(L.max_nG > 0 ? L.max_nG : 1) * 32) + al16((size_t)L.max_irec) +
-               al16(sizeof(ACC) * (size_t)(L.max_coo > 0 ? L.max_coo : 1)) + 8 * (kChunksB + 1) + 16;
+               al16(sizeof(ACC) * (size_t)(L.max_coo > 0 ? L.max_coo : 1)) + al16(8 * 32 * kDW + 16) +
+               8 * (kChunksB + 1) + 16;
     }
 };
 
@@ -96,7 +97,7 @@ template <class T, class ACC, int BP> struct DirSmemB {
 // triangular (zeros stored above the diagonal).
 template <class T, class ACC, int BP, bool POST>
 __global__ void __launch_bounds__(32 * kDW) k_dir_b(DevLevel L, BatchLevel B, const double *r, double *z,
-                                                    const int *skip) {
+                                                    const int *skip, RzBatch rz) {
     constexpr int BB = BP * BP, RPL = BP / 4;
     extern __shared__ __align__(16) unsigned char smem_b[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -109,6 +110,9 @@ __global__ void __launch_bounds__(32 * kDW) k_dir_b(DevLevel L, BatchLevel B, co
     ACC *vG = reinterpret_cast<ACC *>(p);   p += al16(sizeof(ACC) * (size_t)(L.max_nG > 0 ? L.max_nG : 1) * 32);
     unsigned char *rec = p;                 p += al16((size_t)L.max_irec);
     ACC *cvs = reinterpret_cast<ACC *>(p);  p += al16(sizeof(ACC) * (size_t)(L.max_coo > 0 ? L.max_coo : 1));
+    double *red = reinterpret_cast<double *>(p);   // [kDW][32] partials and a flag word
+    int *flag = reinterpret_cast<int *>(red + 32 * kDW);
+    p += al16(8 * 32 * kDW + 16);
     unsigned long long *bars = reinterpret_cast<unsigned long long *>(p);   // kChunksB factor + 1 record
 
     const int nI = L.nI[sub], nG = L.nG[sub], m = L.nblk[sub];
@@ -322,11 +326,60 @@ __global__ void __launch_bounds__(32 * kDW) k_dir_b(DevLevel L, BatchLevel B, co
                 if (v != (ACC)0) atomicAdd(&B.rB[(int64_t)gGi[q] * K + lane], -to_f64(v));
             }
         }
-    } else if (act) {
-        for (int i = warp; i < nI; i += kDW) z[(int64_t)gI[i] * K + lane] = to_f64(xs[i * 32 + lane]);
-        for (int e = warp; e < nown; e += kDW) {
-            const int owp = gO[2 * e], owd = gO[2 * e + 1];
-            z[(int64_t)owd * K + lane] = to_f64(vG[owp * 32 + lane]);
+    } else {
+        double acc = 0.0;   // r.z over the entries of z this substructure writes
+        if (act) {
+            for (int i = warp; i < nI; i += kDW) {
+                const int64_t e = (int64_t)gI[i] * K + lane;
+                const double zv = to_f64(xs[i * 32 + lane]);
+                z[e] = zv;
+                if (rz.sc) acc = fma(r[e], zv, acc);
+            }
+            for (int e = warp; e < nown; e += kDW) {
+                const int owp = gO[2 * e];
+                const int64_t o = (int64_t)gO[2 * e + 1] * K + lane;
+                const double zv = to_f64(vG[owp * 32 + lane]);
+                z[o] = zv;
+                if (rz.sc) acc = fma(r[o], zv, acc);
+            }
+        }
+        if (rz.sc) {
+            // every entry of z is written once, by its owner: per-substructure
+            // partials, summed over the substructures in a fixed order by the
+            // block that finishes last
+            red[warp * 32 + lane] = acc;
+            __syncthreads();
+            if (warp == 0) {
+                double t = 0.0;
+#pragma unroll
+                for (int w = 0; w < kDW; ++w) t += red[w * 32 + lane];
+                if (act) rz.part[(int64_t)sub * K + lane] = t;
+                __threadfence();
+            }
+            __syncthreads();
+            if (tid == 0) *flag = atomicAdd(rz.counter, 1u) == (unsigned)L.nsub - 1u;
+            __syncthreads();
+            if (!*flag) return;
+            __threadfence();
+            double t = 0.0;
+            if (act)
+                for (int sb = warp; sb < L.nsub; sb += kDW) t += __ldcg(&rz.part[(int64_t)sb * K + lane]);
+            red[warp * 32 + lane] = t;
+            __syncthreads();
+            if (warp == 0 && act) {
+                double tot = 0.0;
+#pragma unroll
+                for (int w = 0; w < kDW; ++w) tot += red[w * 32 + lane];
+                BatchScalars *sc = rz.sc;
+                if (!sc->done[lane]) {
+                    const double beta = sc->fresh[lane] ? 0.0 : tot / sc->rho[lane];
+                    sc->fresh[lane] = 0;
+                    sc->beta[lane] = beta;
+                    if (sc->it[lane] > 0) rz.betas[(int64_t)(sc->it[lane] - 1) * K + lane] = beta;
+                    sc->rho[lane] = tot;
+                }
+            }
+            if (tid == 0) *rz.counter = 0u;
         }
     }
 }
@@ -579,10 +632,21 @@ __device__ void grid_reduce_k(double v, int K, double *part, unsigned *counter, 
     if (!last) return;
     __threadfence();
     // thread t sums blocks b = t / K, t / K + per, ... of right-hand side t % K
+    // (four independent partial sums, added in a fixed order)
     double s = 0.0;
-    if ((int)threadIdx.x < per * K)
-        for (unsigned b = threadIdx.x / K; b < gridDim.x; b += per)
-            s += __ldcg(&part[(int64_t)b * K + threadIdx.x % K]);
+    if ((int)threadIdx.x < per * K) {
+        const int kk = threadIdx.x % K;
+        double s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        unsigned b = threadIdx.x / K;
+        for (; b + 3 * per < gridDim.x; b += 4 * per) {
+            s += __ldcg(&part[(int64_t)b * K + kk]);
+            s1 += __ldcg(&part[(int64_t)(b + per) * K + kk]);
+            s2 += __ldcg(&part[(int64_t)(b + 2 * per) * K + kk]);
+            s3 += __ldcg(&part[(int64_t)(b + 3 * per) * K + kk]);
+        }
+        for (; b < gridDim.x; b += per) s += __ldcg(&part[(int64_t)b * K + kk]);
+        s = (s + s1) + (s2 + s3);
+    }
     red[threadIdx.x] = s;
     __syncthreads();
     if (threadIdx.x < K) {
@@ -622,53 +686,86 @@ __global__ void k_b_init(int n, int K, const double *b, int64_t ldb, double *x, 
             sc->done[kk] = tot == 0.0 ? 1 : 0;
         },
         [&]() {
-            sc->K = K; sc->maxit = maxit;
+            sc->K = K; sc->maxit = maxit; sc->step = 0;
             int all = 1;
             for (int kk = 0; kk < K; ++kk) all &= sc->done[kk];
             sc->all_done = all;
         });
 }
 
-// p = z + beta p for the right-hand sides still iterating
-__global__ void k_b_dir(int64_t nK, int K, const double *__restrict__ z, double *__restrict__ p,
-                        const BatchScalars *sc) {
-    pdl_wait();
-    pdl_trigger();
-    if (sc->all_done) return;
-    const int k = threadIdx.x % K;
-    if (sc->done[k]) return;
-    const double bt = sc->beta[k];
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nK; e += (int64_t)gridDim.x * blockDim.x)
-        p[e] = fma(bt, p[e], z[e]);
-}
+// First half of a batched PCG iteration: p_new = z + beta p_old, q = A p_new
+// and alpha_k = rho_k / (p_new . q).  A block owns a BT_X x BT_Y tile of nodes
+// for all K right-hand sides; p_new is formed once per entry of the tile and
+// its halo in shared memory (the FP64 pipe is the limit), from p_old in one
+// direction buffer, and written to the other.
+constexpr int BT_X = 32, BT_Y = 8;
+constexpr size_t bt_smem(int K) { return (size_t)(BT_Y + 2) * (BT_X + 2) * K * 8; }
 
-// q = A p (matrix-free Q1 stencil), pq_k, alpha_k = rho_k / pq_k
-__global__ void k_b_spmv_dot(int nx, int K, const double *__restrict__ w, const double *__restrict__ p,
-                             double *__restrict__ q, double *part, unsigned *counter, BatchScalars *sc,
-                             double *alphas) {
+__global__ void k_b_dir_spmv(int nx, int K, const double *__restrict__ w, const double *__restrict__ z,
+                             double *p0, double *p1, double *__restrict__ q, double *part,
+                             unsigned *counter, BatchScalars *sc, double *alphas) {
+    extern __shared__ __align__(16) double ps[];     // [(BT_Y + 2) * (BT_X + 2)][K]
     pdl_wait();
     pdl_trigger();
     if (sc->all_done) return;
-    const int k = threadIdx.x % K;
     const int n1 = nx - 1;
     const int n = n1 * n1;
-    const int64_t nK = (int64_t)n * K;
+    const int tiles_x = (n1 + BT_X - 1) / BT_X;
+    const int i0 = (blockIdx.x % tiles_x) * BT_X, j0 = (blockIdx.x / tiles_x) * BT_Y;
+    const bool odd = sc->step & 1;
+    const double *po = odd ? p1 : p0;
+    double *pn = odd ? p0 : p1;
+    constexpr int HX = BT_X + 2;
+    const int tot = (BT_Y + 2) * HX * K;
+    // eight entries per thread in flight: the loads of one round are independent
+    for (int e0 = threadIdx.x; e0 < tot; e0 += 8 * blockDim.x) {
+        double a[8], b[8], bt[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = e0 + u * blockDim.x;
+            a[u] = 0.0; b[u] = 0.0; bt[u] = 0.0;
+            if (e < tot) {
+                const int hn = e / K, kk = e - hn * K;
+                const int hy = hn / HX, hx = hn - hy * HX;
+                const int i = i0 + hx - 1, j = j0 + hy - 1;
+                if (i >= 0 && i < n1 && j >= 0 && j < n1) {
+                    const int64_t g = (int64_t)(j * n1 + i) * K + kk;
+                    a[u] = po[g]; b[u] = z[g]; bt[u] = sc->beta[kk];
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = e0 + u * blockDim.x;
+            if (e < tot) ps[e] = fma(bt[u], a[u], b[u]);
+        }
+    }
+    __syncthreads();
+    const int k = threadIdx.x % K;
+    const int per = blockDim.x / K;
+    const bool live = !sc->done[k];
     double s = 0.0;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nK; e += (int64_t)gridDim.x * blockDim.x) {
-        const int g = (int)(e / K);
-        const int jj = g / n1, ii = g - jj * n1;
-        const bool W = ii > 0, E = ii < n1 - 1, S = jj > 0, N = jj < n1 - 1;
-        auto P = [&](int gg) { return p[(int64_t)gg * K + k]; };
-        const double pc = P(g);
+#pragma unroll 4
+    for (int ln = threadIdx.x / K; ln < BT_X * BT_Y; ln += per) {
+        const int lx = ln % BT_X, ly = ln / BT_X;
+        const int i = i0 + lx, j = j0 + ly;
+        if (i >= n1 || j >= n1) continue;
+        const int g = j * n1 + i;
+        const bool W = i > 0, E = i < n1 - 1, S = j > 0, N = j < n1 - 1;
+        const double *c = ps + ((ly + 1) * HX + lx + 1) * K + k;
+        // neighbours outside the domain hold zero in ps; their weights are not read
+        const double pc = c[0];
         double v = w[g] * pc;
-        if (E) v = fma(w[n + g], P(g + 1), v);
-        if (N) v = fma(w[2 * n + g], P(g + n1), v);
-        if (N && E) v = fma(w[3 * n + g], P(g + n1 + 1), v);
-        if (N && W) v = fma(w[4 * n + g], P(g + n1 - 1), v);
-        if (W) v = fma(w[n + g - 1], P(g - 1), v);
-        if (S) v = fma(w[2 * n + g - n1], P(g - n1), v);
-        if (S && W) v = fma(w[3 * n + g - n1 - 1], P(g - n1 - 1), v);
-        if (S && E) v = fma(w[4 * n + g - n1 + 1], P(g - n1 + 1), v);
+        if (E) v = fma(w[n + g], c[K], v);
+        if (N) v = fma(w[2 * n + g], c[HX * K], v);
+        if (N && E) v = fma(w[3 * n + g], c[(HX + 1) * K], v);
+        if (N && W) v = fma(w[4 * n + g], c[(HX - 1) * K], v);
+        if (W) v = fma(w[n + g - 1], c[-K], v);
+        if (S) v = fma(w[2 * n + g - n1], c[-HX * K], v);
+        if (S && W) v = fma(w[3 * n + g - n1 - 1], c[-(HX + 1) * K], v);
+        if (S && E) v = fma(w[4 * n + g - n1 + 1], c[-(HX - 1) * K], v);
+        const int64_t e = (int64_t)g * K + k;
+        if (live) pn[e] = pc;
         q[e] = v;
         s = fma(v, pc, s);
     }
@@ -683,11 +780,12 @@ __global__ void k_b_spmv_dot(int nx, int K, const double *__restrict__ w, const 
 
 // x += alpha p; r -= alpha q; rr_k; convergence; it_k += 1
 __global__ void k_b_update(int64_t nK, int K, double *__restrict__ x, double *__restrict__ r,
-                           const double *__restrict__ p, const double *__restrict__ q, double *part,
-                           unsigned *counter, BatchScalars *sc) {
+                           const double *p0, const double *p1, const double *__restrict__ q,
+                           double *part, unsigned *counter, BatchScalars *sc) {
     pdl_wait();
     pdl_trigger();
     if (sc->all_done) return;
+    const double *__restrict__ p = (sc->step & 1) ? p0 : p1;   // p_new of this step
     const int k = threadIdx.x % K;
     const bool live = !sc->done[k];
     const double a = sc->alpha[k];
@@ -712,28 +810,8 @@ __global__ void k_b_update(int64_t nK, int K, double *__restrict__ x, double *__
             int all = 1;
             for (int kk = 0; kk < K; ++kk) all &= sc->done[kk];
             sc->all_done = all;
+            sc->step += 1;   // every block has read step before the last one gets here
         });
-}
-
-// rho_k = r.z, beta_k (0 on a fresh start)
-__global__ void k_b_rz(int64_t nK, int K, const double *__restrict__ r, const double *__restrict__ z,
-                       double *part, unsigned *counter, BatchScalars *sc, double *betas) {
-    pdl_wait();
-    pdl_trigger();
-    if (sc->all_done) return;
-    const int k = threadIdx.x % K;
-    double s = 0.0;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nK; e += (int64_t)gridDim.x * blockDim.x)
-        s = fma(r[e], z[e], s);
-    grid_reduce_k(s, K, part, counter,
-        [&](int kk, double tot) {
-            if (sc->done[kk]) return;
-            const double beta = sc->fresh[kk] ? 0.0 : tot / sc->rho[kk];
-            sc->fresh[kk] = 0;
-            sc->beta[kk] = beta;
-            if (sc->it[kk] > 0) betas[(int64_t)(sc->it[kk] - 1) * K + kk] = beta;
-            sc->rho[kk] = tot;
-        }, NoPost{});
 }
 
 // res = b - A x (b in the caller's layout, column k at b + k * ldb)
@@ -835,18 +913,19 @@ int pidx_b(int prec) { return prec == BDDC_PREC_FP64 ? 0 : (prec == BDDC_PREC_FP
 
 template <class T, class ACC, int BP>
 void dir_b_launch(const DevLevel &L, const BatchLevel &B, bool post, const double *r, double *z,
-                  const int *skip, cudaStream_t s) {
+                  const int *skip, cudaStream_t s, const RzBatch *rz) {
     const size_t sm = DirSmemB<T, ACC, BP>::bytes(L);
-    if (!post) launch_plain(k_dir_b<T, ACC, BP, false>, L.nsub, 32 * kDW, sm, s, L, B, r, z, skip);
-    else launch_plain(k_dir_b<T, ACC, BP, true>, L.nsub, 32 * kDW, sm, s, L, B, r, z, skip);
+    const RzBatch none{nullptr, nullptr, nullptr, nullptr};
+    if (!post) launch_plain(k_dir_b<T, ACC, BP, false>, L.nsub, 32 * kDW, sm, s, L, B, r, z, skip, none);
+    else launch_plain(k_dir_b<T, ACC, BP, true>, L.nsub, 32 * kDW, sm, s, L, B, r, z, skip, rz ? *rz : none);
 }
 
 template <class T, class ACC>
 void dir_b(const DevLevel &L, const BatchLevel &B, bool post, const double *r, double *z,
-           const int *skip, cudaStream_t s) {
-    if (L.bp == 8) dir_b_launch<T, ACC, 8>(L, B, post, r, z, skip, s);
-    else if (L.bp == 16) dir_b_launch<T, ACC, 16>(L, B, post, r, z, skip, s);
-    else dir_b_launch<T, ACC, 32>(L, B, post, r, z, skip, s);
+           const int *skip, cudaStream_t s, const RzBatch *rz = nullptr) {
+    if (L.bp == 8) dir_b_launch<T, ACC, 8>(L, B, post, r, z, skip, s, rz);
+    else if (L.bp == 16) dir_b_launch<T, ACC, 16>(L, B, post, r, z, skip, s, rz);
+    else dir_b_launch<T, ACC, 32>(L, B, post, r, z, skip, s, rz);
 }
 
 template <class T, class ACC>
@@ -910,7 +989,9 @@ void prepare_batch_kernels() {
     BDDC_DIR_B(__nv_bfloat16, float, 8) BDDC_DIR_B(__nv_bfloat16, float, 16) BDDC_DIR_B(__nv_bfloat16, float, 32)
     BDDC_SMEM_ATTR_B((k_neu_b<double, double>)); BDDC_SMEM_ATTR_B((k_neu_b<float, float>));
     BDDC_SMEM_ATTR_B((k_neu_b<__nv_bfloat16, float>));
-    // (k_gemm_b also has static shared memory: its dynamic limit is its own size)
+    // (k_gemm_b and k_b_dir_spmv also have static shared memory: their
+    // dynamic limits are their own sizes)
+    cudaFuncSetAttribute(k_b_dir_spmv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bt_smem(kMaxBatch));
     cudaFuncSetAttribute(k_gemm_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(GM_S * GM_STAGE));
     BDDC_SMEM_ATTR_B((k_avg_b<double, double>)); BDDC_SMEM_ATTR_B((k_avg_b<float, float>));
     BDDC_SMEM_ATTR_B((k_avg_b<__nv_bfloat16, float>));
@@ -932,15 +1013,15 @@ void apply_level_pre_b(const DevLevel &L, const BatchLevel &B, int prec, const d
 }
 
 void apply_level_post_b(const DevLevel &L, const BatchLevel &B, int prec, const double *r, double *z,
-                        const int *skip, cudaStream_t s, cudaEvent_t *ev) {
+                        const int *skip, cudaStream_t s, cudaEvent_t *ev, const RzBatch *rz) {
     if (ev) cudaEventRecord(ev[0], s);
     if (prec == BDDC_PREC_FP64) avg_b<double, double>(L, B, prec, skip, s);
     else if (prec == BDDC_PREC_FP32) avg_b<float, float>(L, B, prec, skip, s);
     else avg_b<__nv_bfloat16, float>(L, B, prec, skip, s);
     if (ev) cudaEventRecord(ev[1], s);
-    if (prec == BDDC_PREC_FP64) dir_b<double, double>(L, B, true, r, z, skip, s);
-    else if (prec == BDDC_PREC_FP32) dir_b<float, float>(L, B, true, r, z, skip, s);
-    else dir_b<__nv_bfloat16, float>(L, B, true, r, z, skip, s);
+    if (prec == BDDC_PREC_FP64) dir_b<double, double>(L, B, true, r, z, skip, s, rz);
+    else if (prec == BDDC_PREC_FP32) dir_b<float, float>(L, B, true, r, z, skip, s, rz);
+    else dir_b<__nv_bfloat16, float>(L, B, true, r, z, skip, s, rz);
     if (ev) cudaEventRecord(ev[2], s);
 }
 
@@ -956,24 +1037,20 @@ void launch_b_init(int n, int K, const double *b, int64_t ldb, double *x, double
     const int64_t nK = (int64_t)n * K;
     k_b_init<<<vgrid_b(nK, K), bblock(K), 0, s>>>(n, K, b, ldb, x, r, p, part, counter, sc, tol, maxit);
 }
-void launch_b_dir(int n, int K, const double *z, double *p, const BatchScalars *sc, cudaStream_t s) {
-    const int64_t nK = (int64_t)n * K;
-    launch_plain(k_b_dir, vgrid_b(nK, K), bblock(K), 0, s, nK, K, z, p, sc);
+int launch_b_dir_spmv_blocks(int nx) {
+    const int n1 = nx - 1;
+    return ((n1 + BT_X - 1) / BT_X) * ((n1 + BT_Y - 1) / BT_Y);
 }
-void launch_b_spmv_dot(int nx, int K, const double *w, const double *p, double *q, double *part,
-                       unsigned *counter, BatchScalars *sc, double *alphas, cudaStream_t s) {
-    const int64_t nK = (int64_t)(nx - 1) * (nx - 1) * K;
-    launch_plain(k_b_spmv_dot, vgrid_b(nK, K), bblock(K), 0, s, nx, K, w, p, q, part, counter, sc, alphas);
+void launch_b_dir_spmv(int nx, int K, const double *w, const double *z, double *p0, double *p1,
+                       double *q, double *part, unsigned *counter, BatchScalars *sc, double *alphas,
+                       cudaStream_t s) {
+    launch_plain(k_b_dir_spmv, launch_b_dir_spmv_blocks(nx), bblock(K), bt_smem(K), s, nx, K, w, z, p0, p1,
+                 q, part, counter, sc, alphas);
 }
-void launch_b_update(int n, int K, double *x, double *r, const double *p, const double *q,
-                     double *part, unsigned *counter, BatchScalars *sc, cudaStream_t s) {
+void launch_b_update(int n, int K, double *x, double *r, const double *p0, const double *p1,
+                     const double *q, double *part, unsigned *counter, BatchScalars *sc, cudaStream_t s) {
     const int64_t nK = (int64_t)n * K;
-    launch_plain(k_b_update, vgrid_b(nK, K), bblock(K), 0, s, nK, K, x, r, p, q, part, counter, sc);
-}
-void launch_b_rz(int n, int K, const double *r, const double *z, double *part, unsigned *counter,
-                 BatchScalars *sc, double *betas, cudaStream_t s) {
-    const int64_t nK = (int64_t)n * K;
-    launch_plain(k_b_rz, vgrid_b(nK, K), bblock(K), 0, s, nK, K, r, z, part, counter, sc, betas);
+    launch_plain(k_b_update, vgrid_b(nK, K), bblock(K), 0, s, nK, K, x, r, p0, p1, q, part, counter, sc);
 }
 void launch_b_residual(int nx, int K, const double *w, const double *b, int64_t ldb, const double *x,
                        double *res, cudaStream_t s) {

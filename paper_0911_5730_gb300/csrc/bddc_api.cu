@@ -64,9 +64,11 @@ struct LevelData {
 struct BatchWs {
     std::vector<BatchLevel> lv;
     double *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *tmp = nullptr;
+    double *p1 = nullptr;                      // second direction buffer (p is the first)
     double *bcol = nullptr, *xcol = nullptr;   // caller-layout staging for host buffers
     double *part = nullptr, *alphas = nullptr, *betas = nullptr, *nrm = nullptr;
-    unsigned *counter = nullptr;
+    double *rzpart = nullptr;            // [nsub of level 1][32] r.z partials
+    unsigned *counter = nullptr, *rzcounter = nullptr;
     BatchScalars *sc = nullptr;
     BatchScalars *hsc = nullptr;         // pinned mirror
     double *hnrm = nullptr;              // pinned
@@ -780,10 +782,15 @@ BatchWs &batch_ws(bddc_ctx *C, Workspace &W) {
     bw->x = A.alloc_n<double>(n * KB); bw->r = A.alloc_n<double>(n * KB);
     bw->z = A.alloc_n<double>(n * KB); bw->p = A.alloc_n<double>(n * KB);
     bw->q = A.alloc_n<double>(n * KB); bw->tmp = A.alloc_n<double>(n * KB);
+    bw->p1 = A.alloc_n<double>(n * KB);
+    BDDC_CUDA_TRY(cudaMemset(bw->p1, 0, sizeof(double) * n * KB));
     bw->bcol = A.alloc_n<double>(n * KB); bw->xcol = A.alloc_n<double>(n * KB);
-    bw->part = A.alloc_n<double>(1216 * KB + 64);
+    bw->part = A.alloc_n<double>((int64_t)std::max(1216, launch_b_dir_spmv_blocks(C->nx)) * KB + 64);
     bw->counter = A.alloc_n<unsigned>(4);
     BDDC_CUDA_TRY(cudaMemset(bw->counter, 0, 4 * sizeof(unsigned)));
+    bw->rzpart = A.alloc_n<double>((int64_t)std::max(W.lv.empty() ? 1 : W.lv[0].nsub, 1) * KB);
+    bw->rzcounter = A.alloc_n<unsigned>(4);
+    BDDC_CUDA_TRY(cudaMemset(bw->rzcounter, 0, 4 * sizeof(unsigned)));
     bw->sc = A.alloc_n<BatchScalars>(1);
     BDDC_CUDA_TRY(cudaMemset(bw->sc, 0, sizeof(BatchScalars)));
     bw->alphas = A.alloc_n<double>((int64_t)(W.maxit_cap + 1) * KB);
@@ -796,7 +803,7 @@ BatchWs &batch_ws(bddc_ctx *C, Workspace &W) {
 }
 
 void apply_b_rec(bddc_ctx *C, Workspace &W, BatchWs &BW, int l, int prec, const double *r, double *z,
-                 const int *skip, cudaStream_t st) {
+                 const int *skip, cudaStream_t st, const RzBatch *rz = nullptr) {
     const DevLevel &D = W.lv[l];
     const BatchLevel &B = BW.lv[l];
     apply_level_pre_b(D, B, prec, r, skip, st);
@@ -804,7 +811,7 @@ void apply_b_rec(bddc_ctx *C, Workspace &W, BatchWs &BW, int l, int prec, const 
         launch_gemm_b(C->n_top, C->ld_top, C->Ainv, B.rcv, B.ucv, B.K, skip, C->err_dev, st);
     else
         apply_b_rec(C, W, BW, l + 1, prec, B.rcv, B.ucv, skip, st);
-    apply_level_post_b(D, B, prec, r, z, skip, st);
+    apply_level_post_b(D, B, prec, r, z, skip, st, nullptr, rz);
 }
 
 void set_batch_width(BatchWs &BW, int K) {
@@ -819,11 +826,10 @@ cudaGraphExec_t batch_graph(bddc_ctx *C, Workspace &W, BatchWs &BW, int prec, in
     cudaStream_t st = W.stream;
     cudaGraph_t g;
     BDDC_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    launch_b_dir(n, K, BW.z, BW.p, BW.sc, st);
-    launch_b_spmv_dot(C->nx, K, C->w_dev, BW.p, BW.q, BW.part, BW.counter, BW.sc, BW.alphas, st);
-    launch_b_update(n, K, BW.x, BW.r, BW.p, BW.q, BW.part, BW.counter, BW.sc, st);
-    apply_b_rec(C, W, BW, 0, prec, BW.r, BW.z, &BW.sc->all_done, st);
-    launch_b_rz(n, K, BW.r, BW.z, BW.part, BW.counter, BW.sc, BW.betas, st);
+    launch_b_dir_spmv(C->nx, K, C->w_dev, BW.z, BW.p, BW.p1, BW.q, BW.part, BW.counter, BW.sc, BW.alphas, st);
+    launch_b_update(n, K, BW.x, BW.r, BW.p, BW.p1, BW.q, BW.part, BW.counter, BW.sc, st);
+    const RzBatch rz{BW.rzpart, BW.rzcounter, BW.sc, BW.betas};
+    apply_b_rec(C, W, BW, 0, prec, BW.r, BW.z, &BW.sc->all_done, st, &rz);
     BDDC_CUDA_TRY(cudaStreamEndCapture(st, &g));
     cudaGraphExec_t ge;
     BDDC_CUDA_TRY(cudaGraphInstantiate(&ge, g, 0));
@@ -843,17 +849,18 @@ int pcg_batch(bddc_ctx *C, Workspace &W, int prec, const double *b, int64_t ldb,
     cudaStream_t st = W.stream;
     if (maxit > W.maxit_cap) maxit = W.maxit_cap;
     set_batch_width(BW, K);
+    const RzBatch rz{BW.rzpart, BW.rzcounter, BW.sc, BW.betas};
     launch_b_init(n, K, b, ldb, BW.x, BW.r, BW.p, BW.part, BW.counter, BW.sc, rtol, maxit, st);
-    apply_b_rec(C, W, BW, 0, prec, BW.r, BW.z, &BW.sc->all_done, st);
-    launch_b_rz(n, K, BW.r, BW.z, BW.part, BW.counter, BW.sc, BW.betas, st);
+    BDDC_CUDA_TRY(cudaMemsetAsync(BW.rzcounter, 0, sizeof(unsigned), st));
+    apply_b_rec(C, W, BW, 0, prec, BW.r, BW.z, &BW.sc->all_done, st, &rz);
     cudaGraphExec_t g = batch_graph(C, W, BW, prec, K);
     const int per_apply = 4 * (int)W.lv.size() + 1;
-    int launches = 2 + per_apply;
+    int launches = 1 + per_apply;
     int chunk = BW.last_iters > 1 ? std::min(BW.last_iters, 256) : 4;
     BatchScalars &h = *BW.hsc;
     for (;;) {
         for (int k = 0; k < chunk; ++k) BDDC_CUDA_TRY(cudaGraphLaunch(g, st));
-        launches += chunk * (4 + per_apply);
+        launches += chunk * (2 + per_apply);
         BDDC_CUDA_TRY(cudaMemcpyAsync(BW.hsc, BW.sc, sizeof(BatchScalars), cudaMemcpyDeviceToHost, st));
         BDDC_CUDA_TRY(cudaStreamSynchronize(st));
         if (!h.all_done) { chunk = std::max(1, std::min(chunk / 2, 16)); continue; }
@@ -876,9 +883,8 @@ int pcg_batch(bddc_ctx *C, Workspace &W, int prec, const double *b, int64_t ldb,
         h.all_done = 0;
         BDDC_CUDA_TRY(cudaMemcpyAsync(BW.sc, BW.hsc, sizeof(BatchScalars), cudaMemcpyHostToDevice, st));
         launch_b_restart(n, K, BW.tmp, BW.r, BW.sc, st);
-        apply_b_rec(C, W, BW, 0, prec, BW.r, BW.z, &BW.sc->all_done, st);
-        launch_b_rz(n, K, BW.r, BW.z, BW.part, BW.counter, BW.sc, BW.betas, st);
-        launches += 2 + per_apply;
+        apply_b_rec(C, W, BW, 0, prec, BW.r, BW.z, &BW.sc->all_done, st, &rz);
+        launches += 1 + per_apply;
         chunk = 1;
     }
     int kmax = 0;

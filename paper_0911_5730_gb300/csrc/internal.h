@@ -181,7 +181,16 @@ struct BatchScalars {
     double rho[kMaxBatch], pq[kMaxBatch], alpha[kMaxBatch], beta[kMaxBatch], rr[kMaxBatch],
         bb[kMaxBatch], tol2[kMaxBatch];
     int it[kMaxBatch], done[kMaxBatch], conv[kMaxBatch], fresh[kMaxBatch];
-    int K, maxit, all_done, pad_;
+    int K, maxit, all_done;
+    int step;      // lockstep iterations run (selects the direction buffer)
+};
+// r.z of the batched PCG, reduced by the level-1 post-correction as it writes
+// z: part holds [nsub][K] partials, counter is zero between launches.
+struct RzBatch {
+    double *part;
+    unsigned *counter;
+    BatchScalars *sc;
+    double *betas;
 };
 // Whether a level's operators fit the batched kernels' shared-memory slices.
 bool batch_path(const DevLevel &L, int prec);
@@ -191,22 +200,28 @@ void prepare_batch_kernels();
 // ev (optional, 3 events) as for the single right-hand-side launchers.
 void apply_level_pre_b(const DevLevel &L, const BatchLevel &B, int prec, const double *r,
                        const int *skip, cudaStream_t s, cudaEvent_t *ev = nullptr);
+// With rz (level 1 only): rho_k = r_k.z_k and beta_k as well.
 void apply_level_post_b(const DevLevel &L, const BatchLevel &B, int prec, const double *r, double *z,
-                        const int *skip, cudaStream_t s, cudaEvent_t *ev = nullptr);
+                        const int *skip, cudaStream_t s, cudaEvent_t *ev = nullptr,
+                        const RzBatch *rz = nullptr);
 // Y = A X for the top level (A as in launch_dense_symv; X, Y interleaved [ld][K])
 void launch_gemm_b(int n, int ld, const double *A, const double *X, double *Y, int K, const int *skip,
                    int *err, cudaStream_t s);
 // PCG for a batch; b in the caller's layout (column k at b + k * ldb)
-void launch_b_init(int n, int K, const double *b, int64_t ldb, double *x, double *r, double *p,
+// x = 0, r = b, p0 = 0, per-right-hand-side scalars, step = 0
+void launch_b_init(int n, int K, const double *b, int64_t ldb, double *x, double *r, double *p0,
                    double *part, unsigned *counter, BatchScalars *sc, double tol, int maxit,
                    cudaStream_t s);
-void launch_b_dir(int n, int K, const double *z, double *p, const BatchScalars *sc, cudaStream_t s);
-void launch_b_spmv_dot(int nx, int K, const double *w, const double *p, double *q, double *part,
-                       unsigned *counter, BatchScalars *sc, double *alphas, cudaStream_t s);
-void launch_b_update(int n, int K, double *x, double *r, const double *p, const double *q,
-                     double *part, unsigned *counter, BatchScalars *sc, cudaStream_t s);
-void launch_b_rz(int n, int K, const double *r, const double *z, double *part, unsigned *counter,
-                 BatchScalars *sc, double *betas, cudaStream_t s);
+// First half of an iteration: p_new = z + beta p_old (directions alternate
+// between p0 and p1 by sc->step), q = A p_new, alpha = rho / (p_new . q).
+// part must hold launch_b_dir_spmv_blocks(nx) * K doubles.
+int launch_b_dir_spmv_blocks(int nx);
+void launch_b_dir_spmv(int nx, int K, const double *w, const double *z, double *p0, double *p1,
+                       double *q, double *part, unsigned *counter, BatchScalars *sc, double *alphas,
+                       cudaStream_t s);
+// x += alpha p_new; r -= alpha q; rr; convergence; step += 1
+void launch_b_update(int n, int K, double *x, double *r, const double *p0, const double *p1,
+                     const double *q, double *part, unsigned *counter, BatchScalars *sc, cudaStream_t s);
 void launch_b_residual(int nx, int K, const double *w, const double *b, int64_t ldb, const double *x,
                        double *res, cudaStream_t s);
 void launch_b_norm2(int n, int K, const double *v, double *part, unsigned *counter, double *out,

@@ -126,7 +126,9 @@ def test_batch_host_buffers(lib):
     Xd, infd = P.solve(torch.tensor(B, device="cuda"))
     for j in range(4):
         assert infh[j]["iters"] == infd[j]["iters"]
-        assert _relerr(Xh[j], Xd[j].cpu().numpy()) == 0.0
+        # FP64 atomics where three or more substructures meet add in
+        # scheduling order, so two runs agree to rounding, not bit for bit
+        assert _relerr(Xh[j], Xd[j].cpu().numpy()) <= 1e-12
     P.close()
 
 
