@@ -19,11 +19,17 @@ namespace bddc {
 
 namespace {
 
+// Entry (r, c) of a stored b x b block sits at c * b + r, or at c * b + (r ^ c)
+// when the level's blocks are XOR-swizzled (a common power-of-two b).
+__device__ __forceinline__ int64_t fpos(int r, int c, int b, bool swz) {
+    return (int64_t)c * b + (swz ? (r ^ c) : r);
+}
+
 // Interior solve with the block factor of one substructure; x holds the
 // right-hand side on entry (m*b entries, padding zero) and the solution on
 // exit; tmp has b entries.
 template <class T, class ACC>
-__device__ void dirichlet_solve(const T *F, int b, int m, ACC *x, ACC *tmp) {
+__device__ void dirichlet_solve(const T *F, int b, int m, bool swz, ACC *x, ACC *tmp) {
     const int bb = b * b;
     for (int j = 0; j < m; ++j) {
         const T *Linv = F + (int64_t)j * 2 * bb;
@@ -32,14 +38,14 @@ __device__ void dirichlet_solve(const T *F, int b, int m, ACC *x, ACC *tmp) {
             ACC t = x[j * b + r];
             if (j > 0) {
                 const ACC *xp = x + (j - 1) * b;
-                for (int c = 0; c < b; ++c) t -= ld<T, ACC>(Lsub + c * b + r) * xp[c];
+                for (int c = 0; c < b; ++c) t -= ld<T, ACC>(Lsub + fpos(r, c, b, swz)) * xp[c];
             }
             tmp[r] = t;
         }
         __syncthreads();
         for (int r = threadIdx.x; r < b; r += blockDim.x) {
             ACC s = 0;
-            for (int c = 0; c <= r; ++c) s += ld<T, ACC>(Linv + c * b + r) * tmp[c];
+            for (int c = 0; c <= r; ++c) s += ld<T, ACC>(Linv + fpos(r, c, b, swz)) * tmp[c];
             x[j * b + r] = s;
         }
         __syncthreads();
@@ -49,16 +55,17 @@ __device__ void dirichlet_solve(const T *F, int b, int m, ACC *x, ACC *tmp) {
         for (int r = threadIdx.x; r < b; r += blockDim.x) {
             ACC t = x[j * b + r];
             if (j < m - 1) {
+                // L_{j+1,j}^T: entry (r, c) is entry (c, r) of the stored block
                 const T *Lsub1 = F + (int64_t)(j + 1) * 2 * bb + bb;
                 const ACC *xn = x + (j + 1) * b;
-                for (int c = 0; c < b; ++c) t -= ld<T, ACC>(Lsub1 + r * b + c) * xn[c];
+                for (int c = 0; c < b; ++c) t -= ld<T, ACC>(Lsub1 + fpos(c, r, b, swz)) * xn[c];
             }
             tmp[r] = t;
         }
         __syncthreads();
         for (int r = threadIdx.x; r < b; r += blockDim.x) {
             ACC s = 0;
-            for (int c = r; c < b; ++c) s += ld<T, ACC>(Linv + r * b + c) * tmp[c];
+            for (int c = r; c < b; ++c) s += ld<T, ACC>(Linv + fpos(c, r, b, swz)) * tmp[c];
             x[j * b + r] = s;
         }
         __syncthreads();
@@ -81,7 +88,7 @@ __global__ void k_pre(DevLevel L, const double *r, const int *skip) {
     for (int i = threadIdx.x; i < m * b; i += blockDim.x) x[i] = i < nI ? (ACC)r[iI[i]] : (ACC)0;
     for (int q = threadIdx.x; q < nG; q += blockDim.x) tG[q] = 0;
     __syncthreads();
-    if (nI > 0) dirichlet_solve<T, ACC>(O.dir + L.offF[sub], b, m, x, tmp);
+    if (nI > 0) dirichlet_solve<T, ACC>(O.dir + L.offF[sub], b, m, L.bp != 0, x, tmp);
     for (int64_t k = L.offCOO[sub] + threadIdx.x; k < L.offCOO[sub + 1]; k += blockDim.x)
         atomicAdd(&tG[L.cooG[k]], ld<T, ACC>(O.aig + k) * x[L.cooI[k]]);
     __syncthreads();
@@ -165,7 +172,7 @@ __global__ void k_post(DevLevel L, const double *r, double *z, const int *skip) 
     for (int64_t k = L.offCOO[sub] + threadIdx.x; k < L.offCOO[sub + 1]; k += blockDim.x)
         atomicAdd(&x[L.cooI[k]], -ld<T, ACC>(O.aig + k) * uG[L.cooG[k]]);
     __syncthreads();
-    if (nI > 0) dirichlet_solve<T, ACC>(O.dir + L.offF[sub], b, m, x, tmp);
+    if (nI > 0) dirichlet_solve<T, ACC>(O.dir + L.offF[sub], b, m, L.bp != 0, x, tmp);
     for (int i = threadIdx.x; i < nI; i += blockDim.x) z[iI[i]] = (double)x[i];
     for (int64_t k = L.offOwn[sub] + threadIdx.x; k < L.offOwn[sub + 1]; k += blockDim.x) {
         const int id = L.own[k];
@@ -217,107 +224,7 @@ template <int LPR, class ACC> __device__ __forceinline__ ACC lpr_sum(ACC v) {
     return v;
 }
 
-// Block forward / backward substitution by one warp with the block size BP
-// known at compile time; LPR = 32 / BP lanes share a row.  Every loop unrolls
-// completely; the padding of the last block and the upper triangle of Linv
-// are stored zeros.
-template <class T, class ACC, int BP>
-__device__ __forceinline__ void warp_dirichlet(const T *F, int m, ACC *x, ACC *tmp, int lane) {
-    constexpr int LPR = 32 / BP;
-    constexpr int NC = BP / LPR;
-    constexpr int BB = BP * BP;
-    const int r = lane / LPR, h = lane % LPR;
-    // entry (row, col) of a block lives at col*BP + (row ^ col)
-    for (int j = 0; j < m; ++j) {
-        const T *Linv = F + (size_t)j * 2 * BB;
-        const T *Lsub = Linv + BB;
-        ACC a0 = 0, a1 = 0;
-        if (j > 0) {
-            const ACC *xp = x + (j - 1) * BP;
-#pragma unroll
-            for (int i = 0; i < NC; i += 2) {
-                const int c0 = h + LPR * i;
-                a0 += ld<T, ACC>(Lsub + c0 * BP + (r ^ c0)) * xp[c0];
-                if (i + 1 < NC) {
-                    const int c1 = c0 + LPR;
-                    a1 += ld<T, ACC>(Lsub + c1 * BP + (r ^ c1)) * xp[c1];
-                }
-            }
-        }
-        ACC part = lpr_sum<LPR>(a0 + a1);
-        if (h == 0) tmp[r] = x[j * BP + r] - part;
-        __syncwarp();
-        a0 = 0; a1 = 0;
-#pragma unroll
-        for (int i = 0; i < NC; i += 2) {
-            const int c0 = h + LPR * i;
-            a0 += ld<T, ACC>(Linv + c0 * BP + (r ^ c0)) * tmp[c0];
-            if (i + 1 < NC) {
-                const int c1 = c0 + LPR;
-                a1 += ld<T, ACC>(Linv + c1 * BP + (r ^ c1)) * tmp[c1];
-            }
-        }
-        part = lpr_sum<LPR>(a0 + a1);
-        if (h == 0) x[j * BP + r] = part;
-        __syncwarp();
-    }
-    for (int j = m - 1; j >= 0; --j) {
-        const T *Linv = F + (size_t)j * 2 * BB;
-        ACC a0 = 0, a1 = 0;
-        if (j < m - 1) {
-            const T *Lsub1 = F + (size_t)(j + 1) * 2 * BB + BB;
-            const ACC *xn = x + (j + 1) * BP;
-#pragma unroll
-            for (int i = 0; i < NC; i += 2) {
-                const int c0 = h + LPR * i;
-                a0 += ld<T, ACC>(Lsub1 + r * BP + (c0 ^ r)) * xn[c0];
-                if (i + 1 < NC) {
-                    const int c1 = c0 + LPR;
-                    a1 += ld<T, ACC>(Lsub1 + r * BP + (c1 ^ r)) * xn[c1];
-                }
-            }
-        }
-        ACC part = lpr_sum<LPR>(a0 + a1);
-        if (h == 0) tmp[r] = x[j * BP + r] - part;
-        __syncwarp();
-        a0 = 0; a1 = 0;
-#pragma unroll
-        for (int i = 0; i < NC; i += 2) {
-            const int c0 = h + LPR * i;
-            a0 += ld<T, ACC>(Linv + r * BP + (c0 ^ r)) * tmp[c0];
-            if (i + 1 < NC) {
-                const int c1 = c0 + LPR;
-                a1 += ld<T, ACC>(Linv + r * BP + (c1 ^ r)) * tmp[c1];
-            }
-        }
-        part = lpr_sum<LPR>(a0 + a1);
-        if (h == 0) x[j * BP + r] = part;
-        __syncwarp();
-    }
-}
 
-// Gather dst[i] = src[idx[i]] for i < n (zero for n <= i < npad) with eight
-// independent loads in flight per lane.
-template <class ACC>
-__device__ __forceinline__ void warp_gather(ACC *dst, const double *src, const int *idx, int n,
-                                            int npad, int lane) {
-    for (int i0 = 0; i0 < npad; i0 += 256) {
-        int id[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int i = i0 + u * 32 + lane;
-            id[u] = i < n ? __ldg(idx + i) : -1;
-        }
-        double v[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = id[u] >= 0 ? src[id[u]] : 0.0;
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int i = i0 + u * 32 + lane;
-            if (i < npad) dst[i] = (ACC)v[u];
-        }
-    }
-}
 
 // ----------------------------------------------------------------------------
 // Dirichlet solves (4) and (10) with one warp per substructure.

@@ -49,6 +49,107 @@ def grid_grouping(n_sub_side: int, group: int) -> tuple[np.ndarray, int]:
     return ((sj // group) * ng + (si // group)).astype(np.int32), ng * ng
 
 
+def voronoi_decomposition(nx: int, cells: int, seed: int, jitter: float = 0.25,
+                          group: int = 0) -> tuple[np.ndarray, int, np.ndarray | None, int]:
+    """Irregular substructures: a seeded Voronoi partition of the elements.
+
+    ``cells x cells`` seeds sit on a lattice of boxes of ``nx / cells``
+    elements, each moved uniformly by up to ``jitter`` box widths in x and y
+    (so every seed stays inside its own box).  Every element goes to the seed
+    nearest its centroid (ties to the lower seed index; only the 5 x 5 boxes
+    around an element can hold its nearest seed).  A cell whose elements fall
+    apart (connectivity across element edges) keeps its largest piece; every
+    other piece joins the neighbouring cell it shares the most element edges
+    with, repeatedly, until every cell is connected.  Empty cells are dropped
+    and the rest renumbered in seed order.
+
+    With ``group > 0`` the level-2 substructure of a cell is the ``group x
+    group`` block of lattice boxes holding its seed.
+
+    Returns ``(elem_to_sub, n_sub, sub1_to_sub2 or None, n_sub2)``.
+    """
+    from scipy.sparse import coo_matrix
+    from scipy.sparse.csgraph import connected_components
+
+    if nx % cells:
+        raise ValueError("nx must be a multiple of the number of cells per side")
+    w = nx // cells
+    rng = _rng(seed)
+    off = rng.uniform(-jitter, jitter, size=(cells * cells, 2))
+    ia, ib = np.meshgrid(np.arange(cells), np.arange(cells))        # [b, a]
+    sx = (ia.reshape(-1) + 0.5 + off[:, 0]) * w                    # seed s = b * cells + a
+    sy = (ib.reshape(-1) + 0.5 + off[:, 1]) * w
+    ei, ej = np.meshgrid(np.arange(nx), np.arange(nx))              # [ej, ei]
+    cx, cy = (ei + 0.5).reshape(-1), (ej + 0.5).reshape(-1)
+    ba, bb = (ei // w).reshape(-1), (ej // w).reshape(-1)
+    best = np.full(nx * nx, np.inf)
+    arg = np.full(nx * nx, -1, dtype=np.int64)
+    for db in range(-2, 3):
+        for da in range(-2, 3):
+            a2, b2 = ba + da, bb + db
+            ok = (a2 >= 0) & (a2 < cells) & (b2 >= 0) & (b2 < cells)
+            sidx = np.where(ok, b2 * cells + a2, 0)
+            d = np.where(ok, (cx - sx[sidx]) ** 2 + (cy - sy[sidx]) ** 2, np.inf)
+            take = (d < best) | ((d == best) & (sidx < arg))
+            best = np.where(take, d, best)
+            arg = np.where(take, sidx, arg)
+    lab = arg.reshape(nx, nx)                                       # [ej, ei]
+
+    def pieces(lab):
+        idx = np.arange(nx * nx).reshape(nx, nx)
+        h = lab[:, 1:] == lab[:, :-1]
+        v = lab[1:, :] == lab[:-1, :]
+        r = np.concatenate([idx[:, :-1][h], idx[:-1, :][v]])
+        c = np.concatenate([idx[:, 1:][h], idx[1:, :][v]])
+        g = coo_matrix((np.ones(r.size), (r, c)), shape=(nx * nx, nx * nx))
+        return connected_components(g, directed=False)[1].reshape(nx, nx)
+
+    shifts = (((slice(None), slice(1, None)), (slice(None), slice(None, -1))),
+              ((slice(None), slice(None, -1)), (slice(None), slice(1, None))),
+              ((slice(1, None), slice(None)), (slice(None, -1), slice(None))),
+              ((slice(None, -1), slice(None)), (slice(1, None), slice(None))))
+    while True:
+        comp = pieces(lab)
+        flat_l, flat_c = lab.reshape(-1), comp.reshape(-1)
+        size = np.bincount(flat_c)
+        first = np.full(size.size, -1, dtype=np.int64)
+        first[flat_c[::-1]] = np.arange(flat_c.size)[::-1]         # an element of each piece
+        cell_of = flat_l[first]
+        main = {}                                                  # cell -> its largest piece
+        for cpt in np.lexsort((np.arange(size.size), -size)):
+            main.setdefault(int(cell_of[cpt]), int(cpt))
+        is_main = np.zeros(size.size, dtype=bool)
+        is_main[list(main.values())] = True
+        frag = [cpt for cpt in range(size.size) if not is_main[cpt]]
+        if not frag:
+            break
+        moved = False
+        for cpt in frag:
+            mask = comp == cpt
+            cnt = {}
+            for sl_a, sl_b in shifts:
+                # element edges from the piece to the main piece of another cell
+                m = mask[sl_a] & is_main[comp[sl_b]] & (lab[sl_b] != cell_of[cpt])
+                for nb in lab[sl_b][m]:
+                    cnt[int(nb)] = cnt.get(int(nb), 0) + 1
+            if cnt:
+                lab[mask] = min(cnt, key=lambda c: (-cnt[c], c))
+                moved = True
+        if not moved:
+            raise RuntimeError("Voronoi fragments with no neighbouring main piece")
+    used = np.unique(lab)
+    renum = np.full(cells * cells, -1, dtype=np.int64)
+    renum[used] = np.arange(used.size)
+    e2s = renum[lab].reshape(-1).astype(np.int32)
+    if group <= 0:
+        return e2s, int(used.size), None, 0
+    if cells % group:
+        raise ValueError("cells must be a multiple of the group size")
+    ng = cells // group
+    s2 = ((used // cells) // group * ng + (used % cells) // group).astype(np.int32)
+    return e2s, int(used.size), s2, ng * ng
+
+
 def constant_coefficient(nx: int, value: float = 1.0) -> np.ndarray:
     return np.full(nx * nx, value, dtype=np.float64)
 
@@ -156,3 +257,18 @@ def three_level_blocks(nx: int = 1024, sub: int = 8, group: int = 8, tau: float 
     return Workload("three_level_blocks_%d" % nx, nx,
                     block_log_uniform_coefficient(nx, 8, seed), e2s, ns,
                     3, tau, "adaptive", s2, n2, rhs_seed=rhs_seed)
+
+
+def three_level_voronoi(nx: int = 2048, cells: int = 64, group: int = 8, tau: float = 10.0,
+                        part_seed: int = 4001, coef_seed: int = 4002, rhs_seed: int = 4003,
+                        jitter: float = 0.25, levels: int = 3) -> Workload:
+    """2048x2048 mesh cut into 64x64 seeded Voronoi cells (about 700-1600 DOFs
+    each at jitter 0.25), grouped by 8x8 lattice blocks of seeds into 64
+    level-2 substructures; log10 k uniform in [0, 6] per 8x8-element block
+    (not aligned with the cells)."""
+    e2s, ns, s2, n2 = voronoi_decomposition(nx, cells, part_seed, jitter,
+                                            group if levels == 3 else 0)
+    return Workload("three_level_voronoi_%d" % nx if levels == 3 else "two_level_voronoi_%d" % nx,
+                    nx, block_log_uniform_coefficient(nx, 8, coef_seed), e2s, ns, levels, tau,
+                    "adaptive", s2, n2, rhs_seed=rhs_seed)
+

@@ -3,7 +3,7 @@
 Calls only the CPU oracle (oracle/) on the seeded inputs of
 paper_0911_5730_gb300.inputs; nothing here touches the CUDA path.
 
-    python tests/golden/make_golden.py two_level_channels_512
+    python tests/golden/make_golden.py two_level_channels_512 three_level_blocks_1024
 """
 import json
 import os
@@ -22,6 +22,7 @@ from paper_0911_5730_gb300 import inputs          # noqa: E402
 WORKLOADS = {
     "two_level_channels_512": lambda: inputs.two_level_channels(nx=512, sub=16, tau=10.0),
     "two_level_unit_32": lambda: inputs.two_level_unit(),
+    "three_level_blocks_1024": lambda: inputs.three_level_blocks(),
 }
 SAMPLE_STRIDE = 997
 

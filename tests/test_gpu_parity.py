@@ -43,6 +43,11 @@ def _workloads():
     w["channels_64"] = inputs.two_level_channels(nx=64, sub=16)
     w["channels_96_ragged"] = inputs.two_level_channels(nx=96, sub=16, tau=3.0)
     w["three_level_64"] = inputs.three_level_blocks(nx=64, sub=8, group=4, tau=10.0)
+    # config 4's Voronoi cells, small: block size 32 (warp kernels) and, with
+    # cells of about 1000 DOFs, no power-of-two block (generic kernels)
+    w["voronoi_64"] = inputs.three_level_voronoi(nx=64, cells=4, group=2, levels=2)
+    w["voronoi_128_large_cells"] = inputs.three_level_voronoi(nx=128, cells=4, group=2, levels=2)
+    w["voronoi_128_3lev"] = inputs.three_level_voronoi(nx=128, cells=8, group=2, levels=3)
     return w
 
 
@@ -79,7 +84,8 @@ def test_apply_fp64_matches_oracle(lib, name):
     P.close()
 
 
-@pytest.mark.parametrize("name", ["channels_64", "channels_96_ragged", "three_level_64"])
+@pytest.mark.parametrize("name", ["channels_64", "channels_96_ragged", "three_level_64",
+                                  "voronoi_64", "voronoi_128_large_cells", "voronoi_128_3lev"])
 def test_selection_matches_oracle(lib, name):
     wl = WL[name]
     H = _oracle(name)
@@ -100,7 +106,8 @@ def test_selection_matches_oracle(lib, name):
     P.close()
 
 
-@pytest.mark.parametrize("name", ["unit_c+e", "channels_64", "three_level_64"])
+@pytest.mark.parametrize("name", ["unit_c+e", "channels_64", "three_level_64", "voronoi_64",
+                                  "voronoi_128_large_cells", "voronoi_128_3lev"])
 def test_pcg_matches_oracle(lib, name):
     wl = WL[name]
     H = _oracle(name)
@@ -128,7 +135,8 @@ def test_all_interface_exact_one_iteration(lib):
     P.close()
 
 
-@pytest.mark.parametrize("name", ["channels_64", "three_level_64"])
+@pytest.mark.parametrize("name", ["channels_64", "three_level_64", "voronoi_128_large_cells",
+                                  "voronoi_128_3lev"])
 def test_mixed_precision(lib, name):
     wl = WL[name]
     P = lib.Problem.from_workload(wl)

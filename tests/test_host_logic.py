@@ -41,6 +41,9 @@ CASES = [("grid32_8",) + inputs.grid_decomposition(32, 8) + (32,),
 for sd in (1, 2, 3):
     e2s, ns = _nearest_seed_partition(24, 7, sd)
     CASES.append(("seeds24_%d" % sd, e2s, ns, 24))
+for nx, c in ((64, 4), (128, 8)):          # config 4's Voronoi cells, small
+    e2s, ns, _, _ = inputs.voronoi_decomposition(nx, c, 4001)
+    CASES.append(("voronoi%d_%d" % (nx, c), e2s, ns, nx))
 
 
 @pytest.mark.parametrize("name,e2s,ns,nx", CASES, ids=[c[0] for c in CASES])
@@ -57,3 +60,41 @@ def test_block_size_power_of_two_for_grids(bddc):
     for nx, sub, bp in [(512, 16, 16), (64, 8, 8), (32, 8, 8)]:
         e2s, ns = inputs.grid_decomposition(nx, sub)
         assert bddc.inspect(nx, e2s, ns)["block_size"] == bp
+
+
+def _pieces(lab):
+    """Connected pieces (across element edges) of every label, by flood fill."""
+    nx = lab.shape[0]
+    seen = np.zeros_like(lab, dtype=bool)
+    count = {}
+    for j0 in range(nx):
+        for i0 in range(nx):
+            if seen[j0, i0]:
+                continue
+            c = lab[j0, i0]
+            count[c] = count.get(c, 0) + 1
+            stack = [(j0, i0)]
+            seen[j0, i0] = True
+            while stack:
+                j, i = stack.pop()
+                for jj, ii in ((j, i + 1), (j, i - 1), (j + 1, i), (j - 1, i)):
+                    if 0 <= jj < nx and 0 <= ii < nx and not seen[jj, ii] and lab[jj, ii] == c:
+                        seen[jj, ii] = True
+                        stack.append((jj, ii))
+    return count
+
+
+@pytest.mark.parametrize("nx,cells,group", [(64, 4, 2), (128, 8, 4), (256, 16, 8)])
+def test_voronoi_partition_properties(nx, cells, group):
+    e2s, ns, s2, n2 = inputs.voronoi_decomposition(nx, cells, 4001, group=group)
+    again = inputs.voronoi_decomposition(nx, cells, 4001, group=group)
+    assert np.array_equal(e2s, again[0]) and np.array_equal(s2, again[2])     # seeded
+    assert ns == cells * cells and set(np.unique(e2s)) == set(range(ns))
+    pieces = _pieces(e2s.reshape(nx, nx))
+    assert all(v == 1 for v in pieces.values())                                # every cell connected
+    assert n2 == (cells // group) ** 2 and set(np.unique(s2)) == set(range(n2))
+    assert all(np.sum(s2 == g) == group * group for g in range(n2))
+    sizes = np.bincount(e2s)
+    w2 = (nx // cells) ** 2
+    assert sizes.min() >= 0.5 * w2 and sizes.max() <= 1.6 * w2
+

@@ -117,3 +117,39 @@ def test_lanczos_estimate_exact_on_diagonal():
     d = np.array([1.0, 2.0, 5.0, 11.0])
     res = pcg.pcg(np.diag(d), np.ones(4), lambda r: r.copy(), rtol=1e-14, maxit=4)
     assert np.isclose(res.lam_min, 1.0, rtol=1e-10) and np.isclose(res.lam_max, 11.0, rtol=1e-10)
+
+
+# Irregular substructures (config 4's Voronoi cells, small): the same pins.
+def _voronoi(nx=32, cells=4, group=2, seed=4001):
+    e2s, ns, s2, n2 = inputs.voronoi_decomposition(nx, cells, seed, group=group)
+    k = inputs.block_log_uniform_coefficient(nx, 4, seed + 1, 0.0, 3.0)
+    return nx, k, e2s, ns, s2, n2
+
+
+@pytest.mark.parametrize("levels", [2, 3])
+def test_voronoi_all_interface_is_exact(levels):
+    nx, k, e2s, ns, s2, n2 = _voronoi()
+    H = bddc.build(nx, k, e2s, ns, levels, "all", sub1_to_sub2=s2, nsub2=n2)
+    M = _dense_M(H)
+    assert np.linalg.norm(M @ H.A.toarray() - np.eye(H.n)) <= 1e-10 * np.sqrt(H.n)
+
+
+@pytest.mark.parametrize("levels", [2, 3])
+def test_voronoi_adaptive_symmetric_bounded_and_direct(levels):
+    nx, k, e2s, ns, s2, n2 = _voronoi()
+    tau = 10.0
+    H = bddc.build(nx, k, e2s, ns, levels, "adaptive", tau=tau, sub1_to_sub2=s2, nsub2=n2)
+    M = _dense_M(H)
+    assert np.linalg.norm(M - M.T) <= 1e-12 * np.linalg.norm(M)
+    A = H.A.toarray()
+    L = np.linalg.cholesky(A)
+    ev = np.linalg.eigvalsh(L.T @ M @ L)
+    assert ev[0] >= 1.0 - 1e-10
+    # Lemma 1 / Theorem 2: the indicator and the condition number are bounded
+    # by tau^(L-1) by construction of the adaptive constraints
+    assert H.info["omega_tilde"] <= tau ** (levels - 1) * (1 + 1e-9)
+    assert ev[-1] / ev[0] <= tau ** (levels - 1)
+    b = inputs.normal_rhs(H.n, 12)
+    res = pcg.pcg(H.A, b, H.apply, rtol=1e-13, maxit=500)
+    x = spl.spsolve(H.A.tocsc(), b)
+    assert np.linalg.norm(res.x - x) <= 1e-10 * np.linalg.norm(x)
