@@ -300,8 +300,14 @@ const char *bddc_last_error(void);
  * so its result does not depend on what else is in flight.
  * ------------------------------------------------------------------------- */
 
-/* bddc_server_create - hbm_budget in bytes for request buffers (0 = unlimited);
- * max_slots concurrent requests (>= 1). */
+/* bddc_server_create - hbm_budget in bytes for request buffers (0 = unlimited).
+ * Problems whose operators fit the batch kernels are served by continuous
+ * batching: one lockstep batch of 32 right-hand-side slots per problem;
+ * queued right-hand sides (of any request) enter slots as others finish,
+ * between PCG iterations, and each keeps its own PCG state, tolerance and
+ * iteration limit, so its result does not depend on the mix.  Other
+ * problems are served by max_slots (>= 1) worker threads, one right-hand
+ * side at a time each. */
 int bddc_server_create(size_t hbm_budget, int max_slots, bddc_server **out);
 
 /*

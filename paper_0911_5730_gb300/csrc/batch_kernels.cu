@@ -374,6 +374,7 @@ __global__ void __launch_bounds__(32 * kDW) k_dir_b(DevLevel L, BatchLevel B, co
                 if (!sc->done[lane]) {
                     const double beta = sc->fresh[lane] ? 0.0 : tot / sc->rho[lane];
                     sc->fresh[lane] = 0;
+                    sc->hold[lane] = 0;          // joins the next direction update
                     sc->beta[lane] = beta;
                     if (sc->it[lane] > 0) rz.betas[(int64_t)(sc->it[lane] - 1) * K + lane] = beta;
                     sc->rho[lane] = tot;
@@ -681,7 +682,7 @@ __global__ void k_b_init(int n, int K, const double *b, int64_t ldb, double *x, 
     grid_reduce_k(s, K, part, counter,
         [&](int kk, double tot) {
             sc->bb[kk] = tot; sc->rr[kk] = tot; sc->tol2[kk] = tol * tol * tot;
-            sc->it[kk] = 0; sc->fresh[kk] = 1; sc->beta[kk] = 0.0;
+            sc->it[kk] = 0; sc->fresh[kk] = 1; sc->beta[kk] = 0.0; sc->hold[kk] = 0; sc->mx[kk] = maxit;
             sc->conv[kk] = tot == 0.0 ? 1 : 0;
             sc->done[kk] = tot == 0.0 ? 1 : 0;
         },
@@ -743,7 +744,7 @@ __global__ void k_b_dir_spmv(int nx, int K, const double *__restrict__ w, const 
     __syncthreads();
     const int k = threadIdx.x % K;
     const int per = blockDim.x / K;
-    const bool live = !sc->done[k];
+    const bool live = !sc->done[k] && !sc->hold[k];
     double s = 0.0;
 #pragma unroll 4
     for (int ln = threadIdx.x / K; ln < BT_X * BT_Y; ln += per) {
@@ -771,7 +772,7 @@ __global__ void k_b_dir_spmv(int nx, int K, const double *__restrict__ w, const 
     }
     grid_reduce_k(s, K, part, counter,
         [&](int kk, double tot) {
-            if (sc->done[kk]) return;
+            if (sc->done[kk] || sc->hold[kk]) return;
             sc->pq[kk] = tot;
             sc->alpha[kk] = sc->rho[kk] / tot;
             alphas[(int64_t)sc->it[kk] * K + kk] = sc->alpha[kk];
@@ -787,7 +788,7 @@ __global__ void k_b_update(int64_t nK, int K, double *__restrict__ x, double *__
     if (sc->all_done) return;
     const double *__restrict__ p = (sc->step & 1) ? p0 : p1;   // p_new of this step
     const int k = threadIdx.x % K;
-    const bool live = !sc->done[k];
+    const bool live = !sc->done[k] && !sc->hold[k];
     const double a = sc->alpha[k];
     double s = 0.0;
     if (live) {
@@ -800,11 +801,11 @@ __global__ void k_b_update(int64_t nK, int K, double *__restrict__ x, double *__
     }
     grid_reduce_k(s, K, part, counter,
         [&](int kk, double tot) {
-            if (sc->done[kk]) return;
+            if (sc->done[kk] || sc->hold[kk]) return;
             sc->rr[kk] = tot;
             sc->it[kk] += 1;
             if (tot <= sc->tol2[kk]) { sc->conv[kk] = 1; sc->done[kk] = 1; }
-            if (sc->it[kk] >= sc->maxit) sc->done[kk] = 1;
+            if (sc->it[kk] >= sc->mx[kk]) sc->done[kk] = 1;
         },
         [&]() {
             int all = 1;
@@ -869,6 +870,34 @@ __global__ void k_b_scatter(int n, int K, const double *src, double *dst, int64_
     if (e >= (int64_t)n * K) return;
     const int k = (int)(e % K);
     dst[(int64_t)k * ld + e / K] = src[e];
+}
+
+// A new right-hand side in slot k of a running batch.
+__global__ void k_b_admit(int n, int K, int k, const double *__restrict__ b, double *x, double *r,
+                          double *part, unsigned *counter, BatchScalars *sc, double tol, int maxit) {
+    double s = 0.0;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n; g += gridDim.x * blockDim.x) {
+        const double v = b[g];
+        x[(int64_t)g * K + k] = 0.0;
+        r[(int64_t)g * K + k] = v;
+        s = fma(v, v, s);
+    }
+    grid_reduce_k(s, 1, part, counter,
+        [&](int, double tot) {
+            sc->bb[k] = tot; sc->rr[k] = tot; sc->tol2[k] = tol * tol * tot;
+            sc->it[k] = 0; sc->fresh[k] = 1; sc->beta[k] = 0.0; sc->mx[k] = maxit;
+            sc->conv[k] = tot == 0.0 ? 1 : 0;
+            sc->done[k] = tot == 0.0 ? 1 : 0;
+            sc->hold[k] = tot == 0.0 ? 0 : 1;
+        },
+        [&]() {
+            if (!sc->done[k]) sc->all_done = 0;
+        });
+}
+
+__global__ void k_b_column(int n, int K, int k, const double *x, double *dst) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < n) dst[g] = x[(int64_t)g * K + k];
 }
 
 // Both integer-operation conversions against the hardware ones, bit for bit
@@ -1061,6 +1090,15 @@ void launch_b_norm2(int n, int K, const double *v, double *part, unsigned *count
                     cudaStream_t s) {
     const int64_t nK = (int64_t)n * K;
     k_b_norm2<<<vgrid_b(nK, K), bblock(K), 0, s>>>(nK, K, v, part, counter, out);
+}
+void launch_b_admit(int n, int K, int k, const double *b, double *x, double *r, double *part,
+                    unsigned *counter, BatchScalars *sc, double tol, int maxit, cudaStream_t s) {
+    int g = (n + kRB - 1) / kRB;
+    if (g > 152 * 4) g = 152 * 4;
+    k_b_admit<<<g, kRB, 0, s>>>(n, K, k, b, x, r, part, counter, sc, tol, maxit);
+}
+void launch_b_column(int n, int K, int k, const double *x, double *dst, cudaStream_t s) {
+    if (n > 0) k_b_column<<<(n + 255) / 256, 256, 0, s>>>(n, K, k, x, dst);
 }
 void launch_b_restart(int n, int K, const double *res, double *r, const BatchScalars *sc,
                       cudaStream_t s) {

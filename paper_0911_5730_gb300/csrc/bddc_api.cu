@@ -1530,11 +1530,23 @@ struct Request {
     std::vector<double> b, x;
     std::vector<bddc_solve_info> info;
     int nrhs = 1, maxit = 1000, status = BDDC_OK;
+    int remaining = 0;          // right-hand sides not finished (continuous batching)
+    bool started = false;       // holds its share of the budget
     double rtol = 1e-8;
     size_t bytes = 0;
     std::chrono::steady_clock::time_point t_submit, t_done;
     bool done = false;
     std::string err;
+};
+
+// Continuous batching for one problem: a lockstep batch of K slots whose
+// right-hand sides come and go between iterations (see engine_loop).
+struct Engine {
+    bddc_ctx *ctx = nullptr;
+    int K = kMaxBatch;
+    std::deque<std::pair<std::shared_ptr<Request>, int>> pending;   // (request, right-hand side)
+    std::thread th;
+    bool dead = false;
 };
 
 }  // namespace
@@ -1548,9 +1560,10 @@ struct bddc_server {
     bool stop = false;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
-    std::deque<std::shared_ptr<bddc::Request>> queue;
+    std::deque<std::shared_ptr<bddc::Request>> queue;      // problems the batch kernels cannot take
     std::map<uint64_t, std::shared_ptr<bddc::Request>> reqs;
     std::vector<std::thread> workers;
+    std::map<bddc_ctx *, std::unique_ptr<bddc::Engine>> engines;
 };
 
 namespace bddc {
@@ -1615,6 +1628,165 @@ void worker_loop(bddc_server *S) {
     }
 }
 
+// Finish one request's share of the budget and wake its waiters (S->mu held).
+void finish_request(bddc_server *S, Request &R) {
+    R.t_done = std::chrono::steady_clock::now();
+    R.done = true;
+    if (R.started) S->in_use -= R.bytes;
+}
+
+// Continuous batching for one problem.  K slots iterate in lockstep (the
+// batch kernels, one CUDA graph per iteration).  Between chunks of
+// iterations the loop (1) admits queued right-hand sides into free slots,
+// each with its own PCG state starting at x = 0 (k_b_admit; the slot sits out
+// one direction update and joins at that iteration's apply), (2) takes the
+// slots whose recursive residual met the tolerance, checks their FP64 true
+// residual (restarting from it, with beta = 0, if it drifted) and copies the
+// finished ones out.  Every slot's arithmetic is its own column of the batch
+// kernels, so a result does not depend on what else is in the batch.
+void engine_loop(bddc_server *S, Engine *E) {
+    bddc_ctx *C = E->ctx;
+    std::unique_ptr<Workspace> W;
+    struct Slot { std::shared_ptr<Request> R; int j = -1; };
+    std::vector<Slot> slot(E->K);
+    auto fail_all = [&](int code, const std::string &msg) {
+        std::lock_guard<std::mutex> lk(S->mu);
+        E->dead = true;
+        auto fail = [&](const std::shared_ptr<Request> &R) {
+            if (!R || R->done) return;
+            R->status = code;
+            R->err = msg;
+            finish_request(S, *R);
+        };
+        for (auto &sl : slot) fail(sl.R);
+        for (auto &pr : E->pending) fail(pr.first);
+        E->pending.clear();
+    };
+    try {
+        W.reset(new Workspace());
+        make_workspace(C, *W, 10000);
+        BatchWs &BW = batch_ws(C, *W);
+        const int K = E->K;
+        const int n = C->n();
+        cudaStream_t st = W->stream;
+        set_batch_width(BW, K);
+        BDDC_CUDA_TRY(cudaMemsetAsync(BW.bcol, 0, sizeof(double) * (size_t)n * K, st));
+        launch_b_init(n, K, BW.bcol, n, BW.x, BW.r, BW.p, BW.part, BW.counter, BW.sc, 1e-8, 1, st);
+        BDDC_CUDA_TRY(cudaMemsetAsync(BW.rzcounter, 0, sizeof(unsigned), st));
+        BatchScalars &h = *BW.hsc;
+        std::vector<double> hal, hbe;
+        for (;;) {
+            std::vector<int> admitted;
+            {
+                std::unique_lock<std::mutex> lk(S->mu);
+                auto active = [&] {
+                    for (auto &sl : slot) if (sl.R) return true;
+                    return false;
+                };
+                auto admissible = [&] {
+                    if (E->pending.empty()) return false;
+                    const auto &R = E->pending.front().first;
+                    return R->started || !S->budget || S->in_use + R->bytes <= S->budget || S->in_use == 0;
+                };
+                S->cv_work.wait(lk, [&] { return S->stop || active() || admissible(); });
+                if (S->stop && !active() && E->pending.empty()) break;
+                for (int k = 0; k < K && admissible(); ++k) {
+                    if (slot[k].R) continue;
+                    auto pr = E->pending.front();
+                    E->pending.pop_front();
+                    if (!pr.first->started) { pr.first->started = true; S->in_use += pr.first->bytes; }
+                    slot[k].R = pr.first;
+                    slot[k].j = pr.second;
+                    admitted.push_back(k);
+                }
+            }
+            for (int k : admitted) {
+                const Request &R = *slot[k].R;
+                BDDC_CUDA_TRY(cudaMemcpyAsync(BW.bcol + (size_t)k * n, R.b.data() + (size_t)slot[k].j * n,
+                                              sizeof(double) * n, cudaMemcpyHostToDevice, st));
+                launch_b_admit(n, K, k, BW.bcol + (size_t)k * n, BW.x, BW.r, BW.part, BW.counter, BW.sc,
+                               R.rtol, std::min(R.maxit, W->maxit_cap), st);
+            }
+            cudaGraphExec_t g = batch_graph(C, *W, BW, C->prec, K);
+            for (int c = 0; c < 2; ++c) BDDC_CUDA_TRY(cudaGraphLaunch(g, st));
+            BDDC_CUDA_TRY(cudaMemcpyAsync(BW.hsc, BW.sc, sizeof(BatchScalars), cudaMemcpyDeviceToHost, st));
+            BDDC_CUDA_TRY(cudaStreamSynchronize(st));
+            std::vector<int> fin;
+            for (int k = 0; k < K; ++k) if (slot[k].R && h.done[k]) fin.push_back(k);
+            if (fin.empty()) continue;
+            launch_b_residual(C->nx, K, C->w_dev, BW.bcol, n, BW.x, BW.tmp, st);
+            launch_b_norm2(n, K, BW.tmp, BW.part, BW.counter, BW.nrm, st);
+            BDDC_CUDA_TRY(cudaMemcpyAsync(BW.hnrm, BW.nrm, sizeof(double) * K, cudaMemcpyDeviceToHost, st));
+            BDDC_CUDA_TRY(cudaStreamSynchronize(st));
+            bool restart = false;
+            std::vector<int> out;
+            for (int k : fin) {
+                if (h.conv[k] && BW.hnrm[k] > h.tol2[k] && h.it[k] < h.mx[k]) {
+                    h.done[k] = 0; h.conv[k] = 0; h.fresh[k] = 1; h.hold[k] = 1; h.rr[k] = BW.hnrm[k];
+                    restart = true;
+                } else {
+                    out.push_back(k);
+                }
+            }
+            if (restart) {
+                h.all_done = 0;
+                BDDC_CUDA_TRY(cudaMemcpyAsync(BW.sc, BW.hsc, sizeof(BatchScalars), cudaMemcpyHostToDevice, st));
+                launch_b_restart(n, K, BW.tmp, BW.r, BW.sc, st);
+            }
+            int kmax = 0;
+            for (int k : out) kmax = std::max(kmax, std::min(h.it[k], W->maxit_cap));
+            if (hal.size() < (size_t)(kmax + 1) * K) { hal.resize((size_t)(kmax + 1) * K); hbe.resize(hal.size()); }
+            if (kmax > 0) {
+                BDDC_CUDA_TRY(cudaMemcpyAsync(hal.data(), BW.alphas, sizeof(double) * kmax * K, cudaMemcpyDeviceToHost, st));
+                BDDC_CUDA_TRY(cudaMemcpyAsync(hbe.data(), BW.betas, sizeof(double) * kmax * K, cudaMemcpyDeviceToHost, st));
+            }
+            for (int k : out) {
+                Request &R = *slot[k].R;
+                launch_b_column(n, K, k, BW.x, BW.xcol + (size_t)k * n, st);
+                BDDC_CUDA_TRY(cudaMemcpyAsync(R.x.data() + (size_t)slot[k].j * n, BW.xcol + (size_t)k * n,
+                                              sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+            }
+            int kerr = 0;
+            BDDC_CUDA_TRY(cudaMemcpyAsync(&kerr, C->err_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
+            BDDC_CUDA_TRY(cudaStreamSynchronize(st));
+            if (kerr) throw Error(BDDC_E_TIMEOUT, "a bounded device wait gave up during the solve");
+            {
+                std::lock_guard<std::mutex> lk(S->mu);
+                for (int k : out) {
+                    Request &R = *slot[k].R;
+                    const int j = slot[k].j;
+                    const int status = (h.conv[k] && BW.hnrm[k] <= h.tol2[k] * (1 + 1e-12)) ? BDDC_OK : BDDC_E_NOCONV;
+                    const int kit = std::min(h.it[k], W->maxit_cap);
+                    std::vector<double> al(kit + 1), be(kit + 1);
+                    for (int q = 0; q < kit; ++q) { al[q] = hal[(size_t)q * K + k]; be[q] = hbe[(size_t)q * K + k]; }
+                    double lmin = 1.0, lmax = 1.0;
+                    lanczos_extremes(al, be, kit, &lmin, &lmax);
+                    bddc_solve_info &I = R.info[j];
+                    I.iters = h.it[k];
+                    I.status = status;
+                    I.kernel_launches = 0;
+                    I.batch_width = K;
+                    I.relres = h.bb[k] > 0 ? std::sqrt(h.rr[k] / h.bb[k]) : 0.0;
+                    I.relres_true = h.bb[k] > 0 ? std::sqrt(BW.hnrm[k] / h.bb[k]) : 0.0;
+                    I.lam_min = lmin;
+                    I.lam_max = lmax;
+                    I.kappa_est = lmin > 0 ? lmax / lmin : 0.0;
+                    if (status != BDDC_OK) R.status = status;
+                    if (--R.remaining == 0) finish_request(S, R);
+                    slot[k].R.reset();
+                    slot[k].j = -1;
+                }
+            }
+            S->cv_done.notify_all();
+        }
+    } catch (const Error &e) {
+        fail_all(e.code, e.msg);
+    } catch (const std::exception &e) {
+        fail_all(BDDC_E_CUDA, e.what());
+    }
+    S->cv_done.notify_all();
+}
+
 }  // namespace
 }  // namespace bddc
 
@@ -1648,13 +1820,30 @@ int bddc_submit(bddc_server *srv, bddc_ctx *ctx, const double *b_host, int nrhs,
         R->x.assign((size_t)nrhs * n, 0.0);
         R->info.assign(nrhs, bddc_solve_info{});
         R->bytes = request_bytes(ctx, nrhs);
+        R->remaining = nrhs;
         if (srv->budget && R->bytes > srv->budget) throw Error(BDDC_E_BUSY, "request exceeds the HBM budget");
+        const bool batch = ctx->ws && batch_ok(ctx, *ctx->ws, ctx->prec);
         {
             std::lock_guard<std::mutex> lk(srv->mu);
             R->id = srv->next_id++;
             R->t_submit = std::chrono::steady_clock::now();
             srv->reqs[R->id] = R;
-            srv->queue.push_back(R);
+            if (batch) {
+                auto &E = srv->engines[ctx];
+                if (E && E->dead) {            // it has left its locked section: join is safe
+                    E->th.join();
+                    E.reset();
+                }
+                if (!E) {
+                    E.reset(new Engine());
+                    E->ctx = ctx;
+                    E->K = kMaxBatch;
+                    E->th = std::thread(engine_loop, srv, E.get());
+                }
+                for (int j = 0; j < nrhs; ++j) E->pending.emplace_back(R, j);
+            } else {
+                srv->queue.push_back(R);
+            }
         }
         srv->cv_work.notify_all();
         *ticket = R->id;
@@ -1692,6 +1881,8 @@ void bddc_server_destroy(bddc_server *srv) {
     }
     srv->cv_work.notify_all();
     for (auto &t : srv->workers) t.join();
+    for (auto &e : srv->engines)
+        if (e.second->th.joinable()) e.second->th.join();
     delete srv;
 }
 

@@ -181,6 +181,10 @@ struct BatchScalars {
     double rho[kMaxBatch], pq[kMaxBatch], alpha[kMaxBatch], beta[kMaxBatch], rr[kMaxBatch],
         bb[kMaxBatch], tol2[kMaxBatch];
     int it[kMaxBatch], done[kMaxBatch], conv[kMaxBatch], fresh[kMaxBatch];
+    // hold: a right-hand side admitted (or restarted) between iterations sits
+    // out the next direction/update half and joins at that iteration's apply
+    int hold[kMaxBatch];
+    int mx[kMaxBatch];     // iteration limit of each right-hand side
     int K, maxit, all_done;
     int step;      // lockstep iterations run (selects the direction buffer)
 };
@@ -226,6 +230,12 @@ void launch_b_residual(int nx, int K, const double *w, const double *b, int64_t 
                        double *res, cudaStream_t s);
 void launch_b_norm2(int n, int K, const double *v, double *part, unsigned *counter, double *out,
                     cudaStream_t s);
+// Slot k of a running batch takes a new right-hand side b (device [n]):
+// x(:, k) = 0, r(:, k) = b, its scalars reset, hold set; all_done cleared.
+void launch_b_admit(int n, int K, int k, const double *b, double *x, double *r, double *part,
+                    unsigned *counter, BatchScalars *sc, double tol, int maxit, cudaStream_t s);
+// dst[g] = x(g, k)
+void launch_b_column(int n, int K, int k, const double *x, double *dst, cudaStream_t s);
 // r(:, k) = res(:, k) for every k with fresh && !done
 void launch_b_restart(int n, int K, const double *res, double *r, const BatchScalars *sc,
                       cudaStream_t s);

@@ -67,3 +67,54 @@ def test_budget_and_timeout(lib):
     assert e.value.code == -5
     srv.close()
     P.close()
+
+
+def test_continuous_batching_waves(lib):
+    """Requests arrive in waves while earlier ones iterate: more right-hand
+    sides than the 32 slots, with different tolerances, on a problem served by
+    continuous batching (batch_width 32) beside one that needs the generic
+    kernels (served by the worker threads).  Every result equals the solo
+    solve: same iteration count, FP64 solution within 1e-10."""
+    import time
+    batch_wl = inputs.two_level_channels(nx=64, sub=16)
+    generic_wl = inputs.three_level_voronoi(nx=128, cells=4, group=2, levels=2)
+    Pb = lib.Problem.from_workload(batch_wl)
+    Pg = lib.Problem.from_workload(generic_wl)
+    srv = lib.Server(hbm_budget=0, max_slots=2)
+    rng = np.random.default_rng(11)
+    sent = []
+    for wave in range(4):
+        for r in range(12):
+            rtol = 1e-8 if r % 3 else 1e-10
+            b = rng.standard_normal(batch_wl.n_dof)
+            sent.append((Pb, b, rtol, srv.submit(Pb, b, rtol=rtol)))
+        b = rng.standard_normal(generic_wl.n_dof)
+        sent.append((Pg, b, 1e-8, srv.submit(Pg, b, rtol=1e-8)))
+        time.sleep(0.002)
+    for P, b, rtol, t in sent:
+        x, infos, lat = srv.wait(t)
+        assert lat > 0 and infos[0]["status"] == 0
+        assert infos[0]["batch_width"] == (32 if P is Pb else 1)
+        xs, info = P.solve(torch.tensor(b, device="cuda"), rtol=rtol)
+        assert infos[0]["iters"] == info[0]["iters"]
+        xs = xs.cpu().numpy()
+        assert np.linalg.norm(x - xs) <= 1e-10 * np.linalg.norm(xs)
+        assert infos[0]["relres_true"] <= rtol
+    srv.close()
+    Pb.close()
+    Pg.close()
+
+
+def test_continuous_batching_mixed_precision(lib):
+    wl = inputs.two_level_channels(nx=96, sub=16, tau=3.0)
+    P = lib.Problem.from_workload(wl)
+    P.set_precision("fp32")
+    srv = lib.Server(hbm_budget=0, max_slots=1)
+    B = inputs.normal_rhs(wl.n_dof, 13, 40)
+    tickets = [srv.submit(P, B[i:i + 1 + i % 3]) for i in range(0, 36, 3)]
+    for t in tickets:
+        x, infos, lat = srv.wait(t)
+        for i in infos:
+            assert i["status"] == 0 and i["relres_true"] <= 1e-8 and i["batch_width"] == 32
+    srv.close()
+    P.close()
