@@ -27,6 +27,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -191,6 +193,62 @@ def _kernel_bytes(q, n_top, prec_bytes, K=1):
     return b, flops
 
 
+def serving_run(bddc, P, n, rate_rhs, seconds, seed):
+    """Config 5: a seeded Poisson stream of requests, each with 1-64 N(0,1)
+    right-hand sides, offered at rate_rhs right-hand sides per second for
+    `seconds`, served by the library's continuous-batching server.  Returns
+    achieved solves/s over the whole run (first arrival to last completion)
+    and the p50/p99 request latency (submit to completion, from bddc_wait)."""
+    import threading
+    rng = np.random.default_rng(seed)
+    sizes, gaps = [], []
+    t = 0.0
+    while t < seconds:
+        k = int(rng.integers(1, 65))
+        sizes.append(k)
+        gap = rng.exponential(k / rate_rhs)
+        gaps.append(gap)
+        t += gap
+    rhs = [rng.standard_normal((k, n)) for k in sizes]
+    srv = bddc.Server(hbm_budget=0, max_slots=1)
+    tickets, lat = [], []
+    done = threading.Event()
+
+    def collect():
+        i = 0
+        while i < len(sizes):
+            while i >= len(tickets):
+                time.sleep(1e-4)
+            x, infos, ms = srv.wait(tickets[i])
+            assert all(j["status"] == 0 and j["relres_true"] <= RTOL for j in infos)
+            lat.append(ms)
+            i += 1
+        done.set()
+
+    th = threading.Thread(target=collect)
+    th.start()
+    t0 = time.perf_counter()
+    due = t0
+    for k, b, gap in zip(sizes, rhs, gaps):
+        while time.perf_counter() < due:
+            time.sleep(min(1e-3, max(0.0, due - time.perf_counter())))
+        tickets.append(srv.submit(P, b if k > 1 else b[0], rtol=RTOL))
+        due += gap
+    done.wait()
+    wall = time.perf_counter() - t0
+    th.join()
+    srv.close()
+    lat.sort()
+
+    def pct(p):
+        return lat[min(len(lat) - 1, int(math.ceil(p / 100.0 * len(lat))) - 1)]
+
+    return {"offered_rhs_per_s": rate_rhs, "requests": len(sizes), "rhs": int(sum(sizes)),
+            "solves_per_s": sum(sizes) / wall, "latency_ms": {"p50": pct(50), "p99": pct(99)},
+            "stream": "Poisson arrivals (seed %d), 1-64 right-hand sides per request, "
+                      "continuous batching into 32 slots" % seed}
+
+
 def replica_barrier(world):
     """Barrier across the replicas (no-op for one process)."""
     if world > 1:
@@ -280,6 +338,10 @@ def gpu_arm(a):
     t1 = max_over_ranks(sum(ms1) / 1e3)
     t1_64 = max_over_ranks(sum(ms1_64) / 1e3)
 
+    # config 5: a Poisson stream of requests at 0.8 x the measured batch rate
+    P.set_precision("fp32")
+    serving = serving_run(bddc, P, wl.n_dof, 0.8 * value / world, 3.0, 5001)
+
     # end to end: host buffers (pinned), copies inside the timed call
     P.set_precision("fp32")
     bh = torch.from_numpy(Bh).pin_memory()
@@ -350,6 +412,7 @@ def gpu_arm(a):
                    "l2": "512 MiB buffer written between timed steps (untimed)"},
         "latency_ms": {"p50": pct(lat, 50), "p99": pct(lat, 99),
                        "what": "one right-hand side per solve, FP32 apply"},
+        "serving": serving,
         "iterations": iters,
         "compare": {"fp64_solves_per_s": world * BATCH * len(ms64) / t64,
                     "fp64_iterations": inf64[0][0]["iters"],

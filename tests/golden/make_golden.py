@@ -25,6 +25,11 @@ WORKLOADS = {
     "three_level_blocks_1024": lambda: inputs.three_level_blocks(),
 }
 SAMPLE_STRIDE = 997
+LAM_EDGES = 2048          # at most about this many edges per level keep their eigenvalues
+
+
+def _stride(n_edges):
+    return max(1, -(-n_edges // LAM_EDGES))
 
 
 def make(name):
@@ -45,7 +50,10 @@ def make(name):
         "omega_tilde": H.info["omega_tilde"],
         "n_sel": [[int(r["n_sel"]) for r in reps] for reps in H.info["edge_reports"]],
         "edge_pairs": [[list(map(int, r["pair"])) for r in reps] for reps in H.info["edge_reports"]],
-        "lam_top": [[[float(v) for v in r["lam"][:4]] for r in reps] for reps in H.info["edge_reports"]],
+        # top eigenvalues of every LAM_STRIDE-th edge on levels with many edges
+        "lam_stride": [_stride(len(reps)) for reps in H.info["edge_reports"]],
+        "lam_top": [[[float("%.15g" % v) for v in r["lam"][:4]] for r in reps[::_stride(len(reps))]]
+                    for reps in H.info["edge_reports"]],
         "pcg": {"rtol": 1e-8, "iters": res.iters, "kappa": res.kappa, "relres_true": res.relres_true},
         "x_sample_stride": SAMPLE_STRIDE,
         "x_sample": [float(v) for v in res.x[idx]],
