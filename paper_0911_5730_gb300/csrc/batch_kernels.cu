@@ -36,7 +36,9 @@ inline void launch_plain(void (*k)(KArgs...), int grid, int block, size_t smem, 
 // N consecutive storage elements (N * sizeof(T) bytes aligned) into accumulators.
 template <class T, class ACC, int N>
 __device__ __forceinline__ void load_vec(const T *src, ACC (&v)[N]) {
-    if constexpr (std::is_same<T, double>::value) {
+    if constexpr (N == 1) {
+        v[0] = ld<T, ACC>(src);
+    } else if constexpr (std::is_same<T, double>::value) {
 #pragma unroll
         for (int i = 0; i < N / 2; ++i) {
             const double2 q = reinterpret_cast<const double2 *>(src)[i];
@@ -75,18 +77,21 @@ __device__ __forceinline__ void load_vec(const T *src, ACC (&v)[N]) {
     }
 }
 
-// The batched Dirichlet kernel gives one block of kDW warps to one
-// substructure.  Warp w takes right-hand sides 8w .. 8w+7; lane 4g + h holds
-// rows h*RPL .. h*RPL + RPL - 1 (RPL = BP / 4) of every block of right-hand
-// side 8w + g.  The blocks' warps only meet at the gathers and the coupling
-// terms; the sweeps run without block barriers.
-constexpr int kDW = 4;
+// The batched Dirichlet kernel gives one block of LR warps to one
+// substructure, LR lanes to a right-hand side: warp w takes right-hand sides
+// (32/LR) w .. (32/LR)(w+1) - 1; lane LR g + h holds rows h*RPL .. h*RPL +
+// RPL - 1 (RPL = BP / LR) of every block of right-hand side (32/LR) w + g.
+// The block's warps only meet at the gathers and the coupling terms; the
+// sweeps run without block barriers.  LR = 8 for BP >= 16 (eight warps per
+// substructure), 4 for BP = 8.
+constexpr int kMaxDW = 8;
+template <int BP> __host__ __device__ constexpr int lanes_per_rhs() { return BP >= 16 ? 8 : 4; }
 
 template <class T, class ACC, int BP> struct DirSmemB {
     static size_t bytes(const DevLevel &L) {
         return al16(sizeof(T) * (size_t)L.max_fac) + al16(sizeof(ACC) * (size_t)L.max_m * BP * 32) +
                al16(sizeof(ACC) * (size_t)(L.max_nG > 0 ? L.max_nG : 1) * 32) + al16((size_t)L.max_irec) +
-               al16(sizeof(ACC) * (size_t)(L.max_coo > 0 ? L.max_coo : 1)) + al16(8 * 32 * kDW + 16) +
+               al16(sizeof(ACC) * (size_t)(L.max_coo > 0 ? L.max_coo : 1)) + al16(8 * 32 * kMaxDW + 16) +
                8 * (kChunksB + 1) + 16;
     }
 };
@@ -96,9 +101,10 @@ template <class T, class ACC, int BP> struct DirSmemB {
 // L_{j,j-1}] of BP x BP each, element (r, c) at c * BP + (r ^ c), Linv_j lower
 // triangular (zeros stored above the diagonal).
 template <class T, class ACC, int BP, bool POST>
-__global__ void __launch_bounds__(32 * kDW) k_dir_b(DevLevel L, BatchLevel B, const double *r, double *z,
-                                                    const int *skip, RzBatch rz) {
-    constexpr int BB = BP * BP, RPL = BP / 4;
+__global__ void __launch_bounds__(32 * lanes_per_rhs<BP>()) k_dir_b(DevLevel L, BatchLevel B, const double *r,
+                                                                    double *z, const int *skip, RzBatch rz) {
+    constexpr int LR = lanes_per_rhs<BP>(), kDW = LR;
+    constexpr int BB = BP * BP, RPL = BP / LR;
     extern __shared__ __align__(16) unsigned char smem_b[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int sub = blockIdx.x;
@@ -112,7 +118,7 @@ __global__ void __launch_bounds__(32 * kDW) k_dir_b(DevLevel L, BatchLevel B, co
     ACC *cvs = reinterpret_cast<ACC *>(p);  p += al16(sizeof(ACC) * (size_t)(L.max_coo > 0 ? L.max_coo : 1));
     double *red = reinterpret_cast<double *>(p);   // [kDW][32] partials and a flag word
     int *flag = reinterpret_cast<int *>(red + 32 * kDW);
-    p += al16(8 * 32 * kDW + 16);
+    p += al16(8 * 32 * kMaxDW + 16);
     unsigned long long *bars = reinterpret_cast<unsigned long long *>(p);   // kChunksB factor + 1 record
 
     const int nI = L.nI[sub], nG = L.nG[sub], m = L.nblk[sub];
@@ -197,10 +203,10 @@ __global__ void __launch_bounds__(32 * kDW) k_dir_b(DevLevel L, BatchLevel B, co
     }
     __syncthreads();
 
-    const int g = lane >> 2, h = lane & 3;
-    const int kc = warp * 8 + g;           // column of xs: the right-hand side of this lane
+    const int g = lane / LR, h = lane % LR;
+    const int kc = warp * (32 / LR) + g;   // column of xs: the right-hand side of this lane
     const int rb = h * RPL;                // first row of this lane within a block
-    const int src0 = lane & ~3;            // lane holding rows 0 .. RPL-1 of the same right-hand side
+    const int src0 = lane & ~(LR - 1);     // lane holding rows 0 .. RPL-1 of the same right-hand side
     int cw = 0;
     bool ok = true;
     ACC xp[RPL];
@@ -248,22 +254,29 @@ __global__ void __launch_bounds__(32 * kDW) k_dir_b(DevLevel L, BatchLevel B, co
     if (ok) {
         // backward sweep: z_j = Linv_j^T (y_j - L_{j+1,j}^T z_{j+1}).  Each lane
         // forms the column partials of its own rows for all BP output rows and
-        // the four lanes of a right-hand side reduce-scatter them.
-        const bool hiA = (h & 2) != 0, hiB = (h & 1) != 0;
+        // the LR lanes of a right-hand side reduce-scatter them: in the round
+        // with partner h ^ st a lane keeps the half of the rows whose bit st of
+        // the lane index it carries, so it ends with its own RPL rows.
         auto reduce_scatter = [&](ACC (&part)[BP], ACC (&out)[RPL]) {
-            ACC half[BP / 2];
+            ACC buf[BP];
 #pragma unroll
-            for (int i = 0; i < BP / 2; ++i) {
-                const ACC send = hiA ? part[i] : part[BP / 2 + i];
-                const ACC keep = hiA ? part[BP / 2 + i] : part[i];
-                half[i] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+            for (int i = 0; i < BP; ++i) buf[i] = part[i];
+            int len = BP;
+#pragma unroll
+            for (int st = LR / 2; st >= 1; st /= 2) {
+                len /= 2;
+                const bool hi = (h & st) != 0;
+#pragma unroll
+                for (int i = 0; i < BP / 2; ++i) {
+                    if (i < len) {
+                        const ACC send = hi ? buf[i] : buf[len + i];
+                        const ACC keep = hi ? buf[len + i] : buf[i];
+                        buf[i] = keep + __shfl_xor_sync(0xffffffffu, send, st);
+                    }
+                }
             }
 #pragma unroll
-            for (int i = 0; i < RPL; ++i) {
-                const ACC send = hiB ? half[i] : half[RPL + i];
-                const ACC keep = hiB ? half[RPL + i] : half[i];
-                out[i] = keep + __shfl_xor_sync(0xffffffffu, send, 1);
-            }
+            for (int i = 0; i < RPL; ++i) out[i] = buf[i];
         };
         ACC zn[RPL];
 #pragma unroll
@@ -699,7 +712,7 @@ __global__ void k_b_init(int n, int K, const double *b, int64_t ldb, double *x, 
 // for all K right-hand sides; p_new is formed once per entry of the tile and
 // its halo in shared memory (the FP64 pipe is the limit), from p_old in one
 // direction buffer, and written to the other.
-constexpr int BT_X = 32, BT_Y = 8;
+constexpr int BT_X = 16, BT_Y = 8;
 constexpr size_t bt_smem(int K) { return (size_t)(BT_Y + 2) * (BT_X + 2) * K * 8; }
 
 __global__ void k_b_dir_spmv(int nx, int K, const double *__restrict__ w, const double *__restrict__ z,
@@ -945,8 +958,9 @@ void dir_b_launch(const DevLevel &L, const BatchLevel &B, bool post, const doubl
                   const int *skip, cudaStream_t s, const RzBatch *rz) {
     const size_t sm = DirSmemB<T, ACC, BP>::bytes(L);
     const RzBatch none{nullptr, nullptr, nullptr, nullptr};
-    if (!post) launch_plain(k_dir_b<T, ACC, BP, false>, L.nsub, 32 * kDW, sm, s, L, B, r, z, skip, none);
-    else launch_plain(k_dir_b<T, ACC, BP, true>, L.nsub, 32 * kDW, sm, s, L, B, r, z, skip, rz ? *rz : none);
+    constexpr int nt = 32 * lanes_per_rhs<BP>();
+    if (!post) launch_plain(k_dir_b<T, ACC, BP, false>, L.nsub, nt, sm, s, L, B, r, z, skip, none);
+    else launch_plain(k_dir_b<T, ACC, BP, true>, L.nsub, nt, sm, s, L, B, r, z, skip, rz ? *rz : none);
 }
 
 template <class T, class ACC>
