@@ -99,6 +99,167 @@ __global__ void k_pre(DevLevel L, const double *r, const int *skip) {
     }
 }
 
+// Dirichlet solves of large or irregular substructures (no block size the
+// warp kernels take): one block of kSB threads per substructure streams the
+// factor blocks [Linv_j | L_{j,j-1}] through a ring of kNS shared-memory
+// stages with bulk copies (block i always in stage i % kNS), so the copies of
+// the next blocks overlap the solve of the current one.  The forward sweep
+// refills a stage as soon as its block is used; the backward sweep starts
+// from the kNS blocks the forward sweep left in the ring and refills the
+// stage of block j+1 after step j (the last step that needs L_{j+1,j}).
+// kTPR threads share a row of a block solve (column-strided partial sums,
+// shuffle-reduced).  Every wait is bounded; a block whose wait gives up
+// flags *L.err, lets its copies land (bounded) and leaves.
+constexpr int kSB = 256, kNS = 3, kTPR = 4;
+
+struct StreamSmem {
+    size_t stage, x, tmp, vg, total;
+    template <class T, class ACC> __host__ __device__ static StreamSmem of(const DevLevel &L) {
+        StreamSmem m;
+        const size_t mb = L.max_b > 0 ? L.max_b : 1;
+        m.stage = al16(2 * mb * mb * sizeof(T) + 32);        // plus slack to align each copy
+        m.x = al16(sizeof(ACC) * (size_t)(L.max_m > 0 ? L.max_m : 1) * mb);
+        m.tmp = al16(sizeof(ACC) * mb);
+        m.vg = al16(sizeof(ACC) * (size_t)(L.max_nG > 0 ? L.max_nG : 1));
+        m.total = kNS * m.stage + m.x + m.tmp + m.vg + 8 * kNS + 16;
+        return m;
+    }
+};
+
+template <class T, class ACC, bool POST>
+__global__ void __launch_bounds__(kSB) k_dir_s(DevLevel L, const double *r, double *z, const int *skip) {
+    if (skip && *skip) return;
+    extern __shared__ __align__(16) unsigned char smem_s[];
+    const StreamSmem ly = StreamSmem::of<T, ACC>(L);
+    unsigned char *ring = smem_s;
+    ACC *x = reinterpret_cast<ACC *>(smem_s + kNS * ly.stage);
+    ACC *tmp = reinterpret_cast<ACC *>(reinterpret_cast<unsigned char *>(x) + ly.x);
+    ACC *vG = reinterpret_cast<ACC *>(reinterpret_cast<unsigned char *>(tmp) + ly.tmp);
+    unsigned long long *bars = reinterpret_cast<unsigned long long *>(reinterpret_cast<unsigned char *>(vG) + ly.vg);
+    const int sub = blockIdx.x, tid = threadIdx.x;
+    const int nI = L.nI[sub], nG = L.nG[sub], b = L.bsz[sub], m = nI > 0 ? L.nblk[sub] : 0;
+    const bool swz = L.bp != 0;
+    const OpSet<T> &O = Ops<T>::get(L);
+    const T *F = O.dir + L.offF[sub];
+    const size_t bb2 = 2 * (size_t)b * b;
+    // block i: its bytes rounded out to 16-byte boundaries, and where it starts in its stage
+    auto issue = [&](int i) {
+        const uintptr_t a = reinterpret_cast<uintptr_t>(F + (size_t)i * bb2);
+        const uintptr_t al = a & ~uintptr_t(15);
+        const uintptr_t ae = (a + bb2 * sizeof(T) + 15) & ~uintptr_t(15);
+        mbar_expect(&bars[i % kNS], (unsigned)(ae - al));
+        bulk_copy(ring + (size_t)(i % kNS) * ly.stage, reinterpret_cast<const void *>(al), (unsigned)(ae - al),
+                  &bars[i % kNS]);
+    };
+    auto blk = [&](int i) {
+        const uintptr_t a = reinterpret_cast<uintptr_t>(F + (size_t)i * bb2);
+        return reinterpret_cast<const T *>(ring + (size_t)(i % kNS) * ly.stage + (a & 15));
+    };
+    if (tid == 0) {
+        for (int s = 0; s < kNS; ++s) mbar_init(&bars[s]);
+        for (int i = 0; i < kNS && i < m; ++i) issue(i);
+    }
+    const int *iI = L.idxI + L.offI[sub];
+    const int *iG = L.idxG + L.offG[sub];
+    for (int i = tid; i < m * b; i += kSB) x[i] = i < nI ? (ACC)r[iI[i]] : (ACC)0;
+    if (POST) {
+        for (int q = tid; q < nG; q += kSB) vG[q] = (ACC)L.uB[iG[q]];
+        __syncthreads();
+        for (int64_t k = L.offCOO[sub] + tid; k < L.offCOO[sub + 1]; k += kSB)
+            atomicAdd(&x[L.cooI[k]], -ld<T, ACC>(O.aig + k) * vG[L.cooG[k]]);
+    } else {
+        for (int q = tid; q < nG; q += kSB) vG[q] = 0;
+    }
+    __syncthreads();
+    unsigned par = 0;                     // bit s: parity of the next phase of stage s
+    const int part = tid % kTPR, r0 = tid / kTPR;
+    constexpr int RPP = kSB / kTPR;       // rows per pass
+    bool ok = true;
+    auto wait_block = [&](int i) {
+        const int s = i % kNS;
+        const bool got = mbar_wait(&bars[s], (par >> s) & 1u);
+        par ^= 1u << s;
+        return __syncthreads_and(got) != 0;
+    };
+    for (int j = 0; j < m && ok; ++j) {
+        if (!wait_block(j)) { ok = false; break; }
+        const T *Li = blk(j), *Ls = Li + (size_t)b * b;
+        for (int pass = 0; pass * RPP < b; ++pass) {      // the same passes in every thread
+            const int rr = r0 + pass * RPP;
+            ACC a = 0;
+            if (rr < b && j > 0)
+                for (int c = part; c < b; c += kTPR)
+                    a += ld<T, ACC>(Ls + fpos(rr, c, b, swz)) * x[(j - 1) * b + c];
+#pragma unroll
+            for (int o = kTPR / 2; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+            if (rr < b && part == 0) tmp[rr] = x[j * b + rr] - a;
+        }
+        __syncthreads();
+        for (int pass = 0; pass * RPP < b; ++pass) {
+            const int rr = r0 + pass * RPP;
+            ACC a = 0;
+            if (rr < b)
+                for (int c = part; c <= rr; c += kTPR) a += ld<T, ACC>(Li + fpos(rr, c, b, swz)) * tmp[c];
+#pragma unroll
+            for (int o = kTPR / 2; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+            if (rr < b && part == 0) x[j * b + rr] = a;
+        }
+        __syncthreads();
+        if (tid == 0 && j + kNS < m) issue(j + kNS);
+    }
+    for (int j = m - 1; j >= 0 && ok; --j) {
+        if (j < m - kNS && !wait_block(j)) { ok = false; break; }
+        const T *Li = blk(j);
+        for (int pass = 0; pass * RPP < b; ++pass) {
+            const int rr = r0 + pass * RPP;
+            ACC a = 0;
+            if (rr < b && j < m - 1) {
+                const T *Ls1 = blk(j + 1) + (size_t)b * b;     // L_{j+1,j}^T: entry (rr, c) is (c, rr)
+                for (int c = part; c < b; c += kTPR)
+                    a += ld<T, ACC>(Ls1 + fpos(c, rr, b, swz)) * x[(j + 1) * b + c];
+            }
+#pragma unroll
+            for (int o = kTPR / 2; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+            if (rr < b && part == 0) tmp[rr] = x[j * b + rr] - a;
+        }
+        __syncthreads();
+        for (int pass = 0; pass * RPP < b; ++pass) {
+            const int rr = r0 + pass * RPP;
+            ACC a = 0;
+            if (rr < b)
+                for (int c = rr + part; c < b; c += kTPR) a += ld<T, ACC>(Li + fpos(c, rr, b, swz)) * tmp[c];
+#pragma unroll
+            for (int o = kTPR / 2; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+            if (rr < b && part == 0) x[j * b + rr] = a;
+        }
+        __syncthreads();
+        // block j+1 is no longer needed: its stage takes block j+1-kNS
+        if (tid == 0 && j + 1 < m && j + 1 - kNS >= 0 && j + 1 - kNS < m - kNS) issue(j + 1 - kNS);
+    }
+    if (!ok) {
+        if (tid == 0) {
+            atomicExch(L.err, 1);
+            for (int s = 0; s < kNS; ++s) mbar_wait(&bars[s], (par >> s) & 1u);   // bounded
+        }
+        return;
+    }
+    if (!POST) {
+        for (int64_t k = L.offCOO[sub] + tid; k < L.offCOO[sub + 1]; k += kSB)
+            atomicAdd(&vG[L.cooG[k]], ld<T, ACC>(O.aig + k) * x[L.cooI[k]]);
+        __syncthreads();
+        for (int q = tid; q < nG; q += kSB) {
+            if (vG[q] != (ACC)0) atomicAdd(&L.rB[iG[q]], -(double)vG[q]);
+            L.uB[iG[q]] = 0.0;   // consumed by the previous post-correction
+        }
+    } else {
+        for (int i = tid; i < nI; i += kSB) z[iI[i]] = (double)x[i];
+        for (int64_t k = L.offOwn[sub] + tid; k < L.offOwn[sub + 1]; k += kSB) {
+            const int id = L.own[k];
+            z[L.ifaceDof[id]] = L.uB[id];
+        }
+    }
+}
+
 // (6)-(8): f = D_i r_B on Gamma; w = N_i f; r_c += Psi_i^T f.
 template <class T, class ACC>
 __global__ void k_neumann(DevLevel L, const double *r, const int *skip) {
@@ -1008,13 +1169,26 @@ int vec_grid(int64_t n) {
     return (int)g;
 }
 
+// Generic path: the streaming kernel when its stages fit in shared memory,
+// else one warp per substructure reading the factor from global memory.
+template <class T, class ACC> bool stream_fits(const DevLevel &L) {
+    return StreamSmem::of<T, ACC>(L).total <= 227 * 1024;
+}
 template <class T, class ACC> void pre_t(const DevLevel &L, const double *r, const int *skip,
                                          cudaStream_t s) {
+    if (stream_fits<T, ACC>(L)) {
+        k_dir_s<T, ACC, false><<<L.nsub, kSB, StreamSmem::of<T, ACC>(L).total, s>>>(L, r, nullptr, skip);
+        return;
+    }
     const size_t sm = sizeof(ACC) * ((size_t)L.max_m * L.max_b + L.max_b + L.max_nG);
     k_pre<T, ACC><<<L.nsub, 32, sm, s>>>(L, r, skip);
 }
 template <class T, class ACC> void post_t(const DevLevel &L, const double *r, double *z,
                                           const int *skip, cudaStream_t s) {
+    if (stream_fits<T, ACC>(L)) {
+        k_dir_s<T, ACC, true><<<L.nsub, kSB, StreamSmem::of<T, ACC>(L).total, s>>>(L, r, z, skip);
+        return;
+    }
     const size_t sm = sizeof(ACC) * ((size_t)L.max_m * L.max_b + L.max_b + L.max_nG);
     k_post<T, ACC><<<L.nsub, 32, sm, s>>>(L, r, z, skip);
 }
@@ -1114,6 +1288,12 @@ bool warp_path(const DevLevel &L, int prec) {
 void prepare_apply_kernels() {
     const int big = (int)kSmemMax;
 #define BDDC_SMEM_ATTR(k) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, big)
+    BDDC_SMEM_ATTR((k_dir_s<double, double, false>));
+    BDDC_SMEM_ATTR((k_dir_s<double, double, true>));
+    BDDC_SMEM_ATTR((k_dir_s<float, float, false>));
+    BDDC_SMEM_ATTR((k_dir_s<float, float, true>));
+    BDDC_SMEM_ATTR((k_dir_s<__nv_bfloat16, float, false>));
+    BDDC_SMEM_ATTR((k_dir_s<__nv_bfloat16, float, true>));
     BDDC_SMEM_ATTR((k_dir_w<double, double, 8, false>));
     BDDC_SMEM_ATTR((k_dir_w<double, double, 8, true>));
     BDDC_SMEM_ATTR((k_dir_w<double, double, 16, false>));

@@ -25,6 +25,7 @@ WORKLOADS = {
     "three_level_blocks_1024": lambda: inputs.three_level_blocks(),
 }
 SAMPLE_STRIDE = 997
+APPLY_SEED = 19
 LAM_EDGES = 2048          # at most about this many edges per level keep their eigenvalues
 
 
@@ -38,6 +39,8 @@ def make(name):
     H = bddc.build_workload(wl)
     t_setup = time.time() - t0
     b = wl.rhs()
+    r_apply = inputs.normal_rhs(wl.n_dof, APPLY_SEED)
+    z_apply = H.apply(r_apply)
     t0 = time.time()
     res = pcg.pcg(H.A, b, H.apply, rtol=1e-8)
     t_solve = time.time() - t0
@@ -58,6 +61,9 @@ def make(name):
         "x_sample_stride": SAMPLE_STRIDE,
         "x_sample": [float(v) for v in res.x[idx]],
         "x_norm": float(np.linalg.norm(res.x)),
+        # one FP64 apply z = M^{-1} r of r = normal_rhs(n, APPLY_SEED), sampled
+        "apply": {"seed": APPLY_SEED, "z_sample": [float(v) for v in z_apply[idx]],
+                  "z_norm": float(np.linalg.norm(z_apply))},
         "oracle_seconds": {"setup": t_setup, "solve": t_solve},
     }
     with open(os.path.join(HERE, name + ".json"), "w") as f:

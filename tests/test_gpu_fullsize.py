@@ -50,6 +50,16 @@ def test_selection_full_size(prob):
     assert abs(q["omega_tilde"] - g["omega_tilde"]) <= 1e-7 * g["omega_tilde"]
 
 
+def test_apply_full_size_fp64(prob):
+    wl, P, g = prob
+    P.set_precision("fp64")
+    r = torch.tensor(inputs.normal_rhs(wl.n_dof, g["apply"]["seed"]), device="cuda")
+    z = P.apply(r).cpu().numpy()
+    ref = np.array(g["apply"]["z_sample"])
+    assert np.linalg.norm(z[::g["x_sample_stride"]] - ref) <= 1e-10 * np.linalg.norm(ref)
+    assert abs(np.linalg.norm(z) - g["apply"]["z_norm"]) <= 1e-10 * g["apply"]["z_norm"]
+
+
 def test_pcg_full_size_fp64(prob):
     wl, P, g = prob
     P.set_precision("fp64")
