@@ -426,6 +426,8 @@ def gpu_arm(a):
                 "d2h_bytes_per_step": 8 * wl.n_dof * BATCH},
         "roofline": roof,
         "kernels_fp32_apply_batch": kern,
+        "autotuned": {"stencil_tile": P.query(level=None)["tuned_tile"][:2],
+                      "top_product_rows_per_block": P.query(level=None)["tuned_tile"][2]},
         "gpu_launches": launches,
         "cpu_baseline": cpu,
         "clocks": clocks,

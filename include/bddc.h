@@ -111,6 +111,11 @@ typedef struct {
     int64_t neumann_entries[3];   /* sum over substructures of nG^2 */
     int64_t psi_entries[3];       /* sum over substructures of nc * nG */
     int32_t n_interface[3];       /* interface DOFs of the level (each counted once) */
+    /* tile shapes the autotuner chose for the batch kernels of this context
+     * (timed on the context's own operators when its batch workspace is first
+     * used): node tile of the batched PCG stencil (x, y) and rows per block of
+     * the top-level product; 0 before the first batched call */
+    int32_t tuned_tile[3];
     int32_t reserved2;
 } bddc_info;
 

@@ -62,7 +62,8 @@ class Info(C.Structure):
                 ("sum_coarse_local", C.c_int64 * 3), ("band_nnz", C.c_int64 * 3),
                 ("block_entries", C.c_int64 * 3), ("coupling_nnz", C.c_int64 * 3),
                 ("neumann_entries", C.c_int64 * 3), ("psi_entries", C.c_int64 * 3),
-                ("n_interface", C.c_int32 * 3), ("reserved2", C.c_int32)]
+                ("n_interface", C.c_int32 * 3), ("tuned_tile", C.c_int32 * 3),
+                ("reserved2", C.c_int32)]
 
 
 _lib = None
@@ -288,7 +289,8 @@ class Problem:
                "n_corners": list(info.n_corners)[:info.levels - 1],
                "omega_tilde": info.omega_tilde,
                "omega_level": list(info.omega_level)[:info.levels - 1],
-               "setup_ms": info.setup_ms, "device_bytes": info.device_bytes}
+               "setup_ms": info.setup_ms, "device_bytes": info.device_bytes,
+               "tuned_tile": list(info.tuned_tile)}
         nl = info.levels - 1
         for key in ("sum_interior", "sum_interface", "sum_coarse_local", "band_nnz",
                     "block_entries", "coupling_nnz", "neumann_entries", "psi_entries",

@@ -15,6 +15,7 @@
 #include "internal.h"
 #include "device_util.cuh"
 
+#include <algorithm>
 #include <type_traits>
 
 namespace bddc {
@@ -535,17 +536,23 @@ __global__ void k_avg_b(DevLevel L, BatchLevel B, int pidx, const int *skip, uns
 
 // Y = A X, A dense n x n row-major (leading dimension ld, a multiple of 4,
 // zero padded), X and Y interleaved [ld][K] (X zero on rows [n, ld)).  FP64;
-// the FP64 pipe bounds it.  A block owns GM_R rows; the columns stream in
-// chunks of GM_C through a GM_S-stage ring of bulk copies (the GM_R row
-// segments of A and the GM_C x K block of X, contiguous in the interleaved
-// layout), thread 0 refilling a stage once all warps have used it.  Warp w
-// computes rows 2w, 2w + 1 for all K columns (lane k: column k), reading the
-// A entries by broadcast.
-constexpr int GM_R = 16, GM_C = 64, GM_S = 3;
-constexpr size_t GM_STAGE = (size_t)GM_R * GM_C * 8 + (size_t)GM_C * 32 * 8;
+// the FP64 pipe bounds it.  A block of eight warps owns 8 RPW rows; the
+// columns stream in chunks of GM_C through a GM_S-stage ring of bulk copies
+// (the row segments of A and the GM_C x K block of X, contiguous in the
+// interleaved layout), thread 0 refilling a stage once all warps have used
+// it.  Warp w computes rows RPW w .. RPW w + RPW - 1 for all K columns (lane
+// k: column k), reading the A entries by broadcast.  RPW is chosen per
+// problem by the autotuner (gemm_tune).
+constexpr int GM_C = 64, GM_S = 3;
+__host__ __device__ constexpr size_t gm_stage(int rpw) {
+    return (size_t)8 * rpw * GM_C * 8 + (size_t)GM_C * 32 * 8;
+}
 
+template <int RPW>
 __global__ void __launch_bounds__(256) k_gemm_b(int n, int ld, const double *A, const double *X,
                                                 double *Y, int K, const int *skip, int *err) {
+    constexpr int GR = 8 * RPW;
+    constexpr size_t STAGE = gm_stage(RPW);
     extern __shared__ __align__(16) unsigned char smem_g[];
     __shared__ __align__(8) unsigned long long full[GM_S];
     __shared__ int ok_all;
@@ -553,8 +560,8 @@ __global__ void __launch_bounds__(256) k_gemm_b(int n, int ld, const double *A, 
     pdl_trigger();
     if (skip && *skip) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int row0 = blockIdx.x * GM_R;
-    const int nrow = n - row0 < GM_R ? n - row0 : GM_R;
+    const int row0 = blockIdx.x * GR;
+    const int nrow = n - row0 < GR ? n - row0 : GR;
     const int nchunk = (ld + GM_C - 1) / GM_C;
     if (threadIdx.x == 0) {
         for (int s = 0; s < GM_S; ++s) mbar_init(&full[s]);
@@ -562,19 +569,21 @@ __global__ void __launch_bounds__(256) k_gemm_b(int n, int ld, const double *A, 
     }
     __syncthreads();
     auto issue = [&](int c) {   // thread 0: chunk c into stage c % GM_S
-        unsigned char *st = smem_g + (size_t)(c % GM_S) * GM_STAGE;
+        unsigned char *st = smem_g + (size_t)(c % GM_S) * STAGE;
         const int c0 = c * GM_C;
         const int w = ld - c0 < GM_C ? ld - c0 : GM_C;
         const unsigned abytes = (unsigned)(w * 8), xbytes = (unsigned)((size_t)w * K * 8);
         mbar_expect(&full[c % GM_S], abytes * nrow + xbytes);
         for (int r = 0; r < nrow; ++r)
             bulk_copy(st + (size_t)r * GM_C * 8, A + (int64_t)(row0 + r) * ld + c0, abytes, &full[c % GM_S]);
-        bulk_copy(st + (size_t)GM_R * GM_C * 8, X + (int64_t)c0 * K, xbytes, &full[c % GM_S]);
+        bulk_copy(st + (size_t)GR * GM_C * 8, X + (int64_t)c0 * K, xbytes, &full[c % GM_S]);
     };
     if (threadIdx.x == 0)
         for (int c = 0; c < GM_S && c < nchunk; ++c) issue(c);
-    const int r0 = 2 * warp, r1 = r0 + 1;
-    double s0 = 0.0, s1 = 0.0, t0 = 0.0, t1 = 0.0;
+    const int rw = RPW * warp;
+    double sacc[RPW], tacc[RPW];
+#pragma unroll
+    for (int q = 0; q < RPW; ++q) { sacc[q] = 0.0; tacc[q] = 0.0; }
     for (int c = 0; c < nchunk; ++c) {
         const unsigned phase = (unsigned)((c / GM_S) & 1);
         if (!mbar_wait(&full[c % GM_S], phase)) {
@@ -582,22 +591,25 @@ __global__ void __launch_bounds__(256) k_gemm_b(int n, int ld, const double *A, 
         }
         __syncthreads();
         if (!ok_all) break;
-        const unsigned char *st = smem_g + (size_t)(c % GM_S) * GM_STAGE;
-        const double *As = reinterpret_cast<const double *>(st);
-        const double *Xs = reinterpret_cast<const double *>(st + (size_t)GM_R * GM_C * 8);
+        const unsigned char *st = smem_g + (size_t)(c % GM_S) * STAGE;
+        const double *As = reinterpret_cast<const double *>(st) + rw * GM_C;
+        const double *Xs = reinterpret_cast<const double *>(st + (size_t)GR * GM_C * 8);
         const int w = ld - c * GM_C < GM_C ? ld - c * GM_C : GM_C;
-        if (r0 < nrow) {
-            const double *a0 = As + r0 * GM_C, *a1 = As + r1 * GM_C;
+        if (rw < nrow) {
             int i = 0;
             for (; i + 1 < w; i += 2) {
                 const double x0 = lane < K ? Xs[i * K + lane] : 0.0;
                 const double x1 = lane < K ? Xs[(i + 1) * K + lane] : 0.0;
-                s0 = fma(a0[i], x0, s0); s1 = fma(a1[i], x0, s1);
-                t0 = fma(a0[i + 1], x1, t0); t1 = fma(a1[i + 1], x1, t1);
+#pragma unroll
+                for (int q = 0; q < RPW; ++q) {
+                    sacc[q] = fma(As[q * GM_C + i], x0, sacc[q]);
+                    tacc[q] = fma(As[q * GM_C + i + 1], x1, tacc[q]);
+                }
             }
             for (; i < w; ++i) {
                 const double x0 = lane < K ? Xs[i * K + lane] : 0.0;
-                s0 = fma(a0[i], x0, s0); s1 = fma(a1[i], x0, s1);
+#pragma unroll
+                for (int q = 0; q < RPW; ++q) sacc[q] = fma(As[q * GM_C + i], x0, sacc[q]);
             }
         }
         __syncthreads();                                   // every warp is done with the stage
@@ -610,8 +622,9 @@ __global__ void __launch_bounds__(256) k_gemm_b(int n, int ld, const double *A, 
         return;
     }
     if (lane < K) {
-        if (r0 < nrow) Y[(int64_t)(row0 + r0) * K + lane] = s0 + t0;
-        if (r1 < nrow) Y[(int64_t)(row0 + r1) * K + lane] = s1 + t1;
+#pragma unroll
+        for (int q = 0; q < RPW; ++q)
+            if (rw + q < nrow) Y[(int64_t)(row0 + rw + q) * K + lane] = sacc[q] + tacc[q];
     }
 }
 
@@ -709,12 +722,13 @@ __global__ void k_b_init(int n, int K, const double *b, int64_t ldb, double *x, 
 
 // First half of a batched PCG iteration: p_new = z + beta p_old, q = A p_new
 // and alpha_k = rho_k / (p_new . q).  A block owns a BT_X x BT_Y tile of nodes
+// (the tile shape is chosen per problem by the autotuner, dir_spmv_tune)
 // for all K right-hand sides; p_new is formed once per entry of the tile and
 // its halo in shared memory (the FP64 pipe is the limit), from p_old in one
 // direction buffer, and written to the other.
-constexpr int BT_X = 16, BT_Y = 8;
-constexpr size_t bt_smem(int K) { return (size_t)(BT_Y + 2) * (BT_X + 2) * K * 8; }
+__host__ __device__ constexpr size_t bt_smem(int tx, int ty, int K) { return (size_t)(ty + 2) * (tx + 2) * K * 8; }
 
+template <int BT_X, int BT_Y>
 __global__ void k_b_dir_spmv(int nx, int K, const double *__restrict__ w, const double *__restrict__ z,
                              double *p0, double *p1, double *__restrict__ q, double *part,
                              unsigned *counter, BatchScalars *sc, double *alphas) {
@@ -1034,8 +1048,13 @@ void prepare_batch_kernels() {
     BDDC_SMEM_ATTR_B((k_neu_b<__nv_bfloat16, float>));
     // (k_gemm_b and k_b_dir_spmv also have static shared memory: their
     // dynamic limits are their own sizes)
-    cudaFuncSetAttribute(k_b_dir_spmv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bt_smem(kMaxBatch));
-    cudaFuncSetAttribute(k_gemm_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(GM_S * GM_STAGE));
+#define BDDC_TILE_ATTR(X, Y) \
+    cudaFuncSetAttribute(k_b_dir_spmv<X, Y>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bt_smem(X, Y, kMaxBatch));
+    BDDC_TILE_ATTR(16, 8) BDDC_TILE_ATTR(32, 4) BDDC_TILE_ATTR(32, 8) BDDC_TILE_ATTR(8, 16)
+#undef BDDC_TILE_ATTR
+    cudaFuncSetAttribute(k_gemm_b<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(GM_S * gm_stage(1)));
+    cudaFuncSetAttribute(k_gemm_b<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(GM_S * gm_stage(2)));
+    cudaFuncSetAttribute(k_gemm_b<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(GM_S * gm_stage(4)));
     BDDC_SMEM_ATTR_B((k_avg_b<double, double>)); BDDC_SMEM_ATTR_B((k_avg_b<float, float>));
     BDDC_SMEM_ATTR_B((k_avg_b<__nv_bfloat16, float>));
 #undef BDDC_DIR_B
@@ -1068,11 +1087,49 @@ void apply_level_post_b(const DevLevel &L, const BatchLevel &B, int prec, const 
     if (ev) cudaEventRecord(ev[2], s);
 }
 
+// Variants the autotuner chooses from.
+constexpr int kTiles[][2] = {{16, 8}, {32, 4}, {32, 8}, {8, 16}};
+constexpr int kNTiles = 4;
+constexpr int kRpw[] = {1, 2, 4};
+constexpr int kNRpw = 3;
+
 void launch_gemm_b(int n, int ld, const double *A, const double *X, double *Y, int K, const int *skip,
-                   int *err, cudaStream_t s) {
+                   int *err, cudaStream_t s, int variant) {
     if (n <= 0) return;
-    launch_plain(k_gemm_b, (n + GM_R - 1) / GM_R, 256, GM_S * GM_STAGE, s, n, ld, A, X, Y, K, skip, err);
+    switch (variant) {
+    case 0: launch_plain(k_gemm_b<1>, (n + 7) / 8, 256, GM_S * gm_stage(1), s, n, ld, A, X, Y, K, skip, err); break;
+    case 2: launch_plain(k_gemm_b<4>, (n + 31) / 32, 256, GM_S * gm_stage(4), s, n, ld, A, X, Y, K, skip, err); break;
+    default: launch_plain(k_gemm_b<2>, (n + 15) / 16, 256, GM_S * gm_stage(2), s, n, ld, A, X, Y, K, skip, err);
+    }
 }
+
+// Mean device time of `reps` launches of f (one untimed launch first).
+template <class F> float time_launches(F f, int reps, cudaStream_t s) {
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    f();
+    cudaEventRecord(e0, s);
+    for (int i = 0; i < reps; ++i) f();
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return ms / reps;
+}
+
+int gemm_tune(int n, int ld, const double *A, const double *X, double *Y, int K, int *err, cudaStream_t s) {
+    int best = 1;
+    float tb = 1e30f;
+    for (int v = 0; v < kNRpw; ++v) {
+        const float t = time_launches([&] { launch_gemm_b(n, ld, A, X, Y, K, nullptr, err, s, v); }, 3, s);
+        if (t < tb) { tb = t; best = v; }
+    }
+    return best;
+}
+int gemm_rows(int variant) { return 8 * kRpw[variant < 0 || variant >= kNRpw ? 1 : variant]; }
 
 void launch_b_init(int n, int K, const double *b, int64_t ldb, double *x, double *r, double *p,
                    double *part, unsigned *counter, BatchScalars *sc, double tol, int maxit,
@@ -1080,15 +1137,45 @@ void launch_b_init(int n, int K, const double *b, int64_t ldb, double *x, double
     const int64_t nK = (int64_t)n * K;
     k_b_init<<<vgrid_b(nK, K), bblock(K), 0, s>>>(n, K, b, ldb, x, r, p, part, counter, sc, tol, maxit);
 }
-int launch_b_dir_spmv_blocks(int nx) {
+template <int TX, int TY> int tile_blocks(int nx) {
     const int n1 = nx - 1;
-    return ((n1 + BT_X - 1) / BT_X) * ((n1 + BT_Y - 1) / BT_Y);
+    return ((n1 + TX - 1) / TX) * ((n1 + TY - 1) / TY);
+}
+int launch_b_dir_spmv_blocks(int nx) {   // the most blocks any tile variant launches
+    return std::max(std::max(tile_blocks<16, 8>(nx), tile_blocks<32, 4>(nx)),
+                    std::max(tile_blocks<32, 8>(nx), tile_blocks<8, 16>(nx)));
+}
+template <int TX, int TY>
+void dir_spmv_v(int nx, int K, const double *w, const double *z, double *p0, double *p1, double *q,
+                double *part, unsigned *counter, BatchScalars *sc, double *alphas, cudaStream_t s) {
+    launch_plain(k_b_dir_spmv<TX, TY>, tile_blocks<TX, TY>(nx), bblock(K), bt_smem(TX, TY, K), s, nx, K, w, z,
+                 p0, p1, q, part, counter, sc, alphas);
 }
 void launch_b_dir_spmv(int nx, int K, const double *w, const double *z, double *p0, double *p1,
                        double *q, double *part, unsigned *counter, BatchScalars *sc, double *alphas,
-                       cudaStream_t s) {
-    launch_plain(k_b_dir_spmv, launch_b_dir_spmv_blocks(nx), bblock(K), bt_smem(K), s, nx, K, w, z, p0, p1,
-                 q, part, counter, sc, alphas);
+                       cudaStream_t s, int variant) {
+    switch (variant) {
+    case 1: dir_spmv_v<32, 4>(nx, K, w, z, p0, p1, q, part, counter, sc, alphas, s); break;
+    case 2: dir_spmv_v<32, 8>(nx, K, w, z, p0, p1, q, part, counter, sc, alphas, s); break;
+    case 3: dir_spmv_v<8, 16>(nx, K, w, z, p0, p1, q, part, counter, sc, alphas, s); break;
+    default: dir_spmv_v<16, 8>(nx, K, w, z, p0, p1, q, part, counter, sc, alphas, s);
+    }
+}
+int dir_spmv_tune(int nx, int K, const double *w, const double *z, double *p0, double *p1, double *q,
+                  double *part, unsigned *counter, BatchScalars *sc, double *alphas, cudaStream_t s) {
+    int best = 0;
+    float tb = 1e30f;
+    for (int v = 0; v < kNTiles; ++v) {
+        const float t = time_launches(
+            [&] { launch_b_dir_spmv(nx, K, w, z, p0, p1, q, part, counter, sc, alphas, s, v); }, 3, s);
+        if (t < tb) { tb = t; best = v; }
+    }
+    return best;
+}
+void dir_spmv_tile(int variant, int *tx, int *ty) {
+    const int v = variant < 0 || variant >= kNTiles ? 0 : variant;
+    *tx = kTiles[v][0];
+    *ty = kTiles[v][1];
 }
 void launch_b_update(int n, int K, double *x, double *r, const double *p0, const double *p1,
                      const double *q, double *part, unsigned *counter, BatchScalars *sc, cudaStream_t s) {

@@ -73,6 +73,7 @@ struct BatchWs {
     BatchScalars *hsc = nullptr;         // pinned mirror
     double *hnrm = nullptr;              // pinned
     std::map<int, cudaGraphExec_t> graphs;   // key: prec * 64 + K
+    int tile_v = 0, gemm_v = 1;              // autotuned variants (dir_spmv_tune, gemm_tune)
     int last_iters = 0;
     std::vector<double> hal, hbe;
     ~BatchWs() {
@@ -129,6 +130,7 @@ struct bddc_ctx {
     double *Ainv = nullptr;           // top-level inverse, leading dimension ld_top
     int *err_dev = nullptr;           // set by kernels whose bounded waits gave up
     std::unique_ptr<Workspace> ws;
+    int tuned[3] = {0, 0, 0};         // autotuned batch tiles (see bddc_info::tuned_tile)
     double setup_ms = 0.0;
     std::mutex mu;
     int n() const { return (nx - 1) * (nx - 1); }
@@ -798,6 +800,27 @@ BatchWs &batch_ws(bddc_ctx *C, Workspace &W) {
     bw->nrm = A.alloc_n<double>(KB);
     BDDC_CUDA_TRY(cudaHostAlloc((void **)&bw->hsc, sizeof(BatchScalars), cudaHostAllocDefault));
     BDDC_CUDA_TRY(cudaHostAlloc((void **)&bw->hnrm, sizeof(double) * KB, cudaHostAllocDefault));
+    {
+        // autotune the stencil tile and the top-level product on this
+        // problem's operators, with scratch scalars and outputs
+        cudaStream_t st = W.stream;
+        BatchScalars *scs = A.alloc_n<BatchScalars>(1);
+        double *al = A.alloc_n<double>(KB);
+        BDDC_CUDA_TRY(cudaMemsetAsync(scs, 0, sizeof(BatchScalars), st));
+        BDDC_CUDA_TRY(cudaMemsetAsync(bw->z, 0, sizeof(double) * n * KB, st));
+        BDDC_CUDA_TRY(cudaMemsetAsync(bw->p, 0, sizeof(double) * n * KB, st));
+        bw->tile_v = dir_spmv_tune(C->nx, KB, C->w_dev, bw->z, bw->p, bw->p1, bw->q, bw->part, bw->counter,
+                                   scs, al, st);
+        const BatchLevel &top = bw->lv.back();
+        bw->gemm_v = gemm_tune(C->n_top, C->ld_top, C->Ainv, top.rcv, top.ucv, KB, C->err_dev, st);
+        BDDC_CUDA_TRY(cudaStreamSynchronize(st));
+        BDDC_CUDA_TRY(cudaGetLastError());
+        int tx = 0, ty = 0;
+        dir_spmv_tile(bw->tile_v, &tx, &ty);
+        C->tuned[0] = tx;
+        C->tuned[1] = ty;
+        C->tuned[2] = gemm_rows(bw->gemm_v);
+    }
     W.bw = std::move(bw);
     return *W.bw;
 }
@@ -808,7 +831,7 @@ void apply_b_rec(bddc_ctx *C, Workspace &W, BatchWs &BW, int l, int prec, const 
     const BatchLevel &B = BW.lv[l];
     apply_level_pre_b(D, B, prec, r, skip, st);
     if (l + 1 == (int)W.lv.size())
-        launch_gemm_b(C->n_top, C->ld_top, C->Ainv, B.rcv, B.ucv, B.K, skip, C->err_dev, st);
+        launch_gemm_b(C->n_top, C->ld_top, C->Ainv, B.rcv, B.ucv, B.K, skip, C->err_dev, st, BW.gemm_v);
     else
         apply_b_rec(C, W, BW, l + 1, prec, B.rcv, B.ucv, skip, st);
     apply_level_post_b(D, B, prec, r, z, skip, st, nullptr, rz);
@@ -826,7 +849,8 @@ cudaGraphExec_t batch_graph(bddc_ctx *C, Workspace &W, BatchWs &BW, int prec, in
     cudaStream_t st = W.stream;
     cudaGraph_t g;
     BDDC_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    launch_b_dir_spmv(C->nx, K, C->w_dev, BW.z, BW.p, BW.p1, BW.q, BW.part, BW.counter, BW.sc, BW.alphas, st);
+    launch_b_dir_spmv(C->nx, K, C->w_dev, BW.z, BW.p, BW.p1, BW.q, BW.part, BW.counter, BW.sc, BW.alphas, st,
+                      BW.tile_v);
     launch_b_update(n, K, BW.x, BW.r, BW.p, BW.p1, BW.q, BW.part, BW.counter, BW.sc, st);
     const RzBatch rz{BW.rzpart, BW.rzcounter, BW.sc, BW.betas};
     apply_b_rec(C, W, BW, 0, prec, BW.r, BW.z, &BW.sc->all_done, st, &rz);
@@ -1252,6 +1276,7 @@ int bddc_query(const bddc_ctx *ctx, bddc_info *info, int level, int32_t *n_selec
                 info->psi_entries[l] = ctx->L[l].pent;
                 info->n_interface[l] = ctx->L[l].D.n_iface;
             }
+            for (int t = 0; t < 3; ++t) info->tuned_tile[t] = ctx->tuned[t];
             info->n_dof[ctx->L.size()] = ctx->n_top;
             double om = 1.0;
             bool any = false;
@@ -1362,7 +1387,7 @@ int bddc_profile_apply_batch(bddc_ctx *ctx, const double *r_dev, int nrhs, int64
             }
             BDDC_CUDA_TRY(cudaEventRecord(top[0], st));
             launch_gemm_b(ctx->n_top, ctx->ld_top, ctx->Ainv, BW.lv[nl - 1].rcv, BW.lv[nl - 1].ucv, K, nullptr,
-                          ctx->err_dev, st);
+                          ctx->err_dev, st, BW.gemm_v);
             BDDC_CUDA_TRY(cudaEventRecord(top[1], st));
             for (int l = nl - 1; l >= 0; --l)
                 apply_level_post_b(W.lv[l], BW.lv[l], ctx->prec, rin[l], l == 0 ? BW.z : BW.lv[l - 1].ucv,

@@ -209,8 +209,13 @@ void apply_level_post_b(const DevLevel &L, const BatchLevel &B, int prec, const 
                         const int *skip, cudaStream_t s, cudaEvent_t *ev = nullptr,
                         const RzBatch *rz = nullptr);
 // Y = A X for the top level (A as in launch_dense_symv; X, Y interleaved [ld][K])
+// variant: rows per block 8, 16 or 32 (0, 1, 2), chosen by gemm_tune.
 void launch_gemm_b(int n, int ld, const double *A, const double *X, double *Y, int K, const int *skip,
-                   int *err, cudaStream_t s);
+                   int *err, cudaStream_t s, int variant = 1);
+// Autotuning: time every variant on the given (scratch) operands and return
+// the fastest.  Y is overwritten.
+int gemm_tune(int n, int ld, const double *A, const double *X, double *Y, int K, int *err, cudaStream_t s);
+int gemm_rows(int variant);
 // PCG for a batch; b in the caller's layout (column k at b + k * ldb)
 // x = 0, r = b, p0 = 0, per-right-hand-side scalars, step = 0
 void launch_b_init(int n, int K, const double *b, int64_t ldb, double *x, double *r, double *p0,
@@ -220,9 +225,14 @@ void launch_b_init(int n, int K, const double *b, int64_t ldb, double *x, double
 // between p0 and p1 by sc->step), q = A p_new, alpha = rho / (p_new . q).
 // part must hold launch_b_dir_spmv_blocks(nx) * K doubles.
 int launch_b_dir_spmv_blocks(int nx);
+// variant: node tile 16x8, 32x4, 32x8 or 8x16 (0..3), chosen by dir_spmv_tune
+// (which runs every variant on scratch scalars, directions and q).
 void launch_b_dir_spmv(int nx, int K, const double *w, const double *z, double *p0, double *p1,
                        double *q, double *part, unsigned *counter, BatchScalars *sc, double *alphas,
-                       cudaStream_t s);
+                       cudaStream_t s, int variant = 0);
+int dir_spmv_tune(int nx, int K, const double *w, const double *z, double *p0, double *p1, double *q,
+                  double *part, unsigned *counter, BatchScalars *sc, double *alphas, cudaStream_t s);
+void dir_spmv_tile(int variant, int *tx, int *ty);
 // x += alpha p_new; r -= alpha q; rr; convergence; step += 1
 void launch_b_update(int n, int K, double *x, double *r, const double *p0, const double *p1,
                      const double *q, double *part, unsigned *counter, BatchScalars *sc, cudaStream_t s);

@@ -168,3 +168,15 @@ def test_profile_apply_batch(lib):
     ms = P.profile_apply_batch(R, reps=3)
     assert len(ms) == 5 and all(t > 0 for t in ms)       # pre, neumann, top, average, post
     P.close()
+
+
+def test_autotuned_tiles_reported(lib):
+    wl = WL["channels_64"]
+    P = lib.Problem.from_workload(wl)
+    assert P.query(level=None)["tuned_tile"] == [0, 0, 0]           # not tuned before a batch
+    B = torch.tensor(inputs.normal_rhs(wl.n_dof, 71, 4), device="cuda")
+    X, infos = P.solve(B)
+    t = P.query(level=None)["tuned_tile"]
+    assert tuple(t[:2]) in {(16, 8), (32, 4), (32, 8), (8, 16)} and t[2] in (8, 16, 32)
+    assert all(i["status"] == 0 for i in infos)
+    P.close()
