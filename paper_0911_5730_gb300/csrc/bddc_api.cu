@@ -615,6 +615,11 @@ void apply_rec(bddc_ctx *C, Workspace &W, int l, int prec, const double *r, doub
     apply_level_post(D, prec, r, z, skip, st, nullptr, rz);
 }
 
+// PCG iterations per captured graph of the single right-hand-side solve:
+// fewer graph boundaries (each leaves the GPU idle for a few microseconds);
+// iterations past convergence only skip their kernels.
+constexpr int kGraphIters = 2;
+
 cudaGraphExec_t pcg_graph(bddc_ctx *C, Workspace &W, int prec) {
     if (W.graph[prec]) return W.graph[prec];
     const int n = C->n();
@@ -622,16 +627,17 @@ cudaGraphExec_t pcg_graph(bddc_ctx *C, Workspace &W, int prec) {
     cudaGraph_t g;
     BDDC_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     const RzArgs rz{W.rzpart, W.rzcounter, W.sc, W.betas};
-    launch_pcg_dir_spmv(C->nx, C->w_dev, W.z, W.p0, W.p1, W.q, W.part, W.counter, W.sc, W.alphas, st);
-    launch_pcg_update(n, W.x, W.r, W.p0, W.p1, W.q, W.part, W.counter, W.sc, st);
-    apply_rec(C, W, 0, prec, W.r, W.z, &W.sc->done, st, &rz);
+    for (int it = 0; it < kGraphIters; ++it) {
+        launch_pcg_dir_spmv(C->nx, C->w_dev, W.z, W.p0, W.p1, W.q, W.part, W.counter, W.sc, W.alphas, st);
+        launch_pcg_update(n, W.x, W.r, W.p0, W.p1, W.q, W.part, W.counter, W.sc, st);
+        apply_rec(C, W, 0, prec, W.r, W.z, &W.sc->done, st, &rz);
+    }
     BDDC_CUDA_TRY(cudaStreamEndCapture(st, &g));
     BDDC_CUDA_TRY(cudaGraphInstantiate(&W.graph[prec], g, 0));
     cudaGraphDestroy(g);
     return W.graph[prec];
 }
 
-// One right-hand side; runs on W.stream and synchronises it.
 // Extreme eigenvalues of the Lanczos matrix of k CG steps (diagonal
 // 1/alpha_j + beta_{j-1}/alpha_{j-1}, off-diagonal sqrt(beta_j)/alpha_j) by
 // bisection on Sturm counts.  A k x k tridiagonal: host arithmetic on the
@@ -671,6 +677,7 @@ void lanczos_extremes(const std::vector<double> &al, const std::vector<double> &
     }
 }
 
+// One right-hand side; runs on W.stream and synchronises it.
 int pcg_one(bddc_ctx *C, Workspace &W, int prec, const double *b, double *x, double rtol,
             int maxit, bddc_solve_info *info) {
     const int n = C->n();
@@ -685,11 +692,11 @@ int pcg_one(bddc_ctx *C, Workspace &W, int prec, const double *b, double *x, dou
     int launches = 1 + per_apply;
     // launch the previous solve's iteration count before the first check
     // (iterations past convergence only skip their kernels)
-    int chunk = W.last_iters > 1 ? std::min(W.last_iters, 256) : 4;
+    int chunk = W.last_iters > 1 ? std::min((W.last_iters + kGraphIters - 1) / kGraphIters, 128) : 2;
     double rr_true = 0.0;
     for (;;) {
         for (int k = 0; k < chunk; ++k) BDDC_CUDA_TRY(cudaGraphLaunch(g, st));
-        launches += chunk * (2 + per_apply);
+        launches += chunk * kGraphIters * (2 + per_apply);
         BDDC_CUDA_TRY(cudaMemcpyAsync(W.hsc, W.sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, st));
         BDDC_CUDA_TRY(cudaStreamSynchronize(st));
         if (!W.hsc->done) { chunk = std::max(1, std::min(chunk / 2, 16)); continue; }
