@@ -1,10 +1,20 @@
-// apply_kernels.cu - Algorithm 1 (eqs. 4-11) on one level, and the PCG
-// recurrences of Sec. 5.
+// apply_kernels.cu - Algorithm 1 (eqs. 4-11) on one level for one
+// right-hand side, and the PCG recurrences of Sec. 5.
 //
-// Each substructure kernel works on all substructures of a level at once,
-// one thread block per substructure.  Operators are read in the storage
-// type T (double, float or bfloat16) and accumulated in ACC (double for the
-// FP64 path, float otherwise); global vectors stay FP64.
+// Each substructure kernel works on all substructures of a level at once.
+// Three families, chosen per level:
+//  * warp kernels (k_dir_w, k_neumann_r, k_average_r): one warp per
+//    substructure, the operators staged in shared memory by bulk copies,
+//    for levels with a common power-of-two block size and records that fit
+//    the lanes' registers;
+//  * the streaming Dirichlet kernel (k_dir_s): one block per substructure,
+//    factor blocks streamed through a shared-memory ring, for large or
+//    irregular substructures;
+//  * the generic kernels (k_pre, k_neumann, k_average, k_post), reading the
+//    operators from global memory, for everything else.
+// Operators are read in the storage type T (double, float or bfloat16) and
+// accumulated in ACC (double for the FP64 path, float otherwise); global
+// vectors stay FP64.
 //
 // The apply uses two exact rewritings of Algorithm 1:
 //  * the right-hand side of the substructure problem (6) lives on the

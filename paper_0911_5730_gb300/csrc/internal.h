@@ -150,8 +150,8 @@ struct RzArgs {
 // ----------------------------------------------------------------------------
 // Apply / PCG launchers (apply_kernels.cu)
 // ----------------------------------------------------------------------------
-// Down-sweep of one level: interface init, (4)-(5) pre-correction, (6)-(8)
-// substructure correction and coarse right-hand side.
+// Down-sweep of one level: (4)-(5) pre-correction, (6)-(8) substructure
+// correction and coarse right-hand side.
 // ev (optional, 3 events) are recorded before each kernel and after the last.
 // Scratch protocol of a level: rB and rcv are zero when an apply starts
 // (the averaging kernel clears them after use) and the pre-correction clears
