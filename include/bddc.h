@@ -148,7 +148,11 @@ int bddc_setup(const bddc_mesh *mesh, const double *k_elem, const bddc_decomp *d
  * every level, all substructures at once.
  *   r_dev, z_dev : device [nrhs][ld] FP64, column j at offset j*ld; ld >= n.
  *                  r and z must not overlap.
- *   nrhs         : number of right-hand sides (>= 1).
+ *   nrhs         : number of right-hand sides (>= 1).  With nrhs > 1 and
+ *                  operators that fit the batch kernels, up to 32 columns
+ *                  are applied together (each column's result is the same
+ *                  operator applied to it; see bddc_pcg_solve for the
+ *                  workspace the first such call allocates).
  * Runs asynchronously in `stream`; the context serialises its own scratch,
  * so calls on one context must not run concurrently from several threads.
  */
@@ -160,6 +164,14 @@ int bddc_apply(bddc_ctx *ctx, const double *r_dev, double *z_dev, int nrhs, int6
  * ||r||_2 <= rtol ||b||_2 for the recursive and the true residual, or maxit.
  *   b_dev, x_dev : device [nrhs][ld] FP64; each column solved independently.
  *   info_host    : host [nrhs] results (may be NULL).
+ * With nrhs > 1 the columns are solved in lockstep batches of up to 32 when
+ * every level's operators fit the batch kernels (info_host[j].batch_width
+ * says which ran): each column keeps its own PCG scalars, stopping test and
+ * iteration count, and gets the same iterates as a solo solve up to
+ * rounding.  The first batched call on a context allocates its batch
+ * workspace (about 8 * 32 * n doubles plus per-level scratch) and times the
+ * batch kernels' tile variants on the context's operators (bddc_info
+ * tuned_tile).
  * Returns BDDC_E_NOCONV if any column reached maxit (x holds the last iterate).
  * Synchronises `stream` before returning.
  */
