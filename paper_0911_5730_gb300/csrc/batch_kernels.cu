@@ -16,6 +16,7 @@
 #include "device_util.cuh"
 
 #include <algorithm>
+#include <cstdlib>
 #include <type_traits>
 
 namespace bddc {
@@ -77,6 +78,10 @@ __device__ __forceinline__ void load_vec(const T *src, ACC (&v)[N]) {
         }
     }
 }
+
+// Entry (r, c) of a stored b x b block: c * b + r, or c * b + (r ^ c) when the
+// level's blocks are XOR-swizzled.
+__device__ __forceinline__ int fpos_b(int r, int c, int b, bool swz) { return c * b + (swz ? (r ^ c) : r); }
 
 // The batched Dirichlet kernel gives one block of LR warps to one
 // substructure, LR lanes to a right-hand side: warp w takes right-hand sides
@@ -397,6 +402,352 @@ __global__ void __launch_bounds__(32 * lanes_per_rhs<BP>()) k_dir_b(DevLevel L, 
             if (tid == 0) *rz.counter = 0u;
         }
     }
+}
+
+// Batched Dirichlet solves for substructures whose factor does not fit in
+// shared memory (large or irregular cells): one block of kSBT threads per
+// substructure, the factor blocks streamed through a ring of SBN stages as in
+// the single right-hand-side streaming kernel (block i in stage i % SBN; the
+// backward sweep starts from the blocks left in the ring and refills the
+// stage of block j+1 after step j), the right-hand sides in passes of KP
+// (the factor is streamed once per pass).  Thread (rg, kk) of a pass works on
+// right-hand side k0 + kk and rows rg, rg + RG, ... (RG = kSBT / KP) of each
+// block; factor entries are read by all KP threads of a row group at once.
+// The coupling terms are applied by the thread owning the row (row % RG), in
+// entry order.  The interior index arrays are read from global memory.
+constexpr int kSBT = 256, SBN = 3;
+
+struct StreamSmemB {
+    size_t stage, xs, tmp, vg, red, total;
+    template <class T, class ACC> __host__ __device__ static StreamSmemB of(const DevLevel &L, int KP) {
+        StreamSmemB m;
+        const size_t mb = L.max_b > 0 ? L.max_b : 1;
+        m.stage = al16(2 * mb * mb * sizeof(T) + 32);
+        m.xs = al16(sizeof(ACC) * (size_t)(L.max_m > 0 ? L.max_m : 1) * mb * KP);
+        m.tmp = al16(sizeof(ACC) * mb * KP);
+        m.vg = al16(sizeof(ACC) * (size_t)(L.max_nG > 0 ? L.max_nG : 1) * KP);
+        m.red = al16(8 * kSBT + 16);
+        m.total = SBN * m.stage + m.xs + m.tmp + m.vg + m.red + 8 * SBN + 16;
+        return m;
+    }
+};
+
+template <class T, class ACC, bool POST>
+__global__ void __launch_bounds__(kSBT) k_dir_bs(DevLevel L, BatchLevel B, const double *r, double *z,
+                                                 const int *skip, int KP, RzBatch rz) {
+    extern __shared__ __align__(16) unsigned char smem_bs[];
+    if (skip && *skip) return;
+    const StreamSmemB ly = StreamSmemB::of<T, ACC>(L, KP);
+    unsigned char *ring = smem_bs;
+    unsigned char *p = smem_bs + SBN * ly.stage;
+    ACC *xs = reinterpret_cast<ACC *>(p);   p += ly.xs;
+    ACC *tmp = reinterpret_cast<ACC *>(p);  p += ly.tmp;
+    ACC *vG = reinterpret_cast<ACC *>(p);   p += ly.vg;
+    double *red = reinterpret_cast<double *>(p);   // kSBT partials and a flag word
+    int *flag = reinterpret_cast<int *>(red + kSBT);
+    p += ly.red;
+    unsigned long long *bars = reinterpret_cast<unsigned long long *>(p);
+    const int sub = blockIdx.x, tid = threadIdx.x;
+    const int K = B.K;
+    const int nI = L.nI[sub], nG = L.nG[sub], b = L.bsz[sub], m = nI > 0 ? L.nblk[sub] : 0;
+    const bool swz = L.bp != 0;
+    const OpSet<T> &O = Ops<T>::get(L);
+    const T *F = O.dir + L.offF[sub];
+    const size_t bb2 = 2 * (size_t)b * b;
+    const int *iI = L.idxI + L.offI[sub];
+    const int *iG = L.idxG + L.offG[sub];
+    const int64_t c0e = L.offCOO[sub], c1e = L.offCOO[sub + 1];
+    const int RG = kSBT / KP, kk = tid % KP, rg = tid / KP;
+    auto issue = [&](int i) {
+        const uintptr_t a = reinterpret_cast<uintptr_t>(F + (size_t)i * bb2);
+        const uintptr_t al = a & ~uintptr_t(15);
+        const uintptr_t ae = (a + bb2 * sizeof(T) + 15) & ~uintptr_t(15);
+        mbar_expect(&bars[i % SBN], (unsigned)(ae - al));
+        bulk_copy(ring + (size_t)(i % SBN) * ly.stage, reinterpret_cast<const void *>(al), (unsigned)(ae - al),
+                  &bars[i % SBN]);
+    };
+    auto blk = [&](int i) {
+        const uintptr_t a = reinterpret_cast<uintptr_t>(F + (size_t)i * bb2);
+        return reinterpret_cast<const T *>(ring + (size_t)(i % SBN) * ly.stage + (a & 15));
+    };
+    if (tid == 0)
+        for (int s2 = 0; s2 < SBN; ++s2) mbar_init(&bars[s2]);
+    __syncthreads();
+    unsigned par = 0;                     // bit s: parity of the next phase of stage s
+    bool ok = true;
+    auto wait_block = [&](int i) {
+        const int s2 = i % SBN;
+        const bool got = mbar_wait(&bars[s2], (par >> s2) & 1u);
+        par ^= 1u << s2;
+        return __syncthreads_and(got) != 0;
+    };
+    for (int k0 = 0; k0 < K && ok; k0 += KP) {
+        const int k = k0 + kk;
+        const bool act = k < K;
+        if (tid == 0)
+            for (int i = 0; i < SBN && i < m; ++i) issue(i);
+        // right-hand sides of this pass, coalesced over (row, column)
+        for (int e = tid; e < m * b * KP; e += kSBT) {
+            const int i = e / KP, c = e - i * KP;
+            xs[e] = (i < nI && k0 + c < K) ? from_f64<ACC>(r[(int64_t)iI[i] * K + k0 + c]) : (ACC)0;
+        }
+        if (POST) {
+            for (int e = tid; e < nG * KP; e += kSBT) {
+                const int q = e / KP, c = e - q * KP;
+                vG[e] = (k0 + c < K) ? from_f64<ACC>(B.uB[(int64_t)iG[q] * K + k0 + c]) : (ACC)0;
+            }
+            __syncthreads();
+            for (int64_t e = c0e; e < c1e; ++e) {
+                const int il = L.cooI[e];
+                if (il % RG != rg) continue;
+                xs[il * KP + kk] -= ld<T, ACC>(O.aig + e) * vG[L.cooG[e] * KP + kk];
+            }
+        } else {
+            for (int e = tid; e < nG * KP; e += kSBT) vG[e] = 0;
+        }
+        __syncthreads();
+        for (int j = 0; j < m; ++j) {
+            if (!wait_block(j)) { ok = false; break; }
+            const T *Li = blk(j), *Ls = Li + (size_t)b * b;
+            for (int rr = rg; rr < b; rr += RG) {
+                ACC a = 0;
+                if (j > 0)
+                    for (int c = 0; c < b; ++c) a += ld<T, ACC>(Ls + fpos_b(rr, c, b, swz)) * xs[((j - 1) * b + c) * KP + kk];
+                tmp[rr * KP + kk] = xs[(j * b + rr) * KP + kk] - a;
+            }
+            __syncthreads();
+            for (int rr = rg; rr < b; rr += RG) {
+                ACC a = 0;
+                for (int c = 0; c <= rr; ++c) a += ld<T, ACC>(Li + fpos_b(rr, c, b, swz)) * tmp[c * KP + kk];
+                xs[(j * b + rr) * KP + kk] = a;
+            }
+            __syncthreads();
+            if (tid == 0 && j + SBN < m) issue(j + SBN);
+        }
+        for (int j = m - 1; j >= 0 && ok; --j) {
+            if (j < m - SBN && !wait_block(j)) { ok = false; break; }
+            const T *Li = blk(j);
+            for (int rr = rg; rr < b; rr += RG) {
+                ACC a = 0;
+                if (j < m - 1) {
+                    const T *Ls1 = blk(j + 1) + (size_t)b * b;
+                    for (int c = 0; c < b; ++c) a += ld<T, ACC>(Ls1 + fpos_b(c, rr, b, swz)) * xs[((j + 1) * b + c) * KP + kk];
+                }
+                tmp[rr * KP + kk] = xs[(j * b + rr) * KP + kk] - a;
+            }
+            __syncthreads();
+            for (int rr = rg; rr < b; rr += RG) {
+                ACC a = 0;
+                for (int c = rr; c < b; ++c) a += ld<T, ACC>(Li + fpos_b(c, rr, b, swz)) * tmp[c * KP + kk];
+                xs[(j * b + rr) * KP + kk] = a;
+            }
+            __syncthreads();
+            if (tid == 0 && j + 1 < m && j + 1 - SBN >= 0) issue(j + 1 - SBN);
+        }
+        if (!ok) break;
+        if (!POST) {
+            // A_{Gamma I} u_I into vG (owner of row gl: gl % RG), then r_B -= it
+            for (int64_t e = c0e; e < c1e; ++e) {
+                const int gl = L.cooG[e];
+                if (gl % RG != rg) continue;
+                vG[gl * KP + kk] += ld<T, ACC>(O.aig + e) * xs[L.cooI[e] * KP + kk];
+            }
+            __syncthreads();
+            for (int e = tid; e < nG * KP; e += kSBT) {
+                const int q = e / KP, c = e - q * KP;
+                if (k0 + c >= K) continue;
+                const int64_t o = (int64_t)iG[q] * K + k0 + c;
+                const ACC v = vG[e];
+                if (v != (ACC)0) atomicAdd(&B.rB[o], -to_f64(v));
+                B.uB[o] = 0.0;   // consumed by the previous post-correction
+            }
+        } else {
+            double acc = 0.0;
+            for (int i = rg; i < nI; i += RG) {
+                if (!act) break;
+                const int64_t o = (int64_t)iI[i] * K + k;
+                const double zv = to_f64(xs[i * KP + kk]);
+                z[o] = zv;
+                if (rz.sc) acc = fma(r[o], zv, acc);
+            }
+            for (int64_t e = L.offOwn[sub] + rg; e < L.offOwn[sub + 1]; e += RG) {
+                if (!act) break;
+                const int id = L.own[e];
+                const int64_t o = (int64_t)L.ifaceDof[id] * K + k;
+                const double zv = B.uB[(int64_t)id * K + k];
+                z[o] = zv;
+                if (rz.sc) acc = fma(r[o], zv, acc);
+            }
+            if (rz.sc) {
+                // per right-hand side: the row groups summed in a fixed order
+                red[rg * KP + kk] = acc;
+                __syncthreads();
+                if (tid < KP && k0 + tid < K) {
+                    double t = 0.0;
+                    for (int g = 0; g < RG; ++g) t += red[g * KP + tid];
+                    rz.part[(int64_t)sub * K + k0 + tid] = t;
+                }
+            }
+        }
+        // the next pass streams the factor again from block 0: every stage is
+        // idle here (each issued block has been waited for)
+        __syncthreads();
+    }
+    if (!ok) {
+        if (tid == 0) {
+            atomicExch(L.err, 1);
+            for (int s2 = 0; s2 < SBN; ++s2) mbar_wait(&bars[s2], (par >> s2) & 1u);   // bounded
+        }
+        return;
+    }
+    if (POST && rz.sc) {
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) *flag = atomicAdd(rz.counter, 1u) == (unsigned)L.nsub - 1u;
+        __syncthreads();
+        if (!*flag) return;
+        __threadfence();
+        // right-hand side t % 32 of thread t; the eight warps split the substructures
+        const int lane = tid & 31, warp = tid >> 5;
+        double t = 0.0;
+        if (lane < K)
+            for (int sb = warp; sb < L.nsub; sb += kSBT / 32) t += __ldcg(&rz.part[(int64_t)sb * K + lane]);
+        red[warp * 32 + lane] = t;
+        __syncthreads();
+        if (warp == 0 && lane < K) {
+            double tot = 0.0;
+            for (int w = 0; w < kSBT / 32; ++w) tot += red[w * 32 + lane];
+            BatchScalars *sc = rz.sc;
+            if (!sc->done[lane]) {
+                const double beta = sc->fresh[lane] ? 0.0 : tot / sc->rho[lane];
+                sc->fresh[lane] = 0;
+                sc->hold[lane] = 0;
+                sc->beta[lane] = beta;
+                if (sc->it[lane] > 0) rz.betas[(int64_t)(sc->it[lane] - 1) * K + lane] = beta;
+                sc->rho[lane] = tot;
+            }
+        }
+        if (tid == 0) *rz.counter = 0u;
+    }
+}
+
+// (6)-(9) for K right-hand sides when the Neumann records are too large to
+// stage whole: one block of kSBT threads per substructure reads N_i and
+// Psi_i^T from global memory in chunks of contiguous rows, loaded by all
+// threads (coalesced) into shared memory; warp w computes the rows q = w
+// (mod 8) for all right-hand sides (lane k: right-hand side k).
+constexpr int kChunkBytes = 32 * 1024;
+
+template <class T> __host__ __device__ inline int neu_chunk_rows(int nG) {
+    const int rows = kChunkBytes / (int)(sizeof(T) * (nG > 0 ? nG : 1));
+    return rows < 1 ? 1 : (rows > nG ? (nG > 0 ? nG : 1) : rows);
+}
+template <class T, class ACC> __host__ __device__ inline size_t neu_bg_smem(const DevLevel &L) {
+    const size_t mg = L.max_nG > 0 ? L.max_nG : 1, mc = L.max_nc > 0 ? L.max_nc : 1;
+    const size_t row = sizeof(T) * mg;   // one row of N when a row exceeds the chunk
+    const size_t chunk = al16((row > (size_t)kChunkBytes ? row : (size_t)kChunkBytes) + 16);
+    const size_t psi = al16(sizeof(T) * mg * mc);
+    return al16(sizeof(ACC) * mg * 32) + al16(sizeof(ACC) * mc * 32) + (chunk > psi ? chunk : psi) + 16;
+}
+
+template <class T, class ACC>
+__global__ void __launch_bounds__(kSBT) k_neu_bg(DevLevel L, BatchLevel B, int pidx, const double *r,
+                                                 const int *skip) {
+    extern __shared__ __align__(16) unsigned char smem_ng[];
+    (void)pidx;
+    if (skip && *skip) return;
+    const int sub = blockIdx.x, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int K = B.K;
+    const bool act = lane < K;
+    const int nG = L.nG[sub], nc = L.ncl[sub];
+    const size_t mg = L.max_nG > 0 ? L.max_nG : 1, mc = L.max_nc > 0 ? L.max_nc : 1;
+    ACC *f = reinterpret_cast<ACC *>(smem_ng);
+    T *buf = reinterpret_cast<T *>(smem_ng + al16(sizeof(ACC) * mg * 32) + al16(sizeof(ACC) * mc * 32));
+    const OpSet<T> &O = Ops<T>::get(L);
+    const int64_t g0 = L.offG[sub];
+    for (int e = tid; e < nG * 32; e += kSBT) {
+        const int q = e >> 5, k = e & 31;
+        double v = 0.0;
+        if (k < K) {
+            const int id = L.idxG[g0 + q];
+            v = r[(int64_t)L.ifaceDof[id] * K + k] + B.rB[(int64_t)id * K + k];
+        }
+        f[e] = ld<T, ACC>(O.wg + g0 + q) * from_f64<ACC>(v);
+    }
+    // w = N f, N in chunks of rows p (N[p * nG + q])
+    const T *N = O.nmat + L.offN[sub];
+    const int CH = neu_chunk_rows<T>(nG);
+    constexpr int QW = 4;   // output rows per warp and round: q = qb + warp + 8 u, u < QW
+    for (int qb = 0; qb < nG; qb += 8 * QW) {
+        ACC s4[QW] = {};
+        for (int p0 = 0; p0 < nG; p0 += CH) {
+            const int pn = nG - p0 < CH ? nG - p0 : CH;
+            __syncthreads();
+            for (int e = tid; e < pn * nG; e += kSBT) buf[e] = N[(int64_t)p0 * nG + e];
+            __syncthreads();
+            for (int pp = 0; pp < pn; ++pp) {
+                const ACC fv = f[(p0 + pp) * 32 + lane];
+#pragma unroll
+                for (int u = 0; u < QW; ++u) {
+                    const int q = qb + warp + 8 * u;
+                    if (q < nG) s4[u] += ld<T, ACC>(buf + pp * nG + q) * fv;
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < QW; ++u) {
+            const int q = qb + warp + 8 * u;
+            if (q < nG && act) B.w[(g0 + q) * K + lane] = to_f64(s4[u]);
+        }
+    }
+    // r_c += Psi^T f (Psi^T[k * nG + q], staged whole)
+    const T *P = O.psit + L.offP[sub];
+    __syncthreads();
+    for (int e = tid; e < nc * nG; e += kSBT) buf[e] = P[e];
+    __syncthreads();
+    for (int k = warp; k < nc; k += 8) {
+        ACC s0 = 0;
+        for (int q = 0; q < nG; ++q) s0 += ld<T, ACC>(buf + (size_t)k * nG + q) * f[q * 32 + lane];
+        if (act) atomicAdd(&B.rcv[(int64_t)L.rc[L.offC[sub] + k] * K + lane], to_f64(s0));
+    }
+}
+
+// (9) for K right-hand sides, Psi_i read from global memory (staged whole).
+template <class T, class ACC>
+__global__ void __launch_bounds__(kSBT) k_avg_bg(DevLevel L, BatchLevel B, int pidx, const int *skip) {
+    extern __shared__ __align__(16) unsigned char smem_ag[];
+    (void)pidx;
+    if (skip && *skip) return;
+    const int sub = blockIdx.x, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int K = B.K;
+    const bool act = lane < K;
+    const int nG = L.nG[sub], nc = L.ncl[sub];
+    const size_t mg = L.max_nG > 0 ? L.max_nG : 1, mc = L.max_nc > 0 ? L.max_nc : 1;
+    ACC *uc = reinterpret_cast<ACC *>(smem_ag + al16(sizeof(ACC) * mg * 32));
+    T *buf = reinterpret_cast<T *>(smem_ag + al16(sizeof(ACC) * mg * 32) + al16(sizeof(ACC) * mc * 32));
+    const OpSet<T> &O = Ops<T>::get(L);
+    const int64_t g0 = L.offG[sub];
+    const int *rcs = L.rc + L.offC[sub];
+    for (int e = tid; e < nc * 32; e += kSBT) {
+        const int k = e >> 5, kk = e & 31;
+        uc[e] = kk < K ? from_f64<ACC>(B.ucv[(int64_t)rcs[k] * K + kk]) : (ACC)0;
+    }
+    const T *P = O.psit + L.offP[sub];
+    for (int e = tid; e < nc * nG; e += kSBT) buf[e] = P[e];
+    __syncthreads();
+    for (int q = warp; q < nG; q += 8) {
+        ACC v = act ? from_f64<ACC>(B.w[(g0 + q) * K + lane]) : (ACC)0;
+        for (int k = 0; k < nc; ++k) v += ld<T, ACC>(buf + (size_t)k * nG + q) * uc[k * 32 + lane];
+        if (act) {
+            const int id = L.idxG[g0 + q];
+            const int64_t e = (int64_t)id * K + lane;
+            atomicAdd(&B.uB[e], to_f64(ld<T, ACC>(O.wg + g0 + q) * v));
+            B.rB[e] = 0.0;            // consumed by the substructure correction
+        }
+    }
+    __syncthreads();
+    if (act)
+        for (int k = warp; k < nc; k += 8) B.rcv[(int64_t)rcs[k] * K + lane] = 0.0;   // consumed
 }
 
 // (6)-(8) for K right-hand sides: f = D_i r_B on Gamma, w = N_i f,
@@ -1022,18 +1373,96 @@ int vgrid_b(int64_t nK, int K) {
 
 }  // namespace
 
-bool batch_path(const DevLevel &L, int prec) {
-    if (!(L.bp == 8 || L.bp == 16 || L.bp == 32) || !L.irec) return false;
-    const int pi = pidx_b(prec);
-    const size_t a = prec == BDDC_PREC_FP64 ? 8 : 4;
-    size_t dir;
-    if (prec == BDDC_PREC_FP64) dir = dir_slice_b<double, double>(L);
-    else if (prec == BDDC_PREC_FP32) dir = dir_slice_b<float, float>(L);
-    else dir = dir_slice_b<__nv_bfloat16, float>(L);
-    const size_t neu = al16((size_t)L.max_nrec[pi]) + al16(a * (size_t)(L.max_nG > 0 ? L.max_nG : 1) * 32) + 16;
-    const size_t avg = al16((size_t)L.max_nrec[pi]) + al16(a * (size_t)(L.max_nc > 0 ? L.max_nc : 1) * 32) + 16;
-    return dir <= kSmemMaxB && neu <= kSmemMaxB && avg <= kSmemMaxB;
+namespace {
+
+// Which batch kernels a level uses: the staged kernels when the operators
+// fit in shared memory, else the streaming Dirichlet kernel (passes of KP
+// right-hand sides) and the chunked Neumann / averaging kernels.
+struct BatchRoute {
+    bool dir_staged = false, neu_staged = false, avg_staged = false;
+    int kp = 0;             // pass width of the streaming Dirichlet kernel (0: none fits)
+    bool ok = false;
+};
+
+// BDDC_BATCH_STREAM=1 routes every level that the streaming / chunked
+// kernels can take to them, also where the staged kernels fit (read when a
+// batch is launched or captured).
+bool force_stream() {
+    const char *e = std::getenv("BDDC_BATCH_STREAM");
+    return e && e[0] == '1';
 }
+
+template <class T, class ACC> BatchRoute route_t(const DevLevel &L, int prec) {
+    BatchRoute R;
+    const int pi = pidx_b(prec);
+    const size_t a = sizeof(ACC);
+    R.dir_staged = (L.bp == 8 || L.bp == 16 || L.bp == 32) && L.irec && dir_slice_b<T, ACC>(L) <= kSmemMaxB;
+    R.neu_staged = al16((size_t)L.max_nrec[pi]) + al16(a * (size_t)(L.max_nG > 0 ? L.max_nG : 1) * 32) + 16 <= kSmemMaxB;
+    R.avg_staged = al16((size_t)L.max_nrec[pi]) + al16(a * (size_t)(L.max_nc > 0 ? L.max_nc : 1) * 32) + 16 <= kSmemMaxB;
+    if (!R.dir_staged)
+        for (int kp = 16; kp >= 1 && !R.kp; kp /= 2)
+            if (StreamSmemB::of<T, ACC>(L, kp).total <= kSmemMaxB) R.kp = kp;
+    const bool bg = neu_bg_smem<T, ACC>(L) <= kSmemMaxB;
+    if (force_stream()) {
+        if (R.dir_staged) {
+            for (int kp = 16; kp >= 1 && !R.kp; kp /= 2)
+                if (StreamSmemB::of<T, ACC>(L, kp).total <= kSmemMaxB) R.kp = kp;
+            if (R.kp) R.dir_staged = false;
+        }
+        if (bg) R.neu_staged = R.avg_staged = false;
+    }
+    R.ok = (R.dir_staged || R.kp > 0) && (R.neu_staged || bg) && (R.avg_staged || bg);
+    return R;
+}
+
+BatchRoute route(const DevLevel &L, int prec) {
+    if (prec == BDDC_PREC_FP64) return route_t<double, double>(L, prec);
+    if (prec == BDDC_PREC_FP32) return route_t<float, float>(L, prec);
+    return route_t<__nv_bfloat16, float>(L, prec);
+}
+
+}  // namespace
+
+bool batch_path(const DevLevel &L, int prec) { return route(L, prec).ok; }
+
+namespace {
+
+template <class T, class ACC>
+void dir_bs(const DevLevel &L, const BatchLevel &B, bool post, const double *r, double *z, const int *skip,
+            int kp, const RzBatch *rz, cudaStream_t s) {
+    const size_t sm = StreamSmemB::of<T, ACC>(L, kp).total;
+    const RzBatch none{nullptr, nullptr, nullptr, nullptr};
+    if (!post) launch_plain(k_dir_bs<T, ACC, false>, L.nsub, kSBT, sm, s, L, B, r, z, skip, kp, none);
+    else launch_plain(k_dir_bs<T, ACC, true>, L.nsub, kSBT, sm, s, L, B, r, z, skip, kp, rz ? *rz : none);
+}
+
+template <class T, class ACC>
+void pre_b(const DevLevel &L, const BatchLevel &B, int prec, const double *r, const int *skip, cudaStream_t s,
+           cudaEvent_t *ev) {
+    const BatchRoute R = route_t<T, ACC>(L, prec);
+    if (ev) cudaEventRecord(ev[0], s);
+    if (R.dir_staged) dir_b<T, ACC>(L, B, false, r, nullptr, skip, s);
+    else dir_bs<T, ACC>(L, B, false, r, nullptr, skip, R.kp, nullptr, s);
+    if (ev) cudaEventRecord(ev[1], s);
+    if (R.neu_staged) neu_b<T, ACC>(L, B, prec, r, skip, s);
+    else launch_plain(k_neu_bg<T, ACC>, L.nsub, kSBT, neu_bg_smem<T, ACC>(L), s, L, B, pidx_b(prec), r, skip);
+    if (ev) cudaEventRecord(ev[2], s);
+}
+
+template <class T, class ACC>
+void post_b(const DevLevel &L, const BatchLevel &B, int prec, const double *r, double *z, const int *skip,
+            cudaStream_t s, cudaEvent_t *ev, const RzBatch *rz) {
+    const BatchRoute R = route_t<T, ACC>(L, prec);
+    if (ev) cudaEventRecord(ev[0], s);
+    if (R.avg_staged) avg_b<T, ACC>(L, B, prec, skip, s);
+    else launch_plain(k_avg_bg<T, ACC>, L.nsub, kSBT, neu_bg_smem<T, ACC>(L), s, L, B, pidx_b(prec), skip);
+    if (ev) cudaEventRecord(ev[1], s);
+    if (R.dir_staged) dir_b<T, ACC>(L, B, true, r, z, skip, s, rz);
+    else dir_bs<T, ACC>(L, B, true, r, z, skip, R.kp, rz, s);
+    if (ev) cudaEventRecord(ev[2], s);
+}
+
+}  // namespace
 
 void prepare_batch_kernels() {
     const int big = (int)kSmemMaxB;
@@ -1055,6 +1484,13 @@ void prepare_batch_kernels() {
     cudaFuncSetAttribute(k_gemm_b<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(GM_S * gm_stage(1)));
     cudaFuncSetAttribute(k_gemm_b<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(GM_S * gm_stage(2)));
     cudaFuncSetAttribute(k_gemm_b<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(GM_S * gm_stage(4)));
+    BDDC_SMEM_ATTR_B((k_dir_bs<double, double, false>)); BDDC_SMEM_ATTR_B((k_dir_bs<double, double, true>));
+    BDDC_SMEM_ATTR_B((k_dir_bs<float, float, false>)); BDDC_SMEM_ATTR_B((k_dir_bs<float, float, true>));
+    BDDC_SMEM_ATTR_B((k_dir_bs<__nv_bfloat16, float, false>)); BDDC_SMEM_ATTR_B((k_dir_bs<__nv_bfloat16, float, true>));
+    BDDC_SMEM_ATTR_B((k_neu_bg<double, double>)); BDDC_SMEM_ATTR_B((k_neu_bg<float, float>));
+    BDDC_SMEM_ATTR_B((k_neu_bg<__nv_bfloat16, float>));
+    BDDC_SMEM_ATTR_B((k_avg_bg<double, double>)); BDDC_SMEM_ATTR_B((k_avg_bg<float, float>));
+    BDDC_SMEM_ATTR_B((k_avg_bg<__nv_bfloat16, float>));
     BDDC_SMEM_ATTR_B((k_avg_b<double, double>)); BDDC_SMEM_ATTR_B((k_avg_b<float, float>));
     BDDC_SMEM_ATTR_B((k_avg_b<__nv_bfloat16, float>));
 #undef BDDC_DIR_B
@@ -1063,28 +1499,16 @@ void prepare_batch_kernels() {
 
 void apply_level_pre_b(const DevLevel &L, const BatchLevel &B, int prec, const double *r,
                        const int *skip, cudaStream_t s, cudaEvent_t *ev) {
-    if (ev) cudaEventRecord(ev[0], s);
-    if (prec == BDDC_PREC_FP64) dir_b<double, double>(L, B, false, r, nullptr, skip, s);
-    else if (prec == BDDC_PREC_FP32) dir_b<float, float>(L, B, false, r, nullptr, skip, s);
-    else dir_b<__nv_bfloat16, float>(L, B, false, r, nullptr, skip, s);
-    if (ev) cudaEventRecord(ev[1], s);
-    if (prec == BDDC_PREC_FP64) neu_b<double, double>(L, B, prec, r, skip, s);
-    else if (prec == BDDC_PREC_FP32) neu_b<float, float>(L, B, prec, r, skip, s);
-    else neu_b<__nv_bfloat16, float>(L, B, prec, r, skip, s);
-    if (ev) cudaEventRecord(ev[2], s);
+    if (prec == BDDC_PREC_FP64) pre_b<double, double>(L, B, prec, r, skip, s, ev);
+    else if (prec == BDDC_PREC_FP32) pre_b<float, float>(L, B, prec, r, skip, s, ev);
+    else pre_b<__nv_bfloat16, float>(L, B, prec, r, skip, s, ev);
 }
 
 void apply_level_post_b(const DevLevel &L, const BatchLevel &B, int prec, const double *r, double *z,
                         const int *skip, cudaStream_t s, cudaEvent_t *ev, const RzBatch *rz) {
-    if (ev) cudaEventRecord(ev[0], s);
-    if (prec == BDDC_PREC_FP64) avg_b<double, double>(L, B, prec, skip, s);
-    else if (prec == BDDC_PREC_FP32) avg_b<float, float>(L, B, prec, skip, s);
-    else avg_b<__nv_bfloat16, float>(L, B, prec, skip, s);
-    if (ev) cudaEventRecord(ev[1], s);
-    if (prec == BDDC_PREC_FP64) dir_b<double, double>(L, B, true, r, z, skip, s, rz);
-    else if (prec == BDDC_PREC_FP32) dir_b<float, float>(L, B, true, r, z, skip, s, rz);
-    else dir_b<__nv_bfloat16, float>(L, B, true, r, z, skip, s, rz);
-    if (ev) cudaEventRecord(ev[2], s);
+    if (prec == BDDC_PREC_FP64) post_b<double, double>(L, B, prec, r, z, skip, s, ev, rz);
+    else if (prec == BDDC_PREC_FP32) post_b<float, float>(L, B, prec, r, z, skip, s, ev, rz);
+    else post_b<__nv_bfloat16, float>(L, B, prec, r, z, skip, s, ev, rz);
 }
 
 // Variants the autotuner chooses from.
