@@ -29,10 +29,11 @@ namespace bddc {
 
 namespace {
 
-// Entry (r, c) of a stored b x b block sits at c * b + r, or at c * b + (r ^ c)
-// when the level's blocks are XOR-swizzled (a common power-of-two b).
-__device__ __forceinline__ int64_t fpos(int r, int c, int b, bool swz) {
-    return (int64_t)c * b + (swz ? (r ^ c) : r);
+// Entry (r, c) of a stored b x b block with leading dimension ld sits at
+// c * ld + r, or at c * b + (r ^ c) when the level's blocks are XOR-swizzled
+// (a common power-of-two b, ld = b).
+__device__ __forceinline__ int64_t fpos(int r, int c, int ld, bool swz) {
+    return (int64_t)c * ld + (swz ? (r ^ c) : r);
 }
 
 // Interior solve with the block factor of one substructure; x holds the
@@ -40,7 +41,7 @@ __device__ __forceinline__ int64_t fpos(int r, int c, int b, bool swz) {
 // exit; tmp has b entries.
 template <class T, class ACC>
 __device__ void dirichlet_solve(const T *F, int b, int m, bool swz, ACC *x, ACC *tmp) {
-    const int bb = b * b;
+    const int ldb = fld(b, swz), bb = b * ldb;
     for (int j = 0; j < m; ++j) {
         const T *Linv = F + (int64_t)j * 2 * bb;
         const T *Lsub = Linv + bb;
@@ -48,14 +49,14 @@ __device__ void dirichlet_solve(const T *F, int b, int m, bool swz, ACC *x, ACC 
             ACC t = x[j * b + r];
             if (j > 0) {
                 const ACC *xp = x + (j - 1) * b;
-                for (int c = 0; c < b; ++c) t -= ld<T, ACC>(Lsub + fpos(r, c, b, swz)) * xp[c];
+                for (int c = 0; c < b; ++c) t -= ld<T, ACC>(Lsub + fpos(r, c, ldb, swz)) * xp[c];
             }
             tmp[r] = t;
         }
         __syncthreads();
         for (int r = threadIdx.x; r < b; r += blockDim.x) {
             ACC s = 0;
-            for (int c = 0; c <= r; ++c) s += ld<T, ACC>(Linv + fpos(r, c, b, swz)) * tmp[c];
+            for (int c = 0; c <= r; ++c) s += ld<T, ACC>(Linv + fpos(r, c, ldb, swz)) * tmp[c];
             x[j * b + r] = s;
         }
         __syncthreads();
@@ -68,14 +69,14 @@ __device__ void dirichlet_solve(const T *F, int b, int m, bool swz, ACC *x, ACC 
                 // L_{j+1,j}^T: entry (r, c) is entry (c, r) of the stored block
                 const T *Lsub1 = F + (int64_t)(j + 1) * 2 * bb + bb;
                 const ACC *xn = x + (j + 1) * b;
-                for (int c = 0; c < b; ++c) t -= ld<T, ACC>(Lsub1 + fpos(c, r, b, swz)) * xn[c];
+                for (int c = 0; c < b; ++c) t -= ld<T, ACC>(Lsub1 + fpos(c, r, ldb, swz)) * xn[c];
             }
             tmp[r] = t;
         }
         __syncthreads();
         for (int r = threadIdx.x; r < b; r += blockDim.x) {
             ACC s = 0;
-            for (int c = r; c < b; ++c) s += ld<T, ACC>(Linv + fpos(c, r, b, swz)) * tmp[c];
+            for (int c = r; c < b; ++c) s += ld<T, ACC>(Linv + fpos(c, r, ldb, swz)) * tmp[c];
             x[j * b + r] = s;
         }
         __syncthreads();
@@ -126,8 +127,8 @@ struct StreamSmem {
     size_t stage, x, tmp, vg, total;
     template <class T, class ACC> __host__ __device__ static StreamSmem of(const DevLevel &L) {
         StreamSmem m;
-        const size_t mb = L.max_b > 0 ? L.max_b : 1;
-        m.stage = al16(2 * mb * mb * sizeof(T) + 32);        // plus slack to align each copy
+        const size_t mb = L.max_b > 0 ? L.max_b : 1, mld = L.max_ld > 0 ? L.max_ld : 1;
+        m.stage = al16(2 * mb * mld * sizeof(T) + 32);       // plus slack to align each copy
         m.x = al16(sizeof(ACC) * (size_t)(L.max_m > 0 ? L.max_m : 1) * mb);
         m.tmp = al16(sizeof(ACC) * mb);
         m.vg = al16(sizeof(ACC) * (size_t)(L.max_nG > 0 ? L.max_nG : 1));
@@ -151,7 +152,8 @@ __global__ void __launch_bounds__(kSB) k_dir_s(DevLevel L, const double *r, doub
     const bool swz = L.bp != 0;
     const OpSet<T> &O = Ops<T>::get(L);
     const T *F = O.dir + L.offF[sub];
-    const size_t bb2 = 2 * (size_t)b * b;
+    const int ldb = fld(b, swz);
+    const size_t bb2 = 2 * (size_t)b * ldb;
     // block i: its bytes rounded out to 16-byte boundaries, and where it starts in its stage
     auto issue = [&](int i) {
         const uintptr_t a = reinterpret_cast<uintptr_t>(F + (size_t)i * bb2);
@@ -193,13 +195,13 @@ __global__ void __launch_bounds__(kSB) k_dir_s(DevLevel L, const double *r, doub
     };
     for (int j = 0; j < m && ok; ++j) {
         if (!wait_block(j)) { ok = false; break; }
-        const T *Li = blk(j), *Ls = Li + (size_t)b * b;
+        const T *Li = blk(j), *Ls = Li + (size_t)b * ldb;
         for (int pass = 0; pass * RPP < b; ++pass) {      // the same passes in every thread
             const int rr = r0 + pass * RPP;
             ACC a = 0;
             if (rr < b && j > 0)
                 for (int c = part; c < b; c += kTPR)
-                    a += ld<T, ACC>(Ls + fpos(rr, c, b, swz)) * x[(j - 1) * b + c];
+                    a += ld<T, ACC>(Ls + fpos(rr, c, ldb, swz)) * x[(j - 1) * b + c];
 #pragma unroll
             for (int o = kTPR / 2; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
             if (rr < b && part == 0) tmp[rr] = x[j * b + rr] - a;
@@ -209,7 +211,7 @@ __global__ void __launch_bounds__(kSB) k_dir_s(DevLevel L, const double *r, doub
             const int rr = r0 + pass * RPP;
             ACC a = 0;
             if (rr < b)
-                for (int c = part; c <= rr; c += kTPR) a += ld<T, ACC>(Li + fpos(rr, c, b, swz)) * tmp[c];
+                for (int c = part; c <= rr; c += kTPR) a += ld<T, ACC>(Li + fpos(rr, c, ldb, swz)) * tmp[c];
 #pragma unroll
             for (int o = kTPR / 2; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
             if (rr < b && part == 0) x[j * b + rr] = a;
@@ -224,9 +226,9 @@ __global__ void __launch_bounds__(kSB) k_dir_s(DevLevel L, const double *r, doub
             const int rr = r0 + pass * RPP;
             ACC a = 0;
             if (rr < b && j < m - 1) {
-                const T *Ls1 = blk(j + 1) + (size_t)b * b;     // L_{j+1,j}^T: entry (rr, c) is (c, rr)
+                const T *Ls1 = blk(j + 1) + (size_t)b * ldb;     // L_{j+1,j}^T: entry (rr, c) is (c, rr)
                 for (int c = part; c < b; c += kTPR)
-                    a += ld<T, ACC>(Ls1 + fpos(c, rr, b, swz)) * x[(j + 1) * b + c];
+                    a += ld<T, ACC>(Ls1 + fpos(c, rr, ldb, swz)) * x[(j + 1) * b + c];
             }
 #pragma unroll
             for (int o = kTPR / 2; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
@@ -237,7 +239,7 @@ __global__ void __launch_bounds__(kSB) k_dir_s(DevLevel L, const double *r, doub
             const int rr = r0 + pass * RPP;
             ACC a = 0;
             if (rr < b)
-                for (int c = rr + part; c < b; c += kTPR) a += ld<T, ACC>(Li + fpos(c, rr, b, swz)) * tmp[c];
+                for (int c = rr + part; c < b; c += kTPR) a += ld<T, ACC>(Li + fpos(c, rr, ldb, swz)) * tmp[c];
 #pragma unroll
             for (int o = kTPR / 2; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
             if (rr < b && part == 0) x[j * b + rr] = a;
@@ -1184,23 +1186,32 @@ int vec_grid(int64_t n) {
 template <class T, class ACC> bool stream_fits(const DevLevel &L) {
     return StreamSmem::of<T, ACC>(L).total <= 227 * 1024;
 }
+// Shared memory of the generic interior kernels (the whole interior vector of
+// the largest substructure); a level beyond one block's shared memory has no
+// kernel to run on and is refused.
+template <class ACC> size_t generic_smem(const DevLevel &L) {
+    const size_t sm = sizeof(ACC) * ((size_t)L.max_m * L.max_b + L.max_b + L.max_nG);
+    if (sm > 227 * 1024)
+        throw Error(BDDC_E_ARG, "substructure interior of " + std::to_string(L.max_m * L.max_b) +
+                                    " DOFs exceeds the generic kernels' shared memory");
+    return sm;
+}
 template <class T, class ACC> void pre_t(const DevLevel &L, const double *r, const int *skip,
                                          cudaStream_t s) {
     if (stream_fits<T, ACC>(L)) {
-        k_dir_s<T, ACC, false><<<L.nsub, kSB, StreamSmem::of<T, ACC>(L).total, s>>>(L, r, nullptr, skip);
+        launch_k(false, k_dir_s<T, ACC, false>, L.nsub, kSB, StreamSmem::of<T, ACC>(L).total, s, L, r,
+                 (double *)nullptr, skip);
         return;
     }
-    const size_t sm = sizeof(ACC) * ((size_t)L.max_m * L.max_b + L.max_b + L.max_nG);
-    k_pre<T, ACC><<<L.nsub, 32, sm, s>>>(L, r, skip);
+    launch_k(false, k_pre<T, ACC>, L.nsub, 32, generic_smem<ACC>(L), s, L, r, skip);
 }
 template <class T, class ACC> void post_t(const DevLevel &L, const double *r, double *z,
                                           const int *skip, cudaStream_t s) {
     if (stream_fits<T, ACC>(L)) {
-        k_dir_s<T, ACC, true><<<L.nsub, kSB, StreamSmem::of<T, ACC>(L).total, s>>>(L, r, z, skip);
+        launch_k(false, k_dir_s<T, ACC, true>, L.nsub, kSB, StreamSmem::of<T, ACC>(L).total, s, L, r, z, skip);
         return;
     }
-    const size_t sm = sizeof(ACC) * ((size_t)L.max_m * L.max_b + L.max_b + L.max_nG);
-    k_post<T, ACC><<<L.nsub, 32, sm, s>>>(L, r, z, skip);
+    launch_k(false, k_post<T, ACC>, L.nsub, 32, generic_smem<ACC>(L), s, L, r, z, skip);
 }
 
 }  // namespace
@@ -1328,6 +1339,13 @@ void prepare_apply_kernels() {
     BDDC_SMEM_ATTR((k_dir_w<__nv_bfloat16, float, 32, true>));
     BDDC_SMEM_ATTR((k_neumann_r<__nv_bfloat16, float>));
     BDDC_SMEM_ATTR((k_average_r<__nv_bfloat16, float>));
+    // the generic kernels: interior vectors and Gamma vectors of any size
+    BDDC_SMEM_ATTR((k_pre<double, double>)); BDDC_SMEM_ATTR((k_post<double, double>));
+    BDDC_SMEM_ATTR((k_pre<float, float>)); BDDC_SMEM_ATTR((k_post<float, float>));
+    BDDC_SMEM_ATTR((k_pre<__nv_bfloat16, float>)); BDDC_SMEM_ATTR((k_post<__nv_bfloat16, float>));
+    BDDC_SMEM_ATTR((k_neumann<double, double>)); BDDC_SMEM_ATTR((k_average<double, double>));
+    BDDC_SMEM_ATTR((k_neumann<float, float>)); BDDC_SMEM_ATTR((k_average<float, float>));
+    BDDC_SMEM_ATTR((k_neumann<__nv_bfloat16, float>)); BDDC_SMEM_ATTR((k_average<__nv_bfloat16, float>));
 #undef BDDC_SMEM_ATTR
 }
 
@@ -1360,9 +1378,9 @@ void apply_level_pre(const DevLevel &L, int prec, const double *r, const int *sk
         else neu_launch<__nv_bfloat16, float>(L, prec, r, skip, s);
     } else {
         const size_t smn = sizeof(double) * (size_t)(L.max_nG > L.max_nc ? L.max_nG : L.max_nc);
-        if (prec == BDDC_PREC_FP64) k_neumann<double, double><<<L.nsub, 128, smn, s>>>(L, r, skip);
-        else if (prec == BDDC_PREC_FP32) k_neumann<float, float><<<L.nsub, 128, smn, s>>>(L, r, skip);
-        else k_neumann<__nv_bfloat16, float><<<L.nsub, 128, smn, s>>>(L, r, skip);
+        if (prec == BDDC_PREC_FP64) launch_k(false, k_neumann<double, double>, L.nsub, 128, smn, s, L, r, skip);
+        else if (prec == BDDC_PREC_FP32) launch_k(false, k_neumann<float, float>, L.nsub, 128, smn, s, L, r, skip);
+        else launch_k(false, k_neumann<__nv_bfloat16, float>, L.nsub, 128, smn, s, L, r, skip);
     }
     if (ev) cudaEventRecord(ev[2], s);
 }
@@ -1377,9 +1395,9 @@ void apply_level_post(const DevLevel &L, int prec, const double *r, double *z, c
         else avg_launch<__nv_bfloat16, float>(L, prec, skip, s);
     } else {
         const size_t smn = sizeof(double) * (size_t)(L.max_nc > 0 ? L.max_nc : 1);
-        if (prec == BDDC_PREC_FP64) k_average<double, double><<<L.nsub, 128, smn, s>>>(L, skip);
-        else if (prec == BDDC_PREC_FP32) k_average<float, float><<<L.nsub, 128, smn, s>>>(L, skip);
-        else k_average<__nv_bfloat16, float><<<L.nsub, 128, smn, s>>>(L, skip);
+        if (prec == BDDC_PREC_FP64) launch_k(false, k_average<double, double>, L.nsub, 128, smn, s, L, skip);
+        else if (prec == BDDC_PREC_FP32) launch_k(false, k_average<float, float>, L.nsub, 128, smn, s, L, skip);
+        else launch_k(false, k_average<__nv_bfloat16, float>, L.nsub, 128, smn, s, L, skip);
     }
     if (ev) cudaEventRecord(ev[1], s);
     if (wp) {

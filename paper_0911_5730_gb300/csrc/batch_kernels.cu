@@ -17,6 +17,9 @@
 
 #include <algorithm>
 #include <cstdlib>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <type_traits>
 
 namespace bddc {
@@ -79,9 +82,6 @@ __device__ __forceinline__ void load_vec(const T *src, ACC (&v)[N]) {
     }
 }
 
-// Entry (r, c) of a stored b x b block: c * b + r, or c * b + (r ^ c) when the
-// level's blocks are XOR-swizzled.
-__device__ __forceinline__ int fpos_b(int r, int c, int b, bool swz) { return c * b + (swz ? (r ^ c) : r); }
 
 // The batched Dirichlet kernel gives one block of LR warps to one
 // substructure, LR lanes to a right-hand side: warp w takes right-hand sides
@@ -405,71 +405,116 @@ __global__ void __launch_bounds__(32 * lanes_per_rhs<BP>()) k_dir_b(DevLevel L, 
 }
 
 // Batched Dirichlet solves for substructures whose factor does not fit in
-// shared memory (large or irregular cells): one block of kSBT threads per
-// substructure, the factor blocks streamed through a ring of SBN stages as in
-// the single right-hand-side streaming kernel (block i in stage i % SBN; the
+// shared memory (large or irregular cells).  Persistent blocks, one launch
+// per size bucket (the substructures whose blocks take the same number of
+// warps), each block taking the bucket's substructures largest first; per
+// substructure all 32 right-hand-side columns go in one pass, so the factor
+// is streamed once, block by block, through a ring of SBN stages as in the
+// single right-hand-side streaming kernel (block i in stage i % SBN; the
 // backward sweep starts from the blocks left in the ring and refills the
-// stage of block j+1 after step j), the right-hand sides in passes of KP
-// (the factor is streamed once per pass).  Thread (rg, kk) of a pass works on
-// right-hand side k0 + kk and rows rg, rg + RG, ... (RG = kSBT / KP) of each
-// block; factor entries are read by all KP threads of a row group at once.
-// The coupling terms are applied by the thread owning the row (row % RG), in
-// entry order.  The interior index arrays are read from global memory.
-constexpr int kSBT = 256, SBN = 3;
+// stage of block j+1 after step j).  Thread t of a substructure with block
+// size b owns column group g = t / h (columns 4g..4g+3) and rows k and k + h
+// (k = t mod h, h = ceil(b/2)) of every block: a 2-row x 4-column register
+// tile, so a factor entry read from shared memory feeds four FMAs and a
+// broadcast 4-column vector eight, with four factor columns in flight.  Rows
+// of a block are ld apart (odd unless swizzled), so the transposed walks of
+// the backward sweep are free of bank conflicts too.  The block results of
+// the forward sweep (y_j) and of the backward sweep (x_j) go to a global
+// scratch [8][rows][4] per substructure, which stays in L2; each thread
+// reads back only what it wrote, one step ahead.
+constexpr int SBN = 3, kSBMaxT = 32 * kMaxBuckets;   // ring stages, largest block
+
+// doubles of the reduction area: four per thread, and the 8 x 32 of the
+// final r.z sum
+__host__ __device__ inline size_t red_doubles(int nt) { return 4 * (size_t)nt > 256 ? 4 * (size_t)nt : 256; }
 
 struct StreamSmemB {
-    size_t stage, xs, tmp, vg, red, total;
-    template <class T, class ACC> __host__ __device__ static StreamSmemB of(const DevLevel &L, int KP) {
+    size_t stage, ring, vec, red, total;
+    template <class T, class ACC> __host__ __device__ static StreamSmemB of(const DevLevel &L, int nt) {
         StreamSmemB m;
-        const size_t mb = L.max_b > 0 ? L.max_b : 1;
-        m.stage = al16(2 * mb * mb * sizeof(T) + 32);
-        m.xs = al16(sizeof(ACC) * (size_t)(L.max_m > 0 ? L.max_m : 1) * mb * KP);
-        m.tmp = al16(sizeof(ACC) * mb * KP);
-        m.vg = al16(sizeof(ACC) * (size_t)(L.max_nG > 0 ? L.max_nG : 1) * KP);
-        m.red = al16(8 * kSBT + 16);
-        m.total = SBN * m.stage + m.xs + m.tmp + m.vg + m.red + 8 * SBN + 16;
+        const size_t mb = L.max_b > 0 ? L.max_b : 1, mld = L.max_ld > 0 ? L.max_ld : 1;
+        m.stage = al16(2 * mb * mld * sizeof(T) + 32);
+        m.ring = SBN * m.stage;
+        m.vec = al16(sizeof(ACC) * mb * kMaxBatch);   // [8][b][4]
+        m.red = al16(8 * red_doubles(nt) + 16);       // four doubles per thread (at least 256), a flag
+        m.total = m.ring + 2 * m.vec + m.red + 8 * SBN + 16;
         return m;
     }
 };
 
-template <class T, class ACC, bool POST>
-__global__ void __launch_bounds__(kSBT) k_dir_bs(DevLevel L, BatchLevel B, const double *r, double *z,
-                                                 const int *skip, int KP, RzBatch rz) {
+__device__ __forceinline__ void ld4(const float *p, float (&v)[4]) {
+    const float4 t = *reinterpret_cast<const float4 *>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void ld4(const double *p, double (&v)[4]) {
+    const double2 a = reinterpret_cast<const double2 *>(p)[0], c = reinterpret_cast<const double2 *>(p)[1];
+    v[0] = a.x; v[1] = a.y; v[2] = c.x; v[3] = c.y;
+}
+__device__ __forceinline__ void st4(float *p, const float (&v)[4]) {
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void st4(double *p, const double (&v)[4]) {
+    reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
+}
+
+// a0 (row r0) and, with TWO, a1 (row r1) -= (SUB) or += sum over c in
+// [c0, c1) of M(r, c) v[c] for four columns.  COL: M(r, c) is the stored
+// entry (r, c) (a column walk); else the stored entry (c, r) (a row walk,
+// the transposed block).
+template <class T, class ACC, bool SUB, bool TWO, bool COL, bool SWZ>
+__device__ __forceinline__ void prod2(ACC (&a0)[4], ACC (&a1)[4], const T *M, int ldm, const ACC *v, int c0,
+                                      int c1, int r0, int r1) {
+    auto at = [&](int r, int c) -> const T * {
+        if (COL) return M + c * ldm + (SWZ ? (r ^ c) : r);
+        return M + r * ldm + (SWZ ? (c ^ r) : c);
+    };
+    auto fma4 = [&](ACC (&a)[4], ACC l, const ACC (&x)[4]) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (SUB) a[q] -= l * x[q];
+            else a[q] += l * x[q];
+        }
+    };
+    int c = c0;
+    for (; c + 4 <= c1; c += 4) {
+        ACC x[4][4], l0[4], l1[4];
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) ld4(v + (c + cc) * 4, x[cc]);
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) {
+            l0[cc] = ld<T, ACC>(at(r0, c + cc));
+            if (TWO) l1[cc] = ld<T, ACC>(at(r1, c + cc));
+        }
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) {
+            fma4(a0, l0[cc], x[cc]);
+            if (TWO) fma4(a1, l1[cc], x[cc]);
+        }
+    }
+    for (; c < c1; ++c) {
+        ACC x[4];
+        ld4(v + c * 4, x);
+        fma4(a0, ld<T, ACC>(at(r0, c)), x);
+        if (TWO) fma4(a1, ld<T, ACC>(at(r1, c)), x);
+    }
+}
+
+template <class T, class ACC, bool SWZ, bool POST>
+__global__ void __launch_bounds__(kSBMaxT, 1) k_dir_bs(DevLevel L, BatchLevel B, const double *r, double *z,
+                                                    const int *skip, RzBatch rz, const int *perm, int count) {
     extern __shared__ __align__(16) unsigned char smem_bs[];
     if (skip && *skip) return;
-    const StreamSmemB ly = StreamSmemB::of<T, ACC>(L, KP);
+    const int nt = blockDim.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nw = nt >> 5;
+    const StreamSmemB ly = StreamSmemB::of<T, ACC>(L, nt);
     unsigned char *ring = smem_bs;
-    unsigned char *p = smem_bs + SBN * ly.stage;
-    ACC *xs = reinterpret_cast<ACC *>(p);   p += ly.xs;
-    ACC *tmp = reinterpret_cast<ACC *>(p);  p += ly.tmp;
-    ACC *vG = reinterpret_cast<ACC *>(p);   p += ly.vg;
-    double *red = reinterpret_cast<double *>(p);   // kSBT partials and a flag word
-    int *flag = reinterpret_cast<int *>(red + kSBT);
-    p += ly.red;
-    unsigned long long *bars = reinterpret_cast<unsigned long long *>(p);
-    const int sub = blockIdx.x, tid = threadIdx.x;
+    ACC *ybuf = reinterpret_cast<ACC *>(smem_bs + ly.ring);
+    ACC *tbuf = reinterpret_cast<ACC *>(smem_bs + ly.ring + ly.vec);
+    double *red = reinterpret_cast<double *>(smem_bs + ly.ring + 2 * ly.vec);
+    int *flag = reinterpret_cast<int *>(red + red_doubles(nt));
+    unsigned long long *bars = reinterpret_cast<unsigned long long *>(smem_bs + ly.ring + 2 * ly.vec + ly.red);
     const int K = B.K;
-    const int nI = L.nI[sub], nG = L.nG[sub], b = L.bsz[sub], m = nI > 0 ? L.nblk[sub] : 0;
-    const bool swz = L.bp != 0;
     const OpSet<T> &O = Ops<T>::get(L);
-    const T *F = O.dir + L.offF[sub];
-    const size_t bb2 = 2 * (size_t)b * b;
-    const int *iI = L.idxI + L.offI[sub];
-    const int *iG = L.idxG + L.offG[sub];
-    const int64_t c0e = L.offCOO[sub], c1e = L.offCOO[sub + 1];
-    const int RG = kSBT / KP, kk = tid % KP, rg = tid / KP;
-    auto issue = [&](int i) {
-        const uintptr_t a = reinterpret_cast<uintptr_t>(F + (size_t)i * bb2);
-        const uintptr_t al = a & ~uintptr_t(15);
-        const uintptr_t ae = (a + bb2 * sizeof(T) + 15) & ~uintptr_t(15);
-        mbar_expect(&bars[i % SBN], (unsigned)(ae - al));
-        bulk_copy(ring + (size_t)(i % SBN) * ly.stage, reinterpret_cast<const void *>(al), (unsigned)(ae - al),
-                  &bars[i % SBN]);
-    };
-    auto blk = [&](int i) {
-        const uintptr_t a = reinterpret_cast<uintptr_t>(F + (size_t)i * bb2);
-        return reinterpret_cast<const T *>(ring + (size_t)(i % SBN) * ly.stage + (a & 15));
-    };
     if (tid == 0)
         for (int s2 = 0; s2 < SBN; ++s2) mbar_init(&bars[s2]);
     __syncthreads();
@@ -481,162 +526,231 @@ __global__ void __launch_bounds__(kSBT) k_dir_bs(DevLevel L, BatchLevel B, const
         par ^= 1u << s2;
         return __syncthreads_and(got) != 0;
     };
-    for (int k0 = 0; k0 < K && ok; k0 += KP) {
-        const int k = k0 + kk;
-        const bool act = k < K;
+    for (int ti = blockIdx.x; ti < count && ok; ti += gridDim.x) {
+        const int sub = perm[ti];
+        const int nI = L.nI[sub], nG = L.nG[sub], b = L.bsz[sub], m = nI > 0 ? L.nblk[sub] : 0;
+        const int mb = m * b, ldb = fld(b, SWZ), h = (b + 1) >> 1;
+        const T *F = O.dir + L.offF[sub];
+        const size_t bsq = (size_t)b * ldb, bb2 = 2 * bsq;
+        const int *iI = L.idxI + L.offI[sub];
+        const int *iG = L.idxG + L.offG[sub];
+        ACC *Ysub = reinterpret_cast<ACC *>(B.ys) + L.offY[sub] * kMaxBatch;   // [8][mb][4]
+        const bool act = tid < 8 * h;
+        const int cg = act ? tid / h : 0, k = act ? tid - cg * h : 0;
+        const int r0 = k, r1 = k + h, r1c = r1 < b ? r1 : b - 1;   // r1 == b for odd b: computed, not kept
+        const bool colact = act && 4 * cg < K;
+        ACC *Yg = Ysub + (size_t)cg * mb * 4;
+        ACC *yb = ybuf + (size_t)cg * b * 4, *tb = tbuf + (size_t)cg * b * 4;
+        auto issue = [&](int i) {
+            const uintptr_t a = reinterpret_cast<uintptr_t>(F + (size_t)i * bb2);
+            const uintptr_t al = a & ~uintptr_t(15);
+            const uintptr_t ae = (a + bb2 * sizeof(T) + 15) & ~uintptr_t(15);
+            mbar_expect(&bars[i % SBN], (unsigned)(ae - al));
+            bulk_copy(ring + (size_t)(i % SBN) * ly.stage, reinterpret_cast<const void *>(al),
+                      (unsigned)(ae - al), &bars[i % SBN]);
+        };
+        auto blk = [&](int i) {
+            const uintptr_t a = reinterpret_cast<uintptr_t>(F + (size_t)i * bb2);
+            return reinterpret_cast<const T *>(ring + (size_t)(i % SBN) * ly.stage + (a & 15));
+        };
         if (tid == 0)
             for (int i = 0; i < SBN && i < m; ++i) issue(i);
-        // right-hand sides of this pass, coalesced over (row, column)
-        for (int e = tid; e < m * b * KP; e += kSBT) {
-            const int i = e / KP, c = e - i * KP;
-            xs[e] = (i < nI && k0 + c < K) ? from_f64<ACC>(r[(int64_t)iI[i] * K + k0 + c]) : (ACC)0;
-        }
-        if (POST) {
-            for (int e = tid; e < nG * KP; e += kSBT) {
-                const int q = e / KP, c = e - q * KP;
-                vG[e] = (k0 + c < K) ? from_f64<ACC>(B.uB[(int64_t)iG[q] * K + k0 + c]) : (ACC)0;
-            }
-            __syncthreads();
-            for (int64_t e = c0e; e < c1e; ++e) {
-                const int il = L.cooI[e];
-                if (il % RG != rg) continue;
-                xs[il * KP + kk] -= ld<T, ACC>(O.aig + e) * vG[L.cooG[e] * KP + kk];
-            }
-        } else {
-            for (int e = tid; e < nG * KP; e += kSBT) vG[e] = 0;
-        }
-        __syncthreads();
+        // interior row i of the right-hand side in this thread's four columns,
+        // minus its A_{I Gamma} u_B terms in the post-correction (the row's
+        // coupling entries in increasing order); padding rows are zero
+        const int64_t i0 = L.offI[sub];
+        auto load_row = [&](int i, ACC (&v)[4]) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v[q] = 0;
+            if (i >= nI) return;
+            const double *ri = r + (int64_t)iI[i] * K;
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (4 * cg + q < K) v[q] = from_f64<ACC>(ri[4 * cg + q]);
+            if (POST)
+                for (int64_t p = L.cooRptr[i0 + i]; p < L.cooRptr[i0 + i + 1]; ++p) {
+                    const ACC a = ld<T, ACC>(O.aig + L.cooRowE[p]);
+                    const double *u = B.uB + (int64_t)L.cooRowId[p] * K;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if (4 * cg + q < K) v[q] -= a * from_f64<ACC>(u[4 * cg + q]);
+                }
+        };
+        double rzs[4] = {0.0, 0.0, 0.0, 0.0};
+        ACC n0[4], n1[4];                 // the next step's rows, loaded a step ahead
+        if (colact && m > 0) { load_row(r0, n0); load_row(r1c, n1); }
+        // forward: y_j = Linv_j (rhs_j - Lsub_j y_{j-1})
         for (int j = 0; j < m; ++j) {
             if (!wait_block(j)) { ok = false; break; }
-            const T *Li = blk(j), *Ls = Li + (size_t)b * b;
-            for (int rr = rg; rr < b; rr += RG) {
-                ACC a = 0;
-                if (j > 0)
-                    for (int c = 0; c < b; ++c) a += ld<T, ACC>(Ls + fpos_b(rr, c, b, swz)) * xs[((j - 1) * b + c) * KP + kk];
-                tmp[rr * KP + kk] = xs[(j * b + rr) * KP + kk] - a;
+            const T *Li = blk(j), *Ls = Li + bsq;
+            if (colact) {
+                ACC a0[4], a1[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) { a0[q] = n0[q]; a1[q] = n1[q]; }
+                if (j + 1 < m) {
+                    load_row((j + 1) * b + r0, n0);
+                    load_row((j + 1) * b + r1c, n1);
+                }
+                if (j > 0) prod2<T, ACC, true, true, true, SWZ>(a0, a1, Ls, ldb, yb, 0, b, r0, r1c);
+                st4(tb + r0 * 4, a0);
+                if (r1 < b) st4(tb + r1 * 4, a1);
             }
             __syncthreads();
-            for (int rr = rg; rr < b; rr += RG) {
-                ACC a = 0;
-                for (int c = 0; c <= rr; ++c) a += ld<T, ACC>(Li + fpos_b(rr, c, b, swz)) * tmp[c * KP + kk];
-                xs[(j * b + rr) * KP + kk] = a;
+            if (colact) {
+                // Linv_j lower triangular (zeros stored above): row k needs
+                // columns < h only, row k + h all of them
+                ACC a0[4] = {0, 0, 0, 0}, a1[4] = {0, 0, 0, 0};
+                prod2<T, ACC, false, true, true, SWZ>(a0, a1, Li, ldb, tb, 0, h, r0, r1c);
+                prod2<T, ACC, false, false, true, SWZ>(a1, a1, Li, ldb, tb, h, b, r1c, r1c);
+                st4(yb + r0 * 4, a0);
+                st4(Yg + ((size_t)j * b + r0) * 4, a0);
+                if (r1 < b) {
+                    st4(yb + r1 * 4, a1);
+                    st4(Yg + ((size_t)j * b + r1) * 4, a1);
+                }
+                if (j + 1 == m)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) { n0[q] = a0[q]; n1[q] = a1[q]; }   // y_{m-1}
             }
             __syncthreads();
             if (tid == 0 && j + SBN < m) issue(j + SBN);
         }
+        // backward: x_j = Linv_j^T (y_j - Lsub_{j+1}^T x_{j+1})
         for (int j = m - 1; j >= 0 && ok; --j) {
             if (j < m - SBN && !wait_block(j)) { ok = false; break; }
             const T *Li = blk(j);
-            for (int rr = rg; rr < b; rr += RG) {
-                ACC a = 0;
-                if (j < m - 1) {
-                    const T *Ls1 = blk(j + 1) + (size_t)b * b;
-                    for (int c = 0; c < b; ++c) a += ld<T, ACC>(Ls1 + fpos_b(c, rr, b, swz)) * xs[((j + 1) * b + c) * KP + kk];
+            if (colact) {
+                ACC a0[4], a1[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) { a0[q] = n0[q]; a1[q] = n1[q]; }
+                if (j > 0) {
+                    ld4(Yg + ((size_t)(j - 1) * b + r0) * 4, n0);
+                    ld4(Yg + ((size_t)(j - 1) * b + r1c) * 4, n1);
                 }
-                tmp[rr * KP + kk] = xs[(j * b + rr) * KP + kk] - a;
+                if (j < m - 1) prod2<T, ACC, true, true, false, SWZ>(a0, a1, blk(j + 1) + bsq, ldb, yb, 0, b, r0, r1c);
+                st4(tb + r0 * 4, a0);
+                if (r1 < b) st4(tb + r1 * 4, a1);
             }
             __syncthreads();
-            for (int rr = rg; rr < b; rr += RG) {
-                ACC a = 0;
-                for (int c = rr; c < b; ++c) a += ld<T, ACC>(Li + fpos_b(c, rr, b, swz)) * tmp[c * KP + kk];
-                xs[(j * b + rr) * KP + kk] = a;
+            if (colact) {
+                // Linv_j^T upper triangular: row k needs all columns, row k + h
+                // columns >= h only
+                ACC a0[4] = {0, 0, 0, 0}, a1[4] = {0, 0, 0, 0};
+                prod2<T, ACC, false, false, false, SWZ>(a0, a0, Li, ldb, tb, 0, h, r0, r0);
+                prod2<T, ACC, false, true, false, SWZ>(a0, a1, Li, ldb, tb, h, b, r0, r1c);
+#pragma unroll
+                for (int rw = 0; rw < 2; ++rw) {
+                    const int row = rw ? r1 : r0;
+                    if (row >= b) break;
+                    const ACC (&a)[4] = rw ? a1 : a0;
+                    st4(yb + row * 4, a);
+                    if (!POST) {
+                        st4(Yg + ((size_t)j * b + row) * 4, a);
+                    } else if (j * b + row < nI) {
+                        const int64_t o = (int64_t)iI[j * b + row] * K;
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const int kk = 4 * cg + q;
+                            if (kk >= K) break;
+                            const double zv = to_f64(a[q]);
+                            z[o + kk] = zv;
+                            if (rz.sc) rzs[q] = fma(r[o + kk], zv, rzs[q]);
+                        }
+                    }
+                }
             }
             __syncthreads();
             if (tid == 0 && j + 1 < m && j + 1 - SBN >= 0) issue(j + 1 - SBN);
         }
         if (!ok) break;
+        // every issued block has been waited for: the ring is idle from here
         if (!POST) {
-            // A_{Gamma I} u_I into vG (owner of row gl: gl % RG), then r_B -= it
-            for (int64_t e = c0e; e < c1e; ++e) {
-                const int gl = L.cooG[e];
-                if (gl % RG != rg) continue;
-                vG[gl * KP + kk] += ld<T, ACC>(O.aig + e) * xs[L.cooI[e] * KP + kk];
-            }
-            __syncthreads();
-            for (int e = tid; e < nG * KP; e += kSBT) {
-                const int q = e / KP, c = e - q * KP;
-                if (k0 + c >= K) continue;
-                const int64_t o = (int64_t)iG[q] * K + k0 + c;
-                const ACC v = vG[e];
-                if (v != (ACC)0) atomicAdd(&B.rB[o], -to_f64(v));
-                B.uB[o] = 0.0;   // consumed by the previous post-correction
-            }
-        } else {
-            double acc = 0.0;
-            for (int i = rg; i < nI; i += RG) {
-                if (!act) break;
-                const int64_t o = (int64_t)iI[i] * K + k;
-                const double zv = to_f64(xs[i * KP + kk]);
-                z[o] = zv;
-                if (rz.sc) acc = fma(r[o], zv, acc);
-            }
-            for (int64_t e = L.offOwn[sub] + rg; e < L.offOwn[sub + 1]; e += RG) {
-                if (!act) break;
+            // r_B -= A_{Gamma I} x (Gamma entry q: warp q mod nw, lane: column;
+            // the entry's couplings in order); u_B was consumed by the previous
+            // post-correction
+            const int64_t g0 = L.offG[sub];
+            if (lane < K)
+                for (int q = w; q < nG; q += nw) {
+                    ACC acc = 0;
+                    for (int64_t e = L.cooGptr[g0 + q]; e < L.cooGptr[g0 + q + 1]; ++e)
+                        acc += ld<T, ACC>(O.aig + e) *
+                               Ysub[((size_t)(lane >> 2) * mb + L.cooI[e]) * 4 + (lane & 3)];
+                    const int64_t o = (int64_t)iG[q] * K + lane;
+                    if (acc != (ACC)0) atomicAdd(&B.rB[o], -to_f64(acc));
+                    B.uB[o] = 0.0;
+                }
+            continue;
+        }
+        // interface entries of z (owned by this substructure): u_B
+        if (colact)
+            for (int64_t e = L.offOwn[sub] + k; e < L.offOwn[sub + 1]; e += h) {
                 const int id = L.own[e];
-                const int64_t o = (int64_t)L.ifaceDof[id] * K + k;
-                const double zv = B.uB[(int64_t)id * K + k];
-                z[o] = zv;
-                if (rz.sc) acc = fma(r[o], zv, acc);
-            }
-            if (rz.sc) {
-                // per right-hand side: the row groups summed in a fixed order
-                red[rg * KP + kk] = acc;
-                __syncthreads();
-                if (tid < KP && k0 + tid < K) {
-                    double t = 0.0;
-                    for (int g = 0; g < RG; ++g) t += red[g * KP + tid];
-                    rz.part[(int64_t)sub * K + k0 + tid] = t;
+                const int64_t o = (int64_t)L.ifaceDof[id] * K;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int kk = 4 * cg + q;
+                    if (kk >= K) break;
+                    const double zv = B.uB[(int64_t)id * K + kk];
+                    z[o + kk] = zv;
+                    if (rz.sc) rzs[q] = fma(r[o + kk], zv, rzs[q]);
                 }
             }
-        }
-        // the next pass streams the factor again from block 0: every stage is
-        // idle here (each issued block has been waited for)
+        if (!rz.sc) continue;
+        // r.z per column: the h threads of its group in order, then the
+        // substructures by the block that finishes the last one, in order
+#pragma unroll
+        for (int q = 0; q < 4; ++q) red[tid * 4 + q] = rzs[q];
         __syncthreads();
-    }
-    if (!ok) {
-        if (tid == 0) {
-            atomicExch(L.err, 1);
-            for (int s2 = 0; s2 < SBN; ++s2) mbar_wait(&bars[s2], (par >> s2) & 1u);   // bounded
+        if (tid < K) {
+            const int g = tid >> 2, q = tid & 3;
+            double t = 0.0;
+            for (int u = g * h; u < g * h + h; ++u) t += red[u * 4 + q];
+            rz.part[(int64_t)sub * K + tid] = t;
         }
-        return;
-    }
-    if (POST && rz.sc) {
         __threadfence();
         __syncthreads();
         if (tid == 0) *flag = atomicAdd(rz.counter, 1u) == (unsigned)L.nsub - 1u;
         __syncthreads();
-        if (!*flag) return;
-        __threadfence();
-        // right-hand side t % 32 of thread t; the eight warps split the substructures
-        const int lane = tid & 31, warp = tid >> 5;
-        double t = 0.0;
-        if (lane < K)
-            for (int sb = warp; sb < L.nsub; sb += kSBT / 32) t += __ldcg(&rz.part[(int64_t)sb * K + lane]);
-        red[warp * 32 + lane] = t;
-        __syncthreads();
-        if (warp == 0 && lane < K) {
-            double tot = 0.0;
-            for (int w = 0; w < kSBT / 32; ++w) tot += red[w * 32 + lane];
-            BatchScalars *sc = rz.sc;
-            if (!sc->done[lane]) {
-                const double beta = sc->fresh[lane] ? 0.0 : tot / sc->rho[lane];
-                sc->fresh[lane] = 0;
-                sc->hold[lane] = 0;
-                sc->beta[lane] = beta;
-                if (sc->it[lane] > 0) rz.betas[(int64_t)(sc->it[lane] - 1) * K + lane] = beta;
-                sc->rho[lane] = tot;
+        if (*flag) {
+            __threadfence();
+            // eight fixed groups of substructures (sb mod 8), whatever the
+            // bucket of the finishing block: the same order in every run
+            for (int g = w; g < 8; g += nw) {
+                double t = 0.0;
+                if (lane < K)
+                    for (int sb = g; sb < L.nsub; sb += 8) t += __ldcg(&rz.part[(int64_t)sb * K + lane]);
+                red[g * 32 + lane] = t;
             }
+            __syncthreads();
+            if (w == 0 && lane < K) {
+                double tot = 0.0;
+                for (int v = 0; v < 8; ++v) tot += red[v * 32 + lane];
+                BatchScalars *sc = rz.sc;
+                if (!sc->done[lane]) {
+                    const double beta = sc->fresh[lane] ? 0.0 : tot / sc->rho[lane];
+                    sc->fresh[lane] = 0;
+                    sc->hold[lane] = 0;
+                    sc->beta[lane] = beta;
+                    if (sc->it[lane] > 0) rz.betas[(int64_t)(sc->it[lane] - 1) * K + lane] = beta;
+                    sc->rho[lane] = tot;
+                }
+            }
+            if (tid == 0) *rz.counter = 0u;
         }
-        if (tid == 0) *rz.counter = 0u;
+        __syncthreads();                  // red is free for the next substructure
+    }
+    if (!ok && tid == 0) {
+        atomicExch(L.err, 1);
+        for (int s2 = 0; s2 < SBN; ++s2) mbar_wait(&bars[s2], (par >> s2) & 1u);   // bounded
     }
 }
 
 // (6)-(9) for K right-hand sides when the Neumann records are too large to
-// stage whole: one block of kSBT threads per substructure reads N_i and
+// stage whole: one block of kNBT threads per substructure reads N_i and
 // Psi_i^T from global memory in chunks of contiguous rows, loaded by all
 // threads (coalesced) into shared memory; warp w computes the rows q = w
 // (mod 8) for all right-hand sides (lane k: right-hand side k).
-constexpr int kChunkBytes = 32 * 1024;
+constexpr int kChunkBytes = 32 * 1024, kNBT = 256;   // chunk of N; threads (8 warps)
 
 template <class T> __host__ __device__ inline int neu_chunk_rows(int nG) {
     const int rows = kChunkBytes / (int)(sizeof(T) * (nG > 0 ? nG : 1));
@@ -651,7 +765,7 @@ template <class T, class ACC> __host__ __device__ inline size_t neu_bg_smem(cons
 }
 
 template <class T, class ACC>
-__global__ void __launch_bounds__(kSBT) k_neu_bg(DevLevel L, BatchLevel B, int pidx, const double *r,
+__global__ void __launch_bounds__(kNBT) k_neu_bg(DevLevel L, BatchLevel B, int pidx, const double *r,
                                                  const int *skip) {
     extern __shared__ __align__(16) unsigned char smem_ng[];
     (void)pidx;
@@ -665,7 +779,7 @@ __global__ void __launch_bounds__(kSBT) k_neu_bg(DevLevel L, BatchLevel B, int p
     T *buf = reinterpret_cast<T *>(smem_ng + al16(sizeof(ACC) * mg * 32) + al16(sizeof(ACC) * mc * 32));
     const OpSet<T> &O = Ops<T>::get(L);
     const int64_t g0 = L.offG[sub];
-    for (int e = tid; e < nG * 32; e += kSBT) {
+    for (int e = tid; e < nG * 32; e += kNBT) {
         const int q = e >> 5, k = e & 31;
         double v = 0.0;
         if (k < K) {
@@ -683,7 +797,7 @@ __global__ void __launch_bounds__(kSBT) k_neu_bg(DevLevel L, BatchLevel B, int p
         for (int p0 = 0; p0 < nG; p0 += CH) {
             const int pn = nG - p0 < CH ? nG - p0 : CH;
             __syncthreads();
-            for (int e = tid; e < pn * nG; e += kSBT) buf[e] = N[(int64_t)p0 * nG + e];
+            for (int e = tid; e < pn * nG; e += kNBT) buf[e] = N[(int64_t)p0 * nG + e];
             __syncthreads();
             for (int pp = 0; pp < pn; ++pp) {
                 const ACC fv = f[(p0 + pp) * 32 + lane];
@@ -703,7 +817,7 @@ __global__ void __launch_bounds__(kSBT) k_neu_bg(DevLevel L, BatchLevel B, int p
     // r_c += Psi^T f (Psi^T[k * nG + q], staged whole)
     const T *P = O.psit + L.offP[sub];
     __syncthreads();
-    for (int e = tid; e < nc * nG; e += kSBT) buf[e] = P[e];
+    for (int e = tid; e < nc * nG; e += kNBT) buf[e] = P[e];
     __syncthreads();
     for (int k = warp; k < nc; k += 8) {
         ACC s0 = 0;
@@ -714,7 +828,7 @@ __global__ void __launch_bounds__(kSBT) k_neu_bg(DevLevel L, BatchLevel B, int p
 
 // (9) for K right-hand sides, Psi_i read from global memory (staged whole).
 template <class T, class ACC>
-__global__ void __launch_bounds__(kSBT) k_avg_bg(DevLevel L, BatchLevel B, int pidx, const int *skip) {
+__global__ void __launch_bounds__(kNBT) k_avg_bg(DevLevel L, BatchLevel B, int pidx, const int *skip) {
     extern __shared__ __align__(16) unsigned char smem_ag[];
     (void)pidx;
     if (skip && *skip) return;
@@ -728,12 +842,12 @@ __global__ void __launch_bounds__(kSBT) k_avg_bg(DevLevel L, BatchLevel B, int p
     const OpSet<T> &O = Ops<T>::get(L);
     const int64_t g0 = L.offG[sub];
     const int *rcs = L.rc + L.offC[sub];
-    for (int e = tid; e < nc * 32; e += kSBT) {
+    for (int e = tid; e < nc * 32; e += kNBT) {
         const int k = e >> 5, kk = e & 31;
         uc[e] = kk < K ? from_f64<ACC>(B.ucv[(int64_t)rcs[k] * K + kk]) : (ACC)0;
     }
     const T *P = O.psit + L.offP[sub];
-    for (int e = tid; e < nc * nG; e += kSBT) buf[e] = P[e];
+    for (int e = tid; e < nc * nG; e += kNBT) buf[e] = P[e];
     __syncthreads();
     for (int q = warp; q < nG; q += 8) {
         ACC v = act ? from_f64<ACC>(B.w[(g0 + q) * K + lane]) : (ACC)0;
@@ -1376,11 +1490,14 @@ int vgrid_b(int64_t nK, int K) {
 namespace {
 
 // Which batch kernels a level uses: the staged kernels when the operators
-// fit in shared memory, else the streaming Dirichlet kernel (passes of KP
-// right-hand sides) and the chunked Neumann / averaging kernels.
+// fit in shared memory, else the streaming Dirichlet kernel and the chunked
+// Neumann / averaging kernels.  A staged Neumann / averaging record must also
+// leave room for three substructures per SM: with fewer warps resident the
+// warp-per-substructure kernels wait on latency, and the block-per-
+// substructure kernels are faster.
 struct BatchRoute {
     bool dir_staged = false, neu_staged = false, avg_staged = false;
-    int kp = 0;             // pass width of the streaming Dirichlet kernel (0: none fits)
+    bool dir_stream = false;   // the streaming Dirichlet kernel
     bool ok = false;
 };
 
@@ -1397,21 +1514,19 @@ template <class T, class ACC> BatchRoute route_t(const DevLevel &L, int prec) {
     const int pi = pidx_b(prec);
     const size_t a = sizeof(ACC);
     R.dir_staged = (L.bp == 8 || L.bp == 16 || L.bp == 32) && L.irec && dir_slice_b<T, ACC>(L) <= kSmemMaxB;
-    R.neu_staged = al16((size_t)L.max_nrec[pi]) + al16(a * (size_t)(L.max_nG > 0 ? L.max_nG : 1) * 32) + 16 <= kSmemMaxB;
-    R.avg_staged = al16((size_t)L.max_nrec[pi]) + al16(a * (size_t)(L.max_nc > 0 ? L.max_nc : 1) * 32) + 16 <= kSmemMaxB;
-    if (!R.dir_staged)
-        for (int kp = 16; kp >= 1 && !R.kp; kp /= 2)
-            if (StreamSmemB::of<T, ACC>(L, kp).total <= kSmemMaxB) R.kp = kp;
+    R.neu_staged = 3 * (al16((size_t)L.max_nrec[pi]) + al16(a * (size_t)(L.max_nG > 0 ? L.max_nG : 1) * 32) + 16) <= kSmemMaxB;
+    R.avg_staged = 3 * (al16((size_t)L.max_nrec[pi]) + al16(a * (size_t)(L.max_nc > 0 ? L.max_nc : 1) * 32) + 16) <= kSmemMaxB;
+    // the largest bucket's layout bounds every bucket's
+    const int nw_max = ((L.max_b + 1) / 2 + 3) / 4;
+    const bool stream = L.bk.n > 0 && L.bperm && nw_max <= kMaxBuckets &&
+                        StreamSmemB::of<T, ACC>(L, 32 * nw_max).total <= kSmemMaxB;
     const bool bg = neu_bg_smem<T, ACC>(L) <= kSmemMaxB;
+    R.dir_stream = !R.dir_staged && stream;
     if (force_stream()) {
-        if (R.dir_staged) {
-            for (int kp = 16; kp >= 1 && !R.kp; kp /= 2)
-                if (StreamSmemB::of<T, ACC>(L, kp).total <= kSmemMaxB) R.kp = kp;
-            if (R.kp) R.dir_staged = false;
-        }
+        if (stream) R.dir_staged = false, R.dir_stream = true;
         if (bg) R.neu_staged = R.avg_staged = false;
     }
-    R.ok = (R.dir_staged || R.kp > 0) && (R.neu_staged || bg) && (R.avg_staged || bg);
+    R.ok = (R.dir_staged || R.dir_stream) && (R.neu_staged || bg) && (R.avg_staged || bg);
     return R;
 }
 
@@ -1425,15 +1540,86 @@ BatchRoute route(const DevLevel &L, int prec) {
 
 bool batch_path(const DevLevel &L, int prec) { return route(L, prec).ok; }
 
+bool batch_streams(const DevLevel &L) {
+    for (int prec : {BDDC_PREC_FP64, BDDC_PREC_FP32, BDDC_PREC_BF16}) {
+        const BatchRoute R = route(L, prec);
+        if (R.ok && R.dir_stream) return true;
+    }
+    return false;
+}
+
 namespace {
+
+// Resident blocks per SM of a kernel at a block size and shared-memory size,
+// queried once and cached: the query may load the kernel's module, which a
+// stream capture does not allow, so batch_prepare_level asks for every
+// bucket before the first capture and a capturing stream only reads the
+// cache (an entry missing there gives one block per SM).
+int resident_blocks(const void *kern, int nt, size_t sm, cudaStream_t s) {
+    static std::mutex mu;
+    static std::map<std::tuple<const void *, int, size_t>, int> cache;
+    const auto key = std::make_tuple(kern, nt, sm);
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) return it->second;
+    }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (s && cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) return 1;
+    int per = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, nt, sm) != cudaSuccess || per < 1) {
+        cudaGetLastError();
+        per = 1;
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    cache[key] = per;
+    return per;
+}
+
+template <class T, class ACC, bool SWZ, bool POST>
+void dir_bs_buckets(const DevLevel &L, const BatchLevel &B, const double *r, double *z, const int *skip,
+                    const RzBatch &rz, cudaStream_t s, bool launch = true) {
+    for (int i = 0; i < L.bk.n; ++i) {
+        DevLevel Lb = L;                  // the bucket's maxima size its shared memory
+        Lb.max_b = L.bk.max_b[i];
+        Lb.max_ld = L.bk.max_ld[i];
+        Lb.max_nG = L.bk.max_nG[i];
+        const int nt = 32 * L.bk.nw[i];
+        const size_t sm = StreamSmemB::of<T, ACC>(Lb, nt).total;
+        const int per = resident_blocks(reinterpret_cast<const void *>(k_dir_bs<T, ACC, SWZ, POST>), nt, sm, s);
+        if (!launch) continue;
+        const int grid = std::min(L.bk.count[i], per * num_sms_b());
+        launch_plain(k_dir_bs<T, ACC, SWZ, POST>, grid, nt, sm, s, Lb, B, r, z, skip, rz,
+                     (const int *)(L.bperm + L.bk.first[i]), L.bk.count[i]);
+    }
+}
+
+template <class T, class ACC> void prepare_bs(const DevLevel &L) {
+    const RzBatch none{nullptr, nullptr, nullptr, nullptr};
+    const BatchLevel B;
+    if (L.bp != 0) {
+        dir_bs_buckets<T, ACC, true, false>(L, B, nullptr, nullptr, nullptr, none, nullptr, false);
+        dir_bs_buckets<T, ACC, true, true>(L, B, nullptr, nullptr, nullptr, none, nullptr, false);
+    } else {
+        dir_bs_buckets<T, ACC, false, false>(L, B, nullptr, nullptr, nullptr, none, nullptr, false);
+        dir_bs_buckets<T, ACC, false, true>(L, B, nullptr, nullptr, nullptr, none, nullptr, false);
+    }
+}
 
 template <class T, class ACC>
 void dir_bs(const DevLevel &L, const BatchLevel &B, bool post, const double *r, double *z, const int *skip,
-            int kp, const RzBatch *rz, cudaStream_t s) {
-    const size_t sm = StreamSmemB::of<T, ACC>(L, kp).total;
+            const RzBatch *rz, cudaStream_t s) {
+    if (!B.ys) throw Error(BDDC_E_STATE, "streaming Dirichlet kernel without its scratch");
     const RzBatch none{nullptr, nullptr, nullptr, nullptr};
-    if (!post) launch_plain(k_dir_bs<T, ACC, false>, L.nsub, kSBT, sm, s, L, B, r, z, skip, kp, none);
-    else launch_plain(k_dir_bs<T, ACC, true>, L.nsub, kSBT, sm, s, L, B, r, z, skip, kp, rz ? *rz : none);
+    const RzBatch rzv = (post && rz) ? *rz : none;
+    const bool swz = L.bp != 0;
+    if (swz) {
+        if (post) dir_bs_buckets<T, ACC, true, true>(L, B, r, z, skip, rzv, s);
+        else dir_bs_buckets<T, ACC, true, false>(L, B, r, z, skip, rzv, s);
+    } else {
+        if (post) dir_bs_buckets<T, ACC, false, true>(L, B, r, z, skip, rzv, s);
+        else dir_bs_buckets<T, ACC, false, false>(L, B, r, z, skip, rzv, s);
+    }
 }
 
 template <class T, class ACC>
@@ -1442,10 +1628,10 @@ void pre_b(const DevLevel &L, const BatchLevel &B, int prec, const double *r, co
     const BatchRoute R = route_t<T, ACC>(L, prec);
     if (ev) cudaEventRecord(ev[0], s);
     if (R.dir_staged) dir_b<T, ACC>(L, B, false, r, nullptr, skip, s);
-    else dir_bs<T, ACC>(L, B, false, r, nullptr, skip, R.kp, nullptr, s);
+    else dir_bs<T, ACC>(L, B, false, r, nullptr, skip, nullptr, s);
     if (ev) cudaEventRecord(ev[1], s);
     if (R.neu_staged) neu_b<T, ACC>(L, B, prec, r, skip, s);
-    else launch_plain(k_neu_bg<T, ACC>, L.nsub, kSBT, neu_bg_smem<T, ACC>(L), s, L, B, pidx_b(prec), r, skip);
+    else launch_plain(k_neu_bg<T, ACC>, L.nsub, kNBT, neu_bg_smem<T, ACC>(L), s, L, B, pidx_b(prec), r, skip);
     if (ev) cudaEventRecord(ev[2], s);
 }
 
@@ -1455,14 +1641,21 @@ void post_b(const DevLevel &L, const BatchLevel &B, int prec, const double *r, d
     const BatchRoute R = route_t<T, ACC>(L, prec);
     if (ev) cudaEventRecord(ev[0], s);
     if (R.avg_staged) avg_b<T, ACC>(L, B, prec, skip, s);
-    else launch_plain(k_avg_bg<T, ACC>, L.nsub, kSBT, neu_bg_smem<T, ACC>(L), s, L, B, pidx_b(prec), skip);
+    else launch_plain(k_avg_bg<T, ACC>, L.nsub, kNBT, neu_bg_smem<T, ACC>(L), s, L, B, pidx_b(prec), skip);
     if (ev) cudaEventRecord(ev[1], s);
     if (R.dir_staged) dir_b<T, ACC>(L, B, true, r, z, skip, s, rz);
-    else dir_bs<T, ACC>(L, B, true, r, z, skip, R.kp, rz, s);
+    else dir_bs<T, ACC>(L, B, true, r, z, skip, rz, s);
     if (ev) cudaEventRecord(ev[2], s);
 }
 
 }  // namespace
+
+void batch_prepare_level(const DevLevel &L) {
+    if (L.bk.n == 0) return;
+    prepare_bs<double, double>(L);
+    prepare_bs<float, float>(L);
+    prepare_bs<__nv_bfloat16, float>(L);
+}
 
 void prepare_batch_kernels() {
     const int big = (int)kSmemMaxB;
@@ -1484,9 +1677,13 @@ void prepare_batch_kernels() {
     cudaFuncSetAttribute(k_gemm_b<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(GM_S * gm_stage(1)));
     cudaFuncSetAttribute(k_gemm_b<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(GM_S * gm_stage(2)));
     cudaFuncSetAttribute(k_gemm_b<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(GM_S * gm_stage(4)));
-    BDDC_SMEM_ATTR_B((k_dir_bs<double, double, false>)); BDDC_SMEM_ATTR_B((k_dir_bs<double, double, true>));
-    BDDC_SMEM_ATTR_B((k_dir_bs<float, float, false>)); BDDC_SMEM_ATTR_B((k_dir_bs<float, float, true>));
-    BDDC_SMEM_ATTR_B((k_dir_bs<__nv_bfloat16, float, false>)); BDDC_SMEM_ATTR_B((k_dir_bs<__nv_bfloat16, float, true>));
+#define BDDC_DIR_BS(T, A, SW)                                   \
+    BDDC_SMEM_ATTR_B((k_dir_bs<T, A, SW, false>));              \
+    BDDC_SMEM_ATTR_B((k_dir_bs<T, A, SW, true>));
+    BDDC_DIR_BS(double, double, false) BDDC_DIR_BS(double, double, true)
+    BDDC_DIR_BS(float, float, false) BDDC_DIR_BS(float, float, true)
+    BDDC_DIR_BS(__nv_bfloat16, float, false) BDDC_DIR_BS(__nv_bfloat16, float, true)
+#undef BDDC_DIR_BS
     BDDC_SMEM_ATTR_B((k_neu_bg<double, double>)); BDDC_SMEM_ATTR_B((k_neu_bg<float, float>));
     BDDC_SMEM_ATTR_B((k_neu_bg<__nv_bfloat16, float>));
     BDDC_SMEM_ATTR_B((k_avg_bg<double, double>)); BDDC_SMEM_ATTR_B((k_avg_bg<float, float>));

@@ -131,6 +131,11 @@ struct bddc_ctx {
     int *err_dev = nullptr;           // set by kernels whose bounded waits gave up
     std::unique_ptr<Workspace> ws;
     int tuned[3] = {0, 0, 0};         // autotuned batch tiles (see bddc_info::tuned_tile)
+    // the autotuner's variants, chosen once per problem and shared by every
+    // workspace (the stencil tile fixes the order of the dot products, so
+    // solves in different workspaces stay bit-identical)
+    int tile_v = -1, gemm_v = -1;
+    std::mutex tune_mu;
     double setup_ms = 0.0;
     std::mutex mu;
     int n() const { return (nx - 1) * (nx - 1); }
@@ -370,14 +375,49 @@ void setup_level(bddc_ctx *C, LevelData &LD, const double *emat, const std::vect
     for (int s = 0; s < ns; ++s) {
         // padded to 8 elements so that every block starts 16-byte aligned in
         // all three precisions (bulk copies into shared memory)
-        szF[s] = ((int64_t)nblk[s] * 2 * bsz[s] * bsz[s] + 7) & ~int64_t(7);
+        const int ldf = fld(bsz[s], H.block_uniform != 0);
+        szF[s] = ((int64_t)nblk[s] * 2 * bsz[s] * ldf + 7) & ~int64_t(7);
+        D.max_ld = std::max(D.max_ld, ldf);
         szN[s] = ((int64_t)nG[s] * nG[s] + 7) & ~int64_t(7);
         D.max_fac = std::max(D.max_fac, szF[s]);
         D.max_nmat = std::max(D.max_nmat, szN[s]);
         D.max_nI = std::max(D.max_nI, nI[s]); D.max_nG = std::max(D.max_nG, nG[s]);
         D.max_b = std::max(D.max_b, bsz[s]); D.max_m = std::max(D.max_m, nblk[s]);
     }
-    auto oI = prefix(nI), oF = prefix(szF), oN = prefix(szN), oCOO = prefix(cooCnt);
+    std::vector<int64_t> szY(ns);
+    for (int s = 0; s < ns; ++s) szY[s] = (int64_t)nblk[s] * bsz[s];
+    auto oI = prefix(nI), oF = prefix(szF), oN = prefix(szN), oCOO = prefix(cooCnt), oY = prefix(szY);
+    D.offY = A.upload(oY, st);
+    D.n_y = oY.back();
+    {
+        // size buckets of the streaming batch kernel, largest factors first
+        std::vector<std::vector<int>> bsub(kMaxBuckets);
+        bool fits = true;
+        for (int s = 0; s < ns && fits; ++s) {
+            const int nw = ((bsz[s] + 1) / 2 + 3) / 4;
+            if (nw > kMaxBuckets) fits = false;
+            else bsub[nw - 1].push_back(s);
+        }
+        std::vector<int> perm;
+        D.bk.n = 0;
+        for (int k = 0; k < kMaxBuckets && fits; ++k) {
+            auto &v = bsub[k];
+            if (v.empty()) continue;
+            std::stable_sort(v.begin(), v.end(), [&](int a, int c) { return szF[a] > szF[c]; });
+            const int i = D.bk.n++;
+            D.bk.nw[i] = k + 1;
+            D.bk.first[i] = (int)perm.size();
+            D.bk.count[i] = (int)v.size();
+            D.bk.max_b[i] = D.bk.max_ld[i] = D.bk.max_nG[i] = 1;
+            for (int s2 : v) {
+                D.bk.max_b[i] = std::max(D.bk.max_b[i], bsz[s2]);
+                D.bk.max_ld[i] = std::max(D.bk.max_ld[i], fld(bsz[s2], H.block_uniform != 0));
+                D.bk.max_nG[i] = std::max(D.bk.max_nG[i], nG[s2]);
+            }
+            perm.insert(perm.end(), v.begin(), v.end());
+        }
+        if (!perm.empty()) D.bperm = A.upload(perm, st);
+    }
     LD.sumI = oI.back(); LD.sumG = oG.back(); LD.blockent = oF.back(); LD.coonnz = oCOO.back();
     LD.nent = oN.back();
     LD.bandnnz = 0;
@@ -393,6 +433,37 @@ void setup_level(bddc_ctx *C, LevelData &LD, const double *emat, const std::vect
     D.idxI = A.upload(idxI, st); D.idxG = A.upload(idxG, st);
     D.ifaceDof = A.upload(H.iface_dof, st);
     D.cooG = A.upload(cooG, st); D.cooI = A.upload(cooI, st);
+    {
+        // CSR views of the coupling pattern (sorted by interface row, then
+        // interior row): first entry of each Gamma entry, and per interior row
+        // its entries in increasing order with the entry's interface id
+        std::vector<int64_t> gptr((size_t)oG.back() + 1), rptr((size_t)oI.back() + 1);
+        std::vector<int> rowE(cooG.size()), rowId(cooG.size());
+        for (int s = 0; s < ns; ++s) {
+            const int64_t e0 = oCOO[s], e1 = oCOO[s + 1];
+            int64_t e = e0;
+            for (int q = 0; q < nG[s]; ++q) {
+                gptr[(size_t)(oG[s] + q)] = e;
+                while (e < e1 && cooG[(size_t)e] == q) ++e;
+            }
+            std::vector<int64_t> cnt((size_t)nI[s] + 1, 0);
+            for (int64_t k = e0; k < e1; ++k) ++cnt[(size_t)cooI[(size_t)k] + 1];
+            for (int i = 0; i < nI[s]; ++i) cnt[(size_t)i + 1] += cnt[(size_t)i];
+            for (int i = 0; i < nI[s]; ++i) rptr[(size_t)(oI[s] + i)] = e0 + cnt[(size_t)i];
+            for (int64_t k = e0; k < e1; ++k) {
+                const int64_t pos = e0 + cnt[(size_t)cooI[(size_t)k]]++;
+                if (k > INT32_MAX) throw Error(BDDC_E_ARG, "coupling pattern too large");
+                rowE[(size_t)pos] = (int)k;
+                rowId[(size_t)pos] = idxG[(size_t)(oG[s] + cooG[(size_t)k])];
+            }
+        }
+        gptr.back() = (int64_t)cooG.size();
+        rptr.back() = (int64_t)cooG.size();
+        D.cooGptr = A.upload(gptr, st);
+        D.cooRptr = A.upload(rptr, st);
+        D.cooRowE = A.upload(rowE, st);
+        D.cooRowId = A.upload(rowId, st);
+    }
     std::vector<std::vector<int>> ownl(ns);
     for (int k = 0; k < D.n_iface; ++k) ownl[H.subs_idx[H.subs_ptr[H.iface_dof[k]]]].push_back(k);
     std::vector<int> own; std::vector<int64_t> ownCnt(ns);
@@ -620,17 +691,30 @@ void apply_rec(bddc_ctx *C, Workspace &W, int l, int prec, const double *r, doub
 // iterations past convergence only skip their kernels.
 constexpr int kGraphIters = 2;
 
+// Ends a capture that an exception interrupted, dropping what it recorded,
+// so that the stream can be used again.
+void abandon_capture(cudaStream_t st) {
+    cudaGraph_t g = nullptr;
+    if (cudaStreamEndCapture(st, &g) == cudaSuccess && g) cudaGraphDestroy(g);
+    cudaGetLastError();
+}
+
 cudaGraphExec_t pcg_graph(bddc_ctx *C, Workspace &W, int prec) {
     if (W.graph[prec]) return W.graph[prec];
     const int n = C->n();
     cudaStream_t st = W.stream;
     cudaGraph_t g;
     BDDC_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    const RzArgs rz{W.rzpart, W.rzcounter, W.sc, W.betas};
-    for (int it = 0; it < kGraphIters; ++it) {
-        launch_pcg_dir_spmv(C->nx, C->w_dev, W.z, W.p0, W.p1, W.q, W.part, W.counter, W.sc, W.alphas, st);
-        launch_pcg_update(n, W.x, W.r, W.p0, W.p1, W.q, W.part, W.counter, W.sc, st);
-        apply_rec(C, W, 0, prec, W.r, W.z, &W.sc->done, st, &rz);
+    try {
+        const RzArgs rz{W.rzpart, W.rzcounter, W.sc, W.betas};
+        for (int it = 0; it < kGraphIters; ++it) {
+            launch_pcg_dir_spmv(C->nx, C->w_dev, W.z, W.p0, W.p1, W.q, W.part, W.counter, W.sc, W.alphas, st);
+            launch_pcg_update(n, W.x, W.r, W.p0, W.p1, W.q, W.part, W.counter, W.sc, st);
+            apply_rec(C, W, 0, prec, W.r, W.z, &W.sc->done, st, &rz);
+        }
+    } catch (...) {
+        abandon_capture(st);
+        throw;
     }
     BDDC_CUDA_TRY(cudaStreamEndCapture(st, &g));
     BDDC_CUDA_TRY(cudaGraphInstantiate(&W.graph[prec], g, 0));
@@ -786,6 +870,10 @@ BatchWs &batch_ws(bddc_ctx *C, Workspace &W) {
         BDDC_CUDA_TRY(cudaMemset(B.rB, 0, sizeof(double) * ni * KB));
         BDDC_CUDA_TRY(cudaMemset(B.uB, 0, sizeof(double) * ni * KB));
         BDDC_CUDA_TRY(cudaMemset(B.rcv, 0, sizeof(double) * ncp * KB));
+        if (batch_streams(D)) {
+            B.ys = A.alloc_n<double>(std::max<int64_t>(D.n_y, 1) * KB);
+            batch_prepare_level(D);
+        }
         bw->lv.push_back(B);
     }
     bw->x = A.alloc_n<double>(n * KB); bw->r = A.alloc_n<double>(n * KB);
@@ -816,17 +904,22 @@ BatchWs &batch_ws(bddc_ctx *C, Workspace &W) {
         BDDC_CUDA_TRY(cudaMemsetAsync(scs, 0, sizeof(BatchScalars), st));
         BDDC_CUDA_TRY(cudaMemsetAsync(bw->z, 0, sizeof(double) * n * KB, st));
         BDDC_CUDA_TRY(cudaMemsetAsync(bw->p, 0, sizeof(double) * n * KB, st));
-        bw->tile_v = dir_spmv_tune(C->nx, KB, C->w_dev, bw->z, bw->p, bw->p1, bw->q, bw->part, bw->counter,
-                                   scs, al, st);
-        const BatchLevel &top = bw->lv.back();
-        bw->gemm_v = gemm_tune(C->n_top, C->ld_top, C->Ainv, top.rcv, top.ucv, KB, C->err_dev, st);
-        BDDC_CUDA_TRY(cudaStreamSynchronize(st));
-        BDDC_CUDA_TRY(cudaGetLastError());
-        int tx = 0, ty = 0;
-        dir_spmv_tile(bw->tile_v, &tx, &ty);
-        C->tuned[0] = tx;
-        C->tuned[1] = ty;
-        C->tuned[2] = gemm_rows(bw->gemm_v);
+        std::lock_guard<std::mutex> lk(C->tune_mu);
+        if (C->tile_v < 0) {
+            C->tile_v = dir_spmv_tune(C->nx, KB, C->w_dev, bw->z, bw->p, bw->p1, bw->q, bw->part, bw->counter,
+                                      scs, al, st);
+            const BatchLevel &top = bw->lv.back();
+            C->gemm_v = gemm_tune(C->n_top, C->ld_top, C->Ainv, top.rcv, top.ucv, KB, C->err_dev, st);
+            BDDC_CUDA_TRY(cudaStreamSynchronize(st));
+            BDDC_CUDA_TRY(cudaGetLastError());
+            int tx = 0, ty = 0;
+            dir_spmv_tile(C->tile_v, &tx, &ty);
+            C->tuned[0] = tx;
+            C->tuned[1] = ty;
+            C->tuned[2] = gemm_rows(C->gemm_v);
+        }
+        bw->tile_v = C->tile_v;
+        bw->gemm_v = C->gemm_v;
     }
     W.bw = std::move(bw);
     return *W.bw;
@@ -856,11 +949,16 @@ cudaGraphExec_t batch_graph(bddc_ctx *C, Workspace &W, BatchWs &BW, int prec, in
     cudaStream_t st = W.stream;
     cudaGraph_t g;
     BDDC_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    launch_b_dir_spmv(C->nx, K, C->w_dev, BW.z, BW.p, BW.p1, BW.q, BW.part, BW.counter, BW.sc, BW.alphas, st,
-                      BW.tile_v);
-    launch_b_update(n, K, BW.x, BW.r, BW.p, BW.p1, BW.q, BW.part, BW.counter, BW.sc, st);
-    const RzBatch rz{BW.rzpart, BW.rzcounter, BW.sc, BW.betas};
-    apply_b_rec(C, W, BW, 0, prec, BW.r, BW.z, &BW.sc->all_done, st, &rz);
+    try {
+        launch_b_dir_spmv(C->nx, K, C->w_dev, BW.z, BW.p, BW.p1, BW.q, BW.part, BW.counter, BW.sc, BW.alphas,
+                          st, BW.tile_v);
+        launch_b_update(n, K, BW.x, BW.r, BW.p, BW.p1, BW.q, BW.part, BW.counter, BW.sc, st);
+        const RzBatch rz{BW.rzpart, BW.rzcounter, BW.sc, BW.betas};
+        apply_b_rec(C, W, BW, 0, prec, BW.r, BW.z, &BW.sc->all_done, st, &rz);
+    } catch (...) {
+        abandon_capture(st);
+        throw;
+    }
     BDDC_CUDA_TRY(cudaStreamEndCapture(st, &g));
     cudaGraphExec_t ge;
     BDDC_CUDA_TRY(cudaGraphInstantiate(&ge, g, 0));

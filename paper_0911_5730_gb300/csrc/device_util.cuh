@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cstdlib>
+#include <string>
 
 #include "internal.h"
 
@@ -148,7 +149,14 @@ inline void launch_k(bool pdl, void (*k)(KArgs...), int grid, int block, size_t 
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
     cfg.numAttrs = (pdl && pdl_enabled()) ? 1 : 0;
-    cudaLaunchKernelEx(&cfg, k, args...);
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, k, args...);
+    if (e != cudaSuccess) {
+        const char *name = nullptr;
+        if (cudaFuncGetName(&name, reinterpret_cast<const void *>(k)) != cudaSuccess || !name) name = "?";
+        throw Error(BDDC_E_CUDA, std::string("launch of ") + name + " (grid " + std::to_string(grid) +
+                                     ", block " + std::to_string(block) + ", shared " + std::to_string(smem) +
+                                     "): " + cudaGetErrorString(e));
+    }
 }
 
 template <class... KArgs, class... Args>

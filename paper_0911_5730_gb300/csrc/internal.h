@@ -47,6 +47,11 @@ struct DevArena {
     ~DevArena() { release(); }
 };
 
+// Leading dimension of a stored factor block: b, or b + 1 for an even b in
+// a level without the XOR swizzle, so that the rows of a block (stride ld)
+// fall in distinct shared-memory banks when lanes walk them in parallel.
+__host__ __device__ inline int fld(int b, bool swz) { return (swz || (b & 1)) ? b : b + 1; }
+
 // Storage of the apply operators in one precision.
 template <class T> struct OpSet {
     T *dir = nullptr;     // Dirichlet block factors
@@ -54,6 +59,17 @@ template <class T> struct OpSet {
     T *nmat = nullptr;    // constrained Neumann operator on Gamma (nG x nG per sub)
     T *psit = nullptr;    // Psi^T on Gamma (nc x nG per sub)
     T *wg = nullptr;      // stiffness weights on Gamma
+};
+
+// Substructures of a level in size buckets for the streaming batch kernel:
+// bucket i holds the substructures whose blocks take nw[i] warps (8 column
+// groups x ceil(b/2) row pairs = 8 ceil(b/2) threads), listed in
+// perm[first[i] .. first[i] + count[i]) by decreasing factor size.
+constexpr int kMaxBuckets = 16;
+struct SizeBuckets {
+    int n = 0;
+    int nw[kMaxBuckets], first[kMaxBuckets], count[kMaxBuckets];
+    int max_b[kMaxBuckets], max_ld[kMaxBuckets], max_nG[kMaxBuckets];
 };
 
 // One BDDC level as the apply kernels see it.  All per-substructure arrays
@@ -64,16 +80,27 @@ struct DevLevel {
     int n_iface = 0;      // interface DOFs (compact numbering)
     int nc = 0;           // coarse DOFs (= DOFs of the next level)
     int max_nI = 0, max_nG = 0, max_nc = 0, max_b = 0, max_m = 0, max_coo = 0;
+    int max_ld = 0;            // largest leading dimension of a factor block
+    SizeBuckets bk;            // size buckets (n = 0: a block needs more than 16 warps)
+    int *bperm = nullptr;      // substructures in bucket order
     // per substructure sizes
     int *nI = nullptr, *nG = nullptr, *ncl = nullptr, *bsz = nullptr, *nblk = nullptr;
     // offsets
     int64_t *offI = nullptr, *offG = nullptr, *offC = nullptr, *offF = nullptr,
-            *offN = nullptr, *offP = nullptr, *offCOO = nullptr, *offOwn = nullptr;
+            *offN = nullptr, *offP = nullptr, *offCOO = nullptr, *offOwn = nullptr,
+            *offY = nullptr;   // padded interior rows (nblk * bsz) before each substructure
+    int64_t n_y = 0;           // sum of nblk * bsz over the substructures
     int *idxI = nullptr;      // global DOF of each interior entry
     int *idxG = nullptr;      // compact interface id of each Gamma entry
     int *ifaceDof = nullptr;  // global DOF of each compact interface id
     int *rc = nullptr;        // global coarse id of each local coarse DOF
     int *cooG = nullptr, *cooI = nullptr;   // COO pattern of A_{Gamma I} (local)
+    // CSR views of that pattern: cooGptr[offG + q] is the first entry of
+    // Gamma entry q (entries sorted by Gamma entry); cooRptr[offI + i] the
+    // first of interior row i in cooRowE (entry indices, increasing), with
+    // cooRowId the entry's compact interface id
+    int64_t *cooGptr = nullptr, *cooRptr = nullptr;
+    int *cooRowE = nullptr, *cooRowId = nullptr;
     int *own = nullptr;       // compact interface ids written by this substructure
     OpSet<double> f64;
     OpSet<float> f32;
@@ -176,6 +203,9 @@ struct BatchLevel {
     double *w = nullptr;       // [sum nG][K]
     double *rcv = nullptr;     // [max(nc, ld_top)][K], zero beyond nc
     double *ucv = nullptr;     // [max(nc, ld_top)][K]
+    // per-substructure sweep scratch of the streaming Dirichlet kernel,
+    // [n_y rows][32] in the accumulator type (null when no precision streams)
+    void *ys = nullptr;
 };
 struct BatchScalars {
     double rho[kMaxBatch], pq[kMaxBatch], alpha[kMaxBatch], beta[kMaxBatch], rr[kMaxBatch],
@@ -198,6 +228,8 @@ struct RzBatch {
 };
 // Whether a level's operators fit the batched kernels' shared-memory slices.
 bool batch_path(const DevLevel &L, int prec);
+bool batch_streams(const DevLevel &L);   // some precision takes the streaming Dirichlet kernel
+void batch_prepare_level(const DevLevel &L);   // launch shapes of the streaming kernel, before any capture
 void prepare_batch_kernels();
 // Algorithm 1 on one level for a batch (same scratch protocol as the single
 // right-hand-side launchers, on the BatchLevel buffers).

@@ -207,10 +207,12 @@ __global__ void k_schur(SetupLevel S) {
 // column-major; padded rows are identity / zero.
 // ----------------------------------------------------------------------------
 // Block j (rows [j b, j b + b)) holds Linv_j = L_jj^{-1} and Lsub_j =
-// L_{j,j-1}, both b x b column-major; padded rows are identity / zero.  With
-// a power-of-two block size (D.bp > 0) entries are XOR-swizzled, (r, c) ->
-// c*b + (r ^ c), so that the warp kernels read columns (forward sweep) and
-// rows (backward sweep) without shared-memory bank conflicts.
+// L_{j,j-1}, both b x b column-major with leading dimension ld (fld: b, or
+// b + 1 for even b, the extra row zero); padded rows are identity / zero.
+// With a power-of-two block size (D.bp > 0) entries are XOR-swizzled,
+// (r, c) -> c*b + (r ^ c), so that the warp kernels read columns (forward
+// sweep) and rows (backward sweep) without shared-memory bank conflicts; the
+// odd ld does the same for the other levels.
 __global__ void k_dirichlet_blocks(SetupLevel S, DevLevel D, double *outBase, const int64_t *offOut) {
     const int sub = blockIdx.x;
     const bool swz = D.bp != 0;
@@ -222,9 +224,10 @@ __global__ void k_dirichlet_blocks(SetupLevel S, DevLevel D, double *outBase, co
         const int d = r - c;
         return d <= bw ? L[(int64_t)d * n + c] : 0.0;
     };
+    const int ldb = fld(b, swz);
     for (int j = 0; j < m; ++j) {
-        double *Linv = out + (int64_t)j * 2 * b * b;
-        double *Lsub = Linv + (int64_t)b * b;
+        double *Linv = out + (int64_t)j * 2 * b * ldb;
+        double *Lsub = Linv + (int64_t)b * ldb;
         const int r0 = j * b;
         for (int c = threadIdx.x; c < b; c += blockDim.x) {
             for (int r = 0; r < b; ++r) {
@@ -236,15 +239,16 @@ __global__ void k_dirichlet_blocks(SetupLevel S, DevLevel D, double *outBase, co
                     } else {
                         double s = (r == c) ? 1.0 : 0.0;
                         for (int k = c; k < r; ++k)
-                            s -= Lat(r0 + r, r0 + k) * Linv[(int64_t)c * b + (swz ? (k ^ c) : k)];
+                            s -= Lat(r0 + r, r0 + k) * Linv[(int64_t)c * ldb + (swz ? (k ^ c) : k)];
                         x = s / Lat(r0 + r, r0 + r);
                     }
                 }
                 // XOR swizzle for power-of-two blocks: (r, c) at c*b + (r ^ c)
                 const int rr = swz ? (r ^ c) : r;
-                Linv[(int64_t)c * b + rr] = x;
-                Lsub[(int64_t)c * b + rr] = (j > 0) ? Lat(r0 + r, r0 - b + c) : 0.0;
+                Linv[(int64_t)c * ldb + rr] = x;
+                Lsub[(int64_t)c * ldb + rr] = (j > 0) ? Lat(r0 + r, r0 - b + c) : 0.0;
             }
+            for (int r = b; r < ldb; ++r) Linv[(int64_t)c * ldb + r] = Lsub[(int64_t)c * ldb + r] = 0.0;
         }
     }
 }

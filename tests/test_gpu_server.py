@@ -72,36 +72,61 @@ def test_budget_and_timeout(lib):
 def test_continuous_batching_waves(lib):
     """Requests arrive in waves while earlier ones iterate: more right-hand
     sides than the 32 slots, with different tolerances, on a problem served by
-    continuous batching (batch_width 32) beside one that needs the generic
-    kernels (served by the worker threads).  Every result equals the solo
-    solve: same iteration count, FP64 solution within 1e-10."""
+    continuous batching with the staged batch kernels, one served by the
+    streaming batch kernels (irregular cells of about 1000 DOFs), both with
+    batch_width 32, and one whose FP64 blocks (b about 74) exceed the
+    streaming kernel's shared memory, served by the worker threads.  Every
+    result matches the solo solve by the same kernels (for the streaming
+    problem a two-column batch of the request and a zero column, for the
+    others the solve of the request alone): both meet their tolerance on the
+    true residual, and the FP64 solutions agree within 1e-10.  The lanes of a
+    batch are its columns, so the order of a column's dot products depends on
+    the batch width and the last bits of a solve on what it was batched with;
+    where that moves the stopping test across its threshold by one iteration
+    the two solutions are two converged solves one step apart, and agree
+    within 100 x rtol."""
     import time
-    batch_wl = inputs.two_level_channels(nx=64, sub=16)
-    generic_wl = inputs.three_level_voronoi(nx=128, cells=4, group=2, levels=2)
-    Pb = lib.Problem.from_workload(batch_wl)
+    staged_wl = inputs.two_level_channels(nx=64, sub=16)
+    stream_wl = inputs.three_level_voronoi(nx=128, cells=4, group=2, levels=2)
+    generic_wl = inputs.three_level_voronoi(nx=160, cells=2, group=1, levels=2)
+    Ps = lib.Problem.from_workload(staged_wl)
+    Pt = lib.Problem.from_workload(stream_wl)
     Pg = lib.Problem.from_workload(generic_wl)
-    srv = lib.Server(hbm_budget=0, max_slots=2)
+    width = {id(Ps): 32, id(Pt): 32, id(Pg): 1}
+    srv = lib.Server(hbm_budget=0, max_slots=3)
     rng = np.random.default_rng(11)
     sent = []
     for wave in range(4):
         for r in range(12):
             rtol = 1e-8 if r % 3 else 1e-10
-            b = rng.standard_normal(batch_wl.n_dof)
-            sent.append((Pb, b, rtol, srv.submit(Pb, b, rtol=rtol)))
+            for P, wl in ((Ps, staged_wl), (Pt, stream_wl)) if r % 2 else ((Ps, staged_wl),):
+                b = rng.standard_normal(wl.n_dof)
+                sent.append((P, b, rtol, srv.submit(P, b, rtol=rtol)))
         b = rng.standard_normal(generic_wl.n_dof)
         sent.append((Pg, b, 1e-8, srv.submit(Pg, b, rtol=1e-8)))
         time.sleep(0.002)
     for P, b, rtol, t in sent:
         x, infos, lat = srv.wait(t)
         assert lat > 0 and infos[0]["status"] == 0
-        assert infos[0]["batch_width"] == (32 if P is Pb else 1)
-        xs, info = P.solve(torch.tensor(b, device="cuda"), rtol=rtol)
-        assert infos[0]["iters"] == info[0]["iters"]
+        assert infos[0]["batch_width"] == width[id(P)]
+        if P is Pt:
+            pair = np.zeros((2, b.size))
+            pair[0] = b
+            xs, info = P.solve(torch.tensor(pair, device="cuda"), rtol=rtol)
+            assert info[0]["batch_width"] == 2
+            xs = xs[0]
+        else:
+            xs, info = P.solve(torch.tensor(b, device="cuda"), rtol=rtol)
+        name = "staged" if P is Ps else ("stream" if P is Pt else "generic")
+        d_it = abs(infos[0]["iters"] - info[0]["iters"])
+        assert d_it <= 1, (name, rtol, infos[0], info[0])
         xs = xs.cpu().numpy()
-        assert np.linalg.norm(x - xs) <= 1e-10 * np.linalg.norm(xs)
-        assert infos[0]["relres_true"] <= rtol
+        tol = 1e-10 if d_it == 0 else 100 * rtol
+        assert np.linalg.norm(x - xs) <= tol * np.linalg.norm(xs), (name, rtol, d_it)
+        assert infos[0]["relres_true"] <= rtol and info[0]["relres_true"] <= rtol
     srv.close()
-    Pb.close()
+    Ps.close()
+    Pt.close()
     Pg.close()
 
 
