@@ -313,8 +313,10 @@ const char *bddc_last_error(void);
  * one or more right-hand sides) are admitted while their device memory fits
  * the HBM budget and a slot is free; admitted requests run concurrently on
  * separate streams, so work of requests that arrive while others run
- * overlaps on the device.  Each right-hand side is an independent PCG solve,
- * so its result does not depend on what else is in flight.
+ * overlaps on the device.  Each right-hand side is an independent PCG solve;
+ * what else is in flight changes its result only through rounding (the
+ * order of its dot products follows the batch width, and FP64 atomics at
+ * DOFs shared by three or more substructures add in scheduling order).
  * ------------------------------------------------------------------------- */
 
 /* bddc_server_create - hbm_budget in bytes for request buffers (0 = unlimited).
@@ -322,7 +324,7 @@ const char *bddc_last_error(void);
  * batching: one lockstep batch of 32 right-hand-side slots per problem;
  * queued right-hand sides (of any request) enter slots as others finish,
  * between PCG iterations, and each keeps its own PCG state, tolerance and
- * iteration limit, so its result does not depend on the mix.  Other
+ * iteration limit.  Other
  * problems are served by max_slots (>= 1) worker threads, one right-hand
  * side at a time each. */
 int bddc_server_create(size_t hbm_budget, int max_slots, bddc_server **out);
