@@ -179,6 +179,31 @@ int bddc_pcg_solve(bddc_ctx *ctx, const double *b_dev, double *x_dev, int nrhs, 
                    double rtol, int maxit, bddc_solve_info *info_host, void *stream);
 
 /*
+ * bddc_pcg_solve_reduced - A x = b with level 1 reduced to its interface, as
+ * the closing remark of Sec. 4 suggests in place of the interior pre- and
+ * post-corrections of eqs. (4)-(5) and (10)-(11): PCG on the Schur complement
+ * S = A_GG - A_GI A_II^{-1} A_IG (G: the DOFs in two or more level-1
+ * substructures, I: the others) for g = b_G - A_GI A_II^{-1} b_I, with the
+ * preconditioner of eqs. (6)-(9) (substructure correction, coarse correction
+ * of levels 2.. as in bddc_apply, averaging) applied to the interface
+ * residual; then x_I = A_II^{-1} (b_I - A_IG x_G).  One interior solve per
+ * iteration (inside S) instead of two.
+ *   b_dev, x_dev : DEVICE [n], one right-hand side.
+ *   S is applied in FP64 whatever bddc_set_precision chose; the
+ *   preconditioner in the chosen precision.
+ *   The stopping test is ||g - S x_G|| <= rtol ||b||, the full system's
+ *   relative residual once the interior is reconstructed; it is confirmed
+ *   with the true residual b - A x (a restart with a fresh direction if the
+ *   recursion drifted), reported in info_host->relres_true.
+ *   info_host : iterations, residuals and the Lanczos condition number of the
+ *   preconditioned reduced operator (kernel_launches counts graph launches).
+ * Returns BDDC_E_NOCONV at maxit (x holds the reconstructed last iterate).
+ * Synchronises `stream` before returning.
+ */
+int bddc_pcg_solve_reduced(bddc_ctx *ctx, const double *b_dev, double *x_dev, double rtol, int maxit,
+                           bddc_solve_info *info_host, void *stream);
+
+/*
  * bddc_pcg_solve_host - same as bddc_pcg_solve with HOST arrays b_host and
  * x_host ([nrhs][ld]); the host<->device copies are part of the call.
  */

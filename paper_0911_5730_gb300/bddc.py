@@ -22,7 +22,7 @@ ERRORS = {-1: "BDDC_E_ARG", -2: "BDDC_E_NOMEM", -3: "BDDC_E_NOT_SPD", -4: "BDDC_
 CONSTRAINTS = {"corners": 0, "corners+edges": 1, "adaptive": 2, "all": 3}
 PRECISION = {"fp64": 0, "fp32": 1, "bf16": 2}
 
-SYMBOLS = ["bddc_setup", "bddc_apply", "bddc_pcg_solve", "bddc_pcg_solve_host",
+SYMBOLS = ["bddc_setup", "bddc_apply", "bddc_pcg_solve", "bddc_pcg_solve_host", "bddc_pcg_solve_reduced",
            "bddc_set_precision", "bddc_query", "bddc_operator", "bddc_destroy",
            "bddc_last_error", "bddc_server_create", "bddc_submit", "bddc_wait",
            "bddc_server_destroy", "bddc_profile_apply", "bddc_apply_noalloc", "bddc_inspect",
@@ -83,6 +83,7 @@ def load():
     lib.bddc_apply.argtypes = [vp, vp, vp, i32, i64, vp]
     lib.bddc_pcg_solve.argtypes = [vp, vp, vp, i32, i64, dp, i32, vp, vp]
     lib.bddc_pcg_solve_host.argtypes = [vp, vp, vp, i32, i64, dp, i32, vp, vp]
+    lib.bddc_pcg_solve_reduced.argtypes = [vp, vp, vp, dp, i32, vp, vp]
     lib.bddc_set_precision.argtypes = [vp, i32]
     lib.bddc_query.argtypes = [vp, C.POINTER(Info), i32, vp, vp, i32, vp]
     lib.bddc_operator.argtypes = [vp, vp, vp, vp]
@@ -239,6 +240,21 @@ class Problem:
         if check and code not in (BDDC_OK, -4):
             _check(code)
         return x, [i.as_dict() for i in infos]
+
+    def solve_reduced(self, b, x=None, rtol=1e-8, maxit=1000, stream=None, check=True):
+        """PCG on the level-1 interface (one right-hand side, device tensor);
+        returns (x, info dict)."""
+        import torch
+        b = b.contiguous()
+        if x is None:
+            x = torch.empty_like(b)
+        info = SolveInfo()
+        code = self._lib.bddc_pcg_solve_reduced(self.h, _ptr(b), _ptr(x), float(rtol), int(maxit),
+                                                C.cast(C.pointer(info), C.c_void_p),
+                                                C.c_void_p(_stream_ptr(stream)))
+        if check and code not in (BDDC_OK, -4):
+            _check(code)
+        return x, info.as_dict()
 
     def solve_host(self, b, x=None, rtol=1e-8, maxit=1000):
         """PCG with host arrays (numpy, or torch CPU tensors such as pinned

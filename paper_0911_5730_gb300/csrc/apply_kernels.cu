@@ -1358,58 +1358,67 @@ void build_records(DevLevel &D, const int *ownPos, const int *ownDof, cudaStream
 
 bool apply_fuses_rz(const DevLevel &L, int prec) { return warp_path(L, prec); }
 
-void apply_level_pre(const DevLevel &L, int prec, const double *r, const int *skip, cudaStream_t s,
-                     cudaEvent_t *ev) {
-    const bool wp = warp_path(L, prec);
-    if (ev) cudaEventRecord(ev[0], s);
-    if (wp) {
-        if (prec == BDDC_PREC_FP64) dir_dispatch<double, double>(L, false, r, nullptr, skip, s);
-        else if (prec == BDDC_PREC_FP32) dir_dispatch<float, float>(L, false, r, nullptr, skip, s);
-        else dir_dispatch<__nv_bfloat16, float>(L, false, r, nullptr, skip, s);
-    } else {
+void apply_level_dir(const DevLevel &L, int prec, bool post, const double *r, double *z, const int *skip,
+                     cudaStream_t s, const RzArgs *rz) {
+    if (warp_path(L, prec)) {
+        if (prec == BDDC_PREC_FP64) dir_dispatch<double, double>(L, post, r, z, skip, s, rz);
+        else if (prec == BDDC_PREC_FP32) dir_dispatch<float, float>(L, post, r, z, skip, s, rz);
+        else dir_dispatch<__nv_bfloat16, float>(L, post, r, z, skip, s, rz);
+        return;
+    }
+    if (!post) {
         if (prec == BDDC_PREC_FP64) pre_t<double, double>(L, r, skip, s);
         else if (prec == BDDC_PREC_FP32) pre_t<float, float>(L, r, skip, s);
         else pre_t<__nv_bfloat16, float>(L, r, skip, s);
+        return;
     }
-    if (ev) cudaEventRecord(ev[1], s);
-    if (wp) {
+    if (prec == BDDC_PREC_FP64) post_t<double, double>(L, r, z, skip, s);
+    else if (prec == BDDC_PREC_FP32) post_t<float, float>(L, r, z, skip, s);
+    else post_t<__nv_bfloat16, float>(L, r, z, skip, s);
+    if (rz) launch_pcg_rz((int)L.n, r, z, *rz, s);
+}
+
+void apply_level_neumann(const DevLevel &L, int prec, const double *r, const int *skip, cudaStream_t s) {
+    if (warp_path(L, prec)) {
         if (prec == BDDC_PREC_FP64) neu_launch<double, double>(L, prec, r, skip, s);
         else if (prec == BDDC_PREC_FP32) neu_launch<float, float>(L, prec, r, skip, s);
         else neu_launch<__nv_bfloat16, float>(L, prec, r, skip, s);
-    } else {
-        const size_t smn = sizeof(double) * (size_t)(L.max_nG > L.max_nc ? L.max_nG : L.max_nc);
-        if (prec == BDDC_PREC_FP64) launch_k(false, k_neumann<double, double>, L.nsub, 128, smn, s, L, r, skip);
-        else if (prec == BDDC_PREC_FP32) launch_k(false, k_neumann<float, float>, L.nsub, 128, smn, s, L, r, skip);
-        else launch_k(false, k_neumann<__nv_bfloat16, float>, L.nsub, 128, smn, s, L, r, skip);
+        return;
     }
+    const size_t smn = sizeof(double) * (size_t)(L.max_nG > L.max_nc ? L.max_nG : L.max_nc);
+    if (prec == BDDC_PREC_FP64) launch_k(false, k_neumann<double, double>, L.nsub, 128, smn, s, L, r, skip);
+    else if (prec == BDDC_PREC_FP32) launch_k(false, k_neumann<float, float>, L.nsub, 128, smn, s, L, r, skip);
+    else launch_k(false, k_neumann<__nv_bfloat16, float>, L.nsub, 128, smn, s, L, r, skip);
+}
+
+void apply_level_average(const DevLevel &L, int prec, const int *skip, cudaStream_t s) {
+    if (warp_path(L, prec)) {
+        if (prec == BDDC_PREC_FP64) avg_launch<double, double>(L, prec, skip, s);
+        else if (prec == BDDC_PREC_FP32) avg_launch<float, float>(L, prec, skip, s);
+        else avg_launch<__nv_bfloat16, float>(L, prec, skip, s);
+        return;
+    }
+    const size_t smn = sizeof(double) * (size_t)(L.max_nc > 0 ? L.max_nc : 1);
+    if (prec == BDDC_PREC_FP64) launch_k(false, k_average<double, double>, L.nsub, 128, smn, s, L, skip);
+    else if (prec == BDDC_PREC_FP32) launch_k(false, k_average<float, float>, L.nsub, 128, smn, s, L, skip);
+    else launch_k(false, k_average<__nv_bfloat16, float>, L.nsub, 128, smn, s, L, skip);
+}
+
+void apply_level_pre(const DevLevel &L, int prec, const double *r, const int *skip, cudaStream_t s,
+                     cudaEvent_t *ev) {
+    if (ev) cudaEventRecord(ev[0], s);
+    apply_level_dir(L, prec, false, r, nullptr, skip, s, nullptr);
+    if (ev) cudaEventRecord(ev[1], s);
+    apply_level_neumann(L, prec, r, skip, s);
     if (ev) cudaEventRecord(ev[2], s);
 }
 
 void apply_level_post(const DevLevel &L, int prec, const double *r, double *z, const int *skip,
                       cudaStream_t s, cudaEvent_t *ev, const RzArgs *rz) {
-    const bool wp = warp_path(L, prec);
     if (ev) cudaEventRecord(ev[0], s);
-    if (wp) {
-        if (prec == BDDC_PREC_FP64) avg_launch<double, double>(L, prec, skip, s);
-        else if (prec == BDDC_PREC_FP32) avg_launch<float, float>(L, prec, skip, s);
-        else avg_launch<__nv_bfloat16, float>(L, prec, skip, s);
-    } else {
-        const size_t smn = sizeof(double) * (size_t)(L.max_nc > 0 ? L.max_nc : 1);
-        if (prec == BDDC_PREC_FP64) launch_k(false, k_average<double, double>, L.nsub, 128, smn, s, L, skip);
-        else if (prec == BDDC_PREC_FP32) launch_k(false, k_average<float, float>, L.nsub, 128, smn, s, L, skip);
-        else launch_k(false, k_average<__nv_bfloat16, float>, L.nsub, 128, smn, s, L, skip);
-    }
+    apply_level_average(L, prec, skip, s);
     if (ev) cudaEventRecord(ev[1], s);
-    if (wp) {
-        if (prec == BDDC_PREC_FP64) dir_dispatch<double, double>(L, true, r, z, skip, s, rz);
-        else if (prec == BDDC_PREC_FP32) dir_dispatch<float, float>(L, true, r, z, skip, s, rz);
-        else dir_dispatch<__nv_bfloat16, float>(L, true, r, z, skip, s, rz);
-    } else {
-        if (prec == BDDC_PREC_FP64) post_t<double, double>(L, r, z, skip, s);
-        else if (prec == BDDC_PREC_FP32) post_t<float, float>(L, r, z, skip, s);
-        else post_t<__nv_bfloat16, float>(L, r, z, skip, s);
-        if (rz) launch_pcg_rz((int)L.n, r, z, *rz, s);
-    }
+    apply_level_dir(L, prec, true, r, z, skip, s, rz);
     if (ev) cudaEventRecord(ev[2], s);
 }
 

@@ -83,9 +83,29 @@ struct BatchWs {
     }
 };
 
+// Interface-reduced PCG (bddc_pcg_solve_reduced): vectors on the level-1
+// interface ids and the full-length vectors its operator and preconditioner
+// pass through.
+struct ReducedWs {
+    double *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr;   // [n_iface]
+    double *rf = nullptr;      // [n] r placed on Gamma, zero in the interior
+    double *ut = nullptr;      // [n] harmonic extension / reconstructed solution
+    double *qf = nullptr;      // [n] A of it
+    double *zero = nullptr;    // [n] zero right-hand side of the interior sweep
+    double *part = nullptr;
+    unsigned *counter = nullptr;
+    RedScalars *sc = nullptr, *hsc = nullptr;   // device, pinned mirror
+    cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};
+    ~ReducedWs() {
+        for (auto &g : graph) if (g) cudaGraphExecDestroy(g);
+        if (hsc) cudaFreeHost(hsc);
+    }
+};
+
 struct Workspace {
     DevArena arena;
     std::unique_ptr<BatchWs> bw;
+    std::unique_ptr<ReducedWs> red;
     std::vector<DevLevel> lv;
     double *x = nullptr, *r = nullptr, *z = nullptr, *q = nullptr, *tmp = nullptr;
     double *p0 = nullptr, *p1 = nullptr;   // search direction, alternating by iteration
@@ -105,6 +125,7 @@ struct Workspace {
     std::vector<double> hal, hbe;       // host copies of the CG coefficients
     ~Workspace() {
         bw.reset();
+        red.reset();
         for (auto &g : graph) if (g) cudaGraphExecDestroy(g);
         if (hsc) cudaFreeHost(hsc);
         if (hout) cudaFreeHost(hout);
@@ -837,6 +858,160 @@ int pcg_one(bddc_ctx *C, Workspace &W, int prec, const double *b, double *x, dou
     return status;
 }
 
+// ---------------------------------------------------------------------------
+// Level 1 reduced to the interface (the remark closing Sec. 4): PCG on
+// S = A_GG - A_GI A_II^-1 A_IG with the preconditioner of eqs. (6)-(9), no
+// interior pre- or post-correction.  g = b_G - A_GI A_II^-1 b_I before, and
+// x_I = A_II^-1 (b_I - A_IG x_G) after.  S is applied in FP64 (its interior
+// sweep is part of the operator); the preconditioner in the chosen precision.
+// ---------------------------------------------------------------------------
+ReducedWs &reduced_ws(bddc_ctx *C, Workspace &W) {
+    if (W.red) return *W.red;
+    auto R = std::make_unique<ReducedWs>();
+    DevArena &A = W.arena;
+    const int n = C->n(), ng = std::max(W.lv[0].n_iface, 1);
+    R->x = A.alloc_n<double>(ng); R->r = A.alloc_n<double>(ng);
+    R->p = A.alloc_n<double>(ng); R->q = A.alloc_n<double>(ng);
+    R->rf = A.alloc_n<double>(n); R->ut = A.alloc_n<double>(n);
+    R->qf = A.alloc_n<double>(n); R->zero = A.alloc_n<double>(n);
+    BDDC_CUDA_TRY(cudaMemset(R->rf, 0, sizeof(double) * n));
+    BDDC_CUDA_TRY(cudaMemset(R->zero, 0, sizeof(double) * n));
+    R->part = A.alloc_n<double>(red_blocks() + 8);
+    R->counter = A.alloc_n<unsigned>(4);
+    BDDC_CUDA_TRY(cudaMemset(R->counter, 0, 4 * sizeof(unsigned)));
+    R->sc = A.alloc_n<RedScalars>(1);
+    BDDC_CUDA_TRY(cudaMemset(R->sc, 0, sizeof(RedScalars)));
+    BDDC_CUDA_TRY(cudaHostAlloc((void **)&R->hsc, sizeof(RedScalars), cudaHostAllocDefault));
+    W.red = std::move(R);
+    return *W.red;
+}
+
+// z = M r on the interface, in u_B of level 1
+void reduced_precondition(bddc_ctx *C, Workspace &W, ReducedWs &R, int prec, cudaStream_t st) {
+    const DevLevel &D = W.lv[0];
+    const int *skip = &R.sc->done;
+    BDDC_CUDA_TRY(cudaMemsetAsync(D.uB, 0, sizeof(double) * std::max(D.n_iface, 1), st));
+    launch_red_scatter(D.n_iface, D.ifaceDof, R.r, R.rf, skip, st);
+    apply_level_neumann(D, prec, R.rf, skip, st);                            // (6)-(8)
+    if (W.lv.size() == 1)
+        launch_dense_symv(C->n_top, C->ld_top, C->Ainv, D.rcv, D.ucv, skip, st);
+    else
+        apply_rec(C, W, 1, prec, D.rcv, D.ucv, skip, st);                   // level 2 onwards
+    apply_level_average(D, prec, skip, st);                                  // (9)
+}
+
+// one iteration: q = S p, alpha, x and r, then z = M r, beta, p
+void reduced_iteration(bddc_ctx *C, Workspace &W, ReducedWs &R, int prec, cudaStream_t st) {
+    const DevLevel &D = W.lv[0];
+    const int ng = D.n_iface;
+    const int *skip = &R.sc->done;
+    apply_level_dir(D, BDDC_PREC_FP64, true, R.zero, R.ut, skip, st, nullptr);   // u~ = [-A_II^-1 A_IG p; p]
+    launch_q1_spmv(C->nx, C->w_dev, R.ut, R.qf, st);
+    launch_red_pq(ng, D.ifaceDof, R.qf, R.p, R.q, R.part, R.counter, R.sc, W.alphas, skip, st);
+    launch_red_update(ng, R.x, R.r, R.p, R.q, R.part, R.counter, R.sc, skip, st);
+    reduced_precondition(C, W, R, prec, st);
+    launch_red_rz(ng, R.r, D.uB, R.part, R.counter, R.sc, W.betas, skip, st);
+    launch_red_dir(ng, D.uB, R.p, R.sc, skip, st);
+}
+
+cudaGraphExec_t reduced_graph(bddc_ctx *C, Workspace &W, ReducedWs &R, int prec) {
+    if (R.graph[prec]) return R.graph[prec];
+    cudaStream_t st = W.stream;
+    cudaGraph_t g;
+    BDDC_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    try {
+        for (int it = 0; it < kGraphIters; ++it) reduced_iteration(C, W, R, prec, st);
+    } catch (...) {
+        abandon_capture(st);
+        throw;
+    }
+    BDDC_CUDA_TRY(cudaStreamEndCapture(st, &g));
+    BDDC_CUDA_TRY(cudaGraphInstantiate(&R.graph[prec], g, 0));
+    cudaGraphDestroy(g);
+    return R.graph[prec];
+}
+
+int pcg_reduced(bddc_ctx *C, Workspace &W, int prec, const double *b, double *x, double rtol, int maxit,
+                bddc_solve_info *info) {
+    ReducedWs &R = reduced_ws(C, W);
+    const DevLevel &D = W.lv[0];
+    const int n = C->n(), ng = D.n_iface;
+    cudaStream_t st = W.stream;
+    if (maxit > W.maxit_cap) maxit = W.maxit_cap;
+    // g = b_G - (A [A_II^-1 b_I; 0])_G and ||b||^2
+    BDDC_CUDA_TRY(cudaMemsetAsync(D.uB, 0, sizeof(double) * std::max(ng, 1), st));
+    apply_level_dir(D, BDDC_PREC_FP64, true, b, R.ut, nullptr, st, nullptr);
+    launch_q1_spmv(C->nx, C->w_dev, R.ut, R.qf, st);
+    launch_norm2(n, b, W.part, W.counter, &R.sc->bb, st);
+    launch_red_init(ng, D.ifaceDof, b, R.qf, R.x, R.r, R.p, R.part, R.counter, R.sc, rtol, maxit, st);
+    auto start = [&]() {                  // z = M r, p = z
+        reduced_precondition(C, W, R, prec, st);
+        launch_red_rz(ng, R.r, D.uB, R.part, R.counter, R.sc, W.betas, &R.sc->done, st);
+        launch_red_dir(ng, D.uB, R.p, R.sc, &R.sc->done, st);
+    };
+    start();
+    cudaGraphExec_t g = reduced_graph(C, W, R, prec);
+    int chunk = W.last_iters > 1 ? std::min((W.last_iters + kGraphIters - 1) / kGraphIters, 128) : 2;
+    double rr_true = 0.0;
+    int launches = 0;
+    for (;;) {
+        for (int k = 0; k < chunk; ++k) BDDC_CUDA_TRY(cudaGraphLaunch(g, st));
+        launches += chunk;
+        BDDC_CUDA_TRY(cudaMemcpyAsync(R.hsc, R.sc, sizeof(RedScalars), cudaMemcpyDeviceToHost, st));
+        BDDC_CUDA_TRY(cudaStreamSynchronize(st));
+        if (!R.hsc->done) { chunk = std::max(1, std::min(chunk / 2, 16)); continue; }
+        // reconstruct x = [A_II^-1 (b_I - A_IG x_G); x_G] and confirm with the
+        // true residual; restart from it with a fresh direction if needed
+        BDDC_CUDA_TRY(cudaMemcpyAsync(D.uB, R.x, sizeof(double) * std::max(ng, 1), cudaMemcpyDeviceToDevice, st));
+        apply_level_dir(D, BDDC_PREC_FP64, true, b, W.x, nullptr, st, nullptr);
+        launch_residual(C->nx, C->w_dev, b, W.x, W.tmp, st);
+        launch_norm2(n, W.tmp, W.part, W.counter, W.lout, st);
+        BDDC_CUDA_TRY(cudaMemcpyAsync(W.hout, W.lout, sizeof(double), cudaMemcpyDeviceToHost, st));
+        BDDC_CUDA_TRY(cudaStreamSynchronize(st));
+        rr_true = W.hout[0];
+        if (R.hsc->conv && rr_true > R.hsc->tol2 && R.hsc->it < maxit) {
+            RedScalars hs = *R.hsc;
+            hs.done = 0; hs.conv = 0; hs.fresh = 1; hs.rr = rr_true;
+            *R.hsc = hs;
+            BDDC_CUDA_TRY(cudaMemcpyAsync(R.sc, R.hsc, sizeof(RedScalars), cudaMemcpyHostToDevice, st));
+            launch_red_restart(ng, D.ifaceDof, W.tmp, R.r, st);
+            start();
+            chunk = 1;
+            continue;
+        }
+        break;
+    }
+    const RedScalars h = *R.hsc;
+    const int kit = std::min(h.it, W.maxit_cap);
+    if (W.hal.size() < (size_t)kit + 1) { W.hal.resize(kit + 1); W.hbe.resize(kit + 1); }
+    if (kit > 0) {
+        BDDC_CUDA_TRY(cudaMemcpyAsync(W.hal.data(), W.alphas, sizeof(double) * kit, cudaMemcpyDeviceToHost, st));
+        BDDC_CUDA_TRY(cudaMemcpyAsync(W.hbe.data(), W.betas, sizeof(double) * kit, cudaMemcpyDeviceToHost, st));
+    }
+    BDDC_CUDA_TRY(cudaMemcpyAsync(x, W.x, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    int kerr = 0;
+    BDDC_CUDA_TRY(cudaMemcpyAsync(&kerr, C->err_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
+    BDDC_CUDA_TRY(cudaStreamSynchronize(st));
+    BDDC_CUDA_TRY(cudaGetLastError());
+    if (kerr) throw Error(BDDC_E_TIMEOUT, "a bounded device wait gave up during the solve");
+    const int status = (h.conv && rr_true <= h.tol2 * (1 + 1e-12)) ? BDDC_OK : BDDC_E_NOCONV;
+    W.last_iters = h.it;
+    if (info) {
+        double lmin = 1.0, lmax = 1.0;
+        lanczos_extremes(W.hal, W.hbe, kit, &lmin, &lmax);
+        info->iters = h.it;
+        info->status = status;
+        info->kernel_launches = launches;      // graph launches
+        info->batch_width = 1;
+        info->relres = h.bb > 0 ? std::sqrt(h.rr / h.bb) : 0.0;
+        info->relres_true = h.bb > 0 ? std::sqrt(rr_true / h.bb) : 0.0;
+        info->lam_min = lmin;
+        info->lam_max = lmax;
+        info->kappa_est = lmin > 0 ? lmax / lmin : 0.0;
+    }
+    return status;
+}
+
 // Level 1 of Sec. 2: the Q1 elements of the mesh with their free nodes
 // (Dirichlet nodes are dropped slots).
 // ---------------------------------------------------------------------------
@@ -1308,6 +1483,24 @@ int bddc_pcg_solve(bddc_ctx *ctx, const double *b_dev, double *x_dev, int nrhs, 
                 if (s != BDDC_OK) rc = s;
             }
         }
+        BDDC_CUDA_TRY(cudaEventRecord(W.ev, W.stream));
+        BDDC_CUDA_TRY(cudaStreamWaitEvent(st, W.ev, 0));
+        BDDC_CUDA_TRY(cudaStreamSynchronize(st));
+        if (rc != BDDC_OK) set_error("PCG did not reach the tolerance within maxit");
+        return rc;
+    });
+}
+
+int bddc_pcg_solve_reduced(bddc_ctx *ctx, const double *b_dev, double *x_dev, double rtol, int maxit,
+                           bddc_solve_info *info_host, void *stream) {
+    return guarded([&]() -> int {
+        if (!ctx || !b_dev || !x_dev || maxit < 1 || !(rtol > 0)) throw Error(BDDC_E_ARG, "bad argument");
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        Workspace &W = *ctx->ws;
+        cudaStream_t st = (cudaStream_t)stream;
+        BDDC_CUDA_TRY(cudaEventRecord(W.ev, st));
+        BDDC_CUDA_TRY(cudaStreamWaitEvent(W.stream, W.ev, 0));
+        const int rc = pcg_reduced(ctx, W, ctx->prec, b_dev, x_dev, rtol, maxit, info_host);
         BDDC_CUDA_TRY(cudaEventRecord(W.ev, W.stream));
         BDDC_CUDA_TRY(cudaStreamWaitEvent(st, W.ev, 0));
         BDDC_CUDA_TRY(cudaStreamSynchronize(st));

@@ -164,6 +164,13 @@ struct PcgScalars {
     int fresh;        // next r.z starts a new direction sequence (beta = 0)
     int pad_;
 };
+// Scalars of the interface-reduced PCG (reduced_kernels.cu).
+struct RedScalars {
+    double rho, alpha, beta, rr, bb, tol2;
+    int it, done, conv, maxit;
+    int fresh;        // next r.z starts a new direction sequence (beta = 0)
+    int pad_;
+};
 // r.z of the PCG iteration, reduced by the level-1 post-correction kernel
 // when it writes z (part holds one partial per substructure, counter is zero
 // between launches) or by a separate kernel otherwise.
@@ -191,6 +198,34 @@ void apply_level_pre(const DevLevel &L, int prec, const double *r, const int *sk
 // the PCG recurrence, fused into the post-correction where it can be.
 void apply_level_post(const DevLevel &L, int prec, const double *r, double *z, const int *skip,
                       cudaStream_t s, cudaEvent_t *ev = nullptr, const RzArgs *rz = nullptr);
+// The three parts of the two level launchers above, for the interface-reduced
+// solve: the interior sweep (pre: eqs. 4-5; post: eqs. 10-11, z_I from r and
+// u_B, z on the owned interface = u_B), the substructure correction and coarse
+// right-hand side (eqs. 6-8, from r on Gamma plus r_B), and the averaging (9).
+void apply_level_dir(const DevLevel &L, int prec, bool post, const double *r, double *z, const int *skip,
+                     cudaStream_t s, const RzArgs *rz);
+void apply_level_neumann(const DevLevel &L, int prec, const double *r, const int *skip, cudaStream_t s);
+void apply_level_average(const DevLevel &L, int prec, const int *skip, cudaStream_t s);
+
+// ----------------------------------------------------------------------------
+// Interface-reduced PCG (reduced_kernels.cu): vectors of the n_iface compact
+// interface ids; every launch but init and restart is skipped once *skip.
+// ----------------------------------------------------------------------------
+int red_blocks();
+void launch_red_init(int ng, const int *ifaceDof, const double *b, const double *qf, double *x, double *r,
+                     double *p, double *part, unsigned *counter, RedScalars *sc, double tol, int maxit,
+                     cudaStream_t s);
+void launch_red_scatter(int ng, const int *ifaceDof, const double *r, double *rf, const int *skip,
+                        cudaStream_t s);
+void launch_red_rz(int ng, const double *r, const double *z, double *part, unsigned *counter, RedScalars *sc,
+                   double *betas, const int *skip, cudaStream_t s);
+void launch_red_dir(int ng, double *uB, double *p, const RedScalars *sc, const int *skip, cudaStream_t s);
+void launch_red_pq(int ng, const int *ifaceDof, const double *qf, const double *p, double *q, double *part,
+                   unsigned *counter, RedScalars *sc, double *alphas, const int *skip, cudaStream_t s);
+void launch_red_update(int ng, double *x, double *r, const double *p, const double *q, double *part,
+                       unsigned *counter, RedScalars *sc, const int *skip, cudaStream_t s);
+void launch_red_restart(int ng, const int *ifaceDof, const double *res, double *r, cudaStream_t s);
+
 // ----------------------------------------------------------------------------
 // Batches of K <= kMaxBatch right-hand sides (batch_kernels.cu).  Every batch
 // vector is interleaved: entry (g, k) at g * K + k.
