@@ -339,6 +339,32 @@ def gpu_arm(a):
     t1 = max_over_ranks(sum(ms1) / 1e3)
     t1_64 = max_over_ranks(sum(ms1_64) / 1e3)
 
+    # one right-hand side at a time, level 1 reduced to the interface
+    def timed_reduced(prec, K, W):
+        P.set_precision(prec)
+        for _ in range(W):
+            P.solve_reduced(b1, x1, rtol=RTOL)
+        st = torch.cuda.current_stream()
+        ms, its = [], []
+        barrier()
+        torch.cuda.synchronize()
+        for _ in range(K):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            _, info = P.solve_reduced(b1, x1, rtol=RTOL, stream=st)
+            e1.record(st)
+            e1.synchronize()
+            assert info["status"] == 0 and info["relres_true"] <= RTOL, info
+            ms.append(e0.elapsed_time(e1))
+            its.append(info["iters"])
+        barrier()
+        return max_over_ranks(sum(ms) / 1e3), len(ms), its[0]
+
+    tr32, nr32, itr32 = timed_reduced("fp32", a.steps, a.warmup)
+    tr64, nr64, itr64 = timed_reduced("fp64", max(3, a.steps // 2), 1)
+
     # config 5: a Poisson stream of requests at 0.8 x the measured batch rate
     P.set_precision("fp32")
     serving = serving_run(bddc, P, wl.n_dof, 0.8 * value / world, 3.0, 5001)
@@ -421,7 +447,10 @@ def gpu_arm(a):
                     "bf16_iterations": infbf[0][0]["iters"],
                     "mixed_over_fp64": value / (world * BATCH * len(ms64) / t64),
                     "single_rhs_fp32_solves_per_s": world * len(ms1) / t1,
-                    "single_rhs_fp64_solves_per_s": world * len(ms1_64) / t1_64},
+                    "single_rhs_fp64_solves_per_s": world * len(ms1_64) / t1_64,
+                    "reduced_single_rhs_fp32_solves_per_s": world * nr32 / tr32,
+                    "reduced_single_rhs_fp64_solves_per_s": world * nr64 / tr64,
+                    "reduced_iterations": {"fp32": itr32, "fp64": itr64}},
         "setup_ms": setup_s * 1e3,
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 8 * wl.n_dof * BATCH,
                 "d2h_bytes_per_step": 8 * wl.n_dof * BATCH},
