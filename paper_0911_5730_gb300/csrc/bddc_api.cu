@@ -3,6 +3,8 @@
 #include "internal.h"
 
 #include <algorithm>
+#include <exception>
+#include <thread>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -151,6 +153,7 @@ struct bddc_ctx {
     double *Ainv = nullptr;           // top-level inverse, leading dimension ld_top
     int *err_dev = nullptr;           // set by kernels whose bounded waits gave up
     std::unique_ptr<Workspace> ws;
+    std::unique_ptr<Workspace> ws2;   // second batch group of a solve (own stream and scratch)
     int tuned[3] = {0, 0, 0};         // autotuned batch tiles (see bddc_info::tuned_tile)
     // the autotuner's variants, chosen once per problem and shared by every
     // workspace (the stencil tile fixes the order of the dot products, so
@@ -1456,6 +1459,59 @@ int bddc_operator(bddc_ctx *ctx, const double *x_dev, double *y_dev, void *strea
     });
 }
 
+}  // extern "C"
+
+namespace bddc {
+
+Workspace &second_ws(bddc_ctx *ctx) {
+    if (!ctx->ws2) {
+        auto W = std::make_unique<Workspace>();
+        make_workspace(ctx, *W, 10000);
+        ctx->ws2 = std::move(W);
+    }
+    return *ctx->ws2;
+}
+
+// Groups of up to kMaxBatch right-hand sides [j0, j0 + K), two at a time: the
+// first on the context's workspace, the second on a second workspace (its
+// own stream, batch scratch and graphs) from a helper thread.  The two
+// lockstep groups then overlap on the device: the FP64 phases of one (the
+// top-level product, the PCG recurrences) with the FP32 phases of the other.
+template <class F> int run_batch_groups(bddc_ctx *ctx, int nrhs, F &&group) {
+    int rc = BDDC_OK;
+    for (int j0 = 0; j0 < nrhs; j0 += 2 * kMaxBatch) {
+        const int K0 = std::min(kMaxBatch, nrhs - j0);
+        const int j1 = j0 + K0, K1 = std::min(kMaxBatch, nrhs - j1);
+        if (K1 <= 0) {
+            const int s0 = group(*ctx->ws, j0, K0);
+            if (s0 != BDDC_OK) rc = s0;
+            continue;
+        }
+        Workspace &W2 = second_ws(ctx);
+        int s1 = BDDC_OK;
+        std::exception_ptr ep;
+        std::thread t([&] {
+            try { s1 = group(W2, j1, K1); } catch (...) { ep = std::current_exception(); }
+        });
+        int s0 = BDDC_OK;
+        try {
+            s0 = group(*ctx->ws, j0, K0);
+        } catch (...) {
+            t.join();
+            throw;
+        }
+        t.join();
+        if (ep) std::rethrow_exception(ep);
+        if (s0 != BDDC_OK) rc = s0;
+        if (s1 != BDDC_OK) rc = s1;
+    }
+    return rc;
+}
+
+}  // namespace bddc
+
+extern "C" {
+
 int bddc_pcg_solve(bddc_ctx *ctx, const double *b_dev, double *x_dev, int nrhs, int64_t ld,
                    double rtol, int maxit, bddc_solve_info *info_host, void *stream) {
     return guarded([&]() -> int {
@@ -1470,12 +1526,11 @@ int bddc_pcg_solve(bddc_ctx *ctx, const double *b_dev, double *x_dev, int nrhs, 
         BDDC_CUDA_TRY(cudaStreamWaitEvent(W.stream, W.ev, 0));
         int rc = BDDC_OK;
         if (nrhs > 1 && batch_ok(ctx, W, ctx->prec)) {
-            for (int j0 = 0; j0 < nrhs; j0 += kMaxBatch) {
-                const int K = std::min(kMaxBatch, nrhs - j0);
-                const int s = pcg_batch(ctx, W, ctx->prec, b_dev + j0 * ld, ld, x_dev + j0 * ld, ld, K,
-                                        rtol, maxit, info_host ? info_host + j0 : nullptr);
-                if (s != BDDC_OK) rc = s;
-            }
+            if (nrhs > kMaxBatch) BDDC_CUDA_TRY(cudaStreamWaitEvent(second_ws(ctx).stream, W.ev, 0));
+            rc = run_batch_groups(ctx, nrhs, [&](Workspace &Wg, int j0, int K) {
+                return pcg_batch(ctx, Wg, ctx->prec, b_dev + j0 * ld, ld, x_dev + j0 * ld, ld, K, rtol, maxit,
+                                 info_host ? info_host + j0 : nullptr);
+            });
         } else {
             for (int j = 0; j < nrhs; ++j) {
                 const int s = pcg_one(ctx, W, ctx->prec, b_dev + j * ld, x_dev + j * ld, rtol, maxit,
@@ -1521,20 +1576,19 @@ int bddc_pcg_solve_host(bddc_ctx *ctx, const double *b_host, double *x_host, int
         (void)stream;
         int rc = BDDC_OK;
         if (nrhs > 1 && batch_ok(ctx, W, ctx->prec)) {
-            BatchWs &BW = batch_ws(ctx, W);
-            for (int j0 = 0; j0 < nrhs; j0 += kMaxBatch) {
-                const int K = std::min(kMaxBatch, nrhs - j0);
+            rc = run_batch_groups(ctx, nrhs, [&](Workspace &Wg, int j0, int K) {
+                BatchWs &BW = batch_ws(ctx, Wg);
                 for (int k = 0; k < K; ++k)
                     BDDC_CUDA_TRY(cudaMemcpyAsync(BW.bcol + (int64_t)k * n, b_host + (j0 + k) * ld,
-                                                  sizeof(double) * n, cudaMemcpyHostToDevice, W.stream));
-                const int s = pcg_batch(ctx, W, ctx->prec, BW.bcol, n, BW.xcol, n, K, rtol, maxit,
+                                                  sizeof(double) * n, cudaMemcpyHostToDevice, Wg.stream));
+                const int s = pcg_batch(ctx, Wg, ctx->prec, BW.bcol, n, BW.xcol, n, K, rtol, maxit,
                                         info_host ? info_host + j0 : nullptr);
                 for (int k = 0; k < K; ++k)
                     BDDC_CUDA_TRY(cudaMemcpyAsync(x_host + (j0 + k) * ld, BW.xcol + (int64_t)k * n,
-                                                  sizeof(double) * n, cudaMemcpyDeviceToHost, W.stream));
-                BDDC_CUDA_TRY(cudaStreamSynchronize(W.stream));
-                if (s != BDDC_OK) rc = s;
-            }
+                                                  sizeof(double) * n, cudaMemcpyDeviceToHost, Wg.stream));
+                BDDC_CUDA_TRY(cudaStreamSynchronize(Wg.stream));
+                return s;
+            });
             if (rc != BDDC_OK) set_error("PCG did not reach the tolerance within maxit");
             return rc;
         }
@@ -1864,10 +1918,16 @@ struct Request {
 
 // Continuous batching for one problem: a lockstep batch of K slots whose
 // right-hand sides come and go between iterations (see engine_loop).
+// Continuous-batching engines of one problem: kEnginesPerProblem threads,
+// each with its own workspace, stream and lockstep batch of K slots, admitting
+// from one shared queue of (request, right-hand side); two batches in flight
+// overlap the FP64 phases of one with the FP32 phases of the other.
+constexpr int kEnginesPerProblem = 2;
+using PendingQueue = std::deque<std::pair<std::shared_ptr<Request>, int>>;
 struct Engine {
     bddc_ctx *ctx = nullptr;
     int K = kMaxBatch;
-    std::deque<std::pair<std::shared_ptr<Request>, int>> pending;   // (request, right-hand side)
+    std::shared_ptr<PendingQueue> pending;
     std::thread th;
     bool dead = false;
 };
@@ -1886,7 +1946,7 @@ struct bddc_server {
     std::deque<std::shared_ptr<bddc::Request>> queue;      // problems the batch kernels cannot take
     std::map<uint64_t, std::shared_ptr<bddc::Request>> reqs;
     std::vector<std::thread> workers;
-    std::map<bddc_ctx *, std::unique_ptr<bddc::Engine>> engines;
+    std::map<bddc_ctx *, std::vector<std::unique_ptr<bddc::Engine>>> engines;
 };
 
 namespace bddc {
@@ -1982,8 +2042,8 @@ void engine_loop(bddc_server *S, Engine *E) {
             finish_request(S, *R);
         };
         for (auto &sl : slot) fail(sl.R);
-        for (auto &pr : E->pending) fail(pr.first);
-        E->pending.clear();
+        for (auto &pr : (*E->pending)) fail(pr.first);
+        E->pending->clear();
     };
     try {
         W.reset(new Workspace());
@@ -2007,16 +2067,16 @@ void engine_loop(bddc_server *S, Engine *E) {
                     return false;
                 };
                 auto admissible = [&] {
-                    if (E->pending.empty()) return false;
-                    const auto &R = E->pending.front().first;
+                    if (E->pending->empty()) return false;
+                    const auto &R = E->pending->front().first;
                     return R->started || !S->budget || S->in_use + R->bytes <= S->budget || S->in_use == 0;
                 };
                 S->cv_work.wait(lk, [&] { return S->stop || active() || admissible(); });
-                if (S->stop && !active() && E->pending.empty()) break;
+                if (S->stop && !active() && E->pending->empty()) break;
                 for (int k = 0; k < K && admissible(); ++k) {
                     if (slot[k].R) continue;
-                    auto pr = E->pending.front();
-                    E->pending.pop_front();
+                    auto pr = E->pending->front();
+                    E->pending->pop_front();
                     if (!pr.first->started) { pr.first->started = true; S->in_use += pr.first->bytes; }
                     slot[k].R = pr.first;
                     slot[k].j = pr.second;
@@ -2152,18 +2212,23 @@ int bddc_submit(bddc_server *srv, bddc_ctx *ctx, const double *b_host, int nrhs,
             R->t_submit = std::chrono::steady_clock::now();
             srv->reqs[R->id] = R;
             if (batch) {
-                auto &E = srv->engines[ctx];
-                if (E && E->dead) {            // it has left its locked section: join is safe
-                    E->th.join();
-                    E.reset();
+                auto &Es = srv->engines[ctx];
+                auto q = Es.empty() ? std::make_shared<PendingQueue>() : Es.front()->pending;
+                Es.resize(kEnginesPerProblem);
+                for (auto &E : Es) {
+                    if (E && E->dead) {        // it has left its locked section: join is safe
+                        E->th.join();
+                        E.reset();
+                    }
+                    if (!E) {
+                        E.reset(new Engine());
+                        E->ctx = ctx;
+                        E->K = kMaxBatch;
+                        E->pending = q;
+                        E->th = std::thread(engine_loop, srv, E.get());
+                    }
                 }
-                if (!E) {
-                    E.reset(new Engine());
-                    E->ctx = ctx;
-                    E->K = kMaxBatch;
-                    E->th = std::thread(engine_loop, srv, E.get());
-                }
-                for (int j = 0; j < nrhs; ++j) E->pending.emplace_back(R, j);
+                for (int j = 0; j < nrhs; ++j) q->emplace_back(R, j);
             } else {
                 srv->queue.push_back(R);
             }
@@ -2205,7 +2270,8 @@ void bddc_server_destroy(bddc_server *srv) {
     srv->cv_work.notify_all();
     for (auto &t : srv->workers) t.join();
     for (auto &e : srv->engines)
-        if (e.second->th.joinable()) e.second->th.join();
+        for (auto &E : e.second)
+            if (E && E->th.joinable()) E->th.join();
     delete srv;
 }
 

@@ -180,3 +180,25 @@ def test_autotuned_tiles_reported(lib):
     assert tuple(t[:2]) in {(16, 8), (32, 4), (32, 8), (8, 16)} and t[2] in (8, 16, 32)
     assert all(i["status"] == 0 for i in infos)
     P.close()
+
+
+def test_two_groups_in_flight_match_each_group_alone(lib):
+    """64 right-hand sides run as two lockstep groups of 32 at once (the second
+    on its own workspace and stream); each group's results equal the group
+    solved alone (iteration counts, solutions to rounding: FP64 atomics where
+    three or more substructures meet add in scheduling order)."""
+    wl = WL["channels_64"]
+    P = lib.Problem.from_workload(wl)
+    B = torch.tensor(inputs.normal_rhs(wl.n_dof, 81, 64), device="cuda")
+    for prec in ("fp64", "fp32"):
+        P.set_precision(prec)
+        X, infos = P.solve(B)
+        assert [i["batch_width"] for i in infos] == [32] * 64
+        for g in range(2):
+            Xg, ig = P.solve(B[32 * g:32 * g + 32].contiguous())
+            for j in range(32):
+                assert infos[32 * g + j]["iters"] == ig[j]["iters"], (prec, g, j)
+                assert _relerr(X[32 * g + j].cpu().numpy(), Xg[j].cpu().numpy()) <= 1e-12
+        Xh, ih = P.solve_host(B.cpu().numpy())
+        assert _relerr(Xh, X.cpu().numpy()) <= 1e-12
+    P.close()
