@@ -179,6 +179,44 @@ int bddc_pcg_solve(bddc_ctx *ctx, const double *b_dev, double *x_dev, int nrhs, 
                    double rtol, int maxit, bddc_solve_info *info_host, void *stream);
 
 /*
+ * Partitioning (the first step of Algorithm 2 on every level: substructures
+ * with roughly equal numbers of DOFs and few cuts, from a graph partitioner
+ * with weights on vertices and edges).  Host functions; multilevel recursive
+ * bisection (heavy-edge matching, greedy graph growing, Fiduccia-Mattheyses
+ * refinement) and a final pass that makes every part connected.  The result
+ * depends only on the input and `seed`.
+ *
+ * bddc_partition_graph - CSR graph (xadj[n + 1], xadj[0] = 0, adjncy[xadj[n]]
+ *   holding both directions of every edge), vertex weights vwgt[n] and edge
+ *   weights adjwgt[xadj[n]] (NULL = all 1, non-negative) into nparts
+ *   (1..n) parts: part[n] receives 0..nparts-1, *edgecut (may be NULL) the
+ *   cut edge weight.  Each bisection keeps its sides within (1 + imbalance /
+ *   depth) of their targets.  BDDC_E_ARG on malformed input.
+ */
+int bddc_partition_graph(int32_t n, const int64_t *xadj, const int32_t *adjncy, const int32_t *vwgt,
+                         const int32_t *adjwgt, int32_t nparts, double imbalance, uint64_t seed, int32_t *part,
+                         int64_t *edgecut);
+
+/*
+ * bddc_partition_mesh - level-1 substructures of the nx x nx Q1 mesh:
+ *   elem_to_sub[nx*nx] (element (i, j) at j*nx + i) in 0..nparts-1, over the
+ *   elements' dual graph (shared edges).  With k_elem (host [nx*nx], > 0) an
+ *   edge weighs 1 + round(log10(min(k_a, k_b) / min k)), so cuts avoid the
+ *   high-coefficient regions and follow coefficient jumps; NULL: weight 1.
+ */
+int bddc_partition_mesh(const bddc_mesh *mesh, const double *k_elem, int32_t nparts, double imbalance,
+                        uint64_t seed, int32_t *elem_to_sub, int64_t *edgecut);
+
+/*
+ * bddc_group_substructures - level-2 substructures for 3 levels: the level-1
+ *   substructures of elem_to_sub (ids 0..n_sub1-1) grouped into n_sub2 parts
+ *   (sub1_to_sub2[n_sub1]) over their adjacency graph (vertex weight: elements,
+ *   edge weight: element edges the two share).
+ */
+int bddc_group_substructures(const bddc_mesh *mesh, const int32_t *elem_to_sub, int32_t n_sub1, int32_t n_sub2,
+                             double imbalance, uint64_t seed, int32_t *sub1_to_sub2, int64_t *edgecut);
+
+/*
  * bddc_pcg_solve_reduced - A x = b with level 1 reduced to its interface, as
  * the closing remark of Sec. 4 suggests in place of the interior pre- and
  * post-corrections of eqs. (4)-(5) and (10)-(11): PCG on the Schur complement

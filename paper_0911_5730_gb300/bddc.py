@@ -26,7 +26,8 @@ SYMBOLS = ["bddc_setup", "bddc_apply", "bddc_pcg_solve", "bddc_pcg_solve_host", 
            "bddc_set_precision", "bddc_query", "bddc_operator", "bddc_destroy",
            "bddc_last_error", "bddc_server_create", "bddc_submit", "bddc_wait",
            "bddc_server_destroy", "bddc_profile_apply", "bddc_apply_noalloc", "bddc_inspect",
-           "bddc_selftest_wait_timeout", "bddc_selftest_convert", "bddc_profile_apply_batch"]
+           "bddc_selftest_wait_timeout", "bddc_selftest_convert", "bddc_profile_apply_batch",
+           "bddc_partition_graph", "bddc_partition_mesh", "bddc_group_substructures"]
 
 
 class Mesh(C.Structure):
@@ -98,6 +99,9 @@ def load():
     lib.bddc_apply_noalloc.argtypes = [vp, vp, vp, vp]
     lib.bddc_selftest_wait_timeout.argtypes = [vp]
     lib.bddc_selftest_convert.argtypes = [vp, C.c_int64, C.POINTER(C.c_int64), vp]
+    lib.bddc_partition_graph.argtypes = [i32, vp, vp, vp, vp, i32, dp, C.c_uint64, vp, vp]
+    lib.bddc_partition_mesh.argtypes = [vp, vp, i32, dp, C.c_uint64, vp, vp]
+    lib.bddc_group_substructures.argtypes = [vp, vp, i32, i32, dp, C.c_uint64, vp, vp]
     lib.bddc_inspect.argtypes = [C.POINTER(Mesh), C.POINTER(Decomp), vp, vp, vp, vp, i32, vp]
     lib.bddc_server_destroy.argtypes = [vp]
     lib.bddc_server_destroy.restype = None
@@ -151,6 +155,65 @@ def selftest_convert(values):
     _check(load().bddc_selftest_convert(_ptr(values.contiguous()), int(values.numel()),
                                         C.byref(out), None))
     return out.value
+
+
+def partition_graph(xadj, adjncy, nparts, vwgt=None, adjwgt=None, imbalance=0.03, seed=0):
+    """Graph partitioner of Algorithm 2 (host): returns (part, edge cut)."""
+    lib = load()
+    xadj = np.ascontiguousarray(xadj, dtype=np.int64)
+    adjncy = np.ascontiguousarray(adjncy, dtype=np.int32)
+    n = len(xadj) - 1
+    part = np.zeros(n, np.int32)
+    cut = C.c_int64(0)
+    vw = None if vwgt is None else np.ascontiguousarray(vwgt, dtype=np.int32)
+    ew = None if adjwgt is None else np.ascontiguousarray(adjwgt, dtype=np.int32)
+    _check(lib.bddc_partition_graph(n, xadj.ctypes.data_as(C.c_void_p), adjncy.ctypes.data_as(C.c_void_p),
+                                    None if vw is None else vw.ctypes.data_as(C.c_void_p),
+                                    None if ew is None else ew.ctypes.data_as(C.c_void_p),
+                                    int(nparts), float(imbalance), int(seed),
+                                    part.ctypes.data_as(C.c_void_p), C.byref(cut)))
+    return part, cut.value
+
+
+def partition_mesh(nx, nparts, k=None, imbalance=0.03, seed=0):
+    """Level-1 substructures of the nx x nx mesh; returns (elem_to_sub, cut)."""
+    lib = load()
+    mesh = Mesh(nx, nx)
+    e2s = np.zeros(nx * nx, np.int32)
+    cut = C.c_int64(0)
+    kk = None if k is None else np.ascontiguousarray(k, dtype=np.float64)
+    _check(lib.bddc_partition_mesh(C.byref(mesh), None if kk is None else kk.ctypes.data_as(C.c_void_p),
+                                   int(nparts), float(imbalance), int(seed), e2s.ctypes.data_as(C.c_void_p),
+                                   C.byref(cut)))
+    return e2s, cut.value
+
+
+def group_substructures(nx, elem_to_sub, n_sub1, n_sub2, imbalance=0.03, seed=0):
+    """Level-2 substructures over the level-1 ones; returns (sub1_to_sub2, cut)."""
+    lib = load()
+    mesh = Mesh(nx, nx)
+    e2s = np.ascontiguousarray(elem_to_sub, dtype=np.int32)
+    s2 = np.zeros(n_sub1, np.int32)
+    cut = C.c_int64(0)
+    _check(lib.bddc_group_substructures(C.byref(mesh), e2s.ctypes.data_as(C.c_void_p), int(n_sub1),
+                                        int(n_sub2), float(imbalance), int(seed),
+                                        s2.ctypes.data_as(C.c_void_p), C.byref(cut)))
+    return s2, cut.value
+
+
+def partitioned_workload(base, n_sub1, n_sub2=0, seed=0, weighted=True, imbalance=0.03):
+    """`base` (an inputs.Workload) with its decomposition replaced by the
+    graph partitioner's: n_sub1 level-1 substructures (edge weights from the
+    coefficient when `weighted`), grouped into n_sub2 level-2 ones for three
+    levels."""
+    import dataclasses
+    e2s, _ = partition_mesh(base.nx, n_sub1, base.k if weighted else None, imbalance, seed)
+    if base.levels == 3:
+        s2, _ = group_substructures(base.nx, e2s, n_sub1, n_sub2, imbalance, seed)
+        return dataclasses.replace(base, name=base.name + "_partitioned", elem_to_sub=e2s, n_sub1=n_sub1,
+                                   sub1_to_sub2=s2, n_sub2=n_sub2)
+    return dataclasses.replace(base, name=base.name + "_partitioned", elem_to_sub=e2s, n_sub1=n_sub1,
+                               sub1_to_sub2=None, n_sub2=0)
 
 
 class Problem:

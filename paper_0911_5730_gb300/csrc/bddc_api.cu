@@ -1,6 +1,7 @@
 // bddc_api.cu - setup orchestration, the apply recursion, the PCG driver and
 // the C entry points of libbddc.so.
 #include "internal.h"
+#include "partition.h"
 
 #include <algorithm>
 #include <exception>
@@ -1602,6 +1603,99 @@ int bddc_pcg_solve_host(bddc_ctx *ctx, const double *b_host, double *x_host, int
         }
         if (rc != BDDC_OK) set_error("PCG did not reach the tolerance within maxit");
         return rc;
+    });
+}
+
+int bddc_partition_graph(int32_t n, const int64_t *xadj, const int32_t *adjncy, const int32_t *vwgt,
+                         const int32_t *adjwgt, int32_t nparts, double imbalance, uint64_t seed, int32_t *part,
+                         int64_t *edgecut) {
+    return guarded([&]() -> int {
+        if (n < 1 || !xadj || !adjncy || !part || nparts < 1 || nparts > n || !(imbalance >= 0))
+            throw Error(BDDC_E_ARG, "bad argument");
+        if (xadj[0] != 0) throw Error(BDDC_E_ARG, "xadj[0] must be 0");
+        for (int32_t v = 0; v < n; ++v) {
+            if (xadj[v + 1] < xadj[v]) throw Error(BDDC_E_ARG, "xadj not increasing");
+            if (vwgt && vwgt[v] < 0) throw Error(BDDC_E_ARG, "negative vertex weight");
+        }
+        for (int64_t e = 0; e < xadj[n]; ++e) {
+            if (adjncy[e] < 0 || adjncy[e] >= n) throw Error(BDDC_E_ARG, "adjacency index out of range");
+            if (adjwgt && adjwgt[e] < 0) throw Error(BDDC_E_ARG, "negative edge weight");
+        }
+        const int64_t cut = partition_graph(n, xadj, adjncy, vwgt, adjwgt, nparts, imbalance, seed, part);
+        if (edgecut) *edgecut = cut;
+        return BDDC_OK;
+    });
+}
+
+int bddc_partition_mesh(const bddc_mesh *mesh, const double *k_elem, int32_t nparts, double imbalance,
+                        uint64_t seed, int32_t *elem_to_sub, int64_t *edgecut) {
+    return guarded([&]() -> int {
+        if (!mesh || mesh->nx < 2 || mesh->ny != mesh->nx || !elem_to_sub || nparts < 1)
+            throw Error(BDDC_E_ARG, "bad argument");
+        const int nx = mesh->nx, ne = nx * nx;
+        if (nparts > ne) throw Error(BDDC_E_ARG, "more parts than elements");
+        // dual graph: elements sharing an edge; weight 1 + round(log10 of the
+        // smaller coefficient over the smallest), so that cuts go along
+        // coefficient jumps rather than through high-coefficient regions
+        double kmin = 1.0;
+        if (k_elem) {
+            kmin = k_elem[0];
+            for (int e = 0; e < ne; ++e) {
+                if (!(k_elem[e] > 0)) throw Error(BDDC_E_ARG, "coefficients must be positive");
+                kmin = std::min(kmin, k_elem[e]);
+            }
+        }
+        std::vector<int64_t> xadj(ne + 1, 0);
+        std::vector<int32_t> adj, w;
+        adj.reserve((size_t)ne * 4);
+        w.reserve((size_t)ne * 4);
+        for (int e = 0; e < ne; ++e) {
+            const int ei = e % nx, ej = e / nx;
+            const int nb[4] = {ei > 0 ? e - 1 : -1, ei < nx - 1 ? e + 1 : -1, ej > 0 ? e - nx : -1,
+                               ej < nx - 1 ? e + nx : -1};
+            for (int f : nb) {
+                if (f < 0) continue;
+                adj.push_back(f);
+                w.push_back(k_elem ? 1 + (int)std::lround(std::log10(std::min(k_elem[e], k_elem[f]) / kmin)) : 1);
+            }
+            xadj[e + 1] = (int64_t)adj.size();
+        }
+        const int64_t cut = partition_graph(ne, xadj.data(), adj.data(), nullptr, w.data(), nparts, imbalance,
+                                            seed, elem_to_sub);
+        if (edgecut) *edgecut = cut;
+        return BDDC_OK;
+    });
+}
+
+int bddc_group_substructures(const bddc_mesh *mesh, const int32_t *elem_to_sub, int32_t n_sub1, int32_t n_sub2,
+                             double imbalance, uint64_t seed, int32_t *sub1_to_sub2, int64_t *edgecut) {
+    return guarded([&]() -> int {
+        if (!mesh || mesh->nx < 2 || mesh->ny != mesh->nx || !elem_to_sub || !sub1_to_sub2 || n_sub1 < 1 ||
+            n_sub2 < 1 || n_sub2 > n_sub1)
+            throw Error(BDDC_E_ARG, "bad argument");
+        const int nx = mesh->nx, ne = nx * nx;
+        // graph of the level-1 substructures: vertex weight = elements,
+        // edge weight = element edges shared by the two substructures
+        std::vector<int32_t> vw(n_sub1, 0);
+        std::vector<std::map<int, int>> nb(n_sub1);
+        for (int e = 0; e < ne; ++e) {
+            const int s0 = elem_to_sub[e];
+            if (s0 < 0 || s0 >= n_sub1) throw Error(BDDC_E_ARG, "substructure id out of range");
+            ++vw[s0];
+            const int ei = e % nx;
+            if (ei < nx - 1 && elem_to_sub[e + 1] != s0) { ++nb[s0][elem_to_sub[e + 1]]; ++nb[elem_to_sub[e + 1]][s0]; }
+            if (e + nx < ne && elem_to_sub[e + nx] != s0) { ++nb[s0][elem_to_sub[e + nx]]; ++nb[elem_to_sub[e + nx]][s0]; }
+        }
+        std::vector<int64_t> xadj(n_sub1 + 1, 0);
+        std::vector<int32_t> adj, w;
+        for (int s0 = 0; s0 < n_sub1; ++s0) {
+            for (auto &kv : nb[s0]) { adj.push_back(kv.first); w.push_back(kv.second); }
+            xadj[s0 + 1] = (int64_t)adj.size();
+        }
+        const int64_t cut = partition_graph(n_sub1, xadj.data(), adj.data(), vw.data(), w.data(), n_sub2,
+                                            imbalance, seed, sub1_to_sub2);
+        if (edgecut) *edgecut = cut;
+        return BDDC_OK;
     });
 }
 
