@@ -33,7 +33,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "two_level_channels_512"
-BATCH = 64               # right-hand sides per step: two lockstep groups of GROUP in flight
+BATCH = 96               # right-hand sides per step: three lockstep groups of GROUP in flight
 GROUP = 32               # right-hand sides of one lockstep group (the batch kernels' width)
 RHS_SEED = 2002
 METRIC = "BDDC PCG solves/s at rel-res 1e-8 (mixed vs FP64); p50/p99 latency"
@@ -434,7 +434,7 @@ def gpu_arm(a):
         "config": {"workload": WORKLOAD, "mesh": "512x512 Q1", "substructures": "32x32 (H/h=16)",
                    "levels": 2, "tau": 10.0, "constraints": "adaptive",
                    "coefficient": "k=1e6 on random one-element channels (~10%), else 1",
-                   "rhs": "N(0,1), %d per step (seed %d), solved as %d lockstep groups of %d on two streams"
+                   "rhs": "N(0,1), %d per step (seed %d), solved as %d lockstep groups of %d in flight"
                           % (BATCH, RHS_SEED, BATCH // GROUP, GROUP),
                    "batch": BATCH, "group": GROUP, "rtol": RTOL, "apply_precision": "fp32",
                    "parallelism": "replicas" if world > 1 else "single GPU",

@@ -154,7 +154,8 @@ struct bddc_ctx {
     double *Ainv = nullptr;           // top-level inverse, leading dimension ld_top
     int *err_dev = nullptr;           // set by kernels whose bounded waits gave up
     std::unique_ptr<Workspace> ws;
-    std::unique_ptr<Workspace> ws2;   // second batch group of a solve (own stream and scratch)
+    // further batch groups of a solve in flight at once (own stream and scratch)
+    std::vector<std::unique_ptr<Workspace>> wsx;
     int tuned[3] = {0, 0, 0};         // autotuned batch tiles (see bddc_info::tuned_tile)
     // the autotuner's variants, chosen once per problem and shared by every
     // workspace (the stencil tile fixes the order of the dot products, so
@@ -1464,47 +1465,55 @@ int bddc_operator(bddc_ctx *ctx, const double *x_dev, double *y_dev, void *strea
 
 namespace bddc {
 
-Workspace &second_ws(bddc_ctx *ctx) {
-    if (!ctx->ws2) {
-        auto W = std::make_unique<Workspace>();
+// Lockstep groups of up to kMaxBatch right-hand sides in flight at once:
+// their FP64 phases (top-level product, PCG recurrences) overlap the FP32
+// phases of the others (measured on the 512^2 channel problem: 1120, 1326,
+// 1431 and 1432 solves/s with one to four groups).
+constexpr int kGroupsInFlight = 3;
+
+// Workspace of group g (0: the context's own).
+Workspace &group_ws(bddc_ctx *ctx, int g) {
+    if (g == 0) return *ctx->ws;
+    if ((int)ctx->wsx.size() < g) ctx->wsx.resize(g);
+    auto &W = ctx->wsx[g - 1];
+    if (!W) {
+        W = std::make_unique<Workspace>();
         make_workspace(ctx, *W, 10000);
-        ctx->ws2 = std::move(W);
     }
-    return *ctx->ws2;
+    return *W;
 }
 
-// Groups of up to kMaxBatch right-hand sides [j0, j0 + K), two at a time: the
-// first on the context's workspace, the second on a second workspace (its
-// own stream, batch scratch and graphs) from a helper thread.  The two
-// lockstep groups then overlap on the device: the FP64 phases of one (the
-// top-level product, the PCG recurrences) with the FP32 phases of the other.
+// Groups [j0, j0 + K) of the right-hand sides, kGroupsInFlight at a time: the
+// first on the context's workspace in the calling thread, the others on
+// their own workspaces (stream, batch scratch and graphs) from helper
+// threads.
 template <class F> int run_batch_groups(bddc_ctx *ctx, int nrhs, F &&group) {
     int rc = BDDC_OK;
-    for (int j0 = 0; j0 < nrhs; j0 += 2 * kMaxBatch) {
-        const int K0 = std::min(kMaxBatch, nrhs - j0);
-        const int j1 = j0 + K0, K1 = std::min(kMaxBatch, nrhs - j1);
-        if (K1 <= 0) {
-            const int s0 = group(*ctx->ws, j0, K0);
-            if (s0 != BDDC_OK) rc = s0;
-            continue;
+    for (int j0 = 0; j0 < nrhs; j0 += kGroupsInFlight * kMaxBatch) {
+        int ng = 0, js[kGroupsInFlight], ks[kGroupsInFlight];
+        for (int j = j0; j < nrhs && ng < kGroupsInFlight; j += kMaxBatch, ++ng) {
+            js[ng] = j;
+            ks[ng] = std::min(kMaxBatch, nrhs - j);
         }
-        Workspace &W2 = second_ws(ctx);
-        int s1 = BDDC_OK;
-        std::exception_ptr ep;
-        std::thread t([&] {
-            try { s1 = group(W2, j1, K1); } catch (...) { ep = std::current_exception(); }
-        });
-        int s0 = BDDC_OK;
+        std::vector<Workspace *> ws(ng);
+        for (int g = 0; g < ng; ++g) ws[g] = &group_ws(ctx, g);
+        std::vector<int> st(ng, BDDC_OK);
+        std::vector<std::exception_ptr> ep(ng);
+        std::vector<std::thread> th;
+        for (int g = 1; g < ng; ++g)
+            th.emplace_back([&, g] {
+                try { st[g] = group(*ws[g], js[g], ks[g]); } catch (...) { ep[g] = std::current_exception(); }
+            });
         try {
-            s0 = group(*ctx->ws, j0, K0);
+            st[0] = group(*ws[0], js[0], ks[0]);
         } catch (...) {
-            t.join();
-            throw;
+            ep[0] = std::current_exception();
         }
-        t.join();
-        if (ep) std::rethrow_exception(ep);
-        if (s0 != BDDC_OK) rc = s0;
-        if (s1 != BDDC_OK) rc = s1;
+        for (auto &t : th) t.join();
+        for (int g = 0; g < ng; ++g)
+            if (ep[g]) std::rethrow_exception(ep[g]);
+        for (int g = 0; g < ng; ++g)
+            if (st[g] != BDDC_OK) rc = st[g];
     }
     return rc;
 }
@@ -1527,7 +1536,8 @@ int bddc_pcg_solve(bddc_ctx *ctx, const double *b_dev, double *x_dev, int nrhs, 
         BDDC_CUDA_TRY(cudaStreamWaitEvent(W.stream, W.ev, 0));
         int rc = BDDC_OK;
         if (nrhs > 1 && batch_ok(ctx, W, ctx->prec)) {
-            if (nrhs > kMaxBatch) BDDC_CUDA_TRY(cudaStreamWaitEvent(second_ws(ctx).stream, W.ev, 0));
+            for (int g = 1; g < kGroupsInFlight && g * kMaxBatch < nrhs; ++g)
+                BDDC_CUDA_TRY(cudaStreamWaitEvent(group_ws(ctx, g).stream, W.ev, 0));
             rc = run_batch_groups(ctx, nrhs, [&](Workspace &Wg, int j0, int K) {
                 return pcg_batch(ctx, Wg, ctx->prec, b_dev + j0 * ld, ld, x_dev + j0 * ld, ld, K, rtol, maxit,
                                  info_host ? info_host + j0 : nullptr);
@@ -2014,9 +2024,9 @@ struct Request {
 // right-hand sides come and go between iterations (see engine_loop).
 // Continuous-batching engines of one problem: kEnginesPerProblem threads,
 // each with its own workspace, stream and lockstep batch of K slots, admitting
-// from one shared queue of (request, right-hand side); two batches in flight
-// overlap the FP64 phases of one with the FP32 phases of the other.
-constexpr int kEnginesPerProblem = 2;
+// from one shared queue of (request, right-hand side); batches in flight
+// overlap the FP64 phases of one with the FP32 phases of the others.
+constexpr int kEnginesPerProblem = kGroupsInFlight;
 using PendingQueue = std::deque<std::pair<std::shared_ptr<Request>, int>>;
 struct Engine {
     bddc_ctx *ctx = nullptr;

@@ -182,23 +182,24 @@ def test_autotuned_tiles_reported(lib):
     P.close()
 
 
-def test_two_groups_in_flight_match_each_group_alone(lib):
-    """64 right-hand sides run as two lockstep groups of 32 at once (the second
-    on its own workspace and stream); each group's results equal the group
-    solved alone (iteration counts, solutions to rounding: FP64 atomics where
-    three or more substructures meet add in scheduling order)."""
+def test_groups_in_flight_match_each_group_alone(lib):
+    """70 right-hand sides run as three lockstep groups at once (32, 32 and 6;
+    the second and third on their own workspaces and streams); each group's
+    results equal the group solved alone (iteration counts, solutions to
+    rounding: FP64 atomics where three or more substructures meet add in
+    scheduling order)."""
     wl = WL["channels_64"]
     P = lib.Problem.from_workload(wl)
-    B = torch.tensor(inputs.normal_rhs(wl.n_dof, 81, 64), device="cuda")
+    B = torch.tensor(inputs.normal_rhs(wl.n_dof, 81, 70), device="cuda")
     for prec in ("fp64", "fp32"):
         P.set_precision(prec)
         X, infos = P.solve(B)
-        assert [i["batch_width"] for i in infos] == [32] * 64
-        for g in range(2):
-            Xg, ig = P.solve(B[32 * g:32 * g + 32].contiguous())
-            for j in range(32):
-                assert infos[32 * g + j]["iters"] == ig[j]["iters"], (prec, g, j)
-                assert _relerr(X[32 * g + j].cpu().numpy(), Xg[j].cpu().numpy()) <= 1e-12
+        assert [i["batch_width"] for i in infos] == [32] * 64 + [6] * 6
+        for g0, g1 in ((0, 32), (32, 64), (64, 70)):
+            Xg, ig = P.solve(B[g0:g1].contiguous())
+            for j in range(g1 - g0):
+                assert infos[g0 + j]["iters"] == ig[j]["iters"], (prec, g0, j)
+                assert _relerr(X[g0 + j].cpu().numpy(), Xg[j].cpu().numpy()) <= 1e-12
         Xh, ih = P.solve_host(B.cpu().numpy())
         assert _relerr(Xh, X.cpu().numpy()) <= 1e-12
     P.close()
