@@ -168,10 +168,13 @@ int bddc_apply(bddc_ctx *ctx, const double *r_dev, double *z_dev, int nrhs, int6
  * every level's operators fit the batch kernels (info_host[j].batch_width
  * says which ran): each column keeps its own PCG scalars, stopping test and
  * iteration count, and gets the same iterates as a solo solve up to
- * rounding.  The first batched call on a context allocates its batch
- * workspace (about 8 * 32 * n doubles plus per-level scratch) and times the
- * batch kernels' tile variants on the context's operators (bddc_info
- * tuned_tile).
+ * rounding.  Up to three batches run at once (columns 0-31 on the
+ * context's own workspace, 32-63 and 64-95 on two more, each with its own
+ * stream and a host thread of the call), so the FP64 phases of one batch
+ * overlap the FP32 phases of the others.  The first batched call on a
+ * workspace allocates its batch scratch (about 8 * 32 * n doubles plus
+ * per-level scratch); the first on a context times the batch kernels' tile
+ * variants on its operators (bddc_info tuned_tile).
  * Returns BDDC_E_NOCONV if any column reached maxit (x holds the last iterate).
  * Synchronises `stream` before returning.
  */

@@ -13,6 +13,8 @@ definitions so that a reader can check it against the text by eye:
                   optimal augmentation of Theorem 2 and Algorithm 2 (eq. 14).
 * ``pcg``       - preconditioned conjugate gradients with the Lanczos
                   condition-number estimate reported in Tables 1-7.
+* ``reduced``   - level 1 reduced to the interface (the closing remark of
+                  Sec. 4): PCG on the Schur complement with eqs. (6)-(9).
 
 Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  It shares no code with the CUDA

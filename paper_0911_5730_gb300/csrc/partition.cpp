@@ -72,7 +72,6 @@ G coarsen_once(const G &g, Rng &rng, std::vector<int> &cmap) {
     std::vector<int> mark(nc, -1), pos(nc, 0);
     c.xadj.assign(nc + 1, 0);
     for (int cv = 0; cv < nc; ++cv) {
-        const int64_t start = (int64_t)c.adj.size();
         for (int v : members[cv])
             for (int64_t e = g.xadj[v]; e < g.xadj[v + 1]; ++e) {
                 const int cu = cmap[g.adj[e]];
@@ -86,7 +85,6 @@ G coarsen_once(const G &g, Rng &rng, std::vector<int> &cmap) {
                     c.ew[pos[cu]] += g.ew[e];
                 }
             }
-        (void)start;
         c.xadj[cv + 1] = (int64_t)c.adj.size();
     }
     return c;
