@@ -248,7 +248,7 @@ def serving_run(bddc, P, n, rate_rhs, seconds, seed):
     return {"offered_rhs_per_s": rate_rhs, "requests": len(sizes), "rhs": int(sum(sizes)),
             "solves_per_s": sum(sizes) / wall, "latency_ms": {"p50": pct(50), "p99": pct(99)},
             "stream": "Poisson arrivals (seed %d), 1-64 right-hand sides per request, "
-                      "continuous batching into 32 slots" % seed}
+                      "continuous batching: three engines of 32 slots" % seed}
 
 
 def replica_barrier(world):
@@ -366,9 +366,12 @@ def gpu_arm(a):
     tr32, nr32, itr32 = timed_reduced("fp32", a.steps, a.warmup)
     tr64, nr64, itr64 = timed_reduced("fp64", max(3, a.steps // 2), 1)
 
-    # config 5: a Poisson stream of requests at 0.8 x the measured batch rate
+    # config 5: Poisson streams of requests at 0.5, 0.8 and 1.0 x the measured
+    # batch rate (0.8 x is the headline serving entry)
     P.set_precision("fp32")
     serving = serving_run(bddc, P, wl.n_dof, 0.8 * value / world, 3.0, 5001)
+    serving["at_load"] = {"%.1f" % f: serving_run(bddc, P, wl.n_dof, f * value / world, 3.0, 5001)
+                          for f in (0.5, 1.0)}
 
     # end to end: host buffers (pinned), copies inside the timed call
     P.set_precision("fp32")
