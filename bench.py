@@ -195,6 +195,19 @@ def _kernel_bytes(q, n_top, prec_bytes, K=1):
     return b, flops
 
 
+def bench_config(world):
+    """The workload both arms report (the reference arm times the oracle on a
+    bounded sample of it, stated in its cpu_baseline)."""
+    return {"workload": WORKLOAD, "mesh": "512x512 Q1", "substructures": "32x32 (H/h=16)",
+            "levels": 2, "tau": 10.0, "constraints": "adaptive",
+            "coefficient": "k=1e6 on random one-element channels (~10%), else 1",
+            "rhs": "N(0,1), %d per step (seed %d), solved as %d lockstep groups of %d in flight"
+                   % (BATCH, RHS_SEED, BATCH // GROUP, GROUP),
+            "batch": BATCH, "group": GROUP, "rtol": RTOL, "apply_precision": "fp32",
+            "parallelism": "replicas" if world > 1 else "single GPU",
+            "l2": "512 MiB buffer written between timed steps (untimed)"}
+
+
 def serving_run(bddc, P, n, rate_rhs, seconds, seed):
     """Config 5: a seeded Poisson stream of requests, each with 1-64 N(0,1)
     right-hand sides, offered at rate_rhs right-hand sides per second for
@@ -434,14 +447,7 @@ def gpu_arm(a):
         "warmup": a.warmup, "ms_per_step": t32 * 1e3 / a.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "fp32 apply, fp64 PCG",
         "data": "synthetic (seeded inputs, paper's model problem)",
-        "config": {"workload": WORKLOAD, "mesh": "512x512 Q1", "substructures": "32x32 (H/h=16)",
-                   "levels": 2, "tau": 10.0, "constraints": "adaptive",
-                   "coefficient": "k=1e6 on random one-element channels (~10%), else 1",
-                   "rhs": "N(0,1), %d per step (seed %d), solved as %d lockstep groups of %d in flight"
-                          % (BATCH, RHS_SEED, BATCH // GROUP, GROUP),
-                   "batch": BATCH, "group": GROUP, "rtol": RTOL, "apply_precision": "fp32",
-                   "parallelism": "replicas" if world > 1 else "single GPU",
-                   "l2": "512 MiB buffer written between timed steps (untimed)"},
+        "config": bench_config(world),
         "latency_ms": {"p50": pct(lat, 50), "p99": pct(lat, 99),
                        "what": "one right-hand side per solve, FP32 apply"},
         "serving": serving,
@@ -507,7 +513,7 @@ def reference_arm(a):
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * sum(t) / a.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded inputs, paper's model problem)",
-        "config": {"workload": WORKLOAD},
+        "config": bench_config(1),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
