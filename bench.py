@@ -56,6 +56,8 @@ def _args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch", type=int, default=BATCH,
+                    help="right-hand sides per step (groups of %d, up to three in flight)" % GROUP)
     return ap.parse_args()
 
 
@@ -522,6 +524,9 @@ def reference_arm(a):
 
 if __name__ == "__main__":
     args = _args()
+    if args.batch < 1:
+        raise SystemExit("--batch must be positive")
+    BATCH = args.batch
     if args.impl == "reference":
         reference_arm(args)
     else:

@@ -1001,23 +1001,25 @@ __global__ void k_avg_b(DevLevel L, BatchLevel B, int pidx, const int *skip, uns
 
 // Y = A X, A dense n x n row-major (leading dimension ld, a multiple of 4,
 // zero padded), X and Y interleaved [ld][K] (X zero on rows [n, ld)).  FP64;
-// the FP64 pipe bounds it.  A block of eight warps owns 8 RPW rows; the
-// columns stream in chunks of GM_C through a GM_S-stage ring of bulk copies
-// (the row segments of A and the GM_C x K block of X, contiguous in the
-// interleaved layout), thread 0 refilling a stage once all warps have used
-// it.  Warp w computes rows RPW w .. RPW w + RPW - 1 for all K columns (lane
-// k: column k), reading the A entries by broadcast.  RPW is chosen per
-// problem by the autotuner (gemm_tune).
+// the FP64 pipe bounds it.  A block of NW warps owns `rpb` <= NW RPW rows;
+// the columns stream in chunks of GM_C through a GM_S-stage ring of bulk
+// copies (the row segments of A and the GM_C x K block of X, contiguous in
+// the interleaved layout), thread 0 refilling a stage once all warps have
+// used it.  Warp w computes rows RPW w .. RPW w + RPW - 1 for all K columns
+// (lane k: column k), reading the A entries by broadcast.  The variant is
+// chosen per problem by the autotuner (gemm_tune): eight warps with 8, 16 or
+// 32 rows per block, or sixteen warps with ceil(n / SMs) rows per block, one
+// block per SM, so that no SM does more rows than another.
 constexpr int GM_C = 64, GM_S = 3;
-__host__ __device__ constexpr size_t gm_stage(int rpw) {
-    return (size_t)8 * rpw * GM_C * 8 + (size_t)GM_C * 32 * 8;
+__host__ __device__ constexpr size_t gm_stage(int rows) {
+    return (size_t)rows * GM_C * 8 + (size_t)GM_C * 32 * 8;
 }
 
-template <int RPW>
-__global__ void __launch_bounds__(256) k_gemm_b(int n, int ld, const double *A, const double *X,
-                                                double *Y, int K, const int *skip, int *err) {
-    constexpr int GR = 8 * RPW;
-    constexpr size_t STAGE = gm_stage(RPW);
+template <int RPW, int NW>
+__global__ void __launch_bounds__(32 * NW) k_gemm_b(int n, int ld, const double *A, const double *X,
+                                                    double *Y, int K, int rpb, const int *skip, int *err) {
+    constexpr int GR = NW * RPW;
+    constexpr size_t STAGE = gm_stage(GR);
     extern __shared__ __align__(16) unsigned char smem_g[];
     __shared__ __align__(8) unsigned long long full[GM_S];
     __shared__ int ok_all;
@@ -1025,8 +1027,8 @@ __global__ void __launch_bounds__(256) k_gemm_b(int n, int ld, const double *A, 
     pdl_trigger();
     if (skip && *skip) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int row0 = blockIdx.x * GR;
-    const int nrow = n - row0 < GR ? n - row0 : GR;
+    const int row0 = blockIdx.x * rpb;
+    const int nrow = n - row0 < rpb ? n - row0 : rpb;
     const int nchunk = (ld + GM_C - 1) / GM_C;
     if (threadIdx.x == 0) {
         for (int s = 0; s < GM_S; ++s) mbar_init(&full[s]);
@@ -1674,9 +1676,10 @@ void prepare_batch_kernels() {
     cudaFuncSetAttribute(k_b_dir_spmv<X, Y>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bt_smem(X, Y, kMaxBatch));
     BDDC_TILE_ATTR(16, 8) BDDC_TILE_ATTR(32, 4) BDDC_TILE_ATTR(32, 8) BDDC_TILE_ATTR(8, 16)
 #undef BDDC_TILE_ATTR
-    cudaFuncSetAttribute(k_gemm_b<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(GM_S * gm_stage(1)));
-    cudaFuncSetAttribute(k_gemm_b<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(GM_S * gm_stage(2)));
-    cudaFuncSetAttribute(k_gemm_b<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(GM_S * gm_stage(4)));
+    cudaFuncSetAttribute(k_gemm_b<1, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(GM_S * gm_stage(8)));
+    cudaFuncSetAttribute(k_gemm_b<2, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(GM_S * gm_stage(16)));
+    cudaFuncSetAttribute(k_gemm_b<4, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(GM_S * gm_stage(32)));
+    cudaFuncSetAttribute(k_gemm_b<1, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(GM_S * gm_stage(16)));
 #define BDDC_DIR_BS(T, A, SW)                                   \
     BDDC_SMEM_ATTR_B((k_dir_bs<T, A, SW, false>));              \
     BDDC_SMEM_ATTR_B((k_dir_bs<T, A, SW, true>));
@@ -1711,16 +1714,21 @@ void apply_level_post_b(const DevLevel &L, const BatchLevel &B, int prec, const 
 // Variants the autotuner chooses from.
 constexpr int kTiles[][2] = {{16, 8}, {32, 4}, {32, 8}, {8, 16}};
 constexpr int kNTiles = 4;
-constexpr int kRpw[] = {1, 2, 4};
-constexpr int kNRpw = 3;
+constexpr int kNGemm = 4;          // product variants (launch_gemm_b)
 
 void launch_gemm_b(int n, int ld, const double *A, const double *X, double *Y, int K, const int *skip,
                    int *err, cudaStream_t s, int variant) {
     if (n <= 0) return;
     switch (variant) {
-    case 0: launch_plain(k_gemm_b<1>, (n + 7) / 8, 256, GM_S * gm_stage(1), s, n, ld, A, X, Y, K, skip, err); break;
-    case 2: launch_plain(k_gemm_b<4>, (n + 31) / 32, 256, GM_S * gm_stage(4), s, n, ld, A, X, Y, K, skip, err); break;
-    default: launch_plain(k_gemm_b<2>, (n + 15) / 16, 256, GM_S * gm_stage(2), s, n, ld, A, X, Y, K, skip, err);
+    case 0: launch_plain(k_gemm_b<1, 8>, (n + 7) / 8, 256, GM_S * gm_stage(8), s, n, ld, A, X, Y, K, 8, skip, err); break;
+    case 2: launch_plain(k_gemm_b<4, 8>, (n + 31) / 32, 256, GM_S * gm_stage(32), s, n, ld, A, X, Y, K, 32, skip, err); break;
+    case 3: {
+        const int rpb = gemm_rows(3, n);
+        launch_plain(k_gemm_b<1, 16>, (n + rpb - 1) / rpb, 512, GM_S * gm_stage(16), s, n, ld, A, X, Y, K, rpb, skip,
+                     err);
+        break;
+    }
+    default: launch_plain(k_gemm_b<2, 8>, (n + 15) / 16, 256, GM_S * gm_stage(16), s, n, ld, A, X, Y, K, 16, skip, err);
     }
 }
 
@@ -1742,15 +1750,28 @@ template <class F> float time_launches(F f, int reps, cudaStream_t s) {
 }
 
 int gemm_tune(int n, int ld, const double *A, const double *X, double *Y, int K, int *err, cudaStream_t s) {
+    // BDDC_GEMM_VARIANT=0..3 fixes the variant instead of timing them.  The
+    // timing covers 0..2 only: variant 3 (one sixteen-warp block per SM) is
+    // the fastest alone but takes each SM's slot from the other batches in
+    // flight (measured on the 512^2 channel problem: 0.864 against 0.846 of
+    // the FP64 pipe alone, 1375 against 1426 solves/s with three groups)
+    if (const char *e = std::getenv("BDDC_GEMM_VARIANT"))
+        if (e[0] >= '0' && e[0] < '0' + kNGemm && e[1] == 0) return e[0] - '0';
     int best = 1;
     float tb = 1e30f;
-    for (int v = 0; v < kNRpw; ++v) {
+    for (int v = 0; v < kNGemm - 1; ++v) {
         const float t = time_launches([&] { launch_gemm_b(n, ld, A, X, Y, K, nullptr, err, s, v); }, 3, s);
         if (t < tb) { tb = t; best = v; }
     }
     return best;
 }
-int gemm_rows(int variant) { return 8 * kRpw[variant < 0 || variant >= kNRpw ? 1 : variant]; }
+int gemm_rows(int variant, int n) {
+    if (variant == 3) {                // one block per SM, sixteen warps
+        const int r = (n + num_sms_b() - 1) / num_sms_b();
+        return r < 1 ? 1 : (r > 16 ? 16 : r);
+    }
+    return variant == 0 ? 8 : (variant == 2 ? 32 : 16);
+}
 
 void launch_b_init(int n, int K, const double *b, int64_t ldb, double *x, double *r, double *p,
                    double *part, unsigned *counter, BatchScalars *sc, double tol, int maxit,

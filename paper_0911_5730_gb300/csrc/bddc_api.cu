@@ -1096,7 +1096,7 @@ BatchWs &batch_ws(bddc_ctx *C, Workspace &W) {
             dir_spmv_tile(C->tile_v, &tx, &ty);
             C->tuned[0] = tx;
             C->tuned[1] = ty;
-            C->tuned[2] = gemm_rows(C->gemm_v);
+            C->tuned[2] = gemm_rows(C->gemm_v, C->n_top);
         }
         bw->tile_v = C->tile_v;
         bw->gemm_v = C->gemm_v;

@@ -282,7 +282,7 @@ void launch_gemm_b(int n, int ld, const double *A, const double *X, double *Y, i
 // Autotuning: time every variant on the given (scratch) operands and return
 // the fastest.  Y is overwritten.
 int gemm_tune(int n, int ld, const double *A, const double *X, double *Y, int K, int *err, cudaStream_t s);
-int gemm_rows(int variant);
+int gemm_rows(int variant, int n);   // rows per block of a product variant
 // PCG for a batch; b in the caller's layout (column k at b + k * ldb)
 // x = 0, r = b, p0 = 0, per-right-hand-side scalars, step = 0
 void launch_b_init(int n, int K, const double *b, int64_t ldb, double *x, double *r, double *p0,
