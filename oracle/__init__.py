@@ -4,7 +4,9 @@ TEST INFRASTRUCTURE ONLY.  Plain NumPy/SciPy, dense per-substructure
 matrices, loops over substructures and edges, written from the paper's
 definitions so that a reader can check it against the text by eye:
 
-* ``fem``       - Q1 model problem of Sec. 2, eq. (1).
+* ``fem``       - Q1 model problem of Sec. 2, eq. (1), and plane linear
+                  elasticity with bilinear elements (the problem of the
+                  experiments of Sec. 5).
 * ``levels``    - substructures, interface, corners / edges, stiffness
                   weights (Sec. 2, 2.1).
 * ``bddc``      - coarse degrees of freedom, coarse basis, the multilevel

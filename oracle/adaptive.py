@@ -159,8 +159,10 @@ def adaptive_dofs(lv: Level, initial: list[CoarseDof], tau: float,
             Q, R = np.linalg.qr(rows.T)
             d = np.abs(np.diag(R))
             keep = d > DROP_TOL * d.max() if d.size else np.zeros(0, bool)
+            cs = np.unique(lv.comp[edofs])
+            comp = int(cs[0]) if len(cs) == 1 else -1        # mixed components: -1
             for j in np.nonzero(keep)[0]:
-                out.append(CoarseDof(edofs.copy(), Q[:, j].copy(), (s, t), "adaptive"))
+                out.append(CoarseDof(edofs.copy(), Q[:, j].copy(), (s, t), "adaptive", comp))
                 kept += 1
         reps.append({"pair": (s, t), "n_edge": len(edofs), "lam": pp.lam.copy(),
                      "n_sel": nst, "n_kept": kept, "omega": omega,

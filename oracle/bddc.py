@@ -28,27 +28,41 @@ from .levels import Level
 
 @dataclasses.dataclass
 class CoarseDof:
-    """One global coarse DOF: the functional u -> sum_k weights[k] * u[dofs[k]]."""
+    """One global coarse DOF: the functional u -> sum_k weights[k] * u[dofs[k]].
+
+    ``comp`` is the displacement component it measures (-1: mixed) and
+    ``bnd`` whether it is a point value on the boundary of the domain; both
+    carry over to the DOFs of the next level."""
     dofs: np.ndarray
     weights: np.ndarray
     subs: tuple
     kind: str
+    comp: int = 0
+    bnd: bool = False
 
 
 def corner_dofs(lv: Level) -> list[CoarseDof]:
-    return [CoarseDof(np.array([g]), np.array([1.0]), lv.subs_of[g], "corner")
+    return [CoarseDof(np.array([g]), np.array([1.0]), lv.subs_of[g], "corner",
+                      int(lv.comp[g]), bool(lv.bnd[g]))
             for g in lv.corners]
 
 
 def edge_average_dofs(lv: Level) -> list[CoarseDof]:
-    """One arithmetic average over the non-corner DOFs of every edge (Table 1, c+e)."""
-    return [CoarseDof(d, np.full(len(d), 1.0 / len(d)), pair, "edge")
-            for pair, d in lv.edges]
+    """One arithmetic average per edge and displacement component over the
+    edge's non-corner DOFs (Table 1, c+e: 13818 - 4794 = 2 averages on each
+    of the 2 * 48 * 47 edges)."""
+    out = []
+    for pair, d in lv.edges:
+        for c in np.unique(lv.comp[d]):
+            sel = d[lv.comp[d] == c]
+            out.append(CoarseDof(sel, np.full(len(sel), 1.0 / len(sel)), pair, "edge", int(c)))
+    return out
 
 
 def all_interface_dofs(lv: Level) -> list[CoarseDof]:
     """Every interface DOF is a coarse DOF: then W~ = U and BDDC is exact."""
-    return [CoarseDof(np.array([g]), np.array([1.0]), lv.subs_of[g], "all")
+    return [CoarseDof(np.array([g]), np.array([1.0]), lv.subs_of[g], "all",
+                      int(lv.comp[g]), bool(lv.bnd[g]))
             for g in np.nonzero(lv.is_interface)[0]]
 
 
@@ -105,7 +119,8 @@ class BDDCLevel:
 
     def next_level(self, sub_to_next, nsub_next: int) -> Level:
         """Level l+1: level-l substructures become elements (Sec. 2.1)."""
-        return Level(self.nc, self.Rc, self.Ac, sub_to_next, nsub_next)
+        return Level(self.nc, self.Rc, self.Ac, sub_to_next, nsub_next,
+                     [cd.comp for cd in self.cdofs], [cd.bnd for cd in self.cdofs])
 
     # -- pieces of Algorithm 1 -----------------------------------------------------
     def interior_solve(self, r: np.ndarray) -> np.ndarray:
@@ -192,14 +207,20 @@ def coarse_dofs_for(lv: Level, mode: str, tau: float = np.inf, report: dict | No
 
 def build(nx: int, k, elem_to_sub, nsub1: int, levels: int = 2, mode: str = "corners",
           tau: float = np.inf, sub1_to_sub2=None, nsub2: int = 0,
-          modes: list | None = None) -> Hierarchy:
-    """Set up the hierarchy of Algorithm 2 for the Q1 model problem.
+          modes: list | None = None, problem: str = "diffusion", lame=(1.0, 2.0),
+          clamp: str = "left") -> Hierarchy:
+    """Set up the hierarchy of Algorithm 2 for the Q1 model problem, or for
+    plane elasticity (``problem="elasticity"``, Lame parameters k_e * lame,
+    clamped as ``clamp`` says).
 
     ``modes`` overrides ``mode`` per BDDC level (used by the consistency pins).
     """
-    from .levels import level_one
+    from .levels import level_one, level_one_elasticity
     modes = modes or [mode] * (levels - 1)
-    lv = level_one(nx, k, elem_to_sub, nsub1)
+    if problem == "elasticity":
+        lv = level_one_elasticity(nx, k, elem_to_sub, nsub1, lame[0], lame[1], clamp)
+    else:
+        lv = level_one(nx, k, elem_to_sub, nsub1)
     bls, info = [], {"omega": [], "edge_reports": []}
     groupings = [(sub1_to_sub2, nsub2)]
     for l in range(levels - 1):
@@ -219,5 +240,12 @@ def build(nx: int, k, elem_to_sub, nsub1: int, levels: int = 2, mode: str = "cor
 
 
 def build_workload(wl, **kw) -> Hierarchy:
+    problem = getattr(wl, "problem", "diffusion")
+    if problem == "elasticity":
+        kw.setdefault("problem", "elasticity")
+        kw.setdefault("lame", wl.lame)
+        kw.setdefault("clamp", wl.clamp)
+    if getattr(wl, "constraints_level2", None) and wl.levels == 3:
+        kw.setdefault("modes", [wl.constraints, wl.constraints_level2])
     return build(wl.nx, wl.k, wl.elem_to_sub, wl.n_sub1, wl.levels, wl.constraints,
                  wl.tau, wl.sub1_to_sub2, wl.n_sub2, **kw)

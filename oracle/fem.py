@@ -86,3 +86,88 @@ def load_vector(nx: int, f=lambda x, y: 1.0) -> np.ndarray:
                     if nodes[a] >= 0:
                         b[nodes[a]] += 0.25 * h * h * fv * phi[a]
     return b
+
+
+# -- plane linear elasticity (the problem of the experiments of Sec. 5) --------
+
+def elasticity_reference_stiffness(lam: float, mu: float) -> np.ndarray:
+    """Element stiffness of a(u, v) = int lam div u div v + 2 mu eps(u):eps(v)
+    for a square bilinear element, plane strain.
+
+    DOF order 2a + c: node a in (0,0), (1,0), (1,1), (0,1), component c (x, y).
+    In 2D the matrix does not depend on the element size.  Strains in Voigt
+    form (eps_xx, eps_yy, 2 eps_xy) = B u with the material matrix
+    [[lam + 2mu, lam, 0], [lam, lam + 2mu, 0], [0, 0, mu]]; the 2 x 2 Gauss
+    rule is exact (the integrand is at most quadratic in each variable).
+    """
+    D = np.array([[lam + 2 * mu, lam, 0.0], [lam, lam + 2 * mu, 0.0], [0.0, 0.0, mu]])
+    gp = np.array([0.5 - 0.5 / np.sqrt(3.0), 0.5 + 0.5 / np.sqrt(3.0)])
+    K = np.zeros((8, 8))
+    for x in gp:
+        for y in gp:
+            dx = np.array([-(1 - y), 1 - y, y, -y])
+            dy = np.array([-(1 - x), -x, x, 1 - x])
+            B = np.zeros((3, 8))
+            B[0, 0::2] = dx
+            B[1, 1::2] = dy
+            B[2, 0::2] = dy
+            B[2, 1::2] = dx
+            K += 0.25 * B.T @ D @ B
+    return K
+
+
+def elastic_node_index(nx: int, i: int, j: int, clamp: str = "left") -> int:
+    """Node (i, j) -> free node number, or -1 on the clamped side.
+
+    ``clamp="left"``: the nodes with i = 0 (x = 0) are clamped (u = 0), node
+    (i, j) with 1 <= i <= nx is j * nx + (i - 1).  ``clamp="none"``: no node
+    is removed (the mesh before boundary conditions), node (i, j) is
+    j * (nx + 1) + i.  DOF of component c of a node: 2 * node + c.
+    """
+    if clamp == "left":
+        return -1 if i <= 0 else j * nx + (i - 1)
+    return j * (nx + 1) + i
+
+
+def elasticity_elements(nx: int, k: np.ndarray, lam: float, mu: float, clamp: str = "left"):
+    """Element DOF lists and matrices k_e * K_ref of the elasticity problem.
+
+    Returns (elem_dofs, elem_mats, n, comp, on_boundary, coords): per DOF its
+    component, whether its node lies on the boundary of the square (the
+    clamped nodes are gone, so these are the traction-free ones) and its
+    node's coordinates.
+    """
+    kref = elasticity_reference_stiffness(lam, mu)
+    h = 1.0 / nx
+    nodes_i = range(1, nx + 1) if clamp == "left" else range(0, nx + 1)
+    nn = (nx + 1) * len(nodes_i)
+    comp = np.tile([0, 1], nn)
+    bnd = np.zeros(2 * nn, dtype=bool)
+    coords = np.zeros((2 * nn, 2))
+    for j in range(nx + 1):
+        for i in nodes_i:
+            a = elastic_node_index(nx, i, j, clamp)
+            on = i == 0 or j == 0 or i == nx or j == nx
+            bnd[2 * a:2 * a + 2] = on
+            coords[2 * a:2 * a + 2] = (i * h, j * h)
+    dofs, mats = [], []
+    for e in range(nx * nx):
+        ej, ei = divmod(e, nx)
+        nd = [elastic_node_index(nx, ei, ej, clamp), elastic_node_index(nx, ei + 1, ej, clamp),
+              elastic_node_index(nx, ei + 1, ej + 1, clamp), elastic_node_index(nx, ei, ej + 1, clamp)]
+        slots = np.array([2 * a + c if a >= 0 else -1 for a in nd for c in (0, 1)])
+        keep = slots >= 0
+        dofs.append(slots[keep])
+        mats.append(k[e] * kref[np.ix_(keep, keep)])
+    return dofs, mats, 2 * nn, comp, bnd, coords
+
+
+def rigid_modes(coords: np.ndarray, comp: np.ndarray) -> np.ndarray:
+    """The three rigid motions (two translations, the rotation (-y, x)) at
+    every DOF, as columns."""
+    Z = np.zeros((len(comp), 3))
+    Z[comp == 0, 0] = 1.0
+    Z[comp == 1, 1] = 1.0
+    Z[comp == 0, 2] = -coords[comp == 0, 1]
+    Z[comp == 1, 2] = coords[comp == 1, 0]
+    return Z

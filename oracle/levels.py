@@ -14,7 +14,12 @@ Readings of the paper used here:
   otherwise it is interior (the space U_I of Sec. 2).
 * A corner is a DOF in three or more substructures (Sec. 2: substructure
   vertices; on level >= 2 the level-1 corners shared by >= 3 level-2
-  substructures, Sec. 2.1, Sec. 4 "variable number of nodes per element").
+  substructures, Sec. 2.1, Sec. 4 "variable number of nodes per element"),
+  or an interface DOF on the boundary of the domain (where an edge meets a
+  traction-free side; the counts of Tables 1-2, e.g. 4794 = 2 (49^2 - 4)
+  for 48 x 48 substructures, include those vertices).  With zero Dirichlet
+  data on the whole boundary, as in the diffusion problem, no such DOF
+  exists.
 * An edge is a connected chain of non-corner interface DOFs shared by the
   same pair of substructures (Sec. 3: adjacent substructures share an edge).
 * The averaging weights are the standard stiffness scaling named in Sec. 1:
@@ -30,8 +35,14 @@ from . import fem
 
 
 class Level:
-    def __init__(self, n: int, elem_dofs, elem_mats, elem_sub, nsub: int):
+    """``dof_comp``: displacement component of each DOF (0 for a scalar
+    problem); ``dof_bnd``: the DOF lies on the boundary of the domain."""
+
+    def __init__(self, n: int, elem_dofs, elem_mats, elem_sub, nsub: int,
+                 dof_comp=None, dof_bnd=None):
         self.n = int(n)
+        self.comp = np.zeros(self.n, np.int64) if dof_comp is None else np.asarray(dof_comp, np.int64)
+        self.bnd = np.zeros(self.n, bool) if dof_bnd is None else np.asarray(dof_bnd, bool)
         self.elem_dofs = [np.asarray(d, dtype=np.int64) for d in elem_dofs]
         self.elem_mats = [np.asarray(m, dtype=np.float64) for m in elem_mats]
         self.elem_sub = np.asarray(elem_sub, dtype=np.int64)
@@ -70,7 +81,7 @@ class Level:
     # -- interface, corners and edges -------------------------------------------
     def _classify(self):
         self.is_interface = self.mult >= 2
-        self.is_corner = self.mult >= 3
+        self.is_corner = (self.mult >= 3) | (self.is_interface & self.bnd)
         # DOF adjacency: two DOFs are neighbours when an element holds both.
         rows, cols = [], []
         for d in self.elem_dofs:
@@ -123,3 +134,12 @@ class Level:
 def level_one(nx: int, k, elem_to_sub, nsub: int) -> Level:
     dofs, mats = fem.level1_elements(nx, np.asarray(k, dtype=np.float64))
     return Level((nx - 1) ** 2, dofs, mats, elem_to_sub, nsub)
+
+
+def level_one_elasticity(nx: int, k, elem_to_sub, nsub: int, lam: float = 1.0, mu: float = 2.0,
+                         clamp: str = "left") -> Level:
+    dofs, mats, n, comp, bnd, coords = fem.elasticity_elements(
+        nx, np.asarray(k, dtype=np.float64), lam, mu, clamp)
+    lv = Level(n, dofs, mats, elem_to_sub, nsub, comp, bnd)
+    lv.coords = coords
+    return lv

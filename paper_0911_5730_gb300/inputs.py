@@ -1,4 +1,5 @@
-"""Seeded synthetic workloads for the 2D Q1 diffusion model problem.
+"""Seeded synthetic workloads for the 2D Q1 diffusion model problem and for
+plane linear elasticity (the problem of the paper's experiments, Sec. 5).
 
 This module only draws inputs: coefficient fields, decompositions and
 right-hand sides.  It holds none of the BDDC arithmetic, so both the CPU
@@ -209,6 +210,29 @@ def unit_load_rhs(nx: int) -> np.ndarray:
     return np.full((nx - 1) * (nx - 1), h * h)
 
 
+def elasticity_n_dof(nx: int, clamp: str = "left") -> int:
+    """Free DOFs of the plane elasticity problem: two per node, the nodes on
+    the clamped side x = 0 removed (``clamp="left"``) or none (``"none"``)."""
+    return 2 * (nx + 1) * (nx if clamp == "left" else nx + 1)
+
+
+def body_force_rhs(nx: int, clamp: str = "left", f=(0.0, -1.0)) -> np.ndarray:
+    """Load vector of a constant body force f for bilinear elements: every
+    element adds f h^2 / 4 to each of its four nodes (the integral of a hat
+    function over one element).  DOF order: 2 * node + component, node
+    numbering as in ``elasticity`` workloads."""
+    h = 1.0 / nx
+    cnt = np.zeros((nx + 1, nx + 1))                   # [j, i]: elements touching node (i, j)
+    cnt[:-1, :-1] += 1; cnt[:-1, 1:] += 1; cnt[1:, :-1] += 1; cnt[1:, 1:] += 1
+    if clamp == "left":
+        cnt = cnt[:, 1:]
+    w = (cnt * (h * h / 4.0)).reshape(-1)
+    b = np.empty(2 * w.size)
+    b[0::2] = f[0] * w
+    b[1::2] = f[1] * w
+    return b
+
+
 @dataclasses.dataclass
 class Workload:
     name: str
@@ -222,14 +246,23 @@ class Workload:
     sub1_to_sub2: np.ndarray | None = None
     n_sub2: int = 0
     rhs_seed: int | None = None
+    # "diffusion": scalar -div(k grad u) = f, zero Dirichlet data on the whole
+    # boundary.  "elasticity": plane strain with Lame parameters k_e * lame,
+    # clamped on x = 0 (``clamp``), traction free elsewhere.
+    problem: str = "diffusion"
+    lame: tuple = (1.0, 2.0)
+    clamp: str = "left"
+    constraints_level2: str | None = None
 
     @property
     def n_dof(self) -> int:
+        if self.problem == "elasticity":
+            return elasticity_n_dof(self.nx, self.clamp)
         return (self.nx - 1) ** 2
 
     def rhs(self, nrhs: int | None = None) -> np.ndarray:
         if self.rhs_seed is None:
-            b = unit_load_rhs(self.nx)
+            b = body_force_rhs(self.nx, self.clamp) if self.problem == "elasticity" else unit_load_rhs(self.nx)
             return b if nrhs is None else np.tile(b, (nrhs, 1))
         return normal_rhs(self.n_dof, self.rhs_seed, nrhs)
 
@@ -272,3 +305,80 @@ def three_level_voronoi(nx: int = 2048, cells: int = 64, group: int = 8, tau: fl
                     nx, block_log_uniform_coefficient(nx, 8, coef_seed), e2s, ns, levels, tau,
                     "adaptive", s2, n2, rhs_seed=rhs_seed)
 
+
+
+def jagged_grid_decomposition(nx: int, sub: int, pair=(1, 0), amp: int = 2, period: int = 2):
+    """A grid of ``sub x sub`` element blocks with one jagged edge.
+
+    The horizontal edge above substructure ``pair = (si, sj)`` (between it and
+    the one above) becomes a comb: along the edge, leaving ``period`` element
+    columns straight at each end, in runs of ``period`` columns, the boundary
+    is pushed alternately ``amp`` element rows up (the lower substructure takes
+    them) and ``amp`` rows down (the upper one takes them).  Both substructures
+    stay connected, the edge keeps its two end points, and no other
+    substructure meets it (``amp < sub``).  The paper's figure of its jagged
+    edge is not available, so this geometry stands in for it.
+    """
+    e2s, ns = grid_decomposition(nx, sub)
+    m = nx // sub
+    si, sj = pair
+    lo, hi = sj * m + si, (sj + 1) * m + si
+    y0 = (sj + 1) * sub                       # element row where the upper substructure starts
+    e = e2s.reshape(nx, nx).copy()            # [ej, ei]
+    for c in range(period, sub - period):
+        ei = si * sub + c
+        if ((c - period) // period) % 2 == 0:
+            e[y0:y0 + amp, ei] = lo
+        else:
+            e[y0 - amp:y0, ei] = hi
+    return e.reshape(-1).astype(np.int32), ns
+
+
+def jagged_grid_grouping(n_sub_side: int, group: int, pair=(1, 0), amp: int = 1, period: int = 2):
+    """``grid_grouping`` with the horizontal level-2 edge above level-2
+    substructure ``pair`` made a comb of level-1 substructures, as in
+    ``jagged_grid_decomposition``."""
+    s2, n2 = grid_grouping(n_sub_side, group)
+    m = n_sub_side // group
+    si, sj = pair
+    lo, hi = sj * m + si, (sj + 1) * m + si
+    y0 = (sj + 1) * group
+    g = s2.reshape(n_sub_side, n_sub_side).copy()
+    for c in range(period, group - period):
+        x = si * group + c
+        if ((c - period) // period) % 2 == 0:
+            g[y0:y0 + amp, x] = lo
+        else:
+            g[y0 - amp:y0, x] = hi
+    return g.reshape(-1).astype(np.int32), n2
+
+
+def elasticity(nx: int = 768, sub: int = 16, levels: int = 2, group: int = 16,
+               constraints: str = "adaptive", tau: float = 10.0, jagged: bool = True,
+               rhs_seed: int | None = None, k=None, lame=(1.0, 2.0),
+               constraints_level2: str | None = None) -> Workload:
+    """The setting of the paper's experiments (Sec. 5): plane linear elasticity
+    with lambda = 1, mu = 2 on the unit square, 768 x 768 bilinear elements cut
+    into 48 x 48 substructures (H/h = 16) and, for three levels, into 3 x 3
+    level-2 substructures of 16 x 16 level-1 ones; one level-1 edge (between
+    substructures 1 and 1 + 48, the pair the paper numbers (2, 50)) and, for
+    three levels, one level-2 edge (level-2 substructures 1 and 4, the paper's
+    (2, 5)) jagged.  Clamped on x = 0, body force (0, -1) unless ``rhs_seed``
+    asks for N(0, 1) loads; ``k`` scales the Lame parameters per element
+    (default 1)."""
+    m = nx // sub
+    if jagged:
+        e2s, ns = jagged_grid_decomposition(nx, sub, (1, 0))
+    else:
+        e2s, ns = grid_decomposition(nx, sub)
+    s2, n2 = None, 0
+    if levels == 3:
+        if jagged:
+            s2, n2 = jagged_grid_grouping(m, group, (1, 0))
+        else:
+            s2, n2 = grid_grouping(m, group)
+    kk = constant_coefficient(nx) if k is None else np.asarray(k, dtype=np.float64)
+    name = "elasticity_%d_%dlev" % (nx, levels)
+    return Workload(name, nx, kk, e2s, ns, levels, tau, constraints, s2, n2, rhs_seed=rhs_seed,
+                    problem="elasticity", lame=tuple(lame), clamp="left",
+                    constraints_level2=constraints_level2)
