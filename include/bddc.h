@@ -7,10 +7,15 @@
  *
  *     -div(k grad u) = f  on the unit square,  u = 0 on the boundary    (Sec. 2, eq. 1)
  *
+ * or to plane linear elasticity with bilinear elements, clamped on one side
+ * (the problem of the experiments of Sec. 5; see bddc_mesh).
+ *
  * Conventions shared by every entry point:
- *   - Mesh: nx * nx square Q1 elements, h = 1/nx.  Element (ei, ej) has flat
- *     index e = ej*nx + ei.  Free node (i, j), 1 <= i, j <= nx-1, has global
- *     index g = (j-1)*(nx-1) + (i-1); a level-1 vector has n = (nx-1)^2 entries.
+ *   - Mesh: nx * nx square elements, h = 1/nx.  Element (ei, ej) has flat
+ *     index e = ej*nx + ei.  Diffusion: free node (i, j), 1 <= i, j <= nx-1,
+ *     has global index g = (j-1)*(nx-1) + (i-1); a level-1 vector has
+ *     n = (nx-1)^2 entries.  Elasticity: n = 2 nx (nx+1), numbered as
+ *     bddc_mesh says.
  *   - Every function returns an int status: BDDC_OK (0) or a negative
  *     BDDC_E_* code; bddc_last_error() then gives a message for the calling
  *     thread.  No function aborts, exits or traps.
@@ -58,9 +63,27 @@ enum {
  * The top-level coarse solve and PCG are FP64 in every mode. */
 enum { BDDC_PREC_FP64 = 0, BDDC_PREC_FP32 = 1, BDDC_PREC_BF16 = 2 };
 
+/* The problem on the mesh.  Diffusion: -div(k grad u) = f with Q1 elements
+ * and zero Dirichlet data on every side (Sec. 2, eq. 1); one DOF per free
+ * node, node (i, j), 1 <= i, j <= nx-1, is DOF (j-1)(nx-1) + (i-1).
+ * Elasticity: plane-strain linear elasticity with bilinear elements and Lame
+ * parameters k_e * (lame_lambda, lame_mu) on element e (the problem of the
+ * experiments of Sec. 5); two DOFs per node, DOF 2 * node + c for component c
+ * (0: x, 1: y).  With BDDC_CLAMP_LEFT the nodes on x = 0 are clamped and
+ * node (i, j), 1 <= i <= nx, 0 <= j <= nx, is j * nx + (i - 1), so there are
+ * n = 2 nx (nx + 1) DOFs; the other sides are traction free.
+ * BDDC_CLAMP_NONE keeps every node (node (i, j) is j (nx + 1) + i): the mesh
+ * before boundary conditions, which bddc_inspect accepts for counting only. */
+enum { BDDC_PROBLEM_DIFFUSION = 0, BDDC_PROBLEM_ELASTICITY = 1 };
+enum { BDDC_CLAMP_ALL = 0, BDDC_CLAMP_LEFT = 1, BDDC_CLAMP_NONE = 2 };
+
 typedef struct {
     int32_t nx;           /* elements per side (square mesh) */
     int32_t ny;           /* must equal nx */
+    int32_t problem;      /* BDDC_PROBLEM_*; zero-initialised = diffusion */
+    int32_t clamp;        /* BDDC_CLAMP_*: ALL for diffusion, LEFT for elasticity */
+    double lame_lambda;   /* elasticity only: lambda >= 0 */
+    double lame_mu;       /* elasticity only: mu > 0 */
 } bddc_mesh;
 
 typedef struct {
@@ -271,9 +294,11 @@ int bddc_query(const bddc_ctx *ctx, bddc_info *info, int level, int32_t *n_selec
 /*
  * bddc_inspect - host-only classification of a level-1 decomposition (no
  * device work): interface, corners and edges as in Sec. 2 and Sec. 3
- * (corners = DOFs in >= 3 substructures, edges = connected chains of the
- * other interface DOFs shared by one pair), and the interior block size the
- * setup would use.
+ * (corners = DOFs in >= 3 substructures or interface DOFs on the boundary of
+ * the domain, edges = connected chains of the other interface DOFs shared by
+ * one pair), and the interior block size the setup would use.  For
+ * elasticity every count is in DOFs (two per node) and an edge holds both
+ * components; c+e puts one average per edge and component.
  *   n_corners, n_edges : outputs (may be NULL).
  *   edge_pairs         : host [max_edges * 2] or NULL: (s, t) per edge, in
  *                        the numbering of bddc_query.
@@ -288,8 +313,8 @@ int bddc_inspect(const bddc_mesh *mesh, const bddc_decomp *decomp, int32_t *n_co
                  int32_t *block_size);
 
 /*
- * bddc_operator - y = A x for the level-1 Q1 operator (device FP64 [n]); the
- * matrix-free SpMV used by PCG.
+ * bddc_operator - y = A x for the level-1 operator (device FP64 [n]): the Q1
+ * stencil or the matrix-free elasticity operator, the product PCG uses.
  */
 int bddc_operator(bddc_ctx *ctx, const double *x_dev, double *y_dev, void *stream);
 

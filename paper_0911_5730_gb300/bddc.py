@@ -30,8 +30,19 @@ SYMBOLS = ["bddc_setup", "bddc_apply", "bddc_pcg_solve", "bddc_pcg_solve_host", 
            "bddc_partition_graph", "bddc_partition_mesh", "bddc_group_substructures"]
 
 
+PROBLEM = {"diffusion": 0, "elasticity": 1}
+CLAMP = {"all": 0, "left": 1, "none": 2}
+
+
 class Mesh(C.Structure):
-    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32)]
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("problem", C.c_int32), ("clamp", C.c_int32),
+                ("lame_lambda", C.c_double), ("lame_mu", C.c_double)]
+
+
+def _mesh(nx, problem="diffusion", clamp=None, lame=(1.0, 2.0)):
+    if clamp is None:
+        clamp = "left" if problem == "elasticity" else "all"
+    return Mesh(int(nx), int(nx), PROBLEM[problem], CLAMP[clamp], float(lame[0]), float(lame[1]))
 
 
 class Decomp(C.Structure):
@@ -131,17 +142,20 @@ def _ptr(t):
     return C.c_void_p(t.data_ptr())
 
 
-def inspect(nx, elem_to_sub, n_sub1):
-    """Host-only classification of a level-1 decomposition (no GPU needed)."""
+def inspect(nx, elem_to_sub, n_sub1, problem="diffusion", clamp=None):
+    """Host-only classification of a level-1 decomposition (no GPU needed);
+    for elasticity, ``clamp="none"`` classifies the mesh before boundary
+    conditions."""
     lib = load()
+    mesh = _mesh(nx, problem, clamp)
     e2s = np.ascontiguousarray(elem_to_sub, dtype=np.int32)
     dec = Decomp(e2s.ctypes.data_as(C.POINTER(C.c_int32)), int(n_sub1), None, 0)
     nc, ne, bs = C.c_int32(), C.c_int32(), C.c_int32()
-    _check(lib.bddc_inspect(C.byref(Mesh(nx, nx)), C.byref(dec), C.byref(nc), C.byref(ne),
+    _check(lib.bddc_inspect(C.byref(mesh), C.byref(dec), C.byref(nc), C.byref(ne),
                             None, None, 0, C.byref(bs)))
     pairs = np.zeros((max(ne.value, 1), 2), np.int32)
     lens = np.zeros(max(ne.value, 1), np.int32)
-    _check(lib.bddc_inspect(C.byref(Mesh(nx, nx)), C.byref(dec), None, None,
+    _check(lib.bddc_inspect(C.byref(mesh), C.byref(dec), None, None,
                             pairs.ctypes.data_as(C.c_void_p), lens.ctypes.data_as(C.c_void_p),
                             ne.value, None))
     return {"n_corners": nc.value, "n_edges": ne.value, "edge_pairs": pairs[:ne.value],
@@ -217,15 +231,20 @@ def partitioned_workload(base, n_sub1, n_sub2=0, seed=0, weighted=True, imbalanc
 
 
 class Problem:
-    """One problem (mesh, coefficient, decomposition) set up on the GPU."""
+    """One problem (mesh, coefficient, decomposition) set up on the GPU.
+
+    ``problem="elasticity"``: plane strain with Lame parameters k_e * lame,
+    clamped on x = 0, two DOFs per node (see ``bddc_mesh`` in the header)."""
 
     def __init__(self, nx, k, elem_to_sub, n_sub1, levels=2, tau=math.inf,
                  constraints="corners+edges", precision="fp64", sub1_to_sub2=None, n_sub2=0,
-                 constraints_level2=None, hbm_budget=0, stream=None):
+                 constraints_level2=None, hbm_budget=0, stream=None, problem="diffusion",
+                 lame=(1.0, 2.0)):
         lib = load()
         self._lib = lib
         self.nx = int(nx)
-        self.n = (self.nx - 1) ** 2
+        self.problem = problem
+        self.n = 2 * self.nx * (self.nx + 1) if problem == "elasticity" else (self.nx - 1) ** 2
         k = np.ascontiguousarray(k, dtype=np.float64)
         e2s = np.ascontiguousarray(elem_to_sub, dtype=np.int32)
         self._keep = [k, e2s]
@@ -240,13 +259,18 @@ class Problem:
                     -1 if constraints_level2 is None else CONSTRAINTS[constraints_level2],
                     PRECISION[precision], 0, int(hbm_budget))
         h = C.c_void_p()
-        _check(lib.bddc_setup(C.byref(Mesh(self.nx, self.nx)), k.ctypes.data_as(C.c_void_p),
+        _check(lib.bddc_setup(C.byref(_mesh(self.nx, problem, None, lame)), k.ctypes.data_as(C.c_void_p),
                               C.byref(dec), int(levels), float(tau), C.byref(opts),
                               C.c_void_p(_stream_ptr(stream)), C.byref(h)))
         self.h = h
 
     @classmethod
     def from_workload(cls, wl, precision="fp64", **kw):
+        if getattr(wl, "problem", "diffusion") == "elasticity":
+            kw.setdefault("problem", "elasticity")
+            kw.setdefault("lame", wl.lame)
+        if getattr(wl, "constraints_level2", None) and wl.levels == 3:
+            kw.setdefault("constraints_level2", wl.constraints_level2)
         return cls(wl.nx, wl.k, wl.elem_to_sub, wl.n_sub1, wl.levels, wl.tau, wl.constraints,
                    precision, wl.sub1_to_sub2, wl.n_sub2, **kw)
 

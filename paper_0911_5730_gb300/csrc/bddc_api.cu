@@ -45,6 +45,8 @@ struct CDof {
     std::vector<double> w;
     int s = -1, t = -1;      // edge functionals: the pair sharing it; -1 for point DOFs
     bool point = false;
+    int comp = 0;            // displacement component it measures, -1 mixed
+    bool bnd = false;        // a point value on the boundary of the domain
 };
 
 struct LevelData {
@@ -58,7 +60,9 @@ struct LevelData {
     std::vector<std::vector<int>> rc;   // per sub: global coarse ids
     std::vector<int64_t> offAc;
     double *ac = nullptr;              // device coarse element matrices (setup arena)
-    std::vector<double> cz;            // constant function on the coarse DOFs
+    std::vector<double> cz;            // [nz][nc]: the null vectors on the coarse DOFs
+    std::vector<int> ccomp;            // component of each coarse DOF (-1 mixed)
+    std::vector<char> cbnd;            // coarse DOF is a point value on the boundary
     int nc = 0;
     int64_t sumI = 0, sumG = 0, sumC = 0, bandnnz = 0, blockent = 0, coonnz = 0, nent = 0, pent = 0;
 };
@@ -143,6 +147,9 @@ using namespace bddc;
 
 struct bddc_ctx {
     int nx = 0, levels = 2;
+    int problem = BDDC_PROBLEM_DIFFUSION;
+    int64_t n_dof = 0;                // level-1 DOFs (length of every solution vector)
+    ElOp el;                          // the operator of the elasticity problem
     double tau = INFINITY;
     bddc_opts opts{};
     int prec = BDDC_PREC_FP64;
@@ -164,12 +171,39 @@ struct bddc_ctx {
     std::mutex tune_mu;
     double setup_ms = 0.0;
     std::mutex mu;
-    int n() const { return (nx - 1) * (nx - 1); }
+    int n() const { return (int)n_dof; }
 };
 
 namespace bddc {
 
 namespace {
+
+// The operator A of the PCG iteration: the Q1 diffusion stencil or the
+// matrix-free plane-elasticity operator.
+bool elastic(const bddc_ctx *C) { return C->problem == BDDC_PROBLEM_ELASTICITY; }
+void op_spmv(const bddc_ctx *C, const double *x, double *y, cudaStream_t st) {
+    if (elastic(C)) launch_el_spmv(C->el, x, y, st);
+    else launch_q1_spmv(C->nx, C->w_dev, x, y, st);
+}
+void op_residual(const bddc_ctx *C, const double *b, const double *x, double *res, cudaStream_t st) {
+    if (elastic(C)) launch_el_residual(C->el, b, x, res, st);
+    else launch_residual(C->nx, C->w_dev, b, x, res, st);
+}
+void op_dir_spmv(const bddc_ctx *C, const double *z, double *p0, double *p1, double *q, double *part,
+                 unsigned *counter, PcgScalars *sc, double *alphas, cudaStream_t st) {
+    if (elastic(C)) launch_el_dir_spmv(C->el, z, p0, p1, q, part, counter, sc, alphas, st);
+    else launch_pcg_dir_spmv(C->nx, C->w_dev, z, p0, p1, q, part, counter, sc, alphas, st);
+}
+void op_b_dir_spmv(const bddc_ctx *C, int K, const double *z, double *p0, double *p1, double *q, double *part,
+                   unsigned *counter, BatchScalars *sc, double *alphas, cudaStream_t st, int tile_v) {
+    if (elastic(C)) launch_el_b_dir_spmv(C->el, K, z, p0, p1, q, part, counter, sc, alphas, st);
+    else launch_b_dir_spmv(C->nx, K, C->w_dev, z, p0, p1, q, part, counter, sc, alphas, st, tile_v);
+}
+void op_b_residual(const bddc_ctx *C, int K, const double *b, int64_t ldb, const double *x, double *res,
+                   cudaStream_t st) {
+    if (elastic(C)) launch_el_b_residual(C->el, K, b, ldb, x, res, st);
+    else launch_b_residual(C->nx, K, C->w_dev, b, ldb, x, res, st);
+}
 
 template <class T> std::vector<int64_t> prefix(const std::vector<T> &v) {
     std::vector<int64_t> o(v.size() + 1, 0);
@@ -196,18 +230,35 @@ void check_err(int *err_dev, cudaStream_t s, const char *what) {
 
 // Coarse DOFs of one level (Sec. 2 and Tables 1, 6): corners first, then edge
 // functionals in edge order.
+// Edge averages: one per edge and displacement component (Table 1, c+e:
+// 13818 - 4794 = two averages on each of the 2 * 48 * 47 edges).
 std::vector<CDof> base_cdofs(const HLevel &H, int mode) {
     std::vector<CDof> out;
+    auto comp = [&](int g) { return H.comp.empty() ? 0 : H.comp[g]; };
+    auto point = [&](int g) {
+        CDof c; c.dofs = {g}; c.w = {1.0}; c.point = true;
+        c.comp = comp(g); c.bnd = !H.dbnd.empty() && H.dbnd[g];
+        return c;
+    };
     if (mode == BDDC_CONSTR_ALL_INTERFACE) {
         for (int g = 0; g < H.n; ++g)
-            if (H.is_iface[g]) { CDof c; c.dofs = {g}; c.w = {1.0}; c.point = true; out.push_back(c); }
+            if (H.is_iface[g]) out.push_back(point(g));
         return out;
     }
-    for (int g : H.corners) { CDof c; c.dofs = {g}; c.w = {1.0}; c.point = true; out.push_back(c); }
+    for (int g : H.corners) out.push_back(point(g));
     if (mode == BDDC_CONSTR_CORNERS_EDGES) {
         for (const auto &e : H.edges) {
-            CDof c; c.dofs = e.dofs; c.w.assign(e.dofs.size(), 1.0 / (double)e.dofs.size());
-            c.s = e.s; c.t = e.t; out.push_back(c);
+            std::vector<int> cs;
+            for (int g : e.dofs) cs.push_back(comp(g));
+            std::sort(cs.begin(), cs.end());
+            cs.erase(std::unique(cs.begin(), cs.end()), cs.end());
+            for (int cv : cs) {
+                CDof c;
+                for (int g : e.dofs) if (comp(g) == cv) c.dofs.push_back(g);
+                c.w.assign(c.dofs.size(), 1.0 / (double)c.dofs.size());
+                c.s = e.s; c.t = e.t; c.comp = cv;
+                out.push_back(std::move(c));
+            }
         }
     }
     return out;
@@ -237,7 +288,6 @@ void adaptive_edges(LevelData &LD, const SetupLevel &S, double tau, DevArena &tm
         for (int g : ed.dofs) {
             posEs.push_back(gpos_s[g]); posEt.push_back(gpos_t[g]);
             used_s[gpos_s[g]] = 1; used_t[gpos_t[g]] = 1;
-            zEs.push_back(H.dofz[g]); zEt.push_back(H.dofz[g]);
         }
         int nc_ = 0;
         for (int g : Gs)
@@ -265,6 +315,12 @@ void adaptive_edges(LevelData &LD, const SetupLevel &S, double tau, DevArena &tm
     }
     if (max_ne > 127 || max_nk > 128)
         throw Error(BDDC_E_ARG, "edge longer than 127 DOFs is not supported by the edge eigensolver");
+    // null vectors on the edges, [nz][all edge entries] (the same on both sides)
+    const int64_t totE = offE.back();
+    for (int m = 0; m < H.nz; ++m)
+        for (const auto &ed : H.edges)
+            for (int g : ed.dofs) zEs.push_back(H.dofz[(size_t)m * H.n + g]);
+    zEt = zEs;
     EdgeBatch E;
     E.nedge = ne_tot; E.max_ne = max_ne; E.max_nk = max_nk; E.max_no = max_no;
     E.max_eigs = LD.max_eigs;
@@ -276,6 +332,7 @@ void adaptive_edges(LevelData &LD, const SetupLevel &S, double tau, DevArena &tm
     E.posE_s = tmp.upload(posEs, st); E.posE_t = tmp.upload(posEt, st);
     E.posC_s = tmp.upload(posCs, st); E.posC_t = tmp.upload(posCt, st);
     E.posO_s = tmp.upload(posOs, st); E.posO_t = tmp.upload(posOt, st);
+    E.nz = H.nz; E.totE = totE;
     E.zE_s = tmp.upload(zEs, st); E.zE_t = tmp.upload(zEt, st);
     E.nsel = tmp.alloc_n<int>(ne_tot); E.nkept = tmp.alloc_n<int>(ne_tot);
     E.lam = tmp.alloc_n<double>((size_t)ne_tot * LD.max_eigs);
@@ -284,7 +341,7 @@ void adaptive_edges(LevelData &LD, const SetupLevel &S, double tau, DevArena &tm
     const int64_t N2 = 2 * max_ne, NP = N2 + 1, NK = max_nk, MO = max_no, NE = max_ne;
     // must cover the sub-buffers carved in k_edge_eig for the largest edge
     const int64_t stride = MO * MO + MO * NK + 2 * NK * NK + N2 * N2 + NE * NE + NK * NK +
-                           N2 * N2 + (N2 * N2 + NK * N2) + 2 * NP * NP + 4 * (NP / 2 + 1) + N2 +
+                           N2 * N2 + (N2 * N2 + NK * N2) + 2 * NP * NP + 4 * (NP / 2 + 1) + 3 * N2 +
                            N2 * N2 + NE * NE + NP + 64;
     double *work = tmp.alloc_n<double>((size_t)stride * ne_tot);
     launch_edge_eig_work(S, E, tau, work, stride, err, st);
@@ -302,8 +359,14 @@ void adaptive_edges(LevelData &LD, const SetupLevel &S, double tau, DevArena &tm
         const int n_e = ne[e];
         const double om = (k < 2 * n_e && k < LD.max_eigs) ? LD.lam[(size_t)e * LD.max_eigs + k] : 0.0;
         LD.omega = std::max(LD.omega, om);
+        int ecomp = -2;                 // the edge's common component, -1 if mixed
+        for (int g : H.edges[e].dofs) {
+            const int cg = H.comp.empty() ? 0 : H.comp[g];
+            ecomp = ecomp == -2 ? cg : (ecomp == cg ? cg : -1);
+        }
         for (int r = 0; r < LD.nkept[e]; ++r) {
             CDof c;
+            c.comp = ecomp;
             c.dofs = H.edges[e].dofs;
             c.w.assign(rows.begin() + offRows[e] + (int64_t)r * n_e,
                        rows.begin() + offRows[e] + (int64_t)(r + 1) * n_e);
@@ -585,10 +648,16 @@ void setup_level(bddc_ctx *C, LevelData &LD, const double *emat, const std::vect
     launch_neumann_setup(S, D, NB, err, st);
     check_err(err, st, "coarse basis");
 
-    // constant function on the coarse DOFs (null vectors of the next level)
-    LD.cz.assign(ncd, 0.0);
-    for (int q = 0; q < ncd; ++q)
-        for (size_t j = 0; j < cd[q].dofs.size(); ++j) LD.cz[q] += cd[q].w[j] * H.dofz[cd[q].dofs[j]];
+    // the null vectors on the coarse DOFs (those of the next level, Sec. 3:
+    // the coarse basis reproduces them), and what the next level classifies by
+    LD.cz.assign((size_t)H.nz * ncd, 0.0);
+    for (int m = 0; m < H.nz; ++m)
+        for (int q = 0; q < ncd; ++q)
+            for (size_t j = 0; j < cd[q].dofs.size(); ++j)
+                LD.cz[(size_t)m * ncd + q] += cd[q].w[j] * H.dofz[(size_t)m * H.n + cd[q].dofs[j]];
+    LD.ccomp.resize(ncd);
+    LD.cbnd.resize(ncd);
+    for (int q = 0; q < ncd; ++q) { LD.ccomp[q] = cd[q].comp; LD.cbnd[q] = cd[q].bnd ? 1 : 0; }
 
     // ---- reduced-precision copies of the apply operators
     D.f32.dir = A.alloc_n<float>(std::max<int64_t>(oF.back(), 1));
@@ -734,7 +803,7 @@ cudaGraphExec_t pcg_graph(bddc_ctx *C, Workspace &W, int prec) {
     try {
         const RzArgs rz{W.rzpart, W.rzcounter, W.sc, W.betas};
         for (int it = 0; it < kGraphIters; ++it) {
-            launch_pcg_dir_spmv(C->nx, C->w_dev, W.z, W.p0, W.p1, W.q, W.part, W.counter, W.sc, W.alphas, st);
+            op_dir_spmv(C, W.z, W.p0, W.p1, W.q, W.part, W.counter, W.sc, W.alphas, st);
             launch_pcg_update(n, W.x, W.r, W.p0, W.p1, W.q, W.part, W.counter, W.sc, st);
             apply_rec(C, W, 0, prec, W.r, W.z, &W.sc->done, st, &rz);
         }
@@ -811,7 +880,7 @@ int pcg_one(bddc_ctx *C, Workspace &W, int prec, const double *b, double *x, dou
         BDDC_CUDA_TRY(cudaStreamSynchronize(st));
         if (!W.hsc->done) { chunk = std::max(1, std::min(chunk / 2, 16)); continue; }
         // Confirm with the true residual; keep iterating if it is not yet met.
-        launch_residual(C->nx, C->w_dev, b, W.x, W.tmp, st);
+        op_residual(C, b, W.x, W.tmp, st);
         launch_norm2(n, W.tmp, W.part, W.counter, W.lout, st);
         launches += 2;
         BDDC_CUDA_TRY(cudaMemcpyAsync(W.hout, W.lout, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -911,7 +980,7 @@ void reduced_iteration(bddc_ctx *C, Workspace &W, ReducedWs &R, int prec, cudaSt
     const int ng = D.n_iface;
     const int *skip = &R.sc->done;
     apply_level_dir(D, BDDC_PREC_FP64, true, R.zero, R.ut, skip, st, nullptr);   // u~ = [-A_II^-1 A_IG p; p]
-    launch_q1_spmv(C->nx, C->w_dev, R.ut, R.qf, st);
+    op_spmv(C, R.ut, R.qf, st);
     launch_red_pq(ng, D.ifaceDof, R.qf, R.p, R.q, R.part, R.counter, R.sc, W.alphas, skip, st);
     launch_red_update(ng, R.x, R.r, R.p, R.q, R.part, R.counter, R.sc, skip, st);
     reduced_precondition(C, W, R, prec, st);
@@ -946,7 +1015,7 @@ int pcg_reduced(bddc_ctx *C, Workspace &W, int prec, const double *b, double *x,
     // g = b_G - (A [A_II^-1 b_I; 0])_G and ||b||^2
     BDDC_CUDA_TRY(cudaMemsetAsync(D.uB, 0, sizeof(double) * std::max(ng, 1), st));
     apply_level_dir(D, BDDC_PREC_FP64, true, b, R.ut, nullptr, st, nullptr);
-    launch_q1_spmv(C->nx, C->w_dev, R.ut, R.qf, st);
+    op_spmv(C, R.ut, R.qf, st);
     launch_norm2(n, b, W.part, W.counter, &R.sc->bb, st);
     launch_red_init(ng, D.ifaceDof, b, R.qf, R.x, R.r, R.p, R.part, R.counter, R.sc, rtol, maxit, st);
     auto start = [&]() {                  // z = M r, p = z
@@ -969,7 +1038,7 @@ int pcg_reduced(bddc_ctx *C, Workspace &W, int prec, const double *b, double *x,
         // true residual; restart from it with a fresh direction if needed
         BDDC_CUDA_TRY(cudaMemcpyAsync(D.uB, R.x, sizeof(double) * std::max(ng, 1), cudaMemcpyDeviceToDevice, st));
         apply_level_dir(D, BDDC_PREC_FP64, true, b, W.x, nullptr, st, nullptr);
-        launch_residual(C->nx, C->w_dev, b, W.x, W.tmp, st);
+        op_residual(C, b, W.x, W.tmp, st);
         launch_norm2(n, W.tmp, W.part, W.counter, W.lout, st);
         BDDC_CUDA_TRY(cudaMemcpyAsync(W.hout, W.lout, sizeof(double), cudaMemcpyDeviceToHost, st));
         BDDC_CUDA_TRY(cudaStreamSynchronize(st));
@@ -1086,14 +1155,16 @@ BatchWs &batch_ws(bddc_ctx *C, Workspace &W) {
         BDDC_CUDA_TRY(cudaMemsetAsync(bw->p, 0, sizeof(double) * n * KB, st));
         std::lock_guard<std::mutex> lk(C->tune_mu);
         if (C->tile_v < 0) {
-            C->tile_v = dir_spmv_tune(C->nx, KB, C->w_dev, bw->z, bw->p, bw->p1, bw->q, bw->part, bw->counter,
-                                      scs, al, st);
+            // (the elasticity operator has no tile to choose)
+            C->tile_v = elastic(C) ? 0
+                                   : dir_spmv_tune(C->nx, KB, C->w_dev, bw->z, bw->p, bw->p1, bw->q, bw->part,
+                                                   bw->counter, scs, al, st);
             const BatchLevel &top = bw->lv.back();
             C->gemm_v = gemm_tune(C->n_top, C->ld_top, C->Ainv, top.rcv, top.ucv, KB, C->err_dev, st);
             BDDC_CUDA_TRY(cudaStreamSynchronize(st));
             BDDC_CUDA_TRY(cudaGetLastError());
             int tx = 0, ty = 0;
-            dir_spmv_tile(C->tile_v, &tx, &ty);
+            if (!elastic(C)) dir_spmv_tile(C->tile_v, &tx, &ty);
             C->tuned[0] = tx;
             C->tuned[1] = ty;
             C->tuned[2] = gemm_rows(C->gemm_v, C->n_top);
@@ -1130,8 +1201,7 @@ cudaGraphExec_t batch_graph(bddc_ctx *C, Workspace &W, BatchWs &BW, int prec, in
     cudaGraph_t g;
     BDDC_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     try {
-        launch_b_dir_spmv(C->nx, K, C->w_dev, BW.z, BW.p, BW.p1, BW.q, BW.part, BW.counter, BW.sc, BW.alphas,
-                          st, BW.tile_v);
+        op_b_dir_spmv(C, K, BW.z, BW.p, BW.p1, BW.q, BW.part, BW.counter, BW.sc, BW.alphas, st, BW.tile_v);
         launch_b_update(n, K, BW.x, BW.r, BW.p, BW.p1, BW.q, BW.part, BW.counter, BW.sc, st);
         const RzBatch rz{BW.rzpart, BW.rzcounter, BW.sc, BW.betas};
         apply_b_rec(C, W, BW, 0, prec, BW.r, BW.z, &BW.sc->all_done, st, &rz);
@@ -1174,7 +1244,7 @@ int pcg_batch(bddc_ctx *C, Workspace &W, int prec, const double *b, int64_t ldb,
         BDDC_CUDA_TRY(cudaStreamSynchronize(st));
         if (!h.all_done) { chunk = std::max(1, std::min(chunk / 2, 16)); continue; }
         // true residuals of every right-hand side
-        launch_b_residual(C->nx, K, C->w_dev, b, ldb, BW.x, BW.tmp, st);
+        op_b_residual(C, K, b, ldb, BW.x, BW.tmp, st);
         launch_b_norm2(n, K, BW.tmp, BW.part, BW.counter, BW.nrm, st);
         launches += 2;
         BDDC_CUDA_TRY(cudaMemcpyAsync(BW.hnrm, BW.nrm, sizeof(double) * K, cudaMemcpyDeviceToHost, st));
@@ -1262,6 +1332,78 @@ void level_one(HLevel &H, int nx, const bddc_decomp *decomp) {
     H.eptr[nelem] = (int64_t)nelem * 4;
 }
 
+// Level 1 of plane elasticity (bilinear elements, Sec. 5): DOF 2 * node + c;
+// with clamp == BDDC_CLAMP_LEFT the nodes on x = 0 are clamped and node
+// (i, j), i >= 1, is j * nx + (i - 1); with BDDC_CLAMP_NONE (the mesh before
+// boundary conditions, for counting only) node (i, j) is j * (nx + 1) + i.
+// The null vectors of a floating substructure are the rigid motions:
+// (1, 0), (0, 1) and (-y, x).
+void level_one_elastic(HLevel &H, int nx, const bddc_decomp *decomp, int clamp) {
+    const bool left = clamp == BDDC_CLAMP_LEFT;
+    const int per_row = left ? nx : nx + 1;
+    const int nn = per_row * (nx + 1);
+    const int nelem = nx * nx;
+    H.n = 2 * nn;
+    H.nelem = nelem;
+    H.nsub = decomp->n_sub1;
+    H.eptr.resize(nelem + 1);
+    H.eslot.resize((size_t)nelem * 8);
+    H.esub.assign(decomp->elem_to_sub, decomp->elem_to_sub + nelem);
+    H.ebnd.assign(nelem, 0);
+    H.nz = 3;
+    H.dofz.assign((size_t)3 * H.n, 0.0);
+    H.comp.assign(H.n, 0);
+    H.dbnd.assign(H.n, 0);
+    auto node = [&](int i, int j) { return left ? (i <= 0 ? -1 : j * nx + (i - 1)) : j * (nx + 1) + i; };
+    const double h = 1.0 / nx;
+    for (int j = 0; j <= nx; ++j)
+        for (int i = left ? 1 : 0; i <= nx; ++i) {
+            const int a = node(i, j);
+            const char on = (i == 0 || j == 0 || i == nx || j == nx) ? 1 : 0;
+            for (int c = 0; c < 2; ++c) {
+                const int g = 2 * a + c;
+                H.comp[g] = c;
+                H.dbnd[g] = on;
+                H.dofz[g] = c == 0 ? 1.0 : 0.0;
+                H.dofz[(size_t)H.n + g] = c == 1 ? 1.0 : 0.0;
+                H.dofz[(size_t)2 * H.n + g] = c == 0 ? -j * h : i * h;
+            }
+        }
+    for (int e = 0; e < nelem; ++e) {
+        const int ej = e / nx, ei = e % nx;
+        H.eptr[e] = (int64_t)e * 8;
+        const int nd[4] = {node(ei, ej), node(ei + 1, ej), node(ei + 1, ej + 1), node(ei, ej + 1)};
+        for (int a = 0; a < 4; ++a)
+            for (int c = 0; c < 2; ++c) {
+                H.eslot[(size_t)e * 8 + 2 * a + c] = nd[a] < 0 ? -1 : 2 * nd[a] + c;
+                if (nd[a] < 0) H.ebnd[e] = 1;
+            }
+    }
+    H.eptr[nelem] = (int64_t)nelem * 8;
+}
+
+// Level 1 of the problem the mesh names (checked by the caller).
+void level_one_of(HLevel &H, const bddc_mesh *mesh, const bddc_decomp *decomp) {
+    if (mesh->problem == BDDC_PROBLEM_ELASTICITY) level_one_elastic(H, mesh->nx, decomp, mesh->clamp);
+    else level_one(H, mesh->nx, decomp);
+}
+
+// The problem fields of a mesh; `setup` refuses the unclamped elasticity
+// mesh (its stiffness matrix is singular).
+void check_problem(const bddc_mesh *mesh, bool setup) {
+    if (mesh->problem == BDDC_PROBLEM_DIFFUSION) {
+        if (mesh->clamp != BDDC_CLAMP_ALL) throw Error(BDDC_E_ARG, "the diffusion problem is clamped on every side");
+        return;
+    }
+    if (mesh->problem != BDDC_PROBLEM_ELASTICITY) throw Error(BDDC_E_ARG, "unknown problem");
+    if (mesh->clamp != BDDC_CLAMP_LEFT && (setup || mesh->clamp != BDDC_CLAMP_NONE))
+        throw Error(BDDC_E_ARG, setup ? "the elasticity problem is clamped on x = 0 (BDDC_CLAMP_LEFT)"
+                                      : "bad clamp for the elasticity problem");
+    if (setup && (!(mesh->lame_mu > 0.0) || !(mesh->lame_lambda >= 0.0) || !std::isfinite(mesh->lame_lambda) ||
+                  !std::isfinite(mesh->lame_mu)))
+        throw Error(BDDC_E_ARG, "Lame parameters need mu > 0 and lambda >= 0");
+}
+
 template <class F> int guarded(F &&f) {
     try {
         set_error("");
@@ -1296,10 +1438,14 @@ int bddc_setup(const bddc_mesh *mesh, const double *k_elem, const bddc_decomp *d
         if (levels == 3 && (!decomp->sub1_to_sub2 || decomp->n_sub2 < 1))
             throw Error(BDDC_E_ARG, "three levels need sub1_to_sub2");
         if (decomp->n_sub1 < 1) throw Error(BDDC_E_ARG, "n_sub1 must be positive");
+        check_problem(mesh, true);
         const auto t0 = std::chrono::steady_clock::now();
         cudaStream_t st = (cudaStream_t)stream;
         std::unique_ptr<bddc_ctx> C(new bddc_ctx());
         C->nx = mesh->nx;
+        C->problem = mesh->problem;
+        C->n_dof = C->problem == BDDC_PROBLEM_ELASTICITY ? (int64_t)2 * mesh->nx * (mesh->nx + 1)
+                                                         : (int64_t)(mesh->nx - 1) * (mesh->nx - 1);
         C->levels = levels;
         C->tau = tau;
         bddc_opts o{};
@@ -1319,8 +1465,12 @@ int bddc_setup(const bddc_mesh *mesh, const double *k_elem, const bddc_decomp *d
         }
         std::vector<double> kv(k_elem, k_elem + nelem);
         C->k_dev = C->arena.upload(kv, st);
-        C->w_dev = C->arena.alloc_n<double>((size_t)5 * (nx - 1) * (nx - 1));
-        launch_q1_weights(nx, C->k_dev, C->w_dev, st);
+        if (elastic(C.get())) {
+            C->el = make_el_op(nx, C->k_dev, mesh->lame_lambda, mesh->lame_mu);
+        } else {
+            C->w_dev = C->arena.alloc_n<double>((size_t)5 * (nx - 1) * (nx - 1));
+            launch_q1_weights(nx, C->k_dev, C->w_dev, st);
+        }
         C->err_dev = C->arena.alloc_n<int>(1);
         BDDC_CUDA_TRY(cudaMemsetAsync(C->err_dev, 0, sizeof(int), st));
         static std::once_flag prep_once;
@@ -1329,13 +1479,16 @@ int bddc_setup(const bddc_mesh *mesh, const double *k_elem, const bddc_decomp *d
         int *err = tmp.alloc_n<int>(1);
         BDDC_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
 
-        // level 1: Q1 elements
+        // level 1: Q1 elements (4 x 4 element matrices) or bilinear
+        // elasticity elements (8 x 8)
         C->L.resize(levels - 1);
-        level_one(C->L[0].H, nx, decomp);
-        double *emat = tmp.alloc_n<double>((size_t)nelem * 16);
-        launch_q1_element_matrices(nelem, C->k_dev, emat, st);
+        level_one_of(C->L[0].H, mesh, decomp);
+        const int esz = elastic(C.get()) ? 64 : 16;
+        double *emat = tmp.alloc_n<double>((size_t)nelem * esz);
+        if (elastic(C.get())) launch_el_element_matrices(nelem, C->k_dev, C->el, emat, st);
+        else launch_q1_element_matrices(nelem, C->k_dev, emat, st);
         std::vector<int64_t> emOff(nelem);
-        for (int e = 0; e < nelem; ++e) emOff[e] = (int64_t)e * 16;
+        for (int e = 0; e < nelem; ++e) emOff[e] = (int64_t)e * esz;
         setup_level(C.get(), C->L[0], emat, emOff, o.constraints, tau, tmp, err, st);
         if (levels == 3) {
             LevelData &P = C->L[0];
@@ -1350,7 +1503,10 @@ int bddc_setup(const bddc_mesh *mesh, const double *k_elem, const bddc_decomp *d
             H.esub.assign(decomp->sub1_to_sub2, decomp->sub1_to_sub2 + H.nelem);
             H.ebnd.resize(H.nelem);
             for (int s = 0; s < H.nelem; ++s) H.ebnd[s] = !P.H.floating[s];
+            H.nz = P.H.nz;
             H.dofz = P.cz;
+            H.comp = P.ccomp;
+            H.dbnd = P.cbnd;
             const int mode2 = o.constraints_level2 >= 0 ? o.constraints_level2 : o.constraints;
             setup_level(C.get(), C->L[1], P.ac, P.offAc, mode2, tau, tmp, err, st);
         }
@@ -1436,8 +1592,9 @@ int bddc_inspect(const bddc_mesh *mesh, const bddc_decomp *decomp, int32_t *n_co
     return guarded([&]() -> int {
         if (!mesh || !decomp || !decomp->elem_to_sub) throw Error(BDDC_E_ARG, "null argument");
         if (mesh->nx < 2 || mesh->ny != mesh->nx) throw Error(BDDC_E_ARG, "mesh must be square with nx >= 2");
+        check_problem(mesh, false);
         HLevel H;
-        level_one(H, mesh->nx, decomp);
+        level_one_of(H, mesh, decomp);
         H.build();
         const int ne = (int)H.edges.size();
         if (n_corners) *n_corners = (int32_t)H.corners.size();
@@ -1455,7 +1612,7 @@ int bddc_inspect(const bddc_mesh *mesh, const bddc_decomp *decomp, int32_t *n_co
 int bddc_operator(bddc_ctx *ctx, const double *x_dev, double *y_dev, void *stream) {
     return guarded([&]() -> int {
         if (!ctx || !x_dev || !y_dev) throw Error(BDDC_E_ARG, "bad argument");
-        launch_q1_spmv(ctx->nx, ctx->w_dev, x_dev, y_dev, (cudaStream_t)stream);
+        op_spmv(ctx, x_dev, y_dev, (cudaStream_t)stream);
         BDDC_CUDA_TRY(cudaGetLastError());
         return BDDC_OK;
     });
@@ -2057,7 +2214,7 @@ namespace bddc {
 namespace {
 
 size_t request_bytes(const bddc_ctx *ctx, int nrhs) {
-    return (size_t)2 * nrhs * (size_t)(ctx->nx - 1) * (ctx->nx - 1) * sizeof(double);
+    return (size_t)2 * nrhs * (size_t)ctx->n() * sizeof(double);
 }
 
 void worker_loop(bddc_server *S) {
@@ -2201,7 +2358,7 @@ void engine_loop(bddc_server *S, Engine *E) {
             std::vector<int> fin;
             for (int k = 0; k < K; ++k) if (slot[k].R && h.done[k]) fin.push_back(k);
             if (fin.empty()) continue;
-            launch_b_residual(C->nx, K, C->w_dev, BW.bcol, n, BW.x, BW.tmp, st);
+            op_b_residual(C, K, BW.bcol, n, BW.x, BW.tmp, st);
             launch_b_norm2(n, K, BW.tmp, BW.part, BW.counter, BW.nrm, st);
             BDDC_CUDA_TRY(cudaMemcpyAsync(BW.hnrm, BW.nrm, sizeof(double) * K, cudaMemcpyDeviceToHost, st));
             BDDC_CUDA_TRY(cudaStreamSynchronize(st));

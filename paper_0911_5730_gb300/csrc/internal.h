@@ -385,6 +385,25 @@ struct SetupLevel {
 };
 
 void launch_q1_element_matrices(int nelem, const double *k, double *emat, cudaStream_t s);
+
+// Plane elasticity (elastic_kernels.cu): nx elements per side, Lame
+// parameters k_e * (lam, mu) per element, the nodes on x = 0 clamped; K is the
+// 8 x 8 reference element matrix (passed by value to every kernel).
+struct ElOp {
+    int nx = 0;
+    const double *k = nullptr;
+    double K[64];
+};
+ElOp make_el_op(int nx, const double *k_dev, double lam, double mu);
+void launch_el_element_matrices(int nelem, const double *k, const ElOp &op, double *emat, cudaStream_t s);
+void launch_el_spmv(const ElOp &op, const double *x, double *y, cudaStream_t s);
+void launch_el_residual(const ElOp &op, const double *b, const double *x, double *res, cudaStream_t s);
+void launch_el_dir_spmv(const ElOp &op, const double *z, double *p0, double *p1, double *q, double *part,
+                        unsigned *counter, PcgScalars *sc, double *alphas, cudaStream_t s);
+void launch_el_b_dir_spmv(const ElOp &op, int K, const double *z, double *p0, double *p1, double *q, double *part,
+                          unsigned *counter, BatchScalars *sc, double *alphas, cudaStream_t s);
+void launch_el_b_residual(const ElOp &op, int K, const double *b, int64_t ldb, const double *x, double *res,
+                          cudaStream_t s);
 void launch_assemble(const SetupLevel &S, int *err, cudaStream_t s);
 void launch_band_cholesky(const SetupLevel &S, int *err, cudaStream_t s);
 void launch_schur(const SetupLevel &S, int max_nG, cudaStream_t s);
@@ -407,7 +426,11 @@ struct EdgeBatch {
     int *posO_s = nullptr, *posO_t = nullptr;
     int *nos = nullptr, *not_ = nullptr;
     int *floating = nullptr;      // both substructures floating
-    double *zE_s = nullptr, *zE_t = nullptr;   // null-vector values on the edge
+    // null vectors of the pair on the edge: [nz][total edge entries], entry
+    // (m, offE[e] + i); used when both substructures float
+    int nz = 1;
+    int64_t totE = 0;
+    double *zE_s = nullptr, *zE_t = nullptr;
     // outputs
     int *nsel = nullptr, *nkept = nullptr;
     double *lam = nullptr;        // [nedge * max_eigs]

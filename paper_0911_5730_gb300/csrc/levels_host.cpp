@@ -138,13 +138,17 @@ void HLevel::build() {
         std::vector<int64_t> fill(subs_ptr.begin(), subs_ptr.end() - 1);
         for (int s = 0; s < nsub; ++s) for (int g : sub_dofs[s]) subs_idx[fill[g]++] = s;
     }
+    if (!dbnd.empty() && (int)dbnd.size() != n) throw Error(BDDC_E_ARG, "level: boundary flags of the wrong size");
+    if (!comp.empty() && (int)comp.size() != n) throw Error(BDDC_E_ARG, "level: components of the wrong size");
     is_iface.assign(n, 0); is_corner.assign(n, 0);
     corners.clear();
+    // corners: in three or more substructures, or an interface DOF on the
+    // boundary of the domain (where an edge ends on a free side)
     for (int g = 0; g < n; ++g) {
         const int m = mult(g);
         is_iface[g] = m >= 2;
-        is_corner[g] = m >= 3;
-        if (m >= 3) corners.push_back(g);
+        is_corner[g] = m >= 3 || (m >= 2 && !dbnd.empty() && dbnd[g]);
+        if (is_corner[g]) corners.push_back(g);
     }
     // Edges: connected chains of non-corner interface DOFs shared by one pair.
     DSU dsu(n);

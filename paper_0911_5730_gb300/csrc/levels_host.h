@@ -24,7 +24,11 @@ struct HLevel {
     std::vector<int> eslot;         // level DOF of each slot, -1 = Dirichlet (dropped)
     std::vector<int> esub;          // substructure of each element
     std::vector<char> ebnd;         // element touches the Dirichlet boundary
-    std::vector<double> dofz;       // value of the constant function at each DOF
+    int nz = 1;                     // null vectors of a floating substructure's matrix
+                                    // (1: the constants; 3: the rigid motions in 2D)
+    std::vector<double> dofz;       // [nz][n]: their values at each DOF
+    std::vector<int> comp;          // displacement component of each DOF, -1 mixed (empty: all 0)
+    std::vector<char> dbnd;         // DOF on the boundary of the domain (empty: none)
 
     // derived by build()
     std::vector<std::vector<int>> sub_elems, sub_dofs;

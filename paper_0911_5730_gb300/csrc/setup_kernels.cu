@@ -424,13 +424,14 @@ __global__ void k_edge_eig(SetupLevel S, EdgeBatch E, double tau, double *work,
     double *C = w;                 w += (int64_t)np * np;
     double *V = w;                 w += (int64_t)np * np;
     double *cs = w;                w += 4 * (np / 2 + 1);
-    double *nv = w;                w += n2;
+    double *nv = w;                w += 3 * n2;   // up to three orthonormal null vectors
     double *Wk = w;                w += (int64_t)n2 * n2;
     double *Rw = w;                w += (int64_t)ne * ne;
     double *lamv = w;              w += np;
     __shared__ int perm[256];
     __shared__ int order[256];
     __shared__ double sh_a;
+    __shared__ int sh_nz;
 
     // posK = edge positions followed by shared corner positions
     __shared__ int posK_s[128], posK_t[128];
@@ -486,40 +487,69 @@ __global__ void k_edge_eig(SetupLevel S, EdgeBatch E, double tau, double *work,
         Xd[q] = wti * Ss[(int64_t)posEs[i] * nGs + posEs[j]] * wtj +
                 wsi * St[(int64_t)posEt[i] * nGt + posEt[j]] * wsj;
     }
-    // null vector of Mt when both float: the constant function on the edge
-    const int fl = E.floating[e];
+    // null vectors of Mt when both float: the null vectors of the
+    // substructures (the constants; for elasticity the rigid motions) on the
+    // edge, the same on both sides, orthonormalised (two Gram-Schmidt passes;
+    // a vector that the others already span on this edge is dropped)
+    const int nzE = E.floating[e] ? E.nz : 0;
     if (threadIdx.x == 0) {
         double a = 0.0;
         for (int i = 0; i < n2; ++i) a = fmax(a, Mt[i * n2 + i]);
         sh_a = a;
-        if (fl) {
-            double nr = 0.0;
+        int kept = 0;
+        for (int m = 0; m < nzE && m < 3; ++m) {
+            double *v = nv + kept * n2;
             for (int i = 0; i < ne; ++i) {
-                nv[i] = E.zE_s[E.offE[e] + i];
-                nv[ne + i] = E.zE_t[E.offE[e] + i];
+                v[i] = E.zE_s[m * E.totE + E.offE[e] + i];
+                v[ne + i] = E.zE_t[m * E.totE + E.offE[e] + i];
             }
-            for (int i = 0; i < n2; ++i) nr += nv[i] * nv[i];
-            nr = sqrt(nr);
-            for (int i = 0; i < n2; ++i) nv[i] /= nr;
+            double n0 = 0.0;
+            for (int i = 0; i < n2; ++i) n0 += v[i] * v[i];
+            for (int pass = 0; pass < 2; ++pass)
+                for (int p = 0; p < kept; ++p) {
+                    double d = 0.0;
+                    for (int i = 0; i < n2; ++i) d += v[i] * nv[p * n2 + i];
+                    for (int i = 0; i < n2; ++i) v[i] -= d * nv[p * n2 + i];
+                }
+            double nr = 0.0;
+            for (int i = 0; i < n2; ++i) nr += v[i] * v[i];
+            if (nr > 1e-16 * n0 && nr > 0.0) {
+                nr = sqrt(nr);
+                for (int i = 0; i < n2; ++i) v[i] /= nr;
+                ++kept;
+            }
         }
+        sh_nz = kept;
     }
     __syncthreads();
     const double a = sh_a;
-    // Y2 = P Mt P + a nv nv^T, P = I - nv nv^T
-    if (fl) {
+    const int nzk = sh_nz;
+    // Y2 = P Mt P + a N N^T, P = I - N N^T (N: the kept null vectors)
+    if (nzk > 0) {
         // T = Mt P
         for (int q = threadIdx.x; q < n2 * n2; q += blockDim.x) {
             const int i = q / n2, j = q % n2;
-            double mv = 0.0;
-            for (int k = 0; k < n2; ++k) mv += Mt[i * n2 + k] * nv[k];
-            T[q] = Mt[q] - mv * nv[j];
+            double t = Mt[q];
+            for (int m = 0; m < nzk; ++m) {
+                const double *v = nv + m * n2;
+                double mv = 0.0;
+                for (int k = 0; k < n2; ++k) mv += Mt[i * n2 + k] * v[k];
+                t = t - mv * v[j];
+            }
+            T[q] = t;
         }
         __syncthreads();
         for (int q = threadIdx.x; q < n2 * n2; q += blockDim.x) {
             const int i = q / n2, j = q % n2;
-            double vt = 0.0;
-            for (int k = 0; k < n2; ++k) vt += nv[k] * T[k * n2 + j];
-            Y2[q] = T[q] - nv[i] * vt + a * nv[i] * nv[j];
+            double y = T[q];
+            for (int m = 0; m < nzk; ++m) {
+                const double *v = nv + m * n2;
+                double vt = 0.0;
+                for (int k = 0; k < n2; ++k) vt += v[k] * T[k * n2 + j];
+                y = y - v[i] * vt;
+            }
+            for (int m = 0; m < nzk; ++m) y = y + a * nv[m * n2 + i] * nv[m * n2 + j];
+            Y2[q] = y;
         }
     } else {
         for (int q = threadIdx.x; q < n2 * n2; q += blockDim.x) Y2[q] = Mt[q];

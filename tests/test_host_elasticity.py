@@ -1,0 +1,56 @@
+"""Host-side classification of the elasticity problem (bddc_inspect; no GPU).
+
+At the paper's size (768 x 768 bilinear elements, 48 x 48 substructures,
+H/h = 16) the setup's own classification gives the constraint counts of
+Table 1: 4794 corner DOFs and 13818 with one average per edge and component,
+counted on the whole node set as the paper's DOF count 1 182 722 = 2 * 769^2
+does; with the side x = 0 clamped the 47 vertices on it drop out (4700,
+13724).  The oracle reproduces the same counts from its own code
+(tests/test_oracle_elasticity.py); here they are checked against the paper's
+numbers and the closed forms.  Also: the setup refuses the unclamped
+(singular) mesh and bad Lame parameters before any device work.
+"""
+import numpy as np
+import pytest
+
+from paper_0911_5730_gb300 import inputs
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_0911_5730_gb300 import bddc
+    return bddc
+
+
+def test_paper_counts_at_full_size(lib):
+    e2s, ns = inputs.grid_decomposition(768, 16)
+    r = lib.inspect(768, e2s, ns, problem="elasticity", clamp="none")
+    assert r["n_corners"] == 4794                               # Table 1, c
+    assert r["n_corners"] + 2 * r["n_edges"] == 13818           # Table 1, c+e
+    assert r["n_edges"] == 2 * 48 * 47 and set(r["edge_len"]) == {30}
+    r = lib.inspect(768, e2s, ns, problem="elasticity")
+    assert r["n_corners"] == 2 * (49 ** 2 - 4 - 47) == 4700
+    assert r["n_corners"] + 2 * r["n_edges"] == 13724
+    assert r["block_size"] == 32
+
+
+def test_jagged_edge(lib):
+    wl = inputs.elasticity(nx=768)
+    r = lib.inspect(768, wl.elem_to_sub, wl.n_sub1, problem="elasticity")
+    assert r["n_corners"] == 4700 and r["n_edges"] == 2 * 48 * 47
+    pairs = [tuple(p) for p in r["edge_pairs"]]
+    lens = dict(zip(pairs, r["edge_len"]))
+    assert lens[(1, 49)] > 30                                   # the comb is longer
+    assert sorted(set(r["edge_len"]))[:1] == [30]
+
+
+def test_setup_refuses_before_device_work(lib):
+    wl = inputs.elasticity(nx=16, sub=4, levels=2, constraints="corners", jagged=False)
+    with pytest.raises(lib.BDDCError) as e:
+        lib.Problem(16, wl.k, wl.elem_to_sub, wl.n_sub1, problem="elasticity", lame=(1.0, 0.0), stream=0)
+    assert e.value.code == -1
+    with pytest.raises(lib.BDDCError) as e:
+        lib.Problem(16, wl.k, wl.elem_to_sub, wl.n_sub1, problem="elasticity", lame=(-1.0, 2.0), stream=0)
+    assert e.value.code == -1
