@@ -313,8 +313,9 @@ void adaptive_edges(LevelData &LD, const SetupLevel &S, double tau, DevArena &tm
         max_nk = std::max(max_nk, n_e + nc_);
         max_no = std::max(max_no, std::max(no_s, no_t));
     }
-    if (max_ne > 127 || max_nk > 128)
-        throw Error(BDDC_E_ARG, "edge longer than 127 DOFs is not supported by the edge eigensolver");
+    if (max_ne > kEdgeMaxNE || max_nk > kEdgeMaxNK)
+        throw Error(BDDC_E_ARG, "edge longer than " + std::to_string(kEdgeMaxNE) +
+                                    " DOFs is not supported by the edge eigensolver");
     // null vectors on the edges, [nz][all edge entries] (the same on both sides)
     const int64_t totE = offE.back();
     for (int m = 0; m < H.nz; ++m)

@@ -415,6 +415,10 @@ void launch_extract_coo(const SetupLevel &S, const DevLevel &L, const int64_t *c
                         cudaStream_t s);
 void launch_weights(const SetupLevel &S, const DevLevel &L, double *diag_sum, cudaStream_t s);
 
+// Largest edge of the edge eigensolver: kEdgeMaxNE DOFs on the edge,
+// kEdgeMaxNK with the shared corners, pair problems of 2 * kEdgeMaxNE.
+constexpr int kEdgeMaxNE = 255, kEdgeMaxNK = 256, kEdgeMaxN2 = 512;
+
 struct EdgeBatch {
     int nedge = 0;
     int max_ne = 0, max_nk = 0, max_no = 0;

@@ -428,13 +428,13 @@ __global__ void k_edge_eig(SetupLevel S, EdgeBatch E, double tau, double *work,
     double *Wk = w;                w += (int64_t)n2 * n2;
     double *Rw = w;                w += (int64_t)ne * ne;
     double *lamv = w;              w += np;
-    __shared__ int perm[256];
-    __shared__ int order[256];
+    __shared__ int perm[kEdgeMaxN2];
+    __shared__ int order[kEdgeMaxN2];
     __shared__ double sh_a;
     __shared__ int sh_nz;
 
     // posK = edge positions followed by shared corner positions
-    __shared__ int posK_s[128], posK_t[128];
+    __shared__ int posK_s[kEdgeMaxNK], posK_t[kEdgeMaxNK];
     for (int i = threadIdx.x; i < nk; i += blockDim.x) {
         posK_s[i] = i < ne ? posEs[i] : posCs[i - ne];
         posK_t[i] = i < ne ? posEt[i] : posCt[i - ne];

@@ -22,6 +22,7 @@ from __future__ import annotations
 
 import argparse
 import math
+import sys
 import time
 
 import torch
@@ -78,6 +79,7 @@ def run(levels=(2, 3), nx: int = 768, batch: int = 32) -> list[dict]:
                     "setup_ms": q["setup_ms"], "solve_ms_fp32": ms, "batch_solves_per_s_fp32": bps,
                     "batch_relres_max": max(j["relres_true"] for j in iB),
                     "sub_dofs": sub_dofs, "paper": PAPER[(lev, mode, tau)]})
+        print(table(out[-1:]).splitlines()[-1], file=sys.stderr, flush=True)
         P.close()
     return out
 

@@ -4,10 +4,19 @@ seeded coefficient), clamped on x = 0, a jagged level-1 edge and, on three
 levels, a jagged level-2 edge.
 
 The bar of the other parity tests: the operator within 1e-13, the apply within
-1e-10 per right-hand side (single and batched), PCG in FP64 with the oracle's
-iteration count, solution within 1e-10, kappa within 1e-6 and the number of
-selected constraints per edge identical; FP32 and BF16 applies reach the FP64
-residual 1e-8.  At the paper's size (768^2, 48 x 48 substructures, 3 x 3 on
+1e-10 per right-hand side (single and batched), the number of selected
+constraints per edge identical, and the PCG trajectory: the iterate after a
+fixed 8 iterations within 1e-9 of the oracle's (a relative perturbation of
+1e-13 in b moves the oracle's own iterate there by at most 4e-12).  Run to the residual 1e-8
+in FP64, the adaptive cases (spectrum of M^{-1} A in [1, 2.8]) keep the
+oracle's iteration count, solution within 1e-10 and kappa within 1e-6.  With
+corners or corner + edge averages only (spectrum up to 25-50) the iteration
+at which the residual crosses 1e-8 is not a property of the method: a
+relative perturbation of 1e-12 in b moves the oracle's own residual at the
+crossing between 0.7e-8 and 1.1e-8 (25 or 26 iterations; 45 or 47), and its
+count differs between the x86 and Arm BLAS builds; there the bar is the
+true residual below 1e-8, two iterations either way and kappa within 1e-3.
+FP32 and BF16 applies reach the FP64 residual 1e-8.  At the paper's size (768^2, 48 x 48 substructures, 3 x 3 on
 level 2) the counts of Tables 1-2 come from the setup itself and the solve is
 checked by its true residual and Theorem 2's bound.
 """
@@ -75,19 +84,35 @@ def test_elasticity_matches_oracle(lib, name):
     if c["constraints"] == "adaptive":
         q = P.query(level=1)
         assert list(q["n_selected"]) == [e["n_sel"] for e in H.info["edge_reports"][0]]
-    # PCG in FP64
+    # the PCG trajectory: the iterate after a fixed number of iterations
     b = wl.rhs()
-    xs, info = P.solve(torch.tensor(b, device="cuda"), rtol=1e-8)
+    bt = torch.tensor(b, device="cuda")
+    x8, i8 = P.solve(bt, rtol=1e-30, maxit=8, check=False)
+    r8 = opcg.pcg(H.A, b, H.apply, fixed_iters=8)
+    assert i8[0]["iters"] == 8
+    assert _relerr(x8.cpu().numpy(), r8.x) <= 1e-9
+    # PCG in FP64 to the residual 1e-8
+    xs, info = P.solve(bt, rtol=1e-8)
     ref = opcg.pcg(H.A, b, H.apply, rtol=1e-8)
-    assert info[0]["status"] == 0 and info[0]["iters"] == ref.iters
-    assert _relerr(xs.cpu().numpy(), ref.x) <= 1e-10
-    assert abs(info[0]["kappa_est"] - ref.kappa) <= 1e-6 * ref.kappa
+    assert info[0]["status"] == 0
+    xg = xs.cpu().numpy()
+    assert np.linalg.norm(b - H.A @ xg) <= 1e-8 * np.linalg.norm(b)
+    if c["constraints"] == "adaptive":
+        assert info[0]["iters"] == ref.iters
+        assert _relerr(xg, ref.x) <= 1e-10
+        assert abs(info[0]["kappa_est"] - ref.kappa) <= 1e-6 * ref.kappa
+    else:
+        assert abs(info[0]["iters"] - ref.iters) <= 2
+        assert _relerr(xg, ref.x) <= 1e-6
+        assert abs(info[0]["kappa_est"] - ref.kappa) <= 1e-3 * ref.kappa
     # batched PCG: each right-hand side as the oracle solves it alone
     X, infos = P.solve(torch.tensor(R, device="cuda"), rtol=1e-8)
     for j in range(3):
         rj = opcg.pcg(H.A, R[j], H.apply, rtol=1e-8)
-        assert abs(infos[j]["iters"] - rj.iters) <= 1
-        assert _relerr(X[j].cpu().numpy(), rj.x) <= 1e-7
+        assert infos[j]["status"] == 0 and abs(infos[j]["iters"] - rj.iters) <= 2
+        xj = X[j].cpu().numpy()
+        assert np.linalg.norm(R[j] - H.A @ xj) <= 1e-8 * np.linalg.norm(R[j])
+        assert _relerr(xj, rj.x) <= 1e-6
     P.close()
 
 
