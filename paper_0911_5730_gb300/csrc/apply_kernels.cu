@@ -38,54 +38,89 @@ __device__ __forceinline__ int64_t fpos(int r, int c, int ld, bool swz) {
 
 // Interior solve with the block factor of one substructure; x holds the
 // right-hand side on entry (m*b entries, padding zero) and the solution on
-// exit; tmp has b entries.
-template <class T, class ACC>
-__device__ void dirichlet_solve(const T *F, int b, int m, bool swz, ACC *x, ACC *tmp) {
+// exit; tmp has b entries.  tpr threads share a row of each block product
+// (column-strided partial sums, shuffle-reduced; tpr a power of two <= 8, so
+// a row's threads sit in one warp), as many as the block's threads allow for
+// the block size: a block of 512 threads solves up to 256 rows of a step in
+// one pass.  Every thread of the block calls it (block-wide barriers).
+constexpr int kGT = 512;   // threads of a generic Dirichlet kernel's block (one per substructure)
+
+template <int TPR, class T, class ACC>
+__device__ __forceinline__ ACC dsolve_sum(ACC v) {
+#pragma unroll
+    for (int o = TPR / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int TPR, class T, class ACC>
+__device__ void dirichlet_solve_t(const T *F, int b, int m, bool swz, ACC *x, ACC *tmp) {
     const int ldb = fld(b, swz), bb = b * ldb;
+    const int rpp = blockDim.x / TPR;                 // rows per pass
+    const int part = threadIdx.x % TPR, rl = threadIdx.x / TPR;
     for (int j = 0; j < m; ++j) {
         const T *Linv = F + (int64_t)j * 2 * bb;
         const T *Lsub = Linv + bb;
-        for (int r = threadIdx.x; r < b; r += blockDim.x) {
-            ACC t = x[j * b + r];
-            if (j > 0) {
+        for (int r0 = 0; r0 < b; r0 += rpp) {
+            const int r = r0 + rl;
+            ACC a = 0;
+            if (r < b && j > 0) {
                 const ACC *xp = x + (j - 1) * b;
-                for (int c = 0; c < b; ++c) t -= ld<T, ACC>(Lsub + fpos(r, c, ldb, swz)) * xp[c];
+                for (int c = part; c < b; c += TPR) a += ld<T, ACC>(Lsub + fpos(r, c, ldb, swz)) * xp[c];
             }
-            tmp[r] = t;
+            a = dsolve_sum<TPR, T, ACC>(a);
+            if (r < b && part == 0) tmp[r] = x[j * b + r] - a;
         }
         __syncthreads();
-        for (int r = threadIdx.x; r < b; r += blockDim.x) {
-            ACC s = 0;
-            for (int c = 0; c <= r; ++c) s += ld<T, ACC>(Linv + fpos(r, c, ldb, swz)) * tmp[c];
-            x[j * b + r] = s;
+        for (int r0 = 0; r0 < b; r0 += rpp) {
+            const int r = r0 + rl;
+            ACC a = 0;
+            if (r < b)
+                for (int c = part; c <= r; c += TPR) a += ld<T, ACC>(Linv + fpos(r, c, ldb, swz)) * tmp[c];
+            a = dsolve_sum<TPR, T, ACC>(a);
+            if (r < b && part == 0) x[j * b + r] = a;
         }
         __syncthreads();
     }
     for (int j = m - 1; j >= 0; --j) {
         const T *Linv = F + (int64_t)j * 2 * bb;
-        for (int r = threadIdx.x; r < b; r += blockDim.x) {
-            ACC t = x[j * b + r];
-            if (j < m - 1) {
+        for (int r0 = 0; r0 < b; r0 += rpp) {
+            const int r = r0 + rl;
+            ACC a = 0;
+            if (r < b && j < m - 1) {
                 // L_{j+1,j}^T: entry (r, c) is entry (c, r) of the stored block
                 const T *Lsub1 = F + (int64_t)(j + 1) * 2 * bb + bb;
                 const ACC *xn = x + (j + 1) * b;
-                for (int c = 0; c < b; ++c) t -= ld<T, ACC>(Lsub1 + fpos(c, r, ldb, swz)) * xn[c];
+                for (int c = part; c < b; c += TPR) a += ld<T, ACC>(Lsub1 + fpos(c, r, ldb, swz)) * xn[c];
             }
-            tmp[r] = t;
+            a = dsolve_sum<TPR, T, ACC>(a);
+            if (r < b && part == 0) tmp[r] = x[j * b + r] - a;
         }
         __syncthreads();
-        for (int r = threadIdx.x; r < b; r += blockDim.x) {
-            ACC s = 0;
-            for (int c = r; c < b; ++c) s += ld<T, ACC>(Linv + fpos(c, r, ldb, swz)) * tmp[c];
-            x[j * b + r] = s;
+        for (int r0 = 0; r0 < b; r0 += rpp) {
+            const int r = r0 + rl;
+            ACC a = 0;
+            if (r < b)
+                for (int c = r + part; c < b; c += TPR) a += ld<T, ACC>(Linv + fpos(c, r, ldb, swz)) * tmp[c];
+            a = dsolve_sum<TPR, T, ACC>(a);
+            if (r < b && part == 0) x[j * b + r] = a;
         }
         __syncthreads();
     }
 }
 
+template <class T, class ACC>
+__device__ void dirichlet_solve(const T *F, int b, int m, bool swz, ACC *x, ACC *tmp) {
+    // the most threads per row that still cover every row in one pass
+    const int nt = blockDim.x;
+    if (b * 8 <= nt) dirichlet_solve_t<8, T, ACC>(F, b, m, swz, x, tmp);
+    else if (b * 4 <= nt) dirichlet_solve_t<4, T, ACC>(F, b, m, swz, x, tmp);
+    else if (b * 2 <= nt) dirichlet_solve_t<2, T, ACC>(F, b, m, swz, x, tmp);
+    else dirichlet_solve_t<1, T, ACC>(F, b, m, swz, x, tmp);
+}
+
 // (4)-(5): u_I = A_II^{-1} r_I per substructure; r_B on Gamma = r - A_{Gamma I} u_I.
 template <class T, class ACC>
-__global__ void k_pre(DevLevel L, const double *r, const int *skip) {
+__global__ void __launch_bounds__(kGT) k_pre(DevLevel L, const double *r, const int *skip) {
     if (skip && *skip) return;
     extern __shared__ unsigned char smem_raw[];
     ACC *sm = reinterpret_cast<ACC *>(smem_raw);
@@ -327,7 +362,7 @@ __global__ void k_average(DevLevel L, const int *skip) {
 
 // (10)-(11): interior of u = A_II^{-1}(r_I - A_{I Gamma} u_B), interface of u = u_B.
 template <class T, class ACC>
-__global__ void k_post(DevLevel L, const double *r, double *z, const int *skip) {
+__global__ void __launch_bounds__(kGT) k_post(DevLevel L, const double *r, double *z, const int *skip) {
     if (skip && *skip) return;
     extern __shared__ unsigned char smem_raw[];
     ACC *sm = reinterpret_cast<ACC *>(smem_raw);
@@ -1182,9 +1217,16 @@ int vec_grid(int64_t n) {
 }
 
 // Generic path: the streaming kernel when its stages fit in shared memory,
-// else one warp per substructure reading the factor from global memory.
+// else one block of kGT threads per substructure reading the factor from
+// global memory (L2).  BDDC_GENERIC_DIR=1 sends every level that the warp
+// kernels do not take to the latter (read at each launch or capture), so that
+// tests reach it on small problems.
+bool force_generic_dir() {
+    const char *e = std::getenv("BDDC_GENERIC_DIR");
+    return e && e[0] == '1';
+}
 template <class T, class ACC> bool stream_fits(const DevLevel &L) {
-    return StreamSmem::of<T, ACC>(L).total <= 227 * 1024;
+    return !force_generic_dir() && StreamSmem::of<T, ACC>(L).total <= 227 * 1024;
 }
 // Shared memory of the generic interior kernels (the whole interior vector of
 // the largest substructure); a level beyond one block's shared memory has no
@@ -1203,7 +1245,7 @@ template <class T, class ACC> void pre_t(const DevLevel &L, const double *r, con
                  (double *)nullptr, skip);
         return;
     }
-    launch_k(false, k_pre<T, ACC>, L.nsub, 32, generic_smem<ACC>(L), s, L, r, skip);
+    launch_k(false, k_pre<T, ACC>, L.nsub, kGT, generic_smem<ACC>(L), s, L, r, skip);
 }
 template <class T, class ACC> void post_t(const DevLevel &L, const double *r, double *z,
                                           const int *skip, cudaStream_t s) {
@@ -1211,7 +1253,7 @@ template <class T, class ACC> void post_t(const DevLevel &L, const double *r, do
         launch_k(false, k_dir_s<T, ACC, true>, L.nsub, kSB, StreamSmem::of<T, ACC>(L).total, s, L, r, z, skip);
         return;
     }
-    launch_k(false, k_post<T, ACC>, L.nsub, 32, generic_smem<ACC>(L), s, L, r, z, skip);
+    launch_k(false, k_post<T, ACC>, L.nsub, kGT, generic_smem<ACC>(L), s, L, r, z, skip);
 }
 
 }  // namespace

@@ -162,3 +162,35 @@ def test_elasticity_paper_size(lib, levels, constraints, tau):
         assert om <= tau ** (levels - 1) * (1 + 1e-12)
         assert info[0]["kappa_est"] <= om * (1 + 1e-3)
     P.close()
+
+
+GENERIC = {
+    "elastic_2lev_64": lambda: inputs.elasticity(nx=64, sub=16, levels=2, constraints="adaptive", tau=10.0,
+                                                  k=_k(64)),
+    "elastic_3lev_ce": lambda: inputs.elasticity(nx=32, sub=8, levels=3, group=2, constraints="corners+edges",
+                                                  k=_k(32)),
+    "voronoi_2lev": lambda: inputs.three_level_voronoi(nx=128, cells=4, group=2, levels=2, tau=10.0),
+}
+
+
+@pytest.mark.parametrize("name", list(GENERIC))
+def test_generic_dirichlet_kernels(lib, name, monkeypatch):
+    """The one-block-per-substructure Dirichlet kernels (the path of level-2
+    substructures too large for the streaming kernel's stages, as at the
+    paper's size), reached here with BDDC_GENERIC_DIR=1 on every level that
+    the warp kernels do not take."""
+    monkeypatch.setenv("BDDC_GENERIC_DIR", "1")
+    wl = GENERIC[name]()
+    H = obddc.build_workload(wl)
+    P = lib.Problem.from_workload(wl)
+    R = inputs.normal_rhs(wl.n_dof, 17, 2)
+    for j in range(2):
+        z = P.apply(torch.tensor(R[j], device="cuda")).cpu().numpy()
+        assert _relerr(z, H.apply(R[j])) <= 1e-10
+    b = wl.rhs()
+    x8, _ = P.solve(torch.tensor(b, device="cuda"), rtol=1e-30, maxit=8, check=False)
+    assert _relerr(x8.cpu().numpy(), opcg.pcg(H.A, b, H.apply, fixed_iters=8).x) <= 1e-9
+    P.set_precision("fp32")
+    z32 = P.apply(torch.tensor(R[0], device="cuda")).cpu().numpy()
+    assert _relerr(z32, H.apply(R[0])) <= 1e-5
+    P.close()
