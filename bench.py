@@ -56,6 +56,8 @@ def _args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-elasticity", action="store_true",
+                    help="skip the elasticity entry (the paper's own experiment, one process only)")
     ap.add_argument("--batch", type=int, default=BATCH,
                     help="right-hand sides per step (groups of %d, up to three in flight)" % GROUP)
     return ap.parse_args()
@@ -266,6 +268,41 @@ def serving_run(bddc, P, n, rate_rhs, seconds, seed):
                       "continuous batching: three engines of 32 slots" % seed}
 
 
+def elasticity_entry(bddc, batch=32):
+    """The paper's own experiment (Sec. 5): plane elasticity, lambda = 1,
+    mu = 2, 768^2 elements, 48 x 48 substructures, 3 x 3 on level 2, adaptive
+    tau = 3 on both levels; FP32 apply, FP64 PCG to 1e-8.  One solve and a
+    batch of N(0,1) right-hand sides, each timed after a warm-up solve."""
+    import torch
+    from paper_0911_5730_gb300 import inputs
+    wl = inputs.elasticity(nx=768, sub=16, levels=3, group=16, constraints="adaptive", tau=3.0)
+    P = bddc.Problem.from_workload(wl, precision="fp32")
+    try:
+        q = P.query(level=None)
+        b = torch.tensor(wl.rhs(), device="cuda")
+        P.solve(b, rtol=RTOL)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        _, i1 = P.solve(b, rtol=RTOL)
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t) * 1e3
+        B = torch.tensor(inputs.normal_rhs(wl.n_dof, 6001, batch), device="cuda")
+        P.solve(B, rtol=RTOL)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        _, iB = P.solve(B, rtol=RTOL)
+        torch.cuda.synchronize()
+        tb = time.perf_counter() - t
+        return {"workload": "elasticity_768_3lev: 48x48 substructures, 3x3 on level 2, adaptive tau=3",
+                "n_dof": wl.n_dof, "coarse_dofs": q["n_dof"][1:], "setup_ms": q["setup_ms"],
+                "iterations": i1[0]["iters"], "kappa_est": i1[0]["kappa_est"],
+                "relres_true": i1[0]["relres_true"], "single_rhs_ms": ms,
+                "batch": batch, "batch_solves_per_s": batch / tb,
+                "batch_relres_true_max": max(i["relres_true"] for i in iB)}
+    finally:
+        P.close()
+
+
 def replica_barrier(world):
     """Barrier across the replicas (no-op for one process)."""
     if world > 1:
@@ -439,6 +476,12 @@ def gpu_arm(a):
             cpu = cpu_baseline(iters)
         except Exception as ex:       # reported, never silently replaced
             cpu = {"error": str(ex)[:200]}
+    elastic = None
+    if world == 1 and not a.no_elasticity:
+        try:
+            elastic = elasticity_entry(bddc)
+        except Exception as ex:       # reported, never silently replaced
+            elastic = {"error": str(ex)[:200]}
     lat = sorted(ms1)
 
     def pct(v, p):
@@ -465,6 +508,7 @@ def gpu_arm(a):
                     "reduced_single_rhs_fp64_solves_per_s": world * nr64 / tr64,
                     "reduced_iterations": {"fp32": itr32, "fp64": itr64}},
         "setup_ms": setup_s * 1e3,
+        "elasticity": elastic,
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 8 * wl.n_dof * BATCH,
                 "d2h_bytes_per_step": 8 * wl.n_dof * BATCH},
         "roofline": roof,
