@@ -8,7 +8,10 @@ does; with the side x = 0 clamped the 47 vertices on it drop out (4700,
 13724).  The oracle reproduces the same counts from its own code
 (tests/test_oracle_elasticity.py); here they are checked against the paper's
 numbers and the closed forms.  Also: the setup refuses the unclamped
-(singular) mesh and bad Lame parameters before any device work.
+(singular) mesh and bad Lame parameters before any device work, and the
+jagged-edge generators (which stand in for the paper's missing figure) only
+trade elements between the pair, keep both substructures connected and the
+sizes equal, and add no corner.
 """
 import numpy as np
 import pytest
@@ -54,3 +57,41 @@ def test_setup_refuses_before_device_work(lib):
     with pytest.raises(lib.BDDCError) as e:
         lib.Problem(16, wl.k, wl.elem_to_sub, wl.n_sub1, problem="elasticity", lame=(-1.0, 2.0), stream=0)
     assert e.value.code == -1
+
+
+def _connected(nx, e2s, s):
+    from collections import deque
+    lab = e2s.reshape(nx, nx)
+    cells = list(zip(*np.nonzero(lab == s)))
+    seen = {cells[0]}
+    q = deque([cells[0]])
+    while q:
+        j, i = q.popleft()
+        for dj, di in ((0, 1), (0, -1), (1, 0), (-1, 0)):
+            a, b = j + dj, i + di
+            if 0 <= a < nx and 0 <= b < nx and lab[a, b] == s and (a, b) not in seen:
+                seen.add((a, b))
+                q.append((a, b))
+    return len(seen) == len(cells)
+
+
+@pytest.mark.parametrize("nx,sub", [(64, 16), (32, 8), (768, 16)])
+def test_jagged_decomposition_is_a_valid_comb(lib, nx, sub):
+    e2s, ns = inputs.jagged_grid_decomposition(nx, sub, (1, 0))
+    g, _ = inputs.grid_decomposition(nx, sub)
+    moved = np.nonzero(e2s != g)[0]
+    assert set(np.unique(g[moved])) <= {1, 1 + nx // sub}       # only the pair trades elements
+    assert np.all(np.bincount(e2s, minlength=ns) == sub * sub)   # as many teeth each way
+    for s in (1, 1 + nx // sub):
+        assert _connected(nx, e2s, s)
+    r = lib.inspect(nx, e2s, ns, problem="elasticity")
+    rg = lib.inspect(nx, g, ns, problem="elasticity")
+    assert r["n_corners"] == rg["n_corners"] and r["n_edges"] == rg["n_edges"]   # no new corners
+
+
+def test_jagged_grouping_is_a_valid_comb():
+    s2, n2 = inputs.jagged_grid_grouping(48, 16, (1, 0))
+    g2, _ = inputs.grid_grouping(48, 16)
+    moved = np.nonzero(s2 != g2)[0]
+    assert set(np.unique(g2[moved])) <= {1, 4} and len(moved) > 0
+    assert np.all(np.bincount(s2, minlength=n2) == 256)
