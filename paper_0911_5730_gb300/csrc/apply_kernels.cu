@@ -10,8 +10,10 @@
 //  * the streaming Dirichlet kernel (k_dir_s): one block per substructure,
 //    factor blocks streamed through a shared-memory ring, for large or
 //    irregular substructures;
-//  * the generic kernels (k_pre, k_neumann, k_average, k_post), reading the
-//    operators from global memory, for everything else.
+//  * the generic kernels (k_pre, k_neumann, k_average, k_post), one block
+//    per substructure reading the operators from global memory (L2), for
+//    everything else (the level-2 substructures of the three-level
+//    elasticity problem).
 // Operators are read in the storage type T (double, float or bfloat16) and
 // accumulated in ACC (double for the FP64 path, float otherwise); global
 // vectors stay FP64.
