@@ -47,7 +47,7 @@ __device__ __forceinline__ int64_t fpos(int r, int c, int ld, bool swz) {
 // one pass.  Every thread of the block calls it (block-wide barriers).
 constexpr int kGT = 512;   // threads of a generic Dirichlet kernel's block (one per substructure)
 
-template <int TPR, class T, class ACC>
+template <int TPR, class ACC>
 __device__ __forceinline__ ACC dsolve_sum(ACC v) {
 #pragma unroll
     for (int o = TPR / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -69,7 +69,7 @@ __device__ void dirichlet_solve_t(const T *F, int b, int m, bool swz, ACC *x, AC
                 const ACC *xp = x + (j - 1) * b;
                 for (int c = part; c < b; c += TPR) a += ld<T, ACC>(Lsub + fpos(r, c, ldb, swz)) * xp[c];
             }
-            a = dsolve_sum<TPR, T, ACC>(a);
+            a = dsolve_sum<TPR, ACC>(a);
             if (r < b && part == 0) tmp[r] = x[j * b + r] - a;
         }
         __syncthreads();
@@ -78,7 +78,7 @@ __device__ void dirichlet_solve_t(const T *F, int b, int m, bool swz, ACC *x, AC
             ACC a = 0;
             if (r < b)
                 for (int c = part; c <= r; c += TPR) a += ld<T, ACC>(Linv + fpos(r, c, ldb, swz)) * tmp[c];
-            a = dsolve_sum<TPR, T, ACC>(a);
+            a = dsolve_sum<TPR, ACC>(a);
             if (r < b && part == 0) x[j * b + r] = a;
         }
         __syncthreads();
@@ -94,7 +94,7 @@ __device__ void dirichlet_solve_t(const T *F, int b, int m, bool swz, ACC *x, AC
                 const ACC *xn = x + (j + 1) * b;
                 for (int c = part; c < b; c += TPR) a += ld<T, ACC>(Lsub1 + fpos(c, r, ldb, swz)) * xn[c];
             }
-            a = dsolve_sum<TPR, T, ACC>(a);
+            a = dsolve_sum<TPR, ACC>(a);
             if (r < b && part == 0) tmp[r] = x[j * b + r] - a;
         }
         __syncthreads();
@@ -103,7 +103,7 @@ __device__ void dirichlet_solve_t(const T *F, int b, int m, bool swz, ACC *x, AC
             ACC a = 0;
             if (r < b)
                 for (int c = r + part; c < b; c += TPR) a += ld<T, ACC>(Linv + fpos(c, r, ldb, swz)) * tmp[c];
-            a = dsolve_sum<TPR, T, ACC>(a);
+            a = dsolve_sum<TPR, ACC>(a);
             if (r < b && part == 0) x[j * b + r] = a;
         }
         __syncthreads();

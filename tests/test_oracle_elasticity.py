@@ -26,7 +26,9 @@ Checked against what mathematics and the paper fix, not against the oracle:
   omega~ <= tau^2 on three levels;
 * brute force on two substructures: the pair problem is the whole problem,
   so lambda_max(M^{-1} A) is the first local eigenvalue and, after the n
-  selected constraints, the (n+1)-st.
+  selected constraints, the (n+1)-st;
+* Table 3's observation: the jagged edge carries the large local
+  eigenvalues, the regular edges stay in the paper's range.
 """
 import numpy as np
 import pytest
@@ -185,3 +187,20 @@ def test_two_substructure_brute_force():
         n = adaptive.select(lam, tau)
         assert H.bl[0].nc == len(bddc.corner_dofs(lv)) + n
         assert np.isclose(lmax(H), lam[n], rtol=1e-8)
+
+
+def test_jagged_edge_dominates_local_eigenvalues():
+    """Table 3's observation: the jagged edge carries the large eigenvalues
+    (the paper's pair (2, 50): 24.3 ... 13.1 over its first eight, the regular
+    pairs 3.4-12.6 at most).  On a 4 x 4 grid of H/h = 16 substructures with
+    the comb between substructures 1 and 5, the jagged edge's fourth
+    eigenvalue exceeds the first eigenvalue of every regular edge, and those
+    stay within the paper's range."""
+    wl = inputs.elasticity(nx=64, sub=16, levels=2, constraints="adaptive", tau=10.0)
+    H = bddc.build_workload(wl)
+    reps = H.info["edge_reports"][0]
+    jag = [r for r in reps if r["pair"] == (1, 5)][0]
+    reg = [r["lam"][0] for r in reps if r["pair"] != (1, 5)]
+    assert jag["lam"][3] > max(reg)
+    assert 3.0 < min(reg) and max(reg) < 13.0
+    assert jag["n_sel"] >= 4 and all(r["n_sel"] <= 1 for r in reps if r["pair"] != (1, 5))
