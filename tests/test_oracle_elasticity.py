@@ -28,7 +28,9 @@ Checked against what mathematics and the paper fix, not against the oracle:
   so lambda_max(M^{-1} A) is the first local eigenvalue and, after the n
   selected constraints, the (n+1)-st;
 * Table 3's observation: the jagged edge carries the large local
-  eigenvalues, the regular edges stay in the paper's range.
+  eigenvalues, the regular edges stay in the paper's range; Tables 4-5 on
+  level 2: the jagged level-2 edge dominates, and level-2 eigenvalues grow
+  as level 1 is constrained more tightly.
 """
 import numpy as np
 import pytest
@@ -204,3 +206,24 @@ def test_jagged_edge_dominates_local_eigenvalues():
     assert jag["lam"][3] > max(reg)
     assert 3.0 < min(reg) and max(reg) < 13.0
     assert jag["n_sel"] >= 4 and all(r["n_sel"] <= 1 for r in reps if r["pair"] != (1, 5))
+
+
+def test_jagged_level_two_edge_tables_4_and_5():
+    """Tables 4-5's observations on level 2: the jagged level-2 edge has the
+    largest local eigenvalue and needs the most constraints, and the level-2
+    eigenvalues grow when level 1 is constrained more tightly (the paper's
+    jagged pair: 23.2 at tau = 10, 84.3 at tau = 2).  128^2 mesh, 16 x 16
+    level-1 substructures, 2 x 2 on level 2 with the comb between level-2
+    substructures 1 and 3."""
+    top = {}
+    for tau in (10.0, 2.0):
+        wl = inputs.elasticity(nx=128, sub=8, levels=3, group=8, constraints="adaptive", tau=tau)
+        H = bddc.build_workload(wl)
+        reps = H.info["edge_reports"][1]
+        jag = [r for r in reps if r["pair"] == (1, 3)][0]
+        others = [r for r in reps if r["pair"] != (1, 3)]
+        assert jag["lam"][0] > max(r["lam"][0] for r in others)
+        assert jag["n_sel"] >= max(r["n_sel"] for r in others)
+        assert H.info["omega_tilde"] <= tau ** 2 * (1 + 1e-12)
+        top[tau] = jag["lam"][0]
+    assert top[2.0] > top[10.0]
