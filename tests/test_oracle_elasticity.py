@@ -30,10 +30,14 @@ Checked against what mathematics and the paper fix, not against the oracle:
 * Table 3's observation: the jagged edge carries the large local
   eigenvalues, the regular edges stay in the paper's range; Tables 4-5 on
   level 2: the jagged level-2 edge dominates, and level-2 eigenvalues grow
-  as level 1 is constrained more tightly.
+  as level 1 is constrained more tightly;
+* the reading the GPU edge solver implements: the reduced edge form has the
+  literal form's eigenvalues, and its null space is exactly the rigid
+  motions on the edge when both substructures float (none otherwise).
 """
 import numpy as np
 import pytest
+import scipy.linalg as sla
 import scipy.sparse.linalg as spla
 
 from oracle import adaptive, bddc, fem, levels, pcg
@@ -227,3 +231,51 @@ def test_jagged_level_two_edge_tables_4_and_5():
         assert H.info["omega_tilde"] <= tau ** 2 * (1 + 1e-12)
         top[tau] = jag["lam"][0]
     assert top[2.0] > top[10.0]
+
+
+@pytest.mark.parametrize("pair", [(5, 6), (5, 9), (0, 1), (1, 5)])
+def test_reduced_edge_form_projects_the_rigid_motions(pair):
+    """The GPU solves the edge problem in its reduced form (every interface
+    DOF but the edge eliminated by energy minimisation, the shared corners as
+    one unknown) and projects out the rigid motions restricted to the edge,
+    the same on both sides, when both substructures float (Sec. 3: null S is
+    in the range of the rigid-body modes).  Here: the reduced form's non-zero
+    eigenvalues equal the literal Theorem 1 form's, and the numerical null
+    space of the reduced matrix is exactly the span of [z_E; z_E] for the
+    three rigid motions z (floating pairs) or empty (a clamped substructure)."""
+    from test_oracle_adaptive import reduced_edge_pencil
+    wl = inputs.elasticity(nx=64, sub=16, levels=2, constraints="corners")
+    lv = levels.level_one_elasticity(64, wl.k, wl.elem_to_sub, wl.n_sub1)
+    cd = bddc.corner_dofs(lv)
+    (s, t), ed = [(p, d) for p, d in lv.edges if p == pair][0]
+    Ss, St = lv.schur(s), lv.schur(t)
+    pp = adaptive.PairProblem(lv, s, t, ed, Ss, St, cd)
+    lam_r, W, Xd = reduced_edge_pencil(lv, s, t, ed, Ss, St)
+    big = pp.lam[pp.lam > 1e-8 * pp.lam[0]]
+    assert np.allclose(lam_r[:len(big)], big, rtol=1e-8)
+    # the reduced matrix itself: rebuild it and take its null space
+    Gs = list(lv.sub_dofs[s][lv.interface_local(s)])
+    Gt = list(lv.sub_dofs[t][lv.interface_local(t)])
+    shared = [g for g in Gs if g in set(Gt) and lv.is_corner[g]]
+
+    def red(S, G):
+        keep = [G.index(g) for g in ed] + [G.index(g) for g in shared]
+        oth = [a for a in range(len(G)) if a not in keep]
+        return S[np.ix_(keep, keep)] - S[np.ix_(keep, oth)] @ np.linalg.solve(S[np.ix_(oth, oth)], S[np.ix_(oth, keep)])
+
+    Rs, Rt = red(Ss, Gs), red(St, Gt)
+    ne, nc = len(ed), len(shared)
+    M = np.zeros((2 * ne + nc, 2 * ne + nc))
+    M[:ne, :ne], M[:ne, 2 * ne:], M[2 * ne:, :ne] = Rs[:ne, :ne], Rs[:ne, ne:], Rs[ne:, :ne]
+    M[ne:2 * ne, ne:2 * ne], M[ne:2 * ne, 2 * ne:], M[2 * ne:, ne:2 * ne] = Rt[:ne, :ne], Rt[:ne, ne:], Rt[ne:, :ne]
+    M[2 * ne:, 2 * ne:] = Rs[ne:, ne:] + Rt[ne:, ne:]
+    Mt = M[:2 * ne, :2 * ne] - M[:2 * ne, 2 * ne:] @ np.linalg.solve(M[2 * ne:, 2 * ne:], M[2 * ne:, :2 * ne])
+    N = adaptive.null_space_sym(Mt)
+    floating = s % 4 != 0 and t % 4 != 0          # column 0 touches the clamped side
+    if not floating:
+        assert N.shape[1] == 0
+        return
+    zE = fem.rigid_modes(lv.coords[ed], lv.comp[ed])
+    Z = np.vstack([zE, zE])
+    assert N.shape[1] == 3
+    assert np.max(sla.subspace_angles(N, Z)) < 1e-6
