@@ -33,8 +33,11 @@ Checked against what mathematics and the paper fix, not against the oracle:
   as level 1 is constrained more tightly;
 * the reading the GPU edge solver implements: the reduced edge form has the
   literal form's eigenvalues, and its null space is exactly the rigid
-  motions on the edge when both substructures float (none otherwise).
+  motions on the edge when both substructures float (none otherwise); on
+  level 2 exactly the coarse values of the rigid motions.
 """
+import functools
+
 import numpy as np
 import pytest
 import scipy.linalg as sla
@@ -44,6 +47,14 @@ from oracle import adaptive, bddc, fem, levels, pcg
 from paper_0911_5730_gb300 import inputs
 
 LAM, MU = 1.0, 2.0
+
+
+@functools.lru_cache(maxsize=None)
+def _three_level(tau):
+    """128^2 mesh, 16 x 16 level-1 substructures, 2 x 2 on level 2 with the
+    comb between level-2 substructures 1 and 3; adaptive on both levels."""
+    wl = inputs.elasticity(nx=128, sub=8, levels=3, group=8, constraints="adaptive", tau=tau)
+    return bddc.build_workload(wl)
 
 
 def test_element_patch_test_rigid_modes_rank():
@@ -221,8 +232,7 @@ def test_jagged_level_two_edge_tables_4_and_5():
     substructures 1 and 3."""
     top = {}
     for tau in (10.0, 2.0):
-        wl = inputs.elasticity(nx=128, sub=8, levels=3, group=8, constraints="adaptive", tau=tau)
-        H = bddc.build_workload(wl)
+        H = _three_level(tau)
         reps = H.info["edge_reports"][1]
         jag = [r for r in reps if r["pair"] == (1, 3)][0]
         others = [r for r in reps if r["pair"] != (1, 3)]
@@ -231,6 +241,30 @@ def test_jagged_level_two_edge_tables_4_and_5():
         assert H.info["omega_tilde"] <= tau ** 2 * (1 + 1e-12)
         top[tau] = jag["lam"][0]
     assert top[2.0] > top[10.0]
+
+
+def _reduced_mt(lv, s, t, ed, Ss, St):
+    """The reduced edge matrix: every interface DOF of s and t but the edge
+    eliminated by energy minimisation, the shared corners one unknown, then
+    eliminated too."""
+    Gs = list(lv.sub_dofs[s][lv.interface_local(s)])
+    Gt = list(lv.sub_dofs[t][lv.interface_local(t)])
+    shared = [g for g in Gs if g in set(Gt) and lv.is_corner[g]]
+
+    def red(S, G):
+        keep = [G.index(g) for g in ed] + [G.index(g) for g in shared]
+        oth = [a for a in range(len(G)) if a not in keep]
+        return S[np.ix_(keep, keep)] - S[np.ix_(keep, oth)] @ np.linalg.solve(S[np.ix_(oth, oth)], S[np.ix_(oth, keep)])
+
+    Rs, Rt = red(Ss, Gs), red(St, Gt)
+    ne, nc = len(ed), len(shared)
+    M = np.zeros((2 * ne + nc, 2 * ne + nc))
+    M[:ne, :ne], M[:ne, 2 * ne:], M[2 * ne:, :ne] = Rs[:ne, :ne], Rs[:ne, ne:], Rs[ne:, :ne]
+    M[ne:2 * ne, ne:2 * ne], M[ne:2 * ne, 2 * ne:], M[2 * ne:, ne:2 * ne] = Rt[:ne, :ne], Rt[:ne, ne:], Rt[ne:, :ne]
+    M[2 * ne:, 2 * ne:] = Rs[ne:, ne:] + Rt[ne:, ne:]
+    if nc == 0:
+        return M[:2 * ne, :2 * ne]
+    return M[:2 * ne, :2 * ne] - M[:2 * ne, 2 * ne:] @ np.linalg.solve(M[2 * ne:, 2 * ne:], M[2 * ne:, :2 * ne])
 
 
 @pytest.mark.parametrize("pair", [(5, 6), (5, 9), (0, 1), (1, 5)])
@@ -253,23 +287,7 @@ def test_reduced_edge_form_projects_the_rigid_motions(pair):
     lam_r, W, Xd = reduced_edge_pencil(lv, s, t, ed, Ss, St)
     big = pp.lam[pp.lam > 1e-8 * pp.lam[0]]
     assert np.allclose(lam_r[:len(big)], big, rtol=1e-8)
-    # the reduced matrix itself: rebuild it and take its null space
-    Gs = list(lv.sub_dofs[s][lv.interface_local(s)])
-    Gt = list(lv.sub_dofs[t][lv.interface_local(t)])
-    shared = [g for g in Gs if g in set(Gt) and lv.is_corner[g]]
-
-    def red(S, G):
-        keep = [G.index(g) for g in ed] + [G.index(g) for g in shared]
-        oth = [a for a in range(len(G)) if a not in keep]
-        return S[np.ix_(keep, keep)] - S[np.ix_(keep, oth)] @ np.linalg.solve(S[np.ix_(oth, oth)], S[np.ix_(oth, keep)])
-
-    Rs, Rt = red(Ss, Gs), red(St, Gt)
-    ne, nc = len(ed), len(shared)
-    M = np.zeros((2 * ne + nc, 2 * ne + nc))
-    M[:ne, :ne], M[:ne, 2 * ne:], M[2 * ne:, :ne] = Rs[:ne, :ne], Rs[:ne, ne:], Rs[ne:, :ne]
-    M[ne:2 * ne, ne:2 * ne], M[ne:2 * ne, 2 * ne:], M[2 * ne:, ne:2 * ne] = Rt[:ne, :ne], Rt[:ne, ne:], Rt[ne:, :ne]
-    M[2 * ne:, 2 * ne:] = Rs[ne:, ne:] + Rt[ne:, ne:]
-    Mt = M[:2 * ne, :2 * ne] - M[:2 * ne, 2 * ne:] @ np.linalg.solve(M[2 * ne:, 2 * ne:], M[2 * ne:, :2 * ne])
+    Mt = _reduced_mt(lv, s, t, ed, Ss, St)
     N = adaptive.null_space_sym(Mt)
     floating = s % 4 != 0 and t % 4 != 0          # column 0 touches the clamped side
     if not floating:
@@ -277,5 +295,28 @@ def test_reduced_edge_form_projects_the_rigid_motions(pair):
         return
     zE = fem.rigid_modes(lv.coords[ed], lv.comp[ed])
     Z = np.vstack([zE, zE])
+    assert N.shape[1] == 3
+    assert np.max(sla.subspace_angles(N, Z)) < 1e-6
+
+
+@pytest.mark.parametrize("pair", [(1, 3), (0, 1)])
+def test_level_two_edge_null_space_is_the_coarse_rigid_motions(pair):
+    """On level 2 the null vectors are the coarse values of the rigid
+    motions, sum_k w_k z(dof_k) for every level-1 coarse DOF (Sec. 3: the
+    coarse basis functions span the rigid-body modes): the reduced level-2
+    edge matrix of a floating pair (the jagged one, level-2 substructures 1
+    and 3) has exactly that null space, a pair with a clamped substructure
+    none."""
+    H = _three_level(10.0)
+    lv1, lv2 = H.bl[0].lv, H.bl[1].lv
+    Z1 = fem.rigid_modes(lv1.coords, lv1.comp)
+    Zc = np.array([cd.weights @ Z1[cd.dofs] for cd in H.bl[0].cdofs])
+    (s, t), ed = [(p, d) for p, d in lv2.edges if p == pair][0]
+    Mt = _reduced_mt(lv2, s, t, ed, lv2.schur(s), lv2.schur(t))
+    N = adaptive.null_space_sym(Mt)
+    if 0 in pair or 2 in pair:                    # column 0 of the 2 x 2 grid: clamped
+        assert N.shape[1] == 0
+        return
+    Z = np.vstack([Zc[ed], Zc[ed]])
     assert N.shape[1] == 3
     assert np.max(sla.subspace_angles(N, Z)) < 1e-6
