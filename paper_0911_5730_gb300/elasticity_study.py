@@ -30,7 +30,7 @@ import torch
 from . import bddc, inputs
 
 # (levels, constraints, tau) -> the paper's (Nc, C, omega~, kappa, it); Tables 1, 2, 6, 7
-PAPER = {
+TABLE_VALUES = {
     (2, "corners", math.inf): ("4794", "9.3", "-", "18.41", "43"),
     (2, "corners+edges", math.inf): ("13818", "26.9", "-", "18.43", "32"),
     (2, "adaptive", 10.0): ("4805", "9.4", "8.67", "8.34", "34"),
@@ -45,7 +45,7 @@ PAPER = {
 
 
 def rows_for(levels):
-    return [k for k in PAPER if k[0] in levels]
+    return [k for k in TABLE_VALUES if k[0] in levels]
 
 
 def run(levels=(2, 3), nx: int = 768, batch: int = 32) -> list[dict]:
@@ -78,7 +78,7 @@ def run(levels=(2, 3), nx: int = 768, batch: int = 32) -> list[dict]:
                     "iters_fp32": i32[0]["iters"], "relres_fp32": i32[0]["relres_true"],
                     "setup_ms": q["setup_ms"], "solve_ms_fp32": ms, "batch_solves_per_s_fp32": bps,
                     "batch_relres_max": max(j["relres_true"] for j in iB),
-                    "sub_dofs": sub_dofs, "paper": PAPER[(lev, mode, tau)]})
+                    "sub_dofs": sub_dofs, "paper": TABLE_VALUES[(lev, mode, tau)]})
         print(table(out[-1:]).splitlines()[-1], file=sys.stderr, flush=True)
         P.close()
     return out
