@@ -20,7 +20,9 @@ Checked against what mathematics and the paper fix, not against the oracle:
 * the null space of a floating substructure's Schur complement is spanned by
   the rigid motions (three of them);
 * BDDC: every interface DOF constrained gives M^{-1} = A^{-1} (2 and 3
-  levels); M^{-1} is symmetric with eigenvalues of M^{-1} A >= 1; two levels
+  levels); M^{-1} is symmetric with eigenvalues of M^{-1} A >= 1 (2 and 3
+  levels); scaling the material by c scales M^{-1} by exactly 1 / c and
+  keeps the selected constraints; two levels
   with an exact level 2 equal the two-level method; PCG reaches the direct
   solution; adaptive selection meets kappa <= tau (Theorem 2) and
   omega~ <= tau^2 on three levels;
@@ -142,9 +144,10 @@ def test_all_interface_is_exact(lev):
     assert np.linalg.norm(H.apply(b) - x) <= 1e-10 * np.linalg.norm(x)
 
 
-@pytest.mark.parametrize("mode", ["corners", "corners+edges", "adaptive"])
-def test_symmetric_and_lower_bound(mode):
-    wl = inputs.elasticity(nx=16, sub=4, levels=2, constraints=mode, tau=3.0, jagged=False)
+@pytest.mark.parametrize("lev,mode", [(2, "corners"), (2, "corners+edges"), (2, "adaptive"),
+                                      (3, "corners+edges"), (3, "adaptive")])
+def test_symmetric_and_lower_bound(lev, mode):
+    wl = inputs.elasticity(nx=16, sub=4, levels=lev, group=2, constraints=mode, tau=3.0, jagged=False)
     H = bddc.build_workload(wl)
     M = _M(H)
     assert np.abs(M - M.T).max() <= 1e-10 * np.abs(M).max()
@@ -320,3 +323,19 @@ def test_level_two_edge_null_space_is_the_coarse_rigid_motions(pair):
     Z = np.vstack([Zc[ed], Zc[ed]])
     assert N.shape[1] == 3
     assert np.max(sla.subspace_angles(N, Z)) < 1e-6
+
+
+@pytest.mark.parametrize("lev", [2, 3])
+def test_material_scaling_scales_the_preconditioner(lev):
+    """A = sum_e k_e K_e is linear in the Lame parameters, and every BDDC
+    ingredient (interior solves, weights, coarse basis, adaptive selection)
+    is invariant under a common factor except the solves, which scale by its
+    inverse: with (lambda, mu) -> c (lambda, mu), M^{-1} -> M^{-1} / c and the
+    selected constraints stay the same."""
+    base = dict(nx=32, sub=8, levels=lev, group=2, constraints="adaptive", tau=3.0)
+    H1 = bddc.build_workload(inputs.elasticity(**base))
+    H7 = bddc.build_workload(inputs.elasticity(lame=(7.0, 14.0), **base))
+    b = inputs.normal_rhs(H1.n, 23)
+    z1, z7 = H1.apply(b), H7.apply(b)
+    assert np.linalg.norm(7.0 * z7 - z1) <= 1e-11 * np.linalg.norm(z1)
+    assert [r["n_sel"] for r in H1.info["edge_reports"][0]] == [r["n_sel"] for r in H7.info["edge_reports"][0]]
