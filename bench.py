@@ -60,6 +60,10 @@ def _args():
                     help="skip the elasticity entry (the paper's own experiment, one process only)")
     ap.add_argument("--batch", type=int, default=BATCH,
                     help="right-hand sides per step (groups of %d, up to three in flight)" % GROUP)
+    ap.add_argument("--profile-apply", choices=["fp64", "fp32", "bf16"], default=None,
+                    help="only time each kernel of the batched apply (%d right-hand sides) of the "
+                         "workload with CUDA events, print them and exit" % GROUP)
+    ap.add_argument("--reps", type=int, default=20, help="applies timed by --profile-apply")
     return ap.parse_args()
 
 
@@ -526,6 +530,23 @@ def gpu_arm(a):
         torch.distributed.destroy_process_group()
 
 
+def profile_apply(a):
+    """Per-kernel device times of the batched apply (one group of GROUP
+    right-hand sides) in one precision: the entry point of the ncu captures."""
+    import torch
+    from paper_0911_5730_gb300 import bddc, inputs
+    wl = inputs.two_level_channels()
+    P = bddc.Problem.from_workload(wl, precision=a.profile_apply)
+    q = P.query(level=1)
+    B = torch.tensor(inputs.normal_rhs(wl.n_dof, RHS_SEED, GROUP), device="cuda")
+    prof = P.profile_apply_batch(B, reps=a.reps)
+    names = ["pre", "neumann", "top_solve", "average", "post"]
+    route = os.environ.get("BDDC_TC", "default") if q["tc_levels"] & 1 else "sweeps (no dense operands)"
+    print(json.dumps({"workload": WORKLOAD, "precision": a.profile_apply, "rhs": GROUP, "reps": a.reps,
+                      "interior_route": route, "ms": {nm: float(t) for nm, t in zip(names, prof)}}))
+    P.close()
+
+
 def reference_arm(a):
     rank, world, _ = _dist()
     if rank != 0:
@@ -573,5 +594,7 @@ if __name__ == "__main__":
     BATCH = args.batch
     if args.impl == "reference":
         reference_arm(args)
+    elif args.profile_apply:
+        profile_apply(args)
     else:
         gpu_arm(args)

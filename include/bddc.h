@@ -139,7 +139,12 @@ typedef struct {
      * used): node tile of the batched PCG stencil (x, y) and rows per block of
      * the top-level product; 0 before the first batched call */
     int32_t tuned_tile[3];
-    int32_t reserved2;
+    /* bit l-1 set: the batched interior corrections of BDDC level l (eqs. 4-5
+     * and 10-11) run as dense tensor-core products (tcgen05) in FP32 and BF16
+     * applies; the setup formed A_II^{-1} and A_II^{-1} A_{I Gamma} per
+     * substructure in FP64 for it (levels whose interiors hold 128 to 256
+     * DOFs).  Environment BDDC_TC=0 keeps them on the triangular sweeps. */
+    int32_t tc_levels;
 } bddc_info;
 
 /*

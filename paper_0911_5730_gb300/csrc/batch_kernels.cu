@@ -1344,13 +1344,6 @@ __global__ void k_b_norm2(int64_t nK, int K, const double *v, double *part, unsi
     grid_reduce_k(s, K, part, counter, [&](int kk, double tot) { out[kk] = tot; }, NoPost{});
 }
 
-// r(:, k) = res(:, k) for the right-hand sides that restart
-__global__ void k_b_restart(int64_t nK, int K, const double *res, double *r, const BatchScalars *sc) {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= nK) return;
-    const int k = (int)(e % K);
-    if (sc->fresh[k] && !sc->done[k]) r[e] = res[e];
-}
 
 // dst[g * K + k] = src[k * ld + g] and back
 __global__ void k_b_gather(int n, int K, const double *src, int64_t ld, double *dst) {
@@ -1500,6 +1493,7 @@ namespace {
 struct BatchRoute {
     bool dir_staged = false, neu_staged = false, avg_staged = false;
     bool dir_stream = false;   // the streaming Dirichlet kernel
+    bool pre_tc = false, post_tc = false;   // the tensor-core products (tc_kernels.cu)
     bool ok = false;
 };
 
@@ -1528,7 +1522,9 @@ template <class T, class ACC> BatchRoute route_t(const DevLevel &L, int prec) {
         if (stream) R.dir_staged = false, R.dir_stream = true;
         if (bg) R.neu_staged = R.avg_staged = false;
     }
-    R.ok = (R.dir_staged || R.dir_stream) && (R.neu_staged || bg) && (R.avg_staged || bg);
+    R.pre_tc = tc_route(L, prec, false);
+    R.post_tc = tc_route(L, prec, true);
+    R.ok = (R.dir_staged || R.dir_stream || (R.pre_tc && R.post_tc)) && (R.neu_staged || bg) && (R.avg_staged || bg);
     return R;
 }
 
@@ -1629,7 +1625,8 @@ void pre_b(const DevLevel &L, const BatchLevel &B, int prec, const double *r, co
            cudaEvent_t *ev) {
     const BatchRoute R = route_t<T, ACC>(L, prec);
     if (ev) cudaEventRecord(ev[0], s);
-    if (R.dir_staged) dir_b<T, ACC>(L, B, false, r, nullptr, skip, s);
+    if (R.pre_tc) tc_dir_b(L, B, prec, false, r, nullptr, skip, nullptr, s);
+    else if (R.dir_staged) dir_b<T, ACC>(L, B, false, r, nullptr, skip, s);
     else dir_bs<T, ACC>(L, B, false, r, nullptr, skip, nullptr, s);
     if (ev) cudaEventRecord(ev[1], s);
     if (R.neu_staged) neu_b<T, ACC>(L, B, prec, r, skip, s);
@@ -1645,7 +1642,8 @@ void post_b(const DevLevel &L, const BatchLevel &B, int prec, const double *r, d
     if (R.avg_staged) avg_b<T, ACC>(L, B, prec, skip, s);
     else launch_plain(k_avg_bg<T, ACC>, L.nsub, kNBT, neu_bg_smem<T, ACC>(L), s, L, B, pidx_b(prec), skip);
     if (ev) cudaEventRecord(ev[1], s);
-    if (R.dir_staged) dir_b<T, ACC>(L, B, true, r, z, skip, s, rz);
+    if (R.post_tc) tc_dir_b(L, B, prec, true, r, z, skip, rz, s);
+    else if (R.dir_staged) dir_b<T, ACC>(L, B, true, r, z, skip, s, rz);
     else dir_bs<T, ACC>(L, B, true, r, z, skip, rz, s);
     if (ev) cudaEventRecord(ev[2], s);
 }
@@ -1693,6 +1691,7 @@ void prepare_batch_kernels() {
     BDDC_SMEM_ATTR_B((k_avg_bg<__nv_bfloat16, float>));
     BDDC_SMEM_ATTR_B((k_avg_b<double, double>)); BDDC_SMEM_ATTR_B((k_avg_b<float, float>));
     BDDC_SMEM_ATTR_B((k_avg_b<__nv_bfloat16, float>));
+    prepare_tc_kernels();
 #undef BDDC_DIR_B
 #undef BDDC_SMEM_ATTR_B
 }
@@ -1842,11 +1841,6 @@ void launch_b_admit(int n, int K, int k, const double *b, double *x, double *r, 
 }
 void launch_b_column(int n, int K, int k, const double *x, double *dst, cudaStream_t s) {
     if (n > 0) k_b_column<<<(n + 255) / 256, 256, 0, s>>>(n, K, k, x, dst);
-}
-void launch_b_restart(int n, int K, const double *res, double *r, const BatchScalars *sc,
-                      cudaStream_t s) {
-    const int64_t nK = (int64_t)n * K;
-    k_b_restart<<<(int)((nK + 255) / 256), 256, 0, s>>>(nK, K, res, r, sc);
 }
 void launch_selftest_convert(const double *d, int64_t n, unsigned long long *bad, cudaStream_t s) {
     if (n > 0) k_selftest_convert<<<(int)((n + 255) / 256), 256, 0, s>>>(d, n, bad);

@@ -65,6 +65,7 @@ struct LevelData {
     std::vector<char> cbnd;            // coarse DOF is a point value on the boundary
     int nc = 0;
     int64_t sumI = 0, sumG = 0, sumC = 0, bandnnz = 0, blockent = 0, coonnz = 0, nent = 0, pent = 0;
+    std::unique_ptr<TcLevel> tc;       // dense operands of the tensor-core interior corrections
 };
 
 // Buffers of the batched solve (allocated on first use, sized for kMaxBatch).
@@ -575,6 +576,9 @@ void setup_level(bddc_ctx *C, LevelData &LD, const double *emat, const std::vect
     check_err(err, st, "interior Cholesky");
     launch_schur(S, D.max_nG, st);
     launch_dirichlet_blocks(S, D, nullptr, nullptr, st);
+    LD.tc = std::make_unique<TcLevel>();
+    tc_build_level(S, D, nI, nG, idxI, idxG, own, oOwn, H.iface_dof, *LD.tc, A, tmp, st);
+    D.tc = LD.tc->ok ? LD.tc.get() : nullptr;
     double *diag_sum = tmp.alloc_n<double>(std::max(D.n_iface, 1));
     BDDC_CUDA_TRY(cudaMemsetAsync(diag_sum, 0, sizeof(double) * std::max(D.n_iface, 1), st));
     launch_weights(S, D, diag_sum, st);
@@ -888,13 +892,15 @@ int pcg_one(bddc_ctx *C, Workspace &W, int prec, const double *b, double *x, dou
         BDDC_CUDA_TRY(cudaStreamSynchronize(st));
         rr_true = W.hout[0];
         if (W.hsc->conv && rr_true > W.hsc->tol2 && W.hsc->it < maxit) {
-            // the recursive residual drifted: restart from the true residual
-            // with a fresh direction (beta = 0)
+            // the recursive residual met the tolerance but the true one did
+            // not: keep iterating from the same iterate, residual and
+            // direction, as if the recursive test had failed (Sec. 5 stopping
+            // rule, read as in the oracle): the apply the stop skipped gives
+            // z = M r, rho and beta, and the iterations resume
             PcgScalars hs = *W.hsc;
-            hs.done = 0; hs.conv = 0; hs.fresh = 1; hs.rr = rr_true;
+            hs.done = 0; hs.conv = 0;
             *W.hsc = hs;
             BDDC_CUDA_TRY(cudaMemcpyAsync(W.sc, W.hsc, sizeof(PcgScalars), cudaMemcpyHostToDevice, st));
-            BDDC_CUDA_TRY(cudaMemcpyAsync(W.r, W.tmp, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
             apply_rec(C, W, 0, prec, W.r, W.z, &W.sc->done, st, &rz);
             launches += per_apply;
             chunk = 1;
@@ -1036,7 +1042,8 @@ int pcg_reduced(bddc_ctx *C, Workspace &W, int prec, const double *b, double *x,
         BDDC_CUDA_TRY(cudaStreamSynchronize(st));
         if (!R.hsc->done) { chunk = std::max(1, std::min(chunk / 2, 16)); continue; }
         // reconstruct x = [A_II^-1 (b_I - A_IG x_G); x_G] and confirm with the
-        // true residual; restart from it with a fresh direction if needed
+        // true residual; keep iterating (same iterate, residual and direction)
+        // if it is not yet met
         BDDC_CUDA_TRY(cudaMemcpyAsync(D.uB, R.x, sizeof(double) * std::max(ng, 1), cudaMemcpyDeviceToDevice, st));
         apply_level_dir(D, BDDC_PREC_FP64, true, b, W.x, nullptr, st, nullptr);
         op_residual(C, b, W.x, W.tmp, st);
@@ -1046,10 +1053,9 @@ int pcg_reduced(bddc_ctx *C, Workspace &W, int prec, const double *b, double *x,
         rr_true = W.hout[0];
         if (R.hsc->conv && rr_true > R.hsc->tol2 && R.hsc->it < maxit) {
             RedScalars hs = *R.hsc;
-            hs.done = 0; hs.conv = 0; hs.fresh = 1; hs.rr = rr_true;
+            hs.done = 0; hs.conv = 0;
             *R.hsc = hs;
             BDDC_CUDA_TRY(cudaMemcpyAsync(R.sc, R.hsc, sizeof(RedScalars), cudaMemcpyHostToDevice, st));
-            launch_red_restart(ng, D.ifaceDof, W.tmp, R.r, st);
             start();
             chunk = 1;
             continue;
@@ -1253,18 +1259,18 @@ int pcg_batch(bddc_ctx *C, Workspace &W, int prec, const double *b, int64_t ldb,
         bool again = false;
         for (int k = 0; k < K; ++k) {
             if (h.conv[k] && BW.hnrm[k] > h.tol2[k] && h.it[k] < maxit) {
-                // the recursive residual drifted: restart this one from the
-                // true residual with a fresh direction
-                h.done[k] = 0; h.conv[k] = 0; h.fresh[k] = 1; h.rr[k] = BW.hnrm[k];
+                // the true residual is not yet met: this one keeps iterating
+                // from the same iterate, residual and direction (the apply
+                // below gives its z, rho and beta; the others stay done)
+                h.done[k] = 0; h.conv[k] = 0;
                 again = true;
             }
         }
         if (!again) break;
         h.all_done = 0;
         BDDC_CUDA_TRY(cudaMemcpyAsync(BW.sc, BW.hsc, sizeof(BatchScalars), cudaMemcpyHostToDevice, st));
-        launch_b_restart(n, K, BW.tmp, BW.r, BW.sc, st);
         apply_b_rec(C, W, BW, 0, prec, BW.r, BW.z, &BW.sc->all_done, st, &rz);
-        launches += 1 + per_apply;
+        launches += per_apply;
         chunk = 1;
     }
     int kmax = 0;
@@ -1891,6 +1897,9 @@ int bddc_query(const bddc_ctx *ctx, bddc_info *info, int level, int32_t *n_selec
                 info->n_interface[l] = ctx->L[l].D.n_iface;
             }
             for (int t = 0; t < 3; ++t) info->tuned_tile[t] = ctx->tuned[t];
+            info->tc_levels = 0;
+            for (size_t l = 0; l < ctx->L.size(); ++l)
+                if (ctx->L[l].D.tc) info->tc_levels |= 1 << (int)l;
             info->n_dof[ctx->L.size()] = ctx->n_top;
             double om = 1.0;
             bool any = false;
@@ -2286,7 +2295,7 @@ void finish_request(bddc_server *S, Request &R) {
 // each with its own PCG state starting at x = 0 (k_b_admit; the slot sits out
 // one direction update and joins at that iteration's apply), (2) takes the
 // slots whose recursive residual met the tolerance, checks their FP64 true
-// residual (restarting from it, with beta = 0, if it drifted) and copies the
+// residual (a slot whose true residual is not yet met keeps iterating) and copies the
 // finished ones out.  Every slot's arithmetic is its own column of the batch
 // kernels, so a result does not depend on what else is in the batch.
 void engine_loop(bddc_server *S, Engine *E) {
@@ -2363,20 +2372,21 @@ void engine_loop(bddc_server *S, Engine *E) {
             launch_b_norm2(n, K, BW.tmp, BW.part, BW.counter, BW.nrm, st);
             BDDC_CUDA_TRY(cudaMemcpyAsync(BW.hnrm, BW.nrm, sizeof(double) * K, cudaMemcpyDeviceToHost, st));
             BDDC_CUDA_TRY(cudaStreamSynchronize(st));
-            bool restart = false;
+            bool resume = false;
             std::vector<int> out;
             for (int k : fin) {
                 if (h.conv[k] && BW.hnrm[k] > h.tol2[k] && h.it[k] < h.mx[k]) {
-                    h.done[k] = 0; h.conv[k] = 0; h.fresh[k] = 1; h.hold[k] = 1; h.rr[k] = BW.hnrm[k];
-                    restart = true;
+                    // keeps iterating from the same state: it sits out the next
+                    // direction update and rejoins at that iteration's apply
+                    h.done[k] = 0; h.conv[k] = 0; h.hold[k] = 1;
+                    resume = true;
                 } else {
                     out.push_back(k);
                 }
             }
-            if (restart) {
+            if (resume) {
                 h.all_done = 0;
                 BDDC_CUDA_TRY(cudaMemcpyAsync(BW.sc, BW.hsc, sizeof(BatchScalars), cudaMemcpyHostToDevice, st));
-                launch_b_restart(n, K, BW.tmp, BW.r, BW.sc, st);
             }
             int kmax = 0;
             for (int k : out) kmax = std::max(kmax, std::min(h.it[k], W->maxit_cap));

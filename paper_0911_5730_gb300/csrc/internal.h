@@ -2,6 +2,7 @@
 // translation units of libbddc.so.  Not part of the public ABI.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 
@@ -59,6 +60,32 @@ template <class T> struct OpSet {
     T *nmat = nullptr;    // constrained Neumann operator on Gamma (nG x nG per sub)
     T *psit = nullptr;    // Psi^T on Gamma (nc x nG per sub)
     T *wg = nullptr;      // stiffness weights on Gamma
+};
+
+// Dense operands of the tensor-core interior corrections of a level
+// (tc_kernels.cu), built at setup when every substructure's interior fits two
+// MMA tiles: per substructure, in FP32 (two TF32 planes) and in BF16,
+//   pre  [max nG][KpreS]:  H^T, H = A_II^{-1} A_{I Gamma}   (eqs. 4-5: r_B -= H^T r_I)
+//   post [max nI][KpostS]: [A_II^{-1} | -H], H from column KI (eqs. 10-11:
+//                          z_I = A_II^{-1} r_I - H u_B)
+// zero outside each substructure's own rows and columns, with a TMA tensor
+// map over each array (dims: K, rows, substructure).
+struct TcLevel {
+    bool ok = false;
+    int Mpre = 0, Kpre = 0, Mpost = 0, KI = 0, Kpost = 0;   // row and K extents
+    int64_t KpreS = 0, KpostS = 0;                           // row strides (elements)
+    float *pre32 = nullptr, *post32 = nullptr;       // FP32 operand as its high TF32 plane
+    float *pre32lo = nullptr, *post32lo = nullptr;   // and its low TF32 plane (hi + lo = the FP64 value)
+    __nv_bfloat16 *pre16 = nullptr, *post16 = nullptr;
+    CUtensorMap tm[6];   // pre32, post32, pre16, post16, pre32lo, post32lo
+    int64_t bytes = 0;   // device bytes of the six arrays
+    // where the right-hand-side rows of each K row come from, [nsub][Krow]:
+    // the DOF of r (>= 0), -(c + 2) for compact interface id c of u_B, or -1
+    int Krow = 0;
+    int *rowPre = nullptr, *rowPost = nullptr;
+    // owned interface entries of each substructure as (compact id, DOF)
+    int2 *own = nullptr;
+    int64_t *ownOff = nullptr;
 };
 
 // Substructures of a level in size buckets for the streaming batch kernel:
@@ -128,6 +155,7 @@ struct DevLevel {
     int *gdofG = nullptr;     // level DOF of each Gamma entry (concatenated like idxG)
     int64_t max_irec = 0, max_nrec[3] = {0, 0, 0};
     int max_own = 0;          // largest owned-interface list (max_coo: largest coupling)
+    const TcLevel *tc = nullptr;   // host: tensor-core operands of the level, or null
 };
 
 // Byte layout of the records (shared by host and device).
@@ -209,7 +237,7 @@ void apply_level_average(const DevLevel &L, int prec, const int *skip, cudaStrea
 
 // ----------------------------------------------------------------------------
 // Interface-reduced PCG (reduced_kernels.cu): vectors of the n_iface compact
-// interface ids; every launch but init and restart is skipped once *skip.
+// interface ids; every launch but init is skipped once *skip.
 // ----------------------------------------------------------------------------
 int red_blocks();
 void launch_red_init(int ng, const int *ifaceDof, const double *b, const double *qf, double *x, double *r,
@@ -224,7 +252,6 @@ void launch_red_pq(int ng, const int *ifaceDof, const double *qf, const double *
                    unsigned *counter, RedScalars *sc, double *alphas, const int *skip, cudaStream_t s);
 void launch_red_update(int ng, double *x, double *r, const double *p, const double *q, double *part,
                        unsigned *counter, RedScalars *sc, const int *skip, cudaStream_t s);
-void launch_red_restart(int ng, const int *ifaceDof, const double *res, double *r, cudaStream_t s);
 
 // ----------------------------------------------------------------------------
 // Batches of K <= kMaxBatch right-hand sides (batch_kernels.cu).  Every batch
@@ -246,7 +273,7 @@ struct BatchScalars {
     double rho[kMaxBatch], pq[kMaxBatch], alpha[kMaxBatch], beta[kMaxBatch], rr[kMaxBatch],
         bb[kMaxBatch], tol2[kMaxBatch];
     int it[kMaxBatch], done[kMaxBatch], conv[kMaxBatch], fresh[kMaxBatch];
-    // hold: a right-hand side admitted (or restarted) between iterations sits
+    // hold: a right-hand side admitted (or resumed) between iterations sits
     // out the next direction/update half and joins at that iteration's apply
     int hold[kMaxBatch];
     int mx[kMaxBatch];     // iteration limit of each right-hand side
@@ -313,15 +340,31 @@ void launch_b_admit(int n, int K, int k, const double *b, double *x, double *r, 
                     unsigned *counter, BatchScalars *sc, double tol, int maxit, cudaStream_t s);
 // dst[g] = x(g, k)
 void launch_b_column(int n, int K, int k, const double *x, double *dst, cudaStream_t s);
-// r(:, k) = res(:, k) for every k with fresh && !done
-void launch_b_restart(int n, int K, const double *res, double *r, const BatchScalars *sc,
-                      cudaStream_t s);
 // mismatches of the integer-operation binary32/binary64 conversions against
 // the hardware conversions on n values (added to *bad)
 void launch_selftest_convert(const double *d, int64_t n, unsigned long long *bad, cudaStream_t s);
 // caller layout (column k at src + k * ld) <-> interleaved
 void launch_b_gather(int n, int K, const double *src, int64_t ld, double *dst, cudaStream_t s);
 void launch_b_scatter(int n, int K, const double *src, double *dst, int64_t ld, cudaStream_t s);
+
+struct SetupLevel;
+// Tensor-core interior corrections for batches (tc_kernels.cu).
+// Whether the pre- (post = false) or post-correction of the level runs on
+// the tensor cores in this precision (FP32 or BF16): the level has the dense
+// operands and the route is enabled (environment BDDC_TC, see tc_kernels.cu).
+bool tc_route(const DevLevel &L, int prec, bool post);
+// The pre- (eqs. 4-5) or post-correction (eqs. 10-11, with rz at level 1:
+// r.z and beta) of a batch on the tensor cores.
+void tc_dir_b(const DevLevel &L, const BatchLevel &B, int prec, bool post, const double *r, double *z,
+              const int *skip, const RzBatch *rz, cudaStream_t s);
+// Build the dense operands of a level from its banded interior factor and
+// G = L^{-1} A_{I Gamma} (after launch_schur); leaves T.ok false when the
+// level does not qualify.  Device arrays come from A, the FP64 scratch from tmp.
+void tc_build_level(const SetupLevel &S, const DevLevel &D, const std::vector<int> &nI,
+                    const std::vector<int> &nG, const std::vector<int> &idxI, const std::vector<int> &idxG,
+                    const std::vector<int> &own, const std::vector<int64_t> &ownOff,
+                    const std::vector<int> &ifaceDof, TcLevel &T, DevArena &A, DevArena &tmp, cudaStream_t st);
+void prepare_tc_kernels();
 
 // Whether apply_level_post fuses the r.z reduction into its last kernel (one
 // kernel fewer per PCG iteration).
