@@ -29,6 +29,7 @@ class PCGResult:
     converged: bool
     alphas: list
     betas: list
+    true_checks: int = 0   # true residuals computed: more than one if the stop was deferred
 
 
 def lanczos_extremes(alphas, betas):
@@ -59,6 +60,7 @@ def pcg(A, b: np.ndarray, M, rtol: float = 1e-8, maxit: int = 1000,
     rho = float(r @ z)
     alphas, betas = [], []
     it = 0
+    checks = 0
     converged = False
     limit = fixed_iters if fixed_iters is not None else maxit
     while it < limit:
@@ -69,6 +71,7 @@ def pcg(A, b: np.ndarray, M, rtol: float = 1e-8, maxit: int = 1000,
         r -= alpha * q
         alphas.append(alpha)
         if fixed_iters is None and np.linalg.norm(r) <= rtol * bn:
+            checks += 1
             if np.linalg.norm(b - A @ x) <= rtol * bn:
                 converged = True
                 break
@@ -85,4 +88,4 @@ def pcg(A, b: np.ndarray, M, rtol: float = 1e-8, maxit: int = 1000,
     rt = float(np.linalg.norm(b - A @ x) / bn)
     if fixed_iters is not None:
         converged = rt <= rtol
-    return PCGResult(x, it, rr, rt, hi / lo, lo, hi, converged, alphas, betas)
+    return PCGResult(x, it, rr, rt, hi / lo, lo, hi, converged, alphas, betas, checks)

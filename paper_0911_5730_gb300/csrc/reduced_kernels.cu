@@ -154,10 +154,6 @@ __global__ void __launch_bounds__(RT) k_red_update(int ng, double *x, double *r,
     }
 }
 
-// r = (b - A x_full)_G after a restart (res: the full residual)
-__global__ void __launch_bounds__(RT) k_red_restart(int ng, const int *ifaceDof, const double *res, double *r) {
-    for (int i = blockIdx.x * RT + threadIdx.x; i < ng; i += gridDim.x * RT) r[i] = res[ifaceDof[i]];
-}
 
 int red_grid(int ng) {
     const int g = (ng + RT - 1) / RT;
@@ -193,9 +189,6 @@ void launch_red_pq(int ng, const int *ifaceDof, const double *qf, const double *
 void launch_red_update(int ng, double *x, double *r, const double *p, const double *q, double *part,
                        unsigned *counter, RedScalars *sc, const int *skip, cudaStream_t s) {
     launch_k(false, k_red_update, red_grid(ng), RT, 0, s, ng, x, r, p, q, part, counter, sc, skip);
-}
-void launch_red_restart(int ng, const int *ifaceDof, const double *res, double *r, cudaStream_t s) {
-    launch_k(false, k_red_restart, red_grid(ng), RT, 0, s, ng, ifaceDof, res, r);
 }
 
 }  // namespace bddc

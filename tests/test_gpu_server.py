@@ -107,7 +107,7 @@ def test_continuous_batching_waves(lib):
         time.sleep(0.002)
     for P, b, rtol, t in sent:
         x, infos, lat = srv.wait(t)
-        assert lat > 0 and infos[0]["status"] == 0
+        assert lat > 0 and infos[0]["status"] == 0, (rtol, lat, infos[0])
         assert infos[0]["batch_width"] == width[id(P)]
         if P is Pt:
             pair = np.zeros((2, b.size))
