@@ -145,6 +145,12 @@ typedef struct {
      * substructure in FP64 for it (levels whose interiors hold 128 to 256
      * DOFs).  Environment BDDC_TC=0 keeps them on the triangular sweeps. */
     int32_t tc_levels;
+    /* BDDC_OK, or BDDC_E_TIMEOUT if a bounded device wait gave up during the
+     * last bddc_apply or bddc_apply_noalloc on this context (those calls
+     * return before their stream runs; read this once it has been
+     * synchronised).  The solves report such a wait in their own status. */
+    int32_t apply_status;
+    int32_t reserved3;
 } bddc_info;
 
 /*
@@ -183,6 +189,11 @@ int bddc_setup(const bddc_mesh *mesh, const double *k_elem, const bddc_decomp *d
  *                  workspace the first such call allocates).
  * Runs asynchronously in `stream`; the context serialises its own scratch,
  * so calls on one context must not run concurrently from several threads.
+ * A bounded device wait that gives up leaves z undefined; the call cannot
+ * report it (it returns before its stream runs), so it is recorded for
+ * bddc_query (bddc_info.apply_status) once the stream has been synchronised.
+ * BDDC_E_ARG if the current CUDA device is not the one the context was set
+ * up on (every call on a context checks this).
  */
 int bddc_apply(bddc_ctx *ctx, const double *r_dev, double *z_dev, int nrhs, int64_t ld,
                void *stream);
@@ -360,16 +371,21 @@ int bddc_profile_apply_batch(bddc_ctx *ctx, const double *r_dev, int nrhs, int64
  *
  * The per-level scratch of the apply (interface residuals and averages,
  * substructure corrections, coarse vectors) lives in one library-owned,
- * file-scope device array of BDDC_NOALLOC_SCRATCH_BYTES (16 MiB).  Every GPU
- * that loads the library holds that array until the process exits.
+ * file-scope device array of BDDC_NOALLOC_SCRATCH_BYTES (16 MiB), whose first
+ * 256 bytes hold the call's own error word.  Every GPU that loads the library
+ * holds that array until the process exits.
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
  *     before any stream capture.
  *   - A context whose scratch needs more than the array holds is rejected
  *     with BDDC_E_ARG and a message giving both sizes.
- *   - Every call shares the array and the apply re-initialises the parts that
- *     must start at zero, so results do not depend on earlier calls; calls
- *     that overlap on the GPU (other streams, other threads) race on it.
+ *   - Every call shares the array and re-initialises the parts that must
+ *     start at zero (the error word, the interface-residual and coarse
+ *     accumulators), so results do not depend on earlier calls; calls that
+ *     overlap on the GPU (other streams, other threads) race on it.
+ *   - As for bddc_apply, a bounded wait that gave up is recorded for
+ *     bddc_query (bddc_info.apply_status) once the stream has run.
+ *   - BDDC_E_ARG if the current device is not the context's.
  *   r_dev, z_dev : device FP64 [n], not overlapping.
  */
 #define BDDC_NOALLOC_SCRATCH_BYTES (16u << 20)

@@ -75,7 +75,7 @@ class Info(C.Structure):
                 ("block_entries", C.c_int64 * 3), ("coupling_nnz", C.c_int64 * 3),
                 ("neumann_entries", C.c_int64 * 3), ("psi_entries", C.c_int64 * 3),
                 ("n_interface", C.c_int32 * 3), ("tuned_tile", C.c_int32 * 3),
-                ("tc_levels", C.c_int32)]
+                ("tc_levels", C.c_int32), ("apply_status", C.c_int32), ("reserved3", C.c_int32)]
 
 
 _lib = None
@@ -393,7 +393,8 @@ class Problem:
                "omega_tilde": info.omega_tilde,
                "omega_level": list(info.omega_level)[:info.levels - 1],
                "setup_ms": info.setup_ms, "device_bytes": info.device_bytes,
-               "tuned_tile": list(info.tuned_tile), "tc_levels": info.tc_levels}
+               "tuned_tile": list(info.tuned_tile), "tc_levels": info.tc_levels,
+               "apply_status": info.apply_status}
         nl = info.levels - 1
         for key in ("sum_interior", "sum_interface", "sum_coarse_local", "band_nnz",
                     "block_entries", "coupling_nnz", "neumann_entries", "psi_entries",

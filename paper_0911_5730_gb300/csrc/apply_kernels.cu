@@ -1204,16 +1204,23 @@ __global__ void k_selftest_wait(int *err, long polls) {
     }
 }
 
+int num_sms();
+// Largest grid of the vector kernels: eight blocks per SM, at most
+// kMaxVecGrid (the partial-sum buffers hold that many blocks).
+int vec_grid_cap() {
+    const int g = 8 * num_sms();
+    return g < kMaxVecGrid ? g : kMaxVecGrid;
+}
 int grid_for(int64_t n) {
     int64_t g = (n + RB - 1) / RB;
-    if (g > 152 * 8) g = 152 * 8;
+    if (g > vec_grid_cap()) g = vec_grid_cap();
     if (g < 1) g = 1;
     return (int)g;
 }
 // Grid of the FP64 vector kernels of the PCG iteration: about four entries per thread.
 int vec_grid(int64_t n) {
     int64_t g = (n + 4 * RB - 1) / (4 * RB);
-    if (g > 152 * 8) g = 152 * 8;
+    if (g > vec_grid_cap()) g = vec_grid_cap();
     if (g < 1) g = 1;
     return (int)g;
 }
@@ -1274,7 +1281,7 @@ int num_sms() {
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 152;
+        if (n <= 0) n = 1;   // no device answered: the launches that follow report the error
     }
     return n;
 }

@@ -1411,7 +1411,7 @@ int num_sms_b() {
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 152;
+        if (n <= 0) n = 1;   // no device answered: the launches that follow report the error
     }
     return n;
 }
@@ -1475,7 +1475,8 @@ template <class T, class ACC> size_t dir_slice_b(const DevLevel &L) {
 int vgrid_b(int64_t nK, int K) {
     const int bd = bblock(K);
     int64_t g = (nK + 4 * (int64_t)bd - 1) / (4 * (int64_t)bd);
-    if (g > 152 * 8) g = 152 * 8;
+    const int cap = 8 * num_sms_b() < kMaxVecGrid ? 8 * num_sms_b() : kMaxVecGrid;
+    if (g > cap) g = cap;
     if (g < 1) g = 1;
     return (int)g;
 }
@@ -1836,7 +1837,7 @@ void launch_b_norm2(int n, int K, const double *v, double *part, unsigned *count
 void launch_b_admit(int n, int K, int k, const double *b, double *x, double *r, double *part,
                     unsigned *counter, BatchScalars *sc, double tol, int maxit, cudaStream_t s) {
     int g = (n + kRB - 1) / kRB;
-    if (g > 152 * 4) g = 152 * 4;
+    if (g > 4 * num_sms_b()) g = 4 * num_sms_b();
     k_b_admit<<<g, kRB, 0, s>>>(n, K, k, b, x, r, part, counter, sc, tol, maxit);
 }
 void launch_b_column(int n, int K, int k, const double *x, double *dst, cudaStream_t s) {

@@ -125,6 +125,9 @@ struct Workspace {
     PcgScalars *sc = nullptr;
     PcgScalars *hsc = nullptr;        // pinned mirror
     double *hout = nullptr;           // pinned: norms, lanczos
+    // set by the kernels of this workspace whose bounded waits gave up;
+    // cleared when a solve or an apply on the workspace starts
+    int *err = nullptr;
     cudaStream_t stream = nullptr;
     cudaEvent_t ev = nullptr;
     cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};
@@ -160,7 +163,9 @@ struct bddc_ctx {
     std::vector<LevelData> L;
     int n_top = 0, ld_top = 0;
     double *Ainv = nullptr;           // top-level inverse, leading dimension ld_top
-    int *err_dev = nullptr;           // set by kernels whose bounded waits gave up
+    int *err_dev = nullptr;           // set by setup kernels whose bounded waits gave up
+    int device = 0;                   // the CUDA device the context was set up on
+    int *happly = nullptr;            // pinned: the error word of the last bddc_apply(_noalloc)
     std::unique_ptr<Workspace> ws;
     // further batch groups of a solve in flight at once (own stream and scratch)
     std::vector<std::unique_ptr<Workspace>> wsx;
@@ -769,6 +774,9 @@ void make_workspace(bddc_ctx *C, Workspace &W, int maxit_cap) {
     W.alphas = A.alloc_n<double>(maxit_cap + 1);
     W.betas = A.alloc_n<double>(maxit_cap + 1);
     W.lout = A.alloc_n<double>(4);
+    W.err = A.alloc_n<int>(1);
+    BDDC_CUDA_TRY(cudaMemset(W.err, 0, sizeof(int)));
+    for (auto &D : W.lv) D.err = W.err;
     BDDC_CUDA_TRY(cudaHostAlloc((void **)&W.hsc, sizeof(PcgScalars), cudaHostAllocDefault));
     BDDC_CUDA_TRY(cudaHostAlloc((void **)&W.hout, 8 * sizeof(double), cudaHostAllocDefault));
     BDDC_CUDA_TRY(cudaStreamCreateWithFlags(&W.stream, cudaStreamNonBlocking));
@@ -868,6 +876,7 @@ int pcg_one(bddc_ctx *C, Workspace &W, int prec, const double *b, double *x, dou
     cudaStream_t st = W.stream;
     if (maxit > W.maxit_cap) maxit = W.maxit_cap;
     const RzArgs rz{W.rzpart, W.rzcounter, W.sc, W.betas};
+    BDDC_CUDA_TRY(cudaMemsetAsync(W.err, 0, sizeof(int), st));
     launch_pcg_init(n, b, W.x, W.r, W.p0, W.part, W.counter, W.rzcounter, W.sc, rtol, maxit, st);
     apply_rec(C, W, 0, prec, W.r, W.z, &W.sc->done, st, &rz);
     cudaGraphExec_t g = pcg_graph(C, W, prec);
@@ -916,7 +925,7 @@ int pcg_one(bddc_ctx *C, Workspace &W, int prec, const double *b, double *x, dou
     }
     BDDC_CUDA_TRY(cudaMemcpyAsync(x, W.x, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
     int kerr = 0;
-    BDDC_CUDA_TRY(cudaMemcpyAsync(&kerr, C->err_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
+    BDDC_CUDA_TRY(cudaMemcpyAsync(&kerr, W.err, sizeof(int), cudaMemcpyDeviceToHost, st));
     BDDC_CUDA_TRY(cudaStreamSynchronize(st));
     BDDC_CUDA_TRY(cudaGetLastError());
     if (kerr) throw Error(BDDC_E_TIMEOUT, "a bounded device wait gave up during the solve");
@@ -1024,6 +1033,7 @@ int pcg_reduced(bddc_ctx *C, Workspace &W, int prec, const double *b, double *x,
     apply_level_dir(D, BDDC_PREC_FP64, true, b, R.ut, nullptr, st, nullptr);
     op_spmv(C, R.ut, R.qf, st);
     launch_norm2(n, b, W.part, W.counter, &R.sc->bb, st);
+    BDDC_CUDA_TRY(cudaMemsetAsync(W.err, 0, sizeof(int), st));
     launch_red_init(ng, D.ifaceDof, b, R.qf, R.x, R.r, R.p, R.part, R.counter, R.sc, rtol, maxit, st);
     auto start = [&]() {                  // z = M r, p = z
         reduced_precondition(C, W, R, prec, st);
@@ -1071,7 +1081,7 @@ int pcg_reduced(bddc_ctx *C, Workspace &W, int prec, const double *b, double *x,
     }
     BDDC_CUDA_TRY(cudaMemcpyAsync(x, W.x, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
     int kerr = 0;
-    BDDC_CUDA_TRY(cudaMemcpyAsync(&kerr, C->err_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
+    BDDC_CUDA_TRY(cudaMemcpyAsync(&kerr, W.err, sizeof(int), cudaMemcpyDeviceToHost, st));
     BDDC_CUDA_TRY(cudaStreamSynchronize(st));
     BDDC_CUDA_TRY(cudaGetLastError());
     if (kerr) throw Error(BDDC_E_TIMEOUT, "a bounded device wait gave up during the solve");
@@ -1167,7 +1177,7 @@ BatchWs &batch_ws(bddc_ctx *C, Workspace &W) {
                                    : dir_spmv_tune(C->nx, KB, C->w_dev, bw->z, bw->p, bw->p1, bw->q, bw->part,
                                                    bw->counter, scs, al, st);
             const BatchLevel &top = bw->lv.back();
-            C->gemm_v = gemm_tune(C->n_top, C->ld_top, C->Ainv, top.rcv, top.ucv, KB, C->err_dev, st);
+            C->gemm_v = gemm_tune(C->n_top, C->ld_top, C->Ainv, top.rcv, top.ucv, KB, W.err, st);
             BDDC_CUDA_TRY(cudaStreamSynchronize(st));
             BDDC_CUDA_TRY(cudaGetLastError());
             int tx = 0, ty = 0;
@@ -1189,7 +1199,7 @@ void apply_b_rec(bddc_ctx *C, Workspace &W, BatchWs &BW, int l, int prec, const 
     const BatchLevel &B = BW.lv[l];
     apply_level_pre_b(D, B, prec, r, skip, st);
     if (l + 1 == (int)W.lv.size())
-        launch_gemm_b(C->n_top, C->ld_top, C->Ainv, B.rcv, B.ucv, B.K, skip, C->err_dev, st, BW.gemm_v);
+        launch_gemm_b(C->n_top, C->ld_top, C->Ainv, B.rcv, B.ucv, B.K, skip, W.err, st, BW.gemm_v);
     else
         apply_b_rec(C, W, BW, l + 1, prec, B.rcv, B.ucv, skip, st);
     apply_level_post_b(D, B, prec, r, z, skip, st, nullptr, rz);
@@ -1236,6 +1246,7 @@ int pcg_batch(bddc_ctx *C, Workspace &W, int prec, const double *b, int64_t ldb,
     if (maxit > W.maxit_cap) maxit = W.maxit_cap;
     set_batch_width(BW, K);
     const RzBatch rz{BW.rzpart, BW.rzcounter, BW.sc, BW.betas};
+    BDDC_CUDA_TRY(cudaMemsetAsync(W.err, 0, sizeof(int), st));
     launch_b_init(n, K, b, ldb, BW.x, BW.r, BW.p, BW.part, BW.counter, BW.sc, rtol, maxit, st);
     BDDC_CUDA_TRY(cudaMemsetAsync(BW.rzcounter, 0, sizeof(unsigned), st));
     apply_b_rec(C, W, BW, 0, prec, BW.r, BW.z, &BW.sc->all_done, st, &rz);
@@ -1283,7 +1294,7 @@ int pcg_batch(bddc_ctx *C, Workspace &W, int prec, const double *b, int64_t ldb,
     }
     launch_b_scatter(n, K, BW.x, x, ldx, st);
     int kerr = 0;
-    BDDC_CUDA_TRY(cudaMemcpyAsync(&kerr, C->err_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
+    BDDC_CUDA_TRY(cudaMemcpyAsync(&kerr, W.err, sizeof(int), cudaMemcpyDeviceToHost, st));
     BDDC_CUDA_TRY(cudaStreamSynchronize(st));
     BDDC_CUDA_TRY(cudaGetLastError());
     if (kerr) throw Error(BDDC_E_TIMEOUT, "a bounded device wait gave up during the solve");
@@ -1411,6 +1422,16 @@ void check_problem(const bddc_mesh *mesh, bool setup) {
         throw Error(BDDC_E_ARG, "Lame parameters need mu > 0 and lambda >= 0");
 }
 
+// Calls on a context run on the device it was set up on; another current
+// device would mix its memory with that device's, so it is refused.
+void check_device(const bddc_ctx *C) {
+    int d = -1;
+    BDDC_CUDA_TRY(cudaGetDevice(&d));
+    if (d != C->device)
+        throw Error(BDDC_E_ARG, "the context was set up on CUDA device " + std::to_string(C->device) +
+                                    " but device " + std::to_string(d) + " is current");
+}
+
 template <class F> int guarded(F &&f) {
     try {
         set_error("");
@@ -1480,6 +1501,9 @@ int bddc_setup(const bddc_mesh *mesh, const double *k_elem, const bddc_decomp *d
         }
         C->err_dev = C->arena.alloc_n<int>(1);
         BDDC_CUDA_TRY(cudaMemsetAsync(C->err_dev, 0, sizeof(int), st));
+        BDDC_CUDA_TRY(cudaGetDevice(&C->device));
+        BDDC_CUDA_TRY(cudaHostAlloc((void **)&C->happly, sizeof(int), cudaHostAllocDefault));
+        *C->happly = 0;
         static std::once_flag prep_once;
         std::call_once(prep_once, [] { prepare_apply_kernels(); prepare_batch_kernels(); });
         DevArena tmp;
@@ -1572,9 +1596,11 @@ int bddc_apply(bddc_ctx *ctx, const double *r_dev, double *z_dev, int nrhs, int6
         if (!ctx || !r_dev || !z_dev || nrhs < 1) throw Error(BDDC_E_ARG, "bad argument");
         const int n = ctx->n();
         if (ld < n) throw Error(BDDC_E_ARG, "ld < n");
+        check_device(ctx);
         std::lock_guard<std::mutex> lk(ctx->mu);
         cudaStream_t st = (cudaStream_t)stream;
         Workspace &W = *ctx->ws;
+        BDDC_CUDA_TRY(cudaMemsetAsync(W.err, 0, sizeof(int), st));
         if (nrhs > 1 && batch_ok(ctx, W, ctx->prec)) {
             BatchWs &BW = batch_ws(ctx, W);
             for (int j0 = 0; j0 < nrhs; j0 += kMaxBatch) {
@@ -1588,6 +1614,8 @@ int bddc_apply(bddc_ctx *ctx, const double *r_dev, double *z_dev, int nrhs, int6
             for (int j = 0; j < nrhs; ++j)
                 apply_rec(ctx, W, 0, ctx->prec, r_dev + j * ld, z_dev + j * ld, nullptr, st);
         }
+        // whether a bounded wait gave up, for bddc_query once the stream is done
+        BDDC_CUDA_TRY(cudaMemcpyAsync(ctx->happly, W.err, sizeof(int), cudaMemcpyDeviceToHost, st));
         BDDC_CUDA_TRY(cudaGetLastError());
         return BDDC_OK;
     });
@@ -1619,6 +1647,7 @@ int bddc_inspect(const bddc_mesh *mesh, const bddc_decomp *decomp, int32_t *n_co
 int bddc_operator(bddc_ctx *ctx, const double *x_dev, double *y_dev, void *stream) {
     return guarded([&]() -> int {
         if (!ctx || !x_dev || !y_dev) throw Error(BDDC_E_ARG, "bad argument");
+        check_device(ctx);
         op_spmv(ctx, x_dev, y_dev, (cudaStream_t)stream);
         BDDC_CUDA_TRY(cudaGetLastError());
         return BDDC_OK;
@@ -1666,7 +1695,12 @@ template <class F> int run_batch_groups(bddc_ctx *ctx, int nrhs, F &&group) {
         std::vector<std::thread> th;
         for (int g = 1; g < ng; ++g)
             th.emplace_back([&, g] {
-                try { st[g] = group(*ws[g], js[g], ks[g]); } catch (...) { ep[g] = std::current_exception(); }
+                try {
+                    BDDC_CUDA_TRY(cudaSetDevice(ctx->device));
+                    st[g] = group(*ws[g], js[g], ks[g]);
+                } catch (...) {
+                    ep[g] = std::current_exception();
+                }
             });
         try {
             st[0] = group(*ws[0], js[0], ks[0]);
@@ -1693,6 +1727,7 @@ int bddc_pcg_solve(bddc_ctx *ctx, const double *b_dev, double *x_dev, int nrhs, 
             throw Error(BDDC_E_ARG, "bad argument");
         const int n = ctx->n();
         if (ld < n) throw Error(BDDC_E_ARG, "ld < n");
+        check_device(ctx);
         std::lock_guard<std::mutex> lk(ctx->mu);
         Workspace &W = *ctx->ws;
         cudaStream_t st = (cudaStream_t)stream;
@@ -1725,6 +1760,7 @@ int bddc_pcg_solve_reduced(bddc_ctx *ctx, const double *b_dev, double *x_dev, do
                            bddc_solve_info *info_host, void *stream) {
     return guarded([&]() -> int {
         if (!ctx || !b_dev || !x_dev || maxit < 1 || !(rtol > 0)) throw Error(BDDC_E_ARG, "bad argument");
+        check_device(ctx);
         std::lock_guard<std::mutex> lk(ctx->mu);
         Workspace &W = *ctx->ws;
         cudaStream_t st = (cudaStream_t)stream;
@@ -1746,6 +1782,7 @@ int bddc_pcg_solve_host(bddc_ctx *ctx, const double *b_host, double *x_host, int
             throw Error(BDDC_E_ARG, "bad argument");
         const int n = ctx->n();
         if (ld < n) throw Error(BDDC_E_ARG, "ld < n");
+        check_device(ctx);
         std::lock_guard<std::mutex> lk(ctx->mu);
         Workspace &W = *ctx->ws;
         (void)stream;
@@ -1897,6 +1934,7 @@ int bddc_query(const bddc_ctx *ctx, bddc_info *info, int level, int32_t *n_selec
                 info->n_interface[l] = ctx->L[l].D.n_iface;
             }
             for (int t = 0; t < 3; ++t) info->tuned_tile[t] = ctx->tuned[t];
+            info->apply_status = *ctx->happly ? BDDC_E_TIMEOUT : BDDC_OK;
             info->tc_levels = 0;
             for (size_t l = 0; l < ctx->L.size(); ++l)
                 if (ctx->L[l].D.tc) info->tc_levels |= 1 << (int)l;
@@ -1930,6 +1968,7 @@ int bddc_profile_apply(bddc_ctx *ctx, const double *r_dev, int reps, double *ms_
                        int32_t *n_out) {
     return guarded([&]() -> int {
         if (!ctx || !r_dev || reps < 1 || !ms_out) throw Error(BDDC_E_ARG, "bad argument");
+        check_device(ctx);
         std::lock_guard<std::mutex> lk(ctx->mu);
         Workspace &W = *ctx->ws;
         const int nl = (int)W.lv.size();
@@ -1982,6 +2021,7 @@ int bddc_profile_apply_batch(bddc_ctx *ctx, const double *r_dev, int nrhs, int64
             throw Error(BDDC_E_ARG, "bad argument");
         const int n = ctx->n();
         if (ld < n) throw Error(BDDC_E_ARG, "ld < n");
+        check_device(ctx);
         std::lock_guard<std::mutex> lk(ctx->mu);
         Workspace &W = *ctx->ws;
         if (!batch_ok(ctx, W, ctx->prec)) throw Error(BDDC_E_STATE, "operators do not fit the batch kernels");
@@ -2010,7 +2050,7 @@ int bddc_profile_apply_batch(bddc_ctx *ctx, const double *r_dev, int nrhs, int64
             }
             BDDC_CUDA_TRY(cudaEventRecord(top[0], st));
             launch_gemm_b(ctx->n_top, ctx->ld_top, ctx->Ainv, BW.lv[nl - 1].rcv, BW.lv[nl - 1].ucv, K, nullptr,
-                          ctx->err_dev, st, BW.gemm_v);
+                          W.err, st, BW.gemm_v);
             BDDC_CUDA_TRY(cudaEventRecord(top[1], st));
             for (int l = nl - 1; l >= 0; --l)
                 apply_level_post_b(W.lv[l], BW.lv[l], ctx->prec, rin[l], l == 0 ? BW.z : BW.lv[l - 1].ucv,
@@ -2067,11 +2107,13 @@ extern "C" {
 int bddc_apply_noalloc(bddc_ctx *ctx, const double *r_dev, double *z_dev, void *stream) {
     return guarded([&]() -> int {
         if (!ctx || !r_dev || !z_dev) throw Error(BDDC_E_ARG, "bad argument");
+        check_device(ctx);
         const int nl = (int)ctx->L.size();
         if (nl < 1 || nl > 3) throw Error(BDDC_E_STATE, "context has no BDDC level");
-        // carve the scratch of every level, 32-double aligned pieces
+        // carve the scratch of every level, 32-double aligned pieces, after
+        // the call's error word (the first 32 doubles)
         auto up = [](size_t v) { return (v + 31) & ~size_t(31); };
-        size_t need = 0;
+        size_t need = 32;
         size_t sz[3][5];
         for (int l = 0; l < nl; ++l) {
             const DevLevel &D = ctx->L[l].D;
@@ -2087,8 +2129,9 @@ int bddc_apply_noalloc(bddc_ctx *ctx, const double *r_dev, double *z_dev, void *
                                         " bytes exceeds the static scratch of " +
                                         std::to_string((size_t)BDDC_NOALLOC_SCRATCH_BYTES) + " bytes");
         double *base = noalloc_scratch();
+        int *errw = reinterpret_cast<int *>(base);
         DevLevel lv[3];
-        size_t off = 0;
+        size_t off = 32;
         for (int l = 0; l < nl; ++l) {
             lv[l] = ctx->L[l].D;
             lv[l].rB = base + off;  off += sz[l][0];
@@ -2096,12 +2139,20 @@ int bddc_apply_noalloc(bddc_ctx *ctx, const double *r_dev, double *z_dev, void *
             lv[l].w = base + off;   off += sz[l][2];
             lv[l].rcv = base + off; off += sz[l][3];
             lv[l].ucv = base + off; off += sz[l][4];
+            lv[l].err = errw;
         }
         cudaStream_t st = (cudaStream_t)stream;
         const int prec = ctx->prec;
-        // The array keeps whatever the last call (of any context) left in it;
-        // the apply expects its interface and coarse accumulators at zero.
-        BDDC_CUDA_TRY(cudaMemsetAsync(base, 0, off * sizeof(double), st));
+        // The array keeps whatever the last call (of any context) left in it.
+        // The apply expects the error word and its accumulators of the
+        // interface residual r_B and the coarse right-hand side at zero (the
+        // pre-correction clears u_B itself; w and u_c are written before they
+        // are read).
+        BDDC_CUDA_TRY(cudaMemsetAsync(errw, 0, sizeof(int), st));
+        for (int l = 0; l < nl; ++l) {
+            BDDC_CUDA_TRY(cudaMemsetAsync(lv[l].rB, 0, sz[l][0] * sizeof(double), st));
+            BDDC_CUDA_TRY(cudaMemsetAsync(lv[l].rcv, 0, sz[l][3] * sizeof(double), st));
+        }
         const double *rin[3] = {r_dev, nullptr, nullptr};
         for (int l = 0; l < nl; ++l) {
             apply_level_pre(lv[l], prec, rin[l], nullptr, st);
@@ -2110,6 +2161,8 @@ int bddc_apply_noalloc(bddc_ctx *ctx, const double *r_dev, double *z_dev, void *
         launch_dense_symv(ctx->n_top, ctx->ld_top, ctx->Ainv, lv[nl - 1].rcv, lv[nl - 1].ucv, nullptr, st);
         for (int l = nl - 1; l >= 0; --l)
             apply_level_post(lv[l], prec, rin[l], l == 0 ? z_dev : lv[l - 1].ucv, nullptr, st);
+        // whether a bounded wait gave up, for bddc_query once the stream is done
+        BDDC_CUDA_TRY(cudaMemcpyAsync(ctx->happly, errw, sizeof(int), cudaMemcpyDeviceToHost, st));
         BDDC_CUDA_TRY(cudaGetLastError());
         return BDDC_OK;
     });
@@ -2155,6 +2208,7 @@ int bddc_selftest_wait_timeout(void *stream) {
 void bddc_destroy(bddc_ctx *ctx) {
     if (!ctx) return;
     cudaDeviceSynchronize();
+    if (ctx->happly) cudaFreeHost(ctx->happly);
     delete ctx;
 }
 
@@ -2249,6 +2303,7 @@ void worker_loop(bddc_server *S) {
         }
         try {
             bddc_ctx *C = R->ctx;
+            BDDC_CUDA_TRY(cudaSetDevice(C->device));
             auto &W = wss[C];
             if (!W) { W.reset(new Workspace()); make_workspace(C, *W, 10000); }
             const int n = C->n();
@@ -2317,6 +2372,7 @@ void engine_loop(bddc_server *S, Engine *E) {
         E->pending->clear();
     };
     try {
+        BDDC_CUDA_TRY(cudaSetDevice(C->device));
         W.reset(new Workspace());
         make_workspace(C, *W, 10000);
         BatchWs &BW = batch_ws(C, *W);
@@ -2402,7 +2458,7 @@ void engine_loop(bddc_server *S, Engine *E) {
                                               sizeof(double) * n, cudaMemcpyDeviceToHost, st));
             }
             int kerr = 0;
-            BDDC_CUDA_TRY(cudaMemcpyAsync(&kerr, C->err_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
+            BDDC_CUDA_TRY(cudaMemcpyAsync(&kerr, W->err, sizeof(int), cudaMemcpyDeviceToHost, st));
             BDDC_CUDA_TRY(cudaStreamSynchronize(st));
             if (kerr) throw Error(BDDC_E_TIMEOUT, "a bounded device wait gave up during the solve");
             {

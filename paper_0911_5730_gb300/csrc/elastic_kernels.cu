@@ -25,7 +25,7 @@ namespace bddc {
 namespace {
 
 constexpr int kET = 256;            // threads per block
-constexpr int kEMaxGrid = 152 * 8;  // blocks; the partial buffers hold at least this many
+constexpr int kEMaxGrid = kMaxVecGrid;  // blocks; the partial buffers hold at least this many
 
 // local node of offset (ox, oy) in an element: (0,0) 0, (1,0) 1, (1,1) 2, (0,1) 3
 __host__ __device__ constexpr int loc_of(int ox, int oy) { return oy == 0 ? ox : 3 - ox; }

@@ -29,6 +29,10 @@ void set_error(const std::string &msg);
         }                                                                          \
     } while (0)
 
+// Largest grid of the grid-stride vector kernels (eight blocks per SM on this
+// GPU's 152 SMs); the per-block partial-sum buffers are sized for it.
+constexpr int kMaxVecGrid = 1216;
+
 // ----------------------------------------------------------------------------
 // Device buffers owned by a context
 // ----------------------------------------------------------------------------

@@ -21,7 +21,7 @@ namespace bddc {
 namespace {
 
 constexpr int RT = 256;          // threads per block
-constexpr int RG = 152 * 2;      // blocks of every reduction (fixed: the sums' order)
+constexpr int RG = 304;          // blocks of every reduction (fixed, so the order of the sums is the same on every GPU)
 
 // Sum of one value per thread over the grid; true in the last block to finish,
 // which has the total in *out (thread 0).

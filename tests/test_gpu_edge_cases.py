@@ -76,9 +76,20 @@ def test_zero_rhs(lib):
 def test_bounded_wait_timeout(lib):
     code = lib.load().bddc_selftest_wait_timeout(None)
     assert code == -5
-    # the context is still usable afterwards
+    # the device is still usable afterwards, and a wait that gave up elsewhere
+    # is not charged to a context: its solves (single and batched) and
+    # applies report success, and the applies record no timeout
+    # (bddc_info.apply_status)
     wl = inputs.two_level_unit()
     P = lib.Problem.from_workload(wl)
-    x, info = P.solve(torch.tensor(wl.rhs(), device="cuda"))
-    assert info[0]["status"] == 0
+    b = torch.tensor(wl.rhs(), device="cuda")
+    for _ in range(2):
+        x, info = P.solve(b)
+        assert info[0]["status"] == 0
+        X, infos = P.solve(torch.stack([b, 2 * b]))
+        assert all(i["status"] == 0 for i in infos)
+        P.apply(b)
+        torch.cuda.synchronize()
+        assert P.query()["apply_status"] == 0
+        assert lib.load().bddc_selftest_wait_timeout(None) == -5
     P.close()
