@@ -163,3 +163,29 @@ def test_operator_matches_assembled(lib):
     y = P.operator(torch.tensor(x, device="cuda")).cpu().numpy()
     assert _relerr(y, H.A @ x) <= 1e-14
     P.close()
+
+
+def test_stop_deferred_by_true_residual(lib):
+    """The stopping rule when the recursive residual meets the tolerance but
+    the FP64 true residual does not (Sec. 5, read as the oracle reads it): the
+    iteration goes on from the same iterate, residual and direction.  On the
+    64^2 channel problem the true residual cannot fall below about 1.2e-14,
+    while the recursive one keeps falling; with rtol = 1e-14 and maxit = 60
+    every iteration after the first crossing defers the stop, and the solve
+    ends at maxit without converging.  Single and batched solves must do the
+    same as the oracle: BDDC_E_NOCONV after 60 iterations, the solution
+    within 1e-9 of the oracle's and a true residual of the same size."""
+    wl = inputs.two_level_channels(nx=64, sub=16, tau=10.0)
+    H = obddc.build_workload(wl)
+    P = lib.Problem.from_workload(wl)
+    B = inputs.normal_rhs(wl.n_dof, 100, 3)
+    refs = [opcg.pcg(H.A, B[j], H.apply, rtol=1e-14, maxit=60) for j in range(3)]
+    for ref in refs:
+        assert not ref.converged and ref.iters == 60 and ref.true_checks > 20
+    x, info = P.solve(torch.tensor(B[0], device="cuda"), rtol=1e-14, maxit=60, check=False)
+    X, infos = P.solve(torch.tensor(B, device="cuda"), rtol=1e-14, maxit=60, check=False)
+    for got, inf, ref in [(x, info[0], refs[0])] + [(X[j], infos[j], refs[j]) for j in range(3)]:
+        assert inf["status"] == -4 and inf["iters"] == 60, inf
+        assert _relerr(got.cpu().numpy(), ref.x) <= 1e-9
+        assert 0.3 * ref.relres_true <= inf["relres_true"] <= 3 * ref.relres_true
+    P.close()
