@@ -12,7 +12,9 @@ residual) with the BDDC preconditioner applied in the chosen precision.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
 The GPU arm prints one JSON line (rank 0).  `--impl reference` times the CPU
-FP64 oracle on a bounded sample of the same workload instead.
+FP64 oracle on the same workload instead: each step a few PCG iterations of
+the full problem (its setup built first, not timed), solves/s scaled by the
+iteration count of a solve.
 """
 from __future__ import annotations
 
@@ -39,8 +41,6 @@ RHS_SEED = 2002
 METRIC = "BDDC PCG solves/s at rel-res 1e-8 (mixed vs FP64); p50/p99 latency"
 UNIT = "solves/s"
 RTOL = 1e-8
-SAMPLE_NX = 128          # CPU sample: the 128x128 corner of the 512x512 field (64 substructures)
-FULL_SUBS = 1024
 
 # DRAM traffic per launch of the dominant kernel from the ncu capture
 # summarised in profiles/: {kernel: {"bytes", "file", "src"}}, valid only while
@@ -58,6 +58,8 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-elasticity", action="store_true",
                     help="skip the elasticity entry (the paper's own experiment, one process only)")
+    ap.add_argument("--no-serving-mix", action="store_true",
+                    help="skip serving configs 2-4 resident together (one process only)")
     ap.add_argument("--batch", type=int, default=BATCH,
                     help="right-hand sides per step (groups of %d, up to three in flight)" % GROUP)
     ap.add_argument("--profile-apply", choices=["fp64", "fp32", "bf16"], default=None,
@@ -82,7 +84,7 @@ def _peaks():
     return 6800.0, "fallback"
 
 
-FP64_PEAK_GFLOPS = 1250.0   # nominal GB300 FP64 rate (no measured FP64 peak available)
+FP64_NOMINAL_TFLOPS = 1.25  # nominal GB300 FP64 rate (context; the roofline takes the measured one)
 
 
 class Clocks:
@@ -129,52 +131,101 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def _cpu_sample_workload():
-    from paper_0911_5730_gb300 import inputs
-    wl = inputs.two_level_channels()
-    k = wl.k.reshape(wl.nx, wl.nx)[:SAMPLE_NX, :SAMPLE_NX].ravel().copy()
-    e2s, ns = inputs.grid_decomposition(SAMPLE_NX, 16)
-    b = inputs.normal_rhs((SAMPLE_NX - 1) ** 2, 2002)
-    return k, e2s, ns, b
-
-
 def _golden_iters():
     p = os.path.join(ROOT, "tests", "golden", WORKLOAD + ".json")
     if os.path.exists(p):
-        return json.load(open(p))["pcg"]["iters"], "oracle on the full workload (tests/golden)"
+        return json.load(open(p))["pcg"]["iters"], "the oracle's own count on this workload (tests/golden)"
     return None, None
 
 
-def cpu_sample_run(iters=250):
-    """Oracle PCG iterations on the sample; returns seconds per iteration."""
+def cpu_info():
+    """The host's CPU model and core count, for the baseline's record."""
+    model = None
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")) and model is None:
+                model = line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"cpu_model": model or "unknown", "nproc": os.cpu_count()}
+
+
+def oracle_iterations(iters_per_step, steps, warmup):
+    """The oracle (CPU, FP64) on the full workload: build it (setup, not
+    timed), then time `steps` steps of `iters_per_step` PCG iterations each on
+    the workload's first right-hand side.  Returns seconds per step and the
+    setup time."""
     from oracle import bddc as obddc
     from oracle import pcg as opcg
-    k, e2s, ns, b = _cpu_sample_workload()
-    H = obddc.build(SAMPLE_NX, k, e2s, ns, 2, "adaptive", 10.0)
-    opcg.pcg(H.A, b, H.apply, fixed_iters=2)
+    from paper_0911_5730_gb300 import inputs
+    wl = inputs.two_level_channels()
     t0 = time.perf_counter()
-    opcg.pcg(H.A, b, H.apply, fixed_iters=iters)
-    return (time.perf_counter() - t0) / iters, ns
+    H = obddc.build_workload(wl)
+    setup = time.perf_counter() - t0
+    b = inputs.normal_rhs(wl.n_dof, RHS_SEED)
+    for _ in range(warmup):
+        opcg.pcg(H.A, b, H.apply, fixed_iters=iters_per_step)
+    t = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        opcg.pcg(H.A, b, H.apply, fixed_iters=iters_per_step)
+        t.append(time.perf_counter() - t0)
+    return t, setup
 
 
-def cpu_baseline(gpu_iters):
-    """Run the oracle sample in a single-threaded subprocess (spawned, BLAS at 1 thread)."""
-    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1",
-               CUDA_VISIBLE_DEVICES="")
+ORACLE_STEP_ITERS = 3     # PCG iterations of the full workload per oracle step
+
+
+def oracle_start(steps, warmup, threads=1):
+    """oracle_iterations in a new process (no GPU; started with exec, not a
+    fork of this one) with `threads` BLAS threads, set before numpy loads:
+    single-threaded BLAS is the oracle's fastest setting (its setup is
+    thousands of small dense solves, which threads only slow down: 27 s
+    against 174 s with eight on an 8-core x86 host)."""
+    env = dict(os.environ, CUDA_VISIBLE_DEVICES="", OPENBLAS_NUM_THREADS=str(threads),
+               OMP_NUM_THREADS=str(threads), MKL_NUM_THREADS=str(threads))
     code = ("import sys, json; sys.path.insert(0, %r); import bench; "
-            "t, ns = bench.cpu_sample_run(); print(json.dumps({'t_iter': t, 'ns': ns}))" % ROOT)
-    p = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
-                       timeout=900)
-    d = json.loads(p.stdout.strip().splitlines()[-1])
+            "t, s = bench.oracle_iterations(%d, %d, %d); print(json.dumps({'t': t, 'setup': s}))"
+            % (ROOT, ORACLE_STEP_ITERS, steps, warmup))
+    return subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE, stderr=subprocess.PIPE,
+                            text=True, env=env)
+
+
+def oracle_finish(p, timeout=1800):
+    """Seconds per step and setup seconds of a run from oracle_start."""
+    out, err = p.communicate(timeout=timeout)
+    if p.returncode != 0:
+        raise RuntimeError("oracle run failed: " + err[-400:])
+    d = json.loads(out.strip().splitlines()[-1])
+    return d["t"], d["setup"]
+
+
+def cpu_baseline(gpu_iters, proc=None):
+    """The oracle on the full workload, single-threaded, in its own process
+    (proc: one already started by oracle_start(1, 1), so that it runs beside
+    the GPU work): its setup (not timed), then one warm-up step and one timed
+    step of ORACLE_STEP_ITERS PCG iterations; solves/s scaled by the
+    iteration count of a solve."""
+    t, setup = oracle_finish(proc if proc is not None else oracle_start(1, 1))
     iters, src = _golden_iters()
     if iters is None:
-        iters, src = gpu_iters, "GPU iteration count"
-    t_solve = d["t_iter"] * FULL_SUBS / d["ns"] * iters
-    return {"value": 1.0 / t_solve, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": ("oracle PCG (FP64, CPU, 1 thread) on the %dx%d corner of the same coefficient "
-                       "field with %d substructures of 16x16 elements, 250 iterations timed; seconds "
-                       "per iteration scaled by %d/%d substructures and %d iterations per solve (%s)"
-                       % (SAMPLE_NX, SAMPLE_NX, d["ns"], FULL_SUBS, d["ns"], iters, src))}
+        iters, src = gpu_iters, "the GPU solve's iteration count"
+    t_iter = sum(t) / (len(t) * ORACLE_STEP_ITERS)
+    out = {"value": 1.0 / (t_iter * iters), "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": ("oracle PCG (FP64, CPU, one thread) on the full workload (512x512, 1024 substructures, "
+                      "adaptive tau = 10; setup %.0f s, not timed): %d iterations timed, %.3f s per iteration, "
+                      "scaled by %d iterations per solve (%s)"
+                      % (setup, ORACLE_STEP_ITERS, t_iter, iters, src))}
+    out.update(cpu_info())
+    return out
 
 
 def _kernel_bytes(q, n_top, prec_bytes, K=1):
@@ -326,8 +377,11 @@ def replica_max(v, world, device):
 
 
 def gpu_arm(a):
-    import torch
     rank, world, local = _dist()
+    # the CPU baseline runs beside the GPU work, in a process started before
+    # the first CUDA call
+    oracle_proc = oracle_start(1, 1) if rank == 0 and not a.no_cpu_baseline else None
+    import torch
     torch.cuda.set_device(local)
     if world > 1:
         import torch.distributed as dist
@@ -429,6 +483,17 @@ def gpu_arm(a):
     serving["at_load"] = {"%.1f" % f: serving_run(bddc, P, wl.n_dof, f * value / world, 3.0, 5001)
                           for f in (0.5, 1.0)}
 
+    # config 5 over configs 2, 3 and 4 resident together (FP32 and FP64 apply,
+    # HBM-budget admission)
+    mix = None
+    if world == 1 and not a.no_serving_mix:
+        from paper_0911_5730_gb300 import serve_mix
+        try:
+            mix = serve_mix.run(load=0.8, seconds=3.0, seed=5001)
+        except Exception as ex:       # reported, never silently replaced
+            mix = {"error": str(ex)[:300]}
+        P.set_precision("fp32")
+
     # end to end: host buffers (pinned), copies inside the timed call
     P.set_precision("fp32")
     bh = torch.from_numpy(Bh).pin_memory()
@@ -461,11 +526,14 @@ def gpu_arm(a):
         src = hashlib.sha1(open(os.path.join(ROOT, "paper_0911_5730_gb300", "csrc", tr["file"]),
                                 "rb").read()).hexdigest()[:12]
         traffic = tr["bytes"] if src == tr["src"] else None
+    fp64_peak = bddc.fp64_rate(5)
     if dom == "top_solve":
         ach = kf[dom] / (ms_dom * 1e-3) / 1e12
-        roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s",
-                "frac": ach / (FP64_PEAK_GFLOPS / 1e3), "traffic": traffic, "kernel": dom,
-                "peak_kind": "FP64 pipe: 2 FMA/clk/SM x 152 SMs x 2.07 GHz (nominal 1.25 TFLOP/s)"}
+        roof = {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": ach / fp64_peak, "traffic": traffic, "kernel": dom,
+                "peak_kind": "measured: FP64 FMA probe of the library (bddc_selftest_fp64_rate, best of 5 "
+                             "launches, eight independent FMA chains per thread on every SM); nominal %.2f "
+                             "TFLOP/s" % FP64_NOMINAL_TFLOPS}
     else:
         ach = kern[dom]["bytes"] / (ms_dom * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
@@ -477,7 +545,7 @@ def gpu_arm(a):
     cpu = None
     if rank == 0 and not a.no_cpu_baseline:
         try:
-            cpu = cpu_baseline(iters)
+            cpu = cpu_baseline(iters, oracle_proc)
         except Exception as ex:       # reported, never silently replaced
             cpu = {"error": str(ex)[:200]}
     elastic = None
@@ -500,6 +568,7 @@ def gpu_arm(a):
         "latency_ms": {"p50": pct(lat, 50), "p99": pct(lat, 99),
                        "what": "one right-hand side per solve, FP32 apply"},
         "serving": serving,
+        "serving_mix": mix,
         "iterations": iters,
         "compare": {"fp64_solves_per_s": world * BATCH * len(ms64) / t64,
                     "fp64_iterations": inf64[0][0]["iters"],
@@ -548,41 +617,32 @@ def profile_apply(a):
 
 
 def reference_arm(a):
+    """The oracle (the CPU FP64 restatement of the paper's method that the GPU
+    path is checked against) as the reference: the full workload, setup not
+    timed, each step ORACLE_STEP_ITERS PCG iterations on one host core (its
+    fastest setting, see oracle_start); solves/s scaled by the oracle's
+    iteration count of a solve."""
     rank, world, _ = _dist()
     if rank != 0:
         return
-    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
-    from oracle import bddc as obddc
-    from oracle import pcg as opcg
-    k, e2s, ns, b = _cpu_sample_workload()
-    H = obddc.build(SAMPLE_NX, k, e2s, ns, 2, "adaptive", 10.0)
+    t, setup = oracle_finish(oracle_start(a.steps, a.warmup))
     iters, src = _golden_iters()
     if iters is None:
         iters, src = 27, "assumed"
-    per_step_iters = 10
-
-    def step():
-        t0 = time.perf_counter()
-        opcg.pcg(H.A, b, H.apply, fixed_iters=per_step_iters)
-        return (time.perf_counter() - t0) / per_step_iters * FULL_SUBS / ns * iters
-
-    for _ in range(a.warmup):
-        step()
-    t = [step() for _ in range(a.steps)]
-    value = a.steps / sum(t)
-    cores = 1 if os.environ.get("OPENBLAS_NUM_THREADS") == "1" else (os.cpu_count() or 1)
-    sample = ("oracle PCG (FP64, CPU) on the %dx%d corner of the same coefficient field, %d "
-              "substructures, %d iterations per step; scaled by %d/%d substructures and %d "
-              "iterations per solve (%s)" % (SAMPLE_NX, SAMPLE_NX, ns, per_step_iters, FULL_SUBS,
-                                             ns, iters, src))
+    value = a.steps * ORACLE_STEP_ITERS / (sum(t) * iters)
+    cores = 1
+    sample = ("oracle PCG (FP64, CPU, one thread) on the full workload (512x512, 1024 substructures, "
+              "adaptive tau = 10; setup %.0f s, not timed), %d iterations per step; solves/s scaled by %d "
+              "iterations per solve (%s)" % (setup, ORACLE_STEP_ITERS, iters, src))
+    base = {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+    base.update(cpu_info())
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * sum(t) / a.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded inputs, paper's model problem)",
         "config": bench_config(1),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": sample},
+        "cpu_baseline": base,
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 

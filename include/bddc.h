@@ -413,6 +413,18 @@ int bddc_selftest_wait_timeout(void *stream);
  */
 int bddc_selftest_convert(const double *d_dev, int64_t n, int64_t *mismatches, void *stream);
 
+/*
+ * bddc_selftest_fp64_rate - measure this GPU's FP64 fused multiply-add rate,
+ * the ceiling of the kernels bound by FP64 arithmetic (the top-level coarse
+ * product): 8 x SMs blocks of 256 threads, each thread eight independent FMA
+ * chains of 4096 steps, timed with CUDA events on `stream` after one untimed
+ * launch.  *tflops (host) receives 2 x FMAs / seconds / 1e12, the best of
+ * `reps` (>= 1) launches.  Allocates 8 bytes of device memory and waits for
+ * the stream.  BDDC_E_ARG for reps < 1 or a null tflops.  No counterpart in
+ * the paper.
+ */
+int bddc_selftest_fp64_rate(int reps, double *tflops, void *stream);
+
 void bddc_destroy(bddc_ctx *ctx);
 
 /* Message of the last error on the calling thread ("" if none). */

@@ -27,6 +27,7 @@ SYMBOLS = ["bddc_setup", "bddc_apply", "bddc_pcg_solve", "bddc_pcg_solve_host", 
            "bddc_last_error", "bddc_server_create", "bddc_submit", "bddc_wait",
            "bddc_server_destroy", "bddc_profile_apply", "bddc_apply_noalloc", "bddc_inspect",
            "bddc_selftest_wait_timeout", "bddc_selftest_convert", "bddc_profile_apply_batch",
+           "bddc_selftest_fp64_rate",
            "bddc_partition_graph", "bddc_partition_mesh", "bddc_group_substructures"]
 
 
@@ -110,6 +111,7 @@ def load():
     lib.bddc_apply_noalloc.argtypes = [vp, vp, vp, vp]
     lib.bddc_selftest_wait_timeout.argtypes = [vp]
     lib.bddc_selftest_convert.argtypes = [vp, C.c_int64, C.POINTER(C.c_int64), vp]
+    lib.bddc_selftest_fp64_rate.argtypes = [i32, C.POINTER(C.c_double), vp]
     lib.bddc_partition_graph.argtypes = [i32, vp, vp, vp, vp, i32, dp, C.c_uint64, vp, vp]
     lib.bddc_partition_mesh.argtypes = [vp, vp, i32, dp, C.c_uint64, vp, vp]
     lib.bddc_group_substructures.argtypes = [vp, vp, i32, i32, dp, C.c_uint64, vp, vp]
@@ -168,6 +170,13 @@ def selftest_convert(values):
     out = C.c_int64()
     _check(load().bddc_selftest_convert(_ptr(values.contiguous()), int(values.numel()),
                                         C.byref(out), None))
+    return out.value
+
+
+def fp64_rate(reps=5):
+    """Measured FP64 FMA rate of the current GPU in TFLOP/s (best of reps)."""
+    out = C.c_double()
+    _check(load().bddc_selftest_fp64_rate(int(reps), C.byref(out), None))
     return out.value
 
 

@@ -1267,6 +1267,18 @@ template <class T, class ACC> void post_t(const DevLevel &L, const double *r, do
 
 }  // namespace
 
+// SMs of the current device, queried once per process (a thread-safe static:
+// the server's engines and the batch groups launch from several threads)
+int device_sms() {
+    static const int n = [] {
+        int dev = 0, v = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        return v > 0 ? v : 1;   // no device answered: the launches that follow report the error
+    }();
+    return n;
+}
+
 // ----------------------------------------------------------------------------
 // launchers
 // ----------------------------------------------------------------------------
@@ -1275,16 +1287,7 @@ namespace {
 constexpr size_t kSmemMax = 227 * 1024;        // dynamic shared memory of one block
 constexpr size_t kSmemBudget = kSmemMax;
 
-int num_sms() {
-    static int n = 0;
-    if (!n) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 1;   // no device answered: the launches that follow report the error
-    }
-    return n;
-}
+int num_sms() { return device_sms(); }
 
 // Warps (substructures) per block: as many as needed for one wave over the
 // SMs, limited by the shared-memory slices that fit in one block.

@@ -1389,6 +1389,25 @@ __global__ void k_b_column(int n, int K, int k, const double *x, double *dst) {
 
 // Both integer-operation conversions against the hardware ones, bit for bit
 // (NaN results compared as NaN).
+// FP64 fused multiply-add rate: kFmaChains independent chains per thread, so
+// that neither latency nor issue of anything else limits the FP64 pipe.  The
+// sum is written only if it takes a value it cannot reach (it keeps the
+// chains live).  Launched kFmaBlocksPerSm x SMs blocks of 256 threads.
+constexpr int kFmaChains = 8;
+__global__ void __launch_bounds__(256) k_fp64_rate(int iters, double b, double c, double *out) {
+    double a[kFmaChains];
+#pragma unroll
+    for (int j = 0; j < kFmaChains; ++j) a[j] = 1e-3 * threadIdx.x + j;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int j = 0; j < kFmaChains; ++j) a[j] = fma(a[j], b, c);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < kFmaChains; ++j) s += a[j];
+    if (s == -1.0) out[0] = s;
+}
+
 __global__ void k_selftest_convert(const double *d, int64_t n, unsigned long long *bad) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -1405,16 +1424,7 @@ __global__ void k_selftest_convert(const double *d, int64_t n, unsigned long lon
 
 constexpr size_t kSmemMaxB = 227 * 1024;
 
-int num_sms_b() {
-    static int n = 0;
-    if (!n) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 1;   // no device answered: the launches that follow report the error
-    }
-    return n;
-}
+int num_sms_b() { return device_sms(); }
 
 int warps_b(int nsub, size_t slice) {
     const int fit = (int)(kSmemMaxB / slice);
@@ -1845,6 +1855,9 @@ void launch_b_column(int n, int K, int k, const double *x, double *dst, cudaStre
 }
 void launch_selftest_convert(const double *d, int64_t n, unsigned long long *bad, cudaStream_t s) {
     if (n > 0) k_selftest_convert<<<(int)((n + 255) / 256), 256, 0, s>>>(d, n, bad);
+}
+void launch_fp64_rate(int iters, double *out, cudaStream_t s) {
+    k_fp64_rate<<<kFmaBlocksPerSm * num_sms_b(), 256, 0, s>>>(iters, 0.9999999, 1e-9, out);
 }
 void launch_b_gather(int n, int K, const double *src, int64_t ld, double *dst, cudaStream_t s) {
     const int64_t nK = (int64_t)n * K;

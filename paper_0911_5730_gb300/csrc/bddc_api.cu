@@ -12,6 +12,7 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <atomic>
 
 namespace bddc {
 
@@ -165,6 +166,7 @@ struct bddc_ctx {
     double *Ainv = nullptr;           // top-level inverse, leading dimension ld_top
     int *err_dev = nullptr;           // set by setup kernels whose bounded waits gave up
     int device = 0;                   // the CUDA device the context was set up on
+    uint64_t serial = 0;              // unique per context of the process (server keys)
     int *happly = nullptr;            // pinned: the error word of the last bddc_apply(_noalloc)
     std::unique_ptr<Workspace> ws;
     // further batch groups of a solve in flight at once (own stream and scratch)
@@ -1502,6 +1504,10 @@ int bddc_setup(const bddc_mesh *mesh, const double *k_elem, const bddc_decomp *d
         C->err_dev = C->arena.alloc_n<int>(1);
         BDDC_CUDA_TRY(cudaMemsetAsync(C->err_dev, 0, sizeof(int), st));
         BDDC_CUDA_TRY(cudaGetDevice(&C->device));
+        {
+            static std::atomic<uint64_t> next_serial{1};
+            C->serial = next_serial++;
+        }
         BDDC_CUDA_TRY(cudaHostAlloc((void **)&C->happly, sizeof(int), cudaHostAllocDefault));
         *C->happly = 0;
         static std::once_flag prep_once;
@@ -2189,6 +2195,37 @@ int bddc_selftest_convert(const double *d_dev, int64_t n, int64_t *mismatches, v
     });
 }
 
+int bddc_selftest_fp64_rate(int reps, double *tflops, void *stream) {
+    return guarded([&]() -> int {
+        if (reps < 1 || !tflops) throw Error(BDDC_E_ARG, "bad argument");
+        cudaStream_t st = (cudaStream_t)stream;
+        DevArena a;
+        double *out = a.alloc_n<double>(1);
+        const int iters = 4096;
+        const double fmas = (double)kFmaBlocksPerSm * device_sms() * 256.0 * iters * 8.0;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        BDDC_CUDA_TRY(cudaEventCreate(&e0));
+        cudaError_t e = cudaEventCreate(&e1);
+        double best = 0.0;
+        launch_fp64_rate(iters, out, st);      // warm-up (module load, clocks)
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+            e = cudaEventRecord(e0, st);
+            if (e == cudaSuccess) launch_fp64_rate(iters, out, st);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e == cudaSuccess && ms > 0.0f) best = std::max(best, 2.0 * fmas / (ms * 1e-3) / 1e12);
+        }
+        if (e == cudaSuccess) e = cudaGetLastError();
+        cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (e != cudaSuccess) throw Error(BDDC_E_CUDA, cudaGetErrorString(e));
+        *tflops = best;
+        return BDDC_OK;
+    });
+}
+
 int bddc_selftest_wait_timeout(void *stream) {
     return guarded([&]() -> int {
         cudaStream_t st = (cudaStream_t)stream;
@@ -2232,6 +2269,7 @@ struct Request {
     std::vector<double> b, x;
     std::vector<bddc_solve_info> info;
     int nrhs = 1, maxit = 1000, status = BDDC_OK;
+    int prec = BDDC_PREC_FP64;  // the context's apply precision when submitted
     int remaining = 0;          // right-hand sides not finished (continuous batching)
     bool started = false;       // holds its share of the budget
     double rtol = 1e-8;
@@ -2251,6 +2289,7 @@ constexpr int kEnginesPerProblem = kGroupsInFlight;
 using PendingQueue = std::deque<std::pair<std::shared_ptr<Request>, int>>;
 struct Engine {
     bddc_ctx *ctx = nullptr;
+    int prec = BDDC_PREC_FP64;
     int K = kMaxBatch;
     std::shared_ptr<PendingQueue> pending;
     std::thread th;
@@ -2271,7 +2310,9 @@ struct bddc_server {
     std::deque<std::shared_ptr<bddc::Request>> queue;      // problems the batch kernels cannot take
     std::map<uint64_t, std::shared_ptr<bddc::Request>> reqs;
     std::vector<std::thread> workers;
-    std::map<bddc_ctx *, std::vector<std::unique_ptr<bddc::Engine>>> engines;
+    // engines per (context serial, apply precision): a context destroyed and
+    // another set up at the same address never meets the old engines
+    std::map<std::pair<uint64_t, int>, std::vector<std::unique_ptr<bddc::Engine>>> engines;
 };
 
 namespace bddc {
@@ -2282,7 +2323,7 @@ size_t request_bytes(const bddc_ctx *ctx, int nrhs) {
 }
 
 void worker_loop(bddc_server *S) {
-    std::map<bddc_ctx *, std::unique_ptr<Workspace>> wss;
+    std::map<uint64_t, std::unique_ptr<Workspace>> wss;   // by context serial
     DevArena bufs;
     size_t cap = 0;
     double *db = nullptr, *dx = nullptr;
@@ -2304,7 +2345,7 @@ void worker_loop(bddc_server *S) {
         try {
             bddc_ctx *C = R->ctx;
             BDDC_CUDA_TRY(cudaSetDevice(C->device));
-            auto &W = wss[C];
+            auto &W = wss[C->serial];
             if (!W) { W.reset(new Workspace()); make_workspace(C, *W, 10000); }
             const int n = C->n();
             if ((size_t)n > cap) {
@@ -2316,7 +2357,7 @@ void worker_loop(bddc_server *S) {
             for (int j = 0; j < R->nrhs; ++j) {
                 BDDC_CUDA_TRY(cudaMemcpyAsync(db, R->b.data() + (size_t)j * n, sizeof(double) * n,
                                               cudaMemcpyHostToDevice, W->stream));
-                const int s = pcg_one(C, *W, C->prec, db, dx, R->rtol, R->maxit, &R->info[j]);
+                const int s = pcg_one(C, *W, R->prec, db, dx, R->rtol, R->maxit, &R->info[j]);
                 BDDC_CUDA_TRY(cudaMemcpyAsync(R->x.data() + (size_t)j * n, dx, sizeof(double) * n,
                                               cudaMemcpyDeviceToHost, W->stream));
                 BDDC_CUDA_TRY(cudaStreamSynchronize(W->stream));
@@ -2339,6 +2380,7 @@ void worker_loop(bddc_server *S) {
 
 // Finish one request's share of the budget and wake its waiters (S->mu held).
 void finish_request(bddc_server *S, Request &R) {
+    if (R.done) return;   // failed earlier by another engine that held part of it
     R.t_done = std::chrono::steady_clock::now();
     R.done = true;
     if (R.started) S->in_use -= R.bytes;
@@ -2417,7 +2459,7 @@ void engine_loop(bddc_server *S, Engine *E) {
                 launch_b_admit(n, K, k, BW.bcol + (size_t)k * n, BW.x, BW.r, BW.part, BW.counter, BW.sc,
                                R.rtol, std::min(R.maxit, W->maxit_cap), st);
             }
-            cudaGraphExec_t g = batch_graph(C, *W, BW, C->prec, K);
+            cudaGraphExec_t g = batch_graph(C, *W, BW, E->prec, K);
             for (int c = 0; c < 2; ++c) BDDC_CUDA_TRY(cudaGraphLaunch(g, st));
             BDDC_CUDA_TRY(cudaMemcpyAsync(BW.hsc, BW.sc, sizeof(BatchScalars), cudaMemcpyDeviceToHost, st));
             BDDC_CUDA_TRY(cudaStreamSynchronize(st));
@@ -2482,13 +2524,16 @@ void engine_loop(bddc_server *S, Engine *E) {
                     I.lam_min = lmin;
                     I.lam_max = lmax;
                     I.kappa_est = lmin > 0 ? lmax / lmin : 0.0;
-                    if (status != BDDC_OK) R.status = status;
+                    if (status != BDDC_OK && !R.done) R.status = status;
                     if (--R.remaining == 0) finish_request(S, R);
                     slot[k].R.reset();
                     slot[k].j = -1;
                 }
             }
             S->cv_done.notify_all();
+            // a finished request returned its budget: engines and workers
+            // waiting to admit may go on
+            S->cv_work.notify_all();
         }
     } catch (const Error &e) {
         fail_all(e.code, e.msg);
@@ -2496,6 +2541,7 @@ void engine_loop(bddc_server *S, Engine *E) {
         fail_all(BDDC_E_CUDA, e.what());
     }
     S->cv_done.notify_all();
+    S->cv_work.notify_all();
 }
 
 }  // namespace
@@ -2533,14 +2579,18 @@ int bddc_submit(bddc_server *srv, bddc_ctx *ctx, const double *b_host, int nrhs,
         R->bytes = request_bytes(ctx, nrhs);
         R->remaining = nrhs;
         if (srv->budget && R->bytes > srv->budget) throw Error(BDDC_E_BUSY, "request exceeds the HBM budget");
-        const bool batch = ctx->ws && batch_ok(ctx, *ctx->ws, ctx->prec);
+        {
+            std::lock_guard<std::mutex> lk(ctx->mu);
+            R->prec = ctx->prec;
+        }
+        const bool batch = ctx->ws && batch_ok(ctx, *ctx->ws, R->prec);
         {
             std::lock_guard<std::mutex> lk(srv->mu);
             R->id = srv->next_id++;
             R->t_submit = std::chrono::steady_clock::now();
             srv->reqs[R->id] = R;
             if (batch) {
-                auto &Es = srv->engines[ctx];
+                auto &Es = srv->engines[std::make_pair(ctx->serial, R->prec)];
                 auto q = Es.empty() ? std::make_shared<PendingQueue>() : Es.front()->pending;
                 Es.resize(kEnginesPerProblem);
                 for (auto &E : Es) {
@@ -2551,6 +2601,7 @@ int bddc_submit(bddc_server *srv, bddc_ctx *ctx, const double *b_host, int nrhs,
                     if (!E) {
                         E.reset(new Engine());
                         E->ctx = ctx;
+                        E->prec = R->prec;
                         E->K = kMaxBatch;
                         E->pending = q;
                         E->th = std::thread(engine_loop, srv, E.get());

@@ -32,6 +32,8 @@ void set_error(const std::string &msg);
 // Largest grid of the grid-stride vector kernels (eight blocks per SM on this
 // GPU's 152 SMs); the per-block partial-sum buffers are sized for it.
 constexpr int kMaxVecGrid = 1216;
+// SMs of the current device (queried once per process)
+int device_sms();
 
 // ----------------------------------------------------------------------------
 // Device buffers owned by a context
@@ -347,6 +349,10 @@ void launch_b_column(int n, int K, int k, const double *x, double *dst, cudaStre
 // mismatches of the integer-operation binary32/binary64 conversions against
 // the hardware conversions on n values (added to *bad)
 void launch_selftest_convert(const double *d, int64_t n, unsigned long long *bad, cudaStream_t s);
+// the FP64 FMA rate probe: kFmaBlocksPerSm x SMs blocks of 256 threads, each
+// thread 8 independent chains of `iters` FMAs
+constexpr int kFmaBlocksPerSm = 8;
+void launch_fp64_rate(int iters, double *out, cudaStream_t s);
 // caller layout (column k at src + k * ld) <-> interleaved
 void launch_b_gather(int n, int K, const double *src, int64_t ld, double *dst, cudaStream_t s);
 void launch_b_scatter(int n, int K, const double *src, double *dst, int64_t ld, cudaStream_t s);

@@ -666,16 +666,7 @@ __global__ void k_tc_pack(SetupLevel S, const int64_t *offX, const double *Xbase
     }
 }
 
-int tc_sms() {
-    static int n = 0;
-    if (!n) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 1;
-    }
-    return n;
-}
+int tc_sms() { return device_sms(); }
 
 // Operand stages that fit in the shared memory of one of two CTAs per SM
 // (at least two, at most three: two CTAs per SM keep enough copies in flight).
@@ -710,16 +701,16 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 EncodeTiledFn encode_fn() {
-    static EncodeTiledFn fn = nullptr;
-    if (!fn) {
+    static const EncodeTiledFn fn = [] {
         void *p = nullptr;
         cudaDriverEntryPointQueryResult q{};
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
                 cudaSuccess ||
-            q != cudaDriverEntryPointSuccess || !p)
-            throw Error(BDDC_E_CUDA, "cuTensorMapEncodeTiled is not available");
-        fn = reinterpret_cast<EncodeTiledFn>(p);
-    }
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return reinterpret_cast<EncodeTiledFn>(p);
+    }();
+    if (!fn) throw Error(BDDC_E_CUDA, "cuTensorMapEncodeTiled is not available");
     return fn;
 }
 

@@ -1,7 +1,10 @@
 """Write the oracle's results for the full-size workloads to tests/golden/.
 
 Calls only the CPU oracle (oracle/) on the seeded inputs of
-paper_0911_5730_gb300.inputs; nothing here touches the CUDA path.
+paper_0911_5730_gb300.inputs; nothing here touches the CUDA path.  Besides
+the JSON summary, the full FP64 solution and apply vectors go to
+<workload>_x.npy and <workload>_z.npy for the element-by-element parity of
+the full-size GPU tests.
 
     python tests/golden/make_golden.py two_level_channels_512 three_level_blocks_1024
 """
@@ -68,6 +71,8 @@ def make(name):
     }
     with open(os.path.join(HERE, name + ".json"), "w") as f:
         json.dump(out, f)
+    np.save(os.path.join(HERE, name + "_x.npy"), res.x)
+    np.save(os.path.join(HERE, name + "_z.npy"), z_apply)
     print(name, "iters", res.iters, "nc", H.info["n_coarse"], "setup %.1fs solve %.1fs" % (t_setup, t_solve))
 
 
