@@ -137,7 +137,9 @@ typedef struct {
     /* tile shapes the autotuner chose for the batch kernels of this context
      * (timed on the context's own operators when its batch workspace is first
      * used): node tile of the batched PCG stencil (x, y) and rows per block of
-     * the top-level product; 0 before the first batched call */
+     * the top-level product with the dense inverse, or 0 when the batched top
+     * solve uses the block-tridiagonal factor (top_blocks); 0 before the first
+     * batched call */
     int32_t tuned_tile[3];
     /* bit l-1 set: the batched interior corrections of BDDC level l (eqs. 4-5
      * and 10-11) run as dense tensor-core products (tcgen05) in FP32 and BF16
@@ -150,7 +152,14 @@ typedef struct {
      * return before their stream runs; read this once it has been
      * synchronised).  The solves report such a wait in their own status. */
     int32_t apply_status;
-    int32_t reserved3;
+    /* blocks of the top-level factor: the setup orders the coarse DOFs of the
+     * last level by the breadth-first level sets of A_L's graph, merges them
+     * into blocks (A_L is then block tridiagonal) and factors A_L blockwise
+     * in FP64 (Sec. 2.1: the top level is solved directly).  Top levels of
+     * up to 4096 DOFs also keep the dense inverse, formed from that factor,
+     * for the single right-hand-side apply.  0: dense Cholesky instead (a top
+     * level too large for the factor's apply kernel, or none). */
+    int32_t top_blocks;
 } bddc_info;
 
 /*

@@ -163,7 +163,8 @@ struct bddc_ctx {
     double *w_dev = nullptr;          // Q1 stencil weights [5][n]
     std::vector<LevelData> L;
     int n_top = 0, ld_top = 0;
-    double *Ainv = nullptr;           // top-level inverse, leading dimension ld_top
+    double *Ainv = nullptr;           // top-level inverse, leading dimension ld_top (small top levels)
+    std::unique_ptr<TopBand> band;    // top level as a block-tridiagonal Cholesky factor
     int *err_dev = nullptr;           // set by setup kernels whose bounded waits gave up
     int device = 0;                   // the CUDA device the context was set up on
     uint64_t serial = 0;              // unique per context of the process (server keys)
@@ -217,6 +218,39 @@ template <class T> std::vector<int64_t> prefix(const std::vector<T> &v) {
     std::vector<int64_t> o(v.size() + 1, 0);
     for (size_t i = 0; i < v.size(); ++i) o[i + 1] = o[i] + (int64_t)v[i];
     return o;
+}
+
+// Top levels up to this many DOFs also keep the dense inverse (at most
+// 128 MB), formed from the factor kTopInverseCols columns at a time.
+constexpr int kDenseTopMax = 4096;
+constexpr int kTopInverseCols = 256;
+int dense_top_max() {
+    if (const char *e = std::getenv("BDDC_TOP_DENSE_MAX")) return std::atoi(e);
+    return kDenseTopMax;
+}
+
+// Least DOFs of a block of the top-level factor (merged level sets).
+int top_bmin() {
+    if (const char *e = std::getenv("BDDC_TOP_BMIN")) {
+        const int v = std::atoi(e);
+        if (v >= 1) return v;
+    }
+    return 64;
+}
+
+// u = A_L^-1 r on the top level for one right-hand side: the product with
+// the dense inverse where the setup kept one (one pass over it at the HBM
+// rate), else the block-tridiagonal factor.
+void top_solve_1(const bddc_ctx *C, const double *r, double *u, const int *skip, cudaStream_t st) {
+    if (C->Ainv) launch_dense_symv(C->n_top, C->ld_top, C->Ainv, r, u, skip, st);
+    else launch_top_band(*C->band, r, 1, u, 1, 1, skip, st);
+}
+// The same for K interleaved right-hand sides, by the form the autotuner
+// chose (variant >= 0: the dense product of that variant; -1: the factor).
+void top_solve_b(const bddc_ctx *C, int variant, const double *r, double *u, int K, const int *skip, int *err,
+                 cudaStream_t st) {
+    if (variant >= 0) launch_gemm_b(C->n_top, C->ld_top, C->Ainv, r, u, K, skip, err, st, variant);
+    else launch_top_band(*C->band, r, K, u, K, K, skip, st);
 }
 
 void check_err(int *err_dev, cudaStream_t s, const char *what) {
@@ -737,7 +771,8 @@ void setup_level(bddc_ctx *C, LevelData &LD, const double *emat, const std::vect
     }
 }
 
-void make_workspace(bddc_ctx *C, Workspace &W, int maxit_cap) {
+// prio: CUDA stream priority of the workspace's stream (0: the default)
+void make_workspace(bddc_ctx *C, Workspace &W, int maxit_cap, int prio = 0) {
     DevArena &A = W.arena;
     const int n = C->n();
     W.lv.clear();
@@ -781,7 +816,7 @@ void make_workspace(bddc_ctx *C, Workspace &W, int maxit_cap) {
     for (auto &D : W.lv) D.err = W.err;
     BDDC_CUDA_TRY(cudaHostAlloc((void **)&W.hsc, sizeof(PcgScalars), cudaHostAllocDefault));
     BDDC_CUDA_TRY(cudaHostAlloc((void **)&W.hout, 8 * sizeof(double), cudaHostAllocDefault));
-    BDDC_CUDA_TRY(cudaStreamCreateWithFlags(&W.stream, cudaStreamNonBlocking));
+    BDDC_CUDA_TRY(cudaStreamCreateWithPriority(&W.stream, cudaStreamNonBlocking, prio));
     BDDC_CUDA_TRY(cudaEventCreateWithFlags(&W.ev, cudaEventDisableTiming));
 }
 
@@ -790,7 +825,7 @@ void apply_rec(bddc_ctx *C, Workspace &W, int l, int prec, const double *r, doub
     const DevLevel &D = W.lv[l];
     apply_level_pre(D, prec, r, skip, st);
     if (l + 1 == (int)W.lv.size())
-        launch_dense_symv(C->n_top, C->ld_top, C->Ainv, D.rcv, D.ucv, skip, st);
+        top_solve_1(C, D.rcv, D.ucv, skip, st);
     else
         apply_rec(C, W, l + 1, prec, D.rcv, D.ucv, skip, st);
     apply_level_post(D, prec, r, z, skip, st, nullptr, rz);
@@ -986,7 +1021,7 @@ void reduced_precondition(bddc_ctx *C, Workspace &W, ReducedWs &R, int prec, cud
     launch_red_scatter(D.n_iface, D.ifaceDof, R.r, R.rf, skip, st);
     apply_level_neumann(D, prec, R.rf, skip, st);                            // (6)-(8)
     if (W.lv.size() == 1)
-        launch_dense_symv(C->n_top, C->ld_top, C->Ainv, D.rcv, D.ucv, skip, st);
+        top_solve_1(C, D.rcv, D.ucv, skip, st);
     else
         apply_rec(C, W, 1, prec, D.rcv, D.ucv, skip, st);                   // level 2 onwards
     apply_level_average(D, prec, skip, st);                                  // (9)
@@ -1117,6 +1152,24 @@ bool batch_ok(bddc_ctx *C, Workspace &W, int prec) {
     return true;
 }
 
+// Mean time of three top-level solves of K right-hand sides in the given
+// form, after one untimed (ms).
+double time_top_b(const bddc_ctx *C, int variant, const double *r, double *u, int K, int *err, cudaStream_t st) {
+    cudaEvent_t e0, e1;
+    BDDC_CUDA_TRY(cudaEventCreate(&e0));
+    BDDC_CUDA_TRY(cudaEventCreate(&e1));
+    top_solve_b(C, variant, r, u, K, nullptr, err, st);
+    BDDC_CUDA_TRY(cudaEventRecord(e0, st));
+    for (int i = 0; i < 3; ++i) top_solve_b(C, variant, r, u, K, nullptr, err, st);
+    BDDC_CUDA_TRY(cudaEventRecord(e1, st));
+    BDDC_CUDA_TRY(cudaEventSynchronize(e1));
+    float ms = 0.0f;
+    BDDC_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return ms / 3.0;
+}
+
 BatchWs &batch_ws(bddc_ctx *C, Workspace &W) {
     if (W.bw) return *W.bw;
     auto bw = std::make_unique<BatchWs>();
@@ -1179,14 +1232,24 @@ BatchWs &batch_ws(bddc_ctx *C, Workspace &W) {
                                    : dir_spmv_tune(C->nx, KB, C->w_dev, bw->z, bw->p, bw->p1, bw->q, bw->part,
                                                    bw->counter, scs, al, st);
             const BatchLevel &top = bw->lv.back();
-            C->gemm_v = gemm_tune(C->n_top, C->ld_top, C->Ainv, top.rcv, top.ucv, KB, W.err, st);
+            C->gemm_v = C->Ainv ? gemm_tune(C->n_top, C->ld_top, C->Ainv, top.rcv, top.ucv, KB, W.err, st) : -1;
+            if (C->Ainv && C->band) {
+                // the block-tridiagonal factor against the best dense product
+                const double t_dense = time_top_b(C, C->gemm_v, top.rcv, top.ucv, KB, W.err, st);
+                const double t_band = time_top_b(C, -1, top.rcv, top.ucv, KB, W.err, st);
+                if (const char *e = std::getenv("BDDC_TOP_FORM")) {
+                    if (e[0] == 'b') C->gemm_v = -1;
+                } else if (t_band < t_dense) {
+                    C->gemm_v = -1;
+                }
+            }
             BDDC_CUDA_TRY(cudaStreamSynchronize(st));
             BDDC_CUDA_TRY(cudaGetLastError());
             int tx = 0, ty = 0;
             if (!elastic(C)) dir_spmv_tile(C->tile_v, &tx, &ty);
             C->tuned[0] = tx;
             C->tuned[1] = ty;
-            C->tuned[2] = gemm_rows(C->gemm_v, C->n_top);
+            C->tuned[2] = C->gemm_v >= 0 ? gemm_rows(C->gemm_v, C->n_top) : 0;
         }
         bw->tile_v = C->tile_v;
         bw->gemm_v = C->gemm_v;
@@ -1201,7 +1264,7 @@ void apply_b_rec(bddc_ctx *C, Workspace &W, BatchWs &BW, int l, int prec, const 
     const BatchLevel &B = BW.lv[l];
     apply_level_pre_b(D, B, prec, r, skip, st);
     if (l + 1 == (int)W.lv.size())
-        launch_gemm_b(C->n_top, C->ld_top, C->Ainv, B.rcv, B.ucv, B.K, skip, W.err, st, BW.gemm_v);
+        top_solve_b(C, BW.gemm_v, B.rcv, B.ucv, B.K, skip, W.err, st);
     else
         apply_b_rec(C, W, BW, l + 1, prec, B.rcv, B.ucv, skip, st);
     apply_level_post_b(D, B, prec, r, z, skip, st, nullptr, rz);
@@ -1511,7 +1574,7 @@ int bddc_setup(const bddc_mesh *mesh, const double *k_elem, const bddc_decomp *d
         BDDC_CUDA_TRY(cudaHostAlloc((void **)&C->happly, sizeof(int), cudaHostAllocDefault));
         *C->happly = 0;
         static std::once_flag prep_once;
-        std::call_once(prep_once, [] { prepare_apply_kernels(); prepare_batch_kernels(); });
+        std::call_once(prep_once, [] { prepare_apply_kernels(); prepare_batch_kernels(); prepare_top_kernels(); });
         DevArena tmp;
         int *err = tmp.alloc_n<int>(1);
         BDDC_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
@@ -1547,12 +1610,36 @@ int bddc_setup(const bddc_mesh *mesh, const double *k_elem, const bddc_decomp *d
             const int mode2 = o.constraints_level2 >= 0 ? o.constraints_level2 : o.constraints;
             setup_level(C.get(), C->L[1], P.ac, P.offAc, mode2, tau, tmp, err, st);
         }
-        // top level: dense FP64 Cholesky and explicit inverse
+        // top level: A_L as a block-tridiagonal Cholesky factor (FP64, on the
+        // GPU); a small top level also keeps its dense inverse, formed from
+        // that factor, for the single right-hand-side apply
         {
             LevelData &T = C->L.back();
             const int nt = T.nc;
             C->n_top = nt;
+            C->ld_top = std::max(4, (nt + 3) & ~3);
+            bool band = false;
             if (nt > 0) {
+                C->band.reset(new TopBand());
+                band = build_top_band(nt, T.rc, T.offAc, T.ac, top_bmin(), *C->band, C->arena, tmp, err, st);
+                check_err(err, st, "top-level block Cholesky");
+                if (!band) C->band.reset();
+            }
+            if (nt == 0) {
+                C->Ainv = C->arena.alloc_n<double>(4);
+                BDDC_CUDA_TRY(cudaMemsetAsync(C->Ainv, 0, 4 * sizeof(double), st));
+            } else if (band && nt <= dense_top_max()) {
+                // columns of A_L^-1: the factor applied to the identity
+                double *I = tmp.alloc_n<double>((size_t)nt * nt);
+                BDDC_CUDA_TRY(cudaMemsetAsync(I, 0, sizeof(double) * (size_t)nt * nt, st));
+                launch_identity(nt, I, st);
+                C->Ainv = C->arena.alloc_n<double>((size_t)nt * C->ld_top);
+                BDDC_CUDA_TRY(cudaMemsetAsync(C->Ainv, 0, sizeof(double) * (size_t)nt * C->ld_top, st));
+                for (int j0 = 0; j0 < nt; j0 += kTopInverseCols)
+                    launch_top_band(*C->band, I + j0, nt, C->Ainv + j0, C->ld_top, std::min(kTopInverseCols, nt - j0),
+                                    nullptr, st);
+            } else if (!band) {
+                // the factor does not fit the apply kernel: dense Cholesky
                 double *Atop = tmp.alloc_n<double>((size_t)nt * nt);
                 BDDC_CUDA_TRY(cudaMemsetAsync(Atop, 0, sizeof(double) * (size_t)nt * nt, st));
                 std::vector<int> ncl(T.H.nsub);
@@ -1567,13 +1654,9 @@ int bddc_setup(const bddc_mesh *mesh, const double *k_elem, const bddc_decomp *d
                 launch_scatter_dense(T.H.nsub, dn, doc, drc, doac, T.ac, Atop, nt, st);
                 dense_cholesky(nt, Atop, err, st);
                 check_err(err, st, "top-level Cholesky");
-                C->ld_top = (nt + 3) & ~3;
                 C->Ainv = C->arena.alloc_n<double>((size_t)nt * C->ld_top);
                 BDDC_CUDA_TRY(cudaMemsetAsync(C->Ainv, 0, sizeof(double) * (size_t)nt * C->ld_top, st));
                 dense_inverse_from_cholesky(nt, Atop, C->Ainv, C->ld_top, st);
-            } else {
-                C->Ainv = C->arena.alloc_n<double>(4);
-                C->ld_top = 4;
             }
         }
         BDDC_CUDA_TRY(cudaStreamSynchronize(st));
@@ -1940,6 +2023,7 @@ int bddc_query(const bddc_ctx *ctx, bddc_info *info, int level, int32_t *n_selec
                 info->n_interface[l] = ctx->L[l].D.n_iface;
             }
             for (int t = 0; t < 3; ++t) info->tuned_tile[t] = ctx->tuned[t];
+            info->top_blocks = ctx->band ? ctx->band->nb : 0;
             info->apply_status = *ctx->happly ? BDDC_E_TIMEOUT : BDDC_OK;
             info->tc_levels = 0;
             for (size_t l = 0; l < ctx->L.size(); ++l)
@@ -1999,7 +2083,7 @@ int bddc_profile_apply(bddc_ctx *ctx, const double *r_dev, int reps, double *ms_
                 if (l + 1 < nl) rin[l + 1] = W.lv[l].rcv;
             }
             BDDC_CUDA_TRY(cudaEventRecord(top[0], st));
-            launch_dense_symv(ctx->n_top, ctx->ld_top, ctx->Ainv, W.lv[nl - 1].rcv, W.lv[nl - 1].ucv, nullptr, st);
+            top_solve_1(ctx, W.lv[nl - 1].rcv, W.lv[nl - 1].ucv, nullptr, st);
             BDDC_CUDA_TRY(cudaEventRecord(top[1], st));
             for (int l = nl - 1; l >= 0; --l)
                 apply_level_post(W.lv[l], ctx->prec, rin[l], l == 0 ? z : W.lv[l - 1].ucv, nullptr, st, up[l]);
@@ -2055,8 +2139,7 @@ int bddc_profile_apply_batch(bddc_ctx *ctx, const double *r_dev, int nrhs, int64
                 if (l + 1 < nl) rin[l + 1] = BW.lv[l].rcv;
             }
             BDDC_CUDA_TRY(cudaEventRecord(top[0], st));
-            launch_gemm_b(ctx->n_top, ctx->ld_top, ctx->Ainv, BW.lv[nl - 1].rcv, BW.lv[nl - 1].ucv, K, nullptr,
-                          W.err, st, BW.gemm_v);
+            top_solve_b(ctx, BW.gemm_v, BW.lv[nl - 1].rcv, BW.lv[nl - 1].ucv, K, nullptr, W.err, st);
             BDDC_CUDA_TRY(cudaEventRecord(top[1], st));
             for (int l = nl - 1; l >= 0; --l)
                 apply_level_post_b(W.lv[l], BW.lv[l], ctx->prec, rin[l], l == 0 ? BW.z : BW.lv[l - 1].ucv,
@@ -2164,7 +2247,7 @@ int bddc_apply_noalloc(bddc_ctx *ctx, const double *r_dev, double *z_dev, void *
             apply_level_pre(lv[l], prec, rin[l], nullptr, st);
             if (l + 1 < nl) rin[l + 1] = lv[l].rcv;
         }
-        launch_dense_symv(ctx->n_top, ctx->ld_top, ctx->Ainv, lv[nl - 1].rcv, lv[nl - 1].ucv, nullptr, st);
+        top_solve_1(ctx, lv[nl - 1].rcv, lv[nl - 1].ucv, nullptr, st);
         for (int l = nl - 1; l >= 0; --l)
             apply_level_post(lv[l], prec, rin[l], l == 0 ? z_dev : lv[l - 1].ucv, nullptr, st);
         // whether a bounded wait gave up, for bddc_query once the stream is done
@@ -2290,6 +2373,7 @@ using PendingQueue = std::deque<std::pair<std::shared_ptr<Request>, int>>;
 struct Engine {
     bddc_ctx *ctx = nullptr;
     int prec = BDDC_PREC_FP64;
+    int prio = 0;              // stream priority (engine_priority)
     int K = kMaxBatch;
     std::shared_ptr<PendingQueue> pending;
     std::thread th;
@@ -2317,6 +2401,22 @@ struct bddc_server {
 
 namespace bddc {
 namespace {
+
+// Stream priority of a problem's engines: the fewer DOFs (the less work per
+// iteration), the higher, one step per factor of four above 2^16 DOFs, so
+// that the short requests of a small problem are not queued behind the
+// kernels of a large one (the GPU starts the waiting blocks of the
+// higher-priority stream first); all above the default of other work.
+int engine_priority(int64_t n) {
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int p = greatest;
+    for (int64_t m = n >> 16; m > 0 && p < least - 1; m >>= 2) ++p;
+    return p;
+}
 
 size_t request_bytes(const bddc_ctx *ctx, int nrhs) {
     return (size_t)2 * nrhs * (size_t)ctx->n() * sizeof(double);
@@ -2416,7 +2516,7 @@ void engine_loop(bddc_server *S, Engine *E) {
     try {
         BDDC_CUDA_TRY(cudaSetDevice(C->device));
         W.reset(new Workspace());
-        make_workspace(C, *W, 10000);
+        make_workspace(C, *W, 10000, E->prio);
         BatchWs &BW = batch_ws(C, *W);
         const int K = E->K;
         const int n = C->n();
@@ -2602,6 +2702,7 @@ int bddc_submit(bddc_server *srv, bddc_ctx *ctx, const double *b_host, int nrhs,
                         E.reset(new Engine());
                         E->ctx = ctx;
                         E->prec = R->prec;
+                        E->prio = engine_priority(ctx->n_dof);
                         E->K = kMaxBatch;
                         E->pending = q;
                         E->th = std::thread(engine_loop, srv, E.get());

@@ -520,4 +520,56 @@ void launch_scatter_dense(int nsub, const int *ncl, const int64_t *offC, const i
 void dense_cholesky(int n, double *A, int *err, cudaStream_t s);
 void dense_inverse_from_cholesky(int n, const double *L, double *Ainv, int ld, cudaStream_t s);
 
+// ----------------------------------------------------------------------------
+// The top level as a block-tridiagonal Cholesky factor (top_kernels.cu)
+// ----------------------------------------------------------------------------
+// Coarse DOFs of the top level in the order of the breadth-first level sets
+// of A_L's graph, merged into blocks of at least bmin DOFs.
+struct TopOrder {
+    std::vector<int> perm;    // position -> coarse DOF
+    std::vector<int> boff;    // first position of each block, and n
+};
+TopOrder order_top(int n, const std::vector<std::vector<int>> &rc, int bmin);
+
+// Shared memory of one CTA of the apply (y and x of its right-hand sides).
+constexpr size_t kTopSmemMax = 200 * 1024;
+// CTAs of a cluster of the apply (portable cluster size).
+constexpr int kTopCluster = 8;
+
+// Factor blocks, all row-major FP64: Linv_k = L_k^-1 and LinvT_k (b_k x b_k,
+// at offL[k]), F_k = Linv_k M_k-1 (b_k x b_k-1, offF[k]), G_k = Linv_k^T M_k^T
+// (b_k x b_k+1, offG[k]).
+struct TopBand {
+    int n = 0, nb = 0, bmax = 0;
+    int *perm = nullptr, *boff = nullptr;
+    int64_t *offL = nullptr, *offF = nullptr, *offG = nullptr;
+    double *Linv = nullptr, *LinvT = nullptr, *F = nullptr, *G = nullptr;
+    std::vector<int> hboff;
+    size_t bytes = 0;
+};
+struct TopBandArgs {
+    int n, nb, K;
+    int64_t ldx, ldy;
+    const int *perm, *boff;
+    const int64_t *offL, *offF, *offG;
+    const double *Linv, *LinvT, *F, *G;
+    const double *X;
+    double *Y;
+    const int *skip;
+};
+// Assemble A_L from the top-level substructures' coarse matrices (device ac
+// at offAc, coarse ids rc) into blocks and factor it on the GPU (FP64); the
+// factor goes to `keep`.  False (nothing built) when the apply kernel cannot
+// hold the problem.  A pivot <= 0 sets *err (6000000 + block).
+bool build_top_band(int n, const std::vector<std::vector<int>> &rc, const std::vector<int64_t> &offAc,
+                    const double *ac, int bmin, TopBand &T, DevArena &keep, DevArena &tmp, int *err,
+                    cudaStream_t st);
+// Y = A_L^-1 X for K right-hand sides (X, Y row i at i * ldx / i * ldy, K
+// contiguous); nothing when *skip != 0.
+void launch_top_band(const TopBand &T, const double *X, int64_t ldx, double *Y, int64_t ldy, int K,
+                     const int *skip, cudaStream_t s);
+int top_band_cols(int n, int K);   // right-hand sides per cluster
+void launch_identity(int n, double *I, cudaStream_t s);   // ones on the diagonal of a zeroed n x n
+void prepare_top_kernels();
+
 }  // namespace bddc

@@ -67,12 +67,19 @@ def serve(Ps, wls, load, seconds, seed, budget, cap=None):
         rng = np.random.default_rng(seed + 100 + i)
         rate = load * cap[k] / len(keys)
         t, ev = 0.0, []
-        while t < seconds:
+        while True:
             m = int(rng.integers(1, 65))
-            ev.append((t, m, rng.standard_normal((m, wls[k].n_dof))))
             t += rng.exponential(m / rate)
+            if t >= seconds:
+                break
+            ev.append((t, m, rng.standard_normal((m, wls[k].n_dof))))
         plans[k] = ev
-    events = sorted(((t, k, m, b) for k, ev in plans.items() for t, m, b in ev), key=lambda e: e[0])
+    # a short window of large requests can offer far more or less work than
+    # `load` of the GPU: the arrival times are scaled so that the sampled
+    # requests (GPU time at the closed-loop rates) fill `load` of the window
+    work = sum(m / cap[k] for k, ev in plans.items() for _, m, _ in ev)
+    scale = work / (load * seconds) if work > 0 else 1.0
+    events = sorted(((t * scale, k, m, b) for k, ev in plans.items() for t, m, b in ev), key=lambda e: e[0])
     tickets = []
     lat = {k: [] for k in keys}
     bad = []
@@ -109,10 +116,12 @@ def serve(Ps, wls, load, seconds, seed, budget, cap=None):
         def pct(p):
             return ms[min(len(ms) - 1, int(math.ceil(p / 100.0 * len(ms))) - 1)]
 
-        out[PROBLEMS[k][0]] = {"closed_loop_rhs_per_s": cap[k], "offered_rhs_per_s": load * cap[k] / len(keys),
+        out[PROBLEMS[k][0]] = {"closed_loop_rhs_per_s": cap[k],
+                               "offered_rhs_per_s": n_rhs / (seconds * scale),
                                "requests": len(ms), "rhs": n_rhs, "solves_per_s": n_rhs / end,
                                "latency_ms": {"p50": pct(50), "p99": pct(99)}}
-    out["all"] = {"solves_per_s": sum(v["solves_per_s"] for v in out.values())}
+    out["all"] = {"solves_per_s": sum(v["solves_per_s"] for v in out.values()),
+                  "window_s": seconds * scale, "offered_work_s": work}
     return out, cap
 
 
@@ -129,7 +138,8 @@ def run(load: float = 0.8, seconds: float = 3.0, seed: int = 5001, precisions=("
     budget = _budget(wls.values())
     out = {"load": load, "seconds": seconds, "seed": seed, "hbm_budget_bytes": budget,
            "setup_s": setup_s, "stream": "per problem a Poisson stream (seeded), 1-64 N(0,1) right-hand "
-                                         "sides per request, offered at load x (closed-loop rate / problems)"}
+                                         "sides per request at load x (closed-loop rate / problems), arrival "
+                                         "times scaled so that the sampled requests fill `load` of the window"}
     caps = {}
     try:
         for prec in precisions:
