@@ -358,6 +358,40 @@ def elasticity_entry(bddc, batch=32):
         P.close()
 
 
+def config1_entry(bddc):
+    """Config 1 (32x32 unit-coefficient mesh, 4x4 substructures, corners and
+    edge averages): setup, and one solve of its unit load in FP64 and in FP32
+    (mean of 20 after 3 warm-ups, CUDA events)."""
+    import torch
+    from paper_0911_5730_gb300 import inputs
+    wl = inputs.two_level_unit()
+    t = time.perf_counter()
+    P = bddc.Problem.from_workload(wl)
+    torch.cuda.synchronize()
+    out = {"workload": "two_level_unit_32: 32x32, 4x4 substructures, corners + edge averages",
+           "setup_ms": (time.perf_counter() - t) * 1e3}
+    try:
+        b = torch.tensor(wl.rhs(), device="cuda")
+        x = torch.empty_like(b)
+        st = torch.cuda.current_stream()
+        for prec in ("fp64", "fp32"):
+            P.set_precision(prec)
+            for _ in range(3):
+                P.solve(b, x, rtol=RTOL)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            for _ in range(20):
+                _, info = P.solve(b, x, rtol=RTOL, stream=st)
+            e1.record(st)
+            e1.synchronize()
+            assert info[0]["status"] == 0
+            ms = e0.elapsed_time(e1) / 20
+            out[prec] = {"ms_per_solve": ms, "solves_per_s": 1e3 / ms, "iterations": info[0]["iters"]}
+    finally:
+        P.close()
+    return out
+
+
 def replica_barrier(world):
     """Barrier across the replicas (no-op for one process)."""
     if world > 1:
@@ -554,6 +588,12 @@ def gpu_arm(a):
             elastic = elasticity_entry(bddc)
         except Exception as ex:       # reported, never silently replaced
             elastic = {"error": str(ex)[:200]}
+    cfg1 = None
+    if world == 1:
+        try:
+            cfg1 = config1_entry(bddc)
+        except Exception as ex:       # reported, never silently replaced
+            cfg1 = {"error": str(ex)[:200]}
     lat = sorted(ms1)
 
     def pct(v, p):
@@ -582,6 +622,7 @@ def gpu_arm(a):
                     "reduced_iterations": {"fp32": itr32, "fp64": itr64}},
         "setup_ms": setup_s * 1e3,
         "elasticity": elastic,
+        "config1": cfg1,
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 8 * wl.n_dof * BATCH,
                 "d2h_bytes_per_step": 8 * wl.n_dof * BATCH},
         "roofline": roof,

@@ -77,6 +77,7 @@ struct BatchWs {
     double *bcol = nullptr, *xcol = nullptr;   // caller-layout staging for host buffers
     double *part = nullptr, *alphas = nullptr, *betas = nullptr, *nrm = nullptr;
     double *rzpart = nullptr;            // [nsub of level 1][32] r.z partials
+    double *top_s = nullptr;             // scratch of the top-level factor's solve (2 n_top 32)
     unsigned *counter = nullptr, *rzcounter = nullptr;
     BatchScalars *sc = nullptr;
     BatchScalars *hsc = nullptr;         // pinned mirror
@@ -122,6 +123,7 @@ struct Workspace {
     unsigned *rzcounter = nullptr;
     double *part = nullptr, *alphas = nullptr, *betas = nullptr, *lout = nullptr;
     double *bbuf = nullptr;
+    double *top_s = nullptr;               // scratch of the top-level factor's solve (2 n_top)
     unsigned *counter = nullptr;
     PcgScalars *sc = nullptr;
     PcgScalars *hsc = nullptr;        // pinned mirror
@@ -177,6 +179,7 @@ struct bddc_ctx {
     // workspace (the stencil tile fixes the order of the dot products, so
     // solves in different workspaces stay bit-identical)
     int tile_v = -1, gemm_v = -1;
+    double top_ms[2] = {0.0, 0.0};    // the tuner's times of a batched top solve: dense product, factor
     std::mutex tune_mu;
     double setup_ms = 0.0;
     std::mutex mu;
@@ -223,7 +226,7 @@ template <class T> std::vector<int64_t> prefix(const std::vector<T> &v) {
 // Top levels up to this many DOFs also keep the dense inverse (at most
 // 128 MB), formed from the factor kTopInverseCols columns at a time.
 constexpr int kDenseTopMax = 4096;
-constexpr int kTopInverseCols = 256;
+constexpr int kTopInverseCols = 32;
 int dense_top_max() {
     if (const char *e = std::getenv("BDDC_TOP_DENSE_MAX")) return std::atoi(e);
     return kDenseTopMax;
@@ -241,16 +244,19 @@ int top_bmin() {
 // u = A_L^-1 r on the top level for one right-hand side: the product with
 // the dense inverse where the setup kept one (one pass over it at the HBM
 // rate), else the block-tridiagonal factor.
-void top_solve_1(const bddc_ctx *C, const double *r, double *u, const int *skip, cudaStream_t st) {
+// scratch: 2 n_top doubles (the factor's intermediate vectors).
+void top_solve_1(const bddc_ctx *C, const double *r, double *u, const int *skip, double *scratch, int *err,
+                 cudaStream_t st) {
     if (C->Ainv) launch_dense_symv(C->n_top, C->ld_top, C->Ainv, r, u, skip, st);
-    else launch_top_band(*C->band, r, 1, u, 1, 1, skip, st);
+    else launch_top_band(*C->band, r, 1, u, 1, 1, skip, scratch, err, st);
 }
 // The same for K interleaved right-hand sides, by the form the autotuner
 // chose (variant >= 0: the dense product of that variant; -1: the factor).
+// scratch: 2 n_top K doubles.
 void top_solve_b(const bddc_ctx *C, int variant, const double *r, double *u, int K, const int *skip, int *err,
-                 cudaStream_t st) {
+                 double *scratch, cudaStream_t st) {
     if (variant >= 0) launch_gemm_b(C->n_top, C->ld_top, C->Ainv, r, u, K, skip, err, st, variant);
-    else launch_top_band(*C->band, r, K, u, K, K, skip, st);
+    else launch_top_band(*C->band, r, K, u, K, K, skip, scratch, err, st);
 }
 
 void check_err(int *err_dev, cudaStream_t s, const char *what) {
@@ -775,6 +781,12 @@ void setup_level(bddc_ctx *C, LevelData &LD, const double *emat, const std::vect
 void make_workspace(bddc_ctx *C, Workspace &W, int maxit_cap, int prio = 0) {
     DevArena &A = W.arena;
     const int n = C->n();
+    // every initialisation below runs on the workspace's own stream (a plain
+    // cudaMemset would run on the legacy default stream, which the
+    // non-blocking workspace streams do not wait for), and the stream is
+    // synchronised at the end: callers may use the buffers on other streams
+    BDDC_CUDA_TRY(cudaStreamCreateWithPriority(&W.stream, cudaStreamNonBlocking, prio));
+    cudaStream_t ws = W.stream;
     W.lv.clear();
     for (auto &LD : C->L) {
         DevLevel D = LD.D;
@@ -788,36 +800,37 @@ void make_workspace(bddc_ctx *C, Workspace &W, int maxit_cap, int prio = 0) {
         const int ncp = std::max(std::max(D.nc, 1), C->ld_top);
         D.rcv = A.alloc_n<double>(ncp);
         D.ucv = A.alloc_n<double>(ncp);
-        BDDC_CUDA_TRY(cudaMemset(D.rB, 0, sizeof(double) * std::max(D.n_iface, 1)));
-        BDDC_CUDA_TRY(cudaMemset(D.uB, 0, sizeof(double) * std::max(D.n_iface, 1)));
-        BDDC_CUDA_TRY(cudaMemset(D.rcv, 0, sizeof(double) * ncp));
+        BDDC_CUDA_TRY(cudaMemsetAsync(D.rB, 0, sizeof(double) * std::max(D.n_iface, 1), ws));
+        BDDC_CUDA_TRY(cudaMemsetAsync(D.uB, 0, sizeof(double) * std::max(D.n_iface, 1), ws));
+        BDDC_CUDA_TRY(cudaMemsetAsync(D.rcv, 0, sizeof(double) * ncp, ws));
         W.lv.push_back(D);
     }
     W.x = A.alloc_n<double>(n); W.r = A.alloc_n<double>(n); W.z = A.alloc_n<double>(n);
     W.p0 = A.alloc_n<double>(n); W.p1 = A.alloc_n<double>(n);
     W.q = A.alloc_n<double>(n); W.tmp = A.alloc_n<double>(n);
-    BDDC_CUDA_TRY(cudaMemset(W.p0, 0, sizeof(double) * n));
-    BDDC_CUDA_TRY(cudaMemset(W.p1, 0, sizeof(double) * n));
+    BDDC_CUDA_TRY(cudaMemsetAsync(W.p0, 0, sizeof(double) * n, ws));
+    BDDC_CUDA_TRY(cudaMemsetAsync(W.p1, 0, sizeof(double) * n, ws));
     W.bbuf = A.alloc_n<double>(n);
+    W.top_s = A.alloc_n<double>((size_t)2 * std::max(C->n_top, 1));
     W.part = A.alloc_n<double>(std::max<int64_t>(4096, (int64_t)n / 1024 + 1024));   // block partials
     W.rzpart = A.alloc_n<double>(std::max(4096, W.lv.empty() ? 1 : W.lv[0].nsub));
     W.counter = A.alloc_n<unsigned>(4);
     W.rzcounter = A.alloc_n<unsigned>(4);
-    BDDC_CUDA_TRY(cudaMemset(W.counter, 0, 4 * sizeof(unsigned)));
-    BDDC_CUDA_TRY(cudaMemset(W.rzcounter, 0, 4 * sizeof(unsigned)));
+    BDDC_CUDA_TRY(cudaMemsetAsync(W.counter, 0, 4 * sizeof(unsigned), ws));
+    BDDC_CUDA_TRY(cudaMemsetAsync(W.rzcounter, 0, 4 * sizeof(unsigned), ws));
     W.sc = A.alloc_n<PcgScalars>(1);
-    BDDC_CUDA_TRY(cudaMemset(W.sc, 0, sizeof(PcgScalars)));
+    BDDC_CUDA_TRY(cudaMemsetAsync(W.sc, 0, sizeof(PcgScalars), ws));
     W.maxit_cap = maxit_cap;
     W.alphas = A.alloc_n<double>(maxit_cap + 1);
     W.betas = A.alloc_n<double>(maxit_cap + 1);
     W.lout = A.alloc_n<double>(4);
     W.err = A.alloc_n<int>(1);
-    BDDC_CUDA_TRY(cudaMemset(W.err, 0, sizeof(int)));
+    BDDC_CUDA_TRY(cudaMemsetAsync(W.err, 0, sizeof(int), ws));
     for (auto &D : W.lv) D.err = W.err;
     BDDC_CUDA_TRY(cudaHostAlloc((void **)&W.hsc, sizeof(PcgScalars), cudaHostAllocDefault));
     BDDC_CUDA_TRY(cudaHostAlloc((void **)&W.hout, 8 * sizeof(double), cudaHostAllocDefault));
-    BDDC_CUDA_TRY(cudaStreamCreateWithPriority(&W.stream, cudaStreamNonBlocking, prio));
     BDDC_CUDA_TRY(cudaEventCreateWithFlags(&W.ev, cudaEventDisableTiming));
+    BDDC_CUDA_TRY(cudaStreamSynchronize(ws));
 }
 
 void apply_rec(bddc_ctx *C, Workspace &W, int l, int prec, const double *r, double *z,
@@ -825,7 +838,7 @@ void apply_rec(bddc_ctx *C, Workspace &W, int l, int prec, const double *r, doub
     const DevLevel &D = W.lv[l];
     apply_level_pre(D, prec, r, skip, st);
     if (l + 1 == (int)W.lv.size())
-        top_solve_1(C, D.rcv, D.ucv, skip, st);
+        top_solve_1(C, D.rcv, D.ucv, skip, W.top_s, W.err, st);
     else
         apply_rec(C, W, l + 1, prec, D.rcv, D.ucv, skip, st);
     apply_level_post(D, prec, r, z, skip, st, nullptr, rz);
@@ -1001,14 +1014,15 @@ ReducedWs &reduced_ws(bddc_ctx *C, Workspace &W) {
     R->p = A.alloc_n<double>(ng); R->q = A.alloc_n<double>(ng);
     R->rf = A.alloc_n<double>(n); R->ut = A.alloc_n<double>(n);
     R->qf = A.alloc_n<double>(n); R->zero = A.alloc_n<double>(n);
-    BDDC_CUDA_TRY(cudaMemset(R->rf, 0, sizeof(double) * n));
-    BDDC_CUDA_TRY(cudaMemset(R->zero, 0, sizeof(double) * n));
+    BDDC_CUDA_TRY(cudaMemsetAsync(R->rf, 0, sizeof(double) * n, W.stream));
+    BDDC_CUDA_TRY(cudaMemsetAsync(R->zero, 0, sizeof(double) * n, W.stream));
     R->part = A.alloc_n<double>(red_blocks() + 8);
     R->counter = A.alloc_n<unsigned>(4);
-    BDDC_CUDA_TRY(cudaMemset(R->counter, 0, 4 * sizeof(unsigned)));
+    BDDC_CUDA_TRY(cudaMemsetAsync(R->counter, 0, 4 * sizeof(unsigned), W.stream));
     R->sc = A.alloc_n<RedScalars>(1);
-    BDDC_CUDA_TRY(cudaMemset(R->sc, 0, sizeof(RedScalars)));
+    BDDC_CUDA_TRY(cudaMemsetAsync(R->sc, 0, sizeof(RedScalars), W.stream));
     BDDC_CUDA_TRY(cudaHostAlloc((void **)&R->hsc, sizeof(RedScalars), cudaHostAllocDefault));
+    BDDC_CUDA_TRY(cudaStreamSynchronize(W.stream));   // the buffers are zero for any stream
     W.red = std::move(R);
     return *W.red;
 }
@@ -1021,7 +1035,7 @@ void reduced_precondition(bddc_ctx *C, Workspace &W, ReducedWs &R, int prec, cud
     launch_red_scatter(D.n_iface, D.ifaceDof, R.r, R.rf, skip, st);
     apply_level_neumann(D, prec, R.rf, skip, st);                            // (6)-(8)
     if (W.lv.size() == 1)
-        top_solve_1(C, D.rcv, D.ucv, skip, st);
+        top_solve_1(C, D.rcv, D.ucv, skip, W.top_s, W.err, st);
     else
         apply_rec(C, W, 1, prec, D.rcv, D.ucv, skip, st);                   // level 2 onwards
     apply_level_average(D, prec, skip, st);                                  // (9)
@@ -1154,13 +1168,14 @@ bool batch_ok(bddc_ctx *C, Workspace &W, int prec) {
 
 // Mean time of three top-level solves of K right-hand sides in the given
 // form, after one untimed (ms).
-double time_top_b(const bddc_ctx *C, int variant, const double *r, double *u, int K, int *err, cudaStream_t st) {
+double time_top_b(const bddc_ctx *C, int variant, const double *r, double *u, int K, int *err, double *scratch,
+                  cudaStream_t st) {
     cudaEvent_t e0, e1;
     BDDC_CUDA_TRY(cudaEventCreate(&e0));
     BDDC_CUDA_TRY(cudaEventCreate(&e1));
-    top_solve_b(C, variant, r, u, K, nullptr, err, st);
+    top_solve_b(C, variant, r, u, K, nullptr, err, scratch, st);
     BDDC_CUDA_TRY(cudaEventRecord(e0, st));
-    for (int i = 0; i < 3; ++i) top_solve_b(C, variant, r, u, K, nullptr, err, st);
+    for (int i = 0; i < 3; ++i) top_solve_b(C, variant, r, u, K, nullptr, err, scratch, st);
     BDDC_CUDA_TRY(cudaEventRecord(e1, st));
     BDDC_CUDA_TRY(cudaEventSynchronize(e1));
     float ms = 0.0f;
@@ -1188,9 +1203,9 @@ BatchWs &batch_ws(bddc_ctx *C, Workspace &W) {
         B.w = A.alloc_n<double>(std::max<int64_t>(sg, 1) * KB);
         B.rcv = A.alloc_n<double>(ncp * KB);
         B.ucv = A.alloc_n<double>(ncp * KB);
-        BDDC_CUDA_TRY(cudaMemset(B.rB, 0, sizeof(double) * ni * KB));
-        BDDC_CUDA_TRY(cudaMemset(B.uB, 0, sizeof(double) * ni * KB));
-        BDDC_CUDA_TRY(cudaMemset(B.rcv, 0, sizeof(double) * ncp * KB));
+        BDDC_CUDA_TRY(cudaMemsetAsync(B.rB, 0, sizeof(double) * ni * KB, W.stream));
+        BDDC_CUDA_TRY(cudaMemsetAsync(B.uB, 0, sizeof(double) * ni * KB, W.stream));
+        BDDC_CUDA_TRY(cudaMemsetAsync(B.rcv, 0, sizeof(double) * ncp * KB, W.stream));
         if (batch_streams(D)) {
             B.ys = A.alloc_n<double>(std::max<int64_t>(D.n_y, 1) * KB);
             batch_prepare_level(D);
@@ -1201,16 +1216,17 @@ BatchWs &batch_ws(bddc_ctx *C, Workspace &W) {
     bw->z = A.alloc_n<double>(n * KB); bw->p = A.alloc_n<double>(n * KB);
     bw->q = A.alloc_n<double>(n * KB); bw->tmp = A.alloc_n<double>(n * KB);
     bw->p1 = A.alloc_n<double>(n * KB);
-    BDDC_CUDA_TRY(cudaMemset(bw->p1, 0, sizeof(double) * n * KB));
+    BDDC_CUDA_TRY(cudaMemsetAsync(bw->p1, 0, sizeof(double) * n * KB, W.stream));
     bw->bcol = A.alloc_n<double>(n * KB); bw->xcol = A.alloc_n<double>(n * KB);
     bw->part = A.alloc_n<double>((int64_t)std::max(1216, launch_b_dir_spmv_blocks(C->nx)) * KB + 64);
     bw->counter = A.alloc_n<unsigned>(4);
-    BDDC_CUDA_TRY(cudaMemset(bw->counter, 0, 4 * sizeof(unsigned)));
+    BDDC_CUDA_TRY(cudaMemsetAsync(bw->counter, 0, 4 * sizeof(unsigned), W.stream));
     bw->rzpart = A.alloc_n<double>((int64_t)std::max(W.lv.empty() ? 1 : W.lv[0].nsub, 1) * KB);
     bw->rzcounter = A.alloc_n<unsigned>(4);
-    BDDC_CUDA_TRY(cudaMemset(bw->rzcounter, 0, 4 * sizeof(unsigned)));
+    bw->top_s = A.alloc_n<double>((size_t)2 * std::max(C->n_top, 1) * KB);
+    BDDC_CUDA_TRY(cudaMemsetAsync(bw->rzcounter, 0, 4 * sizeof(unsigned), W.stream));
     bw->sc = A.alloc_n<BatchScalars>(1);
-    BDDC_CUDA_TRY(cudaMemset(bw->sc, 0, sizeof(BatchScalars)));
+    BDDC_CUDA_TRY(cudaMemsetAsync(bw->sc, 0, sizeof(BatchScalars), W.stream));
     bw->alphas = A.alloc_n<double>((int64_t)(W.maxit_cap + 1) * KB);
     bw->betas = A.alloc_n<double>((int64_t)(W.maxit_cap + 1) * KB);
     bw->nrm = A.alloc_n<double>(KB);
@@ -1235,13 +1251,13 @@ BatchWs &batch_ws(bddc_ctx *C, Workspace &W) {
             C->gemm_v = C->Ainv ? gemm_tune(C->n_top, C->ld_top, C->Ainv, top.rcv, top.ucv, KB, W.err, st) : -1;
             if (C->Ainv && C->band) {
                 // the block-tridiagonal factor against the best dense product
-                const double t_dense = time_top_b(C, C->gemm_v, top.rcv, top.ucv, KB, W.err, st);
-                const double t_band = time_top_b(C, -1, top.rcv, top.ucv, KB, W.err, st);
-                if (const char *e = std::getenv("BDDC_TOP_FORM")) {
-                    if (e[0] == 'b') C->gemm_v = -1;
-                } else if (t_band < t_dense) {
-                    C->gemm_v = -1;
-                }
+                const double t_dense = time_top_b(C, C->gemm_v, top.rcv, top.ucv, KB, W.err, bw->top_s, st);
+                const double t_band = time_top_b(C, -1, top.rcv, top.ucv, KB, W.err, bw->top_s, st);
+                const char *e = std::getenv("BDDC_TOP_FORM");
+                if (e && e[0] == 'b') C->gemm_v = -1;                   // "band"
+                else if (!(e && e[0] == 'd') && t_band < t_dense) C->gemm_v = -1;   // not "dense"
+                C->top_ms[0] = t_dense;
+                C->top_ms[1] = t_band;
             }
             BDDC_CUDA_TRY(cudaStreamSynchronize(st));
             BDDC_CUDA_TRY(cudaGetLastError());
@@ -1254,6 +1270,7 @@ BatchWs &batch_ws(bddc_ctx *C, Workspace &W) {
         bw->tile_v = C->tile_v;
         bw->gemm_v = C->gemm_v;
     }
+    BDDC_CUDA_TRY(cudaStreamSynchronize(W.stream));   // the buffers are zero for any stream
     W.bw = std::move(bw);
     return *W.bw;
 }
@@ -1264,7 +1281,7 @@ void apply_b_rec(bddc_ctx *C, Workspace &W, BatchWs &BW, int l, int prec, const 
     const BatchLevel &B = BW.lv[l];
     apply_level_pre_b(D, B, prec, r, skip, st);
     if (l + 1 == (int)W.lv.size())
-        top_solve_b(C, BW.gemm_v, B.rcv, B.ucv, B.K, skip, W.err, st);
+        top_solve_b(C, BW.gemm_v, B.rcv, B.ucv, B.K, skip, W.err, BW.top_s, st);
     else
         apply_b_rec(C, W, BW, l + 1, prec, B.rcv, B.ucv, skip, st);
     apply_level_post_b(D, B, prec, r, z, skip, st, nullptr, rz);
@@ -1635,9 +1652,11 @@ int bddc_setup(const bddc_mesh *mesh, const double *k_elem, const bddc_decomp *d
                 launch_identity(nt, I, st);
                 C->Ainv = C->arena.alloc_n<double>((size_t)nt * C->ld_top);
                 BDDC_CUDA_TRY(cudaMemsetAsync(C->Ainv, 0, sizeof(double) * (size_t)nt * C->ld_top, st));
+                double *scr = tmp.alloc_n<double>((size_t)2 * nt * kTopInverseCols);
                 for (int j0 = 0; j0 < nt; j0 += kTopInverseCols)
                     launch_top_band(*C->band, I + j0, nt, C->Ainv + j0, C->ld_top, std::min(kTopInverseCols, nt - j0),
-                                    nullptr, st);
+                                    nullptr, scr, err, st);
+                check_err(err, st, "top-level inverse from the factor");
             } else if (!band) {
                 // the factor does not fit the apply kernel: dense Cholesky
                 double *Atop = tmp.alloc_n<double>((size_t)nt * nt);
@@ -2083,7 +2102,7 @@ int bddc_profile_apply(bddc_ctx *ctx, const double *r_dev, int reps, double *ms_
                 if (l + 1 < nl) rin[l + 1] = W.lv[l].rcv;
             }
             BDDC_CUDA_TRY(cudaEventRecord(top[0], st));
-            top_solve_1(ctx, W.lv[nl - 1].rcv, W.lv[nl - 1].ucv, nullptr, st);
+            top_solve_1(ctx, W.lv[nl - 1].rcv, W.lv[nl - 1].ucv, nullptr, W.top_s, W.err, st);
             BDDC_CUDA_TRY(cudaEventRecord(top[1], st));
             for (int l = nl - 1; l >= 0; --l)
                 apply_level_post(W.lv[l], ctx->prec, rin[l], l == 0 ? z : W.lv[l - 1].ucv, nullptr, st, up[l]);
@@ -2139,7 +2158,7 @@ int bddc_profile_apply_batch(bddc_ctx *ctx, const double *r_dev, int nrhs, int64
                 if (l + 1 < nl) rin[l + 1] = BW.lv[l].rcv;
             }
             BDDC_CUDA_TRY(cudaEventRecord(top[0], st));
-            top_solve_b(ctx, BW.gemm_v, BW.lv[nl - 1].rcv, BW.lv[nl - 1].ucv, K, nullptr, W.err, st);
+            top_solve_b(ctx, BW.gemm_v, BW.lv[nl - 1].rcv, BW.lv[nl - 1].ucv, K, nullptr, W.err, BW.top_s, st);
             BDDC_CUDA_TRY(cudaEventRecord(top[1], st));
             for (int l = nl - 1; l >= 0; --l)
                 apply_level_post_b(W.lv[l], BW.lv[l], ctx->prec, rin[l], l == 0 ? BW.z : BW.lv[l - 1].ucv,
@@ -2213,6 +2232,9 @@ int bddc_apply_noalloc(bddc_ctx *ctx, const double *r_dev, double *z_dev, void *
             sz[l][4] = up(std::max(std::max(D.nc, 1), ctx->ld_top));
             for (int k = 0; k < 5; ++k) need += sz[l][k];
         }
+        // the top-level factor's intermediate vectors (no dense inverse)
+        const size_t ntop_s = ctx->Ainv ? 0 : up((size_t)2 * std::max(ctx->n_top, 1));
+        need += ntop_s;
         if (need > kNoallocDoubles)
             throw Error(BDDC_E_ARG, "apply scratch of " + std::to_string(need * sizeof(double)) +
                                         " bytes exceeds the static scratch of " +
@@ -2230,6 +2252,7 @@ int bddc_apply_noalloc(bddc_ctx *ctx, const double *r_dev, double *z_dev, void *
             lv[l].ucv = base + off; off += sz[l][4];
             lv[l].err = errw;
         }
+        double *top_s = ntop_s ? base + off : nullptr;
         cudaStream_t st = (cudaStream_t)stream;
         const int prec = ctx->prec;
         // The array keeps whatever the last call (of any context) left in it.
@@ -2247,7 +2270,7 @@ int bddc_apply_noalloc(bddc_ctx *ctx, const double *r_dev, double *z_dev, void *
             apply_level_pre(lv[l], prec, rin[l], nullptr, st);
             if (l + 1 < nl) rin[l + 1] = lv[l].rcv;
         }
-        top_solve_1(ctx, lv[nl - 1].rcv, lv[nl - 1].ucv, nullptr, st);
+        top_solve_1(ctx, lv[nl - 1].rcv, lv[nl - 1].ucv, nullptr, top_s, errw, st);
         for (int l = nl - 1; l >= 0; --l)
             apply_level_post(lv[l], prec, rin[l], l == 0 ? z_dev : lv[l - 1].ucv, nullptr, st);
         // whether a bounded wait gave up, for bddc_query once the stream is done

@@ -531,7 +531,7 @@ struct TopOrder {
 };
 TopOrder order_top(int n, const std::vector<std::vector<int>> &rc, int bmin);
 
-// Shared memory of one CTA of the apply (y and x of its right-hand sides).
+// Shared memory of one CTA of a recurrence (the vector of its right-hand sides).
 constexpr size_t kTopSmemMax = 200 * 1024;
 // CTAs of a cluster of the apply (portable cluster size).
 constexpr int kTopCluster = 8;
@@ -541,21 +541,38 @@ constexpr int kTopCluster = 8;
 // (b_k x b_k+1, offG[k]).
 struct TopBand {
     int n = 0, nb = 0, bmax = 0;
-    int *perm = nullptr, *boff = nullptr;
+    int *perm = nullptr, *blk = nullptr, *boff = nullptr;   // blk: block of each position
     int64_t *offL = nullptr, *offF = nullptr, *offG = nullptr;
     double *Linv = nullptr, *LinvT = nullptr, *F = nullptr, *G = nullptr;
     std::vector<int> hboff;
     size_t bytes = 0;
 };
 struct TopBandArgs {
-    int n, nb, K;
+    int n, nb, K, bmax;
     int64_t ldx, ldy;
-    const int *perm, *boff;
+    const int *perm, *blk, *boff;
     const int64_t *offL, *offF, *offG;
     const double *Linv, *LinvT, *F, *G;
     const double *X;
     double *Y;
     const int *skip;
+    int *err;          // set if a bounded wait gave up
+};
+// Shared memory of a CTA of a recurrence for R right-hand sides: the vector
+// [n][R], two stages of its rows of a block's matrix (ceil(bmax / C) rows of
+// at most bmax entries, 16 bytes of alignment slack), the block tables and
+// two mbarriers.
+struct ChainSmem {
+    size_t vs, stage, tab, total;
+    __host__ __device__ static ChainSmem of(int n, int nb, int bmax, int R) {
+        ChainSmem m;
+        const size_t rpc = (size_t)(bmax + kTopCluster - 1) / kTopCluster;
+        m.vs = ((size_t)n * R * sizeof(double) + 15) & ~size_t(15);
+        m.stage = (rpc * (size_t)bmax * sizeof(double) + 16 + 15) & ~size_t(15);
+        m.tab = ((size_t)(nb + 1) * sizeof(int) + 15) & ~size_t(15);
+        m.total = m.vs + 2 * m.stage + m.tab + (((size_t)nb * sizeof(int64_t) + 15) & ~size_t(15)) + 16;
+        return m;
+    }
 };
 // Assemble A_L from the top-level substructures' coarse matrices (device ac
 // at offAc, coarse ids rc) into blocks and factor it on the GPU (FP64); the
@@ -564,11 +581,12 @@ struct TopBandArgs {
 bool build_top_band(int n, const std::vector<std::vector<int>> &rc, const std::vector<int64_t> &offAc,
                     const double *ac, int bmin, TopBand &T, DevArena &keep, DevArena &tmp, int *err,
                     cudaStream_t st);
-// Y = A_L^-1 X for K right-hand sides (X, Y row i at i * ldx / i * ldy, K
-// contiguous); nothing when *skip != 0.
+// Y = A_L^-1 X for K <= 32 right-hand sides (X, Y row i at i * ldx / i * ldy,
+// K contiguous); nothing when *skip != 0.  scratch: 2 n K doubles.  Four
+// launches: g, the forward recurrence, h, the backward recurrence.
 void launch_top_band(const TopBand &T, const double *X, int64_t ldx, double *Y, int64_t ldy, int K,
-                     const int *skip, cudaStream_t s);
-int top_band_cols(int n, int K);   // right-hand sides per cluster
+                     const int *skip, double *scratch, int *err, cudaStream_t s);
+int top_band_cols(const TopBand &T, int K);   // right-hand sides per cluster
 void launch_identity(int n, double *I, cudaStream_t s);   // ones on the diagonal of a zeroed n x n
 void prepare_top_kernels();
 

@@ -18,6 +18,7 @@
 // multiply-adds per right-hand side for blocks of b DOFs, against n^2 for a
 // product with the dense inverse).
 #include "internal.h"
+#include "device_util.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -235,8 +236,9 @@ bool build_top_band(int n, const std::vector<std::vector<int>> &rc, const std::v
     const int nb = (int)O.boff.size() - 1;
     int bmax = 0;
     for (int k = 0; k < nb; ++k) bmax = std::max(bmax, O.boff[k + 1] - O.boff[k]);
-    // the apply kernel holds y and x of a right-hand side in shared memory
-    if ((size_t)2 * n * sizeof(double) > kTopSmemMax) return false;
+    // a recurrence holds the vector of a right-hand side, two stages of its
+    // matrix rows and the block tables in shared memory
+    if (ChainSmem::of(n, nb, bmax, 1).total > kTopSmemMax) return false;
     std::vector<int> pos(n), blk(n);
     for (int p = 0; p < n; ++p) pos[O.perm[p]] = p;
     for (int k = 0; k < nb; ++k)
@@ -311,22 +313,25 @@ bool build_top_band(int n, const std::vector<std::vector<int>> &rc, const std::v
     T.bmax = bmax;
     T.hboff = O.boff;
     T.perm = keep.upload(O.perm, st);
+    T.blk = keep.upload(blk, st);
     T.boff = keep.upload(O.boff, st);
     T.offL = keep.upload(offD, st);
     T.offF = keep.upload(offF, st);
     T.offG = keep.upload(offG, st);
-    T.bytes = sizeof(double) * (size_t)(2 * sD + sF + sG) + sizeof(int) * (size_t)(n + nb + 1) +
+    T.bytes = sizeof(double) * (size_t)(2 * sD + sF + sG) + sizeof(int) * (size_t)(2 * n + nb + 1) +
               sizeof(int64_t) * (size_t)(3 * nb);
     return true;
 }
 
 // ---------------------------------------------------------------------------
-// the apply: one cluster of kTopCluster CTAs per R right-hand sides
+// the apply: g and h by a warp per row over the whole GPU, the two
+// recurrences by one cluster of kTopCluster CTAs per R right-hand sides
 // ---------------------------------------------------------------------------
 namespace {
 
-constexpr int kTopWarps = 4;
+constexpr int kTopWarps = 8;
 constexpr int kTopThreads = 32 * kTopWarps;
+constexpr int kRowLanes = 8, kRowsPerWarp = 32 / kRowLanes;   // a recurrence's rows
 
 __device__ __forceinline__ unsigned cluster_rank() {
     unsigned r;
@@ -348,129 +353,202 @@ __device__ __forceinline__ void st_all(double *local, double v) {
     }
 }
 
-template <int R> __device__ __forceinline__ void warp_sum(double (&v)[R]) {
-#pragma unroll
-    for (int r = 0; r < R; ++r)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v[r] += __shfl_xor_sync(0xffffffffu, v[r], o);
-}
-
-// Rows of block k handled by warp gw of the cluster: i = gw, gw + CW, ...
-// ys, xs: [n][R] in block order, the same in every CTA of the cluster.
-template <int R>
-__global__ void __launch_bounds__(kTopThreads) k_top_band(TopBandArgs a) {
-    if (a.skip && *a.skip) return;          // the same for every CTA of the cluster
-    extern __shared__ double sm[];
-    double *ys = sm, *xs = sm + (size_t)a.n * R;
+// One row per warp, all blocks at once: out[p][c] = sum_j M_k[i][j] in[..][c]
+// for the position p = b0 + i of block k.  LOWER: g = Linv_k r_k (j <= i, the
+// input gathered through perm from rows of stride ldin); else h = Linv_k^T
+// y_k (j >= i, rows of LinvT; input in block order).  out: block order,
+// stride K.  For K > 16 a lane takes one column and the warp walks j: the
+// row's entries (and, for LOWER, their positions' DOFs) are loaded 128 at a
+// time, coalesced, and broadcast by shuffles, so the loads of the input rows
+// are independent of one another.  For K <= 16 the lanes take the columns
+// c = lane mod Kp (Kp: the power of two >= K) and every (32 / Kp)-th j.
+template <bool LOWER>
+__global__ void __launch_bounds__(256) k_top_rows(TopBandArgs a, const double *in, int64_t ldin, double *out) {
+    if (a.skip && *a.skip) return;
+    const int p = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (p >= a.n) return;
     const int lane = threadIdx.x & 31;
-    const int CW = kTopCluster * kTopWarps;
-    const int gw = (int)cluster_rank() * kTopWarps + (threadIdx.x >> 5);
-    const int c0 = (blockIdx.x / kTopCluster) * R;
-    bool live[R];
+    const int k = a.blk[p], b0 = a.boff[k], bk = a.boff[k + 1] - b0, i = p - b0;
+    const double *row = (LOWER ? a.Linv : a.LinvT) + a.offL[k] + (int64_t)i * bk;
+    const int j0 = LOWER ? 0 : i, j1 = LOWER ? i + 1 : bk;
+    double acc = 0.0;
+    if (a.K > 16) {
+        const bool live = lane < a.K;
+        for (int jc = j0; jc < j1; jc += 128) {
+            double mreg[4];
+            int preg[4];
 #pragma unroll
-    for (int r = 0; r < R; ++r) live[r] = c0 + r < a.K;
-    cluster_sync();                         // every CTA runs before shared memory is written remotely
-    // g_k = Linv_k r_k for all blocks
-    for (int k = 0; k < a.nb; ++k) {
-        const int b0 = a.boff[k], bk = a.boff[k + 1] - b0;
-        const double *Lk = a.Linv + a.offL[k];
-        for (int i = gw; i < bk; i += CW) {
-            double acc[R] = {};
-            for (int j = lane; j <= i; j += 32) {
-                const double l = Lk[(int64_t)i * bk + j];
-                const double *x = a.X + (int64_t)a.perm[b0 + j] * a.ldx + c0;
-#pragma unroll
-                for (int r = 0; r < R; ++r)
-                    if (live[r]) acc[r] += l * x[r];
+            for (int t = 0; t < 4; ++t) {
+                const int j = jc + 32 * t + lane;
+                mreg[t] = j < j1 ? row[j] : 0.0;
+                preg[t] = j < j1 ? (LOWER ? a.perm[b0 + j] : b0 + j) : 0;
             }
-            warp_sum<R>(acc);
-            if (lane < R) {
-                double v = 0.0;
 #pragma unroll
-                for (int r = 0; r < R; ++r)
-                    if (lane == r) v = acc[r];
-                st_all(ys + (size_t)(b0 + i) * R + lane, v);
-            }
-        }
-    }
-    cluster_sync();
-    // y_k = g_k - F_k y_k-1
-    for (int k = 1; k < a.nb; ++k) {
-        const int b0 = a.boff[k], bk = a.boff[k + 1] - b0, bp0 = a.boff[k - 1], bp = b0 - bp0;
-        const double *Fk = a.F + a.offF[k];
-        for (int i = gw; i < bk; i += CW) {
-            double acc[R] = {};
-            for (int j = lane; j < bp; j += 32) {
-                const double f = Fk[(int64_t)i * bp + j];
+            for (int t = 0; t < 4; ++t) {
+                const int cnt = min(32, j1 - jc - 32 * t);
+                if (cnt <= 0) break;
+                // eight entries at a time: the shuffles first, then eight
+                // independent loads, then the multiply-adds
+                for (int q0 = 0; q0 < cnt; q0 += 8) {
+                    double mm[8], v[8];
 #pragma unroll
-                for (int r = 0; r < R; ++r) acc[r] += f * ys[(size_t)(bp0 + j) * R + r];
-            }
-            warp_sum<R>(acc);
-            if (lane < R) {
-                double v = 0.0;
+                    for (int u = 0; u < 8; ++u) {
+                        const int q = min(q0 + u, 31);
+                        mm[u] = __shfl_sync(0xffffffffu, mreg[t], q);
+                        const int pr = __shfl_sync(0xffffffffu, preg[t], q);
+                        v[u] = (live && q0 + u < cnt) ? in[(int64_t)pr * ldin + lane] : 0.0;
+                    }
 #pragma unroll
-                for (int r = 0; r < R; ++r)
-                    if (lane == r) v = acc[r];
-                double *dst = ys + (size_t)(b0 + i) * R + lane;
-                st_all(dst, *dst - v);
+                    for (int u = 0; u < 8; ++u) acc = fma(mm[u], v[u], acc);
+                }
             }
         }
-        cluster_sync();
+        if (live) out[(int64_t)p * a.K + lane] = acc;
+        return;
     }
-    // h_k = Linv_k^T y_k for all blocks
-    for (int k = 0; k < a.nb; ++k) {
-        const int b0 = a.boff[k], bk = a.boff[k + 1] - b0;
-        const double *Lt = a.LinvT + a.offL[k];
-        for (int i = gw; i < bk; i += CW) {
-            double acc[R] = {};
-            for (int j = i + lane; j < bk; j += 32) {
-                const double l = Lt[(int64_t)i * bk + j];
-#pragma unroll
-                for (int r = 0; r < R; ++r) acc[r] += l * ys[(size_t)(b0 + j) * R + r];
-            }
-            warp_sum<R>(acc);
-            if (lane < R) {
-                double v = 0.0;
-#pragma unroll
-                for (int r = 0; r < R; ++r)
-                    if (lane == r) v = acc[r];
-                st_all(xs + (size_t)(b0 + i) * R + lane, v);
-            }
+    int kp = 1;
+    while (kp < a.K) kp <<= 1;
+    const int c = lane & (kp - 1), step = 32 / kp;
+    if (c < a.K) {
+        for (int j = j0 + lane / kp; j < j1; j += step) {
+            const double m = row[j];
+            const double v = LOWER ? in[(int64_t)a.perm[b0 + j] * ldin + c] : in[(int64_t)(b0 + j) * ldin + c];
+            acc = fma(m, v, acc);
         }
     }
-    cluster_sync();
-    // x_k = h_k - G_k x_k+1, written out in coarse-DOF order
-    for (int k = a.nb - 1; k >= 0; --k) {
-        const int b0 = a.boff[k], bk = a.boff[k + 1] - b0;
-        const int bn0 = a.boff[k + 1], bn = (k + 1 < a.nb) ? a.boff[k + 2] - bn0 : 0;
-        const double *Gk = a.G + a.offG[k];
-        for (int i = gw; i < bk; i += CW) {
-            double acc[R] = {};
-            for (int j = lane; j < bn; j += 32) {
-                const double g = Gk[(int64_t)i * bn + j];
-#pragma unroll
-                for (int r = 0; r < R; ++r) acc[r] += g * xs[(size_t)(bn0 + j) * R + r];
-            }
-            warp_sum<R>(acc);
-            if (lane < R) {
-                double v = 0.0;
-#pragma unroll
-                for (int r = 0; r < R; ++r)
-                    if (lane == r) v = acc[r];
-                double *dst = xs + (size_t)(b0 + i) * R + lane;
-                const double x = *dst - v;
-                if (k > 0) st_all(dst, x);
-                if (c0 + lane < a.K) a.Y[(int64_t)a.perm[b0 + i] * a.ldy + c0 + lane] = x;
-            }
-        }
-        if (k > 0) cluster_sync();
-    }
-    cluster_sync();                         // no CTA leaves while others may still write to it
+    for (int o = 16; o >= kp; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane < a.K && lane < kp) out[(int64_t)p * a.K + lane] = acc;
 }
 
-template <int R> void launch_r(const TopBandArgs &a, cudaStream_t s) {
+// One recurrence for the R right-hand sides c0 .. c0 + R - 1 of this cluster.
+// FWD: y_0 = g_0, y_k = g_k - F_k y_k-1 (in: g, out: y, both in block
+// order, stride K).  Else: x_nb-1 = h_nb-1, x_k = h_k - G_k x_k+1 (in: h;
+// out: Y through perm).  The cluster's columns of the vector are held, whole,
+// in the shared memory of every CTA of the cluster.  CTA `rank` computes the
+// rows [rank rpc, (rank + 1) rpc) of each block (rpc = ceil(b_k / C)), one
+// row per warp at a time, and stores each result into every CTA of the
+// cluster; then the cluster synchronises.  Its rows of the next block's
+// matrix are one contiguous range, brought into a shared-memory double
+// buffer by a bulk copy two steps ahead.  The loop touches global memory
+// only through those copies (a cluster barrier's acquire would drop what L1
+// holds), and the result goes out after the last step.
+template <int R, bool FWD>
+__global__ void __launch_bounds__(kTopThreads) k_top_chain(TopBandArgs a, const double *in, double *out) {
+    if (a.skip && *a.skip) return;          // the same for every CTA of the cluster
+    extern __shared__ __align__(16) unsigned char sm_top[];
+    const ChainSmem ly = ChainSmem::of(a.n, a.nb, a.bmax, R);
+    double *vs = reinterpret_cast<double *>(sm_top);                                // [n][R]
+    unsigned char *stage0 = sm_top + ly.vs;
+    int *sboff = reinterpret_cast<int *>(sm_top + ly.vs + 2 * ly.stage);            // [nb + 1]
+    int64_t *soff = reinterpret_cast<int64_t *>(sm_top + ly.vs + 2 * ly.stage + ly.tab);   // [nb]
+    unsigned long long *bars = reinterpret_cast<unsigned long long *>(sm_top + ly.total - 16);
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int rank = (int)cluster_rank();
+    const int c0 = (blockIdx.x / kTopCluster) * R;
+    const int nb = a.nb;
+    const double *M = FWD ? a.F : a.G;
+    for (int q = tid; q <= nb; q += kTopThreads) sboff[q] = a.boff[q];
+    for (int q = tid; q < nb; q += kTopThreads) soff[q] = FWD ? a.offF[q] : a.offG[q];
+    for (int q = tid; q < a.n * R; q += kTopThreads) {
+        const int p = q / R, r = q - p * R;
+        vs[q] = c0 + r < a.K ? in[(int64_t)p * a.K + c0 + r] : 0.0;
+    }
+    if (tid == 0) {
+        mbar_init(&bars[0]);
+        mbar_init(&bars[1]);
+    }
+    __syncthreads();
+    // the rows of block k this CTA computes, and the width of their matrix
+    auto my_rows = [&](int k, int &r0, int &r1, int &bo) {
+        const int bk = sboff[k + 1] - sboff[k];
+        const int rpc = (bk + kTopCluster - 1) / kTopCluster;
+        r0 = min(bk, rank * rpc);
+        r1 = min(bk, r0 + rpc);
+        bo = FWD ? sboff[k] - sboff[k - 1] : sboff[k + 2] - sboff[k + 1];
+    };
+    auto issue = [&](int k, int s) {        // thread 0: block k's rows into stage s
+        int r0, r1, bo;
+        my_rows(k, r0, r1, bo);
+        const uintptr_t p0 = reinterpret_cast<uintptr_t>(M + soff[k] + (int64_t)r0 * bo);
+        const size_t bytes = (size_t)(r1 - r0) * bo * sizeof(double);
+        if (bytes == 0) {
+            mbar_expect(&bars[s], 0);
+            return;
+        }
+        const uintptr_t al = p0 & ~uintptr_t(15), ae = (p0 + bytes + 15) & ~uintptr_t(15);
+        mbar_expect(&bars[s], (unsigned)(ae - al));
+        bulk_copy(stage0 + (size_t)s * ly.stage, reinterpret_cast<const void *>(al), (unsigned)(ae - al), &bars[s]);
+    };
+    auto staged = [&](int k, int s) {       // block k's rows of this CTA in stage s
+        int r0, r1, bo;
+        my_rows(k, r0, r1, bo);
+        const uintptr_t p0 = reinterpret_cast<uintptr_t>(M + soff[k] + (int64_t)r0 * bo);
+        return reinterpret_cast<const double *>(stage0 + (size_t)s * ly.stage + (p0 & 15));
+    };
+    // the steps in order, and block nb-1 / 0 whose entries are final as loaded
+    const int first = FWD ? 1 : nb - 2, last = FWD ? nb - 1 : 0, dir = FWD ? 1 : -1;
+    const int nsteps = nb - 1;
+    if (tid == 0)
+        for (int t = 0; t < 2 && t < nsteps; ++t) issue(first + dir * t, t);
+    cluster_sync();                         // every CTA has its copy and runs before remote stores
+    unsigned par = 0;
+    bool ok = true;
+    for (int t = 0; t < nsteps; ++t) {
+        const int k = first + dir * t, s = t & 1;
+        const bool got = mbar_wait(&bars[s], (par >> s) & 1u);
+        par ^= 1u << s;
+        ok = ok && got;
+        if (got) {
+            int r0, r1, bo;
+            my_rows(k, r0, r1, bo);
+            const int b0 = sboff[k], o0 = FWD ? sboff[k - 1] : sboff[k + 1];
+            const double *Mk = staged(k, s);
+            // kRowLanes lanes per row, 32 / kRowLanes rows per warp at once:
+            // the FP64 pipe retires under two lanes per clock per SM here, so
+            // the reduction across lanes (FP64 adds) is kept short
+            const int sub = lane / kRowLanes, l = lane % kRowLanes;
+            for (int i0 = r0 + w * kRowsPerWarp; i0 < r1; i0 += kTopWarps * kRowsPerWarp) {
+                const int i = i0 + sub;
+                double acc[R] = {};
+                if (i < r1) {
+                    const double *mrow = Mk + (int64_t)(i - r0) * bo;
+                    for (int j = l; j < bo; j += kRowLanes) {
+                        const double m = mrow[j];
+#pragma unroll
+                        for (int r = 0; r < R; ++r) acc[r] = fma(m, vs[(size_t)(o0 + j) * R + r], acc[r]);
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+#pragma unroll
+                    for (int o = kRowLanes / 2; o > 0; o >>= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+                if (i < r1 && l < R) {
+                    double v = 0.0;
+#pragma unroll
+                    for (int r = 0; r < R; ++r)
+                        if (l == r) v = acc[r];
+                    double *dst = vs + (size_t)(b0 + i) * R + l;
+                    st_all(dst, *dst - v);
+                }
+            }
+        }
+        cluster_sync();                     // the block is everywhere; stage s is free
+        if (tid == 0 && t + 2 < nsteps) issue(first + dir * (t + 2), s);
+    }
+    (void)last;
+    if (!ok && lane == 0 && a.err) atomicExch(a.err, 1);
+    // the finished vector out: this CTA's share of the positions
+    for (int q = rank * kTopThreads + tid; q < a.n * R; q += kTopCluster * kTopThreads) {
+        const int p = q / R, r = q - p * R;
+        if (c0 + r >= a.K) continue;
+        if (FWD) out[(int64_t)p * a.K + c0 + r] = vs[q];
+        else out[(int64_t)a.perm[p] * a.ldy + c0 + r] = vs[q];
+    }
+}
+
+template <int R, bool FWD> void launch_chain(const TopBandArgs &a, const double *in, double *out, cudaStream_t s) {
     const int clusters = (a.K + R - 1) / R;
-    const size_t smem = sizeof(double) * 2 * (size_t)a.n * R;
+    const size_t smem = ChainSmem::of(a.n, a.nb, a.bmax, R).total;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(clusters * kTopCluster));
     cfg.blockDim = dim3(kTopThreads);
@@ -483,28 +561,39 @@ template <int R> void launch_r(const TopBandArgs &a, cudaStream_t s) {
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    const cudaError_t e = cudaLaunchKernelEx(&cfg, k_top_band<R>, a);
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, k_top_chain<R, FWD>, a, in, out);
     if (e != cudaSuccess)
-        throw Error(BDDC_E_CUDA, std::string("launch of the top-level band solve: ") + cudaGetErrorString(e));
+        throw Error(BDDC_E_CUDA, std::string("launch of the top-level recurrence: ") + cudaGetErrorString(e));
+}
+
+// g in s1 -> y in s2 -> h in s1 -> x in Y
+template <int R> void launch_chains(const TopBandArgs &a, double *s1, double *s2, cudaStream_t s) {
+    launch_chain<R, true>(a, s1, s2, s);
+    k_top_rows<false><<<(a.n + 7) / 8, 256, 0, s>>>(a, s2, a.K, s1);
+    launch_chain<R, false>(a, s1, a.Y, s);
 }
 
 }  // namespace
 
-int top_band_cols(int n, int K) {
-    // right-hand sides per cluster: as many as the shared memory holds, but
-    // spread the batch over at least K / 2 clusters
+int top_band_cols(const TopBand &T, int K) {
+    // right-hand sides per cluster: one (measured on the 512^2 channel
+    // problem, 2253 top-level DOFs in 22 blocks, 32 right-hand sides: 149 us
+    // per solve with one per cluster, 180 with two, 208 with four; a step's
+    // FP64 work per SM is what a recurrence waits on)
+    auto fits = [&](int r) { return ChainSmem::of(T.n, T.nb, T.bmax, r).total <= kTopSmemMax; };
+    (void)K;
     int R = 1;
-    while (R < 4 && R * 2 <= std::max(1, K / 16) && (size_t)2 * n * sizeof(double) * (R * 2) <= kTopSmemMax) R *= 2;
     if (const char *e = std::getenv("BDDC_TOP_COLS")) {
         const int v = std::atoi(e);
-        if ((v == 1 || v == 2 || v == 4) && (size_t)2 * n * sizeof(double) * v <= kTopSmemMax) R = v;
+        if ((v == 1 || v == 2 || v == 4) && fits(v)) R = v;
     }
     return R;
 }
 
 void launch_top_band(const TopBand &T, const double *X, int64_t ldx, double *Y, int64_t ldy, int K, const int *skip,
-                     cudaStream_t s) {
+                     double *scratch, int *err, cudaStream_t s) {
     if (T.nb == 0 || K <= 0) return;
+    if (K > 32) throw Error(BDDC_E_ARG, "top-level solve of more than 32 right-hand sides at once");
     TopBandArgs a;
     a.n = T.n;
     a.nb = T.nb;
@@ -512,6 +601,7 @@ void launch_top_band(const TopBand &T, const double *X, int64_t ldx, double *Y, 
     a.ldx = ldx;
     a.ldy = ldy;
     a.perm = T.perm;
+    a.blk = T.blk;
     a.boff = T.boff;
     a.offL = T.offL;
     a.offF = T.offF;
@@ -523,10 +613,14 @@ void launch_top_band(const TopBand &T, const double *X, int64_t ldx, double *Y, 
     a.X = X;
     a.Y = Y;
     a.skip = skip;
-    switch (top_band_cols(T.n, K)) {
-        case 4: launch_r<4>(a, s); break;
-        case 2: launch_r<2>(a, s); break;
-        default: launch_r<1>(a, s); break;
+    a.err = err;
+    a.bmax = T.bmax;
+    double *s1 = scratch, *s2 = scratch + (size_t)T.n * K;
+    k_top_rows<true><<<(T.n + 7) / 8, 256, 0, s>>>(a, X, ldx, s1);
+    switch (top_band_cols(T, K)) {
+        case 4: launch_chains<4>(a, s1, s2, s); break;
+        case 2: launch_chains<2>(a, s1, s2, s); break;
+        default: launch_chains<1>(a, s1, s2, s); break;
     }
 }
 
@@ -543,9 +637,12 @@ void launch_identity(int n, double *I, cudaStream_t s) {
 
 void prepare_top_kernels() {
     const int big = (int)kTopSmemMax;
-    cudaFuncSetAttribute(k_top_band<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_top_band<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_top_band<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_top_chain<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_top_chain<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_top_chain<4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_top_chain<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_top_chain<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_top_chain<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
 }
 
 }  // namespace bddc
