@@ -237,7 +237,9 @@ def _kernel_bytes(q, n_top, prec_bytes, K=1):
     the coupling A_{Gamma I} per right-hand side; Neumann / Psi products: the
     dense operators once per batch plus the interface vectors per right-hand
     side; top level: the dense FP64 inverse once, the coarse vectors per
-    right-hand side (2 n_top^2 K flops).
+    right-hand side (2 n_top^2 K flops), or, when the batch uses the
+    block-tridiagonal factor (tuned_tile[2] == 0), its blocks once and
+    2 top_fma_per_rhs K flops.
     """
     e = prec_bytes
     sI, sG, sC = q["sum_interior"][0], q["sum_interface"][0], q["sum_coarse_local"][0]
@@ -251,6 +253,10 @@ def _kernel_bytes(q, n_top, prec_bytes, K=1):
         "post": 2 * band * e + coo * (e + 8) + K * (16 * sI + 8 * sG),
     }
     flops = {"top_solve": 2.0 * n_top * n_top * K}
+    if q.get("top_blocks", 0) > 0 and q["tuned_tile"][2] == 0:
+        fma = q["top_fma_per_rhs"]
+        b["top_solve"] = 8 * fma + K * 16 * n_top
+        flops["top_solve"] = 2.0 * fma * K
     return b, flops
 
 
@@ -548,6 +554,7 @@ def gpu_arm(a):
     names = ["pre", "neumann", "top_solve", "average", "post"]
     prof = P.profile_apply_batch(B[:GROUP].contiguous(), reps=20)
     n_top = q["n_dof"][-1]
+    q = dict(q, **{k: v for k, v in P.query(level=None).items() if k in ("tuned_tile", "top_blocks", "top_fma_per_rhs")})
     kb, kf = _kernel_bytes(q, n_top, 4, GROUP)
     kern = {nm: {"ms": float(t), "bytes": kb[nm]} for nm, t in zip(names, prof)}
     iters = inf32[0][0]["iters"]
@@ -561,6 +568,8 @@ def gpu_arm(a):
                                 "rb").read()).hexdigest()[:12]
         traffic = tr["bytes"] if src == tr["src"] else None
     fp64_peak = bddc.fp64_rate(5)
+    top_form = "block-tridiagonal factor" if q.get("top_blocks", 0) > 0 and q["tuned_tile"][2] == 0 \
+        else "dense inverse"
     if dom == "top_solve":
         ach = kf[dom] / (ms_dom * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
@@ -574,6 +583,9 @@ def gpu_arm(a):
                 "traffic": traffic, "kernel": dom, "peak_kind": peak_kind}
     for nm in kern:
         kern[nm]["GBps"] = kern[nm]["bytes"] / (kern[nm]["ms"] * 1e-3) / 1e9
+        kern[nm]["hbm_frac"] = kern[nm]["GBps"] / hbm
+    kern["top_solve"]["fp64_TFLOPs"] = kf["top_solve"] / (kern["top_solve"]["ms"] * 1e-3) / 1e12
+    kern["top_solve"]["fp64_frac"] = kern["top_solve"]["fp64_TFLOPs"] / fp64_peak
     launches = sum(i["kernel_launches"] for inf in inf32 for i in inf)
 
     cpu = None
@@ -628,7 +640,8 @@ def gpu_arm(a):
         "roofline": roof,
         "kernels_fp32_apply_batch": kern,
         "autotuned": {"stencil_tile": P.query(level=None)["tuned_tile"][:2],
-                      "top_product_rows_per_block": P.query(level=None)["tuned_tile"][2]},
+                      "top_product_rows_per_block": P.query(level=None)["tuned_tile"][2],
+                      "top_form": top_form, "top_blocks": q.get("top_blocks", 0)},
         "gpu_launches": launches,
         "cpu_baseline": cpu,
         "clocks": clocks,

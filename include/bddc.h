@@ -160,6 +160,10 @@ typedef struct {
      * for the single right-hand-side apply.  0: dense Cholesky instead (a top
      * level too large for the factor's apply kernel, or none). */
     int32_t top_blocks;
+    /* FP64 multiply-adds per right-hand side of one solve with that factor:
+     * the triangles of Linv_k twice (forward and backward) and the blocks
+     * F_k and G_k (0 without it) */
+    int64_t top_fma_per_rhs;
 } bddc_info;
 
 /*

@@ -76,7 +76,8 @@ class Info(C.Structure):
                 ("block_entries", C.c_int64 * 3), ("coupling_nnz", C.c_int64 * 3),
                 ("neumann_entries", C.c_int64 * 3), ("psi_entries", C.c_int64 * 3),
                 ("n_interface", C.c_int32 * 3), ("tuned_tile", C.c_int32 * 3),
-                ("tc_levels", C.c_int32), ("apply_status", C.c_int32), ("top_blocks", C.c_int32)]
+                ("tc_levels", C.c_int32), ("apply_status", C.c_int32), ("top_blocks", C.c_int32),
+                ("top_fma_per_rhs", C.c_int64)]
 
 
 _lib = None
@@ -403,7 +404,7 @@ class Problem:
                "omega_level": list(info.omega_level)[:info.levels - 1],
                "setup_ms": info.setup_ms, "device_bytes": info.device_bytes,
                "tuned_tile": list(info.tuned_tile), "tc_levels": info.tc_levels,
-               "top_blocks": info.top_blocks,
+               "top_blocks": info.top_blocks, "top_fma_per_rhs": info.top_fma_per_rhs,
                "apply_status": info.apply_status}
         nl = info.levels - 1
         for key in ("sum_interior", "sum_interface", "sum_coarse_local", "band_nnz",

@@ -2043,6 +2043,7 @@ int bddc_query(const bddc_ctx *ctx, bddc_info *info, int level, int32_t *n_selec
             }
             for (int t = 0; t < 3; ++t) info->tuned_tile[t] = ctx->tuned[t];
             info->top_blocks = ctx->band ? ctx->band->nb : 0;
+            info->top_fma_per_rhs = ctx->band ? ctx->band->fma_per_rhs : 0;
             info->apply_status = *ctx->happly ? BDDC_E_TIMEOUT : BDDC_OK;
             info->tc_levels = 0;
             for (size_t l = 0; l < ctx->L.size(); ++l)

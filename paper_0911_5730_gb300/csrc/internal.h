@@ -546,6 +546,7 @@ struct TopBand {
     double *Linv = nullptr, *LinvT = nullptr, *F = nullptr, *G = nullptr;
     std::vector<int> hboff;
     size_t bytes = 0;
+    int64_t fma_per_rhs = 0;   // of one solve: both triangles of every Linv_k, every F_k and G_k
 };
 struct TopBandArgs {
     int n, nb, K, bmax;

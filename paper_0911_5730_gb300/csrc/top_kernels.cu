@@ -311,6 +311,8 @@ bool build_top_band(int n, const std::vector<std::vector<int>> &rc, const std::v
     T.n = n;
     T.nb = nb;
     T.bmax = bmax;
+    T.fma_per_rhs = sF + sG;
+    for (int k = 0; k < nb; ++k) T.fma_per_rhs += bs(k) * (bs(k) + 1);
     T.hboff = O.boff;
     T.perm = keep.upload(O.perm, st);
     T.blk = keep.upload(blk, st);
