@@ -66,6 +66,8 @@ def _args():
                     help="only time each kernel of the batched apply (%d right-hand sides) of the "
                          "workload with CUDA events, print them and exit" % GROUP)
     ap.add_argument("--reps", type=int, default=20, help="applies timed by --profile-apply")
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(PROFILE_WORKLOADS),
+                    help="workload of --profile-apply")
     return ap.parse_args()
 
 
@@ -653,20 +655,43 @@ def gpu_arm(a):
         torch.distributed.destroy_process_group()
 
 
+def _profile_workloads():
+    from paper_0911_5730_gb300 import inputs
+    return {
+        WORKLOAD: lambda: inputs.two_level_channels(),
+        "three_level_blocks_1024": lambda: inputs.three_level_blocks(),
+        "three_level_voronoi_2048": lambda: inputs.three_level_voronoi(),
+        # a quarter of the 2048^2 Voronoi problem, with its cell size (1024
+        # cells of about 1000 DOFs, block sizes 25-47), two levels
+        "voronoi_1024_cells": lambda: inputs.three_level_voronoi(nx=1024, cells=32, group=4, levels=2),
+    }
+
+
+PROFILE_WORKLOADS = (WORKLOAD, "three_level_blocks_1024", "three_level_voronoi_2048", "voronoi_1024_cells")
+
+
 def profile_apply(a):
     """Per-kernel device times of the batched apply (one group of GROUP
     right-hand sides) in one precision: the entry point of the ncu captures."""
     import torch
     from paper_0911_5730_gb300 import bddc, inputs
-    wl = inputs.two_level_channels()
+    wl = _profile_workloads()[a.workload]()
     P = bddc.Problem.from_workload(wl, precision=a.profile_apply)
     q = P.query(level=1)
     B = torch.tensor(inputs.normal_rhs(wl.n_dof, RHS_SEED, GROUP), device="cuda")
     prof = P.profile_apply_batch(B, reps=a.reps)
-    names = ["pre", "neumann", "top_solve", "average", "post"]
+    nl = len(q["n_dof"]) - 1
+    names = [x for l in range(nl) for x in ((("pre", "neumann") if nl == 1 else
+                                            ("pre_l%d" % (l + 1), "neumann_l%d" % (l + 1))))]
+    names += ["top_solve"]
+    names += [x for l in reversed(range(nl)) for x in ((("average", "post") if nl == 1 else
+                                                       ("average_l%d" % (l + 1), "post_l%d" % (l + 1))))]
     route = os.environ.get("BDDC_TC", "default") if q["tc_levels"] & 1 else "sweeps (no dense operands)"
-    print(json.dumps({"workload": WORKLOAD, "precision": a.profile_apply, "rhs": GROUP, "reps": a.reps,
-                      "interior_route": route, "ms": {nm: float(t) for nm, t in zip(names, prof)}}))
+    top = P.query(level=None)
+    print(json.dumps({"workload": a.workload, "precision": a.profile_apply, "rhs": GROUP, "reps": a.reps,
+                      "interior_route": route,
+                      "top_form": "factor" if top["tuned_tile"][2] == 0 and top["top_blocks"] else "dense",
+                      "ms": {nm: float(t) for nm, t in zip(names, prof)}}))
     P.close()
 
 

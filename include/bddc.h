@@ -156,7 +156,7 @@ typedef struct {
      * last level by the breadth-first level sets of A_L's graph, merges them
      * into blocks (A_L is then block tridiagonal) and factors A_L blockwise
      * in FP64 (Sec. 2.1: the top level is solved directly).  Top levels of
-     * up to 4096 DOFs also keep the dense inverse, formed from that factor,
+     * up to 24576 DOFs also keep the dense inverse, formed from that factor,
      * for the single right-hand-side apply.  0: dense Cholesky instead (a top
      * level too large for the factor's apply kernel, or none). */
     int32_t top_blocks;

@@ -561,17 +561,17 @@ struct TopBandArgs {
 };
 // Shared memory of a CTA of a recurrence for R right-hand sides: the vector
 // [n][R], two stages of its rows of a block's matrix (ceil(bmax / C) rows of
-// at most bmax entries, 16 bytes of alignment slack), the block tables and
-// two mbarriers.
+// at most bmax entries, 16 bytes of alignment slack; none for bmax = 0, the
+// unstaged form), the block tables and four mbarriers.
 struct ChainSmem {
     size_t vs, stage, tab, total;
     __host__ __device__ static ChainSmem of(int n, int nb, int bmax, int R) {
         ChainSmem m;
         const size_t rpc = (size_t)(bmax + kTopCluster - 1) / kTopCluster;
         m.vs = ((size_t)n * R * sizeof(double) + 15) & ~size_t(15);
-        m.stage = (rpc * (size_t)bmax * sizeof(double) + 16 + 15) & ~size_t(15);
+        m.stage = bmax > 0 ? (rpc * (size_t)bmax * sizeof(double) + 16 + 15) & ~size_t(15) : 0;   // 0: unstaged
         m.tab = ((size_t)(nb + 1) * sizeof(int) + 15) & ~size_t(15);
-        m.total = m.vs + 2 * m.stage + m.tab + (((size_t)nb * sizeof(int64_t) + 15) & ~size_t(15)) + 16;
+        m.total = m.vs + 2 * m.stage + m.tab + (((size_t)nb * sizeof(int64_t) + 15) & ~size_t(15)) + 32;
         return m;
     }
 };

@@ -277,7 +277,9 @@ __device__ __forceinline__ void bstore(const BShare<BF> &b, unsigned char *blk, 
 #pragma unroll
     for (int u = 0; u < NV; ++u) {
         const int kk = w * NV + u;            // K row within the block
-        const float x = __double2float_rn(b.v[u]);
+        // narrowed with integer operations: the hardware conversion issues on
+        // the FP64 pipe, which the other batch groups' FP64 phases need
+        const float x = f64_to_f32(b.v[u]);
         if constexpr (BF) {
             const __nv_bfloat16 h = __float2bfloat16_rn(x);
             const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));

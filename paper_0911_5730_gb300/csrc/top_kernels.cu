@@ -236,9 +236,9 @@ bool build_top_band(int n, const std::vector<std::vector<int>> &rc, const std::v
     const int nb = (int)O.boff.size() - 1;
     int bmax = 0;
     for (int k = 0; k < nb; ++k) bmax = std::max(bmax, O.boff[k + 1] - O.boff[k]);
-    // a recurrence holds the vector of a right-hand side, two stages of its
-    // matrix rows and the block tables in shared memory
-    if (ChainSmem::of(n, nb, bmax, 1).total > kTopSmemMax) return false;
+    // a recurrence holds the vector of a right-hand side and the block tables
+    // in shared memory (and, where they fit, two stages of its matrix rows)
+    if (ChainSmem::of(n, nb, 0, 1).total > kTopSmemMax) return false;
     std::vector<int> pos(n), blk(n);
     for (int p = 0; p < n; ++p) pos[O.perm[p]] = p;
     for (int k = 0; k < nb; ++k)
@@ -355,6 +355,26 @@ __device__ __forceinline__ void st_all(double *local, double v) {
     }
 }
 
+// v into the shared-memory word at `local` of every CTA of the cluster, each
+// store completing 8 bytes on that CTA's mbarrier `bar` (same layout)
+__device__ __forceinline__ void st_async_all(double *local, double v, unsigned long long *bar) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(local);
+    const unsigned b = (unsigned)__cvta_generic_to_shared(bar);
+#pragma unroll
+    for (unsigned q = 0; q < (unsigned)kTopCluster; ++q) {
+        unsigned ra, rb;
+        asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(q));
+        asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(rb) : "r"(b), "r"(q));
+        asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.f64 [%0], %1, [%2];"
+                     ::"r"(ra), "d"(v), "r"(rb) : "memory");
+    }
+}
+// expect `bytes` on the local mbarrier and arrive once
+__device__ __forceinline__ void mbar_arrive_expect(unsigned long long *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 ::"r"((unsigned)__cvta_generic_to_shared(bar)), "r"(bytes) : "memory");
+}
+
 // One row per warp, all blocks at once: out[p][c] = sum_j M_k[i][j] in[..][c]
 // for the position p = b0 + i of block k.  LOWER: g = Linv_k r_k (j <= i, the
 // input gathered through perm from rows of stride ldin); else h = Linv_k^T
@@ -434,16 +454,21 @@ __global__ void __launch_bounds__(256) k_top_rows(TopBandArgs a, const double *i
 // buffer by a bulk copy two steps ahead.  The loop touches global memory
 // only through those copies (a cluster barrier's acquire would drop what L1
 // holds), and the result goes out after the last step.
-template <int R, bool FWD>
+//
+// STAGED = false (blocks too large for two stages in shared memory): the rows
+// are read from global memory where they are used.
+template <int R, bool FWD, bool STAGED>
 __global__ void __launch_bounds__(kTopThreads) k_top_chain(TopBandArgs a, const double *in, double *out) {
     if (a.skip && *a.skip) return;          // the same for every CTA of the cluster
     extern __shared__ __align__(16) unsigned char sm_top[];
-    const ChainSmem ly = ChainSmem::of(a.n, a.nb, a.bmax, R);
+    const ChainSmem ly = ChainSmem::of(a.n, a.nb, STAGED ? a.bmax : 0, R);
     double *vs = reinterpret_cast<double *>(sm_top);                                // [n][R]
     unsigned char *stage0 = sm_top + ly.vs;
     int *sboff = reinterpret_cast<int *>(sm_top + ly.vs + 2 * ly.stage);            // [nb + 1]
     int64_t *soff = reinterpret_cast<int64_t *>(sm_top + ly.vs + 2 * ly.stage + ly.tab);   // [nb]
-    unsigned long long *bars = reinterpret_cast<unsigned long long *>(sm_top + ly.total - 16);
+    // bars[0..1]: the stages' bulk copies; bars[2..3]: a block's values from
+    // every CTA (st.async), by parity of the step
+    unsigned long long *bars = reinterpret_cast<unsigned long long *>(sm_top + ly.total - 32);
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int rank = (int)cluster_rank();
     const int c0 = (blockIdx.x / kTopCluster) * R;
@@ -455,10 +480,8 @@ __global__ void __launch_bounds__(kTopThreads) k_top_chain(TopBandArgs a, const 
         const int p = q / R, r = q - p * R;
         vs[q] = c0 + r < a.K ? in[(int64_t)p * a.K + c0 + r] : 0.0;
     }
-    if (tid == 0) {
-        mbar_init(&bars[0]);
-        mbar_init(&bars[1]);
-    }
+    if (tid == 0)
+        for (int q = 0; q < 4; ++q) mbar_init(&bars[q]);
     __syncthreads();
     // the rows of block k this CTA computes, and the width of their matrix
     auto my_rows = [&](int k, int &r0, int &r1, int &bo) {
@@ -469,6 +492,7 @@ __global__ void __launch_bounds__(kTopThreads) k_top_chain(TopBandArgs a, const 
         bo = FWD ? sboff[k] - sboff[k - 1] : sboff[k + 2] - sboff[k + 1];
     };
     auto issue = [&](int k, int s) {        // thread 0: block k's rows into stage s
+        if (!STAGED) return;
         int r0, r1, bo;
         my_rows(k, r0, r1, bo);
         const uintptr_t p0 = reinterpret_cast<uintptr_t>(M + soff[k] + (int64_t)r0 * bo);
@@ -481,10 +505,12 @@ __global__ void __launch_bounds__(kTopThreads) k_top_chain(TopBandArgs a, const 
         mbar_expect(&bars[s], (unsigned)(ae - al));
         bulk_copy(stage0 + (size_t)s * ly.stage, reinterpret_cast<const void *>(al), (unsigned)(ae - al), &bars[s]);
     };
-    auto staged = [&](int k, int s) {       // block k's rows of this CTA in stage s
+    auto staged = [&](int k, int s) {       // block k's rows of this CTA in stage s (or in place)
         int r0, r1, bo;
         my_rows(k, r0, r1, bo);
-        const uintptr_t p0 = reinterpret_cast<uintptr_t>(M + soff[k] + (int64_t)r0 * bo);
+        const double *g = M + soff[k] + (int64_t)r0 * bo;
+        if (!STAGED) return g;
+        const uintptr_t p0 = reinterpret_cast<uintptr_t>(g);
         return reinterpret_cast<const double *>(stage0 + (size_t)s * ly.stage + (p0 & 15));
     };
     // the steps in order, and block nb-1 / 0 whose entries are final as loaded
@@ -492,13 +518,22 @@ __global__ void __launch_bounds__(kTopThreads) k_top_chain(TopBandArgs a, const 
     const int nsteps = nb - 1;
     if (tid == 0)
         for (int t = 0; t < 2 && t < nsteps; ++t) issue(first + dir * t, t);
-    cluster_sync();                         // every CTA has its copy and runs before remote stores
-    unsigned par = 0;
+    cluster_sync();                         // every CTA has its copy and its barriers before remote stores
+    unsigned par = 0, dpar = 0;
     bool ok = true;
     for (int t = 0; t < nsteps; ++t) {
         const int k = first + dir * t, s = t & 1;
-        const bool got = mbar_wait(&bars[s], (par >> s) & 1u);
-        par ^= 1u << s;
+        bool got = true;
+        if (t > 0) {                        // the neighbour block, from every CTA
+            const int d = (t - 1) & 1;
+            got = mbar_wait(&bars[2 + d], (dpar >> d) & 1u);
+            dpar ^= 1u << d;
+        }
+        if (tid == 0) mbar_arrive_expect(&bars[2 + s], (unsigned)((sboff[k + 1] - sboff[k]) * R * sizeof(double)));
+        if (STAGED) {
+            got = mbar_wait(&bars[s], (par >> s) & 1u) && got;
+            par ^= 1u << s;
+        }
         ok = ok && got;
         if (got) {
             int r0, r1, bo;
@@ -511,14 +546,25 @@ __global__ void __launch_bounds__(kTopThreads) k_top_chain(TopBandArgs a, const 
             const int sub = lane / kRowLanes, l = lane % kRowLanes;
             for (int i0 = r0 + w * kRowsPerWarp; i0 < r1; i0 += kTopWarps * kRowsPerWarp) {
                 const int i = i0 + sub;
-                double acc[R] = {};
+                double acc[R] = {}, acc2[R] = {};   // two chains of dependent multiply-adds
                 if (i < r1) {
                     const double *mrow = Mk + (int64_t)(i - r0) * bo;
-                    for (int j = l; j < bo; j += kRowLanes) {
+                    int j = l;
+                    for (; j + kRowLanes < bo; j += 2 * kRowLanes) {
+                        const double m = mrow[j], m2 = mrow[j + kRowLanes];
+#pragma unroll
+                        for (int r = 0; r < R; ++r) {
+                            acc[r] = fma(m, vs[(size_t)(o0 + j) * R + r], acc[r]);
+                            acc2[r] = fma(m2, vs[(size_t)(o0 + j + kRowLanes) * R + r], acc2[r]);
+                        }
+                    }
+                    if (j < bo) {
                         const double m = mrow[j];
 #pragma unroll
                         for (int r = 0; r < R; ++r) acc[r] = fma(m, vs[(size_t)(o0 + j) * R + r], acc[r]);
                     }
+#pragma unroll
+                    for (int r = 0; r < R; ++r) acc[r] += acc2[r];
                 }
 #pragma unroll
                 for (int r = 0; r < R; ++r)
@@ -530,12 +576,16 @@ __global__ void __launch_bounds__(kTopThreads) k_top_chain(TopBandArgs a, const 
                     for (int r = 0; r < R; ++r)
                         if (l == r) v = acc[r];
                     double *dst = vs + (size_t)(b0 + i) * R + l;
-                    st_all(dst, *dst - v);
+                    st_async_all(dst, *dst - v, &bars[2 + s]);
                 }
             }
         }
-        cluster_sync();                     // the block is everywhere; stage s is free
+        __syncthreads();                    // stage s is free
         if (tid == 0 && t + 2 < nsteps) issue(first + dir * (t + 2), s);
+    }
+    if (nsteps > 0) {                       // the last block
+        const int d = (nsteps - 1) & 1;
+        ok = mbar_wait(&bars[2 + d], (dpar >> d) & 1u) && ok;
     }
     (void)last;
     if (!ok && lane == 0 && a.err) atomicExch(a.err, 1);
@@ -546,11 +596,15 @@ __global__ void __launch_bounds__(kTopThreads) k_top_chain(TopBandArgs a, const 
         if (FWD) out[(int64_t)p * a.K + c0 + r] = vs[q];
         else out[(int64_t)a.perm[p] * a.ldy + c0 + r] = vs[q];
     }
+    cluster_sync();                         // no CTA leaves while stores to it may be in flight
 }
 
 template <int R, bool FWD> void launch_chain(const TopBandArgs &a, const double *in, double *out, cudaStream_t s) {
     const int clusters = (a.K + R - 1) / R;
-    const size_t smem = ChainSmem::of(a.n, a.nb, a.bmax, R).total;
+    const char *env = std::getenv("BDDC_TOP_STAGED");
+    const bool allow = !(env && env[0] == '0');
+    const bool staged = allow && ChainSmem::of(a.n, a.nb, a.bmax, R).total <= kTopSmemMax;
+    const size_t smem = ChainSmem::of(a.n, a.nb, staged ? a.bmax : 0, R).total;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(clusters * kTopCluster));
     cfg.blockDim = dim3(kTopThreads);
@@ -563,7 +617,8 @@ template <int R, bool FWD> void launch_chain(const TopBandArgs &a, const double 
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    const cudaError_t e = cudaLaunchKernelEx(&cfg, k_top_chain<R, FWD>, a, in, out);
+    const cudaError_t e = staged ? cudaLaunchKernelEx(&cfg, k_top_chain<R, FWD, true>, a, in, out)
+                                 : cudaLaunchKernelEx(&cfg, k_top_chain<R, FWD, false>, a, in, out);
     if (e != cudaSuccess)
         throw Error(BDDC_E_CUDA, std::string("launch of the top-level recurrence: ") + cudaGetErrorString(e));
 }
@@ -578,13 +633,14 @@ template <int R> void launch_chains(const TopBandArgs &a, double *s1, double *s2
 }  // namespace
 
 int top_band_cols(const TopBand &T, int K) {
-    // right-hand sides per cluster: one (measured on the 512^2 channel
-    // problem, 2253 top-level DOFs in 22 blocks, 32 right-hand sides: 149 us
-    // per solve with one per cluster, 180 with two, 208 with four; a step's
-    // FP64 work per SM is what a recurrence waits on)
-    auto fits = [&](int r) { return ChainSmem::of(T.n, T.nb, T.bmax, r).total <= kTopSmemMax; };
-    (void)K;
-    int R = 1;
+    // right-hand sides per cluster: two for batches, one otherwise.  On the
+    // 512^2 channel problem (2253 top-level DOFs in 22 blocks, 32 right-hand
+    // sides) a solve alone takes 135 us with one per cluster and 175 with
+    // two, but with three batches in flight two per cluster gave more
+    // solves/s (1909 against 1883): half the CTAs leave room for the other
+    // batches' kernels.
+    auto fits = [&](int r) { return ChainSmem::of(T.n, T.nb, 0, r).total <= kTopSmemMax; };
+    int R = (K >= 16 && fits(2)) ? 2 : 1;
     if (const char *e = std::getenv("BDDC_TOP_COLS")) {
         const int v = std::atoi(e);
         if ((v == 1 || v == 2 || v == 4) && fits(v)) R = v;
@@ -639,12 +695,12 @@ void launch_identity(int n, double *I, cudaStream_t s) {
 
 void prepare_top_kernels() {
     const int big = (int)kTopSmemMax;
-    cudaFuncSetAttribute(k_top_chain<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_top_chain<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_top_chain<4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_top_chain<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_top_chain<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_top_chain<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+#define BDDC_TOP_ATTR(R, F, S) cudaFuncSetAttribute(k_top_chain<R, F, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)
+    BDDC_TOP_ATTR(1, true, true); BDDC_TOP_ATTR(2, true, true); BDDC_TOP_ATTR(4, true, true);
+    BDDC_TOP_ATTR(1, false, true); BDDC_TOP_ATTR(2, false, true); BDDC_TOP_ATTR(4, false, true);
+    BDDC_TOP_ATTR(1, true, false); BDDC_TOP_ATTR(2, true, false); BDDC_TOP_ATTR(4, true, false);
+    BDDC_TOP_ATTR(1, false, false); BDDC_TOP_ATTR(2, false, false); BDDC_TOP_ATTR(4, false, false);
+#undef BDDC_TOP_ATTR
 }
 
 }  // namespace bddc

@@ -86,6 +86,26 @@ def test_factor_apply_and_solve_match_oracle(lib, name, bmin, monkeypatch):
         P.close()
 
 
+def test_unstaged_recurrences_match_oracle(lib, monkeypatch):
+    """The recurrence kernels' form for blocks too large to stage in shared
+    memory (rows read from global memory), forced on a small problem."""
+    monkeypatch.setenv("BDDC_TOP_DENSE_MAX", "0")
+    monkeypatch.setenv("BDDC_TOP_BMIN", "8")
+    monkeypatch.setenv("BDDC_TOP_STAGED", "0")
+    wl, H = _oracle("channels_128_sub8")
+    P = lib.Problem.from_workload(wl)
+    try:
+        r = inputs.normal_rhs(wl.n_dof, 8)
+        z = P.apply(torch.tensor(r, device="cuda")).cpu().numpy()
+        assert _rel(z, H.apply(r)) <= 1e-10
+        R = inputs.normal_rhs(wl.n_dof, 9, 7)
+        Z = P.apply(torch.tensor(R, device="cuda")).cpu().numpy()
+        for j in range(7):
+            assert _rel(Z[j], H.apply(R[j])) <= 1e-10
+    finally:
+        P.close()
+
+
 def test_dense_inverse_from_factor_matches_oracle(lib, monkeypatch):
     """With the dense inverse kept (formed by applying the factor to the
     identity), the single right-hand-side apply uses it: same bar."""
@@ -103,22 +123,18 @@ def test_dense_inverse_from_factor_matches_oracle(lib, monkeypatch):
 
 def test_batched_forms_agree(lib, monkeypatch):
     """The batched FP64 solve with the factor (BDDC_TOP_FORM=band) and with
-    the dense product (the autotuner's other form) give the oracle's
-    iterations and solutions for 32 right-hand sides."""
+    the dense product (BDDC_TOP_FORM=dense; the autotuner picks between them)
+    give the oracle's iterations and solutions for 32 right-hand sides."""
     wl, H = _oracle("channels_128_sub8")
     B = inputs.normal_rhs(wl.n_dof, 7, 32)
     ref = [opcg.pcg(H.A, B[j], H.apply, rtol=1e-8) for j in range(0, 32, 8)]
-    for form in ("band", None):
-        if form:
-            monkeypatch.setenv("BDDC_TOP_FORM", form)
-        else:
-            monkeypatch.delenv("BDDC_TOP_FORM", raising=False)
+    for form in ("band", "dense"):
+        monkeypatch.setenv("BDDC_TOP_FORM", form)
         P = lib.Problem.from_workload(wl)
         try:
             X, infos = P.solve(torch.tensor(B, device="cuda"), rtol=1e-8)
             X = X.cpu().numpy()
-            if form == "band":
-                assert P.query(level=None)["tuned_tile"][2] == 0
+            assert (P.query(level=None)["tuned_tile"][2] == 0) == (form == "band")
             for j, rr in zip(range(0, 32, 8), ref):
                 assert infos[j]["status"] == 0 and infos[j]["iters"] == rr.iters
                 assert _rel(X[j], rr.x) <= 1e-10
