@@ -45,8 +45,14 @@ RTOL = 1e-8
 # DRAM traffic per launch of the dominant kernel from the ncu capture
 # summarised in profiles/: {kernel: {"bytes", "file", "src"}}, valid only while
 # the sha1 prefix of csrc/<file> equals "src".
-NCU_TRAFFIC = {"top_solve": {"bytes": 41256192, "file": "batch_kernels.cu", "src": "ea43368fcbc1",
-                             "kernel": "k_gemm_b<1, 8>"}}
+NCU_TRAFFIC = {
+    # the block-tridiagonal top solve: k_top_rows (g), k_top_chain (forward),
+    # k_top_rows (h), k_top_chain (backward), two right-hand sides per cluster
+    "top_solve": {"bytes": 8916736, "file": "top_kernels.cu", "src": "7882facf74a4",
+                  "kernel": "k_top_rows + k_top_chain, 4 launches"},
+    "post": {"bytes": 120436224, "file": "batch_kernels.cu", "src": "78a371f18224",
+             "kernel": "k_dir_b<float, float, 16, 1>"},
+}
 
 
 def _args():
@@ -531,7 +537,7 @@ def gpu_arm(a):
     if world == 1 and not a.no_serving_mix:
         from paper_0911_5730_gb300 import serve_mix
         try:
-            mix = serve_mix.run(load=0.8, seconds=3.0, seed=5001)
+            mix = serve_mix.run(load=0.8, seconds=5.0, seed=5001)
         except Exception as ex:       # reported, never silently replaced
             mix = {"error": str(ex)[:300]}
         P.set_precision("fp32")

@@ -164,6 +164,15 @@ typedef struct {
      * the triangles of Linv_k twice (forward and backward) and the blocks
      * F_k and G_k (0 without it) */
     int64_t top_fma_per_rhs;
+    /* the autotuner's choices for the size-bucketed kernels (timed on the
+     * context's operators in its precision when the batch workspace is
+     * first used; 0 before): bit l-1 set: the size buckets of a sweep of
+     * level l's streaming Dirichlet kernel run at once (on forked streams)
+     * rather than one after another; per level, the bytes of N per chunk of
+     * the large-record Neumann kernel (16, 32 or 64 KB; 0: not used or the
+     * default 32 KB) */
+    int32_t tuned_buckets_at_once;
+    int32_t tuned_neu_chunk[3];
 } bddc_info;
 
 /*

@@ -752,14 +752,17 @@ __global__ void __launch_bounds__(kSBMaxT, 1) k_dir_bs(DevLevel L, BatchLevel B,
 // (mod 8) for all right-hand sides (lane k: right-hand side k).
 constexpr int kChunkBytes = 32 * 1024, kNBT = 256;   // chunk of N; threads (8 warps)
 
-template <class T> __host__ __device__ inline int neu_chunk_rows(int nG) {
-    const int rows = kChunkBytes / (int)(sizeof(T) * (nG > 0 ? nG : 1));
+// chunk: bytes of N per chunk (0: kChunkBytes), the autotuner's choice
+template <class T> __host__ __device__ inline int neu_chunk_rows(int nG, int chunk = 0) {
+    const int cb = chunk > 0 ? chunk : kChunkBytes;
+    const int rows = cb / (int)(sizeof(T) * (nG > 0 ? nG : 1));
     return rows < 1 ? 1 : (rows > nG ? (nG > 0 ? nG : 1) : rows);
 }
-template <class T, class ACC> __host__ __device__ inline size_t neu_bg_smem(const DevLevel &L) {
+template <class T, class ACC> __host__ __device__ inline size_t neu_bg_smem(const DevLevel &L, int chunk_bytes = 0) {
     const size_t mg = L.max_nG > 0 ? L.max_nG : 1, mc = L.max_nc > 0 ? L.max_nc : 1;
     const size_t row = sizeof(T) * mg;   // one row of N when a row exceeds the chunk
-    const size_t chunk = al16((row > (size_t)kChunkBytes ? row : (size_t)kChunkBytes) + 16);
+    const size_t cb = chunk_bytes > 0 ? (size_t)chunk_bytes : (size_t)kChunkBytes;
+    const size_t chunk = al16((row > cb ? row : cb) + 16);
     const size_t psi = al16(sizeof(T) * mg * mc);
     return al16(sizeof(ACC) * mg * 32) + al16(sizeof(ACC) * mc * 32) + (chunk > psi ? chunk : psi) + 16;
 }
@@ -790,7 +793,7 @@ __global__ void __launch_bounds__(kNBT) k_neu_bg(DevLevel L, BatchLevel B, int p
     }
     // w = N f, N in chunks of rows p (N[p * nG + q])
     const T *N = O.nmat + L.offN[sub];
-    const int CH = neu_chunk_rows<T>(nG);
+    const int CH = neu_chunk_rows<T>(nG, B.chunk);
     constexpr int QW = 4;   // output rows per warp and round: q = qb + warp + 8 u, u < QW
     for (int qb = 0; qb < nG; qb += 8 * QW) {
         ACC s4[QW] = {};
@@ -1585,9 +1588,13 @@ int resident_blocks(const void *kern, int nt, size_t sm, cudaStream_t s) {
     return per;
 }
 
+// The buckets one after another on s, or (B.bucket_par) at once: bucket 0
+// on s, the others on the fork's streams, joined back into s.
 template <class T, class ACC, bool SWZ, bool POST>
 void dir_bs_buckets(const DevLevel &L, const BatchLevel &B, const double *r, double *z, const int *skip,
                     const RzBatch &rz, cudaStream_t s, bool launch = true) {
+    const BucketFork *F = (launch && B.bucket_par && B.fork && L.bk.n > 1) ? B.fork : nullptr;
+    if (F) BDDC_CUDA_TRY(cudaEventRecord(F->fork, s));
     for (int i = 0; i < L.bk.n; ++i) {
         DevLevel Lb = L;                  // the bucket's maxima size its shared memory
         Lb.max_b = L.bk.max_b[i];
@@ -1598,9 +1605,17 @@ void dir_bs_buckets(const DevLevel &L, const BatchLevel &B, const double *r, dou
         const int per = resident_blocks(reinterpret_cast<const void *>(k_dir_bs<T, ACC, SWZ, POST>), nt, sm, s);
         if (!launch) continue;
         const int grid = std::min(L.bk.count[i], per * num_sms_b());
-        launch_plain(k_dir_bs<T, ACC, SWZ, POST>, grid, nt, sm, s, Lb, B, r, z, skip, rz,
+        cudaStream_t si = s;
+        if (F && i > 0) {
+            si = F->st[i - 1];
+            BDDC_CUDA_TRY(cudaStreamWaitEvent(si, F->fork, 0));
+        }
+        launch_plain(k_dir_bs<T, ACC, SWZ, POST>, grid, nt, sm, si, Lb, B, r, z, skip, rz,
                      (const int *)(L.bperm + L.bk.first[i]), L.bk.count[i]);
+        if (F && i > 0) BDDC_CUDA_TRY(cudaEventRecord(F->join[i - 1], si));
     }
+    if (F)
+        for (int i = 1; i < L.bk.n; ++i) BDDC_CUDA_TRY(cudaStreamWaitEvent(s, F->join[i - 1], 0));
 }
 
 template <class T, class ACC> void prepare_bs(const DevLevel &L) {
@@ -1641,7 +1656,7 @@ void pre_b(const DevLevel &L, const BatchLevel &B, int prec, const double *r, co
     else dir_bs<T, ACC>(L, B, false, r, nullptr, skip, nullptr, s);
     if (ev) cudaEventRecord(ev[1], s);
     if (R.neu_staged) neu_b<T, ACC>(L, B, prec, r, skip, s);
-    else launch_plain(k_neu_bg<T, ACC>, L.nsub, kNBT, neu_bg_smem<T, ACC>(L), s, L, B, pidx_b(prec), r, skip);
+    else launch_plain(k_neu_bg<T, ACC>, L.nsub, kNBT, neu_bg_smem<T, ACC>(L, B.chunk), s, L, B, pidx_b(prec), r, skip);
     if (ev) cudaEventRecord(ev[2], s);
 }
 
@@ -1651,7 +1666,7 @@ void post_b(const DevLevel &L, const BatchLevel &B, int prec, const double *r, d
     const BatchRoute R = route_t<T, ACC>(L, prec);
     if (ev) cudaEventRecord(ev[0], s);
     if (R.avg_staged) avg_b<T, ACC>(L, B, prec, skip, s);
-    else launch_plain(k_avg_bg<T, ACC>, L.nsub, kNBT, neu_bg_smem<T, ACC>(L), s, L, B, pidx_b(prec), skip);
+    else launch_plain(k_avg_bg<T, ACC>, L.nsub, kNBT, neu_bg_smem<T, ACC>(L, B.chunk), s, L, B, pidx_b(prec), skip);
     if (ev) cudaEventRecord(ev[1], s);
     if (R.post_tc) tc_dir_b(L, B, prec, true, r, z, skip, rz, s);
     else if (R.dir_staged) dir_b<T, ACC>(L, B, true, r, z, skip, s, rz);
@@ -1660,6 +1675,65 @@ void post_b(const DevLevel &L, const BatchLevel &B, int prec, const double *r, d
 }
 
 }  // namespace
+
+namespace {
+
+// mean ms of three runs of f after one untimed
+template <class F> double time3(cudaStream_t s, F &&f) {
+    cudaEvent_t e0, e1;
+    BDDC_CUDA_TRY(cudaEventCreate(&e0));
+    BDDC_CUDA_TRY(cudaEventCreate(&e1));
+    f();
+    BDDC_CUDA_TRY(cudaEventRecord(e0, s));
+    for (int i = 0; i < 3; ++i) f();
+    BDDC_CUDA_TRY(cudaEventRecord(e1, s));
+    BDDC_CUDA_TRY(cudaEventSynchronize(e1));
+    float ms = 0.0f;
+    BDDC_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return ms / 3.0;
+}
+
+template <class T, class ACC> void tune_t(const DevLevel &L, BatchLevel &B, int prec, const double *r, cudaStream_t s) {
+    const BatchRoute R = route_t<T, ACC>(L, prec);
+    if (R.dir_stream && !R.pre_tc && L.bk.n > 1 && B.fork && B.ys) {
+        double t[2];
+        for (int par = 0; par < 2; ++par) {
+            B.bucket_par = par;
+            t[par] = time3(s, [&] { dir_bs<T, ACC>(L, B, false, r, nullptr, nullptr, nullptr, s); });
+        }
+        B.bucket_par = t[1] < t[0] ? 1 : 0;
+        if (const char *e = std::getenv("BDDC_BUCKETS")) {   // "serial" or "parallel"
+            if (e[0] == 's') B.bucket_par = 0;
+            if (e[0] == 'p') B.bucket_par = 1;
+        }
+    }
+    if (!R.neu_staged && neu_bg_smem<T, ACC>(L) <= kSmemMaxB) {
+        const int cand[3] = {16 * 1024, 32 * 1024, 64 * 1024};
+        double best = 1e30;
+        int pick = 0;
+        for (int c : cand) {
+            if (neu_bg_smem<T, ACC>(L, c) > kSmemMaxB) continue;
+            B.chunk = c;
+            const double t = time3(s, [&] {
+                launch_plain(k_neu_bg<T, ACC>, L.nsub, kNBT, neu_bg_smem<T, ACC>(L, c), s, L, B, pidx_b(prec), r,
+                             (const int *)nullptr);
+            });
+            if (t < best) best = t, pick = c;
+        }
+        B.chunk = pick;
+    }
+}
+
+}  // namespace
+
+void tune_level_b(const DevLevel &L, BatchLevel &B, int prec, const double *r, cudaStream_t s) {
+    if (prec == BDDC_PREC_FP64) tune_t<double, double>(L, B, prec, r, s);
+    else if (prec == BDDC_PREC_FP32) tune_t<float, float>(L, B, prec, r, s);
+    else tune_t<__nv_bfloat16, float>(L, B, prec, r, s);
+    BDDC_CUDA_TRY(cudaStreamSynchronize(s));
+}
 
 void batch_prepare_level(const DevLevel &L) {
     if (L.bk.n == 0) return;

@@ -86,8 +86,14 @@ struct BatchWs {
     int tile_v = 0, gemm_v = 1;              // autotuned variants (dir_spmv_tune, gemm_tune)
     int last_iters = 0;
     std::vector<double> hal, hbe;
+    BucketFork fork;                         // size buckets of a sweep at once
     ~BatchWs() {
         for (auto &g : graphs) cudaGraphExecDestroy(g.second);
+        for (int i = 0; i < kMaxBuckets; ++i) {
+            if (fork.st[i]) cudaStreamDestroy(fork.st[i]);
+            if (fork.join[i]) cudaEventDestroy(fork.join[i]);
+        }
+        if (fork.fork) cudaEventDestroy(fork.fork);
         if (hsc) cudaFreeHost(hsc);
         if (hnrm) cudaFreeHost(hnrm);
     }
@@ -180,6 +186,8 @@ struct bddc_ctx {
     // solves in different workspaces stay bit-identical)
     int tile_v = -1, gemm_v = -1;
     double top_ms[2] = {0.0, 0.0};    // the tuner's times of a batched top solve: dense product, factor
+    int bucket_par[3] = {0, 0, 0};    // per level: size buckets at once (tune_level_b)
+    int neu_chunk[3] = {0, 0, 0};     // per level: the large-record Neumann kernel's chunk (bytes, 0: default)
     std::mutex tune_mu;
     double setup_ms = 0.0;
     std::mutex mu;
@@ -1236,6 +1244,21 @@ BatchWs &batch_ws(bddc_ctx *C, Workspace &W) {
     BDDC_CUDA_TRY(cudaHostAlloc((void **)&bw->hsc, sizeof(BatchScalars), cudaHostAllocDefault));
     BDDC_CUDA_TRY(cudaHostAlloc((void **)&bw->hnrm, sizeof(double) * KB, cudaHostAllocDefault));
     {
+        // streams for the size buckets of a sweep, at the workspace stream's priority
+        int nbk = 0;
+        for (auto &D : W.lv) nbk = std::max(nbk, D.bk.n);
+        if (nbk > 1) {
+            int prio = 0;
+            BDDC_CUDA_TRY(cudaStreamGetPriority(W.stream, &prio));
+            BDDC_CUDA_TRY(cudaEventCreateWithFlags(&bw->fork.fork, cudaEventDisableTiming));
+            for (int i = 0; i + 1 < nbk; ++i) {
+                BDDC_CUDA_TRY(cudaStreamCreateWithPriority(&bw->fork.st[i], cudaStreamNonBlocking, prio));
+                BDDC_CUDA_TRY(cudaEventCreateWithFlags(&bw->fork.join[i], cudaEventDisableTiming));
+            }
+            for (auto &B : bw->lv) B.fork = &bw->fork;
+        }
+    }
+    {
         // autotune the stencil tile and the top-level product on this
         // problem's operators, with scratch scalars and outputs
         cudaStream_t st = W.stream;
@@ -1269,9 +1292,28 @@ BatchWs &batch_ws(bddc_ctx *C, Workspace &W) {
             C->tuned[0] = tx;
             C->tuned[1] = ty;
             C->tuned[2] = C->gemm_v >= 0 ? gemm_rows(C->gemm_v, C->n_top) : 0;
+            // the streaming Dirichlet kernel's buckets and the Neumann chunk,
+            // per level, in the context's precision
+            for (size_t l = 0; l < W.lv.size() && l < 3; ++l) {
+                BatchLevel &B = bw->lv[l];
+                B.K = KB;
+                tune_level_b(W.lv[l], B, C->prec, bw->r, st);
+                C->bucket_par[l] = B.bucket_par;
+                C->neu_chunk[l] = B.chunk;
+                const int64_t ni = std::max(W.lv[l].n_iface, 1);
+                const int64_t ncp = std::max<int64_t>(std::max(W.lv[l].nc, 1), C->ld_top);
+                BDDC_CUDA_TRY(cudaMemsetAsync(B.rB, 0, sizeof(double) * ni * KB, st));
+                BDDC_CUDA_TRY(cudaMemsetAsync(B.uB, 0, sizeof(double) * ni * KB, st));
+                BDDC_CUDA_TRY(cudaMemsetAsync(B.rcv, 0, sizeof(double) * ncp * KB, st));
+            }
+            BDDC_CUDA_TRY(cudaStreamSynchronize(st));
         }
         bw->tile_v = C->tile_v;
         bw->gemm_v = C->gemm_v;
+        for (size_t l = 0; l < bw->lv.size() && l < 3; ++l) {
+            bw->lv[l].bucket_par = C->bucket_par[l];
+            bw->lv[l].chunk = C->neu_chunk[l];
+        }
     }
     BDDC_CUDA_TRY(cudaStreamSynchronize(W.stream));   // the buffers are zero for any stream
     W.bw = std::move(bw);
@@ -2047,6 +2089,11 @@ int bddc_query(const bddc_ctx *ctx, bddc_info *info, int level, int32_t *n_selec
             for (int t = 0; t < 3; ++t) info->tuned_tile[t] = ctx->tuned[t];
             info->top_blocks = ctx->band ? ctx->band->nb : 0;
             info->top_fma_per_rhs = ctx->band ? ctx->band->fma_per_rhs : 0;
+            info->tuned_buckets_at_once = 0;
+            for (int l = 0; l < 3; ++l) {
+                if (ctx->bucket_par[l]) info->tuned_buckets_at_once |= 1 << l;
+                info->tuned_neu_chunk[l] = ctx->neu_chunk[l];
+            }
             info->apply_status = *ctx->happly ? BDDC_E_TIMEOUT : BDDC_OK;
             info->tc_levels = 0;
             for (size_t l = 0; l < ctx->L.size(); ++l)

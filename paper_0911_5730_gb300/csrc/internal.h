@@ -264,8 +264,21 @@ void launch_red_update(int ng, double *x, double *r, const double *p, const doub
 // vector is interleaved: entry (g, k) at g * K + k.
 // ----------------------------------------------------------------------------
 constexpr int kMaxBatch = 32;
+// Streams and events that let the size buckets of one sweep of the streaming
+// Dirichlet kernel run at once: forked from the workspace stream by an event
+// and joined back (a graph capture follows the fork).  Owned by the batch
+// workspace.
+struct BucketFork {
+    cudaStream_t st[kMaxBuckets] = {};
+    cudaEvent_t fork = nullptr, join[kMaxBuckets] = {};
+};
 struct BatchLevel {
     int K = 0;                 // right-hand sides in the batch
+    // autotuned (tune_level_b): buckets of a sweep at once through `fork`,
+    // and the row chunk of the large-record Neumann kernel in bytes (0: 32 KB)
+    const BucketFork *fork = nullptr;
+    int bucket_par = 0;
+    int chunk = 0;
     double *rB = nullptr;      // [n_iface][K]
     double *uB = nullptr;      // [n_iface][K]
     double *w = nullptr;       // [sum nG][K]
@@ -298,6 +311,14 @@ struct RzBatch {
 bool batch_path(const DevLevel &L, int prec);
 bool batch_streams(const DevLevel &L);   // some precision takes the streaming Dirichlet kernel
 void batch_prepare_level(const DevLevel &L);   // launch shapes of the streaming kernel, before any capture
+// Autotuning of one level's batch kernels in precision prec on the problem's
+// own operators (CUDA events, three launches after one untimed): the size
+// buckets of the streaming Dirichlet kernel one after another or at once
+// (B.bucket_par; needs B.fork), and the row chunk of the large-record
+// Neumann kernel, 16, 32 or 64 KB (B.chunk).  r: any FP64 [n][K] input.
+// Clobbers B.rB, B.uB, B.w, B.rcv and the sweep scratch: the caller zeroes
+// r_B and r_c afterwards.  Runs on s and waits for it.
+void tune_level_b(const DevLevel &L, BatchLevel &B, int prec, const double *r, cudaStream_t s);
 void prepare_batch_kernels();
 // Algorithm 1 on one level for a batch (same scratch protocol as the single
 // right-hand-side launchers, on the BatchLevel buffers).

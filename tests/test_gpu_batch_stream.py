@@ -112,3 +112,39 @@ def test_stream_batch_full_width_mixed(case):
     for j in range(32):
         assert inf32[j]["status"] == 0 and inf32[j]["relres_true"] <= 1e-8, (name, j)
         assert _relerr(X32[j].cpu().numpy(), X64[j].cpu().numpy()) <= 1e-6
+
+
+@pytest.mark.parametrize("mode", ["serial", "parallel"])
+def test_size_buckets_serial_and_at_once(lib, monkeypatch, mode):
+    """The streaming kernel's size buckets launched one after another or at
+    once on forked streams (the autotuner picks; BDDC_BUCKETS forces): 64
+    Voronoi cells of about 1000 DOFs fall in several buckets.  FP64 batched
+    apply within 1e-10 of the oracle, FP32 within 1e-5 of the FP64 apply, and
+    a batched PCG with the oracle's iteration count."""
+    monkeypatch.setenv("BDDC_BUCKETS", mode)
+    monkeypatch.delenv("BDDC_BATCH_STREAM", raising=False)
+    wl = inputs.three_level_voronoi(nx=256, cells=8, group=2, levels=2)
+    if "voronoi_256_cells" not in _cache:
+        _cache["voronoi_256_cells"] = obddc.build_workload(wl)
+    H = _cache["voronoi_256_cells"]
+    P = lib.Problem.from_workload(wl)
+    try:
+        R = inputs.normal_rhs(wl.n_dof, 31, 9)
+        Rt = torch.tensor(R, device="cuda")
+        Z = P.apply(Rt).cpu().numpy()
+        for j in range(9):
+            assert _relerr(Z[j], H.apply(R[j])) <= 1e-10, j
+        assert bool(P.query(level=None)["tuned_buckets_at_once"] & 1) == (mode == "parallel")
+        P.set_precision("fp32")
+        Zm = P.apply(Rt).cpu().numpy()
+        for j in range(9):
+            assert _relerr(Zm[j], Z[j]) <= 1e-5, j
+        P.set_precision("fp64")
+        b = R[:4]
+        X, infos = P.solve(torch.tensor(b, device="cuda"), rtol=1e-8)
+        for j in range(4):
+            res = opcg.pcg(H.A, b[j], H.apply, rtol=1e-8)
+            assert infos[j]["status"] == 0 and infos[j]["iters"] == res.iters
+            assert _relerr(X[j].cpu().numpy(), res.x) <= 1e-10
+    finally:
+        P.close()
