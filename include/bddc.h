@@ -173,6 +173,11 @@ typedef struct {
      * default 32 KB) */
     int32_t tuned_buckets_at_once;
     int32_t tuned_neu_chunk[3];
+    /* per level, the batch kernels the autotuner chose where both fit, for
+     * every precision p (FP64 0, FP32 1, BF16 2): bit 2p set: the streaming
+     * Dirichlet kernel instead of the staged one; bit 2p+1 set: the chunked
+     * Neumann / averaging kernels instead of the staged ones */
+    int32_t tuned_route[3];
 } bddc_info;
 
 /*

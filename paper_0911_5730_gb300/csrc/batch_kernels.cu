@@ -1507,6 +1507,7 @@ namespace {
 struct BatchRoute {
     bool dir_staged = false, neu_staged = false, avg_staged = false;
     bool dir_stream = false;   // the streaming Dirichlet kernel
+    bool stream_fits = false, bg_fits = false;   // the streaming / chunked kernels could run
     bool pre_tc = false, post_tc = false;   // the tensor-core products (tc_kernels.cu)
     bool ok = false;
 };
@@ -1532,10 +1533,11 @@ template <class T, class ACC> BatchRoute route_t(const DevLevel &L, int prec) {
                         StreamSmemB::of<T, ACC>(L, 32 * nw_max).total <= kSmemMaxB;
     const bool bg = neu_bg_smem<T, ACC>(L) <= kSmemMaxB;
     R.dir_stream = !R.dir_staged && stream;
-    if (force_stream()) {
-        if (stream) R.dir_staged = false, R.dir_stream = true;
-        if (bg) R.neu_staged = R.avg_staged = false;
-    }
+    R.stream_fits = stream;
+    R.bg_fits = bg;
+    const bool pdir = (L.route_pref >> (2 * pi)) & 1, pneu = (L.route_pref >> (2 * pi + 1)) & 1;
+    if ((force_stream() || pdir) && stream) R.dir_staged = false, R.dir_stream = true;
+    if ((force_stream() || pneu) && bg) R.neu_staged = R.avg_staged = false;
     R.pre_tc = tc_route(L, prec, false);
     R.post_tc = tc_route(L, prec, true);
     R.ok = (R.dir_staged || R.dir_stream || (R.pre_tc && R.post_tc)) && (R.neu_staged || bg) && (R.avg_staged || bg);
@@ -1555,7 +1557,7 @@ bool batch_path(const DevLevel &L, int prec) { return route(L, prec).ok; }
 bool batch_streams(const DevLevel &L) {
     for (int prec : {BDDC_PREC_FP64, BDDC_PREC_FP32, BDDC_PREC_BF16}) {
         const BatchRoute R = route(L, prec);
-        if (R.ok && R.dir_stream) return true;
+        if (R.ok && (R.dir_stream || R.stream_fits)) return true;
     }
     return false;
 }
@@ -1695,6 +1697,36 @@ template <class F> double time3(cudaStream_t s, F &&f) {
     return ms / 3.0;
 }
 
+// staged against streaming / chunked routes of one precision (L.route_pref)
+template <class T, class ACC>
+void tune_route_t(DevLevel &L, BatchLevel &B, int prec, const double *r, double *z, cudaStream_t s) {
+    const int pi = pidx_b(prec);
+    const char *forced = std::getenv("BDDC_ROUTE");   // "staged" or "stream": no timing
+    for (int part = 0; part < 2; ++part) {            // 0: Dirichlet, 1: Neumann and averaging
+        const int bit = 1 << (2 * pi + part);
+        L.route_pref &= ~bit;
+        const BatchRoute R0 = route_t<T, ACC>(L, prec);
+        const bool both = part == 0 ? (R0.dir_staged && R0.stream_fits && B.ys && !(R0.pre_tc && R0.post_tc))
+                                    : ((R0.neu_staged || R0.avg_staged) && R0.bg_fits);
+        if (!both) continue;
+        if (forced) {
+            if (forced[0] == 's' && forced[1] == 't' && forced[2] == 'r') L.route_pref |= bit;
+            continue;
+        }
+        double t[2];
+        for (int v = 0; v < 2; ++v) {
+            if (v) L.route_pref |= bit;
+            else L.route_pref &= ~bit;
+            t[v] = time3(s, [&] {            // the level's pre- and post-correction steps
+                pre_b<T, ACC>(L, B, prec, r, nullptr, s, nullptr);
+                post_b<T, ACC>(L, B, prec, r, z, nullptr, s, nullptr, nullptr);
+            });
+        }
+        if (t[1] < t[0]) L.route_pref |= bit;
+        else L.route_pref &= ~bit;
+    }
+}
+
 template <class T, class ACC> void tune_t(const DevLevel &L, BatchLevel &B, int prec, const double *r, cudaStream_t s) {
     const BatchRoute R = route_t<T, ACC>(L, prec);
     if (R.dir_stream && !R.pre_tc && L.bk.n > 1 && B.fork && B.ys) {
@@ -1728,7 +1760,10 @@ template <class T, class ACC> void tune_t(const DevLevel &L, BatchLevel &B, int 
 
 }  // namespace
 
-void tune_level_b(const DevLevel &L, BatchLevel &B, int prec, const double *r, cudaStream_t s) {
+void tune_level_b(DevLevel &L, BatchLevel &B, int prec, const double *r, double *z, cudaStream_t s) {
+    tune_route_t<double, double>(L, B, BDDC_PREC_FP64, r, z, s);
+    tune_route_t<float, float>(L, B, BDDC_PREC_FP32, r, z, s);
+    tune_route_t<__nv_bfloat16, float>(L, B, BDDC_PREC_BF16, r, z, s);
     if (prec == BDDC_PREC_FP64) tune_t<double, double>(L, B, prec, r, s);
     else if (prec == BDDC_PREC_FP32) tune_t<float, float>(L, B, prec, r, s);
     else tune_t<__nv_bfloat16, float>(L, B, prec, r, s);

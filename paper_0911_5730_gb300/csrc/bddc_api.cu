@@ -187,6 +187,7 @@ struct bddc_ctx {
     int tile_v = -1, gemm_v = -1;
     double top_ms[2] = {0.0, 0.0};    // the tuner's times of a batched top solve: dense product, factor
     int bucket_par[3] = {0, 0, 0};    // per level: size buckets at once (tune_level_b)
+    int route_pref[3] = {0, 0, 0};    // per level: staged or streaming batch kernels (DevLevel::route_pref)
     int neu_chunk[3] = {0, 0, 0};     // per level: the large-record Neumann kernel's chunk (bytes, 0: default)
     std::mutex tune_mu;
     double setup_ms = 0.0;
@@ -1297,7 +1298,8 @@ BatchWs &batch_ws(bddc_ctx *C, Workspace &W) {
             for (size_t l = 0; l < W.lv.size() && l < 3; ++l) {
                 BatchLevel &B = bw->lv[l];
                 B.K = KB;
-                tune_level_b(W.lv[l], B, C->prec, bw->r, st);
+                tune_level_b(W.lv[l], B, C->prec, bw->r, bw->z, st);
+                C->route_pref[l] = W.lv[l].route_pref;
                 C->bucket_par[l] = B.bucket_par;
                 C->neu_chunk[l] = B.chunk;
                 const int64_t ni = std::max(W.lv[l].n_iface, 1);
@@ -1313,6 +1315,7 @@ BatchWs &batch_ws(bddc_ctx *C, Workspace &W) {
         for (size_t l = 0; l < bw->lv.size() && l < 3; ++l) {
             bw->lv[l].bucket_par = C->bucket_par[l];
             bw->lv[l].chunk = C->neu_chunk[l];
+            W.lv[l].route_pref = C->route_pref[l];
         }
     }
     BDDC_CUDA_TRY(cudaStreamSynchronize(W.stream));   // the buffers are zero for any stream
@@ -2093,6 +2096,7 @@ int bddc_query(const bddc_ctx *ctx, bddc_info *info, int level, int32_t *n_selec
             for (int l = 0; l < 3; ++l) {
                 if (ctx->bucket_par[l]) info->tuned_buckets_at_once |= 1 << l;
                 info->tuned_neu_chunk[l] = ctx->neu_chunk[l];
+                info->tuned_route[l] = ctx->route_pref[l];
             }
             info->apply_status = *ctx->happly ? BDDC_E_TIMEOUT : BDDC_OK;
             info->tc_levels = 0;

@@ -114,6 +114,10 @@ struct DevLevel {
     int nc = 0;           // coarse DOFs (= DOFs of the next level)
     int max_nI = 0, max_nG = 0, max_nc = 0, max_b = 0, max_m = 0, max_coo = 0;
     int max_ld = 0;            // largest leading dimension of a factor block
+    // the batch autotuner's route per precision index p (FP64 0, FP32 1,
+    // BF16 2): bit 2p: the streaming Dirichlet kernel where the staged one
+    // also fits; bit 2p+1: the chunked Neumann / averaging kernels likewise
+    int route_pref = 0;
     SizeBuckets bk;            // size buckets (n = 0: a block needs more than 16 warps)
     int *bperm = nullptr;      // substructures in bucket order
     // per substructure sizes
@@ -309,16 +313,19 @@ struct RzBatch {
 };
 // Whether a level's operators fit the batched kernels' shared-memory slices.
 bool batch_path(const DevLevel &L, int prec);
-bool batch_streams(const DevLevel &L);   // some precision takes the streaming Dirichlet kernel
+bool batch_streams(const DevLevel &L);   // some precision can take the streaming Dirichlet kernel
 void batch_prepare_level(const DevLevel &L);   // launch shapes of the streaming kernel, before any capture
-// Autotuning of one level's batch kernels in precision prec on the problem's
-// own operators (CUDA events, three launches after one untimed): the size
-// buckets of the streaming Dirichlet kernel one after another or at once
-// (B.bucket_par; needs B.fork), and the row chunk of the large-record
-// Neumann kernel, 16, 32 or 64 KB (B.chunk).  r: any FP64 [n][K] input.
-// Clobbers B.rB, B.uB, B.w, B.rcv and the sweep scratch: the caller zeroes
-// r_B and r_c afterwards.  Runs on s and waits for it.
-void tune_level_b(const DevLevel &L, BatchLevel &B, int prec, const double *r, cudaStream_t s);
+// Autotuning of one level's batch kernels on the problem's own operators
+// (CUDA events, three launches after one untimed): for every precision,
+// staged against streaming Dirichlet kernels and staged against chunked
+// Neumann / averaging kernels where both fit (L.route_pref); in precision
+// prec, the size buckets of the streaming Dirichlet kernel one after another
+// or at once (B.bucket_par; needs B.fork), and the row chunk of the
+// large-record Neumann kernel, 16, 32 or 64 KB (B.chunk).  r: any FP64
+// [n][K] input, z: an [n][K] output.  Clobbers B.rB, B.uB, B.w, B.rcv, z and
+// the sweep scratch: the caller zeroes r_B, u_B and r_c afterwards.  Runs on
+// s and waits for it.
+void tune_level_b(DevLevel &L, BatchLevel &B, int prec, const double *r, double *z, cudaStream_t s);
 void prepare_batch_kernels();
 // Algorithm 1 on one level for a batch (same scratch protocol as the single
 // right-hand-side launchers, on the BatchLevel buffers).
