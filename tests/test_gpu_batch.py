@@ -208,3 +208,36 @@ def test_groups_in_flight_match_each_group_alone(lib):
         Xh, ih = P.solve_host(B.cpu().numpy())
         assert _relerr(Xh, X.cpu().numpy()) <= 1e-12
     P.close()
+
+
+@pytest.mark.parametrize("route", ["staged", "stream"])
+@pytest.mark.parametrize("name", ["channels_64", "three_level_64"])
+def test_batch_routes_both_match_oracle(lib, monkeypatch, name, route):
+    """The autotuner picks, per level and precision, staged or streaming
+    Dirichlet kernels and staged or chunked Neumann / averaging kernels where
+    both fit; BDDC_ROUTE forces one of them on every level, so both kinds are
+    held to the batch bar whatever the tuner picks: FP64 apply within 1e-10
+    of the oracle, FP32 / BF16 within 1e-5 / 1e-2 of it, and the reported
+    route bits."""
+    monkeypatch.setenv("BDDC_ROUTE", route)
+    wl = WL[name]
+    H = _oracle(name)
+    P = lib.Problem.from_workload(wl)
+    try:
+        R = inputs.normal_rhs(wl.n_dof, 41, 6)
+        Rt = torch.tensor(R, device="cuda")
+        Z = P.apply(Rt).cpu().numpy()
+        for j in range(6):
+            assert _relerr(Z[j], H.apply(R[j])) <= 1e-10, j
+        routes = P.query(level=None)["tuned_route"]
+        if route == "staged":
+            assert all(r == 0 for r in routes)
+        else:
+            assert routes[0] & 0b000010                     # FP64 Neumann chunked on level 1
+        for prec, tol in (("fp32", 1e-5), ("bf16", 1e-2)):
+            P.set_precision(prec)
+            Zm = P.apply(Rt).cpu().numpy()
+            for j in range(6):
+                assert _relerr(Zm[j], Z[j]) <= tol, (prec, j)
+    finally:
+        P.close()
