@@ -48,9 +48,9 @@ RTOL = 1e-8
 NCU_TRAFFIC = {
     # the block-tridiagonal top solve: k_top_rows (g), k_top_chain (forward),
     # k_top_rows (h), k_top_chain (backward), two right-hand sides per cluster
-    "top_solve": {"bytes": 8916736, "file": "top_kernels.cu", "src": "7882facf74a4",
+    "top_solve": {"bytes": 8916736, "file": "top_kernels.cu", "src": "a11462098415",
                   "kernel": "k_top_rows + k_top_chain, 4 launches"},
-    "post": {"bytes": 120436224, "file": "batch_kernels.cu", "src": "78a371f18224",
+    "post": {"bytes": 120289536, "file": "batch_kernels.cu", "src": "36e7929654d3",
              "kernel": "k_dir_b<float, float, 16, 1>"},
 }
 
@@ -64,6 +64,8 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-elasticity", action="store_true",
                     help="skip the elasticity entry (the paper's own experiment, one process only)")
+    ap.add_argument("--no-serving", action="store_true",
+                    help="skip the config-2 serving runs (threads; for profiler captures)")
     ap.add_argument("--no-serving-mix", action="store_true",
                     help="skip serving configs 2-4 resident together (one process only)")
     ap.add_argument("--batch", type=int, default=BATCH,
@@ -527,9 +529,11 @@ def gpu_arm(a):
     # config 5: Poisson streams of requests at 0.5, 0.8 and 1.0 x the measured
     # batch rate (0.8 x is the headline serving entry)
     P.set_precision("fp32")
-    serving = serving_run(bddc, P, wl.n_dof, 0.8 * value / world, 3.0, 5001)
-    serving["at_load"] = {"%.1f" % f: serving_run(bddc, P, wl.n_dof, f * value / world, 3.0, 5001)
-                          for f in (0.5, 1.0)}
+    serving = None
+    if not a.no_serving:
+        serving = serving_run(bddc, P, wl.n_dof, 0.8 * value / world, 3.0, 5001)
+        serving["at_load"] = {"%.1f" % f: serving_run(bddc, P, wl.n_dof, f * value / world, 3.0, 5001)
+                              for f in (0.5, 1.0)}
 
     # config 5 over configs 2, 3 and 4 resident together (FP32 and FP64 apply,
     # HBM-budget admission)
@@ -651,7 +655,10 @@ def gpu_arm(a):
         "kernels_fp32_apply_batch": kern,
         "autotuned": {"stencil_tile": P.query(level=None)["tuned_tile"][:2],
                       "top_product_rows_per_block": P.query(level=None)["tuned_tile"][2],
-                      "top_form": top_form, "top_blocks": q.get("top_blocks", 0)},
+                      "top_form": top_form, "top_blocks": q.get("top_blocks", 0),
+                      "route_bits_level1": P.query(level=None)["tuned_route"][0],
+                      "buckets_at_once": P.query(level=None)["tuned_buckets_at_once"],
+                      "neumann_chunk_bytes": P.query(level=None)["tuned_neu_chunk"][0]},
         "gpu_launches": launches,
         "cpu_baseline": cpu,
         "clocks": clocks,

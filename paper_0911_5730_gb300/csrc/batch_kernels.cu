@@ -1702,6 +1702,10 @@ template <class T, class ACC>
 void tune_route_t(DevLevel &L, BatchLevel &B, int prec, const double *r, double *z, cudaStream_t s) {
     const int pi = pidx_b(prec);
     const char *forced = std::getenv("BDDC_ROUTE");   // "staged" or "stream": no timing
+    if (const char *bits = std::getenv("BDDC_ROUTE_PREF")) {   // the route bits themselves, every level
+        L.route_pref = std::atoi(bits);
+        return;
+    }
     for (int part = 0; part < 2; ++part) {            // 0: Dirichlet, 1: Neumann and averaging
         const int bit = 1 << (2 * pi + part);
         L.route_pref &= ~bit;
@@ -1755,6 +1759,10 @@ template <class T, class ACC> void tune_t(const DevLevel &L, BatchLevel &B, int 
             if (t < best) best = t, pick = c;
         }
         B.chunk = pick;
+        if (const char *e = std::getenv("BDDC_NEU_CHUNK")) {   // bytes: this chunk
+            const int c = std::atoi(e);
+            if (c > 0 && neu_bg_smem<T, ACC>(L, c) <= kSmemMaxB) B.chunk = c;
+        }
     }
 }
 
@@ -1924,6 +1932,10 @@ void launch_b_dir_spmv(int nx, int K, const double *w, const double *z, double *
 }
 int dir_spmv_tune(int nx, int K, const double *w, const double *z, double *p0, double *p1, double *q,
                   double *part, unsigned *counter, BatchScalars *sc, double *alphas, cudaStream_t s) {
+    if (const char *e = std::getenv("BDDC_TILE_VARIANT")) {   // 0..3: this tile, no timing
+        const int v = std::atoi(e);
+        if (v >= 0 && v < kNTiles) return v;
+    }
     int best = 0;
     float tb = 1e30f;
     for (int v = 0; v < kNTiles; ++v) {

@@ -1849,7 +1849,18 @@ template <class F> int run_batch_groups(bddc_ctx *ctx, int nrhs, F &&group) {
         std::vector<int> st(ng, BDDC_OK);
         std::vector<std::exception_ptr> ep(ng);
         std::vector<std::thread> th;
-        for (int g = 1; g < ng; ++g)
+        // BDDC_GROUPS_SERIAL=1: every group from the calling thread, one
+        // after another (for profilers that serialise kernels anyway)
+        const char *serial_env = std::getenv("BDDC_GROUPS_SERIAL");
+        const bool serial = serial_env && serial_env[0] == '1';
+        for (int g = 1; g < ng && serial; ++g) {
+            try {
+                st[g] = group(*ws[g], js[g], ks[g]);
+            } catch (...) {
+                ep[g] = std::current_exception();
+            }
+        }
+        for (int g = 1; g < ng && !serial; ++g)
             th.emplace_back([&, g] {
                 try {
                     BDDC_CUDA_TRY(cudaSetDevice(ctx->device));

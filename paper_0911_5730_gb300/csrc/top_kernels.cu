@@ -23,6 +23,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
+#include <mutex>
 
 namespace bddc {
 
@@ -651,6 +652,13 @@ int top_band_cols(const TopBand &T, int K) {
 void launch_top_band(const TopBand &T, const double *X, int64_t ldx, double *Y, int64_t ldy, int K, const int *skip,
                      double *scratch, int *err, cudaStream_t s) {
     if (T.nb == 0 || K <= 0) return;
+    // The launches of one solve are enqueued under a process-wide lock:
+    // ThreadSanitizer over the bench saw two threads (batch groups in
+    // flight) write the same driver-owned parameter block while launching
+    // k_top_rows at once.  Only the host-side enqueue is serialised; the
+    // kernels of different streams still run concurrently.
+    static std::mutex launch_mu;
+    std::lock_guard<std::mutex> lk(launch_mu);
     if (K > 32) throw Error(BDDC_E_ARG, "top-level solve of more than 32 right-hand sides at once");
     TopBandArgs a;
     a.n = T.n;
