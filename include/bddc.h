@@ -178,6 +178,11 @@ typedef struct {
      * Dirichlet kernel instead of the staged one; bit 2p+1 set: the chunked
      * Neumann / averaging kernels instead of the staged ones */
     int32_t tuned_route[3];
+    /* the launch shape of the single right-hand-side product with the dense
+     * top-level inverse, timed on that inverse at setup (0: 4 warps per row,
+     * 2 rows per block; 1: 8 and 1; 2: 2 and 4; 3: 4 and 4); -1 without a
+     * dense inverse */
+    int32_t tuned_symv;
 } bddc_info;
 
 /*

@@ -78,7 +78,8 @@ class Info(C.Structure):
                 ("n_interface", C.c_int32 * 3), ("tuned_tile", C.c_int32 * 3),
                 ("tc_levels", C.c_int32), ("apply_status", C.c_int32), ("top_blocks", C.c_int32),
                 ("top_fma_per_rhs", C.c_int64), ("tuned_buckets_at_once", C.c_int32),
-                ("tuned_neu_chunk", C.c_int32 * 3), ("tuned_route", C.c_int32 * 3)]
+                ("tuned_neu_chunk", C.c_int32 * 3), ("tuned_route", C.c_int32 * 3),
+                ("tuned_symv", C.c_int32)]
 
 
 _lib = None
@@ -408,6 +409,7 @@ class Problem:
                "top_blocks": info.top_blocks, "top_fma_per_rhs": info.top_fma_per_rhs,
                "tuned_buckets_at_once": info.tuned_buckets_at_once,
                "tuned_neu_chunk": list(info.tuned_neu_chunk), "tuned_route": list(info.tuned_route),
+               "tuned_symv": info.tuned_symv,
                "apply_status": info.apply_status}
         nl = info.levels - 1
         for key in ("sum_interior", "sum_interface", "sum_coarse_local", "band_nnz",

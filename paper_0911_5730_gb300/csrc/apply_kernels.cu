@@ -823,24 +823,44 @@ __global__ void k_build_nrec(DevLevel D, OpSet<T> O, unsigned char *rec, const i
 
 // y = A x, A dense symmetric n x n row-major with leading dimension ld (a
 // multiple of 4, zero padded; x zero on [n, ld)).  The FP64 pipe bounds it:
-// SV_WR warps share a row (interleaved 64-column strips, 16-byte loads) so
-// that enough warps are resident to keep that pipe busy; the strip sums are
-// added in a fixed order.
-constexpr int SV_WR = 4, SV_ROWS = 2;
-__global__ void __launch_bounds__(32 * SV_WR * SV_ROWS)
+// WR warps share a row (interleaved 64-column strips, 16-byte loads), ROWS
+// rows per block, so that enough warps are resident to keep that pipe busy;
+// the strip sums are added in a fixed order.  A is setup-time data: each
+// warp loads its first four strips of A before waiting for the previous
+// kernel of the stream (programmatic dependent launch), so that part of the
+// read overlaps that kernel's tail.  The launch shape is autotuned per
+// problem (symv_tune).
+template <int WR, int ROWS>
+__global__ void __launch_bounds__(32 * WR * ROWS)
 k_dense_symv(int n, int ld, const double *A, const double *x, double *y, const int *skip) {
-    __shared__ double part[SV_ROWS][SV_WR];
+    __shared__ double part[ROWS][WR];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int lr = warp / WR, ws = warp % WR;
+    const int row = blockIdx.x * ROWS + lr;
+    constexpr int step = 64 * WR;
+    const double *a = A + (int64_t)(row < n ? row : 0) * ld;
+    const int c0 = 64 * ws + 2 * lane;
+    double2 pre[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int c = c0 + u * step;
+        pre[u] = (row < n && c < ld) ? *reinterpret_cast<const double2 *>(a + c) : make_double2(0.0, 0.0);
+    }
     pdl_wait();
     pdl_trigger();
     if (skip && *skip) return;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int lr = warp / SV_WR, ws = warp % SV_WR;
-    const int row = blockIdx.x * SV_ROWS + lr;
     double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
     if (row < n) {
-        const double *a = A + (int64_t)row * ld;
-        int c = 64 * ws + 2 * lane;
-        constexpr int step = 64 * SV_WR;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int c = c0 + u * step;
+            if (c < ld) {
+                const double2 xv = *reinterpret_cast<const double2 *>(x + c);
+                if (u & 1) { s2 = fma(pre[u].x, xv.x, s2); s3 = fma(pre[u].y, xv.y, s3); }
+                else { s0 = fma(pre[u].x, xv.x, s0); s1 = fma(pre[u].y, xv.y, s1); }
+            }
+        }
+        int c = c0 + 4 * step;
         for (; c + 3 * step < ld; c += 4 * step) {
             double2 av[4], xv[4];
 #pragma unroll
@@ -862,12 +882,12 @@ k_dense_symv(int n, int ld, const double *A, const double *x, double *y, const i
     for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
     if (lane == 0) part[lr][ws] = sum;
     __syncthreads();
-    if (threadIdx.x < SV_ROWS) {
-        const int rr = blockIdx.x * SV_ROWS + threadIdx.x;
+    if (threadIdx.x < ROWS) {
+        const int rr = blockIdx.x * ROWS + threadIdx.x;
         if (rr < n) {
             double t = 0.0;
 #pragma unroll
-            for (int k = 0; k < SV_WR; ++k) t += part[threadIdx.x][k];
+            for (int k = 0; k < WR; ++k) t += part[threadIdx.x][k];
             y[rr] = t;
         }
     }
@@ -1477,9 +1497,38 @@ void apply_level_post(const DevLevel &L, int prec, const double *r, double *z, c
 }
 
 void launch_dense_symv(int n, int ld, const double *A, const double *x, double *y, const int *skip,
-                       cudaStream_t s) {
+                       cudaStream_t s, int variant) {
     if (n <= 0) return;
-    launch_pdl(k_dense_symv, (n + SV_ROWS - 1) / SV_ROWS, 32 * SV_WR * SV_ROWS, 0, s, n, ld, A, x, y, skip);
+    switch (variant) {   // (warps per row, rows per block)
+        case 1: launch_pdl(k_dense_symv<8, 1>, n, 256, 0, s, n, ld, A, x, y, skip); break;
+        case 2: launch_pdl(k_dense_symv<2, 4>, (n + 3) / 4, 256, 0, s, n, ld, A, x, y, skip); break;
+        case 3: launch_pdl(k_dense_symv<4, 4>, (n + 3) / 4, 512, 0, s, n, ld, A, x, y, skip); break;
+        default: launch_pdl(k_dense_symv<4, 2>, (n + 1) / 2, 256, 0, s, n, ld, A, x, y, skip); break;
+    }
+}
+int symv_tune(int n, int ld, const double *A, const double *x, double *y, cudaStream_t s) {
+    if (const char *e = std::getenv("BDDC_SYMV_VARIANT")) {
+        const int v = std::atoi(e);
+        if (v >= 0 && v < 4) return v;
+    }
+    int best = 0;
+    float tb = 1e30f;
+    cudaEvent_t e0, e1;
+    BDDC_CUDA_TRY(cudaEventCreate(&e0));
+    BDDC_CUDA_TRY(cudaEventCreate(&e1));
+    for (int v = 0; v < 4; ++v) {
+        launch_dense_symv(n, ld, A, x, y, nullptr, s, v);
+        BDDC_CUDA_TRY(cudaEventRecord(e0, s));
+        for (int i = 0; i < 5; ++i) launch_dense_symv(n, ld, A, x, y, nullptr, s, v);
+        BDDC_CUDA_TRY(cudaEventRecord(e1, s));
+        BDDC_CUDA_TRY(cudaEventSynchronize(e1));
+        float ms = 0.0f;
+        BDDC_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < tb) { tb = ms; best = v; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return best;
 }
 
 void launch_q1_weights(int nx, const double *k, double *w, cudaStream_t s) {

@@ -185,6 +185,7 @@ struct bddc_ctx {
     // workspace (the stencil tile fixes the order of the dot products, so
     // solves in different workspaces stay bit-identical)
     int tile_v = -1, gemm_v = -1;
+    int symv_v = 0;                   // launch shape of the single right-hand-side top product (symv_tune)
     double top_ms[2] = {0.0, 0.0};    // the tuner's times of a batched top solve: dense product, factor
     int bucket_par[3] = {0, 0, 0};    // per level: size buckets at once (tune_level_b)
     int route_pref[3] = {0, 0, 0};    // per level: staged or streaming batch kernels (DevLevel::route_pref)
@@ -259,7 +260,7 @@ int top_bmin() {
 // scratch: 2 n_top doubles (the factor's intermediate vectors).
 void top_solve_1(const bddc_ctx *C, const double *r, double *u, const int *skip, double *scratch, int *err,
                  cudaStream_t st) {
-    if (C->Ainv) launch_dense_symv(C->n_top, C->ld_top, C->Ainv, r, u, skip, st);
+    if (C->Ainv) launch_dense_symv(C->n_top, C->ld_top, C->Ainv, r, u, skip, st, C->symv_v);
     else launch_top_band(*C->band, r, 1, u, 1, 1, skip, scratch, err, st);
 }
 // The same for K interleaved right-hand sides, by the form the autotuner
@@ -1725,6 +1726,11 @@ int bddc_setup(const bddc_mesh *mesh, const double *k_elem, const bddc_decomp *d
                 BDDC_CUDA_TRY(cudaMemsetAsync(C->Ainv, 0, sizeof(double) * (size_t)nt * C->ld_top, st));
                 dense_inverse_from_cholesky(nt, Atop, C->Ainv, C->ld_top, st);
             }
+            if (nt > 0 && C->Ainv) {
+                double *xs = tmp.alloc_n<double>((size_t)2 * C->ld_top);
+                BDDC_CUDA_TRY(cudaMemsetAsync(xs, 0, sizeof(double) * 2 * (size_t)C->ld_top, st));
+                C->symv_v = symv_tune(nt, C->ld_top, C->Ainv, xs, xs + C->ld_top, st);
+            }
         }
         BDDC_CUDA_TRY(cudaStreamSynchronize(st));
         BDDC_CUDA_TRY(cudaGetLastError());
@@ -2109,6 +2115,7 @@ int bddc_query(const bddc_ctx *ctx, bddc_info *info, int level, int32_t *n_selec
                 info->tuned_neu_chunk[l] = ctx->neu_chunk[l];
                 info->tuned_route[l] = ctx->route_pref[l];
             }
+            info->tuned_symv = ctx->n_top > 0 && ctx->Ainv ? ctx->symv_v : -1;
             info->apply_status = *ctx->happly ? BDDC_E_TIMEOUT : BDDC_OK;
             info->tc_levels = 0;
             for (size_t l = 0; l < ctx->L.size(); ++l)

@@ -410,7 +410,10 @@ bool apply_fuses_rz(const DevLevel &L, int prec);
 // y = A x with A dense n x n, leading dimension ld (a multiple of 4, zero
 // padded); x must be readable and zero on [n, ld).
 void launch_dense_symv(int n, int ld, const double *A, const double *x, double *y, const int *skip,
-                       cudaStream_t s);
+                       cudaStream_t s, int variant = 0);
+// The fastest launch shape of launch_dense_symv on A (0..3; x, y scratch of
+// ld doubles, x zero beyond n); BDDC_SYMV_VARIANT fixes it.
+int symv_tune(int n, int ld, const double *A, const double *x, double *y, cudaStream_t s);
 // Raise the dynamic shared-memory limit of the warp-per-substructure kernels (once).
 void prepare_apply_kernels();
 // Build the per-substructure records of a level (after its operators exist).

@@ -140,3 +140,27 @@ def test_batched_forms_agree(lib, monkeypatch):
                 assert _rel(X[j], rr.x) <= 1e-10
         finally:
             P.close()
+
+
+@pytest.mark.parametrize("variant", ["0", "1", "2", "3", None])
+def test_dense_inverse_launch_shapes_match_oracle(lib, variant, monkeypatch):
+    """Every launch shape of the single right-hand-side product with the dense
+    inverse (BDDC_SYMV_VARIANT; None: the setup's own timing picks one) gives
+    the oracle's apply, on a top level whose size is no multiple of the rows
+    per block."""
+    if variant is None:
+        monkeypatch.delenv("BDDC_SYMV_VARIANT", raising=False)
+    else:
+        monkeypatch.setenv("BDDC_SYMV_VARIANT", variant)
+    wl, H = _oracle("unit_c+e")
+    P = lib.Problem.from_workload(wl)
+    try:
+        q = P.query(level=None)
+        assert q["tuned_symv"] in (0, 1, 2, 3)
+        if variant is not None:
+            assert q["tuned_symv"] == int(variant)
+        r = inputs.normal_rhs(wl.n_dof, 12)
+        z = P.apply(torch.tensor(r, device="cuda")).cpu().numpy()
+        assert _rel(z, H.apply(r)) <= 1e-10
+    finally:
+        P.close()
