@@ -176,7 +176,10 @@ typedef struct {
     /* per level, the batch kernels the autotuner chose where both fit, for
      * every precision p (FP64 0, FP32 1, BF16 2): bit 2p set: the streaming
      * Dirichlet kernel instead of the staged one; bit 2p+1 set: the chunked
-     * Neumann / averaging kernels instead of the staged ones */
+     * Neumann / averaging kernels instead of the staged ones; bit 6+p set:
+     * the Dirichlet kernel with a lane per right-hand side (a warp per
+     * substructure, its factor streamed through a ring) instead of the
+     * staged one */
     int32_t tuned_route[3];
     /* the launch shape of the single right-hand-side product with the dense
      * top-level inverse, timed on that inverse at setup (0: 4 warps per row,

@@ -404,6 +404,363 @@ __global__ void __launch_bounds__(32 * lanes_per_rhs<BP>()) k_dir_b(DevLevel L, 
     }
 }
 
+// The Dirichlet corrections with a lane per right-hand side, streamed
+// (blocks of up to 16 rows, FP32 accumulation).  A block of kLSW warps takes
+// kLSW substructures, one per warp, so every warp of the SM runs sweeps and
+// little shared memory is needed per substructure: the factor blocks come
+// through a ring of kLSRing slots (block j in slot j % kLSRing, copied
+// kLSRing steps ahead; the backward sweep starts from the blocks left in the
+// ring and refills the slot of block j+1 after step j), the right-hand side
+// rows of block j are loaded into registers two steps ahead, and the forward
+// sweep's y_j go to the sweep scratch (same thread writes and reads them
+// back, two steps ahead).  Each lane holds all rows of its right-hand side's
+// block: a factor column is a broadcast read feeding BP multiply-adds per
+// lane and no value crosses lanes.  The coupling entries A_{I Gamma} (post:
+// b_I -= A_{I Gamma} u_B; pre: the product A_{Gamma I} x_I) are grouped by
+// the block of their interior row at the start (a stable counting sort by
+// ballots), so each step applies only its own.
+constexpr int kLSW = 4, kLSRing = 4;
+
+template <class T, int BP> struct LaneSmem {
+    size_t slot, ring, bsm, vg, rec, cvs, srt, bst, bars, warp, total;
+    __host__ __device__ static LaneSmem of(const DevLevel &L) {
+        LaneSmem m;
+        m.slot = al16(2 * (size_t)BP * BP * sizeof(T));
+        m.ring = kLSRing * m.slot;
+        m.bsm = al16(sizeof(float) * BP * 32);
+        m.vg = al16(sizeof(float) * (size_t)(L.max_nG > 0 ? L.max_nG : 1) * 32);
+        m.rec = al16((size_t)L.max_irec);
+        m.cvs = al16(sizeof(float) * (size_t)(L.max_coo > 0 ? L.max_coo : 1));
+        m.srt = al16(2 * (size_t)(L.max_coo > 0 ? L.max_coo : 1));
+        m.bst = al16(2 * (size_t)(L.max_m + 2));
+        m.bars = al16(8 * (kLSRing + 1));
+        m.warp = m.ring + m.bsm + m.vg + m.rec + m.cvs + m.srt + m.bst + m.bars;
+        m.total = kLSW * m.warp + al16(8 * 32 * kLSW + 16);
+        return m;
+    }
+};
+
+template <class T, int BP, bool POST>
+__global__ void __launch_bounds__(32 * kLSW) k_dir_ls(DevLevel L, BatchLevel B, const double *r, double *z,
+                                                     const int *skip, RzBatch rz) {
+    using ACC = float;
+    constexpr int BB = BP * BP;
+    if (skip && *skip) return;
+    extern __shared__ __align__(16) unsigned char smem_ls[];
+    const LaneSmem<T, BP> ly = LaneSmem<T, BP>::of(L);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int sub = blockIdx.x * kLSW + warp;
+    const bool live = sub < L.nsub;
+    const int K = B.K;
+    const bool act = lane < K;
+    unsigned char *p = smem_ls + (size_t)warp * ly.warp;
+    T *ring = reinterpret_cast<T *>(p);          p += ly.ring;
+    ACC *bsm = reinterpret_cast<ACC *>(p);       p += ly.bsm;
+    ACC *vG = reinterpret_cast<ACC *>(p);        p += ly.vg;
+    unsigned char *rec = p;                      p += ly.rec;
+    ACC *cvs = reinterpret_cast<ACC *>(p);       p += ly.cvs;
+    unsigned short *srt = reinterpret_cast<unsigned short *>(p);   p += ly.srt;
+    unsigned short *bst = reinterpret_cast<unsigned short *>(p);   p += ly.bst;
+    unsigned long long *bars = reinterpret_cast<unsigned long long *>(p);   // ring slots, then the record
+    double *red = reinterpret_cast<double *>(smem_ls + (size_t)kLSW * ly.warp);   // [kLSW][32]
+    int *flag = reinterpret_cast<int *>(red + 32 * kLSW);
+
+    const int nI = live ? L.nI[sub] : 0, nG = live ? L.nG[sub] : 0, m = live ? L.nblk[sub] : 0;
+    const int ncoo = live ? L.ncoo[sub] : 0, nown = live ? L.nown[sub] : 0;
+    const IRecLayout lay(nI, nG, ncoo, nown);
+    const unsigned slot_bytes = 2u * BB * (unsigned)sizeof(T);
+    const T *F = live ? Ops<T>::get(L).dir + L.offF[sub] : nullptr;
+    unsigned ph = 0, pend = 0;      // per ring slot: parity of its next completion, a copy in flight
+    bool ok = true;
+    double acc = 0.0;               // post: r.z over the entries of z this substructure writes
+    if (live) {
+        if (lane == 0) {
+            for (int s = 0; s <= kLSRing; ++s) mbar_init(&bars[s]);
+            mbar_expect(&bars[kLSRing], (unsigned)lay.bytes);
+            bulk_copy(rec, L.irec + L.irecOff[sub], (unsigned)lay.bytes, &bars[kLSRing]);
+        }
+        __syncwarp();
+        for (int j = 0; j < m && j < kLSRing; ++j) {
+            if (lane == 0) {
+                mbar_expect(&bars[j], slot_bytes);
+                bulk_copy(ring + (size_t)j * 2 * BB, F + (size_t)j * 2 * BB, slot_bytes, &bars[j]);
+            }
+            pend |= 1u << j;
+        }
+    }
+    pdl_wait();
+    pdl_trigger();
+    if (live) ok = __all_sync(0xffffffffu, mbar_wait(&bars[kLSRing], 0));
+    if (live && ok) {
+        const double *gC = reinterpret_cast<const double *>(rec + lay.cv);
+        const int *gI = reinterpret_cast<const int *>(rec + lay.iI);
+        const int *gGi = reinterpret_cast<const int *>(rec + lay.iG);
+        const int *gP = reinterpret_cast<const int *>(rec + lay.pr);
+        const int *gO = reinterpret_cast<const int *>(rec + lay.ow);
+        float *ys = reinterpret_cast<float *>(B.ys) + L.offY[sub] * 32;
+        for (int e = lane; e < ncoo; e += 32) cvs[e] = from_f64<ACC>(gC[e]);
+        {
+            // entries by the block of their interior row, in entry order within a block
+            int run = 0;
+            for (int b = 0; b < m; ++b) {
+                if (lane == 0) bst[b] = (unsigned short)run;
+                for (int c0 = 0; c0 < ncoo; c0 += 32) {
+                    const int e = c0 + lane;
+                    const int key = e < ncoo ? (gP[e] & 0xffff) / BP : -1;
+                    const unsigned mask = __ballot_sync(0xffffffffu, key == b);
+                    if (key == b) srt[run + __popc(mask & ((1u << lane) - 1u))] = (unsigned short)e;
+                    run += __popc(mask);
+                }
+            }
+            if (lane == 0) bst[m] = (unsigned short)run;
+        }
+        if (POST) {
+            for (int q0 = 0; q0 < nG; q0 += 16) {
+                double v[16];
+#pragma unroll
+                for (int u = 0; u < 16; ++u)
+                    v[u] = (q0 + u < nG && act) ? B.uB[(int64_t)gGi[q0 + u] * K + lane] : 0.0;
+#pragma unroll
+                for (int u = 0; u < 16; ++u)
+                    if (q0 + u < nG) vG[(q0 + u) * 32 + lane] = from_f64<ACC>(v[u]);
+            }
+        } else {
+            for (int q = 0; q < nG; ++q) {
+                vG[q * 32 + lane] = 0;
+                if (act) B.uB[(int64_t)gGi[q] * K + lane] = 0.0;   // consumed by the previous post-correction
+            }
+        }
+        __syncwarp();
+
+        auto load_rows = [&](double (&d)[BP], int j) {
+#pragma unroll
+            for (int q = 0; q < BP; ++q) {
+                const int row = j * BP + q;
+                d[q] = (j >= 0 && j < m && row < nI && act) ? r[(int64_t)gI[row] * K + lane] : 0.0;
+            }
+        };
+        auto wait_slot = [&](int s) -> bool {
+            const bool w = __all_sync(0xffffffffu, mbar_wait(&bars[s], (ph >> s) & 1u));
+            ph ^= 1u << s;
+            pend &= ~(1u << s);
+            return w;
+        };
+        auto refill = [&](int s, int blk) {   // after __syncwarp: every lane is done with slot s
+            if (lane == 0) {
+                mbar_expect(&bars[s], slot_bytes);
+                bulk_copy(ring + (size_t)s * 2 * BB, F + (size_t)blk * 2 * BB, slot_bytes, &bars[s]);
+            }
+            pend |= 1u << s;
+        };
+
+        // forward sweep: y_j = Linv_j (b_j - L_{j,j-1} y_{j-1})
+        ACC xp[BP];
+#pragma unroll
+        for (int q = 0; q < BP; ++q) xp[q] = 0;
+        auto fstep = [&](int j, double (&d)[BP]) -> bool {
+#pragma unroll
+            for (int q = 0; q < BP; ++q) bsm[q * 32 + lane] = from_f64<ACC>(d[q]);
+            load_rows(d, j + 2);
+            if (POST) {
+                const int e1 = bst[j + 1];
+                for (int e = bst[j]; e < e1; ++e) {
+                    const int k = srt[e], pr = gP[k];
+                    bsm[((pr & 0xffff) - j * BP) * 32 + lane] -= cvs[k] * vG[(pr >> 16) * 32 + lane];
+                }
+            }
+            ACC t[BP];
+#pragma unroll
+            for (int q = 0; q < BP; ++q) t[q] = bsm[q * 32 + lane];
+            const int s = j % kLSRing;
+            if (!wait_slot(s)) return false;
+            const T *Li = ring + (size_t)s * 2 * BB;
+            const T *Ls = Li + BB;
+            if (j > 0) {
+#pragma unroll
+                for (int c = 0; c < BP; ++c) {
+                    ACC col[BP];
+                    load_vec<T, ACC, BP>(Ls + c * BP, col);
+#pragma unroll
+                    for (int q = 0; q < BP; ++q) t[q] -= col[q ^ c] * xp[c];
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < BP; ++q) xp[q] = 0;
+#pragma unroll
+            for (int c = 0; c < BP; ++c) {
+                ACC col[BP];
+                load_vec<T, ACC, BP>(Li + c * BP, col);
+#pragma unroll
+                for (int q = c; q < BP; ++q) xp[q] += col[q ^ c] * t[c];
+            }
+#pragma unroll
+            for (int q = 0; q < BP; ++q) ys[(j * BP + q) * 32 + lane] = xp[q];
+            __syncwarp();
+            if (j + kLSRing < m) refill(s, j + kLSRing);
+            return true;
+        };
+        {
+            double da[BP], db[BP];
+            load_rows(da, 0);
+            load_rows(db, 1);
+            for (int j = 0; j < m && ok; j += 2) {
+                ok = fstep(j, da);
+                if (ok && j + 1 < m) ok = fstep(j + 1, db);
+            }
+        }
+
+        // backward sweep: z_j = Linv_j^T (y_j - L_{j+1,j}^T z_{j+1})
+        if (ok) {
+            ACC zn[BP];
+#pragma unroll
+            for (int q = 0; q < BP; ++q) zn[q] = 0;
+            auto load_back = [&](ACC (&y)[BP], double (&rr)[BP], int j) {
+#pragma unroll
+                for (int q = 0; q < BP; ++q) {
+                    const int row = j * BP + q;
+                    y[q] = j >= 0 ? ys[row * 32 + lane] : (ACC)0;
+                    if (POST) rr[q] = (j >= 0 && row < nI && act) ? r[(int64_t)gI[row] * K + lane] : 0.0;
+                }
+            };
+            auto bstep = [&](int j, ACC (&y)[BP], double (&rr)[BP]) -> bool {
+                ACC t[BP];
+                double rc[BP];
+#pragma unroll
+                for (int q = 0; q < BP; ++q) {
+                    t[q] = y[q];
+                    if (POST) rc[q] = rr[q];
+                }
+                load_back(y, rr, j - 2);
+                const int s = j % kLSRing;
+                if (j < m - kLSRing && !wait_slot(s)) return false;
+                if (j < m - 1) {
+                    const T *Ls1 = ring + (size_t)((j + 1) % kLSRing) * 2 * BB + BB;
+#pragma unroll
+                    for (int c = 0; c < BP; ++c) {
+                        ACC col[BP];
+                        load_vec<T, ACC, BP>(Ls1 + c * BP, col);
+                        ACC a = 0;
+#pragma unroll
+                        for (int q = 0; q < BP; ++q) a += col[q ^ c] * zn[q];
+                        t[c] -= a;
+                    }
+                }
+                const T *Li = ring + (size_t)s * 2 * BB;
+#pragma unroll
+                for (int c = 0; c < BP; ++c) {
+                    ACC col[BP];
+                    load_vec<T, ACC, BP>(Li + c * BP, col);
+                    ACC a = 0;
+#pragma unroll
+                    for (int q = c; q < BP; ++q) a += col[q ^ c] * t[q];
+                    zn[c] = a;
+                }
+                if (POST) {
+#pragma unroll
+                    for (int q = 0; q < BP; ++q) {
+                        const int row = j * BP + q;
+                        if (row < nI && act) {
+                            const double zv = to_f64(zn[q]);
+                            z[(int64_t)gI[row] * K + lane] = zv;
+                            acc = fma(rc[q], zv, acc);
+                        }
+                    }
+                } else {
+                    // A_{Gamma I} x_I: this block's entries
+#pragma unroll
+                    for (int q = 0; q < BP; ++q) bsm[q * 32 + lane] = zn[q];
+                    const int e1 = bst[j + 1];
+                    for (int e = bst[j]; e < e1; ++e) {
+                        const int k = srt[e], pr = gP[k];
+                        vG[(pr >> 16) * 32 + lane] += cvs[k] * bsm[((pr & 0xffff) - j * BP) * 32 + lane];
+                    }
+                }
+                __syncwarp();
+                if (j <= m - 2 && j + 1 - kLSRing >= 0) refill((j + 1) % kLSRing, j + 1 - kLSRing);
+                return true;
+            };
+            ACC ya[BP], yb[BP];
+            double ra[BP], rb[BP];
+            load_back(ya, ra, m - 1);
+            load_back(yb, rb, m - 2);
+            for (int j = m - 1; j >= 0 && ok; j -= 2) {
+                ok = bstep(j, ya, ra);
+                if (ok && j - 1 >= 0) ok = bstep(j - 1, yb, rb);
+            }
+        }
+        if (ok) {
+            if (POST) {
+                if (act) {
+                    for (int e = 0; e < nown; ++e) {
+                        const int64_t o = (int64_t)gO[2 * e + 1] * K + lane;
+                        const double zv = to_f64(vG[gO[2 * e] * 32 + lane]);
+                        z[o] = zv;
+                        acc = fma(r[o], zv, acc);
+                    }
+                }
+            } else if (act) {
+                for (int q = 0; q < nG; ++q) {
+                    const ACC v = vG[q * 32 + lane];
+                    if (v != (ACC)0) atomicAdd(&B.rB[(int64_t)gGi[q] * K + lane], -to_f64(v));
+                }
+            }
+        }
+    }
+    if (live && !ok) {
+        if (lane == 0) atomicExch(L.err, 1);
+        for (int s = 0; s < kLSRing; ++s)   // bounded: copies in flight land before the warp exits
+            if ((pend >> s) & 1u) mbar_wait(&bars[s], (ph >> s) & 1u);
+        mbar_wait(&bars[kLSRing], 0);
+    }
+    if (POST && rz.sc) {
+        // per-block partials (the warps' in a fixed order), summed over the
+        // blocks in a fixed order by the block that finishes last
+        red[warp * 32 + lane] = (live && act) ? acc : 0.0;
+        __syncthreads();
+        if (warp == 0) {
+            double t = 0.0;
+#pragma unroll
+            for (int w = 0; w < kLSW; ++w) t += red[w * 32 + lane];
+            if (act) rz.part[(int64_t)blockIdx.x * K + lane] = t;
+            __threadfence();
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) *flag = atomicAdd(rz.counter, 1u) == gridDim.x - 1u;
+        __syncthreads();
+        if (!*flag) return;
+        __threadfence();
+        double t = 0.0;
+        if (act) {
+            int sb = warp;
+            for (; sb + 7 * kLSW < (int)gridDim.x; sb += 8 * kLSW) {
+                double v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) v[u] = __ldcg(&rz.part[(int64_t)(sb + u * kLSW) * K + lane]);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) t += v[u];
+            }
+            for (; sb < (int)gridDim.x; sb += kLSW) t += __ldcg(&rz.part[(int64_t)sb * K + lane]);
+        }
+        red[warp * 32 + lane] = t;
+        __syncthreads();
+        if (warp == 0 && act) {
+            double tot = 0.0;
+#pragma unroll
+            for (int w = 0; w < kLSW; ++w) tot += red[w * 32 + lane];
+            BatchScalars *sc = rz.sc;
+            if (!sc->done[lane]) {
+                const double beta = sc->fresh[lane] ? 0.0 : tot / sc->rho[lane];
+                sc->fresh[lane] = 0;
+                sc->hold[lane] = 0;          // joins the next direction update
+                sc->beta[lane] = beta;
+                if (sc->it[lane] > 0) rz.betas[(int64_t)(sc->it[lane] - 1) * K + lane] = beta;
+                sc->rho[lane] = tot;
+            }
+        }
+        if (threadIdx.x == 0) *rz.counter = 0u;
+    }
+}
+
 // Batched Dirichlet solves for substructures whose factor does not fit in
 // shared memory (large or irregular cells).  Persistent blocks, one launch
 // per size bucket (the substructures whose blocks take the same number of
@@ -1458,6 +1815,34 @@ void dir_b(const DevLevel &L, const BatchLevel &B, bool post, const double *r, d
     else dir_b_launch<T, ACC, 32>(L, B, post, r, z, skip, s, rz);
 }
 
+// The lane-per-right-hand-side kernel (k_dir_ls) takes FP32 accumulation and
+// uniform blocks of 8 or 16 rows.
+template <class T, class ACC> size_t lane_smem(const DevLevel &L) {
+    if (!std::is_same<ACC, float>::value || !(L.bp == 8 || L.bp == 16) || !L.irec) return 0;
+    return L.bp == 8 ? LaneSmem<T, 8>::of(L).total : LaneSmem<T, 16>::of(L).total;
+}
+
+template <class T, class ACC>
+void dir_ls(const DevLevel &L, const BatchLevel &B, bool post, const double *r, double *z, const int *skip,
+            cudaStream_t s, const RzBatch *rz = nullptr) {
+    if constexpr (std::is_same<ACC, float>::value) {
+        if (!B.ys) throw Error(BDDC_E_STATE, "lane Dirichlet kernel without its scratch");
+        const RzBatch none{nullptr, nullptr, nullptr, nullptr};
+        const RzBatch rzv = (post && rz) ? *rz : none;
+        const size_t sm = lane_smem<T, ACC>(L);
+        const int grid = (L.nsub + kLSW - 1) / kLSW;
+        if (L.bp == 8) {
+            if (post) launch_plain(k_dir_ls<T, 8, true>, grid, 32 * kLSW, sm, s, L, B, r, z, skip, rzv);
+            else launch_plain(k_dir_ls<T, 8, false>, grid, 32 * kLSW, sm, s, L, B, r, z, skip, rzv);
+        } else {
+            if (post) launch_plain(k_dir_ls<T, 16, true>, grid, 32 * kLSW, sm, s, L, B, r, z, skip, rzv);
+            else launch_plain(k_dir_ls<T, 16, false>, grid, 32 * kLSW, sm, s, L, B, r, z, skip, rzv);
+        }
+    } else {
+        throw Error(BDDC_E_STATE, "lane Dirichlet kernel in FP64");
+    }
+}
+
 template <class T, class ACC>
 void neu_b(const DevLevel &L, const BatchLevel &B, int prec, const double *r, const int *skip,
            cudaStream_t s) {
@@ -1509,8 +1894,13 @@ struct BatchRoute {
     bool dir_stream = false;   // the streaming Dirichlet kernel
     bool stream_fits = false, bg_fits = false;   // the streaming / chunked kernels could run
     bool pre_tc = false, post_tc = false;   // the tensor-core products (tc_kernels.cu)
+    bool lane_fits = false, dir_lane = false;   // the lane-per-right-hand-side Dirichlet kernel
     bool ok = false;
 };
+
+// Bit of DevLevel::route_pref that selects the lane-per-right-hand-side
+// Dirichlet kernel in precision index pi.
+constexpr int lane_bit(int pi) { return 1 << (6 + pi); }
 
 // BDDC_BATCH_STREAM=1 routes every level that the streaming / chunked
 // kernels can take to them, also where the staged kernels fit (read when a
@@ -1540,7 +1930,15 @@ template <class T, class ACC> BatchRoute route_t(const DevLevel &L, int prec) {
     if ((force_stream() || pneu) && bg) R.neu_staged = R.avg_staged = false;
     R.pre_tc = tc_route(L, prec, false);
     R.post_tc = tc_route(L, prec, true);
-    R.ok = (R.dir_staged || R.dir_stream || (R.pre_tc && R.post_tc)) && (R.neu_staged || bg) && (R.avg_staged || bg);
+    const size_t ls = lane_smem<T, ACC>(L);
+    R.lane_fits = ls > 0 && ls <= kSmemMaxB;
+    R.dir_lane = R.lane_fits && (L.route_pref & lane_bit(pi));
+    if (const char *e = std::getenv("BDDC_DIR_LANE")) {   // "1" / "0": the lane kernel where it fits, or never
+        if (e[0] == '1') R.dir_lane = R.lane_fits;
+        if (e[0] == '0') R.dir_lane = false;
+    }
+    if (R.dir_lane) R.dir_staged = R.dir_stream = false;
+    R.ok = (R.dir_staged || R.dir_stream || R.dir_lane || (R.pre_tc && R.post_tc)) && (R.neu_staged || bg) && (R.avg_staged || bg);
     return R;
 }
 
@@ -1553,6 +1951,10 @@ BatchRoute route(const DevLevel &L, int prec) {
 }  // namespace
 
 bool batch_path(const DevLevel &L, int prec) { return route(L, prec).ok; }
+
+bool batch_lane(const DevLevel &L) {
+    return lane_smem<float, float>(L) > 0 && lane_smem<float, float>(L) <= kSmemMaxB;
+}
 
 bool batch_streams(const DevLevel &L) {
     for (int prec : {BDDC_PREC_FP64, BDDC_PREC_FP32, BDDC_PREC_BF16}) {
@@ -1654,6 +2056,7 @@ void pre_b(const DevLevel &L, const BatchLevel &B, int prec, const double *r, co
     const BatchRoute R = route_t<T, ACC>(L, prec);
     if (ev) cudaEventRecord(ev[0], s);
     if (R.pre_tc) tc_dir_b(L, B, prec, false, r, nullptr, skip, nullptr, s);
+    else if (R.dir_lane) dir_ls<T, ACC>(L, B, false, r, nullptr, skip, s);
     else if (R.dir_staged) dir_b<T, ACC>(L, B, false, r, nullptr, skip, s);
     else dir_bs<T, ACC>(L, B, false, r, nullptr, skip, nullptr, s);
     if (ev) cudaEventRecord(ev[1], s);
@@ -1671,6 +2074,7 @@ void post_b(const DevLevel &L, const BatchLevel &B, int prec, const double *r, d
     else launch_plain(k_avg_bg<T, ACC>, L.nsub, kNBT, neu_bg_smem<T, ACC>(L, B.chunk), s, L, B, pidx_b(prec), skip);
     if (ev) cudaEventRecord(ev[1], s);
     if (R.post_tc) tc_dir_b(L, B, prec, true, r, z, skip, rz, s);
+    else if (R.dir_lane) dir_ls<T, ACC>(L, B, true, r, z, skip, s, rz);
     else if (R.dir_staged) dir_b<T, ACC>(L, B, true, r, z, skip, s, rz);
     else dir_bs<T, ACC>(L, B, true, r, z, skip, rz, s);
     if (ev) cudaEventRecord(ev[2], s);
@@ -1706,28 +2110,53 @@ void tune_route_t(DevLevel &L, BatchLevel &B, int prec, const double *r, double 
         L.route_pref = std::atoi(bits);
         return;
     }
-    for (int part = 0; part < 2; ++part) {            // 0: Dirichlet, 1: Neumann and averaging
-        const int bit = 1 << (2 * pi + part);
+    auto steps = [&] {            // the level's pre- and post-correction steps
+        pre_b<T, ACC>(L, B, prec, r, nullptr, s, nullptr);
+        post_b<T, ACC>(L, B, prec, r, z, nullptr, s, nullptr, nullptr);
+    };
+    {
+        // Dirichlet kernel: staged, lane per right-hand side, or streaming,
+        // among those that fit
+        const int sbit = 1 << (2 * pi), lbit = lane_bit(pi);
+        L.route_pref &= ~(sbit | lbit);
+        const BatchRoute R0 = route_t<T, ACC>(L, prec);
+        if (R0.dir_staged && !(R0.pre_tc && R0.post_tc)) {
+            int cand[3] = {0, 0, 0}, nc = 1;
+            if (R0.lane_fits && B.ys) cand[nc++] = lbit;
+            if (R0.stream_fits && B.ys) cand[nc++] = sbit;
+            int pick = 0;
+            if (forced) {
+                if (forced[0] == 's' && forced[1] == 't' && forced[2] == 'r' && R0.stream_fits && B.ys) pick = sbit;
+            } else if (nc > 1) {
+                double best = 1e30;
+                for (int i = 0; i < nc; ++i) {
+                    L.route_pref = (L.route_pref & ~(sbit | lbit)) | cand[i];
+                    const double t = time3(s, steps);
+                    if (t < best) best = t, pick = cand[i];
+                }
+            }
+            L.route_pref = (L.route_pref & ~(sbit | lbit)) | pick;
+        }
+    }
+    {
+        // Neumann and averaging kernels: staged or chunked
+        const int bit = 1 << (2 * pi + 1);
         L.route_pref &= ~bit;
         const BatchRoute R0 = route_t<T, ACC>(L, prec);
-        const bool both = part == 0 ? (R0.dir_staged && R0.stream_fits && B.ys && !(R0.pre_tc && R0.post_tc))
-                                    : ((R0.neu_staged || R0.avg_staged) && R0.bg_fits);
-        if (!both) continue;
-        if (forced) {
-            if (forced[0] == 's' && forced[1] == 't' && forced[2] == 'r') L.route_pref |= bit;
-            continue;
+        if ((R0.neu_staged || R0.avg_staged) && R0.bg_fits) {
+            if (forced) {
+                if (forced[0] == 's' && forced[1] == 't' && forced[2] == 'r') L.route_pref |= bit;
+            } else {
+                double t[2];
+                for (int v = 0; v < 2; ++v) {
+                    if (v) L.route_pref |= bit;
+                    else L.route_pref &= ~bit;
+                    t[v] = time3(s, steps);
+                }
+                if (t[1] < t[0]) L.route_pref |= bit;
+                else L.route_pref &= ~bit;
+            }
         }
-        double t[2];
-        for (int v = 0; v < 2; ++v) {
-            if (v) L.route_pref |= bit;
-            else L.route_pref &= ~bit;
-            t[v] = time3(s, [&] {            // the level's pre- and post-correction steps
-                pre_b<T, ACC>(L, B, prec, r, nullptr, s, nullptr);
-                post_b<T, ACC>(L, B, prec, r, z, nullptr, s, nullptr, nullptr);
-            });
-        }
-        if (t[1] < t[0]) L.route_pref |= bit;
-        else L.route_pref &= ~bit;
     }
 }
 
@@ -1791,6 +2220,11 @@ void prepare_batch_kernels() {
 #define BDDC_DIR_B(T, A, BPV)                                   \
     BDDC_SMEM_ATTR_B((k_dir_b<T, A, BPV, false>));              \
     BDDC_SMEM_ATTR_B((k_dir_b<T, A, BPV, true>));
+#define BDDC_DIR_LS(T, BPV)                                     \
+    BDDC_SMEM_ATTR_B((k_dir_ls<T, BPV, false>));                \
+    BDDC_SMEM_ATTR_B((k_dir_ls<T, BPV, true>));
+    BDDC_DIR_LS(float, 8) BDDC_DIR_LS(float, 16) BDDC_DIR_LS(__nv_bfloat16, 8) BDDC_DIR_LS(__nv_bfloat16, 16)
+#undef BDDC_DIR_LS
     BDDC_DIR_B(double, double, 8) BDDC_DIR_B(double, double, 16) BDDC_DIR_B(double, double, 32)
     BDDC_DIR_B(float, float, 8) BDDC_DIR_B(float, float, 16) BDDC_DIR_B(float, float, 32)
     BDDC_DIR_B(__nv_bfloat16, float, 8) BDDC_DIR_B(__nv_bfloat16, float, 16) BDDC_DIR_B(__nv_bfloat16, float, 32)

@@ -1219,7 +1219,7 @@ BatchWs &batch_ws(bddc_ctx *C, Workspace &W) {
         BDDC_CUDA_TRY(cudaMemsetAsync(B.rB, 0, sizeof(double) * ni * KB, W.stream));
         BDDC_CUDA_TRY(cudaMemsetAsync(B.uB, 0, sizeof(double) * ni * KB, W.stream));
         BDDC_CUDA_TRY(cudaMemsetAsync(B.rcv, 0, sizeof(double) * ncp * KB, W.stream));
-        if (batch_streams(D)) {
+        if (batch_streams(D) || batch_lane(D)) {
             B.ys = A.alloc_n<double>(std::max<int64_t>(D.n_y, 1) * KB);
             batch_prepare_level(D);
         }

@@ -116,7 +116,8 @@ struct DevLevel {
     int max_ld = 0;            // largest leading dimension of a factor block
     // the batch autotuner's route per precision index p (FP64 0, FP32 1,
     // BF16 2): bit 2p: the streaming Dirichlet kernel where the staged one
-    // also fits; bit 2p+1: the chunked Neumann / averaging kernels likewise
+    // also fits; bit 2p+1: the chunked Neumann / averaging kernels likewise;
+    // bit 6+p: the lane-per-right-hand-side Dirichlet kernel likewise
     int route_pref = 0;
     SizeBuckets bk;            // size buckets (n = 0: a block needs more than 16 warps)
     int *bperm = nullptr;      // substructures in bucket order
@@ -288,8 +289,9 @@ struct BatchLevel {
     double *w = nullptr;       // [sum nG][K]
     double *rcv = nullptr;     // [max(nc, ld_top)][K], zero beyond nc
     double *ucv = nullptr;     // [max(nc, ld_top)][K]
-    // per-substructure sweep scratch of the streaming Dirichlet kernel,
-    // [n_y rows][32] in the accumulator type (null when no precision streams)
+    // per-substructure sweep scratch of the streaming and lane-per-right-
+    // hand-side Dirichlet kernels, [n_y rows][32] in the accumulator type
+    // (null when neither can run)
     void *ys = nullptr;
 };
 struct BatchScalars {
@@ -314,10 +316,12 @@ struct RzBatch {
 // Whether a level's operators fit the batched kernels' shared-memory slices.
 bool batch_path(const DevLevel &L, int prec);
 bool batch_streams(const DevLevel &L);   // some precision can take the streaming Dirichlet kernel
+bool batch_lane(const DevLevel &L);      // FP32 / BF16 can take the lane-per-right-hand-side Dirichlet kernel
 void batch_prepare_level(const DevLevel &L);   // launch shapes of the streaming kernel, before any capture
 // Autotuning of one level's batch kernels on the problem's own operators
 // (CUDA events, three launches after one untimed): for every precision,
-// staged against streaming Dirichlet kernels and staged against chunked
+// the staged, lane-per-right-hand-side and streaming Dirichlet kernels, and
+// staged against chunked
 // Neumann / averaging kernels where both fit (L.route_pref); in precision
 // prec, the size buckets of the streaming Dirichlet kernel one after another
 // or at once (B.bucket_par; needs B.fork), and the row chunk of the

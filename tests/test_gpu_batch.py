@@ -241,3 +241,40 @@ def test_batch_routes_both_match_oracle(lib, monkeypatch, name, route):
                 assert _relerr(Zm[j], Z[j]) <= tol, (prec, j)
     finally:
         P.close()
+
+
+@pytest.mark.parametrize("name", ["channels_64", "channels_96_ragged", "three_level_64"])
+def test_lane_sweeps_match_oracle(lib, monkeypatch, name):
+    """The Dirichlet kernel with a lane per right-hand side (a warp per
+    substructure runs both sweeps, the factor streamed through a ring;
+    BDDC_DIR_LANE=1), on every level where it fits (blocks of 16 rows on the
+    channel problems, 8 on the three-level one) and for both corrections
+    (BDDC_TC=0): FP32 applies within 1e-5 and
+    BF16 within 1e-2 of the oracle's apply, for a full batch of 32 and a
+    ragged one of 5, and the FP32 batched PCG meets the tolerance by its true
+    residual with the oracle's iteration count (+-1)."""
+    monkeypatch.setenv("BDDC_DIR_LANE", "1")
+    monkeypatch.setenv("BDDC_TC", "0")
+    wl = WL[name]
+    H = _oracle(name)
+    P = lib.Problem.from_workload(wl)
+    try:
+        for K in (32, 5):
+            R = inputs.normal_rhs(wl.n_dof, 43 + K, K)
+            ref = [H.apply(R[j]) for j in range(K)]
+            Rt = torch.tensor(R, device="cuda")
+            for prec, tol in (("fp32", 1e-5), ("bf16", 1e-2)):
+                P.set_precision(prec)
+                Z = P.apply(Rt).cpu().numpy()
+                for j in range(K):
+                    assert _relerr(Z[j], ref[j]) <= tol, (prec, K, j)
+        P.set_precision("fp32")
+        b = wl.rhs()
+        res = opcg.pcg(H.A, b, H.apply, rtol=1e-8)
+        B = np.stack([b] + [inputs.normal_rhs(wl.n_dof, 90 + j) for j in range(7)])
+        X, infos = P.solve(torch.tensor(B, device="cuda"), rtol=1e-8)
+        assert infos[0]["status"] == 0 and abs(infos[0]["iters"] - res.iters) <= 1
+        for i in infos:
+            assert i["status"] == 0 and i["relres_true"] <= 1e-8
+    finally:
+        P.close()
