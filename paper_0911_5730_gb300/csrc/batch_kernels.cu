@@ -422,7 +422,7 @@ __global__ void __launch_bounds__(32 * lanes_per_rhs<BP>()) k_dir_b(DevLevel L, 
 constexpr int kLSW = 4, kLSRing = 4;
 
 template <class T, int BP> struct LaneSmem {
-    size_t slot, ring, bsm, vg, rec, cvs, srt, bst, bars, warp, total;
+    size_t slot, ring, bsm, vg, rec, srt, bst, bars, warp, total;
     __host__ __device__ static LaneSmem of(const DevLevel &L) {
         LaneSmem m;
         m.slot = al16(2 * (size_t)BP * BP * sizeof(T));
@@ -430,11 +430,10 @@ template <class T, int BP> struct LaneSmem {
         m.bsm = al16(sizeof(float) * BP * 32);
         m.vg = al16(sizeof(float) * (size_t)(L.max_nG > 0 ? L.max_nG : 1) * 32);
         m.rec = al16((size_t)L.max_irec);
-        m.cvs = al16(sizeof(float) * (size_t)(L.max_coo > 0 ? L.max_coo : 1));
         m.srt = al16(2 * (size_t)(L.max_coo > 0 ? L.max_coo : 1));
         m.bst = al16(2 * (size_t)(L.max_m + 2));
         m.bars = al16(8 * (kLSRing + 1));
-        m.warp = m.ring + m.bsm + m.vg + m.rec + m.cvs + m.srt + m.bst + m.bars;
+        m.warp = m.ring + m.bsm + m.vg + m.rec + m.srt + m.bst + m.bars;
         m.total = kLSW * m.warp + al16(8 * 32 * kLSW + 16);
         return m;
     }
@@ -458,7 +457,6 @@ __global__ void __launch_bounds__(32 * kLSW) k_dir_ls(DevLevel L, BatchLevel B, 
     ACC *bsm = reinterpret_cast<ACC *>(p);       p += ly.bsm;
     ACC *vG = reinterpret_cast<ACC *>(p);        p += ly.vg;
     unsigned char *rec = p;                      p += ly.rec;
-    ACC *cvs = reinterpret_cast<ACC *>(p);       p += ly.cvs;
     unsigned short *srt = reinterpret_cast<unsigned short *>(p);   p += ly.srt;
     unsigned short *bst = reinterpret_cast<unsigned short *>(p);   p += ly.bst;
     unsigned long long *bars = reinterpret_cast<unsigned long long *>(p);   // ring slots, then the record
@@ -498,31 +496,66 @@ __global__ void __launch_bounds__(32 * kLSW) k_dir_ls(DevLevel L, BatchLevel B, 
         const int *gP = reinterpret_cast<const int *>(rec + lay.pr);
         const int *gO = reinterpret_cast<const int *>(rec + lay.ow);
         float *ys = reinterpret_cast<float *>(B.ys) + L.offY[sub] * 32;
-        for (int e = lane; e < ncoo; e += 32) cvs[e] = from_f64<ACC>(gC[e]);
+        // post: the first 32 rows of u_B in flight while the entries are sorted
+        double uv[32];
+        if (POST) {
+#pragma unroll
+            for (int u = 0; u < 32; ++u) uv[u] = (u < nG && act) ? B.uB[(int64_t)gGi[u] * K + lane] : 0.0;
+        }
+        // the coupling values narrowed in place: entry e's binary32 in the
+        // first half of its binary64 slot (read and written by one lane)
+        ACC *cvs = reinterpret_cast<ACC *>(rec + lay.cv);
+        for (int e = lane; e < ncoo; e += 32) {
+            const double v = gC[e];
+            cvs[2 * e] = from_f64<ACC>(v);
+        }
         {
-            // entries by the block of their interior row, in entry order within a block
-            int run = 0;
-            for (int b = 0; b < m; ++b) {
-                if (lane == 0) bst[b] = (unsigned short)run;
-                for (int c0 = 0; c0 < ncoo; c0 += 32) {
-                    const int e = c0 + lane;
-                    const int key = e < ncoo ? (gP[e] & 0xffff) / BP : -1;
-                    const unsigned mask = __ballot_sync(0xffffffffu, key == b);
-                    if (key == b) srt[run + __popc(mask & ((1u << lane) - 1u))] = (unsigned short)e;
-                    run += __popc(mask);
+            // entries by the block of their interior row, in entry order
+            // within a block: counts (shared atomics), their prefix sums, then
+            // each chunk of 32 entries placed in order (lanes of one block
+            // found by __match_any_sync, ranked by lane)
+            int *cnt = reinterpret_cast<int *>(bsm);   // [m + 1]; bsm is free until the sweeps
+            for (int b = lane; b <= m; b += 32) cnt[b] = 0;
+            __syncwarp();
+            for (int e = lane; e < ncoo; e += 32) atomicAdd(&cnt[(gP[e] & 0xffff) / BP], 1);
+            __syncwarp();
+            if (lane == 0) {
+                int run = 0;
+                for (int b = 0; b < m; ++b) {
+                    const int c = cnt[b];
+                    bst[b] = (unsigned short)run;
+                    cnt[b] = run;
+                    run += c;
                 }
+                bst[m] = (unsigned short)run;
             }
-            if (lane == 0) bst[m] = (unsigned short)run;
+            __syncwarp();
+            for (int c0 = 0; c0 < ncoo; c0 += 32) {
+                const int e = c0 + lane;
+                const int key = e < ncoo ? (gP[e] & 0xffff) / BP : -1;
+                const unsigned peers = __match_any_sync(0xffffffffu, key);
+                const unsigned below = peers & ((1u << lane) - 1u);
+                const int base = key >= 0 ? cnt[key] : 0;
+                __syncwarp();
+                if (key >= 0) {
+                    srt[base + __popc(below)] = (unsigned short)e;
+                    if (below == 0) cnt[key] = base + __popc(peers);
+                }
+                __syncwarp();
+            }
         }
         if (POST) {
-            for (int q0 = 0; q0 < nG; q0 += 16) {
-                double v[16];
+            for (int q0 = 0; q0 < nG; q0 += 32) {
 #pragma unroll
-                for (int u = 0; u < 16; ++u)
-                    v[u] = (q0 + u < nG && act) ? B.uB[(int64_t)gGi[q0 + u] * K + lane] : 0.0;
+                for (int u = 0; u < 32; ++u)
+                    if (q0 + u < nG) vG[(q0 + u) * 32 + lane] = from_f64<ACC>(uv[u]);
+                if (q0 + 32 < nG) {
 #pragma unroll
-                for (int u = 0; u < 16; ++u)
-                    if (q0 + u < nG) vG[(q0 + u) * 32 + lane] = from_f64<ACC>(v[u]);
+                    for (int u = 0; u < 32; ++u) {
+                        const int q = q0 + 32 + u;
+                        uv[u] = (q < nG && act) ? B.uB[(int64_t)gGi[q] * K + lane] : 0.0;
+                    }
+                }
             }
         } else {
             for (int q = 0; q < nG; ++q) {
@@ -565,7 +598,7 @@ __global__ void __launch_bounds__(32 * kLSW) k_dir_ls(DevLevel L, BatchLevel B, 
                 const int e1 = bst[j + 1];
                 for (int e = bst[j]; e < e1; ++e) {
                     const int k = srt[e], pr = gP[k];
-                    bsm[((pr & 0xffff) - j * BP) * 32 + lane] -= cvs[k] * vG[(pr >> 16) * 32 + lane];
+                    bsm[((pr & 0xffff) - j * BP) * 32 + lane] -= cvs[2 * k] * vG[(pr >> 16) * 32 + lane];
                 }
             }
             ACC t[BP];
@@ -614,23 +647,23 @@ __global__ void __launch_bounds__(32 * kLSW) k_dir_ls(DevLevel L, BatchLevel B, 
             ACC zn[BP];
 #pragma unroll
             for (int q = 0; q < BP; ++q) zn[q] = 0;
-            auto load_back = [&](ACC (&y)[BP], double (&rr)[BP], int j) {
+            auto load_y = [&](ACC (&y)[BP], int j) {
 #pragma unroll
-                for (int q = 0; q < BP; ++q) {
-                    const int row = j * BP + q;
-                    y[q] = j >= 0 ? ys[row * 32 + lane] : (ACC)0;
-                    if (POST) rr[q] = (j >= 0 && row < nI && act) ? r[(int64_t)gI[row] * K + lane] : 0.0;
-                }
+                for (int q = 0; q < BP; ++q) y[q] = j >= 0 ? ys[(j * BP + q) * 32 + lane] : (ACC)0;
             };
-            auto bstep = [&](int j, ACC (&y)[BP], double (&rr)[BP]) -> bool {
-                ACC t[BP];
-                double rc[BP];
+            // column dot products in four partial sums (fixed order)
+            auto dot4 = [](const ACC (&col)[BP], const ACC (&v)[BP], int c, int q0) -> ACC {
+                ACC a[4] = {0, 0, 0, 0};
 #pragma unroll
-                for (int q = 0; q < BP; ++q) {
-                    t[q] = y[q];
-                    if (POST) rc[q] = rr[q];
-                }
-                load_back(y, rr, j - 2);
+                for (int q = 0; q < BP; ++q)
+                    if (q >= q0) a[q & 3] += col[q ^ c] * v[q];
+                return (a[0] + a[1]) + (a[2] + a[3]);
+            };
+            auto bstep = [&](int j, ACC (&y)[BP]) -> bool {
+                ACC t[BP];
+#pragma unroll
+                for (int q = 0; q < BP; ++q) t[q] = y[q];
+                load_y(y, j - 2);
                 const int s = j % kLSRing;
                 if (j < m - kLSRing && !wait_slot(s)) return false;
                 if (j < m - 1) {
@@ -639,10 +672,7 @@ __global__ void __launch_bounds__(32 * kLSW) k_dir_ls(DevLevel L, BatchLevel B, 
                     for (int c = 0; c < BP; ++c) {
                         ACC col[BP];
                         load_vec<T, ACC, BP>(Ls1 + c * BP, col);
-                        ACC a = 0;
-#pragma unroll
-                        for (int q = 0; q < BP; ++q) a += col[q ^ c] * zn[q];
-                        t[c] -= a;
+                        t[c] -= dot4(col, zn, c, 0);
                     }
                 }
                 const T *Li = ring + (size_t)s * 2 * BB;
@@ -650,20 +680,13 @@ __global__ void __launch_bounds__(32 * kLSW) k_dir_ls(DevLevel L, BatchLevel B, 
                 for (int c = 0; c < BP; ++c) {
                     ACC col[BP];
                     load_vec<T, ACC, BP>(Li + c * BP, col);
-                    ACC a = 0;
-#pragma unroll
-                    for (int q = c; q < BP; ++q) a += col[q ^ c] * t[q];
-                    zn[c] = a;
+                    zn[c] = dot4(col, t, c, c);
                 }
                 if (POST) {
 #pragma unroll
                     for (int q = 0; q < BP; ++q) {
                         const int row = j * BP + q;
-                        if (row < nI && act) {
-                            const double zv = to_f64(zn[q]);
-                            z[(int64_t)gI[row] * K + lane] = zv;
-                            acc = fma(rc[q], zv, acc);
-                        }
+                        if (row < nI && act) z[(int64_t)gI[row] * K + lane] = to_f64(zn[q]);
                     }
                 } else {
                     // A_{Gamma I} x_I: this block's entries
@@ -672,7 +695,7 @@ __global__ void __launch_bounds__(32 * kLSW) k_dir_ls(DevLevel L, BatchLevel B, 
                     const int e1 = bst[j + 1];
                     for (int e = bst[j]; e < e1; ++e) {
                         const int k = srt[e], pr = gP[k];
-                        vG[(pr >> 16) * 32 + lane] += cvs[k] * bsm[((pr & 0xffff) - j * BP) * 32 + lane];
+                        vG[(pr >> 16) * 32 + lane] += cvs[2 * k] * bsm[((pr & 0xffff) - j * BP) * 32 + lane];
                     }
                 }
                 __syncwarp();
@@ -680,22 +703,47 @@ __global__ void __launch_bounds__(32 * kLSW) k_dir_ls(DevLevel L, BatchLevel B, 
                 return true;
             };
             ACC ya[BP], yb[BP];
-            double ra[BP], rb[BP];
-            load_back(ya, ra, m - 1);
-            load_back(yb, rb, m - 2);
+            load_y(ya, m - 1);
+            load_y(yb, m - 2);
             for (int j = m - 1; j >= 0 && ok; j -= 2) {
-                ok = bstep(j, ya, ra);
-                if (ok && j - 1 >= 0) ok = bstep(j - 1, yb, rb);
+                ok = bstep(j, ya);
+                if (ok && j - 1 >= 0) ok = bstep(j - 1, yb);
             }
+        }
+        if (ok && POST && rz.sc && act) {
+            // r.z over the interior entries just written (read back by the
+            // lane that wrote them), in four partial sums
+            double a4[4] = {0.0, 0.0, 0.0, 0.0};
+            for (int i0 = 0; i0 < nI; i0 += 32) {
+                double rv[32], zv[32];
+#pragma unroll
+                for (int u = 0; u < 32; ++u) {
+                    const bool in = i0 + u < nI;
+                    const int64_t e = in ? (int64_t)gI[i0 + u] * K + lane : 0;
+                    rv[u] = in ? r[e] : 0.0;
+                    zv[u] = in ? z[e] : 0.0;
+                }
+#pragma unroll
+                for (int u = 0; u < 32; ++u) a4[u & 3] = fma(rv[u], zv[u], a4[u & 3]);
+            }
+            acc = (a4[0] + a4[1]) + (a4[2] + a4[3]);
         }
         if (ok) {
             if (POST) {
                 if (act) {
-                    for (int e = 0; e < nown; ++e) {
-                        const int64_t o = (int64_t)gO[2 * e + 1] * K + lane;
-                        const double zv = to_f64(vG[gO[2 * e] * 32 + lane]);
-                        z[o] = zv;
-                        acc = fma(r[o], zv, acc);
+                    for (int e0 = 0; e0 < nown; e0 += 8) {
+                        double rv[8], zv[8];
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            const int e = e0 + u;
+                            const bool in = e < nown;
+                            const int64_t o = in ? (int64_t)gO[2 * e + 1] * K + lane : 0;
+                            zv[u] = in ? to_f64(vG[gO[2 * e] * 32 + lane]) : 0.0;
+                            if (in) z[o] = zv[u];
+                            rv[u] = in ? r[o] : 0.0;
+                        }
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) acc = fma(rv[u], zv[u], acc);
                     }
                 }
             } else if (act) {
