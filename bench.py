@@ -50,8 +50,8 @@ NCU_TRAFFIC = {
     # k_top_rows (h), k_top_chain (backward), two right-hand sides per cluster
     "top_solve": {"bytes": 8916736, "file": "top_kernels.cu", "src": "a11462098415",
                   "kernel": "k_top_rows + k_top_chain, 4 launches"},
-    "post": {"bytes": 120289536, "file": "batch_kernels.cu", "src": "36e7929654d3",
-             "kernel": "k_dir_b<float, float, 16, 1>"},
+    "post": {"bytes": 180122496, "file": "batch_kernels.cu", "src": "9218cd3c0162",
+             "kernel": "k_dir_ls<float, 16, 1>"},
 }
 
 
