@@ -50,7 +50,7 @@ NCU_TRAFFIC = {
     # k_top_rows (h), k_top_chain (backward), two right-hand sides per cluster
     "top_solve": {"bytes": 8916736, "file": "top_kernels.cu", "src": "a11462098415",
                   "kernel": "k_top_rows + k_top_chain, 4 launches"},
-    "post": {"bytes": 180122496, "file": "batch_kernels.cu", "src": "9218cd3c0162",
+    "post": {"bytes": 180157056, "file": "batch_kernels.cu", "src": "acfb4d52fbb4",
              "kernel": "k_dir_ls<float, 16, 1>"},
 }
 

@@ -1867,6 +1867,7 @@ void dir_b(const DevLevel &L, const BatchLevel &B, bool post, const double *r, d
 // uniform blocks of 8 or 16 rows.
 template <class T, class ACC> size_t lane_smem(const DevLevel &L) {
     if (!std::is_same<ACC, float>::value || !(L.bp == 8 || L.bp == 16) || !L.irec) return 0;
+    if (L.max_m + 1 > 32 * L.bp) return 0;   // the sort's block counts live in the block buffer
     return L.bp == 8 ? LaneSmem<T, 8>::of(L).total : LaneSmem<T, 16>::of(L).total;
 }
 
@@ -1982,7 +1983,7 @@ template <class T, class ACC> BatchRoute route_t(const DevLevel &L, int prec) {
     R.lane_fits = ls > 0 && ls <= kSmemMaxB;
     R.dir_lane = R.lane_fits && (L.route_pref & lane_bit(pi));
     if (const char *e = std::getenv("BDDC_DIR_LANE")) {   // "1" / "0": the lane kernel where it fits, or never
-        if (e[0] == '1') R.dir_lane = R.lane_fits;
+        if (e[0] == '1') R.dir_lane = R.lane_fits && batch_lane(L);
         if (e[0] == '0') R.dir_lane = false;
     }
     if (R.dir_lane) R.dir_staged = R.dir_stream = false;
@@ -2001,7 +2002,8 @@ BatchRoute route(const DevLevel &L, int prec) {
 bool batch_path(const DevLevel &L, int prec) { return route(L, prec).ok; }
 
 bool batch_lane(const DevLevel &L) {
-    return lane_smem<float, float>(L) > 0 && lane_smem<float, float>(L) <= kSmemMaxB;
+    auto fits = [](size_t b) { return b > 0 && b <= kSmemMaxB; };
+    return fits(lane_smem<float, float>(L)) || fits(lane_smem<__nv_bfloat16, float>(L));
 }
 
 bool batch_streams(const DevLevel &L) {
