@@ -658,7 +658,10 @@ def gpu_arm(a):
                       "top_form": top_form, "top_blocks": q.get("top_blocks", 0),
                       "route_bits_level1": P.query(level=None)["tuned_route"][0],
                       "buckets_at_once": P.query(level=None)["tuned_buckets_at_once"],
-                      "neumann_chunk_bytes": P.query(level=None)["tuned_neu_chunk"][0]},
+                      "neumann_chunk_bytes": P.query(level=None)["tuned_neu_chunk"][0],
+                      # single right-hand side: the dense top product's launch shape
+                      # (0: 4x2, 1: 8x1, 2: 2x4, 3: 4x4 warps per row x rows per block)
+                      "top_product_single_rhs_shape": P.query(level=None)["tuned_symv"]},
         "gpu_launches": launches,
         "cpu_baseline": cpu,
         "clocks": clocks,
