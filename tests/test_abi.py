@@ -66,3 +66,34 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert code == -1
     assert lib.bddc_apply(None, None, None, 1, 1, None) == -1
     assert lib.bddc_pcg_solve(None, None, None, 1, 1, 1e-8, 10, None, None) == -1
+
+
+def test_binding_struct_layouts_match_header(tmp_path):
+    """The ctypes structures of the binding have the sizes and field offsets
+    that a C compiler gives the header's structures (a C program built from
+    include/bddc.h prints them)."""
+    import shutil
+    import subprocess
+    from paper_0911_5730_gb300 import bddc
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    pairs = {"bddc_mesh": bddc.Mesh, "bddc_decomp": bddc.Decomp, "bddc_opts": bddc.Opts,
+             "bddc_solve_info": bddc.SolveInfo, "bddc_info": bddc.Info}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "bddc.h"', "int main(void) {"]
+    for cname, py in pairs.items():
+        lines.append('printf("%s sizeof %%zu\\n", sizeof(%s));' % (cname, cname))
+        for f, _ in py._fields_:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (cname, f, cname, f))
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True, capture_output=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, py in pairs.items():
+        assert got[(cname, "sizeof")] == C.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
