@@ -2,7 +2,8 @@
 (two levels), the 1024x1024 three-level problem (log-uniform coefficient per
 8x8 block) and the 2048x2048 three-level problem on 4096 Voronoi cells, all
 set up once and kept on the device, each fed by its own seeded Poisson stream
-of requests of 1-64 N(0,1) right-hand sides, served at once by one server
+of requests of 1-64 N(0,1) right-hand sides (at least one request per
+problem in the window), served at once by one server
 (continuous batching, three engines per problem and precision) that admits
 requests by an HBM budget.
 
@@ -54,14 +55,13 @@ def _budget(wls):
     return int(sum(2 * 2 * 64 * 8 * wl.n_dof for wl in wls))
 
 
-def serve(Ps, wls, load, seconds, seed, budget, cap=None):
-    """One mixed stream over the resident problems Ps (same keys as wls),
-    offered at load x cap[k] / len(Ps) right-hand sides per second per
-    problem (cap: the closed-loop rates, measured here if not given)."""
-    keys = list(Ps)
-    if cap is None:
-        cap = {k: _capacity(Ps[k], wls[k].n_dof, seed + i) for i, k in enumerate(keys)}
-    srv = bddc.Server(hbm_budget=budget, max_slots=1)
+def arrivals(keys, cap, load, seconds, seed):
+    """Per problem a seeded Poisson stream of requests of 1-64 right-hand
+    sides at load x cap[k] / len(keys) right-hand sides per second over
+    `seconds`: lists of (arrival time, right-hand sides, seed of their
+    values).  A problem whose stream draws no request in the window (a slow
+    one in a short window) gets one, of a drawn size at a drawn time, so
+    that every problem is measured."""
     plans = {}
     for i, k in enumerate(keys):
         rng = np.random.default_rng(seed + 100 + i)
@@ -72,14 +72,29 @@ def serve(Ps, wls, load, seconds, seed, budget, cap=None):
             t += rng.exponential(m / rate)
             if t >= seconds:
                 break
-            ev.append((t, m, rng.standard_normal((m, wls[k].n_dof))))
+            ev.append((t, m, int(rng.integers(1 << 31))))
+        if not ev:
+            ev.append((float(rng.uniform(0.0, seconds)), int(rng.integers(1, 65)), int(rng.integers(1 << 31))))
         plans[k] = ev
+    return plans
+
+
+def serve(Ps, wls, load, seconds, seed, budget, cap=None):
+    """One mixed stream over the resident problems Ps (same keys as wls),
+    offered at load x cap[k] / len(Ps) right-hand sides per second per
+    problem (cap: the closed-loop rates, measured here if not given)."""
+    keys = list(Ps)
+    if cap is None:
+        cap = {k: _capacity(Ps[k], wls[k].n_dof, seed + i) for i, k in enumerate(keys)}
+    srv = bddc.Server(hbm_budget=budget, max_slots=1)
+    plans = arrivals(keys, cap, load, seconds, seed)
     # a short window of large requests can offer far more or less work than
     # `load` of the GPU: the arrival times are scaled so that the sampled
     # requests (GPU time at the closed-loop rates) fill `load` of the window
     work = sum(m / cap[k] for k, ev in plans.items() for _, m, _ in ev)
     scale = work / (load * seconds) if work > 0 else 1.0
-    events = sorted(((t * scale, k, m, b) for k, ev in plans.items() for t, m, b in ev), key=lambda e: e[0])
+    events = sorted(((t * scale, k, m, np.random.default_rng(rs).standard_normal((m, wls[k].n_dof)))
+                     for k, ev in plans.items() for t, m, rs in ev), key=lambda e: e[0])
     tickets = []
     lat = {k: [] for k in keys}
     bad = []

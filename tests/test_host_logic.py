@@ -98,3 +98,25 @@ def test_voronoi_partition_properties(nx, cells, group):
     w2 = (nx // cells) ** 2
     assert sizes.min() >= 0.5 * w2 and sizes.max() <= 1.6 * w2
 
+
+
+def test_serving_mix_arrivals():
+    """The mixed serving stream's arrivals (config 5): per problem a seeded
+    Poisson stream of 1-64 right-hand sides per request at its share of the
+    load, the same for the same seed, inside the window, and at least one
+    request for a problem too slow to draw one."""
+    pytest.importorskip("torch")
+    from paper_0911_5730_gb300 import serve_mix
+    cap = {"fast": 2000.0, "slow": 1e-3}
+    a = serve_mix.arrivals(["fast", "slow"], cap, 0.8, 3.0, 5001)
+    b = serve_mix.arrivals(["fast", "slow"], cap, 0.8, 3.0, 5001)
+    assert a == b
+    assert len(a["slow"]) == 1
+    for k, ev in a.items():
+        ts = [t for t, _, _ in ev]
+        assert ts == sorted(ts) or k == "slow"
+        assert all(0.0 <= t < 3.0 for t in ts)
+        assert all(1 <= m <= 64 for _, m, _ in ev)
+    # the fast stream offers about load / problems of its rate over the window
+    offered = sum(m for _, m, _ in a["fast"]) / 3.0
+    assert 0.5 * 800.0 < offered < 1.5 * 800.0
