@@ -60,8 +60,9 @@ def arrivals(keys, cap, load, seconds, seed):
     sides at load x cap[k] / len(keys) right-hand sides per second over
     `seconds`: lists of (arrival time, right-hand sides, seed of their
     values).  A problem whose stream draws no request in the window (a slow
-    one in a short window) gets one, of a drawn size at a drawn time, so
-    that every problem is measured."""
+    one in a short window) gets one at a drawn time, of a drawn size but no
+    more right-hand sides than its stream offers in the window on average,
+    so that every problem is measured without adding much work."""
     plans = {}
     for i, k in enumerate(keys):
         rng = np.random.default_rng(seed + 100 + i)
@@ -74,7 +75,9 @@ def arrivals(keys, cap, load, seconds, seed):
                 break
             ev.append((t, m, int(rng.integers(1 << 31))))
         if not ev:
-            ev.append((float(rng.uniform(0.0, seconds)), int(rng.integers(1, 65)), int(rng.integers(1 << 31))))
+            # no larger than the stream's expected right-hand sides in the window
+            m = min(int(rng.integers(1, 65)), max(1, int(rate * seconds)))
+            ev.append((float(rng.uniform(0.0, seconds)), m, int(rng.integers(1 << 31))))
         plans[k] = ev
     return plans
 

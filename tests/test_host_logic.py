@@ -120,3 +120,43 @@ def test_serving_mix_arrivals():
     # the fast stream offers about load / problems of its rate over the window
     offered = sum(m for _, m, _ in a["fast"]) / 3.0
     assert 0.5 * 800.0 < offered < 1.5 * 800.0
+
+
+def test_serving_mix_bookkeeping_with_a_fake_server(monkeypatch):
+    """serve_mix.serve end to end on the CPU against a stand-in server that
+    completes every request at once: every submitted right-hand side is
+    counted once per problem, none is reported failed, and every problem
+    (also one too slow to draw a request) gets latencies."""
+    pytest.importorskip("torch")
+    from paper_0911_5730_gb300 import serve_mix
+
+    class FakeServer:
+        def __init__(self, hbm_budget=0, max_slots=1):
+            self.n = 0
+
+        def submit(self, P, b, rtol=1e-8):
+            self.n += 1
+            return (P, 1 if np.ndim(b) == 1 else len(b))
+
+        def wait(self, t):
+            _, m = t
+            return None, [{"status": 0, "iters": 1, "relres_true": 1e-9}] * m, 0.5
+
+        def close(self):
+            pass
+
+    monkeypatch.setattr(serve_mix.bddc, "Server", FakeServer)
+
+    class W:
+        n_dof = 16
+
+    keys = ["channels", "blocks", "voronoi"]
+    cap = {"channels": 3000.0, "blocks": 600.0, "voronoi": 50.0}
+    out, _ = serve_mix.serve({k: k for k in keys}, {k: W() for k in keys}, 0.8, 0.3, 7, 0, cap=cap)
+    plans = serve_mix.arrivals(keys, cap, 0.8, 0.3, 7)
+    for k in keys:
+        name = serve_mix.PROBLEMS[k][0]
+        assert out[name]["rhs"] == sum(m for _, m, _ in plans[k])
+        assert out[name]["requests"] == len(plans[k]) >= 1
+        assert out[name]["latency_ms"]["p50"] == 0.5
+    assert out["all"]["failed_rhs"] == 0
